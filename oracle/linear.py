@@ -1,0 +1,245 @@
+"""ORACLE (test infrastructure only) -- RIDG for linear advection q_t + a . grad q = 0.
+
+Prediction (Sec. 2.2, eq. pred_full_system).  On the region R_i of 3^d space-time
+elements every residual is divided by |T_j| and written in reference coordinates
+(x = x_j + h xi / 2, t = t^n + dt (tau + 1) / 2).  With nu_d = a_d dt / h_d and the 1D
+tables D[a, b] = int phi_a' phi_b and traces phi(+-1), the pieces of eq.
+pred_full_system become, per region element j and test function Psi_k = psi_alpha Phi_s:
+
+  time term       [psi_alpha(1) psi_gamma(1) - D_{alpha gamma}] delta_{s s'}  W_j
+  internal flux   - sum_d nu_d delta_{alpha gamma} (D along dim d)           W_j
+  surface flux    Rusanov flux on faces interior to R_i; for linear flux it is the
+                  upwind flux a+ w_L + a- w_R (a+ = max(a,0), a- = min(a,0)).
+                  On the boundary of R_i only the trace internal to R_i is used
+                  (F(w_int) . n), which insulates the region.
+  causal source   - psi_alpha(-1) Q^n_{j, s}
+
+The region system A W_R = B Q_R is assembled from these Kronecker factors, factored
+once (it does not depend on the element on a uniform periodic mesh) and solved for every
+element's region; only the centre element's W_i is kept (Sec. 2.2, fig. RIDG_2D).
+
+Correction (Sec. 2.3): with W-bar the tau-mean (psi_0) block of W_i,
+  Q^{n+1}_i = Q^n_i + sum_d nu_d (D along d) W-bar_i
+              - sum_d [ phi(+1) (x)_d F_{i+1/2} - phi(-1) (x)_d F_{i-1/2} ]
+where the face value F_{i+1/2} = nu+ trace_{+1}(W-bar_i) + nu- trace_{-1}(W-bar_{i+e_d})
+is computed once per face and applied to both neighbours.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+
+from . import basis
+
+
+# ---------------------------------------------------------------------------
+# mesh helpers
+# ---------------------------------------------------------------------------
+def cell_sizes(w) -> np.ndarray:
+    return np.array([(w["hi"][k] - w["lo"][k]) / w["n"][k] for k in range(w["dim"])])
+
+
+def grid_shape(w) -> tuple:
+    """Array shape of a cell field: (n_z, n_y, n_x) truncated to the dimension."""
+    return tuple(reversed(tuple(w["n"][: w["dim"]])))
+
+
+def cell_axis(d: int, dd: int) -> int:
+    """Axis of a (grid ...) array that runs along spatial dimension dd."""
+    return d - 1 - dd
+
+
+def time_step(w, max_speed: float, T: float | None = None):
+    """Sec. 5 / eq. comms: dt = nu h / (max wave speed).  When a final time T is given
+    the step is shortened so that an integer number of steps lands on T:
+    N_t = ceil(T / dt_cfl) (with a 1e-9 guard against rounding), dt = T / N_t."""
+    h = float(np.min(cell_sizes(w)))
+    dt = w["cfl"] * h / max_speed
+    if T is None:
+        return dt, None
+    nt = int(math.ceil(T / dt - 1e-9))
+    return T / nt, nt
+
+
+def advection_time_step(w, T=None):
+    return time_step(w, float(np.max(np.abs(w["vel"][: w["dim"]]))), T)
+
+
+# ---------------------------------------------------------------------------
+# the region system of eq. pred_full_system
+# ---------------------------------------------------------------------------
+def region_system(d: int, M: int, nu) -> tuple[np.ndarray, np.ndarray]:
+    """Return (A, B) with A W_R = B Q_R for one region.
+
+    W_R stacks the 3^d space-time blocks (region element r, then alpha, then s);
+    Q_R stacks the 3^d spatial blocks.  Everything is divided by |T_j|."""
+    nb = M + 1
+    thS = nb ** d
+    thT = nb * thS
+    D = basis.deriv_matrix(nb)
+    ep, em = basis.trace_plus(nb), basis.trace_minus(nb)
+    I1 = np.eye(nb)
+    IS = np.eye(thS)
+
+    def along(dd, X):  # spatial operator acting along dimension dd only
+        mats = [I1] * d
+        mats[dd] = X
+        return basis.kron_x_fastest(mats)
+
+    offs = basis.region_offsets(d)
+    index = {tuple(o): r for r, o in enumerate(offs)}
+    nR = len(offs)
+    A = np.zeros((nR * thT, nR * thT))
+    B = np.zeros((nR * thT, nR * thS))
+    time_term = np.outer(ep, ep) - D          # psi(1) psi(1)^T - int psi' psi
+    source = em.reshape(nb, 1)                # psi_alpha(-1)
+    for r, o in enumerate(offs):
+        rr = slice(r * thT, (r + 1) * thT)
+        A[rr, rr] += np.kron(time_term, IS)
+        B[rr, r * thS:(r + 1) * thS] += np.kron(source, IS)
+        for dd in range(d):
+            nu_d = float(nu[dd])
+            nup, num = max(nu_d, 0.0), min(nu_d, 0.0)
+            A[rr, rr] -= nu_d * np.kron(I1, along(dd, D))           # internal flux
+            # face at xi_d = +1, outward normal +e_d
+            o2 = o.copy(); o2[dd] += 1
+            if tuple(o2) in index:
+                r2 = index[tuple(o2)]
+                A[rr, rr] += nup * np.kron(I1, along(dd, np.outer(ep, ep)))
+                A[rr, r2 * thT:(r2 + 1) * thT] += num * np.kron(I1, along(dd, np.outer(ep, em)))
+            else:   # region boundary: own (interior) trace only
+                A[rr, rr] += nu_d * np.kron(I1, along(dd, np.outer(ep, ep)))
+            # face at xi_d = -1, outward normal -e_d
+            o2 = o.copy(); o2[dd] -= 1
+            if tuple(o2) in index:
+                r2 = index[tuple(o2)]
+                A[rr, r2 * thT:(r2 + 1) * thT] -= nup * np.kron(I1, along(dd, np.outer(em, ep)))
+                A[rr, rr] -= num * np.kron(I1, along(dd, np.outer(em, em)))
+            else:
+                A[rr, rr] -= nu_d * np.kron(I1, along(dd, np.outer(em, em)))
+    return A, B
+
+
+def nu_of(w, dt) -> np.ndarray:
+    return np.asarray(w["vel"][: w["dim"]], dtype=np.float64) * dt / cell_sizes(w)
+
+
+# ---------------------------------------------------------------------------
+# prediction and correction
+# ---------------------------------------------------------------------------
+def gather_region(Q: np.ndarray, w) -> np.ndarray:
+    """X[e, r, :] = Q of the r-th vertex neighbour of cell e (periodic)."""
+    d = w["dim"]
+    g = grid_shape(w)
+    Qg = Q.reshape(g + (Q.shape[-1],))
+    out = []
+    for o in basis.region_offsets(d):
+        shifted = Qg
+        for dd in range(d):
+            if o[dd]:
+                shifted = np.roll(shifted, -int(o[dd]), axis=cell_axis(d, dd))
+        out.append(shifted.reshape(-1, Q.shape[-1]))
+    return np.stack(out, axis=1)
+
+
+def predict(Q: np.ndarray, w, dt: float, chunk: int = 8192) -> np.ndarray:
+    """Centre-element space-time coefficients W_i for every cell, shape (cells, theta_T).
+    Each region system is solved with the LU factors of A (computed once)."""
+    d, M = w["dim"], w["M"]
+    nb = M + 1
+    thS, thT = nb ** d, nb ** (d + 1)
+    A, B = region_system(d, M, nu_of(w, dt))
+    lu = sla.lu_factor(A)
+    rc = (3 ** d - 1) // 2
+    ncell = Q.shape[0]
+    W = np.empty((ncell, thT))
+    for e0 in range(0, ncell, chunk):
+        e1 = min(ncell, e0 + chunk)
+        X = gather_region(Q, w)[e0:e1] if ncell <= chunk else _gather_rows(Q, w, e0, e1)
+        rhs = B @ X.reshape(e1 - e0, -1).T                     # (n, cells)
+        sol = sla.lu_solve(lu, rhs)
+        W[e0:e1] = sol[rc * thT:(rc + 1) * thT].T
+    return W
+
+
+def _gather_rows(Q, w, e0, e1):
+    return gather_cells(Q, w, np.arange(e0, e1))
+
+
+def gather_cells(Q, w, e):
+    """X[c, r, :] = Q of the r-th vertex neighbour of cell e[c] (periodic)."""
+    d = w["dim"]
+    n = w["n"]
+    e = np.asarray(e)
+    idx = [(e // int(np.prod(n[:k]))) % n[k] for k in range(d)]
+    cols = []
+    for o in basis.region_offsets(d):
+        lin = np.zeros_like(e)
+        stride = 1
+        for k in range(d):
+            lin += ((idx[k] + int(o[k])) % n[k]) * stride
+            stride *= n[k]
+        cols.append(Q[lin])
+    return np.stack(cols, axis=1)
+
+
+def _apply_along(T, mat, axis):
+    return np.moveaxis(np.tensordot(mat, T, axes=([1], [axis])), 0, axis)
+
+
+def _trace_along(T, vec, axis):
+    return np.tensordot(T, vec, axes=([axis], [0]))
+
+
+def _outer_along(F, vec, axis):
+    shape = [1] * (F.ndim + 1)
+    shape[axis] = vec.size
+    return np.expand_dims(F, axis) * vec.reshape(shape)
+
+
+def correct(Q: np.ndarray, Wbar: np.ndarray, w, dt: float) -> np.ndarray:
+    """Q^{n+1} from Q^n and the tau-mean prediction W-bar (both (cells, theta_S))."""
+    d, M = w["dim"], w["M"]
+    nb = M + 1
+    g = grid_shape(w)
+    modes = (nb,) * d
+    Wg = Wbar.reshape(g + modes)
+    dQ = np.zeros_like(Wg)
+    D = basis.deriv_matrix(nb)
+    ep, em = basis.trace_plus(nb), basis.trace_minus(nb)
+    nu = nu_of(w, dt)
+    for dd in range(d):
+        ca = cell_axis(d, dd)
+        ma = d + (d - 1 - dd)           # mode axis of dimension dd
+        nup, num = max(nu[dd], 0.0), min(nu[dd], 0.0)
+        dQ += nu[dd] * _apply_along(Wg, D, ma)                       # volume term
+        tr_p = _trace_along(Wg, ep, ma)                              # W-bar_i at xi_d = +1
+        tr_m = _trace_along(Wg, em, ma)                              # W-bar_i at xi_d = -1
+        flux = nup * tr_p + num * np.roll(tr_m, -1, axis=ca)         # face i+1/2, once
+        dQ -= _outer_along(flux, ep, ma)                             # outflow through +1
+        dQ += _outer_along(np.roll(flux, 1, axis=ca), em, ma)        # inflow through -1
+    return Q + dQ.reshape(Q.shape)
+
+
+def step(Q: np.ndarray, w, dt: float) -> np.ndarray:
+    nb = w["M"] + 1
+    thS = nb ** w["dim"]
+    W = predict(Q, w, dt)
+    return correct(Q, W[:, :thS], w, dt)
+
+
+def run(Q0: np.ndarray, w, dt: float, nsteps: int) -> np.ndarray:
+    Q = Q0.copy()
+    for _ in range(nsteps):
+        Q = step(Q, w, dt)
+    return Q
+
+
+def mass(Q: np.ndarray, w) -> float:
+    """sum_i |T_i| Q_{i,0} (the cell average is the phi_0 coefficient)."""
+    nb = w["M"] + 1
+    thS = nb ** w["dim"]
+    vol = float(np.prod(cell_sizes(w)))
+    return float(Q.reshape(Q.shape[0], -1, thS)[:, :, 0].sum(axis=0).sum() * vol)

@@ -1,0 +1,293 @@
+"""Seeded synthetic inputs for the RIDG workloads.
+
+This module produces initial data and exact solutions as cell-wise coefficients in
+the orthonormal tensor Legendre basis of Sec. 2.1 (Phi_s = prod_d sqrt(2 b_d + 1) P_{b_d},
+normalised so that (1/|T|) int_T Phi_k Phi_l = delta_kl), ordered x-fastest.  It holds
+none of the prediction / correction arithmetic: both the CUDA path and the oracle take
+their inputs from here, so that neither depends on the other.
+
+Workload parameters (mesh, degree, velocity, CFL number, final time) are the synthetic
+stand-ins for the paper's analytic test problems (eqs. adv1d, adv2d, burger2d, adv3d);
+the sine / Fourier / vortex initial data replace the paper's bump profiles.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from numpy.polynomial import legendre as npleg
+
+# ---------------------------------------------------------------------------
+# workload table
+# ---------------------------------------------------------------------------
+WORKLOADS = {
+    # 1D advection u_t + u_x = 0 on [0,1], 64 cells, degree 3, u0 = sin(2 pi x)
+    "adv1d_n64_q3": dict(flux="advection", dim=1, n=(64,), M=3, vel=(1.0,),
+                         lo=(0.0,), hi=(1.0,), cfl=0.45, T=1.0, ic="sin"),
+    # 2D advection u_t + u_x + 0.5 u_y = 0 on [0,1]^2, 256^2 cells, Q3
+    "adv2d_n256_q3": dict(flux="advection", dim=2, n=(256, 256), M=3, vel=(1.0, 0.5),
+                          lo=(0.0, 0.0), hi=(1.0, 1.0), cfl=0.35, T=1.0, ic="sin"),
+    # 3D advection with velocity (1, 0.7, 0.3) on [0,1]^3, 96^3 cells, Q2,
+    # product of sines plus seeded uniform 1e-3 coefficient noise
+    "adv3d_n96_q2": dict(flux="advection", dim=3, n=(96, 96, 96), M=2,
+                         vel=(1.0, 0.7, 0.3), lo=(0.0,) * 3, hi=(1.0,) * 3,
+                         cfl=0.30, T=1.0, ic="sin+noise"),
+    # 2D compressible Euler, isentropic vortex on [0,10]^2, 512^2 cells, Q2
+    "euler2d_n512_q2": dict(flux="euler", dim=2, n=(512, 512), M=2, gamma=1.4,
+                            lo=(0.0, 0.0), hi=(10.0, 10.0), cfl=0.35, T=1.0,
+                            ic="vortex"),
+}
+
+
+def workload(name: str, **override) -> dict:
+    """Parameters of a named workload; keyword overrides (e.g. a smaller mesh)."""
+    w = dict(WORKLOADS[name])
+    w.update(override)
+    w["name"] = name
+    return w
+
+
+# ---------------------------------------------------------------------------
+# 1D Legendre helpers (library evaluation of P_b; used only to project data)
+# ---------------------------------------------------------------------------
+def _legendre_orthonormal(nb: int, x: np.ndarray) -> np.ndarray:
+    """V[b, ...] = sqrt(2b+1) P_b(x)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty((nb,) + x.shape)
+    for b in range(nb):
+        c = np.zeros(b + 1)
+        c[b] = 1.0
+        out[b] = math.sqrt(2 * b + 1) * npleg.legval(x, c)
+    return out
+
+
+def _cell_points(n: int, lo: float, hi: float, nq: int):
+    """Gauss points of every cell: x[i, q], reference weights w[q] (sum 2), V[b, q]."""
+    xi, w = npleg.leggauss(nq)
+    h = (hi - lo) / n
+    centres = lo + (np.arange(n) + 0.5) * h
+    return centres[:, None] + 0.5 * h * xi[None, :], w, xi
+
+
+def project_1d(f, n: int, lo: float, hi: float, nb: int, nq: int | None = None) -> np.ndarray:
+    """c[i, b] = (1/h) int_{cell i} f(x) phi_b(x) dx for a 1D function f."""
+    nq = nq or nb + 8
+    x, w, xi = _cell_points(n, lo, hi, nq)
+    V = _legendre_orthonormal(nb, xi)
+    return 0.5 * np.einsum("iq,q,bq->ib", f(x), w, V)
+
+
+def _outer_modes(factors):
+    """Combine per-dimension coefficient tables c_d[i_d, b_d] (d = 0 is x) into
+    c[cells (z, y, x) ..., modes x-fastest]."""
+    d = len(factors)
+    out = factors[0]  # (nx, nb)
+    for k in range(1, d):
+        f = factors[k]
+        # out: (cells_prev..., modes_prev) ; f: (n_k, nb)
+        out = np.einsum("...m,ib->i...bm", out, f)
+        # merge mode axes: new modes index = b * prev + m  (x fastest)
+        sh = out.shape
+        out = out.reshape(sh[:-2] + (sh[-2] * sh[-1],))
+    return out
+
+
+def project_separable(fs, w: dict, nb: int, nq: int | None = None) -> np.ndarray:
+    """Coefficients of prod_d fs[d](x_d) on the workload's mesh, shape (cells, nb^d)."""
+    d = w["dim"]
+    facs = [project_1d(fs[k], w["n"][k], w["lo"][k], w["hi"][k], nb, nq) for k in range(d)]
+    c = _outer_modes(facs)
+    return c.reshape(-1, nb ** d)
+
+
+def project_tensor(f, w: dict, nb: int, nq: int | None = None, m: int = 1,
+                   chunk: int = 64) -> np.ndarray:
+    """Coefficients of a general f(x, y[, z]) -> (m, ...) by tensor Gauss quadrature.
+    Returns shape (cells, m, nb^d).  Cells are processed in slabs of the slowest axis."""
+    d = w["dim"]
+    nq = nq or nb + 8
+    xi, wq = npleg.leggauss(nq)
+    V = _legendre_orthonormal(nb, xi)  # (nb, nq)
+    n = w["n"]
+    h = [(w["hi"][k] - w["lo"][k]) / n[k] for k in range(d)]
+    pts = [w["lo"][k] + (np.arange(n[k]) + 0.5)[:, None] * h[k] + 0.5 * h[k] * xi[None, :]
+           for k in range(d)]  # pts[k][i, q]
+    ncell = int(np.prod(n))
+    out = np.empty((ncell, m, nb ** d))
+    if d == 1:
+        vals = np.asarray(f(pts[0])).reshape(m, n[0], nq)
+        c = 0.5 * np.einsum("rip,p,bp->irb", vals, wq, V)
+        out[:] = c
+        return out
+    if d == 2:
+        X = pts[0][None, :, None, :]   # (1, nx, 1, qx)
+        for j0 in range(0, n[1], chunk):
+            j1 = min(n[1], j0 + chunk)
+            Y = pts[1][j0:j1, None, :, None]  # (ny', 1, qy, 1)
+            Xb, Yb = np.broadcast_arrays(X, Y)
+            vals = np.asarray(f(Xb, Yb)).reshape(m, j1 - j0, n[0], nq, nq)
+            # modes: s = bx + nb * by
+            c = 0.25 * np.einsum("rjipq,p,q,cp,bq->jircb", vals, wq, wq, V, V)
+            out[j0 * n[0]:j1 * n[0]] = c.reshape((j1 - j0) * n[0], m, nb * nb)
+        return out
+    X = pts[0][None, None, :, None, None, :]
+    Y = pts[1][None, :, None, None, :, None]
+    for k0 in range(0, n[2], max(1, chunk // 8)):
+        k1 = min(n[2], k0 + max(1, chunk // 8))
+        Z = pts[2][k0:k1, None, None, :, None, None]
+        Xb, Yb, Zb = np.broadcast_arrays(X, Y, Z)
+        vals = np.asarray(f(Xb, Yb, Zb)).reshape(m, k1 - k0, n[1], n[0], nq, nq, nq)
+        c = 0.125 * np.einsum("rkjiopq,o,p,q,ao,bp,cq->kjirabc", vals, wq, wq, wq, V, V, V)
+        out[k0 * n[0] * n[1]:k1 * n[0] * n[1]] = c.reshape(-1, m, nb ** 3)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# initial data and exact solutions
+# ---------------------------------------------------------------------------
+def _sin2pi(shift: float):
+    return lambda x: np.sin(2.0 * np.pi * (x - shift))
+
+
+def advection_noise(w: dict, seed: int = 0) -> np.ndarray:
+    """i.i.d. U(-1e-3, 1e-3) added to every Q(M) coefficient of every cell (PCG64)."""
+    nb = w["M"] + 1
+    ncell = int(np.prod(w["n"]))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(-1e-3, 1e-3, size=(ncell, nb ** w["dim"]))
+
+
+def initial_state(w: dict, seed: int = 0) -> np.ndarray:
+    """Initial coefficients Q^0 in the canonical layout, shape (cells, m * theta_S)."""
+    nb = w["M"] + 1
+    if w["flux"] == "advection":
+        q = project_separable([_sin2pi(0.0)] * w["dim"], w, nb)
+        if w["ic"] == "sin+noise":
+            q = q + advection_noise(w, seed)
+        return np.ascontiguousarray(q)
+    if w["flux"] == "euler":
+        return np.ascontiguousarray(
+            project_tensor(lambda x, y: vortex_state(x, y, 0.0, w.get("gamma", 1.4)), w, nb, m=4
+                           ).reshape(-1, 4 * nb ** 2))
+    if w["flux"] == "burgers":
+        return np.ascontiguousarray(burgers_initial(w, nb))
+    raise ValueError(w["flux"])
+
+
+def exact_coefficients(w: dict, t: float, nb: int | None = None) -> np.ndarray:
+    """Projection of the exact solution at time t onto Q(nb-1) cell-wise (default
+    nb = M + 2, the Q(M+1) space the L2 error definition of Sec. 4 needs)."""
+    nb = nb or w["M"] + 2
+    if w["flux"] == "advection":
+        if w["ic"] != "sin":
+            raise ValueError("exact coefficients are available for the noise-free data only")
+        a = w["vel"]
+        return np.ascontiguousarray(
+            project_separable([_sin2pi(a[k] * t) for k in range(w["dim"])], w, nb))
+    if w["flux"] == "euler":
+        return np.ascontiguousarray(
+            project_tensor(lambda x, y: vortex_state(x, y, t, w.get("gamma", 1.4)), w, nb, m=4
+                           ).reshape(-1, 4 * nb ** 2))
+    if w["flux"] == "burgers":
+        return np.ascontiguousarray(
+            project_tensor(lambda x, y: burgers_exact(w, x, y, t), w, nb).reshape(-1, nb ** 2))
+    raise ValueError(w["flux"])
+
+
+# --- isentropic vortex (ambient (rho,u,v,p) = (1,1,1,1), strength 5, centre (5,5)) --
+def vortex_state(x, y, t, gamma=1.4, eps=5.0, xc=5.0, yc=5.0, L=10.0):
+    """Conserved variables (rho, rho u, rho v, E) of the translating isentropic vortex."""
+    dx = x - (xc + t)
+    dy = y - (yc + t)
+    dx = dx - L * np.round(dx / L)
+    dy = dy - L * np.round(dy / L)
+    r2 = dx * dx + dy * dy
+    f = np.exp(0.5 * (1.0 - r2))
+    u = 1.0 - eps / (2 * np.pi) * f * dy
+    v = 1.0 + eps / (2 * np.pi) * f * dx
+    T = 1.0 - (gamma - 1.0) * eps ** 2 / (8 * gamma * np.pi ** 2) * f * f
+    rho = T ** (1.0 / (gamma - 1.0))
+    p = rho * T
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return np.stack([rho, rho * u, rho * v, E])
+
+
+# --- Burgers ensemble: 5 Fourier modes, amplitudes summing to 0.5 ---------------
+def burgers_modes(seed: int):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ks = [(k, l) for k in range(-3, 4) for l in range(-3, 4) if (k, l) != (0, 0)]
+    idx = rng.choice(len(ks), size=5, replace=False)
+    kl = np.array([ks[i] for i in idx], dtype=np.float64)
+    ph = rng.uniform(0.0, 2 * np.pi, size=5)
+    a = rng.uniform(0.0, 1.0, size=5)
+    a = 0.5 * a / a.sum()
+    return kl, ph, a
+
+
+def burgers_u0(modes, x, y):
+    kl, ph, a = modes
+    u = np.zeros(np.broadcast(x, y).shape)
+    for m in range(len(a)):
+        u = u + a[m] * np.cos(2 * np.pi * (kl[m, 0] * x + kl[m, 1] * y) + ph[m])
+    return u
+
+
+def burgers_u0_grad_sum(modes, x, y):
+    kl, ph, a = modes
+    g = np.zeros(np.broadcast(x, y).shape)
+    for m in range(len(a)):
+        g = g - a[m] * 2 * np.pi * (kl[m, 0] + kl[m, 1]) * np.sin(
+            2 * np.pi * (kl[m, 0] * x + kl[m, 1] * y) + ph[m])
+    return g
+
+
+def burgers_ensemble(count: int = 64, seed: int = 0, nmin: int = 64, nmax: int = 512,
+                     mmin: int = 1, mmax: int = 4, cfl: float = 0.35):
+    """The batched ensemble: instance sizes N ~ U{nmin..nmax} (N x N), degrees
+    M ~ U{mmin..mmax}, Fourier data seeded per instance."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Ns = rng.integers(nmin, nmax + 1, size=count)
+    Ms = rng.integers(mmin, mmax + 1, size=count)
+    out = []
+    for i in range(count):
+        out.append(dict(flux="burgers", dim=2, n=(int(Ns[i]), int(Ns[i])), M=int(Ms[i]),
+                        lo=(0.0, 0.0), hi=(1.0, 1.0), cfl=cfl, T=None, ic="fourier",
+                        seed=int(seed * 1000 + i), name=f"burgers_{i}"))
+    return out
+
+
+def burgers_initial(w: dict, nb: int) -> np.ndarray:
+    modes = burgers_modes(w["seed"])
+    kl, ph, a = modes
+    facs = []
+    # cos(2pi(kx+ly)+ph) = cos(2pi kx + ph) cos(2pi ly) - sin(2pi kx + ph) sin(2pi ly)
+    c = 0.0
+    for m in range(5):
+        k, l = kl[m]
+        cx = project_1d(lambda x: np.cos(2 * np.pi * k * x + ph[m]), w["n"][0], 0.0, 1.0, nb)
+        sx = project_1d(lambda x: np.sin(2 * np.pi * k * x + ph[m]), w["n"][0], 0.0, 1.0, nb)
+        cy = project_1d(lambda y: np.cos(2 * np.pi * l * y), w["n"][1], 0.0, 1.0, nb)
+        sy = project_1d(lambda y: np.sin(2 * np.pi * l * y), w["n"][1], 0.0, 1.0, nb)
+        c = c + a[m] * (_outer_modes([cx, cy]) - _outer_modes([sx, sy]))
+    return c.reshape(-1, nb * nb)
+
+
+def burgers_shock_time(w: dict) -> float:
+    """t* = 1 / max(-(d/dx + d/dy) u0) for u_t + (u^2/2)_x + (u^2/2)_y = 0."""
+    modes = burgers_modes(w["seed"])
+    g = np.linspace(0, 1, 1025)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    m = np.max(-burgers_u0_grad_sum(modes, X, Y))
+    return 1.0 / m
+
+
+def burgers_exact(w: dict, x, y, t, iters: int = 60):
+    """Pre-shock solution u = u0(x - u t, y - u t), solved pointwise by Newton."""
+    modes = burgers_modes(w["seed"])
+    u = burgers_u0(modes, x, y)
+    for _ in range(iters):
+        xs, ys = x - u * t, y - u * t
+        g = u - burgers_u0(modes, xs, ys)
+        dg = 1.0 + t * burgers_u0_grad_sum(modes, xs, ys)
+        u = u - g / dg
+    return u

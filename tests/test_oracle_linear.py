@@ -1,0 +1,210 @@
+"""Pins of the linear-flux oracle against what the paper and the mathematics fix."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import error as oerr
+from oracle import linear as L
+from oracle import nonlinear as NL
+from paper_2101_01231_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _w(d, n, M, vel, cfl=0.4, T=0.25):
+    return dict(flux="advection", dim=d, n=tuple([n] * d), M=M, vel=tuple(vel[:d]),
+                lo=(0.0,) * d, hi=(1.0,) * d, cfl=cfl, T=T, ic="sin")
+
+
+@pytest.mark.parametrize("d,M,vel", [(1, 3, (1.0,)), (2, 2, (1.0, -0.5)), (3, 1, (1.0, 0.7, -0.3))])
+def test_constant_state_is_preserved(d, M, vel):
+    # A constant state must predict W = that constant (region-boundary faces use the
+    # interior trace; eq. pred_full_system with the reading of Sec. 2.2's insulation).
+    w = _w(d, 4, M, vel)
+    thS = (M + 1) ** d
+    Q = np.zeros((4 ** d, thS))
+    Q[:, 0] = 1.7
+    W = L.predict(Q, w, 0.03)
+    assert np.allclose(W[:, 0], 1.7, atol=1e-13)
+    assert np.abs(W[:, 1:]).max() < 1e-13
+    Q1 = L.correct(Q, W[:, :thS], w, 0.03)
+    assert np.allclose(Q1, Q, atol=1e-13)
+
+
+def test_dropping_region_boundary_terms_breaks_constants():
+    # The other reading (no surface term at all on the region boundary) does not keep
+    # constants: this pins which reading the oracle implements.
+    d, M = 1, 2
+    nu = np.array([0.4])
+    A, B = L.region_system(d, M, nu)
+    nb = M + 1
+    thT = nb * nb ** d
+    Qc = np.zeros(3 * nb)
+    Qc[::nb] = 1.0
+    W = np.zeros(3 * thT)
+    W[::thT] = 1.0
+    assert np.abs(A @ W - B @ Qc).max() < 1e-13
+    # remove the boundary face term of the left region element
+    from oracle import basis
+    em = basis.trace_minus(nb)
+    A2 = A.copy()
+    A2[0:thT, 0:thT] += nu[0] * np.kron(np.eye(nb), np.outer(em, em))
+    assert np.abs(A2 @ W - B @ Qc).max() > 1e-3
+
+
+def test_zero_velocity_returns_q_extended_in_time():
+    d, M = 2, 3
+    w = _w(d, 4, M, (0.0, 0.0))
+    rng = np.random.default_rng(1)
+    Q = rng.standard_normal((16, (M + 1) ** d))
+    W = L.predict(Q, w, 0.05)
+    thS = (M + 1) ** d
+    assert np.allclose(W[:, :thS], Q, atol=1e-13)
+    assert np.abs(W[:, thS:]).max() < 1e-13
+
+
+@pytest.mark.parametrize("d,M,vel", [(1, 3, (1.0,)), (2, 2, (1.0, 0.5)), (2, 1, (-0.6, 1.0))])
+def test_mass_conserved_to_roundoff(d, M, vel):
+    w = _w(d, 8, M, vel)
+    rng = np.random.default_rng(2)
+    Q0 = rng.standard_normal((8 ** d, (M + 1) ** d)) + 3.0
+    dt, _ = L.advection_time_step(w)
+    Q = L.run(Q0, w, dt, 10)
+    m0, m1 = L.mass(Q0, w), L.mass(Q, w)
+    assert abs(m1 - m0) <= 1e-14 * abs(m0) * 10
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_convergence_order_1d(M):
+    errs = []
+    for N in (16, 32):
+        w = _w(1, N, M, (1.0,), cfl=0.45)
+        dt, nt = L.advection_time_step(w, T=0.25)
+        Q = L.run(I.initial_state(w), w, dt, nt)
+        errs.append(oerr.l2_relative_error(Q, I.exact_coefficients(w, 0.25), M, 1))
+    order = oerr.observed_order(errs[0], errs[1], 1 / 16, 1 / 32)
+    assert order > M + 1 - 0.35, (errs, order)
+
+
+def test_convergence_order_2d():
+    errs = []
+    for N in (8, 16):
+        w = _w(2, N, 2, (1.0, 0.5), cfl=0.35)
+        dt, nt = L.advection_time_step(w, T=0.25)
+        Q = L.run(I.initial_state(w), w, dt, nt)
+        errs.append(oerr.l2_relative_error(Q, I.exact_coefficients(w, 0.25), 2, 2))
+    order = oerr.observed_order(errs[0], errs[1], 1 / 8, 1 / 16)
+    assert order > 2.7, (errs, order)
+
+
+def test_exact_solution_2d_sign():
+    # a = (1, 0.5), T = 1 moves sin(2 pi x) sin(2 pi y) to its negative
+    w = _w(2, 4, 3, (1.0, 0.5))
+    X0 = I.exact_coefficients(w, 0.0)
+    X1 = I.exact_coefficients(w, 1.0)
+    assert np.allclose(X1, -X0, atol=1e-12)
+
+
+def test_paper_1d_observed_orders():
+    """Table table:1D: observed orders (eq. Mratio) for RIDG M = 3 and 5 at nu = 0.9 on
+    the bump of eq. adv1d.  The final time is not given, so only the orders are pinned."""
+    ref = json.load(open(os.path.join(GOLDEN, "paper_1d_table.json")))
+
+    def bump(x):
+        r2 = (x - 0.5) ** 2
+        out = np.zeros_like(x)
+        m = r2 < 1.0 / 9.0
+        out[m] = np.exp(1.0 / (r2[m] - 1.0 / 9.0))
+        return out
+
+    for M, meshes in ((3, (50, 70, 120)), (5, (30, 50))):
+        row = ref["rows"][str(M)]
+        errs = []
+        for N in meshes:
+            w = dict(flux="advection", dim=1, n=(N,), M=M, vel=(1.0,), lo=(0.0,), hi=(1.0,),
+                     cfl=0.9)
+            dt, nt = L.advection_time_step(w, T=1.0)
+            Q = L.run(I.project_1d(bump, N, 0.0, 1.0, M + 1, nq=40), w, dt, nt)
+            X = I.project_1d(bump, N, 0.0, 1.0, M + 2, nq=40)
+            errs.append(oerr.l2_relative_error(Q, X, M, 1))
+        for k in range(1, len(meshes)):
+            order = oerr.observed_order(errs[k - 1], errs[k], 1 / meshes[k - 1], 1 / meshes[k])
+            assert abs(order - row["order"][k]) < 0.7, (M, meshes[k], order)
+
+
+def _symbol(M, nu, theta):
+    """Amplification matrix of one linear RIDG step for the Fourier mode e^{i theta j}:
+    built from the oracle step applied to the real and imaginary parts on a mesh with
+    N cells (theta = 2 pi k / N)."""
+    N = 32
+    w = dict(flux="advection", dim=1, n=(N,), M=M, vel=(1.0,), lo=(0.0,), hi=(1.0,), cfl=nu)
+    dt = nu / N
+    nb = M + 1
+    j = np.arange(N)
+    G = np.zeros((nb, nb), dtype=complex)
+    for s in range(nb):
+        e = np.zeros(nb)
+        e[s] = 1.0
+        Qr = np.cos(theta * j)[:, None] * e
+        Qi = np.sin(theta * j)[:, None] * e
+        out = L.step(Qr, w, dt) + 1j * L.step(Qi, w, dt)
+        G[:, s] = out[0]       # cell 0 carries the amplitude of e^{i theta 0}
+    return G
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_linear_stability(M):
+    # The 1D workloads run at nu = 0.45 = half of the nu = 0.9 the paper uses for RIDG
+    # at every degree (Sec. 6.1, table table:1D): strictly stable there.  At nu = 0.9
+    # itself the paper's claim is empirical (runs of a few hundred steps); the oracle's
+    # largest per-step growth there stays below 1e-3, invisible over such runs.
+    for k in range(0, 17):
+        theta = 2 * np.pi * k / 32
+        rho = max(abs(np.linalg.eigvals(_symbol(M, 0.45, theta))))
+        assert rho <= 1.0 + 1e-12
+        rho9 = max(abs(np.linalg.eigvals(_symbol(M, 0.9, theta))))
+        assert rho9 <= 1.0 + 1e-3
+
+
+def test_time_loop_matches_symbol_power():
+    M, nu, k = 2, 0.45, 3
+    N = 32
+    theta = 2 * np.pi * k / N
+    G = _symbol(M, nu, theta)
+    w = dict(flux="advection", dim=1, n=(N,), M=M, vel=(1.0,), lo=(0.0,), hi=(1.0,), cfl=nu)
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(M + 1) + 1j * rng.standard_normal(M + 1)
+    j = np.arange(N)
+    Q0 = np.real(np.exp(1j * theta * j)[:, None] * v)
+    Q = L.run(Q0, w, nu / N, 12)
+    ref = np.real(np.exp(1j * theta * j)[:, None] * (np.linalg.matrix_power(G, 12) @ v))
+    assert np.abs(Q - ref).max() < 1e-12
+
+
+def test_quadrature_assembly_matches_closed_form_system():
+    # brute force: the residual of eq. pred_full_system by quadrature with F = a q equals
+    # the Kronecker-assembled A W - B Q.
+    rng = np.random.default_rng(4)
+    for d, M, vel in ((1, 3, (0.8,)), (2, 2, (1.0, -0.5)), (3, 1, (1.0, 0.7, -0.3))):
+        lam = np.full(d, 0.07)
+        A, B = L.region_system(d, M, np.asarray(vel) * lam)
+        tb = NL.Tables(d, M, nq=M + 3)
+        W = rng.standard_normal((2, 3 ** d, 1, tb.thT))
+        Q = rng.standard_normal((2, 3 ** d, 1, tb.thS))
+        R, _ = NL.residual(W, Q, NL.Advection(vel), tb, lam)
+        ref = W.reshape(2, -1) @ A.T - Q.reshape(2, -1) @ B.T
+        assert np.abs(R.reshape(2, -1) - ref).max() < 1e-13
+
+
+def test_error_metric_definition():
+    # If Q is the exact Q(M) projection the error is the truncation part alone.
+    w = _w(2, 8, 2, (1.0, 0.5))
+    X = I.exact_coefficients(w, 0.0)
+    inside = oerr.modes_in(3, 4, 2)
+    Q = X[:, inside]
+    e = oerr.l2_relative_error(Q, X, 2, 2)
+    ref = np.sqrt((X[:, ~inside] ** 2).sum() / (X ** 2).sum())
+    assert abs(e - ref) < 1e-15
+    assert oerr.l2_relative_error(Q + 1.0, X, 2, 2) > e
