@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""RIDG step throughput on one GB300 (element-DOF updates/s).
+
+Workload: 2D linear advection u_t + u_x + 0.5 u_y = 0 on the periodic unit square,
+256 x 256 cells, tensor Q3 (16 spatial / 64 space-time coefficients), 3 x 3 regions,
+u0 = sin(2 pi x) sin(2 pi y), CFL 0.35, final time 1 (732 steps).  A step is one
+prediction + correction over the whole mesh.  Inputs are seeded synthetic data resident in
+HBM; before every timed step a 256 MB buffer (larger than the 129 MB L2) is rewritten so
+that each step starts with a cold L2.
+
+The timed arm reports the precision chosen with --precision (default: the mixed BF16
+tensor-core prediction when the library supports it, else FP64) and, beside it, the FP64
+path and the oracle (on the host cores).  --impl reference times the oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "adv2d_n256_q3"
+T_FINAL = 1.0
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
+    p.add_argument("--slices", type=int, default=0)
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _golden():
+    p = os.path.join(ROOT, "tests", "golden", "oracle_accuracy.json")
+    return json.load(open(p)) if os.path.exists(p) else {}
+
+
+# ---------------------------------------------------------------------------------------
+# the oracle on the host (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------------------
+def cpu_oracle(w, seconds, steps=None):
+    """Time oracle steps of the full workload until `seconds` of CPU work (or `steps`)."""
+    from oracle import linear as OL
+    from paper_2101_01231_gb300 import inputs as I
+    q = I.initial_state(w)
+    dt, _ = OL.advection_time_step(w, T=T_FINAL)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        q = OL.step(q, w, dt)
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and n >= steps) or (steps is None and el >= seconds):
+            break
+    cells = int(np.prod(w["n"]))
+    dof = cells * (w["M"] + 1) ** w["dim"]
+    return dict(value=dof * n / el, unit="element-DOF updates/s", cores=os.cpu_count(),
+                kind="oracle", steps=n, seconds=round(el, 3),
+                sample=f"{n} full oracle steps of {w['name']} ({cells} cells, region LU solves, "
+                       f"numpy/scipy on all host cores)")
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2101_01231_gb300 import inputs as I
+    w = I.workload(args.workload)
+    for _ in range(max(1, min(args.warmup, 3))):
+        cpu_oracle(w, 0, steps=1)  # warm-up (tables, BLAS threads)
+    t_all = 0.0
+    n_all = 0
+    for _ in range(args.steps):
+        r = cpu_oracle(w, 0, steps=1)
+        t_all += r["seconds"]
+        n_all += 1
+        if t_all > 120:
+            break
+    cells = int(np.prod(w["n"]))
+    dof = cells * (w["M"] + 1) ** w["dim"]
+    value = dof * n_all / t_all
+    line = {
+        "impl": "reference", "metric": "element-DOF updates/s per RIDG step",
+        "value": value, "unit": "element-DOF updates/s", "n_gpus": ws, "steps": n_all,
+        "warmup": 1, "ms_per_step": 1e3 * t_all / n_all, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "cells": cells, "order": w["M"], "steps_to_T": None},
+        "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value,
+                         "unit": "element-DOF updates/s",
+                         "sample": f"{n_all} full oracle steps on the host cores"},
+        "e2e": {"value": value, "unit": "element-DOF updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        rows = []
+        try:
+            for line in open(self.f.name):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2101_01231_gb300 import inputs as I
+    from paper_2101_01231_gb300 import ridg as R
+
+    w = I.workload(args.workload)
+    prec_name = args.precision
+    prec = {"fp64": R.RIDG_PREC_FP64, "mixed": R.RIDG_PREC_MIXED_BF16}
+    if prec_name == "auto":
+        prec_name = "mixed"
+        try:
+            s_try = R.Solver(w["dim"], w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"],
+                             hi=w["hi"], precision=R.RIDG_PREC_MIXED_BF16, slices=args.slices)
+            s_try.close()
+        except R.RidgError:
+            prec_name = "fp64"
+
+    def make(pname):
+        return R.Solver(w["dim"], w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"],
+                        hi=w["hi"], precision=prec[pname], slices=args.slices)
+
+    cells = int(np.prod(w["n"]))
+    thS = (w["M"] + 1) ** w["dim"]
+    K = 3 ** w["dim"] * thS
+    dof = cells * thS
+    q0 = I.initial_state(w)
+
+    def accuracy(pname):
+        s = make(pname)
+        s.set_state(q0)
+        nt = s.set_final_time(T_FINAL)
+        s.step(nt)
+        s.sync()
+        e = s.l2_error(I.exact_coefficients(w, T_FINAL))
+        s.close()
+        return e, nt
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB
+
+    def timed(pname, steps, warmup, clocks=None):
+        s = make(pname)
+        s.set_state(q0)
+        s.set_final_time(T_FINAL)
+        for _ in range(warmup):
+            with torch.cuda.stream(s.stream):
+                flush.fill_(1.0)
+            s.profile_step(1)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        if clocks:
+            clocks.start()
+        tp = tc = tt = 0.0
+        for i in range(steps):
+            with torch.cuda.stream(s.stream):
+                flush.fill_(float(i))
+            p = s.profile_step(1)
+            tp += p["predict_ms"]
+            tc += p["correct_ms"]
+            tt += p["step_ms"]
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        ck = clocks.stop() if clocks else None
+        return s, tt / steps, tp / steps, tc / steps, ck
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        gpu_id = str(torch.cuda.current_device())
+    clocks = Clocks(gpu_id)
+    s, ms_step, ms_pred, ms_corr, ck = timed(prec_name, args.steps, args.warmup, clocks)
+    t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step = float(t.item())
+    value = ws * dof / (ms_step * 1e-3)
+
+    # end to end through the C ABI with host buffers: H2D state, one step, D2H state
+    qh = torch.from_numpy(q0.copy()).pin_memory().numpy()
+    n_e2e = min(args.steps, 50)
+    for _ in range(3):
+        s.set_state(qh)
+        s.step(1)
+        s.get_state(qh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        s.set_state(qh)
+        s.step(1)
+        s.get_state(qh)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    s.close()
+
+    # the FP64 form beside the headline precision (same timing rules, fewer steps)
+    fp64 = None
+    if prec_name != "fp64":
+        s2, ms64, mp64, mc64, _ = timed("fp64", max(20, args.steps // 5), args.warmup)
+        s2.close()
+        fp64 = {"ms_per_step": ms64, "value": dof / (ms64 * 1e-3), "predict_ms": mp64,
+                "correct_ms": mc64}
+
+    err, nt = accuracy(prec_name)
+    err64 = accuracy("fp64")[0] if prec_name != "fp64" else err
+    gold = _golden().get(args.workload, {})
+    err_oracle = gold.get("l2_error")
+
+    hbm, bf16, src = _peaks()
+    flops_pred = 2.0 * thS * K * cells     # algorithmic: time-mean rows of P times X, per launch
+    if prec_name == "fp64":
+        # FP64 FMA pipe: 152 SMs x 2 FP64 FMA / clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+        peak = 1.25e3
+        roof = {"bound": "alu", "kernel": "predict_fp64", "achieved": flops_pred / (ms_pred * 1e-3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "nominal FP64 rate of the recipe (152 SMs x 4 flop/clk x 2.07 GHz)"}
+    else:
+        roof = {"bound": "tensor", "kernel": "predict_mixed_bf16",
+                "achieved": flops_pred / (ms_pred * 1e-3) / 1e12, "peak": bf16,
+                "unit": "TFLOP/s", "traffic": None, "peak_source": f"bf16 dense, {src}"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    line = {
+        "metric": "element-DOF updates/s per RIDG step",
+        "value": value, "unit": "element-DOF updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec_name == "fp64" else "bf16x{}+f64".format(s.opt.slices or 5),
+        "data": "synthetic",
+        "config": {"workload": w["name"], "cells": cells, "order": w["M"], "theta_s": thS,
+                   "precision": prec_name, "steps_to_T": nt, "l2_flush": "256 MB rewrite before each timed step",
+                   "l2_error": err, "l2_error_fp64_gpu": err64, "l2_error_oracle": err_oracle,
+                   "equal_accuracy": (err <= 1.05 * err_oracle) if err_oracle else None},
+        "kernels_ms": {"predict": ms_pred, "correct": ms_corr},
+        "fp64_path": fp64,
+        "roofline": roof,
+        "e2e": {"value": ws * dof / e2e_s, "unit": "element-DOF updates/s",
+                "h2d_bytes_per_step": int(q0.nbytes), "d2h_bytes_per_step": int(q0.nbytes)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": ck,
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_oracle(w, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

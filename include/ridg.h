@@ -1,0 +1,212 @@
+/*
+ * ridg.h -- C ABI of the GB300 RIDG library (regionally-implicit discontinuous Galerkin).
+ *
+ * One RIDG time step (Sec. 2) on a uniform, fully periodic Cartesian mesh in 1, 2 or 3
+ * dimensions has two parts:
+ *   prediction  (Sec. 2.2, eq. pred_full_system): for every cell i the space-time DG
+ *               system on its region R_i of 3^d vertex neighbours (eq. region) is solved
+ *               and only the centre cell's space-time coefficients W_i are kept;
+ *               for a linear flux this is a precomputed region-to-cell operator applied
+ *               to every cell, for a nonlinear flux a Newton iteration (Sec. 3) with the
+ *               quasi-quadrature-free Jacobian (eqs. Jacproj, Jacobian2);
+ *   correction  (Sec. 2.3): Q^{n+1}_i = Q^n_i + volume integral of grad Phi . F(w_i)
+ *               - surface integral of the Rusanov flux, both from the predicted W.
+ *
+ * Conventions shared by every entry point
+ *   - Basis: Phi_s = prod_d sqrt(2 b_d + 1) P_{b_d}(xi_d) on each cell, orthonormal in
+ *     the element-average sense (Sec. 2.1), degree M per dimension, theta_S = (M+1)^d
+ *     modes ordered with b_x fastest.  The space-time basis Psi_k = psi_a(tau) Phi_s has
+ *     theta_T = (M+1)^(d+1) modes, k = a * theta_S + s (time slowest), so the first
+ *     theta_S entries of W_i are its time mean.
+ *   - Cells are numbered e = i_x + n_x (i_y + n_y i_z).
+ *   - State layout ("canonical"): q[(e * m + r) * theta_S + s], r = conserved variable.
+ *     Prediction layout: w[(e * m + r) * theta_T + k].
+ *   - All arithmetic that defines the result is FP64 unless a mixed precision is chosen
+ *     (see ridg_options.precision); the state is always held in FP64.
+ *   - Every call returns an int status (RIDG_OK = 0); nothing is thrown across the ABI.
+ *     The handle keeps a message for the last failure (ridg_last_error).
+ *   - A handle is bound to the CUDA device that was current at ridg_create and issues all
+ *     work on its stream (ridg_options.stream, or a non-blocking stream the handle creates
+ *     when that is NULL; CUDA-graph capture needs a stream other than the legacy one).
+ *     Device pointers passed in must be on that device; the caller orders them against
+ *     the handle's stream.  A handle is not thread-safe.
+ *   - Ownership: the caller owns every buffer it passes; the library owns its internal
+ *     device state and releases it in ridg_destroy.
+ */
+#ifndef RIDG_H_
+#define RIDG_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----- status codes ------------------------------------------------------------- */
+enum {
+  RIDG_OK = 0,
+  RIDG_EINVAL = 1,      /* invalid argument, unsupported dimension / degree / flux      */
+  RIDG_ENOMEM = 2,      /* host or device allocation failed                              */
+  RIDG_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error)       */
+  RIDG_ENONFINITE = 4,  /* a non-finite value was found in the state                     */
+  RIDG_ENOCONV = 5,     /* Newton hit its iteration cap in some regions; the step still
+                           completed and ridg_info reports how many regions                */
+  RIDG_ETIMEOUT = 6,    /* a bounded device-side wait gave up                             */
+  RIDG_ESTATE = 7       /* call out of order (e.g. correct before predict, no dt yet)    */
+};
+
+/* ----- problem description -------------------------------------------------------- */
+typedef struct {
+  int dim;          /* 1, 2 or 3                                                        */
+  int n[3];         /* cells per dimension (entries beyond dim ignored), each >= 3      */
+  double lo[3];     /* domain [lo_d, hi_d], periodic on every face                      */
+  double hi[3];
+} ridg_mesh;
+
+enum { RIDG_FLUX_ADVECTION = 0, RIDG_FLUX_BURGERS = 1, RIDG_FLUX_EULER = 2 };
+
+typedef struct {
+  int kind;         /* RIDG_FLUX_*                                                      */
+  double vel[3];    /* advection velocity a (ADVECTION)                                 */
+  double gamma;     /* ratio of specific heats (EULER, 2D only, m = 4)                  */
+} ridg_flux;
+
+enum {
+  RIDG_PREC_FP64 = 0,        /* every step of the path in FP64                           */
+  RIDG_PREC_MIXED_BF16 = 1,  /* linear prediction as a sliced BF16 tensor-core contraction
+                                with FP32 accumulation recombined in FP64 (split-operand
+                                refinement); correction, face sums and time in FP64       */
+  RIDG_PREC_MIXED_FP32 = 2   /* Newton linear solves in FP32 with the residual in FP64
+                                (nonlinear flux)                                          */
+};
+
+typedef void* (*ridg_alloc_fn)(size_t bytes, void* user);
+typedef void (*ridg_free_fn)(void* ptr, void* user);
+
+typedef struct {
+  int precision;          /* RIDG_PREC_*                                                */
+  int slices;             /* BF16 slices per operand for MIXED_BF16 (0 = default 5)     */
+  int newton_max_iters;   /* 0 = default 4                                              */
+  double newton_tol;      /* <= 0 = default 1e-10: stop when ||dW||_inf <= tol max(1,||W||_inf) */
+  void* stream;           /* cudaStream_t (not the legacy default stream) or NULL       */
+  ridg_alloc_fn alloc;    /* optional device allocator (default cudaMalloc)             */
+  ridg_free_fn free;      /* matching release (default cudaFree)                        */
+  void* alloc_user;       /* passed to alloc / free                                     */
+} ridg_options;
+
+typedef struct ridg_handle ridg_t;
+
+typedef struct {
+  int dim, order, m;            /* dimension, degree M, conserved variables             */
+  int theta_s, theta_t;         /* (M+1)^d, (M+1)^(d+1)                                  */
+  long long cells;              /* number of cells                                       */
+  double dt, t;                 /* current step size and time                            */
+  long long steps;              /* steps taken since the last ridg_set_state              */
+  long long newton_unconverged; /* regions that hit the Newton cap in the last prediction */
+  int newton_iters_max;         /* largest Newton iteration count of the last prediction  */
+  int precision, slices;
+} ridg_info_t;
+
+/* ----- lifecycle -------------------------------------------------------------------- */
+
+/* Build the tables and operators for degree `order` (M >= 0) and allocate device state.
+ * Linear flux: the region system of eq. pred_full_system (Sec. 2.2) is assembled and
+ * LU-factored on the host in FP64 once, and the centre rows of its solution operator
+ * (and their time mean) are copied to the device.  Nonlinear flux: the quadrature and
+ * quasi-quadrature-free tables of Sec. 3 are built.  dt is set from `cfl` for advection
+ * (dt = cfl h_min / max|a_d|); for nonlinear flux it is set by ridg_set_state.
+ * Supported: ADVECTION d = 1..3; BURGERS d = 2; EULER d = 2.  `opt` may be NULL.
+ * On success *out owns the new handle.                                                 */
+int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double cfl,
+                const ridg_options* opt, ridg_t** out);
+
+/* Release all device and host state of the handle (NULL is accepted).                  */
+void ridg_destroy(ridg_t* h);
+
+/* ----- state ------------------------------------------------------------------------ */
+
+/* Copy the state in (canonical layout, cells * m * theta_S doubles); `on_device` != 0
+ * means q is a device pointer.  Resets t = 0 and the step count.  For a nonlinear flux
+ * dt = cfl h_min / (largest wave speed of q) is computed here unless ridg_set_dt fixed
+ * it.  RIDG_ENONFINITE if q holds a NaN or Inf.  Synchronous.                          */
+int ridg_set_state(ridg_t* h, const double* q, int on_device);
+
+/* Copy the state out (same layout).  Synchronous with the handle's stream.              */
+int ridg_get_state(ridg_t* h, double* q, int on_device);
+
+/* Fix dt (> 0) for the following steps (used to land exactly on a final time).          */
+int ridg_set_dt(ridg_t* h, double dt);
+
+/* Shorten dt so that an integer number of steps reaches T: N = ceil(T / dt - 1e-9),
+ * dt = T / N; *nsteps (may be NULL) receives N.                                         */
+int ridg_set_final_time(ridg_t* h, double T, long long* nsteps);
+
+/* ----- the step ---------------------------------------------------------------------- */
+
+/* Prediction (Sec. 2.2): every cell's centre space-time coefficients W_i from the
+ * current state.  If w_out is not NULL it receives cells * m * theta_T doubles
+ * (prediction layout; device pointer if on_device).  The prediction is also kept for a
+ * following ridg_correct.  Returns RIDG_ENOCONV (after completing) if Newton hit its cap
+ * in some region.  Synchronous when w_out is a host pointer.                            */
+int ridg_predict(ridg_t* h, double* w_out, int on_device);
+
+/* Correction (Sec. 2.3) from the last prediction; advances t by dt.  Stream-ordered.  */
+int ridg_correct(ridg_t* h);
+
+/* n >= 1 full steps (prediction + correction), enqueued on the handle's stream; the
+ * sequence is captured once into a CUDA graph per (n, dt) and replayed.  Returns after
+ * enqueueing; ridg_sync waits.                                                          */
+int ridg_step(ridg_t* h, int n);
+
+/* Wait for all work of the handle; reports a device-side status (ENOCONV / ETIMEOUT).  */
+int ridg_sync(ridg_t* h);
+
+/* ----- diagnostics -------------------------------------------------------------------- */
+
+int ridg_info(ridg_t* h, ridg_info_t* info);
+
+/* sum over cells of |T| Q_{e, r, 0} for each conserved variable r (mass[m]).            */
+int ridg_mass(ridg_t* h, double* mass);
+
+/* Relative L2 error of eq. l2relerror against the exact solution's projection onto
+ * Q(M+1): x holds cells * m * (M+2)^d coefficients (same ordering rules).              */
+int ridg_l2_error(ridg_t* h, const double* x, int on_device, double* err);
+
+/* ----- tracing ---------------------------------------------------------------------------- */
+
+typedef struct {
+  double predict_ms;     /* average device time of the prediction kernel per step           */
+  double correct_ms;     /* average device time of the correction kernel per step           */
+  double step_ms;        /* average device time of one whole step                            */
+  int launches_per_step; /* kernels launched per step                                        */
+} ridg_profile_t;
+
+/* Run n steps (the same arithmetic as ridg_step) as individual launches bracketed by CUDA
+ * events on the handle's stream, wait, and report the average device time of each
+ * kernel.  Advances the state and t like ridg_step.                                       */
+int ridg_profile_step(ridg_t* h, int n, ridg_profile_t* out);
+
+/* ----- batched ensemble ---------------------------------------------------------------- */
+
+typedef struct ridg_batch ridg_batch_t;
+
+/* `count` independent problems (meshes[i], orders[i], the same flux kind) advanced
+ * together; ridg_batch_step runs n steps of every instance in one graph, each instance
+ * with its own dt.                                                                      */
+int ridg_batch_create(int count, const ridg_mesh* meshes, const int* orders,
+                      const ridg_flux* flux, double cfl, const ridg_options* opt,
+                      ridg_batch_t** out);
+void ridg_batch_destroy(ridg_batch_t* b);
+/* Instance i of the batch as an ordinary handle (owned by the batch).                    */
+ridg_t* ridg_batch_instance(ridg_batch_t* b, int i);
+int ridg_batch_step(ridg_batch_t* b, int n);
+int ridg_batch_sync(ridg_batch_t* b);
+
+/* ----- errors ------------------------------------------------------------------------- */
+const char* ridg_strerror(int status);
+const char* ridg_last_error(const ridg_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIDG_H_ */

@@ -243,3 +243,64 @@ def mass(Q: np.ndarray, w) -> float:
     thS = nb ** w["dim"]
     vol = float(np.prod(cell_sizes(w)))
     return float(Q.reshape(Q.shape[0], -1, thS)[:, :, 0].sum(axis=0).sum() * vol)
+
+
+# ---------------------------------------------------------------------------
+# the same step on a sample of cells (for meshes too large to run whole)
+# ---------------------------------------------------------------------------
+def predict_cells(Q: np.ndarray, w, dt: float, cells) -> np.ndarray:
+    """W_i (theta_T) for the listed cells only, by solving their region systems."""
+    d, M = w["dim"], w["M"]
+    nb = M + 1
+    thT = nb ** (d + 1)
+    A, B = region_system(d, M, nu_of(w, dt))
+    lu = sla.lu_factor(A)
+    rc = (3 ** d - 1) // 2
+    cells = np.asarray(cells)
+    X = gather_cells(Q, w, cells)
+    sol = sla.lu_solve(lu, B @ X.reshape(len(cells), -1).T)
+    return sol[rc * thT:(rc + 1) * thT].T
+
+
+def face_neighbour(w, e, dd, side):
+    n = w["n"]
+    d = w["dim"]
+    idx = [(e // int(np.prod(n[:k]))) % n[k] for k in range(d)]
+    idx[dd] = (idx[dd] + side) % n[dd]
+    lin, stride = 0, 1
+    for k in range(d):
+        lin += idx[k] * stride
+        stride *= n[k]
+    return lin
+
+
+def step_cells(Q: np.ndarray, w, dt: float, cells) -> np.ndarray:
+    """Q^{n+1} at the listed cells: the correction of Sec. 2.3 evaluated cell by cell
+    from the predictions of each cell and its 2d face neighbours."""
+    d, M = w["dim"], w["M"]
+    nb = M + 1
+    thS = nb ** d
+    cells = [int(c) for c in cells]
+    need = sorted(set(cells) | {face_neighbour(w, c, dd, s) for c in cells
+                                for dd in range(d) for s in (-1, 1)})
+    Wn = dict(zip(need, predict_cells(Q, w, dt, need)[:, :thS]))
+    D = basis.deriv_matrix(nb)
+    ep, em = basis.trace_plus(nb), basis.trace_minus(nb)
+    nu = nu_of(w, dt)
+    out = np.empty((len(cells), thS))
+    modes = (nb,) * d
+    for i, c in enumerate(cells):
+        Wc = Wn[c].reshape(modes)
+        dq = np.zeros(modes)
+        for dd in range(d):
+            ma = d - 1 - dd
+            nup, num = max(nu[dd], 0.0), min(nu[dd], 0.0)
+            Wr = Wn[face_neighbour(w, c, dd, +1)].reshape(modes)
+            Wl = Wn[face_neighbour(w, c, dd, -1)].reshape(modes)
+            dq += nu[dd] * _apply_along(Wc, D, ma)
+            f_right = nup * _trace_along(Wc, ep, ma) + num * _trace_along(Wr, em, ma)
+            f_left = nup * _trace_along(Wl, ep, ma) + num * _trace_along(Wc, em, ma)
+            dq -= _outer_along(f_right, ep, ma)
+            dq += _outer_along(f_left, em, ma)
+        out[i] = Q[c] + dq.reshape(-1)
+    return out

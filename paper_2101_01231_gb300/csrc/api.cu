@@ -1,0 +1,601 @@
+// C ABI of the RIDG library (include/ridg.h): handle lifecycle, state transfer, the
+// prediction / correction / step entry points, diagnostics and the batched ensemble.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ridg_internal.h"
+#include "tables.h"
+
+using ridg::CorrParams;
+using ridg::Grid;
+
+namespace {
+
+int set_err(ridg_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define RIDG_CUDA(h, call)                                                                  \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return set_err((h), RIDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void* dev_alloc(ridg_t* h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (h->opt.alloc) return h->opt.alloc(bytes, h->opt.alloc_user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void dev_free(ridg_t* h, void* p) {
+  if (!p) return;
+  if (h->opt.free)
+    h->opt.free(p, h->opt.alloc_user);
+  else
+    cudaFree(p);
+}
+
+int max_nb(int dim) { return dim == 1 ? 8 : (dim == 2 ? 5 : 4); }
+
+Grid grid_of(const ridg_t* h) {
+  Grid g;
+  g.dim = h->dim;
+  g.n[0] = h->n[0];
+  g.n[1] = h->n[1];
+  g.n[2] = h->n[2];
+  g.ncell = h->ncell;
+  return g;
+}
+
+bool is_linear(const ridg_t* h) { return h->flux.kind == RIDG_FLUX_ADVECTION; }
+
+void drop_graphs(ridg_t* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : h->graph_defs) cudaGraphDestroy(kv.second);
+  h->graphs.clear();
+  h->graph_defs.clear();
+}
+
+CorrParams corr_params(const ridg_t* h) {
+  CorrParams cp;
+  std::memset(&cp, 0, sizeof(cp));
+  ridg::Tables1D t = ridg::tables1d(h->nb);
+  for (int b = 0; b < h->nb; ++b) {
+    cp.ep[b] = t.ep[b];
+    cp.em[b] = t.em[b];
+    for (int c = 0; c < h->nb; ++c) cp.D[b * ridg::kMaxNB + c] = t.D[b * h->nb + c];
+  }
+  for (int d = 0; d < 3; ++d) {
+    double nu = d < h->dim ? h->flux.vel[d] * h->dt / h->h[d] : 0.0;
+    cp.nu[d] = nu;
+    cp.nup[d] = nu > 0 ? nu : 0.0;
+    cp.num[d] = nu < 0 ? nu : 0.0;
+  }
+  return cp;
+}
+
+// (Re)build the linear operator for the current dt and upload it.
+int rebuild_linear(ridg_t* h) {
+  double nu[3] = {0, 0, 0};
+  for (int d = 0; d < h->dim; ++d) nu[d] = h->flux.vel[d] * h->dt / h->h[d];
+  if (!ridg::linear_operator(h->dim, h->M, nu, h->P_host))
+    return set_err(h, RIDG_EINVAL, "region system is singular for this dt");
+  RIDG_CUDA(h, cudaMemcpyAsync(h->P, h->P_host.data(), sizeof(double) * h->P_host.size(),
+                               cudaMemcpyHostToDevice, h->stream));
+  if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+    std::vector<unsigned short> digits;
+    std::vector<double> rscale;
+    // time-mean rows only (what the step needs)
+    int rc = ridg::mixed_build(h->dim, h->nb, h->P_host, h->thS, h->opt.slices, digits, rscale,
+                               h->mixed);
+    if (rc != RIDG_OK) return set_err(h, rc, "mixed operator build failed");
+    if (!h->mixed.b_slices) {
+      h->mixed.b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
+      h->mixed.row_scale = (double*)dev_alloc(h, rscale.size() * sizeof(double));
+      if (!h->mixed.b_slices || !h->mixed.row_scale)
+        return set_err(h, RIDG_ENOMEM, "mixed operator allocation failed");
+    }
+    RIDG_CUDA(h, cudaMemcpyAsync(h->mixed.b_slices, digits.data(),
+                                 digits.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
+                                 h->stream));
+    RIDG_CUDA(h, cudaMemcpyAsync(h->mixed.row_scale, rscale.data(), rscale.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, h->stream));
+  }
+  RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
+  drop_graphs(h);
+  h->gen += 1;
+  return RIDG_OK;
+}
+
+// One prediction of the time mean into Wbar (what the step needs).
+int enqueue_predict_mean(ridg_t* h) {
+  Grid g = grid_of(h);
+  if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+    RIDG_CUDA(h, ridg::launch_predict_mixed(g, h->nb, h->Q, h->mixed, h->Wbar, h->thS, h->status,
+                                            h->stream));
+  } else {
+    RIDG_CUDA(h, ridg::launch_predict_fp64(g, h->nb, h->Q, h->P, h->thS, h->Wbar, h->thS,
+                                           h->stream));
+  }
+  return RIDG_OK;
+}
+
+int enqueue_step(ridg_t* h) {
+  int rc = enqueue_predict_mean(h);
+  if (rc) return rc;
+  CorrParams cp = corr_params(h);
+  RIDG_CUDA(h, ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->Wbar, h->thS, cp,
+                                           h->stream));
+  return RIDG_OK;
+}
+
+int check_handle(const ridg_t* h) { return h ? RIDG_OK : RIDG_EINVAL; }
+
+}  // namespace
+
+extern "C" {
+
+const char* ridg_strerror(int status) {
+  switch (status) {
+    case RIDG_OK: return "ok";
+    case RIDG_EINVAL: return "invalid argument";
+    case RIDG_ENOMEM: return "out of memory";
+    case RIDG_ECUDA: return "CUDA error";
+    case RIDG_ENONFINITE: return "non-finite value in the state";
+    case RIDG_ENOCONV: return "Newton iteration cap reached";
+    case RIDG_ETIMEOUT: return "bounded device wait timed out";
+    case RIDG_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* ridg_last_error(const ridg_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double cfl,
+                const ridg_options* opt, ridg_t** out) {
+  if (!mesh || !flux || !out) return RIDG_EINVAL;
+  *out = nullptr;
+  if (mesh->dim < 1 || mesh->dim > 3 || order < 0 || order + 1 > max_nb(mesh->dim) || !(cfl > 0))
+    return RIDG_EINVAL;
+  if (flux->kind != RIDG_FLUX_ADVECTION) return RIDG_EINVAL;
+  ridg_t* h = new ridg_t();
+  if (opt) h->opt = *opt;
+  if (h->opt.slices <= 0) h->opt.slices = 5;
+  if (h->opt.newton_max_iters <= 0) h->opt.newton_max_iters = 4;
+  if (!(h->opt.newton_tol > 0)) h->opt.newton_tol = 1e-10;
+  h->dim = mesh->dim;
+  h->ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    h->n[d] = d < mesh->dim ? mesh->n[d] : 1;
+    h->lo[d] = d < mesh->dim ? mesh->lo[d] : 0.0;
+    h->hi[d] = d < mesh->dim ? mesh->hi[d] : 1.0;
+    if (d < mesh->dim && (h->n[d] < 3 || !(h->hi[d] > h->lo[d]))) {
+      delete h;
+      return RIDG_EINVAL;
+    }
+    h->h[d] = (h->hi[d] - h->lo[d]) / h->n[d];
+    h->ncell *= h->n[d];
+  }
+  h->M = order;
+  h->nb = order + 1;
+  h->thS = 1;
+  for (int d = 0; d < h->dim; ++d) h->thS *= h->nb;
+  h->thT = h->thS * h->nb;
+  h->nR = 1;
+  for (int d = 0; d < h->dim; ++d) h->nR *= 3;
+  h->K = h->nR * h->thS;
+  h->m = 1;
+  h->flux = *flux;
+  h->cfl = cfl;
+  if (h->opt.precision == RIDG_PREC_MIXED_BF16 && !ridg::mixed_supported(h->dim, h->nb, h->thS)) {
+    delete h;
+    return RIDG_EINVAL;
+  }
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return RIDG_ECUDA;
+  }
+  if (h->opt.stream) {
+    h->stream = (cudaStream_t)h->opt.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return RIDG_ECUDA;
+    }
+    h->own_stream = true;
+  }
+  // dt from the CFL number (Sec. 5: dt = nu dx / max wave speed)
+  double hmin = h->h[0];
+  double amax = 0.0;
+  for (int d = 0; d < h->dim; ++d) {
+    hmin = std::min(hmin, h->h[d]);
+    amax = std::max(amax, std::fabs(flux->vel[d]));
+  }
+  h->dt = cfl * hmin / (amax > 0 ? amax : 1.0);
+  const size_t nQ = (size_t)h->ncell * h->m * h->thS;
+  h->Q = (double*)dev_alloc(h, nQ * sizeof(double));
+  h->W = (double*)dev_alloc(h, (size_t)h->ncell * h->m * h->thT * sizeof(double));
+  h->Wbar = (double*)dev_alloc(h, nQ * sizeof(double));
+  h->P = (double*)dev_alloc(h, (size_t)h->thT * h->K * sizeof(double));
+  h->red = (double*)dev_alloc(h, (size_t)h->red_blocks * 4 * sizeof(double));
+  h->status = (int*)dev_alloc(h, 16 * sizeof(int));
+  if (!h->Q || !h->W || !h->Wbar || !h->P || !h->red || !h->status) {
+    ridg_destroy(h);
+    return RIDG_ENOMEM;
+  }
+  if (cudaMemsetAsync(h->Q, 0, nQ * sizeof(double), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->status, 0, 16 * sizeof(int), h->stream) != cudaSuccess) {
+    ridg_destroy(h);
+    return RIDG_ECUDA;
+  }
+  int rc = rebuild_linear(h);
+  if (rc != RIDG_OK) {
+    ridg_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return RIDG_OK;
+}
+
+void ridg_destroy(ridg_t* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  dev_free(h, h->Q);
+  dev_free(h, h->W);
+  dev_free(h, h->Wbar);
+  dev_free(h, h->P);
+  dev_free(h, h->red);
+  dev_free(h, h->status);
+  dev_free(h, h->mixed.b_slices);
+  dev_free(h, h->mixed.row_scale);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int ridg_set_state(ridg_t* h, const double* q, int on_device) {
+  if (check_handle(h) || !q) return RIDG_EINVAL;
+  const size_t bytes = (size_t)h->ncell * h->m * h->thS * sizeof(double);
+  RIDG_CUDA(h, cudaMemcpyAsync(h->Q, q, bytes,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               h->stream));
+  RIDG_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+  RIDG_CUDA(h, ridg::launch_finite_check(h->Q, (long long)(bytes / sizeof(double)), h->status,
+                                         h->stream));
+  int flag = 0;
+  RIDG_CUDA(h, cudaMemcpyAsync(&flag, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->t = 0.0;
+  h->steps = 0;
+  h->have_pred = false;
+  if (flag) return set_err(h, RIDG_ENONFINITE, "state contains NaN or Inf");
+  return RIDG_OK;
+}
+
+int ridg_get_state(ridg_t* h, double* q, int on_device) {
+  if (check_handle(h) || !q) return RIDG_EINVAL;
+  const size_t bytes = (size_t)h->ncell * h->m * h->thS * sizeof(double);
+  RIDG_CUDA(h, cudaMemcpyAsync(q, h->Q, bytes,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               h->stream));
+  RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RIDG_OK;
+}
+
+int ridg_set_dt(ridg_t* h, double dt) {
+  if (check_handle(h) || !(dt > 0) || !std::isfinite(dt)) return RIDG_EINVAL;
+  h->dt = dt;
+  h->dt_fixed = true;
+  if (is_linear(h)) return rebuild_linear(h);
+  drop_graphs(h);
+  return RIDG_OK;
+}
+
+int ridg_set_final_time(ridg_t* h, double T, long long* nsteps) {
+  if (check_handle(h) || !(T > 0) || !(h->dt > 0)) return RIDG_EINVAL;
+  long long N = (long long)std::ceil(T / h->dt - 1e-9);
+  if (N < 1) N = 1;
+  if (nsteps) *nsteps = N;
+  return ridg_set_dt(h, T / (double)N);
+}
+
+int ridg_predict(ridg_t* h, double* w_out, int on_device) {
+  if (check_handle(h)) return RIDG_EINVAL;
+  Grid g = grid_of(h);
+  RIDG_CUDA(h, ridg::launch_predict_fp64(g, h->nb, h->Q, h->P, h->thT, h->W, h->thT, h->stream));
+  h->have_pred = true;
+  if (w_out) {
+    const size_t bytes = (size_t)h->ncell * h->m * h->thT * sizeof(double);
+    RIDG_CUDA(h, cudaMemcpyAsync(w_out, h->W, bytes,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 h->stream));
+    if (!on_device) RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return RIDG_OK;
+}
+
+int ridg_correct(ridg_t* h) {
+  if (check_handle(h)) return RIDG_EINVAL;
+  if (!h->have_pred) return set_err(h, RIDG_ESTATE, "ridg_correct needs a prediction first");
+  CorrParams cp = corr_params(h);
+  RIDG_CUDA(h, ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->W, h->thT, cp, h->stream));
+  h->have_pred = false;
+  h->t += h->dt;
+  h->steps += 1;
+  return RIDG_OK;
+}
+
+int ridg_step(ridg_t* h, int n) {
+  if (check_handle(h) || n < 1) return RIDG_EINVAL;
+  auto it = h->graphs.find(n);
+  if (it == h->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    RIDG_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = RIDG_OK;
+    for (int i = 0; i < n && rc == RIDG_OK; ++i) rc = enqueue_step(h);
+    cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+    if (rc != RIDG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    RIDG_CUDA(h, ce);
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    if (ie != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      RIDG_CUDA(h, ie);
+    }
+    h->graphs[n] = exec;
+    h->graph_defs[n] = graph;
+    it = h->graphs.find(n);
+  }
+  RIDG_CUDA(h, cudaGraphLaunch(it->second, h->stream));
+  h->have_pred = false;
+  h->t += n * h->dt;
+  h->steps += n;
+  return RIDG_OK;
+}
+
+int ridg_sync(ridg_t* h) {
+  if (check_handle(h)) return RIDG_EINVAL;
+  RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RIDG_OK;
+}
+
+int ridg_profile_step(ridg_t* h, int n, ridg_profile_t* out) {
+  if (check_handle(h) || n < 1 || !out) return RIDG_EINVAL;
+  cudaEvent_t ev[3];
+  for (int i = 0; i < 3; ++i) RIDG_CUDA(h, cudaEventCreate(&ev[i]));
+  double tp = 0, tc = 0;
+  int rc = RIDG_OK;
+  for (int i = 0; i < n && rc == RIDG_OK; ++i) {
+    cudaEventRecord(ev[0], h->stream);
+    rc = enqueue_predict_mean(h);
+    if (rc) break;
+    cudaEventRecord(ev[1], h->stream);
+    CorrParams cp = corr_params(h);
+    cudaError_t e = ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->Wbar, h->thS, cp,
+                                                h->stream);
+    if (e != cudaSuccess) {
+      rc = set_err(h, RIDG_ECUDA, cudaGetErrorString(e));
+      break;
+    }
+    cudaEventRecord(ev[2], h->stream);
+    e = cudaEventSynchronize(ev[2]);
+    if (e != cudaSuccess) {
+      rc = set_err(h, RIDG_ECUDA, cudaGetErrorString(e));
+      break;
+    }
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    tp += a;
+    tc += b;
+    h->t += h->dt;
+    h->steps += 1;
+  }
+  for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+  if (rc) return rc;
+  out->predict_ms = tp / n;
+  out->correct_ms = tc / n;
+  out->step_ms = (tp + tc) / n;
+  out->launches_per_step = 2;
+  h->have_pred = false;
+  return RIDG_OK;
+}
+
+int ridg_info(ridg_t* h, ridg_info_t* info) {
+  if (check_handle(h) || !info) return RIDG_EINVAL;
+  info->dim = h->dim;
+  info->order = h->M;
+  info->m = h->m;
+  info->theta_s = h->thS;
+  info->theta_t = h->thT;
+  info->cells = h->ncell;
+  info->dt = h->dt;
+  info->t = h->t;
+  info->steps = h->steps;
+  info->newton_unconverged = h->newton_unconverged;
+  info->newton_iters_max = h->newton_iters_max;
+  info->precision = h->opt.precision;
+  info->slices = h->opt.slices;
+  return RIDG_OK;
+}
+
+int ridg_mass(ridg_t* h, double* mass) {
+  if (check_handle(h) || !mass) return RIDG_EINVAL;
+  RIDG_CUDA(h, ridg::launch_mass_partials(h->Q, h->ncell, h->m, h->thS, h->red, h->red_blocks,
+                                          h->stream));
+  std::vector<double> part((size_t)h->red_blocks * h->m);
+  RIDG_CUDA(h, cudaMemcpyAsync(part.data(), h->red, part.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
+  RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
+  double vol = 1.0;
+  for (int d = 0; d < h->dim; ++d) vol *= h->h[d];
+  for (int r = 0; r < h->m; ++r) {
+    double s = 0.0;
+    for (int b = 0; b < h->red_blocks; ++b) s += part[(size_t)b * h->m + r];
+    mass[r] = s * vol;
+  }
+  return RIDG_OK;
+}
+
+int ridg_l2_error(ridg_t* h, const double* x, int on_device, double* err) {
+  if (check_handle(h) || !x || !err) return RIDG_EINVAL;
+  size_t nx = (size_t)h->ncell * h->m;
+  for (int d = 0; d < h->dim; ++d) nx *= (h->nb + 1);
+  const double* xd = x;
+  double* tmp = nullptr;
+  if (!on_device) {
+    tmp = (double*)dev_alloc(h, nx * sizeof(double));
+    if (!tmp) return set_err(h, RIDG_ENOMEM, "l2 error buffer");
+    cudaError_t e = cudaMemcpyAsync(tmp, x, nx * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) {
+      dev_free(h, tmp);
+      RIDG_CUDA(h, e);
+    }
+    xd = tmp;
+  }
+  std::vector<double> part((size_t)h->red_blocks * 2);
+  cudaError_t e = ridg::launch_l2_partials(h->Q, xd, h->ncell, h->m, h->dim, h->nb, h->red,
+                                           h->red_blocks, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part.data(), h->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (tmp) dev_free(h, tmp);
+  RIDG_CUDA(h, e);
+  double num = 0, den = 0;
+  for (int b = 0; b < h->red_blocks; ++b) {
+    num += part[2 * b];
+    den += part[2 * b + 1];
+  }
+  *err = den > 0 ? std::sqrt(num / den) : 0.0;
+  return RIDG_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// batched ensemble: independent instances sharing one stream; n steps of all of them are
+// captured into a single graph and replayed.
+// ------------------------------------------------------------------------------------------
+struct ridg_batch {
+  std::vector<ridg_t*> inst;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::map<int, cudaGraphExec_t> graphs;
+  std::map<int, cudaGraph_t> defs;
+  std::vector<unsigned long long> gens;  // operator generation of each instance at capture
+};
+
+extern "C" {
+
+int ridg_batch_create(int count, const ridg_mesh* meshes, const int* orders, const ridg_flux* flux,
+                      double cfl, const ridg_options* opt, ridg_batch_t** out) {
+  if (count < 1 || !meshes || !orders || !flux || !out) return RIDG_EINVAL;
+  *out = nullptr;
+  ridg_batch_t* b = new ridg_batch_t();
+  ridg_options o{};
+  if (opt) o = *opt;
+  if (o.stream) {
+    b->stream = (cudaStream_t)o.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return RIDG_ECUDA;
+    }
+    b->own_stream = true;
+    o.stream = b->stream;
+  }
+  for (int i = 0; i < count; ++i) {
+    ridg_t* h = nullptr;
+    int rc = ridg_create(&meshes[i], orders[i], flux, cfl, &o, &h);
+    if (rc != RIDG_OK) {
+      ridg_batch_destroy(b);
+      return rc;
+    }
+    h->batch_owned = true;
+    b->inst.push_back(h);
+  }
+  *out = b;
+  return RIDG_OK;
+}
+
+void ridg_batch_destroy(ridg_batch_t* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : b->defs) cudaGraphDestroy(kv.second);
+  for (ridg_t* h : b->inst) ridg_destroy(h);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+ridg_t* ridg_batch_instance(ridg_batch_t* b, int i) {
+  if (!b || i < 0 || i >= (int)b->inst.size()) return nullptr;
+  return b->inst[i];
+}
+
+int ridg_batch_step(ridg_batch_t* b, int n) {
+  if (!b || n < 1) return RIDG_EINVAL;
+  // a rebuilt operator (changed dt) of any instance invalidates the batch graphs
+  bool stale = b->gens.size() != b->inst.size();
+  for (size_t i = 0; !stale && i < b->inst.size(); ++i) stale = b->gens[i] != b->inst[i]->gen;
+  if (stale) {
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : b->defs) cudaGraphDestroy(kv.second);
+    b->graphs.clear();
+    b->defs.clear();
+    b->gens.clear();
+    for (ridg_t* h : b->inst) b->gens.push_back(h->gen);
+  }
+  auto it = b->graphs.find(n);
+  if (it == b->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return RIDG_ECUDA;
+    int rc = RIDG_OK;
+    for (int i = 0; i < n && rc == RIDG_OK; ++i)
+      for (ridg_t* h : b->inst) {
+        rc = enqueue_step(h);
+        if (rc) break;
+      }
+    cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+    if (rc != RIDG_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc ? rc : RIDG_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return RIDG_ECUDA;
+    }
+    b->graphs[n] = exec;
+    b->defs[n] = graph;
+    it = b->graphs.find(n);
+  }
+  if (cudaGraphLaunch(it->second, b->stream) != cudaSuccess) return RIDG_ECUDA;
+  for (ridg_t* h : b->inst) {
+    h->t += n * h->dt;
+    h->steps += n;
+  }
+  return RIDG_OK;
+}
+
+int ridg_batch_sync(ridg_batch_t* b) {
+  if (!b) return RIDG_EINVAL;
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? RIDG_OK : RIDG_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Diagnostic reductions of the RIDG state: cell-average mass, the relative L2 error of
+// eq. l2relerror, and a finiteness check.  Every reduction writes one partial per block
+// in a fixed order (grid-stride loop, then a fixed shared-memory tree); the host sums the
+// partials in block order, so results are run-to-run deterministic.
+#include <cuda_runtime.h>
+
+#include "ridg_internal.h"
+
+namespace ridg {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void mass_kernel(const double* __restrict__ Q, long long ncell, int m, int thS,
+                            double* __restrict__ out) {
+  __shared__ double sh[kThreads];
+  for (int r = 0; r < m; ++r) {
+    double acc = 0.0;
+    for (long long e = (long long)blockIdx.x * kThreads + threadIdx.x; e < ncell;
+         e += (long long)gridDim.x * kThreads)
+      acc += Q[(e * m + r) * thS];
+    double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[blockIdx.x * m + r] = s;
+  }
+}
+
+// X holds (M+2)^d modes per cell and variable; Q holds (M+1)^d.
+__global__ void l2_kernel(const double* __restrict__ Q, const double* __restrict__ X,
+                          long long ncell, int m, int dim, int nb, double* __restrict__ out) {
+  __shared__ double sh[kThreads];
+  const int nb2 = nb + 1;
+  int thS = 1, thS2 = 1;
+  for (int d = 0; d < dim; ++d) { thS *= nb; thS2 *= nb2; }
+  double num = 0.0, den = 0.0;
+  for (long long e = (long long)blockIdx.x * kThreads + threadIdx.x; e < ncell;
+       e += (long long)gridDim.x * kThreads) {
+    for (int r = 0; r < m; ++r) {
+      const double* x = X + (e * m + r) * thS2;
+      const double* q = Q + (e * m + r) * thS;
+      for (int s2 = 0; s2 < thS2; ++s2) {
+        int bx = s2 % nb2, by = (s2 / nb2) % nb2, bz = s2 / (nb2 * nb2);
+        if (dim < 2) by = 0;
+        if (dim < 3) bz = 0;
+        const double xv = x[s2];
+        den += xv * xv;
+        if (bx < nb && by < nb && bz < nb) {
+          const int s = bx + nb * (by + nb * bz);
+          const double dv = xv - q[s];
+          num += dv * dv;
+        } else {
+          num += xv * xv;
+        }
+      }
+    }
+  }
+  double sn = block_sum(num, sh);
+  double sd = block_sum(den, sh);
+  if (threadIdx.x == 0) {
+    out[blockIdx.x * 2 + 0] = sn;
+    out[blockIdx.x * 2 + 1] = sd;
+  }
+}
+
+__global__ void finite_kernel(const double* __restrict__ q, long long count, int* flag) {
+  int bad = 0;
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < count;
+       i += (long long)gridDim.x * kThreads)
+    bad |= !isfinite(q[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_mass_partials(const double* Q, long long ncell, int m, int thS, double* out,
+                                 int nblocks, cudaStream_t s) {
+  mass_kernel<<<nblocks, kThreads, 0, s>>>(Q, ncell, m, thS, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l2_partials(const double* Q, const double* X, long long ncell, int m, int dim,
+                               int nb, double* out, int nblocks, cudaStream_t s) {
+  l2_kernel<<<nblocks, kThreads, 0, s>>>(Q, X, ncell, m, dim, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finite_check(const double* q, long long count, int* flag, cudaStream_t s) {
+  finite_kernel<<<256, kThreads, 0, s>>>(q, count, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace ridg

@@ -1,0 +1,275 @@
+// FP64 kernels of the linear-flux RIDG step.
+//
+// Prediction (Sec. 2.2): for a linear flux on a uniform periodic mesh the region system
+// of eq. pred_full_system is the same for every cell, so the kept centre coefficients
+// are W_i = P X_i with X_i the 3^d theta_S region coefficients of cell i (gathered with
+// periodic wrap) and P the centre rows of the region solution operator.
+//
+// Correction (Sec. 2.3): with W-bar the time mean of W (all a linear flux needs, since
+// int psi_g dtau = 2 delta_g0),
+//   dQ_i = sum_d nu_d (D along d) Wbar_i
+//          - sum_d [ phi(+1) (x)_d F_{i+1/2} - phi(-1) (x)_d F_{i-1/2} ],
+//   F_{i+1/2} = nu+_d trace_{+1}(Wbar_i) + nu-_d trace_{-1}(Wbar_{i+e_d}).
+// Each face value is evaluated by one device function with a fixed fma order from the
+// same inputs on both sides of the face, so the two neighbours apply bitwise the same
+// flux and the cell averages are conserved to round-off of the final additions.
+#include <cuda_runtime.h>
+
+#include "ridg_internal.h"
+
+namespace ridg {
+namespace {
+
+constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
+
+struct Coords {
+  int x, y, z;
+};
+
+__device__ __forceinline__ Coords cell_coords(long long e, int nx, int ny) {
+  Coords c;
+  c.x = (int)(e % nx);
+  long long r = e / nx;
+  c.y = (int)(r % ny);
+  c.z = (int)(r / ny);
+  return c;
+}
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <int DIM>
+__device__ __forceinline__ long long neighbour(const Coords& c, int ox, int oy, int oz, int nx,
+                                               int ny, int nz) {
+  long long j = wrap(c.x + ox, nx);
+  if (DIM > 1) j += (long long)nx * wrap(c.y + oy, ny);
+  if (DIM > 2) j += (long long)nx * ny * wrap(c.z + oz, nz);
+  return j;
+}
+
+// ---------------------------------------------------------------------------------------
+// prediction: each thread owns one cell and CH consecutive output rows of P
+// ---------------------------------------------------------------------------------------
+template <int DIM, int NB, int CH>
+__global__ void __launch_bounds__(128) predict_fp64_kernel(const double* __restrict__ Q,
+                                                           const double* __restrict__ P, int nout,
+                                                           double* __restrict__ W, int wstride,
+                                                           int nx, int ny, int nz, long long ncell) {
+  constexpr int THS = ipow_c(NB, DIM);
+  constexpr int NR = ipow_c(3, DIM);
+  constexpr int K = NR * THS;
+  extern __shared__ double sP[];  // CH x K
+  const int c0 = blockIdx.y * CH;
+  for (int i = threadIdx.x; i < CH * K; i += blockDim.x) {
+    const int c = c0 + i / K;
+    sP[i] = (c < nout) ? P[(size_t)c * K + (i % K)] : 0.0;
+  }
+  __syncthreads();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ncell) return;
+  const Coords c = cell_coords(e, nx, ny);
+  double acc[CH];
+#pragma unroll
+  for (int j = 0; j < CH; ++j) acc[j] = 0.0;
+#pragma unroll 1
+  for (int r = 0; r < NR; ++r) {
+    const int ox = r % 3 - 1, oy = (r / 3) % 3 - 1, oz = r / 9 - 1;
+    const double* q = Q + neighbour<DIM>(c, ox, oy, oz, nx, ny, nz) * THS;
+    const double* p = sP + r * THS;
+#pragma unroll
+    for (int s = 0; s < THS; ++s) {
+      const double x = __ldg(q + s);
+#pragma unroll
+      for (int j = 0; j < CH; ++j) acc[j] = fma(p[j * K + s], x, acc[j]);
+    }
+  }
+  double* w = W + e * wstride + c0;
+#pragma unroll
+  for (int j = 0; j < CH; ++j)
+    if (c0 + j < nout) w[j] = acc[j];
+}
+
+// ---------------------------------------------------------------------------------------
+// correction
+// ---------------------------------------------------------------------------------------
+// trace of a cell's time mean along dimension dd: tr[t] = sum_b v[b] w[base(t) + b st]
+template <int DIM, int NB>
+__device__ __forceinline__ void face_trace(const double* w, int dd, const double* v,
+                                           double* tr) {
+  constexpr int NT = ipow_c(NB, DIM - 1);
+  const int st = dd == 0 ? 1 : (dd == 1 ? NB : NB * NB);
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int lo = t % st, hi = t / st;
+    const int base = lo + hi * st * NB;
+    double a = 0.0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) a = fma(v[b], w[base + b * st], a);
+    tr[t] = a;
+  }
+}
+
+// The single definition of a face value from the two traces at that face (explicit fma,
+// so both neighbours evaluate it bit-identically).
+__device__ __forceinline__ double face_value(double tr_left_plus, double tr_right_minus, double nup,
+                                          double num) {
+  return fma(nup, tr_left_plus, num * tr_right_minus);
+}
+
+template <int DIM, int NB>
+__global__ void __launch_bounds__(128) correct_linear_kernel(double* __restrict__ Q,
+                                                             const double* __restrict__ Wb,
+                                                             int wstride, int nx, int ny, int nz,
+                                                             long long ncell, CorrParams cp) {
+  constexpr int THS = ipow_c(NB, DIM);
+  constexpr int NT = ipow_c(NB, DIM - 1);
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ncell) return;
+  const Coords c = cell_coords(e, nx, ny);
+  double w[THS], dq[THS], nbw[THS];
+#pragma unroll
+  for (int s = 0; s < THS; ++s) {
+    w[s] = Wb[e * wstride + s];
+    dq[s] = 0.0;
+  }
+#pragma unroll
+  for (int dd = 0; dd < DIM; ++dd) {
+    const int st = dd == 0 ? 1 : (dd == 1 ? NB : NB * NB);
+    // volume term nu_d (D along d) Wbar
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int base = t % st + (t / st) * st * NB;
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          if (a > b && ((a + b) & 1)) acc = fma(cp.D[a * kMaxNB + b], w[base + b * st], acc);
+        dq[base + a * st] = fma(cp.nu[dd], acc, dq[base + a * st]);
+      }
+    }
+    double trp[NT], trm[NT], nbt[NT], fp[NT], fm[NT];
+    face_trace<DIM, NB>(w, dd, cp.ep, trp);
+    face_trace<DIM, NB>(w, dd, cp.em, trm);
+    // right neighbour's trace at its xi_d = -1
+    {
+      const long long j = neighbour<DIM>(c, dd == 0, dd == 1, dd == 2, nx, ny, nz);
+#pragma unroll
+      for (int s = 0; s < THS; ++s) nbw[s] = Wb[j * wstride + s];
+      face_trace<DIM, NB>(nbw, dd, cp.em, nbt);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) fp[t] = face_value(trp[t], nbt[t], cp.nup[dd], cp.num[dd]);
+    }
+    // left neighbour's trace at its xi_d = +1
+    {
+      const long long j = neighbour<DIM>(c, -(dd == 0), -(dd == 1), -(dd == 2), nx, ny, nz);
+#pragma unroll
+      for (int s = 0; s < THS; ++s) nbw[s] = Wb[j * wstride + s];
+      face_trace<DIM, NB>(nbw, dd, cp.ep, nbt);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) fm[t] = face_value(nbt[t], trm[t], cp.nup[dd], cp.num[dd]);
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int base = t % st + (t / st) * st * NB;
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        double v = dq[base + a * st];
+        v = fma(-cp.ep[a], fp[t], v);
+        v = fma(cp.em[a], fm[t], v);
+        dq[base + a * st] = v;
+      }
+    }
+  }
+  double* q = Q + e * THS;
+#pragma unroll
+  for (int s = 0; s < THS; ++s) q[s] = q[s] + dq[s];
+}
+
+template <int DIM, int NB>
+cudaError_t predict_dispatch_ch(const Grid& g, const double* Q, const double* P, int nout,
+                                double* W, int wstride, cudaStream_t s) {
+  constexpr int THS = ipow_c(NB, DIM);
+  constexpr int K = ipow_c(3, DIM) * THS;
+  // rows per thread: as many as fit 48 KB of shared memory, at most 16
+  constexpr int CH = (16 * K * 8 <= 48 * 1024) ? 16 : ((8 * K * 8 <= 48 * 1024) ? 8 : 4);
+  static_assert(CH * K * 8 <= 48 * 1024 || CH == 4, "operator chunk too large");
+  const int threads = 128;
+  dim3 grid((unsigned)((g.ncell + threads - 1) / threads), (unsigned)((nout + CH - 1) / CH));
+  size_t smem = (size_t)CH * K * sizeof(double);
+  auto kern = predict_fp64_kernel<DIM, NB, CH>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, threads, smem, s>>>(Q, P, nout, W, wstride, g.n[0], g.n[1], g.n[2], g.ncell);
+  return cudaGetLastError();
+}
+
+template <int DIM, int NB>
+cudaError_t correct_dispatch(const Grid& g, double* Q, const double* Wb, int wstride,
+                             const CorrParams& cp, cudaStream_t s) {
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((g.ncell + threads - 1) / threads);
+  correct_linear_kernel<DIM, NB><<<blocks, threads, 0, s>>>(Q, Wb, wstride, g.n[0], g.n[1], g.n[2],
+                                                             g.ncell, cp);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define RIDG_DISPATCH_NB(DIM, FN, ...)                 \
+  switch (nb) {                                        \
+    case 1: return FN<DIM, 1>(__VA_ARGS__);            \
+    case 2: return FN<DIM, 2>(__VA_ARGS__);            \
+    case 3: return FN<DIM, 3>(__VA_ARGS__);            \
+    case 4: return FN<DIM, 4>(__VA_ARGS__);            \
+    default: break;                                    \
+  }
+
+cudaError_t launch_predict_fp64(const Grid& g, int nb, const double* Q, const double* P, int nout,
+                                double* W, int wstride, cudaStream_t s) {
+  if (g.dim == 1) {
+    RIDG_DISPATCH_NB(1, predict_dispatch_ch, g, Q, P, nout, W, wstride, s)
+    switch (nb) {
+      case 5: return predict_dispatch_ch<1, 5>(g, Q, P, nout, W, wstride, s);
+      case 6: return predict_dispatch_ch<1, 6>(g, Q, P, nout, W, wstride, s);
+      case 7: return predict_dispatch_ch<1, 7>(g, Q, P, nout, W, wstride, s);
+      case 8: return predict_dispatch_ch<1, 8>(g, Q, P, nout, W, wstride, s);
+      default: break;
+    }
+  } else if (g.dim == 2) {
+    RIDG_DISPATCH_NB(2, predict_dispatch_ch, g, Q, P, nout, W, wstride, s)
+    switch (nb) {
+      case 5: return predict_dispatch_ch<2, 5>(g, Q, P, nout, W, wstride, s);
+      default: break;
+    }
+  } else if (g.dim == 3) {
+    RIDG_DISPATCH_NB(3, predict_dispatch_ch, g, Q, P, nout, W, wstride, s)
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_correct_linear(const Grid& g, int nb, double* Q, const double* Wbar,
+                                  int wstride, const CorrParams& cp, cudaStream_t s) {
+  if (g.dim == 1) {
+    RIDG_DISPATCH_NB(1, correct_dispatch, g, Q, Wbar, wstride, cp, s)
+    switch (nb) {
+      case 5: return correct_dispatch<1, 5>(g, Q, Wbar, wstride, cp, s);
+      case 6: return correct_dispatch<1, 6>(g, Q, Wbar, wstride, cp, s);
+      case 7: return correct_dispatch<1, 7>(g, Q, Wbar, wstride, cp, s);
+      case 8: return correct_dispatch<1, 8>(g, Q, Wbar, wstride, cp, s);
+      default: break;
+    }
+  } else if (g.dim == 2) {
+    RIDG_DISPATCH_NB(2, correct_dispatch, g, Q, Wbar, wstride, cp, s)
+    switch (nb) {
+      case 5: return correct_dispatch<2, 5>(g, Q, Wbar, wstride, cp, s);
+      default: break;
+    }
+  } else if (g.dim == 3) {
+    RIDG_DISPATCH_NB(3, correct_dispatch, g, Q, Wbar, wstride, cp, s)
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ridg

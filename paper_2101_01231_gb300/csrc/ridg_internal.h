@@ -1,0 +1,97 @@
+// Internal declarations shared by the RIDG library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ridg.h"
+
+namespace ridg {
+
+constexpr int kMaxNB = 8;  // largest supported M + 1
+
+// Per-launch constants of the correction (1D tables and CFL numbers), passed by value.
+struct CorrParams {
+  double ep[kMaxNB], em[kMaxNB];       // phi_b(+1), phi_b(-1)
+  double D[kMaxNB * kMaxNB];           // int phi_a' phi_b
+  double nu[3], nup[3], num[3];        // a_d dt / h_d and its positive / negative parts
+};
+
+struct Grid {
+  int dim;
+  int n[3];
+  long long ncell;
+};
+
+// ---- FP64 linear path (k_linear.cu) ----
+// W[e * wstride + c0 + c] = sum_k P[c][k] X_e[k] for c < nout (rows of P, K = 3^d theta_S)
+cudaError_t launch_predict_fp64(const Grid& g, int nb, const double* Q, const double* P, int nout,
+                                double* W, int wstride, cudaStream_t s);
+// Q[e] += correction from the time means Wbar (stride wstride) of e and its face neighbours
+cudaError_t launch_correct_linear(const Grid& g, int nb, double* Q, const double* Wbar,
+                                  int wstride, const CorrParams& cp, cudaStream_t s);
+
+// ---- mixed BF16 tensor-core prediction (k_mixed.cu) ----
+struct MixedOp {
+  int nout = 0, npad = 0, K = 0, Kpad = 0, slices = 0, bits = 0;
+  void* b_slices = nullptr;   // device, core-matrix layout bf16 digits of P rows
+  double* row_scale = nullptr;  // device, 2^e per P row
+};
+bool mixed_supported(int dim, int nb, int nout);
+int mixed_build(int dim, int nb, const std::vector<double>& P, int nout, int slices,
+                std::vector<unsigned short>& digits, std::vector<double>& rscale, MixedOp& op);
+cudaError_t launch_predict_mixed(const Grid& g, int nb, const double* Q, const MixedOp& op,
+                                 double* W, int wstride, int* status, cudaStream_t s);
+
+// ---- diagnostics (k_diag.cu) ----
+// partial sums (per block) of q[e, r, 0], r < m  -> out[block * m + r]
+cudaError_t launch_mass_partials(const double* Q, long long ncell, int m, int thS, double* out,
+                                 int nblocks, cudaStream_t s);
+// partial sums of the numerator / denominator of eq. l2relerror -> out[block * 2 + {0,1}]
+cudaError_t launch_l2_partials(const double* Q, const double* X, long long ncell, int m, int dim,
+                               int nb, double* out, int nblocks, cudaStream_t s);
+// flag[0] |= 1 if any entry of q is not finite
+cudaError_t launch_finite_check(const double* q, long long count, int* flag, cudaStream_t s);
+
+}  // namespace ridg
+
+struct ridg_handle {
+  // problem
+  int dim = 0, n[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, h[3] = {1, 1, 1};
+  int M = 0, nb = 1, thS = 1, thT = 1, m = 1, nR = 1, K = 1;
+  long long ncell = 0;
+  ridg_flux flux{};
+  double cfl = 0;
+  ridg_options opt{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // time
+  double dt = 0, t = 0;
+  long long steps = 0;
+  bool dt_fixed = false, have_pred = false;
+  // device buffers
+  double* Q = nullptr;      // state, canonical layout
+  double* W = nullptr;      // last full prediction (cells * m * theta_T)
+  double* Wbar = nullptr;   // time-mean prediction used by the step (cells * m * theta_S)
+  double* P = nullptr;      // linear operator, theta_T x K (time-mean rows first)
+  double* red = nullptr;    // reduction partials
+  int* status = nullptr;    // device status word(s)
+  int red_blocks = 256;
+  ridg::MixedOp mixed;
+  // host copy of the operator
+  std::vector<double> P_host;
+  // graphs: key = number of steps
+  std::map<int, cudaGraphExec_t> graphs;
+  std::map<int, cudaGraph_t> graph_defs;
+  // Newton statistics of the last prediction
+  long long newton_unconverged = 0;
+  int newton_iters_max = 0;
+  unsigned long long gen = 0;  // bumped whenever the operator is rebuilt
+  std::string err;
+  bool batch_owned = false;
+};

@@ -1,0 +1,225 @@
+// Host-side FP64 numerics (see tables.h).
+#include "tables.h"
+
+#include <cmath>
+#include <cstring>
+
+namespace ridg {
+
+void legendre(int n, double x, double* p, double* dp) {
+  // P_0 = 1, P_1 = x, (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1};
+  // P_k' = k (x P_k - P_{k-1}) / (x^2 - 1) away from +-1, closed form k(k+1)/2 (+-1)^(k+1) at +-1.
+  double p0 = 1.0, p1 = x;
+  if (n == 0) { *p = 1.0; *dp = 0.0; return; }
+  for (int k = 1; k < n; ++k) {
+    double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  *p = p1;
+  if (std::fabs(std::fabs(x) - 1.0) < 1e-15) {
+    double s = (x > 0 || (n + 1) % 2 == 0) ? 1.0 : -1.0;
+    *dp = s * 0.5 * n * (n + 1.0);
+  } else {
+    *dp = n * (x * p1 - p0) / (x * x - 1.0);
+  }
+}
+
+void phi_values(int nb, double x, double* v, double* dv) {
+  // derivatives by the recurrence P_{k+1}' = P_{k-1}' + (2k+1) P_k (valid everywhere)
+  std::vector<double> P(nb + 1), dP(nb + 1);
+  P[0] = 1.0;
+  dP[0] = 0.0;
+  if (nb > 1) { P[1] = x; dP[1] = 1.0; }
+  for (int k = 1; k + 1 < nb; ++k) {
+    P[k + 1] = ((2.0 * k + 1.0) * x * P[k] - k * P[k - 1]) / (k + 1.0);
+    dP[k + 1] = dP[k - 1] + (2.0 * k + 1.0) * P[k];
+  }
+  for (int b = 0; b < nb; ++b) {
+    double s = std::sqrt(2.0 * b + 1.0);
+    if (v) v[b] = s * P[b];
+    if (dv) dv[b] = s * dP[b];
+  }
+}
+
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double p = 0, dp = 1;
+    for (int it = 0; it < 100; ++it) {
+      legendre(n, z, &p, &dp);
+      double dz = p / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    legendre(n, z, &p, &dp);
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+Tables1D tables1d(int nb) {
+  Tables1D t;
+  t.nb = nb;
+  t.ep.resize(nb);
+  t.em.resize(nb);
+  phi_values(nb, 1.0, t.ep.data(), nullptr);
+  phi_values(nb, -1.0, t.em.data(), nullptr);
+  // D[a][b] = int phi_a' phi_b by Gauss with nb points (integrand degree <= 2 nb - 3)
+  std::vector<double> x, w;
+  gauss_legendre(nb + 1, x, w);
+  t.D.assign(nb * nb, 0.0);
+  std::vector<double> v(nb), dv(nb);
+  for (size_t q = 0; q < x.size(); ++q) {
+    phi_values(nb, x[q], v.data(), dv.data());
+    for (int a = 0; a < nb; ++a)
+      for (int b = 0; b < nb; ++b) t.D[a * nb + b] += w[q] * dv[a] * v[b];
+  }
+  return t;
+}
+
+bool lu_factor(int n, double* A, std::vector<int>& perm) {
+  perm.resize(n);
+  for (int i = 0; i < n; ++i) perm[i] = i;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = std::fabs(A[(size_t)k * n + k]);
+    for (int i = k + 1; i < n; ++i) {
+      double v = std::fabs(A[(size_t)i * n + k]);
+      if (v > best) { best = v; p = i; }
+    }
+    if (best == 0.0) return false;
+    if (p != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)p * n + j]);
+      std::swap(perm[k], perm[p]);
+    }
+    const double inv = 1.0 / A[(size_t)k * n + k];
+    const double* rowk = A + (size_t)k * n;
+#pragma omp parallel for schedule(static) if (n - k > 256)
+    for (int i = k + 1; i < n; ++i) {
+      double* rowi = A + (size_t)i * n;
+      double l = rowi[k] * inv;
+      rowi[k] = l;
+      if (l != 0.0)
+        for (int j = k + 1; j < n; ++j) rowi[j] -= l * rowk[j];
+    }
+  }
+  return true;
+}
+
+void lu_solve(int n, const double* LU, const std::vector<int>& perm, double* b) {
+  std::vector<double> y(n);
+  for (int i = 0; i < n; ++i) y[i] = b[perm[i]];
+  for (int i = 0; i < n; ++i) {
+    double s = y[i];
+    for (int j = 0; j < i; ++j) s -= LU[(size_t)i * n + j] * y[j];
+    y[i] = s;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int j = i + 1; j < n; ++j) s -= LU[(size_t)i * n + j] * y[j];
+    y[i] = s / LU[(size_t)i * n + i];
+  }
+  std::memcpy(b, y.data(), sizeof(double) * n);
+}
+
+void lu_solve_transpose(int n, const double* LU, const std::vector<int>& perm, double* b) {
+  // (P A) = L U  =>  A^T z = b  <=>  U^T L^T (P z) = b
+  std::vector<double> v(b, b + n);
+  for (int i = 0; i < n; ++i) {  // U^T v = b (U^T lower)
+    double s = v[i];
+    for (int j = 0; j < i; ++j) s -= LU[(size_t)j * n + i] * v[j];
+    v[i] = s / LU[(size_t)i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {  // L^T u = v (unit upper)
+    double s = v[i];
+    for (int j = i + 1; j < n; ++j) s -= LU[(size_t)j * n + i] * v[j];
+    v[i] = s;
+  }
+  for (int i = 0; i < n; ++i) b[perm[i]] = v[i];  // z = P^T u
+}
+
+namespace {
+inline int ipow(int b, int e) {
+  int r = 1;
+  while (e--) r *= b;
+  return r;
+}
+}  // namespace
+
+bool linear_operator(int dim, int M, const double* nu, std::vector<double>& P) {
+  const int nb = M + 1, thS = ipow(nb, dim), thT = nb * thS, nR = ipow(3, dim);
+  const int n = nR * thT, K = nR * thS;
+  Tables1D t = tables1d(nb);
+  auto D = [&](int a, int b) { return t.D[a * nb + b]; };
+  std::vector<double> A((size_t)n * n, 0.0);
+  // spatial digit b_dd of mode s
+  auto digit = [&](int s, int dd) { return (s / ipow(nb, dd)) % nb; };
+  auto off = [&](int r, int dd) { return (r / ipow(3, dd)) % 3 - 1; };
+  auto region_index = [&](const int* o) {
+    int r = 0;
+    for (int dd = dim - 1; dd >= 0; --dd) r = r * 3 + (o[dd] + 1);
+    return r;
+  };
+  for (int r = 0; r < nR; ++r) {
+    int o[3] = {0, 0, 0};
+    for (int dd = 0; dd < dim; ++dd) o[dd] = off(r, dd);
+    for (int k = 0; k < thT; ++k) {
+      const int al = k / thS, s = k % thS;
+      double* row = A.data() + (size_t)(r * thT + k) * n;
+      // time term: [psi_a(1) psi_g(1) - D_ag] delta_ss'
+      for (int g = 0; g < nb; ++g) row[r * thT + g * thS + s] += t.ep[al] * t.ep[g] - D(al, g);
+      for (int dd = 0; dd < dim; ++dd) {
+        const int st = ipow(nb, dd), bd = digit(s, dd), base = s - bd * st;
+        const double nud = nu[dd], nup = nud > 0 ? nud : 0.0, num = nud < 0 ? nud : 0.0;
+        for (int b2 = 0; b2 < nb; ++b2) {
+          const int l = al * thS + base + b2 * st;  // same time index, same other digits
+          // internal flux: -nu_d D[bd][b2]
+          row[r * thT + l] -= nud * D(bd, b2);
+          // face at +1 (outward +e_dd)
+          int o2[3] = {o[0], o[1], o[2]};
+          o2[dd] += 1;
+          if (o2[dd] <= 1) {
+            const int r2 = region_index(o2);
+            row[r * thT + l] += nup * t.ep[bd] * t.ep[b2];
+            row[r2 * thT + l] += num * t.ep[bd] * t.em[b2];
+          } else {
+            row[r * thT + l] += nud * t.ep[bd] * t.ep[b2];
+          }
+          // face at -1 (outward -e_dd)
+          o2[dd] -= 2;
+          if (o2[dd] >= -1) {
+            const int r2 = region_index(o2);
+            row[r2 * thT + l] -= nup * t.em[bd] * t.ep[b2];
+            row[r * thT + l] -= num * t.em[bd] * t.em[b2];
+          } else {
+            row[r * thT + l] -= nud * t.em[bd] * t.em[b2];
+          }
+        }
+      }
+    }
+  }
+  std::vector<int> perm;
+  if (!lu_factor(n, A.data(), perm)) return false;
+  // P[c][(r, s)] = sum_a z_c[(r, a, s)] psi_a(-1),  A^T z_c = e_{centre, c}
+  const int rc = (nR - 1) / 2;
+  P.assign((size_t)thT * K, 0.0);
+#pragma omp parallel for schedule(dynamic)
+  for (int c = 0; c < thT; ++c) {
+    std::vector<double> z(n, 0.0);
+    z[rc * thT + c] = 1.0;
+    lu_solve_transpose(n, A.data(), perm, z.data());
+    for (int r = 0; r < nR; ++r)
+      for (int s = 0; s < thS; ++s) {
+        double acc = 0.0;
+        for (int a = 0; a < nb; ++a) acc += z[r * thT + a * thS + s] * t.em[a];
+        P[(size_t)c * K + r * thS + s] = acc;
+      }
+  }
+  return true;
+}
+
+}  // namespace ridg

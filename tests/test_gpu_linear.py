@@ -1,0 +1,252 @@
+"""Parity of the CUDA linear-flux path (through the C ABI) with the oracle."""
+import numpy as np
+import pytest
+
+from oracle import error as oerr
+from oracle import linear as OL
+from paper_2101_01231_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+# (dim, n, M, velocity): tiny meshes where every region wraps, ragged sizes, both signs,
+# M = 0 and the largest degrees per dimension
+CASES = [
+    (1, (64,), 3, (1.0,)),
+    (1, (7,), 0, (-0.8,)),
+    (1, (5,), 7, (0.6,)),
+    (2, (12, 10), 3, (1.0, 0.5)),
+    (2, (3, 3), 2, (-0.4, 1.0)),
+    (2, (17, 9), 4, (0.7, -0.9)),
+    (3, (6, 5, 4), 2, (1.0, 0.7, 0.3)),
+    (3, (3, 3, 3), 3, (-1.0, 0.2, 0.5)),
+    (3, (4, 4, 5), 1, (-0.3, -0.6, 0.9)),
+]
+TOL_STEP = 1e-12      # relative, per step (max-norm over all coefficients)
+TOL_FINAL = 1e-10     # relative, at the final time
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2101_01231_gb300 import ridg
+    return ridg
+
+
+def _w(dim, n, M, vel, cfl=0.35):
+    return dict(flux="advection", dim=dim, n=tuple(n), M=M, vel=tuple(vel), lo=(0.0,) * dim,
+                hi=(1.0,) * dim, cfl=cfl, ic="sin")
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _solver(R, w, **kw):
+    return R.Solver(w["dim"], w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"], hi=w["hi"], **kw)
+
+
+@pytest.mark.parametrize("dim,n,M,vel", CASES)
+def test_prediction_matches_oracle(R, dim, n, M, vel):
+    w = _w(dim, n, M, vel)
+    s = _solver(R, w)
+    rng = np.random.default_rng(11)
+    q = rng.standard_normal((s.cells, s.theta_s))
+    s.set_state(q)
+    dt = s.info()["dt"]
+    W = s.predict()
+    assert _rel(W, OL.predict(q, w, dt)) < TOL_STEP
+    s.close()
+
+
+@pytest.mark.parametrize("dim,n,M,vel", CASES)
+def test_step_matches_oracle(R, dim, n, M, vel):
+    w = _w(dim, n, M, vel)
+    s = _solver(R, w)
+    rng = np.random.default_rng(12)
+    q = rng.standard_normal((s.cells, s.theta_s))
+    s.set_state(q)
+    dt = s.info()["dt"]
+    s.step(1)
+    assert _rel(s.get_state(), OL.step(q, w, dt)) < TOL_STEP
+    # predict + correct is the same step
+    s.set_state(q)
+    s.predict()
+    s.correct()
+    assert _rel(s.get_state(), OL.step(q, w, dt)) < TOL_STEP
+    s.close()
+
+
+@pytest.mark.parametrize("name,override,T", [
+    ("adv1d_n64_q3", {}, 1.0),
+    ("adv2d_n256_q3", {"n": (32, 24)}, 0.25),
+    ("adv3d_n96_q2", {"n": (8, 8, 6), "ic": "sin"}, 0.2),
+])
+def test_final_time_parity_and_accuracy(R, name, override, T):
+    w = I.workload(name, **override)
+    s = _solver(R, w)
+    q0 = I.initial_state(w)
+    s.set_state(q0)
+    nt = s.set_final_time(T)
+    dt_o, nt_o = OL.advection_time_step(w, T=T)
+    assert nt == nt_o and abs(s.info()["dt"] - dt_o) < 1e-15
+    s.step(nt)
+    s.sync()
+    qg = s.get_state()
+    qo = OL.run(q0, w, dt_o, nt_o)
+    assert _rel(qg, qo) < TOL_FINAL
+    # the L2-error diagnostic of eq. l2relerror, evaluated on the oracle's own final state
+    X = I.exact_coefficients(w, T)
+    s.set_state(qo)
+    e_gpu = s.l2_error(X)
+    e_orc = oerr.l2_relative_error(qo, X, w["M"], w["dim"])
+    assert abs(e_gpu - e_orc) <= 1e-12 * e_orc
+    s.close()
+
+
+def test_config1_full_run(R):
+    # 1D, 64 cells, degree 3, u0 = sin(2 pi x), nu = 0.45, to t = 1: 143 steps
+    w = I.workload("adv1d_n64_q3")
+    s = _solver(R, w)
+    q0 = I.initial_state(w)
+    s.set_state(q0)
+    assert s.set_final_time(1.0) == 143
+    s.step(143)
+    qg = s.get_state()
+    dt, nt = OL.advection_time_step(w, T=1.0)
+    assert _rel(qg, OL.run(q0, w, dt, nt)) < TOL_FINAL
+    s.close()
+
+
+@pytest.mark.parametrize("dim,n,M,vel", [CASES[0], CASES[3], CASES[6]])
+def test_mass_conserved(R, dim, n, M, vel):
+    w = _w(dim, n, M, vel)
+    s = _solver(R, w)
+    rng = np.random.default_rng(13)
+    q = rng.standard_normal((s.cells, s.theta_s)) + 2.0
+    s.set_state(q)
+    m0 = s.mass()[0]
+    s.step(40)
+    m1 = s.mass()[0]
+    assert abs(m1 - m0) <= 1e-14 * abs(m0) * 4
+    s.close()
+
+
+def test_graph_replay_is_deterministic(R):
+    w = _w(2, (12, 10), 3, (1.0, 0.5))
+    s = _solver(R, w)
+    q = np.random.default_rng(14).standard_normal((s.cells, s.theta_s))
+    outs = []
+    for _ in range(2):
+        s.set_state(q)
+        s.step(7)
+        outs.append(s.get_state())
+    assert np.array_equal(outs[0], outs[1])
+    s.close()
+
+
+def test_config2_full_size_sampled(R):
+    # 256 x 256, Q3, a = (1, 0.5): one step from the initial data, checked at sampled
+    # cells (corners, edges, random interior) against the oracle's region solves
+    w = I.workload("adv2d_n256_q3")
+    s = _solver(R, w)
+    q0 = I.initial_state(w)
+    s.set_state(q0)
+    dt = s.info()["dt"]
+    W = s.predict()
+    rng = np.random.default_rng(15)
+    n = w["n"][0]
+    cells = np.unique(np.concatenate([[0, n - 1, n * (n - 1), n * n - 1, n * 128 + 77],
+                                      rng.integers(0, n * n, 48)]))
+    Wo = OL.predict_cells(q0, w, dt, cells)
+    assert _rel(W[cells], Wo) < TOL_STEP
+    s.set_state(q0)
+    s.step(1)
+    q1 = s.get_state()
+    assert _rel(q1[cells], OL.step_cells(q0, w, dt, cells)) < TOL_STEP
+    s.close()
+
+
+def test_config3_full_size_sampled(R):
+    # 96^3, Q2, a = (1, 0.7, 0.3), product of sines plus seeded 1e-3 coefficient noise
+    w = I.workload("adv3d_n96_q2")
+    s = _solver(R, w)
+    q0 = I.initial_state(w)
+    s.set_state(q0)
+    dt = s.info()["dt"]
+    s.step(1)
+    q1 = s.get_state()
+    rng = np.random.default_rng(16)
+    N = 96 ** 3
+    cells = np.unique(np.concatenate([[0, 95, 96 * 95, N - 1], rng.integers(0, N, 28)]))
+    assert _rel(q1[cells], OL.step_cells(q0, w, dt, cells)) < TOL_STEP
+    s.close()
+
+
+def test_device_pointers_and_torch_allocator(R):
+    import torch
+    w = _w(2, (12, 10), 2, (1.0, -0.5))
+    s = _solver(R, w, use_torch_allocator=True)
+    q = torch.randn(s.cells, s.theta_s, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    s.set_state(q)
+    W = torch.empty(s.cells, s.theta_t, dtype=torch.float64, device="cuda")
+    s.predict(W)
+    s.sync()
+    dt = s.info()["dt"]
+    assert _rel(W.cpu().numpy(), OL.predict(q.cpu().numpy(), w, dt)) < TOL_STEP
+    out = torch.empty_like(q)
+    s.get_state(out)
+    assert torch.equal(out, q)
+    s.close()
+
+
+def test_invalid_arguments_and_states(R):
+    w = _w(2, (4, 4), 1, (1.0, 0.0))
+    with pytest.raises(R.RidgError) as e:
+        R.ridg_create(R.make_mesh(4, (4, 4, 4)), 1, R.make_flux("advection", (1, 0, 0)), 0.3)
+    assert e.value.status == R.RIDG_EINVAL
+    with pytest.raises(R.RidgError):
+        R.ridg_create(R.make_mesh(2, (4, 2)), 1, R.make_flux("advection", (1, 0)), 0.3)
+    with pytest.raises(R.RidgError):
+        R.ridg_create(R.make_mesh(3, (4, 4, 4)), 9, R.make_flux("advection", (1, 0, 0)), 0.3)
+    s = _solver(R, w)
+    with pytest.raises(R.RidgError) as e:
+        s.correct()
+    assert e.value.status == R.RIDG_ESTATE
+    q = np.zeros((s.cells, s.theta_s))
+    q[3, 1] = np.nan
+    with pytest.raises(R.RidgError) as e:
+        s.set_state(q)
+    assert e.value.status == R.RIDG_ENONFINITE
+    with pytest.raises(R.RidgError):
+        s.set_dt(-1.0)
+    s.close()
+
+
+def test_batched_instances_match_separate_runs(R):
+    from paper_2101_01231_gb300.ridg import (make_flux, make_mesh, ridg_batch_create,
+                                             ridg_batch_destroy, ridg_batch_instance,
+                                             ridg_batch_step, ridg_batch_sync, ridg_get_state,
+                                             ridg_set_state, ridg_info)
+    shapes = [((12, 10), 3), ((9, 9), 2), ((5, 7), 1)]
+    meshes = [make_mesh(2, n) for n, _ in shapes]
+    b = ridg_batch_create(meshes, [M for _, M in shapes], make_flux("advection", (1.0, 0.5)), 0.35)
+    rng = np.random.default_rng(17)
+    qs = []
+    for i, (n, M) in enumerate(shapes):
+        h = ridg_batch_instance(b, i)
+        q = rng.standard_normal((n[0] * n[1], (M + 1) ** 2))
+        ridg_set_state(h, q)
+        qs.append(q)
+    ridg_batch_step(b, 3)
+    ridg_batch_sync(b)
+    for i, (n, M) in enumerate(shapes):
+        h = ridg_batch_instance(b, i)
+        out = np.empty_like(qs[i])
+        ridg_get_state(h, out)
+        w = _w(2, n, M, (1.0, 0.5))
+        dt = ridg_info(h)["dt"]
+        assert _rel(out, OL.run(qs[i], w, dt, 3)) < TOL_STEP
+    ridg_batch_destroy(b)
