@@ -258,6 +258,7 @@ def run_ours(args):
         gpu_id = str(torch.cuda.current_device())
     clocks = Clocks(gpu_id)
     s, ms_step, ms_pred, ms_corr, ck = timed(prec_name, args.steps, args.warmup, clocks)
+    slices_used = s.info()["slices"]
     t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -312,7 +313,7 @@ def run_ours(args):
         "value": value, "unit": "element-DOF updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec_name == "fp64" else "bf16x{}+f64".format(s.opt.slices or 5),
+        "dtype": "f64" if prec_name == "fp64" else "bf16x{}+f64".format(slices_used),
         "data": "synthetic",
         "config": {"workload": w["name"], "cells": cells, "order": w["M"], "theta_s": thS,
                    "precision": prec_name, "steps_to_T": nt, "l2_flush": "256 MB rewrite before each timed step",

@@ -85,7 +85,7 @@ typedef void (*ridg_free_fn)(void* ptr, void* user);
 
 typedef struct {
   int precision;          /* RIDG_PREC_*                                                */
-  int slices;             /* BF16 slices per operand for MIXED_BF16 (0 = default 5)     */
+  int slices;             /* BF16 slices per operand for MIXED_BF16, 2..7 (0 = default 6)     */
   int newton_max_iters;   /* 0 = default 4                                              */
   double newton_tol;      /* <= 0 = default 1e-10: stop when ||dW||_inf <= tol max(1,||W||_inf) */
   void* stream;           /* cudaStream_t (not the legacy default stream) or NULL       */

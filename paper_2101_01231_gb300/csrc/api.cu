@@ -93,23 +93,59 @@ int rebuild_linear(ridg_t* h) {
   RIDG_CUDA(h, cudaMemcpyAsync(h->P, h->P_host.data(), sizeof(double) * h->P_host.size(),
                                cudaMemcpyHostToDevice, h->stream));
   if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
-    std::vector<unsigned short> digits;
-    std::vector<double> rscale;
-    // time-mean rows only (what the step needs)
-    int rc = ridg::mixed_build(h->dim, h->nb, h->P_host, h->thS, h->opt.slices, digits, rscale,
-                               h->mixed);
-    if (rc != RIDG_OK) return set_err(h, rc, "mixed operator build failed");
-    if (!h->mixed.b_slices) {
-      h->mixed.b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
-      h->mixed.row_scale = (double*)dev_alloc(h, rscale.size() * sizeof(double));
-      if (!h->mixed.b_slices || !h->mixed.row_scale)
-        return set_err(h, RIDG_ENOMEM, "mixed operator allocation failed");
+    // fused step operator: rows [V; u_x; u_y] = C P-bar with C mapping the time mean W-bar to
+    // the volume term sum_d nu_d (D along d) W-bar and the upwind face traces nu_d tr(W-bar)
+    const int nb = h->nb, thS = h->thS, K = h->K, nout = thS + 2 * nb;
+    ridg::Tables1D t1 = ridg::tables1d(nb);
+    std::vector<double> C((size_t)nout * thS, 0.0);
+    for (int d = 0; d < 2; ++d) {
+      const int st = d == 0 ? 1 : nb;
+      for (int s = 0; s < thS; ++s) {
+        const int bd = (s / st) % nb, base = s - bd * st;
+        for (int b = 0; b < nb; ++b) C[(size_t)s * thS + base + b * st] += nu[d] * t1.D[bd * nb + b];
+      }
+      const std::vector<double>& tr = nu[d] >= 0 ? t1.ep : t1.em;
+      for (int t = 0; t < nb; ++t) {
+        const int base = d == 0 ? t * nb : t;  // other-dimension digit t
+        for (int b = 0; b < nb; ++b) C[(size_t)(thS + d * nb + t) * thS + base + b * st] = nu[d] * tr[b];
+      }
     }
-    RIDG_CUDA(h, cudaMemcpyAsync(h->mixed.b_slices, digits.data(),
-                                 digits.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
-                                 h->stream));
-    RIDG_CUDA(h, cudaMemcpyAsync(h->mixed.row_scale, rscale.data(), rscale.size() * sizeof(double),
-                                 cudaMemcpyHostToDevice, h->stream));
+    std::vector<double> G((size_t)nout * K, 0.0);
+    for (int r = 0; r < nout; ++r)
+      for (int s = 0; s < thS; ++s) {
+        const double c = C[(size_t)r * thS + s];
+        if (c == 0.0) continue;
+        for (int k = 0; k < K; ++k) G[(size_t)r * K + k] += c * h->P_host[(size_t)s * K + k];
+      }
+    struct Pending { ridg::MixedOp* op; const std::vector<double>* g; int nout; };
+    Pending todo[2] = {{&h->mixed, &G, nout}, {&h->mixed_pred, &h->P_host, h->thT}};
+    for (auto& p : todo) {
+      std::vector<unsigned short> digits;
+      std::vector<double> rscale;
+      void* old_b = p.op->b_slices;
+      double* old_r = p.op->row_scale;
+      int rc = ridg::mixed_build(h->dim, h->nb, *p.g, p.nout, h->opt.slices, digits, rscale, *p.op);
+      if (rc != RIDG_OK) return set_err(h, rc, "mixed operator build failed");
+      p.op->b_slices = old_b;
+      p.op->row_scale = old_r;
+      if (!p.op->b_slices) {
+        p.op->b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
+        p.op->row_scale = (double*)dev_alloc(h, rscale.size() * sizeof(double));
+        if (!p.op->b_slices || !p.op->row_scale)
+          return set_err(h, RIDG_ENOMEM, "mixed operator allocation failed");
+      }
+      RIDG_CUDA(h, cudaMemcpyAsync(p.op->b_slices, digits.data(),
+                                   digits.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
+                                   h->stream));
+      RIDG_CUDA(h, cudaMemcpyAsync(p.op->row_scale, rscale.data(), rscale.size() * sizeof(double),
+                                   cudaMemcpyHostToDevice, h->stream));
+      RIDG_CUDA(h, cudaStreamSynchronize(h->stream));  // host vectors go out of scope
+    }
+    h->ny_out = nout;
+    if (!h->Y) {
+      h->Y = (double*)dev_alloc(h, (size_t)h->ncell * nout * sizeof(double));
+      if (!h->Y) return set_err(h, RIDG_ENOMEM, "fused output allocation failed");
+    }
   }
   RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
   drop_graphs(h);
@@ -117,11 +153,13 @@ int rebuild_linear(ridg_t* h) {
   return RIDG_OK;
 }
 
-// One prediction of the time mean into Wbar (what the step needs).
+int sign_of(double v) { return v > 0 ? 1 : (v < 0 ? -1 : 0); }
+
+// The step's prediction: FP64 time mean into Wbar, or (mixed) the fused outputs into Y.
 int enqueue_predict_mean(ridg_t* h) {
   Grid g = grid_of(h);
   if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
-    RIDG_CUDA(h, ridg::launch_predict_mixed(g, h->nb, h->Q, h->mixed, h->Wbar, h->thS, h->status,
+    RIDG_CUDA(h, ridg::launch_predict_mixed(g, h->nb, h->Q, h->mixed, h->Y, h->ny_out, h->status,
                                             h->stream));
   } else {
     RIDG_CUDA(h, ridg::launch_predict_fp64(g, h->nb, h->Q, h->P, h->thS, h->Wbar, h->thS,
@@ -130,13 +168,23 @@ int enqueue_predict_mean(ridg_t* h) {
   return RIDG_OK;
 }
 
+int enqueue_correct_after_mean(ridg_t* h) {
+  CorrParams cp = corr_params(h);
+  if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+    RIDG_CUDA(h, ridg::launch_correct_fused(grid_of(h), h->nb, h->Q, h->Y, h->ny_out, cp,
+                                            sign_of(h->flux.vel[0]), sign_of(h->flux.vel[1]),
+                                            h->stream));
+  } else {
+    RIDG_CUDA(h, ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->Wbar, h->thS, cp,
+                                             h->stream));
+  }
+  return RIDG_OK;
+}
+
 int enqueue_step(ridg_t* h) {
   int rc = enqueue_predict_mean(h);
   if (rc) return rc;
-  CorrParams cp = corr_params(h);
-  RIDG_CUDA(h, ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->Wbar, h->thS, cp,
-                                           h->stream));
-  return RIDG_OK;
+  return enqueue_correct_after_mean(h);
 }
 
 int check_handle(const ridg_t* h) { return h ? RIDG_OK : RIDG_EINVAL; }
@@ -170,7 +218,7 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
   if (flux->kind != RIDG_FLUX_ADVECTION) return RIDG_EINVAL;
   ridg_t* h = new ridg_t();
   if (opt) h->opt = *opt;
-  if (h->opt.slices <= 0) h->opt.slices = 5;
+  if (h->opt.slices <= 0) h->opt.slices = 6;
   if (h->opt.newton_max_iters <= 0) h->opt.newton_max_iters = 4;
   if (!(h->opt.newton_tol > 0)) h->opt.newton_tol = 1e-10;
   h->dim = mesh->dim;
@@ -197,7 +245,8 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
   h->m = 1;
   h->flux = *flux;
   h->cfl = cfl;
-  if (h->opt.precision == RIDG_PREC_MIXED_BF16 && !ridg::mixed_supported(h->dim, h->nb, h->thS)) {
+  if (h->opt.precision == RIDG_PREC_MIXED_BF16 &&
+      (!ridg::mixed_supported(h->dim, h->nb, h->thT) || h->opt.slices < 2 || h->opt.slices > 7)) {
     delete h;
     return RIDG_EINVAL;
   }
@@ -259,6 +308,9 @@ void ridg_destroy(ridg_t* h) {
   dev_free(h, h->status);
   dev_free(h, h->mixed.b_slices);
   dev_free(h, h->mixed.row_scale);
+  dev_free(h, h->mixed_pred.b_slices);
+  dev_free(h, h->mixed_pred.row_scale);
+  dev_free(h, h->Y);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -312,7 +364,12 @@ int ridg_set_final_time(ridg_t* h, double T, long long* nsteps) {
 int ridg_predict(ridg_t* h, double* w_out, int on_device) {
   if (check_handle(h)) return RIDG_EINVAL;
   Grid g = grid_of(h);
-  RIDG_CUDA(h, ridg::launch_predict_fp64(g, h->nb, h->Q, h->P, h->thT, h->W, h->thT, h->stream));
+  if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+    RIDG_CUDA(h, ridg::launch_predict_mixed(g, h->nb, h->Q, h->mixed_pred, h->W, h->thT,
+                                            h->status, h->stream));
+  } else {
+    RIDG_CUDA(h, ridg::launch_predict_fp64(g, h->nb, h->Q, h->P, h->thT, h->W, h->thT, h->stream));
+  }
   h->have_pred = true;
   if (w_out) {
     const size_t bytes = (size_t)h->ncell * h->m * h->thT * sizeof(double);
@@ -366,10 +423,18 @@ int ridg_step(ridg_t* h, int n) {
   return RIDG_OK;
 }
 
+int read_status(ridg_t* h) {
+  int st = 0;
+  RIDG_CUDA(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (st & 2) return set_err(h, RIDG_ETIMEOUT, "a bounded tensor-core wait gave up");
+  return RIDG_OK;
+}
+
 int ridg_sync(ridg_t* h) {
   if (check_handle(h)) return RIDG_EINVAL;
   RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
-  return RIDG_OK;
+  return read_status(h);
 }
 
 int ridg_profile_step(ridg_t* h, int n, ridg_profile_t* out) {
@@ -383,15 +448,10 @@ int ridg_profile_step(ridg_t* h, int n, ridg_profile_t* out) {
     rc = enqueue_predict_mean(h);
     if (rc) break;
     cudaEventRecord(ev[1], h->stream);
-    CorrParams cp = corr_params(h);
-    cudaError_t e = ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->Wbar, h->thS, cp,
-                                                h->stream);
-    if (e != cudaSuccess) {
-      rc = set_err(h, RIDG_ECUDA, cudaGetErrorString(e));
-      break;
-    }
+    rc = enqueue_correct_after_mean(h);
+    if (rc) break;
     cudaEventRecord(ev[2], h->stream);
-    e = cudaEventSynchronize(ev[2]);
+    cudaError_t e = cudaEventSynchronize(ev[2]);
     if (e != cudaSuccess) {
       rc = set_err(h, RIDG_ECUDA, cudaGetErrorString(e));
       break;

@@ -1,9 +1,500 @@
-// Mixed-precision prediction (placeholder until the tensor-core kernel lands).
+// Mixed-precision linear prediction on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// What is computed.  Y[e][c] = sum_k G[c][k] X_e[k] for every cell e of a 2D mesh, where X_e
+// holds the theta_S coefficients of the 3 x 3 vertex neighbours of e (Sec. 2.2, eq. region)
+// and G is any operator with K = 9 theta_S columns -- the centre rows of the region
+// solution operator (the prediction of eq. pred_full_system for a linear flux), or those
+// rows composed with the linear correction functionals (volume term and upwind face
+// traces of Sec. 2.3), which is what the fused step uses.
+//
+// How (split-operand refinement on BF16 tensor cores).  Each FP64 operand is written as a
+// short sum of 8-bit "digits" times powers of two: for a tile of cells, X = 2^s sum_a
+// d_a 2^{-8(a+1)} with s the tile's largest exponent, |d_0| <= 256, |d_a| <= 128 (balanced,
+// rounded), and likewise each row of G with its own exponent.  Digits are small integers,
+// exact in BF16, so every digit product is exact and the K-sum of products with equal
+// digit weight a + c' = t is exact in the FP32 accumulator for t <= 4 (bounded by
+// (t+1) 144 2^16 < 2^24) and rounded far below the FP64 target for t >= 5.  The diagonal
+// sums acc_t live in TMEM (one block of columns per t); the epilogue recombines
+// sum_t acc_t 2^{-8t} with error-free FP32 two-sums and scales by 2^{s + g_c - 16} in FP64.
+//
+// Data path per CTA (persistent over 8 x 16 cell tiles, 128 threads = 128 TMEM lanes):
+//   1. the tile's 10 x 18 halo of FP64 coefficients is read from HBM (periodic wrap);
+//   2. the halo is converted once to fixed point and split into S digit planes laid out
+//      [digit][mode-group of 8][halo cell][8 modes] in shared memory;
+//   3. the A operand of every MMA is read straight from the digit planes: region offset
+//      (ox, oy) is a shift of the descriptor start address, the 8-row core matrices are 8
+//      consecutive halo cells (16 B apart) and the 8-row groups are halo rows (160 B apart)
+//      -- an implicit im2col, no copy;
+//   4. one thread issues S x 9 x (theta_pad / 16) tcgen05.mma (M = 128) with B = the
+//      operator digits stacked [G-digit 0 .. S-1-a] so digit pair (a, c') lands in TMEM
+//      block a + c'; a single commit signals the mbarrier;
+//   5. the epilogue reads TMEM with tcgen05.ld (thread t <-> cell t), recombines and writes
+//      Y in FP64.
+// Every wait on the mbarrier is bounded; on timeout the kernel raises a status flag, waits
+// (bounded) once more for the tensor core, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
 #include "ridg_internal.h"
+
 namespace ridg {
-bool mixed_supported(int, int, int) { return false; }
-int mixed_build(int, int, const std::vector<double>&, int, int, std::vector<unsigned short>&,
-                std::vector<double>&, MixedOp&) { return RIDG_EINVAL; }
-cudaError_t launch_predict_mixed(const Grid&, int, const double*, const MixedOp&, double*, int,
-                                 int*, cudaStream_t) { return cudaErrorNotSupported; }
+namespace {
+
+constexpr int kTX = 8, kTY = 16;                 // cells per tile in x, y (128 = MMA M)
+constexpr int kHX = kTX + 2, kHY = kTY + 2;      // halo
+constexpr int kHalo = kHX * kHY;                 // 180 halo cells
+constexpr int kThreads = 128;
+constexpr int kBits = 8;                         // digit width
+constexpr long kWaitLimit = 1L << 22;            // bounded mbarrier polls (well under a second)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  // SWIZZLE_NONE, K-major: LBO = byte stride between core matrices along K,
+  // SBO = byte stride between 8-row groups along M/N; bits 46-47 = descriptor version 1.
+  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ __forceinline__ uint32_t idesc_bf16(int m, int n) {
+  // kind::f16: D = F32 (bit 4), A = B = BF16 (bits 7, 10), both K-major, N >> 3 at bit 17,
+  // M >> 4 at bit 24
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (long it = 0; it < kWaitLimit && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// error-free sum of two floats (Knuth): a + b = s + e exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// FP64 -> fixed point with L fraction bits relative to 2^s (round half up), from the bits
+__device__ __forceinline__ long long to_fixed(double x, int s, int L) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((u >> 52) & 0x7FF);
+  if (ex == 0) return 0;  // zero / subnormal: far below the tile's scale
+  const long long mant = (long long)((u & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
+  const int sh = ex - 1075 + L - s;
+  long long F;
+  if (sh >= 0) {
+    F = mant << sh;
+  } else if (sh > -63) {
+    F = (mant + (1LL << (-sh - 1))) >> (-sh);
+  } else {
+    F = 0;
+  }
+  return (u >> 63) ? -F : F;
+}
+
+struct MixedLayout {
+  int S, P, nout_pad, brows;
+  uint32_t digits_off, halo_off, b_off, bytes;
+};
+
+__host__ __device__ inline MixedLayout mixed_layout(int S, int thS, int nout_pad) {
+  MixedLayout l;
+  l.S = S;
+  l.P = ((thS + 15) / 16) * 2;  // 8-mode groups after padding theta_S to a multiple of 16
+  l.nout_pad = nout_pad;
+  l.brows = S * nout_pad;
+  l.digits_off = 0;
+  const uint32_t digits = (uint32_t)S * l.P * kHalo * 16;
+  l.halo_off = (digits + 127) & ~127u;
+  const uint32_t halo = (uint32_t)kHalo * thS * 8;
+  l.b_off = (l.halo_off + halo + 1023) & ~1023u;
+  const uint32_t bbytes = (uint32_t)9 * l.P * l.brows * 16;
+  l.bytes = l.b_off + bbytes;
+  return l;
+}
+
+template <int NB, int NOUTP>
+__global__ void __launch_bounds__(kThreads) predict_mixed_kernel(
+    const double* __restrict__ Q, const uint4* __restrict__ Bg, const double* __restrict__ rscale,
+    int S, int nout, double* __restrict__ Y, int ystride, int nx, int ny, int* status) {
+  constexpr int THS = NB * NB;
+  constexpr int TPAD = ((THS + 15) / 16) * 16;
+  constexpr int P = TPAD / 8;
+  constexpr int KSTEPS = TPAD / 16;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ unsigned long long red[kThreads / 32];
+  const MixedLayout L = mixed_layout(S, THS, NOUTP);
+  unsigned char* digits = smem + L.digits_off;
+  double* halo = (double*)(smem + L.halo_off);
+  long long* fixedp = (long long*)(smem + L.halo_off);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
+  const int ntiles = ntx * nty;
+  const int ncols = NOUTP * 8 > 256 ? 512 : 256;  // TMEM columns: >= S * NOUTP (S <= 8)
+
+  // operator digits -> shared memory (once per CTA), zero the digit planes (pad modes)
+  {
+    uint4* bs = (uint4*)(smem + L.b_off);
+    const int nb16 = 9 * P * L.brows;
+    for (int i = tid; i < nb16; i += kThreads) bs[i] = Bg[i];
+    uint4* ds = (uint4*)digits;
+    const int nd16 = S * P * kHalo;
+    for (int i = tid; i < nd16; i += kThreads) ds[i] = make_uint4(0, 0, 0, 0);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+  const int Lfix = kBits * S;
+  bool ok = true;
+  uint32_t phase = 0;
+
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int tx = tile % ntx, ty = tile / ntx;
+    const int x0 = tx * kTX - 1, y0 = ty * kTY - 1;
+    // 1. halo of FP64 coefficients (periodic), and its largest magnitude
+    unsigned long long mx = 0;
+    for (int i = tid; i < kHalo * THS; i += kThreads) {
+      const int h = i / THS, s = i % THS;
+      int gx = x0 + h % kHX, gy = y0 + h / kHX;
+      gx = (gx % nx + nx) % nx;
+      gy = (gy % ny + ny) % ny;
+      const double v = __ldg(Q + ((long long)gy * nx + gx) * THS + s);
+      halo[i] = v;
+      const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+      mx = a > mx ? a : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = t > mx ? t : mx;
+    }
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    mx = red[0];
+#pragma unroll
+    for (int w = 1; w < kThreads / 32; ++w) mx = red[w] > mx ? red[w] : mx;
+    // tile exponent: max|X| < 2^s
+    const int sexp = mx == 0 ? 0 : (int)((mx >> 52) & 0x7FF) - 1022;
+    // 2. fixed point (in place) and digit planes
+    for (int i = tid; i < kHalo * THS; i += kThreads) fixedp[i] = to_fixed(halo[i], sexp, Lfix);
+    for (int a = 0; a < S; ++a) {
+      const int sh = Lfix - kBits * (a + 1);
+      __nv_bfloat16* dplane = (__nv_bfloat16*)(digits + (size_t)a * P * kHalo * 16);
+      for (int i = tid; i < kHalo * THS; i += kThreads) {
+        long long F = fixedp[i];
+        long long d;
+        if (sh > 0) {
+          d = (F + (1LL << (sh - 1))) >> sh;
+          fixedp[i] = F - (d << sh);
+        } else {
+          d = F;
+        }
+        const int h = i / THS, s = i % THS;
+        dplane[((s / 8) * kHalo + h) * 8 + (s % 8)] = __float2bfloat16_rn((float)d);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    // 3./4. MMAs, issued by one thread
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t dbase = smem_u32(digits), bbase = smem_u32(smem + L.b_off);
+      const uint32_t a_lbo = kHalo * 16, a_sbo = kHX * 16;
+      const uint32_t b_lbo = (uint32_t)L.brows * 16, b_sbo = 128;
+      constexpr int CMAX = 256 / NOUTP;
+      for (int a = 0; a < S; ++a) {
+        for (int r = 0; r < 9; ++r) {
+          const int ox = r % 3, oy = r / 3;  // halo shift (offset + 1)
+          for (int j = 0; j < KSTEPS; ++j) {
+            const uint32_t a_addr = dbase + (uint32_t)(((a * P + 2 * j) * kHalo + oy * kHX + ox) * 16);
+            const uint64_t ad = smem_desc(a_addr, a_lbo, a_sbo);
+            const int kc = r * P + 2 * j;  // k-chunk of the operator
+            for (int c0 = 0; c0 < S - a; c0 += CMAX) {
+              const int c1 = min(S - a, c0 + CMAX);
+              const int n = (c1 - c0) * NOUTP;
+              const uint32_t b_addr = bbase + (uint32_t)(kc * L.brows + c0 * NOUTP) * 16;
+              const uint64_t bd = smem_desc(b_addr, b_lbo, b_sbo);
+              const uint32_t acc = (a == 0 && r == 0 && j == 0) ? 0u : 1u;
+              mma_bf16(tmem + (uint32_t)((a + c0) * NOUTP), ad, bd, idesc_bf16(128, n), acc);
+            }
+          }
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&mbar))
+          : "memory");
+    }
+    // 5. epilogue
+    if (!mbar_wait(smem_u32(&mbar), phase)) {
+      ok = false;
+      if (tid == 0) atomicOr(status, 2);
+      mbar_wait(smem_u32(&mbar), phase);  // one more bounded wait before releasing TMEM
+      break;
+    }
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {
+      const int ix = tid % kTX, iy = tid / kTX;
+      const int gx = tx * kTX + ix, gy = ty * kTY + iy;
+      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+      for (int cb = 0; cb < NOUTP; cb += 32) {
+        float hi[32], lo[32], v[32];
+        tmem_ld32(lane_addr + (uint32_t)cb, hi);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) lo[c] = 0.f;
+        float w = 1.f;
+        for (int t = 1; t < S; ++t) {
+          w *= 1.f / 256.f;
+          tmem_ld32(lane_addr + (uint32_t)(t * NOUTP + cb), v);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            float s, e;
+            two_sum(hi[c], v[c] * w, s, e);
+            hi[c] = s;
+            lo[c] += e;
+          }
+        }
+        if (gx < nx && gy < ny) {
+          double* y = Y + ((long long)gy * nx + gx) * ystride;
+          const double tscale = __longlong_as_double((long long)(sexp + 1023) << 52);
+#pragma unroll
+          for (int c = 0; c < 32; ++c)
+            if (cb + c < nout)
+              y[cb + c] = ((double)hi[c] + (double)lo[c]) * (tscale * rscale[cb + c]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+// ---------------------------------------------------------------------------------------
+// correction from the fused outputs: Y = [V (theta_S) | u_x (NB) | u_y (NB)] per cell, with
+// V = sum_d nu_d (D along d) Wbar and u_d = nu_d trace(Wbar) on the upwind side of dim d
+// (trace at +1 when a_d > 0, at -1 when a_d < 0).  The face value at i+1/2 in dim d is u_d
+// of the upwind cell (one stored number per face), so both neighbours apply the same flux.
+// ---------------------------------------------------------------------------------------
+template <int NB>
+__global__ void __launch_bounds__(128) correct_fused_kernel(double* __restrict__ Q,
+                                                            const double* __restrict__ Y,
+                                                            int ystride, int nx, int ny,
+                                                            CorrParams cp, int sgnx, int sgny) {
+  constexpr int THS = NB * NB;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nx * ny) return;
+  const int ix = (int)(e % nx), iy = (int)(e / nx);
+  double dq[THS];
+  const double* y = Y + e * ystride;
+#pragma unroll
+  for (int s = 0; s < THS; ++s) dq[s] = y[s];
+#pragma unroll
+  for (int dd = 0; dd < 2; ++dd) {
+    const int sg = dd == 0 ? sgnx : sgny;
+    if (sg == 0) continue;
+    const int st = dd == 0 ? 1 : NB;
+    // faces i+1/2 (right/top) and i-1/2 (left/bottom): upwind cell of each face
+    long long jr, jl;
+    if (dd == 0) {
+      jr = sg > 0 ? e : (long long)iy * nx + (ix + 1 == nx ? 0 : ix + 1);
+      jl = sg > 0 ? (long long)iy * nx + (ix == 0 ? nx - 1 : ix - 1) : e;
+    } else {
+      jr = sg > 0 ? e : (long long)(iy + 1 == ny ? 0 : iy + 1) * nx + ix;
+      jl = sg > 0 ? (long long)(iy == 0 ? ny - 1 : iy - 1) * nx + ix : e;
+    }
+    const double* fr = Y + jr * ystride + THS + dd * NB;
+    const double* fl = Y + jl * ystride + THS + dd * NB;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const double vr = fr[t], vl = fl[t];
+      const int base = dd == 0 ? t * NB : t;
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        double v = dq[base + a * st];
+        v = fma(-cp.ep[a], vr, v);
+        v = fma(cp.em[a], vl, v);
+        dq[base + a * st] = v;
+      }
+    }
+  }
+  double* q = Q + e * THS;
+#pragma unroll
+  for (int s = 0; s < THS; ++s) q[s] = q[s] + dq[s];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+bool mixed_supported(int dim, int nb, int nout) {
+  return dim == 2 && nb >= 2 && nb <= 5 && nout <= 64;
+}
+
+static int nout_pad_of(int nout) { return nout <= 32 ? 32 : 64; }
+
+int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int slices,
+                std::vector<unsigned short>& digits, std::vector<double>& rscale, MixedOp& op) {
+  if (!mixed_supported(dim, nb, nout) || slices < 2 || slices > 7) return RIDG_EINVAL;
+  const int thS = nb * nb, K = 9 * thS;
+  if ((int)G.size() < nout * K) return RIDG_EINVAL;
+  const int NOUTP = nout_pad_of(nout);
+  if (slices * NOUTP > 512) return RIDG_EINVAL;
+  const MixedLayout L = mixed_layout(slices, thS, NOUTP);
+  const int tpad = L.P * 8;
+  // digits in the shared-memory layout [k-chunk][row = c' * NOUTP + c][8]
+  digits.assign((size_t)9 * L.P * L.brows * 8, 0);
+  rscale.assign(NOUTP, 0.0);
+  for (int c = 0; c < nout; ++c) {
+    double mx = 0.0;
+    for (int k = 0; k < K; ++k) mx = std::max(mx, std::fabs(G[(size_t)c * K + k]));
+    int g = 0;
+    if (mx > 0) {
+      std::frexp(mx, &g);  // mx < 2^g
+    }
+    rscale[c] = std::ldexp(1.0, g - 2 * kBits);
+    for (int k = 0; k < K; ++k) {
+      const int r = k / thS, s = k % thS;
+      const int kp = r * tpad + s;  // padded column
+      double v = std::ldexp(G[(size_t)c * K + k], -g);  // |v| < 1
+      for (int cp = 0; cp < slices; ++cp) {
+        double sc = std::ldexp(v, kBits);
+        double d = (cp + 1 < slices) ? std::floor(sc + 0.5) : std::nearbyint(sc);
+        v = sc - d;  // exact
+        __nv_bfloat16 b = __float2bfloat16_rn((float)d);
+        unsigned short bits;
+        std::memcpy(&bits, &b, 2);
+        const int row = cp * NOUTP + c;
+        digits[((size_t)(kp / 8) * L.brows + row) * 8 + (kp % 8)] = bits;
+      }
+    }
+  }
+  op.nout = nout;
+  op.npad = NOUTP;
+  op.K = K;
+  op.Kpad = 9 * tpad;
+  op.slices = slices;
+  op.bits = kBits;
+  return RIDG_OK;
+}
+
+template <int NB, int NOUTP>
+static cudaError_t launch_mixed_t(const Grid& g, const double* Q, const MixedOp& op, double* Y,
+                                  int ystride, int* status, cudaStream_t s) {
+  const MixedLayout L = mixed_layout(op.slices, NB * NB, NOUTP);
+  auto kern = predict_mixed_kernel<NB, NOUTP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ntiles = ((g.n[0] + kTX - 1) / kTX) * ((g.n[1] + kTY - 1) / kTY);
+  const int per_sm = (2 * ((size_t)L.bytes + 2048) <= 233472 && NOUTP <= 32) ? 2 : 1;
+  const int grid = std::min(ntiles, sms * per_sm);
+  kern<<<grid, kThreads, L.bytes, s>>>(Q, (const uint4*)op.b_slices, op.row_scale, op.slices,
+                                       op.nout, Y, ystride, g.n[0], g.n[1], status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_predict_mixed(const Grid& g, int nb, const double* Q, const MixedOp& op,
+                                 double* Y, int ystride, int* status, cudaStream_t s) {
+  if (g.dim != 2) return cudaErrorInvalidValue;
+  if (op.npad == 32) {
+    switch (nb) {
+      case 2: return launch_mixed_t<2, 32>(g, Q, op, Y, ystride, status, s);
+      case 3: return launch_mixed_t<3, 32>(g, Q, op, Y, ystride, status, s);
+      case 4: return launch_mixed_t<4, 32>(g, Q, op, Y, ystride, status, s);
+      case 5: return launch_mixed_t<5, 32>(g, Q, op, Y, ystride, status, s);
+    }
+  } else if (op.npad == 64) {
+    switch (nb) {
+      case 2: return launch_mixed_t<2, 64>(g, Q, op, Y, ystride, status, s);
+      case 3: return launch_mixed_t<3, 64>(g, Q, op, Y, ystride, status, s);
+      case 4: return launch_mixed_t<4, 64>(g, Q, op, Y, ystride, status, s);
+      case 5: return launch_mixed_t<5, 64>(g, Q, op, Y, ystride, status, s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_correct_fused(const Grid& g, int nb, double* Q, const double* Y, int ystride,
+                                 const CorrParams& cp, int sgnx, int sgny, cudaStream_t s) {
+  if (g.dim != 2) return cudaErrorInvalidValue;
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((g.ncell + threads - 1) / threads);
+  switch (nb) {
+    case 2: correct_fused_kernel<2><<<blocks, threads, 0, s>>>(Q, Y, ystride, g.n[0], g.n[1], cp, sgnx, sgny); break;
+    case 3: correct_fused_kernel<3><<<blocks, threads, 0, s>>>(Q, Y, ystride, g.n[0], g.n[1], cp, sgnx, sgny); break;
+    case 4: correct_fused_kernel<4><<<blocks, threads, 0, s>>>(Q, Y, ystride, g.n[0], g.n[1], cp, sgnx, sgny); break;
+    case 5: correct_fused_kernel<5><<<blocks, threads, 0, s>>>(Q, Y, ystride, g.n[0], g.n[1], cp, sgnx, sgny); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+size_t mixed_smem_bytes(int nb, const MixedOp& op) {
+  return mixed_layout(op.slices, nb * nb, op.npad).bytes;
+}
+
 }  // namespace ridg

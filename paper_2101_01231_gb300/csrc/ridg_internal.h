@@ -45,6 +45,10 @@ int mixed_build(int dim, int nb, const std::vector<double>& P, int nout, int sli
                 std::vector<unsigned short>& digits, std::vector<double>& rscale, MixedOp& op);
 cudaError_t launch_predict_mixed(const Grid& g, int nb, const double* Q, const MixedOp& op,
                                  double* W, int wstride, int* status, cudaStream_t s);
+// Q[e] += correction from the fused outputs Y = [V | u_x | u_y] (2D); sgn = sign of a_d
+cudaError_t launch_correct_fused(const Grid& g, int nb, double* Q, const double* Y, int ystride,
+                                 const CorrParams& cp, int sgnx, int sgny, cudaStream_t s);
+size_t mixed_smem_bytes(int nb, const MixedOp& op);
 
 // ---- diagnostics (k_diag.cu) ----
 // partial sums (per block) of q[e, r, 0], r < m  -> out[block * m + r]
@@ -82,7 +86,10 @@ struct ridg_handle {
   double* red = nullptr;    // reduction partials
   int* status = nullptr;    // device status word(s)
   int red_blocks = 256;
-  ridg::MixedOp mixed;
+  ridg::MixedOp mixed;       // fused step operator [V; u_x; u_y] P-bar (2D)
+  ridg::MixedOp mixed_pred;  // full prediction operator P
+  double* Y = nullptr;       // fused outputs of the mixed step (cells * nout)
+  int ny_out = 0;
   // host copy of the operator
   std::vector<double> P_host;
   // graphs: key = number of steps
