@@ -73,6 +73,8 @@ CorrParams corr_params(const ridg_t* h) {
   for (int b = 0; b < h->nb; ++b) {
     cp.ep[b] = t.ep[b];
     cp.em[b] = t.em[b];
+    cp.eph[b] = (float)t.ep[b];
+    cp.epl[b] = (float)(t.ep[b] - (double)cp.eph[b]);
     for (int c = 0; c < h->nb; ++c) cp.D[b * ridg::kMaxNB + c] = t.D[b * h->nb + c];
   }
   for (int d = 0; d < 3; ++d) {
@@ -122,18 +124,19 @@ int rebuild_linear(ridg_t* h) {
     for (auto& p : todo) {
       std::vector<unsigned short> digits;
       std::vector<double> rscale;
-      void* old_b = p.op->b_slices;
-      double* old_r = p.op->row_scale;
-      int rc = ridg::mixed_build(h->dim, h->nb, *p.g, p.nout, h->opt.slices, digits, rscale, *p.op);
+      std::vector<float> rowmul;
+      int rc = ridg::mixed_build(h->dim, h->nb, *p.g, p.nout, h->opt.slices, digits, rscale,
+                                 rowmul, *p.op);
       if (rc != RIDG_OK) return set_err(h, rc, "mixed operator build failed");
-      p.op->b_slices = old_b;
-      p.op->row_scale = old_r;
       if (!p.op->b_slices) {
         p.op->b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
         p.op->row_scale = (double*)dev_alloc(h, rscale.size() * sizeof(double));
-        if (!p.op->b_slices || !p.op->row_scale)
+        p.op->row_mul = (float*)dev_alloc(h, rowmul.size() * sizeof(float));
+        if (!p.op->b_slices || !p.op->row_scale || !p.op->row_mul)
           return set_err(h, RIDG_ENOMEM, "mixed operator allocation failed");
       }
+      RIDG_CUDA(h, cudaMemcpyAsync(p.op->row_mul, rowmul.data(), rowmul.size() * sizeof(float),
+                                   cudaMemcpyHostToDevice, h->stream));
       RIDG_CUDA(h, cudaMemcpyAsync(p.op->b_slices, digits.data(),
                                    digits.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
                                    h->stream));
@@ -143,8 +146,10 @@ int rebuild_linear(ridg_t* h) {
     }
     h->ny_out = nout;
     if (!h->Y) {
+      const size_t ntiles = (size_t)((h->n[0] + 7) / 8) * ((h->n[1] + 15) / 16);
       h->Y = (double*)dev_alloc(h, (size_t)h->ncell * nout * sizeof(double));
-      if (!h->Y) return set_err(h, RIDG_ENOMEM, "fused output allocation failed");
+      h->texp = (int*)dev_alloc(h, ntiles * sizeof(int));
+      if (!h->Y || !h->texp) return set_err(h, RIDG_ENOMEM, "fused output allocation failed");
     }
   }
   RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -159,7 +164,7 @@ int sign_of(double v) { return v > 0 ? 1 : (v < 0 ? -1 : 0); }
 int enqueue_predict_mean(ridg_t* h) {
   Grid g = grid_of(h);
   if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
-    RIDG_CUDA(h, ridg::launch_predict_mixed(g, h->nb, h->Q, h->mixed, h->Y, h->ny_out, h->status,
+    RIDG_CUDA(h, ridg::launch_predict_fused(g, h->nb, h->Q, h->mixed, h->Y, h->texp, h->status,
                                             h->stream));
   } else {
     RIDG_CUDA(h, ridg::launch_predict_fp64(g, h->nb, h->Q, h->P, h->thS, h->Wbar, h->thS,
@@ -171,9 +176,9 @@ int enqueue_predict_mean(ridg_t* h) {
 int enqueue_correct_after_mean(ridg_t* h) {
   CorrParams cp = corr_params(h);
   if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
-    RIDG_CUDA(h, ridg::launch_correct_fused(grid_of(h), h->nb, h->Q, h->Y, h->ny_out, cp,
-                                            sign_of(h->flux.vel[0]), sign_of(h->flux.vel[1]),
-                                            h->stream));
+    RIDG_CUDA(h, ridg::launch_correct_fused(grid_of(h), h->nb, h->Q, h->Y, h->texp,
+                                            h->mixed.gmax, cp, sign_of(h->flux.vel[0]),
+                                            sign_of(h->flux.vel[1]), h->stream));
   } else {
     RIDG_CUDA(h, ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->Wbar, h->thS, cp,
                                              h->stream));
@@ -308,9 +313,12 @@ void ridg_destroy(ridg_t* h) {
   dev_free(h, h->status);
   dev_free(h, h->mixed.b_slices);
   dev_free(h, h->mixed.row_scale);
+  dev_free(h, h->mixed.row_mul);
   dev_free(h, h->mixed_pred.b_slices);
   dev_free(h, h->mixed_pred.row_scale);
+  dev_free(h, h->mixed_pred.row_mul);
   dev_free(h, h->Y);
+  dev_free(h, h->texp);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -365,7 +373,7 @@ int ridg_predict(ridg_t* h, double* w_out, int on_device) {
   if (check_handle(h)) return RIDG_EINVAL;
   Grid g = grid_of(h);
   if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
-    RIDG_CUDA(h, ridg::launch_predict_mixed(g, h->nb, h->Q, h->mixed_pred, h->W, h->thT,
+    RIDG_CUDA(h, ridg::launch_predict_mixed(g, h->nb, h->Q, h->mixed_pred, h->W, h->thT, 1,
                                             h->status, h->stream));
   } else {
     RIDG_CUDA(h, ridg::launch_predict_fp64(g, h->nb, h->Q, h->P, h->thT, h->W, h->thT, h->stream));

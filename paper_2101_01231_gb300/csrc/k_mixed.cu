@@ -48,7 +48,7 @@ namespace {
 constexpr int kTX = 8, kTY = 16;                 // cells per tile in x, y (128 = MMA M)
 constexpr int kHX = kTX + 2, kHY = kTY + 2;      // halo
 constexpr int kHalo = kHX * kHY;                 // 180 halo cells
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;                    // 8 warps: 2 per TMEM lane quadrant
 constexpr int kBits = 8;                         // digit width
 constexpr long kWaitLimit = 1L << 22;            // bounded mbarrier polls (well under a second)
 
@@ -109,6 +109,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 // error-free sum of two floats (Knuth): a + b = s + e exactly
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -136,7 +150,7 @@ __device__ __forceinline__ long long to_fixed(double x, int s, int L) {
 
 struct MixedLayout {
   int S, P, nout_pad, brows;
-  uint32_t digits_off, halo_off, b_off, bytes;
+  uint32_t digits_off, b_off, bytes;
 };
 
 __host__ __device__ inline MixedLayout mixed_layout(int S, int thS, int nout_pad) {
@@ -147,43 +161,43 @@ __host__ __device__ inline MixedLayout mixed_layout(int S, int thS, int nout_pad
   l.brows = S * nout_pad;
   l.digits_off = 0;
   const uint32_t digits = (uint32_t)S * l.P * kHalo * 16;
-  l.halo_off = (digits + 127) & ~127u;
-  const uint32_t halo = (uint32_t)kHalo * thS * 8;
-  l.b_off = (l.halo_off + halo + 1023) & ~1023u;
+  l.b_off = (digits + 1023) & ~1023u;
   const uint32_t bbytes = (uint32_t)9 * l.P * l.brows * 16;
   l.bytes = l.b_off + bbytes;
   return l;
 }
 
-template <int NB, int NOUTP>
-__global__ void __launch_bounds__(kThreads) predict_mixed_kernel(
+// one work item = 8 consecutive modes (one core-matrix row) of one halo cell
+constexpr int kMaxItems = 3;  // ceil(180 * P / 256) for P <= 4
+
+template <int NB, int NOUTP, bool OUTF2>
+__global__ void __launch_bounds__(kThreads, 2) predict_mixed_kernel(
     const double* __restrict__ Q, const uint4* __restrict__ Bg, const double* __restrict__ rscale,
-    int S, int nout, double* __restrict__ Y, int ystride, int nx, int ny, int* status) {
+    const float* __restrict__ rowmul, int S, int nout, void* __restrict__ Yv, long long ystride_e,
+    long long ystride_c, int* __restrict__ texp, int nx, int ny, int* status) {
   constexpr int THS = NB * NB;
   constexpr int TPAD = ((THS + 15) / 16) * 16;
   constexpr int P = TPAD / 8;
   constexpr int KSTEPS = TPAD / 16;
+  constexpr int NITEMS = kHalo * P;
+  constexpr int IPT = (NITEMS + kThreads - 1) / kThreads;  // items per thread
+  static_assert(IPT <= kMaxItems, "too many halo items per thread");
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ unsigned long long red[kThreads / 32];
   const MixedLayout L = mixed_layout(S, THS, NOUTP);
   unsigned char* digits = smem + L.digits_off;
-  double* halo = (double*)(smem + L.halo_off);
-  long long* fixedp = (long long*)(smem + L.halo_off);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
   const int ntiles = ntx * nty;
-  const int ncols = NOUTP * 8 > 256 ? 512 : 256;  // TMEM columns: >= S * NOUTP (S <= 8)
+  const int ncols = NOUTP * 8 > 256 ? 512 : 256;  // TMEM columns: >= S * NOUTP (S <= 7)
 
-  // operator digits -> shared memory (once per CTA), zero the digit planes (pad modes)
+  // operator digits -> shared memory (once per CTA)
   {
     uint4* bs = (uint4*)(smem + L.b_off);
     const int nb16 = 9 * P * L.brows;
     for (int i = tid; i < nb16; i += kThreads) bs[i] = Bg[i];
-    uint4* ds = (uint4*)digits;
-    const int nd16 = S * P * kHalo;
-    for (int i = tid; i < nd16; i += kThreads) ds[i] = make_uint4(0, 0, 0, 0);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -205,18 +219,42 @@ __global__ void __launch_bounds__(kThreads) predict_mixed_kernel(
 
   for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const int tx = tile % ntx, ty = tile / ntx;
-    const int x0 = tx * kTX - 1, y0 = ty * kTY - 1;
-    // 1. halo of FP64 coefficients (periodic), and its largest magnitude
+    // 1. halo values of this thread's items (8 modes of one halo cell each), and the max
+    double v[IPT][8];
     unsigned long long mx = 0;
-    for (int i = tid; i < kHalo * THS; i += kThreads) {
-      const int h = i / THS, s = i % THS;
-      int gx = x0 + h % kHX, gy = y0 + h / kHX;
-      gx = (gx % nx + nx) % nx;
-      gy = (gy % ny + ny) % ny;
-      const double v = __ldg(Q + ((long long)gy * nx + gx) * THS + s);
-      halo[i] = v;
-      const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
-      mx = a > mx ? a : mx;
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      const int item = tid + it * kThreads;
+      const int h = item % kHalo, p = item / kHalo;
+      int gx = tx * kTX - 1 + h % kHX, gy = ty * kTY - 1 + h / kHX;
+      while (gx < 0) gx += nx;
+      while (gx >= nx) gx -= nx;
+      while (gy < 0) gy += ny;
+      while (gy >= ny) gy -= ny;
+      const double* q = Q + ((long long)gy * nx + gx) * THS + p * 8;
+      if (item < NITEMS) {
+        if (THS % 8 == 0) {
+          const double2* q2 = (const double2*)q;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            double2 t = __ldg(q2 + j);
+            v[it][2 * j] = t.x;
+            v[it][2 * j + 1] = t.y;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[it][j] = (p * 8 + j < THS) ? __ldg(q + j) : 0.0;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[it][j] = 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const unsigned long long a =
+            (unsigned long long)__double_as_longlong(v[it][j]) & 0x7FFFFFFFFFFFFFFFULL;
+        mx = a > mx ? a : mx;
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -230,24 +268,56 @@ __global__ void __launch_bounds__(kThreads) predict_mixed_kernel(
     for (int w = 1; w < kThreads / 32; ++w) mx = red[w] > mx ? red[w] : mx;
     // tile exponent: max|X| < 2^s
     const int sexp = mx == 0 ? 0 : (int)((mx >> 52) & 0x7FF) - 1022;
-    // 2. fixed point (in place) and digit planes
-    for (int i = tid; i < kHalo * THS; i += kThreads) fixedp[i] = to_fixed(halo[i], sexp, Lfix);
-    for (int a = 0; a < S; ++a) {
-      const int sh = Lfix - kBits * (a + 1);
-      __nv_bfloat16* dplane = (__nv_bfloat16*)(digits + (size_t)a * P * kHalo * 16);
-      for (int i = tid; i < kHalo * THS; i += kThreads) {
-        long long F = fixedp[i];
-        long long d;
-        if (sh > 0) {
-          d = (F + (1LL << (sh - 1))) >> sh;
-          fixedp[i] = F - (d << sh);
-        } else {
-          d = F;
+    // 2. fixed point (L = 8 S fraction bits), balanced base-256 digits from its bytes, and
+    //    the digit planes [digit][mode group][halo cell][8 modes] (one 16 B store each)
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      const int item = tid + it * kThreads;
+      uint32_t packed[7][4];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const long long F = to_fixed(v[it][j], sexp, Lfix);
+        const uint32_t lo32 = (uint32_t)F, hi32 = (uint32_t)((unsigned long long)F >> 32);
+        const int neg = (int)(hi32 >> 31);
+        int carry = 0;
+        int d[7];
+#pragma unroll
+        for (int a = 6; a >= 0; --a) {
+          if (a < S) {
+            const int k = S - 1 - a;  // byte index of digit a
+            const uint32_t byte = (k < 4 ? (lo32 >> (8 * k)) : (hi32 >> (8 * (k - 4)))) & 0xFFu;
+            if (a > 0) {
+              const int t = (int)byte + carry;
+              carry = (t + 128) >> 8;
+              d[a] = t - (carry << 8);
+            } else {
+              d[0] = (int)byte - (neg << 8) + carry;
+            }
+          } else {
+            d[a] = 0;
+          }
         }
-        const int h = i / THS, s = i % THS;
-        dplane[((s / 8) * kHalo + h) * 8 + (s % 8)] = __float2bfloat16_rn((float)d);
+#pragma unroll
+        for (int a = 0; a < 7; ++a) {
+          // |d| <= 256: exact in FP32 by the 1.5 * 2^23 trick, and its BF16 is the top half
+          const uint32_t b = __float_as_uint(__int_as_float(0x4B400000 + d[a]) - 12582912.0f) >> 16;
+          if (j & 1)
+            packed[a][j / 2] |= b << 16;
+          else
+            packed[a][j / 2] = b;
+        }
+      }
+      if (item < NITEMS) {
+        const int h = item % kHalo, p = item / kHalo;
+#pragma unroll
+        for (int a = 0; a < 7; ++a)
+          if (a < S) {
+            uint4* dst = (uint4*)(digits + ((size_t)(a * P + p) * kHalo + h) * 16);
+            *dst = make_uint4(packed[a][0], packed[a][1], packed[a][2], packed[a][3]);
+          }
       }
     }
+    if (OUTF2 && tid == 0) texp[tile] = sexp;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     // 3./4. MMAs, issued by one thread
@@ -280,7 +350,8 @@ __global__ void __launch_bounds__(kThreads) predict_mixed_kernel(
               smem_u32(&mbar))
           : "memory");
     }
-    // 5. epilogue
+    // 5. epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its 32 cells) and half of the
+    //    columns of every block
     if (!mbar_wait(smem_u32(&mbar), phase)) {
       ok = false;
       if (tid == 0) atomicOr(status, 2);
@@ -290,34 +361,48 @@ __global__ void __launch_bounds__(kThreads) predict_mixed_kernel(
     phase ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     {
-      const int ix = tid % kTX, iy = tid / kTX;
+      const int quad = warp & 3, half = warp >> 2;
+      const int cell = quad * 32 + lane;
+      const int ix = cell % kTX, iy = cell / kTX;
       const int gx = tx * kTX + ix, gy = ty * kTY + iy;
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+      const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
+      const long long e = (long long)gy * nx + gx;
 #pragma unroll 1
-      for (int cb = 0; cb < NOUTP; cb += 32) {
-        float hi[32], lo[32], v[32];
-        tmem_ld32(lane_addr + (uint32_t)cb, hi);
+      for (int cb = half * (NOUTP / 2); cb < (half + 1) * (NOUTP / 2); cb += 16) {
+        float hi[16], lo[16], vv[16];
+        tmem_ld16(lane_addr + (uint32_t)cb, hi);
 #pragma unroll
-        for (int c = 0; c < 32; ++c) lo[c] = 0.f;
+        for (int c = 0; c < 16; ++c) lo[c] = 0.f;
         float w = 1.f;
         for (int t = 1; t < S; ++t) {
           w *= 1.f / 256.f;
-          tmem_ld32(lane_addr + (uint32_t)(t * NOUTP + cb), v);
+          tmem_ld16(lane_addr + (uint32_t)(t * NOUTP + cb), vv);
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            float s, e;
-            two_sum(hi[c], v[c] * w, s, e);
-            hi[c] = s;
-            lo[c] += e;
+          for (int c = 0; c < 16; ++c) {
+            float s2, e2;
+            two_sum(hi[c], vv[c] * w, s2, e2);
+            hi[c] = s2;
+            lo[c] += e2;
           }
         }
         if (gx < nx && gy < ny) {
-          double* y = Y + ((long long)gy * nx + gx) * ystride;
-          const double tscale = __longlong_as_double((long long)(sexp + 1023) << 52);
+          if (OUTF2) {
+            // (hi, lo) scaled to the common row exponent; value = (hi + lo) 2^(s + gmax - 16)
+            float2* y = (float2*)Yv + e * ystride_e + (long long)cb * ystride_c;
 #pragma unroll
-          for (int c = 0; c < 32; ++c)
-            if (cb + c < nout)
-              y[cb + c] = ((double)hi[c] + (double)lo[c]) * (tscale * rscale[cb + c]);
+            for (int c = 0; c < 16; ++c)
+              if (cb + c < nout) {
+                const float m = rowmul[cb + c];
+                y[c * ystride_c] = make_float2(hi[c] * m, lo[c] * m);
+              }
+          } else {
+            double* y = (double*)Yv + e * ystride_e + (long long)cb * ystride_c;
+            const double tscale = __longlong_as_double((long long)(sexp + 1023) << 52);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+              if (cb + c < nout)
+                y[c * ystride_c] = ((double)hi[c] + (double)lo[c]) * (tscale * rscale[cb + c]);
+          }
         }
       }
     }
@@ -331,56 +416,139 @@ __global__ void __launch_bounds__(kThreads) predict_mixed_kernel(
 }
 
 // ---------------------------------------------------------------------------------------
-// correction from the fused outputs: Y = [V (theta_S) | u_x (NB) | u_y (NB)] per cell, with
-// V = sum_d nu_d (D along d) Wbar and u_d = nu_d trace(Wbar) on the upwind side of dim d
-// (trace at +1 when a_d > 0, at -1 when a_d < 0).  The face value at i+1/2 in dim d is u_d
-// of the upwind cell (one stored number per face), so both neighbours apply the same flux.
+// correction from the fused outputs.  Y holds, output-major, [V (theta_S) | u_x (NB) | u_y
+// (NB)] per cell as double-float pairs (hi, lo) whose value is (hi + lo) 2^(texp + gmax - 16)
+// with texp the exponent of the cell's tile: V = sum_d nu_d (D along d) Wbar, and u_d =
+// nu_d trace(Wbar) on the upwind side of dim d (trace at +1 when a_d > 0, at -1 when
+// a_d < 0).  The face value at i+1/2 in dim d is u_d of the upwind cell -- one stored pair
+// per face, applied with opposite signs to both neighbours.  With phi_a(-1) = (-1)^a
+// phi_a(+1) the update of mode (a, t) along d is phi_a(+1) (-F_{i+1/2} + (-1)^a F_{i-1/2}).
+// The sums run in double-float FP32 after aligning every pair to the largest exponent
+// involved (power-of-two scaling, exact); only the final state update is FP64.
 // ---------------------------------------------------------------------------------------
+struct DF {
+  float h, l;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  float s2 = __fadd_rn(s, e);
+  return DF{s2, __fsub_rn(e, __fsub_rn(s2, s))};
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.h, -a.l}; }
+
+// (ch + cl) * (a.h + a.l) to double-float accuracy
+__device__ __forceinline__ DF df_mul_const(float ch, float cl, DF a) {
+  const float p = __fmul_rn(ch, a.h);
+  float e = __fmaf_rn(ch, a.h, -p);
+  e = __fmaf_rn(ch, a.l, e);
+  e = __fmaf_rn(cl, a.h, e);
+  const float s = __fadd_rn(p, e);
+  return DF{s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+
+__device__ __forceinline__ DF df_scale(DF a, float m) { return DF{a.h * m, a.l * m}; }
+
+// exact power of two 2^k as a float for k in [-126, 127]; 0 below
+__device__ __forceinline__ float pow2f(int k) {
+  return k < -126 ? 0.f : __uint_as_float((uint32_t)(k + 127) << 23);
+}
+
+// float * 2^k as a double, by exponent arithmetic on the bits (exact; 0 stays 0)
+__device__ __forceinline__ double f2d_scaled(float f, int k) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e8 = (b >> 23) & 0xFF;
+  if (e8 == 0) return 0.0;  // zero (denormal pairs do not occur: values are digit sums)
+  const int e11 = (int)e8 - 127 + 1023 + k;
+  if (e11 <= 0) return 0.0;
+  const uint32_t hiw = (b & 0x80000000u) | ((uint32_t)e11 << 20) | ((b & 0x7FFFFFu) >> 3);
+  const uint32_t low = (b & 0x7u) << 29;
+  return __hiloint2double((int)hiw, (int)low);
+}
+
 template <int NB>
 __global__ void __launch_bounds__(128) correct_fused_kernel(double* __restrict__ Q,
-                                                            const double* __restrict__ Y,
-                                                            int ystride, int nx, int ny,
-                                                            CorrParams cp, int sgnx, int sgny) {
+                                                            const float2* __restrict__ Y,
+                                                            const int* __restrict__ texp,
+                                                            int nx, int ny, CorrParams cp,
+                                                            int gmax, int sgnx, int sgny) {
   constexpr int THS = NB * NB;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)nx * ny) return;
-  const int ix = (int)(e % nx), iy = (int)(e / nx);
-  double dq[THS];
-  const double* y = Y + e * ystride;
+  constexpr int PITCH = THS + 1;  // odd pitch: conflict-free row access
+  __shared__ double sq[128 * PITCH];
+  const long long ncell = (long long)nx * ny;
+  const long long e0 = (long long)blockIdx.x * 128;
+  const int nblk = (int)min((long long)128, ncell - e0);
+  const int ntx = (nx + kTX - 1) / kTX;
+  // coalesced load of the block's state rows
+  for (int i = threadIdx.x; i < nblk * THS; i += 128) sq[(i / THS) * PITCH + i % THS] = Q[e0 * THS + i];
+  __syncthreads();
+  const long long e = e0 + threadIdx.x;
+  if (threadIdx.x < nblk) {
+    const int ix = (int)(e % nx), iy = (int)(e / nx);
+    // the cells whose stored values enter: own, and per dim the upwind cells of both faces
+    long long jr[2], jl[2];
+    int kr[2], kl[2];
+    const int kown = texp[(ix / kTX) + (iy / kTY) * ntx];
+    int kmax = kown;
 #pragma unroll
-  for (int s = 0; s < THS; ++s) dq[s] = y[s];
-#pragma unroll
-  for (int dd = 0; dd < 2; ++dd) {
-    const int sg = dd == 0 ? sgnx : sgny;
-    if (sg == 0) continue;
-    const int st = dd == 0 ? 1 : NB;
-    // faces i+1/2 (right/top) and i-1/2 (left/bottom): upwind cell of each face
-    long long jr, jl;
-    if (dd == 0) {
-      jr = sg > 0 ? e : (long long)iy * nx + (ix + 1 == nx ? 0 : ix + 1);
-      jl = sg > 0 ? (long long)iy * nx + (ix == 0 ? nx - 1 : ix - 1) : e;
-    } else {
-      jr = sg > 0 ? e : (long long)(iy + 1 == ny ? 0 : iy + 1) * nx + ix;
-      jl = sg > 0 ? (long long)(iy == 0 ? ny - 1 : iy - 1) * nx + ix : e;
+    for (int dd = 0; dd < 2; ++dd) {
+      const int sg = dd == 0 ? sgnx : sgny;
+      int rx = ix, ry = iy, lx = ix, ly = iy;
+      if (dd == 0) {
+        if (sg > 0) lx = ix == 0 ? nx - 1 : ix - 1; else rx = ix + 1 == nx ? 0 : ix + 1;
+      } else {
+        if (sg > 0) ly = iy == 0 ? ny - 1 : iy - 1; else ry = iy + 1 == ny ? 0 : iy + 1;
+      }
+      jr[dd] = (long long)ry * nx + rx;
+      jl[dd] = (long long)ly * nx + lx;
+      kr[dd] = texp[(rx / kTX) + (ry / kTY) * ntx];
+      kl[dd] = texp[(lx / kTX) + (ly / kTY) * ntx];
+      if (sg != 0) kmax = max(kmax, max(kr[dd], kl[dd]));
     }
-    const double* fr = Y + jr * ystride + THS + dd * NB;
-    const double* fl = Y + jl * ystride + THS + dd * NB;
+    DF dq[THS];
+    const float mown = pow2f(kown - kmax);
 #pragma unroll
-    for (int t = 0; t < NB; ++t) {
-      const double vr = fr[t], vl = fl[t];
-      const int base = dd == 0 ? t * NB : t;
+    for (int s = 0; s < THS; ++s) {
+      const float2 y = Y[s * ncell + e];  // volume term V
+      dq[s] = df_scale(DF{y.x, y.y}, mown);
+    }
 #pragma unroll
-      for (int a = 0; a < NB; ++a) {
-        double v = dq[base + a * st];
-        v = fma(-cp.ep[a], vr, v);
-        v = fma(cp.em[a], vl, v);
-        dq[base + a * st] = v;
+    for (int dd = 0; dd < 2; ++dd) {
+      const int sg = dd == 0 ? sgnx : sgny;
+      if (sg == 0) continue;
+      const int st = dd == 0 ? 1 : NB;
+      const float mr = pow2f(kr[dd] - kmax), ml = pow2f(kl[dd] - kmax);
+      const float2* u = Y + (long long)(THS + dd * NB) * ncell;
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        const float2 a = u[t * ncell + jr[dd]], b = u[t * ncell + jl[dd]];
+        const DF fr = df_scale(DF{a.x, a.y}, mr), fl = df_scale(DF{b.x, b.y}, ml);
+        const DF w_even = df_add(fl, df_neg(fr));          // -F(i+1/2) + F(i-1/2)
+        const DF w_odd = df_neg(df_add(fl, fr));           // -F(i+1/2) - F(i-1/2)
+        const int base = dd == 0 ? t * NB : t;
+#pragma unroll
+        for (int a2 = 0; a2 < NB; ++a2) {
+          const DF w = (a2 & 1) ? w_odd : w_even;
+          const DF c = (a2 == 0) ? w : df_mul_const(cp.eph[a2], cp.epl[a2], w);
+          dq[base + a2 * st] = df_add(dq[base + a2 * st], c);
+        }
       }
     }
-  }
-  double* q = Q + e * THS;
+    const int kfin = kmax + gmax - 16;
+    double* q = sq + threadIdx.x * PITCH;
 #pragma unroll
-  for (int s = 0; s < THS; ++s) q[s] = q[s] + dq[s];
+    for (int s = 0; s < THS; ++s) {
+      double v = q[s];
+      v = v + f2d_scaled(dq[s].h, kfin);
+      v = v + f2d_scaled(dq[s].l, kfin);
+      q[s] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nblk * THS; i += 128) Q[e0 * THS + i] = sq[(i / THS) * PITCH + i % THS];
 }
 
 }  // namespace
@@ -395,7 +563,8 @@ bool mixed_supported(int dim, int nb, int nout) {
 static int nout_pad_of(int nout) { return nout <= 32 ? 32 : 64; }
 
 int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int slices,
-                std::vector<unsigned short>& digits, std::vector<double>& rscale, MixedOp& op) {
+                std::vector<unsigned short>& digits, std::vector<double>& rscale,
+                std::vector<float>& rowmul, MixedOp& op) {
   if (!mixed_supported(dim, nb, nout) || slices < 2 || slices > 7) return RIDG_EINVAL;
   const int thS = nb * nb, K = 9 * thS;
   if ((int)G.size() < nout * K) return RIDG_EINVAL;
@@ -406,6 +575,8 @@ int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int sli
   // digits in the shared-memory layout [k-chunk][row = c' * NOUTP + c][8]
   digits.assign((size_t)9 * L.P * L.brows * 8, 0);
   rscale.assign(NOUTP, 0.0);
+  rowmul.assign(NOUTP, 0.0f);
+  std::vector<int> gexp(NOUTP, -100000);
   for (int c = 0; c < nout; ++c) {
     double mx = 0.0;
     for (int k = 0; k < K; ++k) mx = std::max(mx, std::fabs(G[(size_t)c * K + k]));
@@ -414,6 +585,7 @@ int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int sli
       std::frexp(mx, &g);  // mx < 2^g
     }
     rscale[c] = std::ldexp(1.0, g - 2 * kBits);
+    gexp[c] = mx > 0 ? g : -100000;
     for (int k = 0; k < K; ++k) {
       const int r = k / thS, s = k % thS;
       const int kp = r * tpad + s;  // padded column
@@ -430,6 +602,12 @@ int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int sli
       }
     }
   }
+  int gmax = -100000;
+  for (int c = 0; c < nout; ++c) gmax = std::max(gmax, gexp[c]);
+  if (gmax == -100000) gmax = 0;
+  for (int c = 0; c < nout; ++c)
+    rowmul[c] = gexp[c] == -100000 ? 0.0f : (gexp[c] - gmax < -126 ? 0.0f : std::ldexp(1.0f, gexp[c] - gmax));
+  op.gmax = gmax;
   op.nout = nout;
   op.npad = NOUTP;
   op.K = K;
@@ -439,11 +617,12 @@ int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int sli
   return RIDG_OK;
 }
 
-template <int NB, int NOUTP>
-static cudaError_t launch_mixed_t(const Grid& g, const double* Q, const MixedOp& op, double* Y,
-                                  int ystride, int* status, cudaStream_t s) {
+template <int NB, int NOUTP, bool OUTF2>
+static cudaError_t launch_mixed_t(const Grid& g, const double* Q, const MixedOp& op, void* Y,
+                                  long long ys_e, long long ys_c, int* texp, int* status,
+                                  cudaStream_t s) {
   const MixedLayout L = mixed_layout(op.slices, NB * NB, NOUTP);
-  auto kern = predict_mixed_kernel<NB, NOUTP>;
+  auto kern = predict_mixed_kernel<NB, NOUTP, OUTF2>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -452,44 +631,57 @@ static cudaError_t launch_mixed_t(const Grid& g, const double* Q, const MixedOp&
   const int ntiles = ((g.n[0] + kTX - 1) / kTX) * ((g.n[1] + kTY - 1) / kTY);
   const int per_sm = (2 * ((size_t)L.bytes + 2048) <= 233472 && NOUTP <= 32) ? 2 : 1;
   const int grid = std::min(ntiles, sms * per_sm);
-  kern<<<grid, kThreads, L.bytes, s>>>(Q, (const uint4*)op.b_slices, op.row_scale, op.slices,
-                                       op.nout, Y, ystride, g.n[0], g.n[1], status);
+  kern<<<grid, kThreads, L.bytes, s>>>(Q, (const uint4*)op.b_slices, op.row_scale, op.row_mul,
+                                       op.slices, op.nout, Y, ys_e, ys_c, texp, g.n[0], g.n[1],
+                                       status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_predict_mixed(const Grid& g, int nb, const double* Q, const MixedOp& op,
-                                 double* Y, int ystride, int* status, cudaStream_t s) {
+                                 double* Y, long long ys_e, long long ys_c, int* status,
+                                 cudaStream_t s) {
   if (g.dim != 2) return cudaErrorInvalidValue;
+#define RIDG_MIXED_CASE(NBV, NP) \
+  case NBV: return launch_mixed_t<NBV, NP, false>(g, Q, op, Y, ys_e, ys_c, nullptr, status, s);
   if (op.npad == 32) {
-    switch (nb) {
-      case 2: return launch_mixed_t<2, 32>(g, Q, op, Y, ystride, status, s);
-      case 3: return launch_mixed_t<3, 32>(g, Q, op, Y, ystride, status, s);
-      case 4: return launch_mixed_t<4, 32>(g, Q, op, Y, ystride, status, s);
-      case 5: return launch_mixed_t<5, 32>(g, Q, op, Y, ystride, status, s);
-    }
+    switch (nb) { RIDG_MIXED_CASE(2, 32) RIDG_MIXED_CASE(3, 32) RIDG_MIXED_CASE(4, 32) RIDG_MIXED_CASE(5, 32) }
   } else if (op.npad == 64) {
-    switch (nb) {
-      case 2: return launch_mixed_t<2, 64>(g, Q, op, Y, ystride, status, s);
-      case 3: return launch_mixed_t<3, 64>(g, Q, op, Y, ystride, status, s);
-      case 4: return launch_mixed_t<4, 64>(g, Q, op, Y, ystride, status, s);
-      case 5: return launch_mixed_t<5, 64>(g, Q, op, Y, ystride, status, s);
-    }
+    switch (nb) { RIDG_MIXED_CASE(2, 64) RIDG_MIXED_CASE(3, 64) RIDG_MIXED_CASE(4, 64) RIDG_MIXED_CASE(5, 64) }
   }
+#undef RIDG_MIXED_CASE
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_correct_fused(const Grid& g, int nb, double* Q, const double* Y, int ystride,
-                                 const CorrParams& cp, int sgnx, int sgny, cudaStream_t s) {
+cudaError_t launch_predict_fused(const Grid& g, int nb, const double* Q, const MixedOp& op,
+                                 void* Y2, int* texp, int* status, cudaStream_t s) {
   if (g.dim != 2) return cudaErrorInvalidValue;
-  const int threads = 128;
-  const unsigned blocks = (unsigned)((g.ncell + threads - 1) / threads);
+#define RIDG_MIXED_CASE(NBV, NP) \
+  case NBV: return launch_mixed_t<NBV, NP, true>(g, Q, op, Y2, 1, g.ncell, texp, status, s);
+  if (op.npad == 32) {
+    switch (nb) { RIDG_MIXED_CASE(2, 32) RIDG_MIXED_CASE(3, 32) RIDG_MIXED_CASE(4, 32) }
+  } else if (op.npad == 64) {
+    switch (nb) { RIDG_MIXED_CASE(5, 64) }
+  }
+#undef RIDG_MIXED_CASE
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_correct_fused(const Grid& g, int nb, double* Q, const void* Y2,
+                                 const int* texp, int gmax, const CorrParams& cp, int sgnx,
+                                 int sgny, cudaStream_t s) {
+  if (g.dim != 2) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)((g.ncell + 127) / 128);
+  const float2* Y = (const float2*)Y2;
+#define RIDG_CORR_CASE(NBV)                                                                  \
+  case NBV:                                                                                   \
+    correct_fused_kernel<NBV><<<blocks, 128, 0, s>>>(Q, Y, texp, g.n[0], g.n[1], cp, gmax,    \
+                                                     sgnx, sgny);                             \
+    break;
   switch (nb) {
-    case 2: correct_fused_kernel<2><<<blocks, threads, 0, s>>>(Q, Y, ystride, g.n[0], g.n[1], cp, sgnx, sgny); break;
-    case 3: correct_fused_kernel<3><<<blocks, threads, 0, s>>>(Q, Y, ystride, g.n[0], g.n[1], cp, sgnx, sgny); break;
-    case 4: correct_fused_kernel<4><<<blocks, threads, 0, s>>>(Q, Y, ystride, g.n[0], g.n[1], cp, sgnx, sgny); break;
-    case 5: correct_fused_kernel<5><<<blocks, threads, 0, s>>>(Q, Y, ystride, g.n[0], g.n[1], cp, sgnx, sgny); break;
+    RIDG_CORR_CASE(2) RIDG_CORR_CASE(3) RIDG_CORR_CASE(4) RIDG_CORR_CASE(5)
     default: return cudaErrorInvalidValue;
   }
+#undef RIDG_CORR_CASE
   return cudaGetLastError();
 }
 

@@ -16,6 +16,7 @@ constexpr int kMaxNB = 8;  // largest supported M + 1
 // Per-launch constants of the correction (1D tables and CFL numbers), passed by value.
 struct CorrParams {
   double ep[kMaxNB], em[kMaxNB];       // phi_b(+1), phi_b(-1)
+  float eph[kMaxNB], epl[kMaxNB];      // phi_b(+1) as a double-float pair
   double D[kMaxNB * kMaxNB];           // int phi_a' phi_b
   double nu[3], nup[3], num[3];        // a_d dt / h_d and its positive / negative parts
 };
@@ -36,18 +37,27 @@ cudaError_t launch_correct_linear(const Grid& g, int nb, double* Q, const double
 
 // ---- mixed BF16 tensor-core prediction (k_mixed.cu) ----
 struct MixedOp {
-  int nout = 0, npad = 0, K = 0, Kpad = 0, slices = 0, bits = 0;
-  void* b_slices = nullptr;   // device, core-matrix layout bf16 digits of P rows
-  double* row_scale = nullptr;  // device, 2^e per P row
+  int nout = 0, npad = 0, K = 0, Kpad = 0, slices = 0, bits = 0, gmax = 0;
+  void* b_slices = nullptr;     // device, core-matrix layout bf16 digits of the operator rows
+  double* row_scale = nullptr;  // device, 2^(g_c - 16) per row
+  float* row_mul = nullptr;     // device, 2^(g_c - gmax) per row
 };
 bool mixed_supported(int dim, int nb, int nout);
 int mixed_build(int dim, int nb, const std::vector<double>& P, int nout, int slices,
-                std::vector<unsigned short>& digits, std::vector<double>& rscale, MixedOp& op);
+                std::vector<unsigned short>& digits, std::vector<double>& rscale,
+                std::vector<float>& rowmul, MixedOp& op);
+// output c of cell e goes to W[e * ys_e + c * ys_c]
 cudaError_t launch_predict_mixed(const Grid& g, int nb, const double* Q, const MixedOp& op,
-                                 double* W, int wstride, int* status, cudaStream_t s);
-// Q[e] += correction from the fused outputs Y = [V | u_x | u_y] (2D); sgn = sign of a_d
-cudaError_t launch_correct_fused(const Grid& g, int nb, double* Q, const double* Y, int ystride,
-                                 const CorrParams& cp, int sgnx, int sgny, cudaStream_t s);
+                                 double* W, long long ys_e, long long ys_c, int* status,
+                                 cudaStream_t s);
+// fused step operator outputs [V | u_x | u_y] as output-major double-float pairs plus one
+// exponent per 8 x 16 tile
+cudaError_t launch_predict_fused(const Grid& g, int nb, const double* Q, const MixedOp& op,
+                                 void* Y2, int* texp, int* status, cudaStream_t s);
+// Q[e] += correction from those outputs; sgn = sign of a_d
+cudaError_t launch_correct_fused(const Grid& g, int nb, double* Q, const void* Y2,
+                                 const int* texp, int gmax, const CorrParams& cp, int sgnx,
+                                 int sgny, cudaStream_t s);
 size_t mixed_smem_bytes(int nb, const MixedOp& op);
 
 // ---- diagnostics (k_diag.cu) ----
@@ -88,7 +98,8 @@ struct ridg_handle {
   int red_blocks = 256;
   ridg::MixedOp mixed;       // fused step operator [V; u_x; u_y] P-bar (2D)
   ridg::MixedOp mixed_pred;  // full prediction operator P
-  double* Y = nullptr;       // fused outputs of the mixed step (cells * nout)
+  double* Y = nullptr;       // fused outputs of the mixed step (cells * nout pairs)
+  int* texp = nullptr;       // per-tile exponents of the fused outputs
   int ny_out = 0;
   // host copy of the operator
   std::vector<double> P_host;
