@@ -146,11 +146,20 @@ int rebuild_linear(ridg_t* h) {
     }
     h->ny_out = nout;
     if (!h->Y) {
-      const size_t ntiles = (size_t)((h->n[0] + 7) / 8) * ((h->n[1] + 15) / 16);
+      Grid g = grid_of(h);
       h->Y = (double*)dev_alloc(h, (size_t)h->ncell * nout * sizeof(double));
-      h->texp = (int*)dev_alloc(h, ntiles * sizeof(int));
-      if (!h->Y || !h->texp) return set_err(h, RIDG_ENOMEM, "fused output allocation failed");
+      h->ms.planes = dev_alloc(h, ridg::mixed_plane_bytes(g, h->nb, h->opt.slices));
+      h->ms.exps = (int*)dev_alloc(h, 4 * sizeof(int));
+      h->ms.maxbits = (unsigned long long*)dev_alloc(h, 2 * sizeof(unsigned long long));
+      if (!h->Y || !h->ms.planes || !h->ms.exps || !h->ms.maxbits)
+        return set_err(h, RIDG_ENOMEM, "mixed-path allocation failed");
+      RIDG_CUDA(h, cudaMemsetAsync(h->ms.planes, 0, ridg::mixed_plane_bytes(g, h->nb, h->opt.slices),
+                                   h->stream));
+      if (ridg::mixed_make_map(g, h->nb, h->opt.slices, h->ms.planes, h->ms.map) != RIDG_OK)
+        return set_err(h, RIDG_ECUDA, "tensor map creation failed");
+      h->ms.status = h->status;
     }
+    h->ms.valid = false;
   }
   RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
   drop_graphs(h);
@@ -160,12 +169,20 @@ int rebuild_linear(ridg_t* h) {
 
 int sign_of(double v) { return v > 0 ? 1 : (v < 0 ? -1 : 0); }
 
+// Mixed path: make the digit planes describe the current state (outside graph capture).
+int ensure_digits(ridg_t* h) {
+  if (h->opt.precision != RIDG_PREC_MIXED_BF16 || h->ms.valid) return RIDG_OK;
+  RIDG_CUDA(h, ridg::launch_mixed_refresh(grid_of(h), h->nb, h->opt.slices, h->Q, h->ms, h->stream));
+  h->ms.valid = true;
+  return RIDG_OK;
+}
+
 // The step's prediction: FP64 time mean into Wbar, or (mixed) the fused outputs into Y.
 int enqueue_predict_mean(ridg_t* h) {
   Grid g = grid_of(h);
   if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
-    RIDG_CUDA(h, ridg::launch_predict_fused(g, h->nb, h->Q, h->mixed, h->Y, h->texp, h->status,
-                                            h->stream));
+    RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed, h->ms, h->Y, 1, h->ncell, true,
+                                         h->stream));
   } else {
     RIDG_CUDA(h, ridg::launch_predict_fp64(g, h->nb, h->Q, h->P, h->thS, h->Wbar, h->thS,
                                            h->stream));
@@ -176,9 +193,9 @@ int enqueue_predict_mean(ridg_t* h) {
 int enqueue_correct_after_mean(ridg_t* h) {
   CorrParams cp = corr_params(h);
   if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
-    RIDG_CUDA(h, ridg::launch_correct_fused(grid_of(h), h->nb, h->Q, h->Y, h->texp,
+    RIDG_CUDA(h, ridg::launch_mixed_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
                                             h->mixed.gmax, cp, sign_of(h->flux.vel[0]),
-                                            sign_of(h->flux.vel[1]), h->stream));
+                                            sign_of(h->flux.vel[1]), h->ms, h->stream));
   } else {
     RIDG_CUDA(h, ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->Wbar, h->thS, cp,
                                              h->stream));
@@ -318,7 +335,9 @@ void ridg_destroy(ridg_t* h) {
   dev_free(h, h->mixed_pred.row_scale);
   dev_free(h, h->mixed_pred.row_mul);
   dev_free(h, h->Y);
-  dev_free(h, h->texp);
+  dev_free(h, h->ms.planes);
+  dev_free(h, h->ms.exps);
+  dev_free(h, h->ms.maxbits);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -338,6 +357,7 @@ int ridg_set_state(ridg_t* h, const double* q, int on_device) {
   h->t = 0.0;
   h->steps = 0;
   h->have_pred = false;
+  h->ms.valid = false;
   if (flag) return set_err(h, RIDG_ENONFINITE, "state contains NaN or Inf");
   return RIDG_OK;
 }
@@ -373,8 +393,10 @@ int ridg_predict(ridg_t* h, double* w_out, int on_device) {
   if (check_handle(h)) return RIDG_EINVAL;
   Grid g = grid_of(h);
   if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
-    RIDG_CUDA(h, ridg::launch_predict_mixed(g, h->nb, h->Q, h->mixed_pred, h->W, h->thT, 1,
-                                            h->status, h->stream));
+    int rc = ensure_digits(h);
+    if (rc) return rc;
+    RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed_pred, h->ms, h->W, h->thT, 1, false,
+                                         h->stream));
   } else {
     RIDG_CUDA(h, ridg::launch_predict_fp64(g, h->nb, h->Q, h->P, h->thT, h->W, h->thT, h->stream));
   }
@@ -394,6 +416,7 @@ int ridg_correct(ridg_t* h) {
   if (!h->have_pred) return set_err(h, RIDG_ESTATE, "ridg_correct needs a prediction first");
   CorrParams cp = corr_params(h);
   RIDG_CUDA(h, ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->W, h->thT, cp, h->stream));
+  h->ms.valid = false;
   h->have_pred = false;
   h->t += h->dt;
   h->steps += 1;
@@ -402,6 +425,8 @@ int ridg_correct(ridg_t* h) {
 
 int ridg_step(ridg_t* h, int n) {
   if (check_handle(h) || n < 1) return RIDG_EINVAL;
+  int rc0 = ensure_digits(h);
+  if (rc0) return rc0;
   auto it = h->graphs.find(n);
   if (it == h->graphs.end()) {
     cudaGraph_t graph = nullptr;
@@ -436,6 +461,8 @@ int read_status(ridg_t* h) {
   RIDG_CUDA(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
   if (st & 2) return set_err(h, RIDG_ETIMEOUT, "a bounded tensor-core wait gave up");
+  if (st & 4)
+    return set_err(h, RIDG_ENONFINITE, "state outgrew the mixed-precision digit range in a step");
   return RIDG_OK;
 }
 
@@ -447,6 +474,8 @@ int ridg_sync(ridg_t* h) {
 
 int ridg_profile_step(ridg_t* h, int n, ridg_profile_t* out) {
   if (check_handle(h) || n < 1 || !out) return RIDG_EINVAL;
+  int rc0 = ensure_digits(h);
+  if (rc0) return rc0;
   cudaEvent_t ev[3];
   for (int i = 0; i < 3; ++i) RIDG_CUDA(h, cudaEventCreate(&ev[i]));
   double tp = 0, tc = 0;

@@ -1,37 +1,37 @@
-// Mixed-precision linear prediction on the 5th-generation tensor cores (tcgen05, sm_103a).
+// Mixed-precision RIDG step for a linear flux in 2D on the 5th-generation tensor cores
+// (tcgen05 + TMA, sm_103a).
 //
-// What is computed.  Y[e][c] = sum_k G[c][k] X_e[k] for every cell e of a 2D mesh, where X_e
-// holds the theta_S coefficients of the 3 x 3 vertex neighbours of e (Sec. 2.2, eq. region)
-// and G is any operator with K = 9 theta_S columns -- the centre rows of the region
-// solution operator (the prediction of eq. pred_full_system for a linear flux), or those
-// rows composed with the linear correction functionals (volume term and upwind face
-// traces of Sec. 2.3), which is what the fused step uses.
+// What is computed.  Y[e][c] = sum_k G[c][k] X_e[k] for every cell e, where X_e holds the
+// theta_S coefficients of the 3 x 3 vertex neighbours of e (Sec. 2.2, eq. region) and G is
+// the centre-row region operator (the prediction of eq. pred_full_system for a linear
+// flux), optionally composed with the linear correction functionals of Sec. 2.3 (volume
+// term and upwind face traces) -- the "fused" step outputs [V | u_x | u_y].
 //
-// How (split-operand refinement on BF16 tensor cores).  Each FP64 operand is written as a
-// short sum of 8-bit "digits" times powers of two: for a tile of cells, X = 2^s sum_a
-// d_a 2^{-8(a+1)} with s the tile's largest exponent, |d_0| <= 256, |d_a| <= 128 (balanced,
-// rounded), and likewise each row of G with its own exponent.  Digits are small integers,
-// exact in BF16, so every digit product is exact and the K-sum of products with equal
-// digit weight a + c' = t is exact in the FP32 accumulator for t <= 4 (bounded by
-// (t+1) 144 2^16 < 2^24) and rounded far below the FP64 target for t >= 5.  The diagonal
-// sums acc_t live in TMEM (one block of columns per t); the epilogue recombines
-// sum_t acc_t 2^{-8t} with error-free FP32 two-sums and scales by 2^{s + g_c - 16} in FP64.
+// Split-operand refinement on BF16 tensor cores.  Every FP64 coefficient is written as a
+// sum of S balanced base-256 digits, X = 2^s sum_a d_a 2^{-8(a+1)}, with one exponent s
+// for the whole state (s = e + 1, 2^e > max |Q|): |d_0| <= 256, |d_a| <= 128.  The rows of
+// G get their own exponents.  Digits are small integers, exact in BF16; digit products
+// are exact; the K-sum of the products with equal weight a + c' = t is exact in the FP32
+// accumulator for t <= 4 (bounded by (t+1) 144 2^16 < 2^24) and rounded far below the FP64
+// target for t >= 5.  The diagonal sums acc_t live in TMEM (one block of columns per t);
+// the epilogue recombines sum_t acc_t 2^{-8t} with error-free FP32 two-sums.
 //
-// Data path per CTA (persistent over 8 x 16 cell tiles, 128 threads = 128 TMEM lanes):
-//   1. the tile's 10 x 18 halo of FP64 coefficients is read from HBM (periodic wrap);
-//   2. the halo is converted once to fixed point and split into S digit planes laid out
-//      [digit][mode-group of 8][halo cell][8 modes] in shared memory;
-//   3. the A operand of every MMA is read straight from the digit planes: region offset
-//      (ox, oy) is a shift of the descriptor start address, the 8-row core matrices are 8
-//      consecutive halo cells (16 B apart) and the 8-row groups are halo rows (160 B apart)
-//      -- an implicit im2col, no copy;
-//   4. one thread issues S x 9 x (theta_pad / 16) tcgen05.mma (M = 128) with B = the
-//      operator digits stacked [G-digit 0 .. S-1-a] so digit pair (a, c') lands in TMEM
-//      block a + c'; a single commit signals the mbarrier;
-//   5. the epilogue reads TMEM with tcgen05.ld (thread t <-> cell t), recombines and writes
-//      Y in FP64.
-// Every wait on the mbarrier is bounded; on timeout the kernel raises a status flag, waits
-// (bounded) once more for the tensor core, frees its TMEM and returns.
+// Data path (one step = two kernels):
+//   mixed_gemm_kernel      persistent, warp-specialised, 2-stage pipeline per CTA:
+//     warp 0 / lane 0: TMA + MMA.  Each 8 x 16 cell tile's operand is one 4D TMA box of the
+//       ghost-padded digit planes [digit, 8-mode group][y + 2][x + 2][8 modes] (10 x 18
+//       halo cells), landing in shared memory exactly in the K-major core-matrix layout:
+//       the A operand of the MMA for region offset (ox, oy) is the same buffer with the
+//       descriptor start shifted by (oy * 10 + ox) cells (implicit im2col, no copy).
+//       S x 9 x (theta_pad / 16) tcgen05.mma (M = 128); B = operator digits stacked so the
+//       pair (a, c') lands in TMEM block a + c'.  One commit per tile.
+//     warps 1..4: epilogue (thread <-> TMEM lane <-> cell); TMEM is double-buffered.
+//   mixed_correct_kernel   the correction from the fused outputs in double-float FP32 with
+//       the final conservative state update in FP64, the new state's maximum, and the
+//       digit planes of the new state for the next step's TMA.
+// Every wait is bounded; on timeout a kernel raises a status bit, waits once more (bounded)
+// for the tensor core, frees its TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -45,12 +45,18 @@
 namespace ridg {
 namespace {
 
-constexpr int kTX = 8, kTY = 16;                 // cells per tile in x, y (128 = MMA M)
-constexpr int kHX = kTX + 2, kHY = kTY + 2;      // halo
-constexpr int kHalo = kHX * kHY;                 // 180 halo cells
-constexpr int kThreads = 256;                    // 8 warps: 2 per TMEM lane quadrant
-constexpr int kBits = 8;                         // digit width
-constexpr long kWaitLimit = 1L << 22;            // bounded mbarrier polls (well under a second)
+constexpr int kTX = 8, kTY = 16;             // cells per tile in x, y (128 = MMA M)
+constexpr int kHX = kTX + 2, kHY = kTY + 2;  // halo
+constexpr int kHalo = kHX * kHY;             // 180 halo cells
+constexpr int kBits = 8;                     // digit width
+constexpr long kWaitLimit = 1L << 22;        // bounded mbarrier polls (well under a second)
+constexpr int kGemmThreads = 288;            // warp 0: TMA + MMA, warps 1..8: epilogue
+constexpr int kStages = 3;                   // shared-memory stages of the operand boxes
+constexpr int kMaxMma = 80;                  // MMA descriptors per tile (table size)
+
+// status bits
+constexpr int kStatusTimeout = 2;
+constexpr int kStatusRange = 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -80,6 +86,19 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b,
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+__device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
   uint32_t done = 0;
   for (long it = 0; it < kWaitLimit && !done; ++it) {
@@ -93,34 +112,41 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
   return done != 0;
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+// the same bounded wait with a short sleep between polls (for warps that only consume)
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (long it = 0; it < kWaitLimit && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    if (!done) __nanosleep(64);
+  }
+  return done != 0;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint32_t mbar) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%16];"
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      : "memory");
+}
+
+// 8 consecutive TMEM columns of this thread's lane (no wait: see tmem_wait_ld)
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
+        "=r"(r[7])
       : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // error-free sum of two floats (Knuth): a + b = s + e exactly
@@ -134,12 +160,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 __device__ __forceinline__ long long to_fixed(double x, int s, int L) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((u >> 52) & 0x7FF);
-  if (ex == 0) return 0;  // zero / subnormal: far below the tile's scale
+  if (ex == 0) return 0;  // zero / subnormal: far below the state's scale
   const long long mant = (long long)((u & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
   const int sh = ex - 1075 + L - s;
   long long F;
   if (sh >= 0) {
-    F = mant << sh;
+    F = sh < 11 ? (mant << sh) : (1LL << 62);  // out of range: flagged by the caller
   } else if (sh > -63) {
     F = (mant + (1LL << (-sh - 1))) >> (-sh);
   } else {
@@ -148,56 +174,159 @@ __device__ __forceinline__ long long to_fixed(double x, int s, int L) {
   return (u >> 63) ? -F : F;
 }
 
-struct MixedLayout {
-  int S, P, nout_pad, brows;
-  uint32_t digits_off, b_off, bytes;
+// S balanced base-256 digits of 8 consecutive coefficients, packed as BF16 (one 16 B row
+// per digit).  Returns false if a value does not fit below 2^s.
+template <int S>
+__device__ __forceinline__ bool make_digit_rows(const double* v, int s, uint4* rows) {
+  constexpr int L = kBits * S;
+  uint32_t packed[S][4];
+  bool fits = true;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const long long F = to_fixed(v[j], s, L);
+    fits &= (F < (1LL << L)) && (F > -(1LL << L));
+    const uint32_t lo32 = (uint32_t)F, hi32 = (uint32_t)((unsigned long long)F >> 32);
+    const int neg = (int)(hi32 >> 31);
+    int carry = 0;
+    int d[S];
+#pragma unroll
+    for (int a = S - 1; a >= 0; --a) {
+      const int k = S - 1 - a;  // byte index of digit a
+      const uint32_t byte = (k < 4 ? (lo32 >> (8 * k)) : (hi32 >> (8 * (k - 4)))) & 0xFFu;
+      if (a > 0) {
+        const int t = (int)byte + carry;
+        carry = (t + 128) >> 8;
+        d[a] = t - (carry << 8);
+      } else {
+        d[0] = (int)byte - (neg << 8) + carry;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+      // |d| <= 256: exact in FP32 by the 1.5 * 2^23 trick, and its BF16 is the top half
+      const uint32_t b = __float_as_uint(__int_as_float(0x4B400000 + d[a]) - 12582912.0f) >> 16;
+      if (j & 1)
+        packed[a][j / 2] |= b << 16;
+      else
+        packed[a][j / 2] = b;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < S; ++a) rows[a] = make_uint4(packed[a][0], packed[a][1], packed[a][2], packed[a][3]);
+  return fits;
+}
+
+__device__ __forceinline__ int exponent_above(unsigned long long absbits) {
+  // e with max < 2^e (0 for a zero maximum)
+  return absbits == 0 ? 0 : (int)((absbits >> 52) & 0x7FF) - 1022;
+}
+
+struct GemmLayout {
+  int P, brows;
+  uint32_t stage_bytes, b_off, bar_off, tab_off, bytes;
 };
 
-__host__ __device__ inline MixedLayout mixed_layout(int S, int thS, int nout_pad) {
-  MixedLayout l;
-  l.S = S;
+struct MmaEntry {
+  uint64_t bdesc;   // operator digits (B) descriptor
+  uint32_t aoff16;  // A start offset inside a stage, in 16 B units
+  uint32_t dcol;    // TMEM column of D
+  uint32_t idesc;   // instruction descriptor
+  uint32_t acc;     // accumulate into D
+};
+
+__host__ __device__ inline GemmLayout gemm_layout(int S, int thS, int nout_pad) {
+  GemmLayout l;
   l.P = ((thS + 15) / 16) * 2;  // 8-mode groups after padding theta_S to a multiple of 16
-  l.nout_pad = nout_pad;
   l.brows = S * nout_pad;
-  l.digits_off = 0;
-  const uint32_t digits = (uint32_t)S * l.P * kHalo * 16;
-  l.b_off = (digits + 1023) & ~1023u;
+  l.stage_bytes = (((uint32_t)S * l.P * kHalo * 16) + 1023) & ~1023u;
+  l.b_off = kStages * l.stage_bytes;
   const uint32_t bbytes = (uint32_t)9 * l.P * l.brows * 16;
-  l.bytes = l.b_off + bbytes;
+  l.bar_off = (l.b_off + bbytes + 63) & ~63u;
+  l.tab_off = l.bar_off + 128;
+  l.bytes = l.tab_off + kMaxMma * (uint32_t)sizeof(MmaEntry);
   return l;
 }
 
-// one work item = 8 consecutive modes (one core-matrix row) of one halo cell
-constexpr int kMaxItems = 3;  // ceil(180 * P / 256) for P <= 4
-
+// ---------------------------------------------------------------------------------------
+// the tensor-core contraction
+// ---------------------------------------------------------------------------------------
 template <int NB, int NOUTP, bool OUTF2>
-__global__ void __launch_bounds__(kThreads, 2) predict_mixed_kernel(
-    const double* __restrict__ Q, const uint4* __restrict__ Bg, const double* __restrict__ rscale,
-    const float* __restrict__ rowmul, int S, int nout, void* __restrict__ Yv, long long ystride_e,
-    long long ystride_c, int* __restrict__ texp, int nx, int ny, int* status) {
+__global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
+    const __grid_constant__ CUtensorMap dmap, const uint4* __restrict__ Bg,
+    const double* __restrict__ rscale, const float* __restrict__ rowmul, int S, int nout,
+    void* __restrict__ Yv, long long ystride_e, long long ystride_c, int* __restrict__ exps,
+    unsigned long long* __restrict__ maxbits, int nx, int ny, int* status) {
   constexpr int THS = NB * NB;
   constexpr int TPAD = ((THS + 15) / 16) * 16;
   constexpr int P = TPAD / 8;
   constexpr int KSTEPS = TPAD / 16;
-  constexpr int NITEMS = kHalo * P;
-  constexpr int IPT = (NITEMS + kThreads - 1) / kThreads;  // items per thread
-  static_assert(IPT <= kMaxItems, "too many halo items per thread");
+  constexpr int CMAX = 256 / NOUTP;  // operator digits per MMA (N <= 256)
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base_sh;
-  __shared__ unsigned long long red[kThreads / 32];
-  const MixedLayout L = mixed_layout(S, THS, NOUTP);
-  unsigned char* digits = smem + L.digits_off;
+  __shared__ int nmma_sh;
+  const GemmLayout L = gemm_layout(S, THS, NOUTP);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
   const int ntiles = ntx * nty;
-  const int ncols = NOUTP * 8 > 256 ? 512 : 256;  // TMEM columns: >= S * NOUTP (S <= 7)
+  const int tcols = S * NOUTP;  // TMEM columns per stage
+  const int tstages = 2 * tcols <= 512 ? 2 : 1;
+  const int ncols = tstages * tcols <= 256 ? 256 : 512;
+  // barriers: full[3] (TMA landed), done[3] (MMAs of a stage complete), empty[2] (TMEM
+  // stage read out by the 256 epilogue threads)
+  const uint32_t bar = smem_u32(smem + L.bar_off);
+  const uint32_t full0 = bar, done0 = bar + 8u * kStages, empty0 = bar + 16u * kStages;
+  const uint32_t box_bytes = (uint32_t)S * P * kHalo * 16;
+  const int sexp = exps[0];  // exponent the digit planes were made with
 
+  if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(full0 + 8u * i, 1);
+      mbar_init(done0 + 8u * i, 1);
+    }
+    for (int i = 0; i < 2; ++i) mbar_init(empty0 + 8u * i, 256);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // the first operand boxes are in flight while the operator digits are loaded
+    for (int i = 0; i < kStages - 1; ++i) {
+      const int tile = blockIdx.x + i * gridDim.x;
+      if (tile < ntiles) {
+        mbar_expect_tx(full0 + 8u * i, box_bytes);
+        tma_load_4d(smem_u32(smem + i * L.stage_bytes), &dmap, 0, (tile % ntx) * kTX,
+                    (tile / ntx) * kTY, 0, full0 + 8u * i);
+      }
+    }
+    if (OUTF2 && blockIdx.x == 0) {
+      // rotate the running maximum: the correction that follows accumulates a fresh one
+      maxbits[0] = maxbits[1];
+      maxbits[1] = 0;
+      exps[1] = sexp;  // exponent of this step's outputs, read by the correction
+    }
+    // the per-tile MMA sequence (offsets relative to a stage)
+    MmaEntry* tab = (MmaEntry*)(smem + L.tab_off);
+    const uint32_t bbase = smem_u32(smem + L.b_off);
+    const uint32_t b_lbo = (uint32_t)L.brows * 16, b_sbo = 128;
+    int n = 0;
+    for (int a = 0; a < S; ++a)
+      for (int r = 0; r < 9; ++r)
+        for (int j = 0; j < KSTEPS; ++j)
+          for (int c0 = 0; c0 < S - a; c0 += CMAX) {
+            const int kc = r * P + 2 * j;
+            const int nn = (min(S - a, c0 + CMAX) - c0) * NOUTP;
+            MmaEntry m;
+            m.bdesc = smem_desc(bbase + (uint32_t)(kc * L.brows + c0 * NOUTP) * 16, b_lbo, b_sbo);
+            m.aoff16 = (uint32_t)((a * P + 2 * j) * kHalo + (r / 3) * kHX + (r % 3));
+            m.dcol = (uint32_t)((a + c0) * NOUTP);
+            m.idesc = idesc_bf16(128, nn);
+            m.acc = (a == 0 && r == 0 && j == 0) ? 0u : 1u;
+            if (n < kMaxMma) tab[n] = m;
+            ++n;
+          }
+    nmma_sh = n;
+  }
   // operator digits -> shared memory (once per CTA)
   {
     uint4* bs = (uint4*)(smem + L.b_off);
     const int nb16 = 9 * P * L.brows;
-    for (int i = tid; i < nb16; i += kThreads) bs[i] = Bg[i];
+    for (int i = tid; i < nb16; i += kGemmThreads) bs[i] = Bg[i];
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -205,184 +334,96 @@ __global__ void __launch_bounds__(kThreads, 2) predict_mixed_kernel(
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
-  const int Lfix = kBits * S;
-  bool ok = true;
-  uint32_t phase = 0;
 
-  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const int tx = tile % ntx, ty = tile / ntx;
-    // 1. halo values of this thread's items (8 modes of one halo cell each), and the max
-    double v[IPT][8];
-    unsigned long long mx = 0;
-#pragma unroll
-    for (int it = 0; it < IPT; ++it) {
-      const int item = tid + it * kThreads;
-      const int h = item % kHalo, p = item / kHalo;
-      int gx = tx * kTX - 1 + h % kHX, gy = ty * kTY - 1 + h / kHX;
-      while (gx < 0) gx += nx;
-      while (gx >= nx) gx -= nx;
-      while (gy < 0) gy += ny;
-      while (gy >= ny) gy -= ny;
-      const double* q = Q + ((long long)gy * nx + gx) * THS + p * 8;
-      if (item < NITEMS) {
-        if (THS % 8 == 0) {
-          const double2* q2 = (const double2*)q;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            double2 t = __ldg(q2 + j);
-            v[it][2 * j] = t.x;
-            v[it][2 * j + 1] = t.y;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) v[it][j] = (p * 8 + j < THS) ? __ldg(q + j) : 0.0;
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[it][j] = 0.0;
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const unsigned long long a =
-            (unsigned long long)__double_as_longlong(v[it][j]) & 0x7FFFFFFFFFFFFFFFULL;
-        mx = a > mx ? a : mx;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
-      mx = t > mx ? t : mx;
-    }
-    if (lane == 0) red[warp] = mx;
-    __syncthreads();
-    mx = red[0];
-#pragma unroll
-    for (int w = 1; w < kThreads / 32; ++w) mx = red[w] > mx ? red[w] : mx;
-    // tile exponent: max|X| < 2^s
-    const int sexp = mx == 0 ? 0 : (int)((mx >> 52) & 0x7FF) - 1022;
-    // 2. fixed point (L = 8 S fraction bits), balanced base-256 digits from its bytes, and
-    //    the digit planes [digit][mode group][halo cell][8 modes] (one 16 B store each)
-#pragma unroll
-    for (int it = 0; it < IPT; ++it) {
-      const int item = tid + it * kThreads;
-      uint32_t packed[7][4];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const long long F = to_fixed(v[it][j], sexp, Lfix);
-        const uint32_t lo32 = (uint32_t)F, hi32 = (uint32_t)((unsigned long long)F >> 32);
-        const int neg = (int)(hi32 >> 31);
-        int carry = 0;
-        int d[7];
-#pragma unroll
-        for (int a = 6; a >= 0; --a) {
-          if (a < S) {
-            const int k = S - 1 - a;  // byte index of digit a
-            const uint32_t byte = (k < 4 ? (lo32 >> (8 * k)) : (hi32 >> (8 * (k - 4)))) & 0xFFu;
-            if (a > 0) {
-              const int t = (int)byte + carry;
-              carry = (t + 128) >> 8;
-              d[a] = t - (carry << 8);
-            } else {
-              d[0] = (int)byte - (neg << 8) + carry;
-            }
-          } else {
-            d[a] = 0;
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < 7; ++a) {
-          // |d| <= 256: exact in FP32 by the 1.5 * 2^23 trick, and its BF16 is the top half
-          const uint32_t b = __float_as_uint(__int_as_float(0x4B400000 + d[a]) - 12582912.0f) >> 16;
-          if (j & 1)
-            packed[a][j / 2] |= b << 16;
-          else
-            packed[a][j / 2] = b;
-        }
-      }
-      if (item < NITEMS) {
-        const int h = item % kHalo, p = item / kHalo;
-#pragma unroll
-        for (int a = 0; a < 7; ++a)
-          if (a < S) {
-            uint4* dst = (uint4*)(digits + ((size_t)(a * P + p) * kHalo + h) * 16);
-            *dst = make_uint4(packed[a][0], packed[a][1], packed[a][2], packed[a][3]);
-          }
-      }
-    }
-    if (OUTF2 && tid == 0) texp[tile] = sexp;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    // 3./4. MMAs, issued by one thread
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t dbase = smem_u32(digits), bbase = smem_u32(smem + L.b_off);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer: TMA + MMA ----------------
+      const int nmma = nmma_sh;
+      const MmaEntry* tab = (const MmaEntry*)(smem + L.tab_off);
+      bool ok = nmma <= kMaxMma;
       const uint32_t a_lbo = kHalo * 16, a_sbo = kHX * 16;
-      const uint32_t b_lbo = (uint32_t)L.brows * 16, b_sbo = 128;
-      constexpr int CMAX = 256 / NOUTP;
-      for (int a = 0; a < S; ++a) {
-        for (int r = 0; r < 9; ++r) {
-          const int ox = r % 3, oy = r / 3;  // halo shift (offset + 1)
-          for (int j = 0; j < KSTEPS; ++j) {
-            const uint32_t a_addr = dbase + (uint32_t)(((a * P + 2 * j) * kHalo + oy * kHX + ox) * 16);
-            const uint64_t ad = smem_desc(a_addr, a_lbo, a_sbo);
-            const int kc = r * P + 2 * j;  // k-chunk of the operator
-            for (int c0 = 0; c0 < S - a; c0 += CMAX) {
-              const int c1 = min(S - a, c0 + CMAX);
-              const int n = (c1 - c0) * NOUTP;
-              const uint32_t b_addr = bbase + (uint32_t)(kc * L.brows + c0 * NOUTP) * 16;
-              const uint64_t bd = smem_desc(b_addr, b_lbo, b_sbo);
-              const uint32_t acc = (a == 0 && r == 0 && j == 0) ? 0u : 1u;
-              mma_bf16(tmem + (uint32_t)((a + c0) * NOUTP), ad, bd, idesc_bf16(128, n), acc);
-            }
-          }
+      int k = 0;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++k) {
+        const int st = k % kStages, ts = k % tstages;
+        if (!mbar_wait(full0 + 8u * st, (k / kStages) & 1)) { ok = false; break; }
+        if (k >= tstages && !mbar_wait(empty0 + 8u * ts, ((k - tstages) / tstages) & 1)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t abase = smem_desc(smem_u32(smem + st * L.stage_bytes), a_lbo, a_sbo);
+        const uint32_t tst = tmem + (uint32_t)(ts * tcols);
+        for (int i = 0; i < nmma; ++i) {
+          const MmaEntry m = tab[i];
+          mma_bf16(tst + m.dcol, abase + m.aoff16, m.bdesc, m.idesc, m.acc);
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                done0 + 8u * st)
+            : "memory");
+        // keep kStages - 1 boxes in flight: refill the stage the previous tile used
+        const int nxt = tile + (kStages - 1) * gridDim.x;
+        if (nxt < ntiles) {
+          const int s2 = (k + kStages - 1) % kStages;
+          if (k >= 1 && !mbar_wait(done0 + 8u * s2, ((k - 1) / kStages) & 1)) { ok = false; break; }
+          mbar_expect_tx(full0 + 8u * s2, box_bytes);
+          tma_load_4d(smem_u32(smem + s2 * L.stage_bytes), &dmap, 0, (nxt % ntx) * kTX,
+                      (nxt / ntx) * kTY, 0, full0 + 8u * s2);
         }
       }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&mbar))
-          : "memory");
+      if (!ok) atomicOr(status, kStatusTimeout);
     }
-    // 5. epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its 32 cells) and half of the
-    //    columns of every block
-    if (!mbar_wait(smem_u32(&mbar), phase)) {
-      ok = false;
-      if (tid == 0) atomicOr(status, 2);
-      mbar_wait(smem_u32(&mbar), phase);  // one more bounded wait before releasing TMEM
-      break;
-    }
-    phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    {
-      const int quad = warp & 3, half = warp >> 2;
-      const int cell = quad * 32 + lane;
-      const int ix = cell % kTX, iy = cell / kTX;
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: warps 1..8, two per TMEM lane quadrant ----------------
+    const int quad = warp & 3;                 // lanes 32 quad .. this warp may read
+    const int part = (warp - 1) >> 2;          // which half of the output columns
+    const int cell = quad * 32 + lane;
+    const int ix = cell % kTX, iy = cell / kTX;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
+    int k = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+      const int st = k % kStages, ts = k % tstages;
+      if (!mbar_wait_sleep(done0 + 8u * st, (k / kStages) & 1)) {
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int tx = tile % ntx, ty = tile / ntx;
       const int gx = tx * kTX + ix, gy = ty * kTY + iy;
-      const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
       const long long e = (long long)gy * nx + gx;
+      const uint32_t tbase = lane_addr + (uint32_t)(ts * tcols);
 #pragma unroll 1
-      for (int cb = half * (NOUTP / 2); cb < (half + 1) * (NOUTP / 2); cb += 16) {
-        float hi[16], lo[16], vv[16];
-        tmem_ld16(lane_addr + (uint32_t)cb, hi);
+      for (int cb = part * (NOUTP / 2); cb < (part + 1) * (NOUTP / 2); cb += 8) {
+        if (cb >= nout) break;
+        uint32_t raw[7][8];  // every diagonal block of these 8 columns, one wait
 #pragma unroll
-        for (int c = 0; c < 16; ++c) lo[c] = 0.f;
+        for (int t = 0; t < 7; ++t)
+          if (t < S) tmem_ld8_nowait(tbase + (uint32_t)(t * NOUTP + cb), raw[t]);
+        tmem_wait_ld();
+        float hi[8], lo[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          hi[c] = __uint_as_float(raw[0][c]);
+          lo[c] = 0.f;
+        }
         float w = 1.f;
-        for (int t = 1; t < S; ++t) {
-          w *= 1.f / 256.f;
-          tmem_ld16(lane_addr + (uint32_t)(t * NOUTP + cb), vv);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            float s2, e2;
-            two_sum(hi[c], vv[c] * w, s2, e2);
-            hi[c] = s2;
-            lo[c] += e2;
+        for (int t = 1; t < 7; ++t) {
+          if (t < S) {
+            w *= 1.f / 256.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              float s2, e2;
+              two_sum(hi[c], __uint_as_float(raw[t][c]) * w, s2, e2);
+              hi[c] = s2;
+              lo[c] += e2;
+            }
           }
         }
         if (gx < nx && gy < ny) {
@@ -390,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 2) predict_mixed_kernel(
             // (hi, lo) scaled to the common row exponent; value = (hi + lo) 2^(s + gmax - 16)
             float2* y = (float2*)Yv + e * ystride_e + (long long)cb * ystride_c;
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
+            for (int c = 0; c < 8; ++c)
               if (cb + c < nout) {
                 const float m = rowmul[cb + c];
                 y[c * ystride_c] = make_float2(hi[c] * m, lo[c] * m);
@@ -399,15 +440,21 @@ __global__ void __launch_bounds__(kThreads, 2) predict_mixed_kernel(
             double* y = (double*)Yv + e * ystride_e + (long long)cb * ystride_c;
             const double tscale = __longlong_as_double((long long)(sexp + 1023) << 52);
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
+            for (int c = 0; c < 8; ++c)
               if (cb + c < nout)
                 y[c * ystride_c] = ((double)hi[c] + (double)lo[c]) * (tscale * rscale[cb + c]);
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(empty0 + 8u * ts);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+  }
+  // drain: make sure no MMA is still writing TMEM before it is released (bounded)
+  if (tid == 0) {
+    int k_last = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) ++k_last;
+    if (k_last > 0) mbar_wait(done0 + 8u * ((k_last - 1) % kStages), ((k_last - 1) / kStages) & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -416,15 +463,101 @@ __global__ void __launch_bounds__(kThreads, 2) predict_mixed_kernel(
 }
 
 // ---------------------------------------------------------------------------------------
+// digit planes of the state (ghost-padded): plane (a * P + p), row (y + 1), column (x + 1)
+// ---------------------------------------------------------------------------------------
+template <int NB, int S>
+__device__ __forceinline__ bool write_cell_digits(const double* q, int ix, int iy, int nx, int ny,
+                                                  int s, uint4* __restrict__ planes) {
+  constexpr int THS = NB * NB;
+  constexpr int P = ((THS + 15) / 16) * 2;
+  const long long plane = (long long)(nx + 2) * (ny + 2);
+  // padded positions holding this cell: itself and its periodic ghost copies
+  int px[2] = {ix + 1, -1}, py[2] = {iy + 1, -1};
+  if (ix == 0) px[1] = nx + 1;
+  if (ix == nx - 1) px[1] = 0;
+  if (iy == 0) py[1] = ny + 1;
+  if (iy == ny - 1) py[1] = 0;
+  bool fits = true;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = (p * 8 + j < THS) ? q[p * 8 + j] : 0.0;
+    uint4 rows[S];
+    fits &= make_digit_rows<S>(v, s, rows);
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+      uint4* base = planes + (long long)(a * P + p) * plane;
+#pragma unroll
+      for (int yi = 0; yi < 2; ++yi) {
+        if (py[yi] < 0) continue;
+#pragma unroll
+        for (int xi = 0; xi < 2; ++xi) {
+          if (px[xi] < 0) continue;
+          base[(long long)py[yi] * (nx + 2) + px[xi]] = rows[a];
+        }
+      }
+    }
+  }
+  return fits;
+}
+
+__device__ __forceinline__ unsigned long long block_max_bits(unsigned long long v,
+                                                             unsigned long long* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t > v ? t : v;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long r = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = sh[w] > r ? sh[w] : r;
+  return r;
+}
+
+// max |q| of the state -> maxbits[1]
+__global__ void state_max_kernel(const double* __restrict__ q, long long count,
+                                 unsigned long long* maxbits) {
+  __shared__ unsigned long long sh[8];
+  unsigned long long m = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(q[i]) & 0x7FFFFFFFFFFFFFFFULL;
+    m = a > m ? a : m;
+  }
+  m = block_max_bits(m, sh);
+  if (threadIdx.x == 0) atomicMax(maxbits + 1, m);
+}
+
+// digit planes of the current state from maxbits[1]; exps[0] = their exponent
+template <int NB, int S>
+__global__ void state_digits_kernel(const double* __restrict__ Q, int nx, int ny,
+                                    const unsigned long long* maxbits, int* exps,
+                                    uint4* __restrict__ planes, int* status) {
+  constexpr int THS = NB * NB;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = exponent_above(maxbits[1]) + 1;
+  if (e == 0) exps[0] = s;
+  if (e >= (long long)nx * ny) return;
+  double q[THS];
+#pragma unroll
+  for (int i = 0; i < THS; ++i) q[i] = Q[e * THS + i];
+  if (!write_cell_digits<NB, S>(q, (int)(e % nx), (int)(e / nx), nx, ny, s, planes))
+    atomicOr(status, kStatusRange);
+}
+
+// ---------------------------------------------------------------------------------------
 // correction from the fused outputs.  Y holds, output-major, [V (theta_S) | u_x (NB) | u_y
-// (NB)] per cell as double-float pairs (hi, lo) whose value is (hi + lo) 2^(texp + gmax - 16)
-// with texp the exponent of the cell's tile: V = sum_d nu_d (D along d) Wbar, and u_d =
-// nu_d trace(Wbar) on the upwind side of dim d (trace at +1 when a_d > 0, at -1 when
+// (NB)] per cell as double-float pairs (hi, lo) whose value is (hi + lo) 2^(s + gmax - 16)
+// with s the exponent of this step's digit planes: V = sum_d nu_d (D along d) Wbar and u_d
+// = nu_d trace(Wbar) on the upwind side of dim d (trace at +1 when a_d > 0, at -1 when
 // a_d < 0).  The face value at i+1/2 in dim d is u_d of the upwind cell -- one stored pair
 // per face, applied with opposite signs to both neighbours.  With phi_a(-1) = (-1)^a
 // phi_a(+1) the update of mode (a, t) along d is phi_a(+1) (-F_{i+1/2} + (-1)^a F_{i-1/2}).
-// The sums run in double-float FP32 after aligning every pair to the largest exponent
-// involved (power-of-two scaling, exact); only the final state update is FP64.
+// The sums run in double-float FP32; the final state update is FP64.  The kernel then
+// writes the new state's digit planes (exponent from the previous maximum plus one bit of
+// headroom, checked) and accumulates the new maximum.
 // ---------------------------------------------------------------------------------------
 struct DF {
   float h, l;
@@ -450,13 +583,6 @@ __device__ __forceinline__ DF df_mul_const(float ch, float cl, DF a) {
   return DF{s, __fsub_rn(e, __fsub_rn(s, p))};
 }
 
-__device__ __forceinline__ DF df_scale(DF a, float m) { return DF{a.h * m, a.l * m}; }
-
-// exact power of two 2^k as a float for k in [-126, 127]; 0 below
-__device__ __forceinline__ float pow2f(int k) {
-  return k < -126 ? 0.f : __uint_as_float((uint32_t)(k + 127) << 23);
-}
-
 // float * 2^k as a double, by exponent arithmetic on the bits (exact; 0 stays 0)
 __device__ __forceinline__ double f2d_scaled(float f, int k) {
   const uint32_t b = __float_as_uint(f);
@@ -469,65 +595,53 @@ __device__ __forceinline__ double f2d_scaled(float f, int k) {
   return __hiloint2double((int)hiw, (int)low);
 }
 
-template <int NB>
-__global__ void __launch_bounds__(128) correct_fused_kernel(double* __restrict__ Q,
-                                                            const float2* __restrict__ Y,
-                                                            const int* __restrict__ texp,
-                                                            int nx, int ny, CorrParams cp,
-                                                            int gmax, int sgnx, int sgny) {
+template <int NB, int S>
+__global__ void __launch_bounds__(128) mixed_correct_kernel(
+    double* __restrict__ Q, const float2* __restrict__ Y, int nx, int ny, CorrParams cp, int gmax,
+    int sgnx, int sgny, int* __restrict__ exps, unsigned long long* __restrict__ maxbits,
+    uint4* __restrict__ planes, int* status) {
   constexpr int THS = NB * NB;
   constexpr int PITCH = THS + 1;  // odd pitch: conflict-free row access
   __shared__ double sq[128 * PITCH];
+  __shared__ unsigned long long shmax[4];
   const long long ncell = (long long)nx * ny;
   const long long e0 = (long long)blockIdx.x * 128;
   const int nblk = (int)min((long long)128, ncell - e0);
-  const int ntx = (nx + kTX - 1) / kTX;
+  const int ys = exps[1];                                  // exponent of Y
+  const int snext = exponent_above(maxbits[0]) + 1;        // exponent for the new digits
   // coalesced load of the block's state rows
   for (int i = threadIdx.x; i < nblk * THS; i += 128) sq[(i / THS) * PITCH + i % THS] = Q[e0 * THS + i];
   __syncthreads();
   const long long e = e0 + threadIdx.x;
+  unsigned long long mymax = 0;
+  bool fits = true;
   if (threadIdx.x < nblk) {
     const int ix = (int)(e % nx), iy = (int)(e / nx);
-    // the cells whose stored values enter: own, and per dim the upwind cells of both faces
-    long long jr[2], jl[2];
-    int kr[2], kl[2];
-    const int kown = texp[(ix / kTX) + (iy / kTY) * ntx];
-    int kmax = kown;
-#pragma unroll
-    for (int dd = 0; dd < 2; ++dd) {
-      const int sg = dd == 0 ? sgnx : sgny;
-      int rx = ix, ry = iy, lx = ix, ly = iy;
-      if (dd == 0) {
-        if (sg > 0) lx = ix == 0 ? nx - 1 : ix - 1; else rx = ix + 1 == nx ? 0 : ix + 1;
-      } else {
-        if (sg > 0) ly = iy == 0 ? ny - 1 : iy - 1; else ry = iy + 1 == ny ? 0 : iy + 1;
-      }
-      jr[dd] = (long long)ry * nx + rx;
-      jl[dd] = (long long)ly * nx + lx;
-      kr[dd] = texp[(rx / kTX) + (ry / kTY) * ntx];
-      kl[dd] = texp[(lx / kTX) + (ly / kTY) * ntx];
-      if (sg != 0) kmax = max(kmax, max(kr[dd], kl[dd]));
-    }
     DF dq[THS];
-    const float mown = pow2f(kown - kmax);
 #pragma unroll
     for (int s = 0; s < THS; ++s) {
       const float2 y = Y[s * ncell + e];  // volume term V
-      dq[s] = df_scale(DF{y.x, y.y}, mown);
+      dq[s] = DF{y.x, y.y};
     }
 #pragma unroll
     for (int dd = 0; dd < 2; ++dd) {
       const int sg = dd == 0 ? sgnx : sgny;
       if (sg == 0) continue;
       const int st = dd == 0 ? 1 : NB;
-      const float mr = pow2f(kr[dd] - kmax), ml = pow2f(kl[dd] - kmax);
+      int rx = ix, ry = iy, lx = ix, ly = iy;
+      if (dd == 0) {
+        if (sg > 0) lx = ix == 0 ? nx - 1 : ix - 1; else rx = ix + 1 == nx ? 0 : ix + 1;
+      } else {
+        if (sg > 0) ly = iy == 0 ? ny - 1 : iy - 1; else ry = iy + 1 == ny ? 0 : iy + 1;
+      }
+      const long long jr = (long long)ry * nx + rx, jl = (long long)ly * nx + lx;
       const float2* u = Y + (long long)(THS + dd * NB) * ncell;
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
-        const float2 a = u[t * ncell + jr[dd]], b = u[t * ncell + jl[dd]];
-        const DF fr = df_scale(DF{a.x, a.y}, mr), fl = df_scale(DF{b.x, b.y}, ml);
-        const DF w_even = df_add(fl, df_neg(fr));          // -F(i+1/2) + F(i-1/2)
-        const DF w_odd = df_neg(df_add(fl, fr));           // -F(i+1/2) - F(i-1/2)
+        const float2 a = u[t * ncell + jr], b = u[t * ncell + jl];
+        const DF fr = DF{a.x, a.y}, fl = DF{b.x, b.y};
+        const DF w_even = df_add(fl, df_neg(fr));  // -F(i+1/2) + F(i-1/2)
+        const DF w_odd = df_neg(df_add(fl, fr));   // -F(i+1/2) - F(i-1/2)
         const int base = dd == 0 ? t * NB : t;
 #pragma unroll
         for (int a2 = 0; a2 < NB; ++a2) {
@@ -537,7 +651,8 @@ __global__ void __launch_bounds__(128) correct_fused_kernel(double* __restrict__
         }
       }
     }
-    const int kfin = kmax + gmax - 16;
+    const int kfin = ys + gmax - 16;
+    double qn[THS];
     double* q = sq + threadIdx.x * PITCH;
 #pragma unroll
     for (int s = 0; s < THS; ++s) {
@@ -545,7 +660,17 @@ __global__ void __launch_bounds__(128) correct_fused_kernel(double* __restrict__
       v = v + f2d_scaled(dq[s].h, kfin);
       v = v + f2d_scaled(dq[s].l, kfin);
       q[s] = v;
+      qn[s] = v;
+      const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+      mymax = a > mymax ? a : mymax;
     }
+    fits = write_cell_digits<NB, S>(qn, ix, iy, nx, ny, snext, planes);
+  }
+  if (!fits) atomicOr(status, kStatusRange);
+  const unsigned long long bm = block_max_bits(mymax, shmax);
+  if (threadIdx.x == 0) {
+    atomicMax(maxbits + 1, bm);
+    if (blockIdx.x == 0) exps[0] = snext;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nblk * THS; i += 128) Q[e0 * THS + i] = sq[(i / THS) * PITCH + i % THS];
@@ -557,7 +682,7 @@ __global__ void __launch_bounds__(128) correct_fused_kernel(double* __restrict__
 // host side
 // ------------------------------------------------------------------------------------------
 bool mixed_supported(int dim, int nb, int nout) {
-  return dim == 2 && nb >= 2 && nb <= 5 && nout <= 64;
+  return dim == 2 && nb >= 2 && nb <= 4 && nout <= 64;
 }
 
 static int nout_pad_of(int nout) { return nout <= 32 ? 32 : 64; }
@@ -570,7 +695,7 @@ int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int sli
   if ((int)G.size() < nout * K) return RIDG_EINVAL;
   const int NOUTP = nout_pad_of(nout);
   if (slices * NOUTP > 512) return RIDG_EINVAL;
-  const MixedLayout L = mixed_layout(slices, thS, NOUTP);
+  const GemmLayout L = gemm_layout(slices, thS, NOUTP);
   const int tpad = L.P * 8;
   // digits in the shared-memory layout [k-chunk][row = c' * NOUTP + c][8]
   digits.assign((size_t)9 * L.P * L.brows * 8, 0);
@@ -581,9 +706,7 @@ int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int sli
     double mx = 0.0;
     for (int k = 0; k < K; ++k) mx = std::max(mx, std::fabs(G[(size_t)c * K + k]));
     int g = 0;
-    if (mx > 0) {
-      std::frexp(mx, &g);  // mx < 2^g
-    }
+    if (mx > 0) std::frexp(mx, &g);  // mx < 2^g
     rscale[c] = std::ldexp(1.0, g - 2 * kBits);
     gexp[c] = mx > 0 ? g : -100000;
     for (int k = 0; k < K; ++k) {
@@ -606,7 +729,8 @@ int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int sli
   for (int c = 0; c < nout; ++c) gmax = std::max(gmax, gexp[c]);
   if (gmax == -100000) gmax = 0;
   for (int c = 0; c < nout; ++c)
-    rowmul[c] = gexp[c] == -100000 ? 0.0f : (gexp[c] - gmax < -126 ? 0.0f : std::ldexp(1.0f, gexp[c] - gmax));
+    rowmul[c] = gexp[c] == -100000 ? 0.0f
+                                   : (gexp[c] - gmax < -126 ? 0.0f : std::ldexp(1.0f, gexp[c] - gmax));
   op.gmax = gmax;
   op.nout = nout;
   op.npad = NOUTP;
@@ -617,76 +741,134 @@ int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int sli
   return RIDG_OK;
 }
 
+size_t mixed_plane_bytes(const Grid& g, int nb, int slices) {
+  const int thS = nb * nb, P = ((thS + 15) / 16) * 2;
+  return (size_t)(g.n[0] + 2) * (g.n[1] + 2) * slices * P * 16;
+}
+
+int mixed_make_map(const Grid& g, int nb, int slices, void* planes, void* map_out) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return RIDG_ECUDA;
+  const int thS = nb * nb, P = ((thS + 15) / 16) * 2;
+  // dims (fastest first): 8 modes (BF16), padded x, padded y, digit x mode group
+  cuuint64_t dims[4] = {8, (cuuint64_t)(g.n[0] + 2), (cuuint64_t)(g.n[1] + 2),
+                        (cuuint64_t)slices * P};
+  cuuint64_t strides[3] = {16, (cuuint64_t)(g.n[0] + 2) * 16,
+                           (cuuint64_t)(g.n[0] + 2) * (g.n[1] + 2) * 16};
+  cuuint32_t box[4] = {8, (cuuint32_t)kHX, (cuuint32_t)kHY, (cuuint32_t)(slices * P)};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = ((EncodeFn)fn)((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, planes,
+                              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RIDG_OK : RIDG_ECUDA;
+}
+
 template <int NB, int NOUTP, bool OUTF2>
-static cudaError_t launch_mixed_t(const Grid& g, const double* Q, const MixedOp& op, void* Y,
-                                  long long ys_e, long long ys_c, int* texp, int* status,
-                                  cudaStream_t s) {
-  const MixedLayout L = mixed_layout(op.slices, NB * NB, NOUTP);
-  auto kern = predict_mixed_kernel<NB, NOUTP, OUTF2>;
+static cudaError_t launch_gemm_t(const Grid& g, const void* map, const MixedOp& op, void* Y,
+                                 long long ys_e, long long ys_c, MixedState& ms, cudaStream_t s) {
+  const GemmLayout L = gemm_layout(op.slices, NB * NB, NOUTP);
+  auto kern = mixed_gemm_kernel<NB, NOUTP, OUTF2>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int ntiles = ((g.n[0] + kTX - 1) / kTX) * ((g.n[1] + kTY - 1) / kTY);
-  const int per_sm = (2 * ((size_t)L.bytes + 2048) <= 233472 && NOUTP <= 32) ? 2 : 1;
-  const int grid = std::min(ntiles, sms * per_sm);
-  kern<<<grid, kThreads, L.bytes, s>>>(Q, (const uint4*)op.b_slices, op.row_scale, op.row_mul,
-                                       op.slices, op.nout, Y, ys_e, ys_c, texp, g.n[0], g.n[1],
-                                       status);
+  const int grid = std::min(ntiles, sms);
+  kern<<<grid, kGemmThreads, L.bytes, s>>>(*(const CUtensorMap*)map, (const uint4*)op.b_slices,
+                                           op.row_scale, op.row_mul, op.slices, op.nout, Y, ys_e,
+                                           ys_c, ms.exps, ms.maxbits, g.n[0], g.n[1], ms.status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_predict_mixed(const Grid& g, int nb, const double* Q, const MixedOp& op,
-                                 double* Y, long long ys_e, long long ys_c, int* status,
-                                 cudaStream_t s) {
+cudaError_t launch_mixed_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
+                              long long ys_e, long long ys_c, bool fused, cudaStream_t s) {
   if (g.dim != 2) return cudaErrorInvalidValue;
-#define RIDG_MIXED_CASE(NBV, NP) \
-  case NBV: return launch_mixed_t<NBV, NP, false>(g, Q, op, Y, ys_e, ys_c, nullptr, status, s);
-  if (op.npad == 32) {
-    switch (nb) { RIDG_MIXED_CASE(2, 32) RIDG_MIXED_CASE(3, 32) RIDG_MIXED_CASE(4, 32) RIDG_MIXED_CASE(5, 32) }
-  } else if (op.npad == 64) {
-    switch (nb) { RIDG_MIXED_CASE(2, 64) RIDG_MIXED_CASE(3, 64) RIDG_MIXED_CASE(4, 64) RIDG_MIXED_CASE(5, 64) }
-  }
-#undef RIDG_MIXED_CASE
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_predict_fused(const Grid& g, int nb, const double* Q, const MixedOp& op,
-                                 void* Y2, int* texp, int* status, cudaStream_t s) {
-  if (g.dim != 2) return cudaErrorInvalidValue;
-#define RIDG_MIXED_CASE(NBV, NP) \
-  case NBV: return launch_mixed_t<NBV, NP, true>(g, Q, op, Y2, 1, g.ncell, texp, status, s);
-  if (op.npad == 32) {
-    switch (nb) { RIDG_MIXED_CASE(2, 32) RIDG_MIXED_CASE(3, 32) RIDG_MIXED_CASE(4, 32) }
-  } else if (op.npad == 64) {
-    switch (nb) { RIDG_MIXED_CASE(5, 64) }
-  }
-#undef RIDG_MIXED_CASE
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_correct_fused(const Grid& g, int nb, double* Q, const void* Y2,
-                                 const int* texp, int gmax, const CorrParams& cp, int sgnx,
-                                 int sgny, cudaStream_t s) {
-  if (g.dim != 2) return cudaErrorInvalidValue;
-  const unsigned blocks = (unsigned)((g.ncell + 127) / 128);
-  const float2* Y = (const float2*)Y2;
-#define RIDG_CORR_CASE(NBV)                                                                  \
+#define RIDG_GEMM_CASE(NBV, NP)                                                              \
   case NBV:                                                                                   \
-    correct_fused_kernel<NBV><<<blocks, 128, 0, s>>>(Q, Y, texp, g.n[0], g.n[1], cp, gmax,    \
-                                                     sgnx, sgny);                             \
-    break;
-  switch (nb) {
-    RIDG_CORR_CASE(2) RIDG_CORR_CASE(3) RIDG_CORR_CASE(4) RIDG_CORR_CASE(5)
-    default: return cudaErrorInvalidValue;
+    return fused ? launch_gemm_t<NBV, NP, true>(g, ms.map, op, Y, ys_e, ys_c, ms, s)          \
+                 : launch_gemm_t<NBV, NP, false>(g, ms.map, op, Y, ys_e, ys_c, ms, s);
+  if (op.npad == 32) {
+    switch (nb) { RIDG_GEMM_CASE(2, 32) RIDG_GEMM_CASE(3, 32) RIDG_GEMM_CASE(4, 32) }
+  } else if (op.npad == 64) {
+    switch (nb) { RIDG_GEMM_CASE(2, 64) RIDG_GEMM_CASE(3, 64) RIDG_GEMM_CASE(4, 64) RIDG_GEMM_CASE(5, 64) }
   }
-#undef RIDG_CORR_CASE
+#undef RIDG_GEMM_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <int NB, int S>
+static cudaError_t launch_refresh_t(const Grid& g, const double* Q, MixedState& ms, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ms.maxbits, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  state_max_kernel<<<256, 256, 0, s>>>(Q, g.ncell * NB * NB, ms.maxbits);
+  const unsigned blocks = (unsigned)((g.ncell + 127) / 128);
+  state_digits_kernel<NB, S><<<blocks, 128, 0, s>>>(Q, g.n[0], g.n[1], ms.maxbits, ms.exps,
+                                                    (uint4*)ms.planes, ms.status);
   return cudaGetLastError();
 }
 
-size_t mixed_smem_bytes(int nb, const MixedOp& op) {
-  return mixed_layout(op.slices, nb * nb, op.npad).bytes;
+template <int NB, int S>
+static cudaError_t launch_correct_t(const Grid& g, double* Q, const void* Y, int gmax,
+                                    const CorrParams& cp, int sgnx, int sgny, MixedState& ms,
+                                    cudaStream_t s) {
+  const unsigned blocks = (unsigned)((g.ncell + 127) / 128);
+  mixed_correct_kernel<NB, S><<<blocks, 128, 0, s>>>(Q, (const float2*)Y, g.n[0], g.n[1], cp, gmax,
+                                                     sgnx, sgny, ms.exps, ms.maxbits,
+                                                     (uint4*)ms.planes, ms.status);
+  return cudaGetLastError();
+}
+
+#define RIDG_NB_S_SWITCH(FN, ...)                                                             \
+  switch (nb * 16 + slices) {                                                                 \
+    case 2 * 16 + 2: return FN<2, 2>(__VA_ARGS__);                                            \
+    case 2 * 16 + 3: return FN<2, 3>(__VA_ARGS__);                                            \
+    case 2 * 16 + 4: return FN<2, 4>(__VA_ARGS__);                                            \
+    case 2 * 16 + 5: return FN<2, 5>(__VA_ARGS__);                                            \
+    case 2 * 16 + 6: return FN<2, 6>(__VA_ARGS__);                                            \
+    case 2 * 16 + 7: return FN<2, 7>(__VA_ARGS__);                                            \
+    case 3 * 16 + 2: return FN<3, 2>(__VA_ARGS__);                                            \
+    case 3 * 16 + 3: return FN<3, 3>(__VA_ARGS__);                                            \
+    case 3 * 16 + 4: return FN<3, 4>(__VA_ARGS__);                                            \
+    case 3 * 16 + 5: return FN<3, 5>(__VA_ARGS__);                                            \
+    case 3 * 16 + 6: return FN<3, 6>(__VA_ARGS__);                                            \
+    case 3 * 16 + 7: return FN<3, 7>(__VA_ARGS__);                                            \
+    case 4 * 16 + 2: return FN<4, 2>(__VA_ARGS__);                                            \
+    case 4 * 16 + 3: return FN<4, 3>(__VA_ARGS__);                                            \
+    case 4 * 16 + 4: return FN<4, 4>(__VA_ARGS__);                                            \
+    case 4 * 16 + 5: return FN<4, 5>(__VA_ARGS__);                                            \
+    case 4 * 16 + 6: return FN<4, 6>(__VA_ARGS__);                                            \
+    case 4 * 16 + 7: return FN<4, 7>(__VA_ARGS__);                                            \
+    case 5 * 16 + 2: return FN<5, 2>(__VA_ARGS__);                                            \
+    case 5 * 16 + 3: return FN<5, 3>(__VA_ARGS__);                                            \
+    case 5 * 16 + 4: return FN<5, 4>(__VA_ARGS__);                                            \
+    case 5 * 16 + 5: return FN<5, 5>(__VA_ARGS__);                                            \
+    case 5 * 16 + 6: return FN<5, 6>(__VA_ARGS__);                                            \
+    case 5 * 16 + 7: return FN<5, 7>(__VA_ARGS__);                                            \
+    default: break;                                                                           \
+  }
+
+cudaError_t launch_mixed_refresh(const Grid& g, int nb, int slices, const double* Q,
+                                 MixedState& ms, cudaStream_t s) {
+  if (g.dim != 2) return cudaErrorInvalidValue;
+  RIDG_NB_S_SWITCH(launch_refresh_t, g, Q, ms, s)
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_mixed_correct(const Grid& g, int nb, int slices, double* Q, const void* Y,
+                                 int gmax, const CorrParams& cp, int sgnx, int sgny,
+                                 MixedState& ms, cudaStream_t s) {
+  if (g.dim != 2) return cudaErrorInvalidValue;
+  RIDG_NB_S_SWITCH(launch_correct_t, g, Q, Y, gmax, cp, sgnx, sgny, ms, s)
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace ridg

@@ -42,23 +42,33 @@ struct MixedOp {
   double* row_scale = nullptr;  // device, 2^(g_c - 16) per row
   float* row_mul = nullptr;     // device, 2^(g_c - gmax) per row
 };
+// Device-side state of the mixed path: the ghost-padded BF16 digit planes of the current
+// state, the TMA descriptor over them, and the exponent / maximum bookkeeping.
+struct MixedState {
+  void* planes = nullptr;                 // [digit x mode group][y + 2][x + 2][8] bf16
+  alignas(64) unsigned char map[128];     // CUtensorMap over the planes
+  int* exps = nullptr;                    // [0] exponent of the planes, [1] of the outputs
+  unsigned long long* maxbits = nullptr;  // [0] max |Q| of the current state, [1] accumulator
+  int* status = nullptr;                  // shared status word
+  bool valid = false;                     // planes describe the current state
+};
 bool mixed_supported(int dim, int nb, int nout);
 int mixed_build(int dim, int nb, const std::vector<double>& P, int nout, int slices,
                 std::vector<unsigned short>& digits, std::vector<double>& rscale,
                 std::vector<float>& rowmul, MixedOp& op);
-// output c of cell e goes to W[e * ys_e + c * ys_c]
-cudaError_t launch_predict_mixed(const Grid& g, int nb, const double* Q, const MixedOp& op,
-                                 double* W, long long ys_e, long long ys_c, int* status,
-                                 cudaStream_t s);
-// fused step operator outputs [V | u_x | u_y] as output-major double-float pairs plus one
-// exponent per 8 x 16 tile
-cudaError_t launch_predict_fused(const Grid& g, int nb, const double* Q, const MixedOp& op,
-                                 void* Y2, int* texp, int* status, cudaStream_t s);
-// Q[e] += correction from those outputs; sgn = sign of a_d
-cudaError_t launch_correct_fused(const Grid& g, int nb, double* Q, const void* Y2,
-                                 const int* texp, int gmax, const CorrParams& cp, int sgnx,
-                                 int sgny, cudaStream_t s);
-size_t mixed_smem_bytes(int nb, const MixedOp& op);
+size_t mixed_plane_bytes(const Grid& g, int nb, int slices);
+int mixed_make_map(const Grid& g, int nb, int slices, void* planes, void* map_out);
+// Y[e * ys_e + c * ys_c] = (G X_e)[c]: FP64 (fused == false) or, for the fused step
+// operator, double-float pairs output-major with the exponent in exps[1]
+cudaError_t launch_mixed_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
+                              long long ys_e, long long ys_c, bool fused, cudaStream_t s);
+// max |Q| and the digit planes of Q (after the state changed outside the mixed step)
+cudaError_t launch_mixed_refresh(const Grid& g, int nb, int slices, const double* Q,
+                                 MixedState& ms, cudaStream_t s);
+// the correction from the fused outputs, plus the new state's planes and maximum
+cudaError_t launch_mixed_correct(const Grid& g, int nb, int slices, double* Q, const void* Y,
+                                 int gmax, const CorrParams& cp, int sgnx, int sgny,
+                                 MixedState& ms, cudaStream_t s);
 
 // ---- diagnostics (k_diag.cu) ----
 // partial sums (per block) of q[e, r, 0], r < m  -> out[block * m + r]
@@ -99,7 +109,7 @@ struct ridg_handle {
   ridg::MixedOp mixed;       // fused step operator [V; u_x; u_y] P-bar (2D)
   ridg::MixedOp mixed_pred;  // full prediction operator P
   double* Y = nullptr;       // fused outputs of the mixed step (cells * nout pairs)
-  int* texp = nullptr;       // per-tile exponents of the fused outputs
+  ridg::MixedState ms;       // digit planes and exponent bookkeeping of the mixed path
   int ny_out = 0;
   // host copy of the operator
   std::vector<double> P_host;
