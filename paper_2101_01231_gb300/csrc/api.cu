@@ -155,7 +155,9 @@ int rebuild_linear(ridg_t* h) {
         return set_err(h, RIDG_ENOMEM, "mixed-path allocation failed");
       RIDG_CUDA(h, cudaMemsetAsync(h->ms.planes, 0, ridg::mixed_plane_bytes(g, h->nb, h->opt.slices),
                                    h->stream));
-      if (ridg::mixed_make_map(g, h->nb, h->opt.slices, h->ms.planes, h->ms.map) != RIDG_OK)
+      if (ridg::mixed_make_map(g, h->nb, h->opt.slices, nout, h->ms.planes, h->ms.map) != RIDG_OK ||
+          ridg::mixed_make_map(g, h->nb, h->opt.slices, h->thT, h->ms.planes, h->ms.map_pred) !=
+              RIDG_OK)
         return set_err(h, RIDG_ECUDA, "tensor map creation failed");
       h->ms.status = h->status;
     }

@@ -17,15 +17,20 @@
 // the epilogue recombines sum_t acc_t 2^{-8t} with error-free FP32 two-sums.
 //
 // Data path (one step = two kernels):
-//   mixed_gemm_kernel      persistent, warp-specialised, 2-stage pipeline per CTA:
-//     warp 0 / lane 0: TMA + MMA.  Each 8 x 16 cell tile's operand is one 4D TMA box of the
-//       ghost-padded digit planes [digit, 8-mode group][y + 2][x + 2][8 modes] (10 x 18
-//       halo cells), landing in shared memory exactly in the K-major core-matrix layout:
-//       the A operand of the MMA for region offset (ox, oy) is the same buffer with the
-//       descriptor start shifted by (oy * 10 + ox) cells (implicit im2col, no copy).
+//   mixed_gemm_kernel      persistent, warp-specialised pipeline per CTA:
+//     warp 0 / lane 0: TMA.  For every digit of an 8 x 16 cell tile the operand is
+//       three 3D TMA boxes of the ghost-padded digit planes [digit, 8-mode group][y + 2]
+//       [(x + 2) x 8 modes], 8 x 18 cells each, at x offsets 0, 1, 2: they land in shared
+//       memory exactly in the K-major core-matrix layout, so the A operand of the MMA for
+//       region offset (ox, oy) is copy ox with its descriptor start moved by oy halo rows
+//       (128 B, keeping every core matrix 128-byte aligned) -- an implicit im2col without
+//       any copy by the SM.  Digits stream through a ring of slots, so the TMA runs a tile
+//       ahead of the tensor core.
+//     warp 1 / lane 0: MMA.  Descriptors are formed in registers (constant offsets).
 //       S x 9 x (theta_pad / 16) tcgen05.mma (M = 128); B = operator digits stacked so the
 //       pair (a, c') lands in TMEM block a + c'.  One commit per tile.
-//     warps 1..4: epilogue (thread <-> TMEM lane <-> cell); TMEM is double-buffered.
+//     warps 2..9: epilogue (thread <-> TMEM lane <-> cell, two warps per lane quadrant);
+//       TMEM is double-buffered.
 //   mixed_correct_kernel   the correction from the fused outputs in double-float FP32 with
 //       the final conservative state update in FP64, the new state's maximum, and the
 //       digit planes of the new state for the next step's TMA.
@@ -47,12 +52,12 @@ namespace {
 
 constexpr int kTX = 8, kTY = 16;             // cells per tile in x, y (128 = MMA M)
 constexpr int kHX = kTX + 2, kHY = kTY + 2;  // halo
-constexpr int kHalo = kHX * kHY;             // 180 halo cells
+constexpr int kCopy = kTX * kHY;             // cells of one x-shifted halo copy (8 x 18)
 constexpr int kBits = 8;                     // digit width
 constexpr long kWaitLimit = 1L << 22;        // bounded mbarrier polls (well under a second)
-constexpr int kGemmThreads = 288;            // warp 0: TMA + MMA, warps 1..8: epilogue
-constexpr int kStages = 3;                   // shared-memory stages of the operand boxes
-constexpr int kMaxMma = 80;                  // MMA descriptors per tile (table size)
+constexpr int kGemmThreads = 320;            // warp 0: TMA, warp 1: MMA, warps 2..9: epilogue
+constexpr int kMaxSlots = 8;                 // ring of per-digit operand slots
+constexpr uint32_t kSmemLimit = 232448;      // opt-in shared memory per block
 
 // status bits
 constexpr int kStatusTimeout = 2;
@@ -127,12 +132,12 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint32_t mbar, uint32_t phase) {
   return done != 0;
 }
 
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, int c3, uint32_t mbar) {
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint32_t mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%6];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(0), "r"(mbar)
       : "memory");
 }
 
@@ -143,6 +148,15 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7])
       : "r"(taddr));
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_wait_ld() {
@@ -222,28 +236,40 @@ __device__ __forceinline__ int exponent_above(unsigned long long absbits) {
 }
 
 struct GemmLayout {
-  int P, brows;
-  uint32_t stage_bytes, b_off, bar_off, tab_off, bytes;
+  int P, brows, slots, nmma, G, groups;
+  uint32_t copy_bytes, slot_bytes, b_off, bbytes, bar_off, bytes;
 };
 
-struct MmaEntry {
-  uint64_t bdesc;   // operator digits (B) descriptor
-  uint32_t aoff16;  // A start offset inside a stage, in 16 B units
-  uint32_t dcol;    // TMEM column of D
-  uint32_t idesc;   // instruction descriptor
-  uint32_t acc;     // accumulate into D
-};
+// MMAs of digit a: 9 region offsets x k-steps x operator-digit chunks (N <= 256)
+__host__ __device__ inline int gemm_nmma_digit(int S, int P, int nout_pad, int a) {
+  const int cmax = 256 / nout_pad;
+  return 9 * (P / 2) * ((S - a + cmax - 1) / cmax);
+}
 
+// Shared memory: a ring of slots, each holding G digits of one tile (three x-shifted copies
+// of the 8 x 18 halo box per digit), then the operator digits, then the barriers.  G is
+// the largest group of digits for which two slots fit.
 __host__ __device__ inline GemmLayout gemm_layout(int S, int thS, int nout_pad) {
   GemmLayout l;
   l.P = ((thS + 15) / 16) * 2;  // 8-mode groups after padding theta_S to a multiple of 16
   l.brows = S * nout_pad;
-  l.stage_bytes = (((uint32_t)S * l.P * kHalo * 16) + 1023) & ~1023u;
-  l.b_off = kStages * l.stage_bytes;
-  const uint32_t bbytes = (uint32_t)9 * l.P * l.brows * 16;
-  l.bar_off = (l.b_off + bbytes + 63) & ~63u;
-  l.tab_off = l.bar_off + 128;
-  l.bytes = l.tab_off + kMaxMma * (uint32_t)sizeof(MmaEntry);
+  l.nmma = 0;
+  for (int a = 0; a < S; ++a) l.nmma += gemm_nmma_digit(S, l.P, nout_pad, a);
+  l.bbytes = (uint32_t)9 * l.P * l.brows * 16;
+  const uint32_t digit_bytes = 3u * l.P * kCopy * 16;
+  const uint32_t rest = l.bbytes + 256 + 1024;
+  const uint32_t avail = rest < kSmemLimit ? kSmemLimit - rest : 0;
+  int G = S;
+  while (G > 1 && 2 * ((3u * G * l.P * kCopy * 16 + 1023) & ~1023u) > avail) --G;
+  l.G = G;
+  l.groups = (S + G - 1) / G;
+  l.copy_bytes = (uint32_t)G * l.P * kCopy * 16;      // G digits, one x-shifted copy
+  l.slot_bytes = ((3 * l.copy_bytes) + 1023) & ~1023u;
+  int slots = (int)(avail / l.slot_bytes);
+  l.slots = slots > kMaxSlots ? kMaxSlots : slots;
+  l.b_off = (uint32_t)l.slots * l.slot_bytes;
+  l.bar_off = (l.b_off + l.bbytes + 63) & ~63u;
+  l.bytes = l.bar_off + 256;
   return l;
 }
 
@@ -257,84 +283,69 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
     void* __restrict__ Yv, long long ystride_e, long long ystride_c, int* __restrict__ exps,
     unsigned long long* __restrict__ maxbits, int nx, int ny, int* status) {
   constexpr int THS = NB * NB;
-  constexpr int TPAD = ((THS + 15) / 16) * 16;
-  constexpr int P = TPAD / 8;
-  constexpr int KSTEPS = TPAD / 16;
-  constexpr int CMAX = 256 / NOUTP;  // operator digits per MMA (N <= 256)
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t tmem_base_sh;
-  __shared__ int nmma_sh;
   const GemmLayout L = gemm_layout(S, THS, NOUTP);
+  const int NSL = L.slots;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
   const int ntiles = ntx * nty;
-  const int tcols = S * NOUTP;  // TMEM columns per stage
+  const int mytiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int nitems = mytiles * L.groups;  // (tile, digit group) pairs of this CTA
+  const int tcols = S * NOUTP;     // TMEM columns per stage
   const int tstages = 2 * tcols <= 512 ? 2 : 1;
   const int ncols = tstages * tcols <= 256 ? 256 : 512;
-  // barriers: full[3] (TMA landed), done[3] (MMAs of a stage complete), empty[2] (TMEM
-  // stage read out by the 256 epilogue threads)
+  // barriers: full[slot] (TMA landed), done[slot] (MMAs reading the slot complete),
+  // tdone[2] (all MMAs of a tile complete), empty[2] (TMEM stage read out by the 256
+  // epilogue threads), opload (operator digits + MMA table)
   const uint32_t bar = smem_u32(smem + L.bar_off);
-  const uint32_t full0 = bar, done0 = bar + 8u * kStages, empty0 = bar + 16u * kStages;
-  const uint32_t box_bytes = (uint32_t)S * P * kHalo * 16;
+  const uint32_t full0 = bar, done0 = bar + 8u * kMaxSlots, tdone0 = bar + 16u * kMaxSlots,
+                 empty0 = tdone0 + 16u, opload = tdone0 + 32u;
+  const uint32_t copy_bytes = L.copy_bytes;
   const int sexp = exps[0];  // exponent the digit planes were made with
 
+  auto issue_item = [&](int item) {
+    const int kk = item / L.groups, q = item % L.groups, sl = item % NSL;
+    const int tile = blockIdx.x + kk * gridDim.x;
+    const uint32_t dst = smem_u32(smem + sl * L.slot_bytes);
+    const uint32_t fb = full0 + 8u * sl;
+    mbar_expect_tx(fb, 3 * copy_bytes);  // out-of-range planes are zero-filled and counted
+    const int x0 = (tile % ntx) * kTX, y0 = (tile / ntx) * kTY;
+#pragma unroll
+    for (int ox = 0; ox < 3; ++ox)  // x and the 8 modes form one contiguous dimension
+      tma_load_3d(dst + ox * copy_bytes, &dmap, (x0 + ox) * 8, y0, q * L.G * L.P, fb);
+  };
+
   if (tid == 0) {
-    for (int i = 0; i < kStages; ++i) {
+    for (int i = 0; i < kMaxSlots; ++i) {
       mbar_init(full0 + 8u * i, 1);
       mbar_init(done0 + 8u * i, 1);
     }
-    for (int i = 0; i < 2; ++i) mbar_init(empty0 + 8u * i, 256);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    // the first operand boxes are in flight while the operator digits are loaded
-    for (int i = 0; i < kStages - 1; ++i) {
-      const int tile = blockIdx.x + i * gridDim.x;
-      if (tile < ntiles) {
-        mbar_expect_tx(full0 + 8u * i, box_bytes);
-        tma_load_4d(smem_u32(smem + i * L.stage_bytes), &dmap, 0, (tile % ntx) * kTX,
-                    (tile / ntx) * kTY, 0, full0 + 8u * i);
-      }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tdone0 + 8u * i, 1);
+      mbar_init(empty0 + 8u * i, 256);
     }
+    mbar_init(opload, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // operator digits: one asynchronous bulk copy
+    mbar_expect_tx(opload, L.bbytes);
+    for (uint32_t off = 0; off < L.bbytes; off += 32768u)
+      bulk_load(smem_u32(smem + L.b_off + off), (const unsigned char*)Bg + off,
+                min(32768u, L.bbytes - off), opload);
+    for (int i = 0; i < NSL && i < nitems; ++i) issue_item(i);
     if (OUTF2 && blockIdx.x == 0) {
       // rotate the running maximum: the correction that follows accumulates a fresh one
       maxbits[0] = maxbits[1];
       maxbits[1] = 0;
       exps[1] = sexp;  // exponent of this step's outputs, read by the correction
     }
-    // the per-tile MMA sequence (offsets relative to a stage)
-    MmaEntry* tab = (MmaEntry*)(smem + L.tab_off);
-    const uint32_t bbase = smem_u32(smem + L.b_off);
-    const uint32_t b_lbo = (uint32_t)L.brows * 16, b_sbo = 128;
-    int n = 0;
-    for (int a = 0; a < S; ++a)
-      for (int r = 0; r < 9; ++r)
-        for (int j = 0; j < KSTEPS; ++j)
-          for (int c0 = 0; c0 < S - a; c0 += CMAX) {
-            const int kc = r * P + 2 * j;
-            const int nn = (min(S - a, c0 + CMAX) - c0) * NOUTP;
-            MmaEntry m;
-            m.bdesc = smem_desc(bbase + (uint32_t)(kc * L.brows + c0 * NOUTP) * 16, b_lbo, b_sbo);
-            m.aoff16 = (uint32_t)((a * P + 2 * j) * kHalo + (r / 3) * kHX + (r % 3));
-            m.dcol = (uint32_t)((a + c0) * NOUTP);
-            m.idesc = idesc_bf16(128, nn);
-            m.acc = (a == 0 && r == 0 && j == 0) ? 0u : 1u;
-            if (n < kMaxMma) tab[n] = m;
-            ++n;
-          }
-    nmma_sh = n;
   }
-  // operator digits -> shared memory (once per CTA)
-  {
-    uint4* bs = (uint4*)(smem + L.b_off);
-    const int nb16 = 9 * P * L.brows;
-    for (int i = tid; i < nb16; i += kGemmThreads) bs[i] = Bg[i];
-  }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_sh)),
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -342,54 +353,85 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- producer: TMA + MMA ----------------
-      const int nmma = nmma_sh;
-      const MmaEntry* tab = (const MmaEntry*)(smem + L.tab_off);
-      bool ok = nmma <= kMaxMma;
-      const uint32_t a_lbo = kHalo * 16, a_sbo = kHX * 16;
-      int k = 0;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++k) {
-        const int st = k % kStages, ts = k % tstages;
-        if (!mbar_wait(full0 + 8u * st, (k / kStages) & 1)) { ok = false; break; }
+      // ---------------- TMA producer: refill a slot once its MMAs are done ----------------
+      bool ok = NSL >= 2;
+      for (int item = NSL; item < nitems && ok; ++item) {
+        const int p = item - NSL, sp = p % NSL;
+        if (!mbar_wait_sleep(done0 + 8u * sp, (p / NSL) & 1)) { ok = false; break; }
+        issue_item(item);
+      }
+      if (!ok) atomicOr(status, kStatusTimeout);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      constexpr int P = ((THS + 15) / 16) * 2;
+      constexpr int KSTEPS = P / 2;
+      constexpr int CMAX = 256 / NOUTP;
+      const uint32_t brows = (uint32_t)L.brows;
+      const uint64_t bdesc0 = smem_desc(smem_u32(smem + L.b_off), brows * 16, 128);
+      bool ok = NSL >= 2 && mbar_wait(opload, 0);
+      int item = 0;
+      for (int k = 0; k < mytiles && ok; ++k) {
+        const int ts = k % tstages;
         if (k >= tstages && !mbar_wait(empty0 + 8u * ts, ((k - tstages) / tstages) & 1)) {
           ok = false;
           break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t abase = smem_desc(smem_u32(smem + st * L.stage_bytes), a_lbo, a_sbo);
         const uint32_t tst = tmem + (uint32_t)(ts * tcols);
-        for (int i = 0; i < nmma; ++i) {
-          const MmaEntry m = tab[i];
-          mma_bf16(tst + m.dcol, abase + m.aoff16, m.bdesc, m.idesc, m.acc);
+        for (int q = 0; q < L.groups; ++q, ++item) {
+          const int sl = item % NSL;
+          if (!mbar_wait(full0 + 8u * sl, (item / NSL) & 1)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // A: LBO = plane stride inside a copy, SBO = one halo row of 8 cells (128 B)
+          const uint64_t adesc0 = smem_desc(smem_u32(smem + sl * L.slot_bytes), kCopy * 16, 128);
+          const uint32_t copy16 = copy_bytes / 16;
+          const int a_end = min(S, (q + 1) * L.G);
+          for (int a = q * L.G; a < a_end; ++a) {
+            const uint32_t dig = (uint32_t)((a - q * L.G) * P * kCopy);
+            for (int c0 = 0; c0 < S - a; c0 += CMAX) {
+              const int nn = (min(S - a, c0 + CMAX) - c0) * NOUTP;
+              const uint32_t idesc = idesc_bf16(128, nn);
+              const uint32_t dcol = tst + (uint32_t)((a + c0) * NOUTP);
+#pragma unroll
+              for (int r = 0; r < 9; ++r) {
+#pragma unroll
+                for (int j = 0; j < KSTEPS; ++j) {
+                  const uint32_t aoff = (uint32_t)(r % 3) * copy16 + dig +
+                                        (uint32_t)(2 * j * kCopy) + (uint32_t)((r / 3) * kTX);
+                  const uint32_t boff = (uint32_t)(r * P + 2 * j) * brows + (uint32_t)(c0 * NOUTP);
+                  const uint32_t acc = (a == 0 && r == 0 && j == 0) ? 0u : 1u;
+                  mma_bf16(dcol, adesc0 + aoff, bdesc0 + boff, idesc, acc);
+                }
+              }
+            }
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  done0 + 8u * sl)
+              : "memory");
         }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                done0 + 8u * st)
-            : "memory");
-        // keep kStages - 1 boxes in flight: refill the stage the previous tile used
-        const int nxt = tile + (kStages - 1) * gridDim.x;
-        if (nxt < ntiles) {
-          const int s2 = (k + kStages - 1) % kStages;
-          if (k >= 1 && !mbar_wait(done0 + 8u * s2, ((k - 1) / kStages) & 1)) { ok = false; break; }
-          mbar_expect_tx(full0 + 8u * s2, box_bytes);
-          tma_load_4d(smem_u32(smem + s2 * L.stage_bytes), &dmap, 0, (nxt % ntx) * kTX,
-                      (nxt / ntx) * kTY, 0, full0 + 8u * s2);
-        }
+        if (ok)
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  tdone0 + 8u * ts)
+              : "memory");
       }
       if (!ok) atomicOr(status, kStatusTimeout);
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: warps 1..8, two per TMEM lane quadrant ----------------
+    // ---------------- epilogue: warps 2..9, two per TMEM lane quadrant ----------------
     const int quad = warp & 3;                 // lanes 32 quad .. this warp may read
-    const int part = (warp - 1) >> 2;          // which half of the output columns
+    const int part = (warp - 2) >> 2;          // which half of the output columns
     const int cell = quad * 32 + lane;
     const int ix = cell % kTX, iy = cell / kTX;
     const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
     int k = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-      const int st = k % kStages, ts = k % tstages;
-      if (!mbar_wait_sleep(done0 + 8u * st, (k / kStages) & 1)) {
+      const int ts = k % tstages;
+      if (!mbar_wait_sleep(tdone0 + 8u * ts, (k / tstages) & 1)) {
         if (lane == 0) atomicOr(status, kStatusTimeout);
         break;
       }
@@ -451,14 +493,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
     }
   }
   // drain: make sure no MMA is still writing TMEM before it is released (bounded)
-  if (tid == 0) {
-    int k_last = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) ++k_last;
-    if (k_last > 0) mbar_wait(done0 + 8u * ((k_last - 1) % kStages), ((k_last - 1) / kStages) & 1);
-  }
+  if (tid == 0 && mytiles > 0)
+    mbar_wait(tdone0 + 8u * ((mytiles - 1) % tstages), ((mytiles - 1) / tstages) & 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
+  if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
@@ -725,6 +764,7 @@ int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int sli
       }
     }
   }
+  if (L.bytes > kSmemLimit || L.slots < 2) return RIDG_EINVAL;
   int gmax = -100000;
   for (int c = 0; c < nout; ++c) gmax = std::max(gmax, gexp[c]);
   if (gmax == -100000) gmax = 0;
@@ -746,7 +786,7 @@ size_t mixed_plane_bytes(const Grid& g, int nb, int slices) {
   return (size_t)(g.n[0] + 2) * (g.n[1] + 2) * slices * P * 16;
 }
 
-int mixed_make_map(const Grid& g, int nb, int slices, void* planes, void* map_out) {
+int mixed_make_map(const Grid& g, int nb, int slices, int nout, void* planes, void* map_out) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -757,14 +797,16 @@ int mixed_make_map(const Grid& g, int nb, int slices, void* planes, void* map_ou
       q != cudaDriverEntryPointSuccess || !fn)
     return RIDG_ECUDA;
   const int thS = nb * nb, P = ((thS + 15) / 16) * 2;
-  // dims (fastest first): 8 modes (BF16), padded x, padded y, digit x mode group
-  cuuint64_t dims[4] = {8, (cuuint64_t)(g.n[0] + 2), (cuuint64_t)(g.n[1] + 2),
+  // dims (fastest first): padded x times 8 modes (BF16, contiguous), padded y, digit x
+  // mode group; a box row is 8 cells x 8 modes = 128 B
+  cuuint64_t dims[3] = {(cuuint64_t)(g.n[0] + 2) * 8, (cuuint64_t)(g.n[1] + 2),
                         (cuuint64_t)slices * P};
-  cuuint64_t strides[3] = {16, (cuuint64_t)(g.n[0] + 2) * 16,
+  cuuint64_t strides[2] = {(cuuint64_t)(g.n[0] + 2) * 16,
                            (cuuint64_t)(g.n[0] + 2) * (g.n[1] + 2) * 16};
-  cuuint32_t box[4] = {8, (cuuint32_t)kHX, (cuuint32_t)kHY, (cuuint32_t)(slices * P)};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = ((EncodeFn)fn)((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, planes,
+  const GemmLayout L = gemm_layout(slices, thS, nout_pad_of(nout));
+  cuuint32_t box[3] = {(cuuint32_t)kTX * 8, (cuuint32_t)kHY, (cuuint32_t)(L.G * P)};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = ((EncodeFn)fn)((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, planes,
                               dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -795,7 +837,7 @@ cudaError_t launch_mixed_gemm(const Grid& g, int nb, const MixedOp& op, MixedSta
 #define RIDG_GEMM_CASE(NBV, NP)                                                              \
   case NBV:                                                                                   \
     return fused ? launch_gemm_t<NBV, NP, true>(g, ms.map, op, Y, ys_e, ys_c, ms, s)          \
-                 : launch_gemm_t<NBV, NP, false>(g, ms.map, op, Y, ys_e, ys_c, ms, s);
+                 : launch_gemm_t<NBV, NP, false>(g, ms.map_pred, op, Y, ys_e, ys_c, ms, s);
   if (op.npad == 32) {
     switch (nb) { RIDG_GEMM_CASE(2, 32) RIDG_GEMM_CASE(3, 32) RIDG_GEMM_CASE(4, 32) }
   } else if (op.npad == 64) {

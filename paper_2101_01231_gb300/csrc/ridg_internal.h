@@ -46,7 +46,8 @@ struct MixedOp {
 // state, the TMA descriptor over them, and the exponent / maximum bookkeeping.
 struct MixedState {
   void* planes = nullptr;                 // [digit x mode group][y + 2][x + 2][8] bf16
-  alignas(64) unsigned char map[128];     // CUtensorMap over the planes
+  alignas(64) unsigned char map[128];     // CUtensorMap over the planes (fused step)
+  alignas(64) unsigned char map_pred[128];  // the same for the full prediction
   int* exps = nullptr;                    // [0] exponent of the planes, [1] of the outputs
   unsigned long long* maxbits = nullptr;  // [0] max |Q| of the current state, [1] accumulator
   int* status = nullptr;                  // shared status word
@@ -57,7 +58,7 @@ int mixed_build(int dim, int nb, const std::vector<double>& P, int nout, int sli
                 std::vector<unsigned short>& digits, std::vector<double>& rscale,
                 std::vector<float>& rowmul, MixedOp& op);
 size_t mixed_plane_bytes(const Grid& g, int nb, int slices);
-int mixed_make_map(const Grid& g, int nb, int slices, void* planes, void* map_out);
+int mixed_make_map(const Grid& g, int nb, int slices, int nout, void* planes, void* map_out);
 // Y[e * ys_e + c * ys_c] = (G X_e)[c]: FP64 (fused == false) or, for the fused step
 // operator, double-float pairs output-major with the exponent in exps[1]
 cudaError_t launch_mixed_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
