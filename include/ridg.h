@@ -52,7 +52,8 @@ enum {
   RIDG_ENOCONV = 5,     /* Newton hit its iteration cap in some regions; the step still
                            completed and ridg_info reports how many regions                */
   RIDG_ETIMEOUT = 6,    /* a bounded device-side wait gave up                             */
-  RIDG_ESTATE = 7       /* call out of order (e.g. correct before predict, no dt yet)    */
+  RIDG_ESTATE = 7,      /* call out of order (e.g. correct before predict, no dt yet)    */
+  RIDG_ETOOBIG = 8      /* problem larger than the fixed scratch of ridg_l2_error_noalloc  */
 };
 
 /* ----- problem description -------------------------------------------------------- */
@@ -171,6 +172,22 @@ int ridg_mass(ridg_t* h, double* mass);
 /* Relative L2 error of eq. l2relerror against the exact solution's projection onto
  * Q(M+1): x holds cells * m * (M+2)^d coefficients (same ordering rules).              */
 int ridg_l2_error(ridg_t* h, const double* x, int on_device, double* err);
+
+/* The same relative L2 error as ridg_l2_error for a state q (cells * m * (order+1)^dim) and
+ * exact coefficients x (cells * m * (order+2)^dim), both already in device memory, with no
+ * handle and no allocation of any kind.  The paper has no counterpart: this entry point is
+ * for callers that cannot call cudaMalloc where they need the diagnostic -- code running
+ * while another component captures the stream into a CUDA graph, code whose device memory
+ * is owned by a pool that must see every allocation, and time-critical loops that cannot
+ * afford the device synchronisation of cudaMalloc / cudaFree.  Its scratch is a fixed
+ * file-scope device array of 1 MiB (65536 pairs of partial sums, one pair per 256 cells),
+ * held by every GPU that loads the library until the process exits; larger problems
+ * (more than 16,777,216 cells) are rejected with RIDG_ETOOBIG before any work.  The first
+ * call on a device looks up the array's device address (make that first call before any
+ * stream capture).  Work is issued on `stream` (NULL = legacy default stream) and the call
+ * waits for it.  Every call shares the array: calls that overlap on the GPU race.        */
+int ridg_l2_error_noalloc(const double* q, const double* x, long long cells, int m, int dim,
+                          int order, void* stream, double* err);
 
 /* ----- tracing ---------------------------------------------------------------------------- */
 

@@ -227,6 +227,7 @@ const char* ridg_strerror(int status) {
     case RIDG_ENOCONV: return "Newton iteration cap reached";
     case RIDG_ETIMEOUT: return "bounded device wait timed out";
     case RIDG_ESTATE: return "call out of order";
+    case RIDG_ETOOBIG: return "problem larger than the fixed scratch of the no-allocation entry point";
     default: return "unknown status";
   }
 }

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libridg.so")
 
 RIDG_OK, RIDG_EINVAL, RIDG_ENOMEM, RIDG_ECUDA, RIDG_ENONFINITE, RIDG_ENOCONV, RIDG_ETIMEOUT, \
-    RIDG_ESTATE = range(8)
+    RIDG_ESTATE, RIDG_ETOOBIG = range(9)
 RIDG_FLUX_ADVECTION, RIDG_FLUX_BURGERS, RIDG_FLUX_EULER = range(3)
 RIDG_PREC_FP64, RIDG_PREC_MIXED_BF16, RIDG_PREC_MIXED_FP32 = range(3)
 
@@ -66,6 +66,8 @@ EXPORTS = {
     "ridg_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ridg_profile_t)]),
     "ridg_mass": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "ridg_l2_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "ridg_l2_error_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_int,
+                                        C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
     "ridg_batch_create": (C.c_int, [C.c_int, C.POINTER(ridg_mesh), C.POINTER(C.c_int),
                                     C.POINTER(ridg_flux), C.c_double, C.POINTER(ridg_options),
                                     C.POINTER(C.c_void_p)]),
@@ -242,6 +244,18 @@ def ridg_l2_error(h, x):
     p, dev = _ptr(x)
     e = C.c_double()
     _check(_lib.ridg_l2_error(h, p, dev, C.byref(e)), h)
+    return e.value
+
+
+def ridg_l2_error_noalloc(q, x, cells, m, dim, order, stream=None):
+    """Relative L2 error of device arrays q and x with no device allocation (fixed scratch)."""
+    pq, dq = _ptr(q)
+    px, dx = _ptr(x)
+    if not (dq and dx):
+        raise ValueError("ridg_l2_error_noalloc takes device arrays")
+    e = C.c_double()
+    _check(_lib.ridg_l2_error_noalloc(pq, px, int(cells), int(m), int(dim), int(order),
+                                      stream, C.byref(e)))
     return e.value
 
 
