@@ -172,18 +172,23 @@ class Clocks:
 # our arm
 # ---------------------------------------------------------------------------------------
 def _recorded_traffic(prec_name):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, used only
-    while the kernel source is unchanged since the capture (else None)."""
+    """DRAM bytes per launch of the dominant kernel, from the committed ncu summaries under
+    profiles/ (a line `roofline-traffic: <precision> <source> sha256_16=<h> dram_bytes=<n>`),
+    used only while that kernel source is unchanged since the capture (else None)."""
+    import glob
     import hashlib
-    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-    if not os.path.exists(p):
-        return None
-    rec = json.load(open(p)).get(prec_name)
-    if not rec:
-        return None
-    src = os.path.join(ROOT, "paper_2101_01231_gb300", "csrc", rec["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return rec["dram_bytes"] if h == rec["sha256_16"] else None
+    for p in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(p):
+            f = line.split()
+            if len(f) != 5 or f[0] != "roofline-traffic:" or f[1] != prec_name:
+                continue
+            kv = dict(x.split("=", 1) for x in f[3:])
+            src = os.path.join(ROOT, "paper_2101_01231_gb300", "csrc", f[2])
+            if not os.path.exists(src):
+                return None
+            h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            return int(kv["dram_bytes"]) if h == kv.get("sha256_16") else None
+    return None
 
 
 def _peaks():
