@@ -179,8 +179,43 @@ int ensure_digits(ridg_t* h) {
   return RIDG_OK;
 }
 
-// The step's prediction: FP64 time mean into Wbar, or (mixed) the fused outputs into Y.
+// Newton prediction of every cell's centre W (nonlinear flux).
+int enqueue_newton(ridg_t* h) {
+  ridg::NewtonArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.tb = h->nl.tb;
+  a.plan = h->plan;
+  a.Q = h->Q;
+  a.W = h->W;
+  a.nx = h->n[0];
+  a.ny = h->n[1];
+  a.ncell = h->ncell;
+  a.lam[0] = h->dt / h->h[0];
+  a.lam[1] = h->dt / h->h[1];
+  a.gamma = h->flux.gamma;
+  a.max_iters = h->opt.newton_max_iters;
+  a.tol = h->opt.newton_tol;
+  a.scratch = h->nl_scratch;
+  a.scratch_per_cta = h->nl_scratch_cta;
+  a.counter = h->nl_words;
+  a.stats = h->nl_words + 1;
+  RIDG_CUDA(h, ridg::launch_newton(h->nb, h->m, h->flux.kind,
+                                   h->opt.precision == RIDG_PREC_MIXED_FP32, a, h->nl_grid,
+                                   h->stream));
+  return RIDG_OK;
+}
+
+int enqueue_nl_correct(ridg_t* h) {
+  RIDG_CUDA(h, ridg::launch_nl_correct(h->nb, h->m, h->flux.kind, h->nl.tb, h->Q, h->W, h->n[0],
+                                       h->n[1], h->ncell, h->dt / h->h[0], h->dt / h->h[1],
+                                       h->flux.gamma, h->stream));
+  return RIDG_OK;
+}
+
+// The step's prediction: FP64 time mean into Wbar, or (mixed) the fused outputs into Y; for
+// a nonlinear flux the Newton prediction.
 int enqueue_predict_mean(ridg_t* h) {
+  if (!is_linear(h)) return enqueue_newton(h);
   Grid g = grid_of(h);
   if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
     RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed, h->ms, h->Y, 1, h->ncell, true,
@@ -193,6 +228,7 @@ int enqueue_predict_mean(ridg_t* h) {
 }
 
 int enqueue_correct_after_mean(ridg_t* h) {
+  if (!is_linear(h)) return enqueue_nl_correct(h);
   CorrParams cp = corr_params(h);
   if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
     RIDG_CUDA(h, ridg::launch_mixed_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
@@ -209,6 +245,21 @@ int enqueue_step(ridg_t* h) {
   int rc = enqueue_predict_mean(h);
   if (rc) return rc;
   return enqueue_correct_after_mean(h);
+}
+
+// Newton statistics since they were last cleared: regions at the iteration cap, largest
+// iteration count, flags (1: zero pivot, 2: non-finite update).
+int read_newton_stats(ridg_t* h) {
+  int st[3] = {0, 0, 0};
+  RIDG_CUDA(h, cudaMemcpyAsync(st, h->nl_words + 1, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+  RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->newton_unconverged = st[0];
+  h->newton_iters_max = st[1];
+  if (st[2] & 2) return set_err(h, RIDG_ENONFINITE, "Newton produced a non-finite update");
+  if (st[2] & 1) return set_err(h, RIDG_ENONFINITE, "zero pivot in a Newton block solve");
+  if (st[0] > 0)
+    return set_err(h, RIDG_ENOCONV, std::to_string(st[0]) + " regions hit the Newton iteration cap");
+  return RIDG_OK;
 }
 
 int check_handle(const ridg_t* h) { return h ? RIDG_OK : RIDG_EINVAL; }
@@ -240,7 +291,18 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
   *out = nullptr;
   if (mesh->dim < 1 || mesh->dim > 3 || order < 0 || order + 1 > max_nb(mesh->dim) || !(cfl > 0))
     return RIDG_EINVAL;
-  if (flux->kind != RIDG_FLUX_ADVECTION) return RIDG_EINVAL;
+  const int prec = opt ? opt->precision : RIDG_PREC_FP64;
+  int m = 1;
+  if (flux->kind == RIDG_FLUX_ADVECTION) {
+    if (prec != RIDG_PREC_FP64 && prec != RIDG_PREC_MIXED_BF16) return RIDG_EINVAL;
+  } else if (flux->kind == RIDG_FLUX_BURGERS || flux->kind == RIDG_FLUX_EULER) {
+    m = flux->kind == RIDG_FLUX_EULER ? 4 : 1;
+    if (mesh->dim != 2 || !ridg::newton_supported(order + 1, m)) return RIDG_EINVAL;
+    if (prec != RIDG_PREC_FP64 && prec != RIDG_PREC_MIXED_FP32) return RIDG_EINVAL;
+    if (flux->kind == RIDG_FLUX_EULER && !(flux->gamma > 1.0)) return RIDG_EINVAL;
+  } else {
+    return RIDG_EINVAL;
+  }
   ridg_t* h = new ridg_t();
   if (opt) h->opt = *opt;
   if (h->opt.slices <= 0) h->opt.slices = 6;
@@ -267,7 +329,7 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
   h->nR = 1;
   for (int d = 0; d < h->dim; ++d) h->nR *= 3;
   h->K = h->nR * h->thS;
-  h->m = 1;
+  h->m = m;
   h->flux = *flux;
   h->cfl = cfl;
   if (h->opt.precision == RIDG_PREC_MIXED_BF16 &&
@@ -295,27 +357,64 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
     hmin = std::min(hmin, h->h[d]);
     amax = std::max(amax, std::fabs(flux->vel[d]));
   }
-  h->dt = cfl * hmin / (amax > 0 ? amax : 1.0);
+  // linear flux: the speed is known now; nonlinear flux: dt is set from the state
+  h->dt = is_linear(h) ? cfl * hmin / (amax > 0 ? amax : 1.0) : 0.0;
   const size_t nQ = (size_t)h->ncell * h->m * h->thS;
   h->Q = (double*)dev_alloc(h, nQ * sizeof(double));
   h->W = (double*)dev_alloc(h, (size_t)h->ncell * h->m * h->thT * sizeof(double));
-  h->Wbar = (double*)dev_alloc(h, nQ * sizeof(double));
-  h->P = (double*)dev_alloc(h, (size_t)h->thT * h->K * sizeof(double));
   h->red = (double*)dev_alloc(h, (size_t)h->red_blocks * 4 * sizeof(double));
   h->status = (int*)dev_alloc(h, 16 * sizeof(int));
-  if (!h->Q || !h->W || !h->Wbar || !h->P || !h->red || !h->status) {
+  if (is_linear(h)) {
+    h->Wbar = (double*)dev_alloc(h, nQ * sizeof(double));
+    h->P = (double*)dev_alloc(h, (size_t)h->thT * h->K * sizeof(double));
+  }
+  if (!h->Q || !h->W || !h->red || !h->status || (is_linear(h) && (!h->Wbar || !h->P))) {
     ridg_destroy(h);
     return RIDG_ENOMEM;
+  }
+  if (!is_linear(h)) {
+    size_t tb_bytes = 0;
+    ridg::nl_tables_upload(h->nb, h->nl, nullptr, &tb_bytes, h->stream);
+    void* tb_mem = dev_alloc(h, tb_bytes);
+    h->plan = ridg::build_elim_plan();
+    h->nl_grid = ridg::newton_grid(h->nb, h->m, h->opt.precision == RIDG_PREC_MIXED_FP32);
+    h->nl_scratch_cta = ridg::newton_scratch_per_cta(h->nb, h->m,
+                                                     h->opt.precision == RIDG_PREC_MIXED_FP32, h->plan);
+    const size_t scratch = h->nl_scratch_cta * (size_t)h->nl_grid;
+    h->nl_scratch = h->nl_grid > 0 ? dev_alloc(h, scratch) : nullptr;
+    h->nl_words = (int*)dev_alloc(h, 8 * sizeof(int));
+    if (!tb_mem || !h->nl_scratch || !h->nl_words) {
+      dev_free(h, tb_mem);
+      ridg_destroy(h);
+      return RIDG_ENOMEM;
+    }
+    int rc = ridg::nl_tables_upload(h->nb, h->nl, tb_mem, &tb_bytes, h->stream);
+    if (rc != RIDG_OK) {
+      dev_free(h, tb_mem);
+      ridg_destroy(h);
+      return rc;
+    }
+    // the blocks' zero padding is never written again
+    if (cudaMemsetAsync(h->nl_scratch, 0, scratch, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->nl_words, 0, 8 * sizeof(int), h->stream) != cudaSuccess) {
+      ridg_destroy(h);
+      return RIDG_ECUDA;
+    }
   }
   if (cudaMemsetAsync(h->Q, 0, nQ * sizeof(double), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->status, 0, 16 * sizeof(int), h->stream) != cudaSuccess) {
     ridg_destroy(h);
     return RIDG_ECUDA;
   }
-  int rc = rebuild_linear(h);
-  if (rc != RIDG_OK) {
+  if (is_linear(h)) {
+    int rc = rebuild_linear(h);
+    if (rc != RIDG_OK) {
+      ridg_destroy(h);
+      return rc;
+    }
+  } else if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
     ridg_destroy(h);
-    return rc;
+    return RIDG_ECUDA;
   }
   *out = h;
   return RIDG_OK;
@@ -341,6 +440,9 @@ void ridg_destroy(ridg_t* h) {
   dev_free(h, h->ms.planes);
   dev_free(h, h->ms.exps);
   dev_free(h, h->ms.maxbits);
+  dev_free(h, h->nl.mem);
+  dev_free(h, h->nl_scratch);
+  dev_free(h, h->nl_words);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -362,6 +464,23 @@ int ridg_set_state(ridg_t* h, const double* q, int on_device) {
   h->have_pred = false;
   h->ms.valid = false;
   if (flag) return set_err(h, RIDG_ENONFINITE, "state contains NaN or Inf");
+  if (!is_linear(h) && !h->dt_fixed) {
+    // Sec. 5: dt = cfl h_min / (largest wave speed of the state)
+    unsigned long long bits = 0;
+    RIDG_CUDA(h, ridg::launch_max_speed(h->nb, h->m, h->flux.kind, h->nl.tb, h->Q, h->ncell,
+                                        h->flux.gamma, (unsigned long long*)(h->nl_words + 4),
+                                        h->stream));
+    RIDG_CUDA(h, cudaMemcpyAsync(&bits, h->nl_words + 4, sizeof(bits), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
+    double smax = 0.0;
+    std::memcpy(&smax, &bits, sizeof(smax));
+    if (!(smax > 0.0) || !std::isfinite(smax))
+      return set_err(h, RIDG_EINVAL, "the state has no positive finite wave speed; set dt");
+    h->dt = h->cfl * std::min(h->h[0], h->h[1]) / smax;
+    drop_graphs(h);
+    h->gen += 1;
+  }
   return RIDG_OK;
 }
 
@@ -381,6 +500,7 @@ int ridg_set_dt(ridg_t* h, double dt) {
   h->dt_fixed = true;
   if (is_linear(h)) return rebuild_linear(h);
   drop_graphs(h);
+  h->gen += 1;
   return RIDG_OK;
 }
 
@@ -395,7 +515,20 @@ int ridg_set_final_time(ridg_t* h, double T, long long* nsteps) {
 int ridg_predict(ridg_t* h, double* w_out, int on_device) {
   if (check_handle(h)) return RIDG_EINVAL;
   Grid g = grid_of(h);
-  if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+  if (!is_linear(h)) {
+    if (!(h->dt > 0)) return set_err(h, RIDG_ESTATE, "no dt yet: call ridg_set_state first");
+    RIDG_CUDA(h, cudaMemsetAsync(h->nl_words + 1, 0, 3 * sizeof(int), h->stream));
+    int rc = enqueue_newton(h);
+    if (rc) return rc;
+    h->have_pred = true;
+    if (w_out) {
+      const size_t bytes = (size_t)h->ncell * h->m * h->thT * sizeof(double);
+      RIDG_CUDA(h, cudaMemcpyAsync(w_out, h->W, bytes,
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                   h->stream));
+    }
+    return read_newton_stats(h);
+  } else if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
     int rc = ensure_digits(h);
     if (rc) return rc;
     RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed_pred, h->ms, h->W, h->thT, 1, false,
@@ -417,8 +550,13 @@ int ridg_predict(ridg_t* h, double* w_out, int on_device) {
 int ridg_correct(ridg_t* h) {
   if (check_handle(h)) return RIDG_EINVAL;
   if (!h->have_pred) return set_err(h, RIDG_ESTATE, "ridg_correct needs a prediction first");
-  CorrParams cp = corr_params(h);
-  RIDG_CUDA(h, ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->W, h->thT, cp, h->stream));
+  if (!is_linear(h)) {
+    int rc = enqueue_nl_correct(h);
+    if (rc) return rc;
+  } else {
+    CorrParams cp = corr_params(h);
+    RIDG_CUDA(h, ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->W, h->thT, cp, h->stream));
+  }
   h->ms.valid = false;
   h->have_pred = false;
   h->t += h->dt;
@@ -428,8 +566,11 @@ int ridg_correct(ridg_t* h) {
 
 int ridg_step(ridg_t* h, int n) {
   if (check_handle(h) || n < 1) return RIDG_EINVAL;
+  if (!(h->dt > 0)) return set_err(h, RIDG_ESTATE, "no dt yet: call ridg_set_state first");
   int rc0 = ensure_digits(h);
   if (rc0) return rc0;
+  if (!is_linear(h))  // Newton statistics of this call's steps (read by ridg_sync)
+    RIDG_CUDA(h, cudaMemsetAsync(h->nl_words + 1, 0, 3 * sizeof(int), h->stream));
   auto it = h->graphs.find(n);
   if (it == h->graphs.end()) {
     cudaGraph_t graph = nullptr;
@@ -466,6 +607,7 @@ int read_status(ridg_t* h) {
   if (st & 2) return set_err(h, RIDG_ETIMEOUT, "a bounded tensor-core wait gave up");
   if (st & 4)
     return set_err(h, RIDG_ENONFINITE, "state outgrew the mixed-precision digit range in a step");
+  if (!is_linear(h)) return read_newton_stats(h);
   return RIDG_OK;
 }
 
@@ -477,8 +619,10 @@ int ridg_sync(ridg_t* h) {
 
 int ridg_profile_step(ridg_t* h, int n, ridg_profile_t* out) {
   if (check_handle(h) || n < 1 || !out) return RIDG_EINVAL;
+  if (!(h->dt > 0)) return set_err(h, RIDG_ESTATE, "no dt yet: call ridg_set_state first");
   int rc0 = ensure_digits(h);
   if (rc0) return rc0;
+  if (!is_linear(h)) RIDG_CUDA(h, cudaMemsetAsync(h->nl_words + 1, 0, 3 * sizeof(int), h->stream));
   cudaEvent_t ev[3];
   for (int i = 0; i < 3; ++i) RIDG_CUDA(h, cudaEventCreate(&ev[i]));
   double tp = 0, tc = 0;
@@ -511,6 +655,7 @@ int ridg_profile_step(ridg_t* h, int n, ridg_profile_t* out) {
   out->step_ms = (tp + tc) / n;
   out->launches_per_step = 2;
   h->have_pred = false;
+  if (!is_linear(h)) return read_newton_stats(h);
   return RIDG_OK;
 }
 

@@ -1,0 +1,10 @@
+// Newton prediction with FP32 linear solves and the FP64 residual (RIDG_PREC_MIXED_FP32):
+// the factorisation only steers the iteration, the FP64 residual fixes the converged point.
+#include "k_newton.cuh"
+
+namespace ridg {
+cudaError_t launch_newton_f32(int nb, int m, int kind, const NewtonArgs& a, int grid,
+                              cudaStream_t s) {
+  return newton::launch_typed<float>(nb, m, kind, a, grid, s);
+}
+}  // namespace ridg

@@ -71,6 +71,69 @@ cudaError_t launch_mixed_correct(const Grid& g, int nb, int slices, double* Q, c
                                  int gmax, const CorrParams& cp, int sgnx, int sgny,
                                  MixedState& ms, cudaStream_t s);
 
+// ---- nonlinear flux, 2D: Newton prediction (k_newton*.cu) and correction (k_nonlinear.cu) ----
+// Device copies of the host-built tables (nl_tables.h), all inside one allocation.
+struct NlDev {
+  const double *Mt, *em;                // time term, psi_a(-1)
+  const double *PsiV, *dPsiV, *wV;      // residual volume rule
+  const double *PsiF, *wF;              // residual face rule
+  const double *PhiV, *dPhiV, *PhiF;    // spatial basis at the same points (correction)
+  const double *PsiAtP, *PsiAtFP, *P1;  // projection rule of eq. Jacproj
+  const double* PhiEq;                  // spatial basis on a 6 x 6 equispaced grid (wave speed)
+  const int *bptr[2], *bp[2];           // volume triple-product lists per direction
+  const double* bval[2];
+  const int *gptr[8], *gp[8];           // face lists, index dd * 4 + side_k * 2 + side_l
+  const double* gval[8];
+};
+// Block elimination plan for the 3 x 3 region: blocks are eliminated corners first, then the
+// edge cells, then the centre; each pivot's later neighbours and the fill they create.
+struct NlPlan {
+  int order[9];
+  int nn[9];
+  int nbr[9][3];
+  int slot[81];        // storage slot of block (i, j), -1 if it stays zero
+  int first[9][3][3];  // 1: this update creates the block (write, do not accumulate)
+  int nslots;
+};
+NlPlan build_elim_plan();
+struct NlDevTables {
+  NlDev tb{};
+  void* mem = nullptr;
+  size_t bytes = 0;
+};
+// Build the tables for degree nb - 1 and copy them into `mem` (device, `bytes` long; call
+// with mem == nullptr first to get the size).
+int nl_tables_upload(int nb, NlDevTables& out, void* mem, size_t* bytes, cudaStream_t s);
+bool newton_supported(int nb, int m);
+// CTAs of the persistent Newton kernel and the scratch each needs (bytes)
+int newton_grid(int nb, int m, bool fp32);
+size_t newton_scratch_per_cta(int nb, int m, bool fp32, const NlPlan& plan);
+struct NewtonArgs {
+  NlDev tb;
+  NlPlan plan;
+  const double* Q;
+  double* W;         // centre prediction, cells x m x theta_T
+  int nx, ny;
+  long long ncell;
+  double lam[2];     // dt / h_d
+  double gamma;
+  int max_iters;
+  double tol;
+  void* scratch;     // per-CTA block storage
+  size_t scratch_per_cta;
+  int* counter;      // work counter (zeroed before the launch)
+  int* stats;        // [0] unconverged regions, [1] largest iteration count, [2] flags
+};
+cudaError_t launch_newton(int nb, int m, int flux_kind, bool fp32, const NewtonArgs& a, int grid,
+                          cudaStream_t s);
+cudaError_t launch_nl_correct(int nb, int m, int flux_kind, const NlDev& tb, double* Q,
+                              const double* W, int nx, int ny, long long ncell, double lamx,
+                              double lamy, double gamma, cudaStream_t s);
+// largest wave speed of Q over a 6 x 6 equispaced grid of every cell -> *out (as bits)
+cudaError_t launch_max_speed(int nb, int m, int flux_kind, const NlDev& tb, const double* Q,
+                             long long ncell, double gamma, unsigned long long* out,
+                             cudaStream_t s);
+
 // ---- diagnostics (k_diag.cu) ----
 // partial sums (per block) of q[e, r, 0], r < m  -> out[block * m + r]
 cudaError_t launch_mass_partials(const double* Q, long long ncell, int m, int thS, double* out,
@@ -117,6 +180,13 @@ struct ridg_handle {
   // graphs: key = number of steps
   std::map<int, cudaGraphExec_t> graphs;
   std::map<int, cudaGraph_t> graph_defs;
+  // nonlinear flux: tables, elimination plan, per-CTA block storage of the Newton kernel
+  ridg::NlDevTables nl;
+  ridg::NlPlan plan{};
+  void* nl_scratch = nullptr;
+  size_t nl_scratch_cta = 0;
+  int nl_grid = 0;
+  int* nl_words = nullptr;  // [0] work counter, [1..3] Newton statistics, [4..5] max speed bits
   // Newton statistics of the last prediction
   long long newton_unconverged = 0;
   int newton_iters_max = 0;

@@ -230,7 +230,7 @@ def ridg_info(h):
 
 def ridg_profile_step(h, n=1):
     p = ridg_profile_t()
-    _check(_lib.ridg_profile_step(h, int(n), C.byref(p)), h)
+    _check(_lib.ridg_profile_step(h, int(n), C.byref(p)), h, allow=(RIDG_ENOCONV,))
     return {k: getattr(p, k) for k, _ in ridg_profile_t._fields_}
 
 
@@ -326,9 +326,11 @@ class Solver:
         return out
 
     def predict(self, out=None):
+        """The centre prediction of every cell; `last_status` is RIDG_ENOCONV when Newton hit
+        its iteration cap somewhere (the prediction is still complete)."""
         if out is None:
             out = np.empty((self.cells, self.m * self.theta_t))
-        ridg_predict(self.h, out)
+        self.last_status = ridg_predict(self.h, out)
         return out
 
     def correct(self):
@@ -338,7 +340,8 @@ class Solver:
         return ridg_step(self.h, n)
 
     def sync(self):
-        return ridg_sync(self.h)
+        self.last_status = ridg_sync(self.h)
+        return self.last_status
 
     def info(self):
         return ridg_info(self.h)
