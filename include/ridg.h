@@ -106,6 +106,8 @@ typedef struct {
   long long newton_unconverged; /* regions that hit the Newton cap in the last prediction */
   int newton_iters_max;         /* largest Newton iteration count of the last prediction  */
   int precision, slices;
+  long long newton_iters_total; /* Newton iterations summed over the regions of the last
+                                   prediction (or of the steps of the last ridg_step)      */
 } ridg_info_t;
 
 /* ----- lifecycle -------------------------------------------------------------------- */

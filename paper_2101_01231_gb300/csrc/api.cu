@@ -199,6 +199,7 @@ int enqueue_newton(ridg_t* h) {
   a.scratch_per_cta = h->nl_scratch_cta;
   a.counter = h->nl_words;
   a.stats = h->nl_words + 1;
+  a.iters_total = (unsigned long long*)(h->nl_words + 6);
   RIDG_CUDA(h, ridg::launch_newton(h->nb, h->m, h->flux.kind,
                                    h->opt.precision == RIDG_PREC_MIXED_FP32, a, h->nl_grid,
                                    h->stream));
@@ -247,18 +248,28 @@ int enqueue_step(ridg_t* h) {
   return enqueue_correct_after_mean(h);
 }
 
+cudaError_t clear_newton_stats(ridg_t* h) {
+  cudaError_t e = cudaMemsetAsync(h->nl_words + 1, 0, 3 * sizeof(int), h->stream);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(h->nl_words + 6, 0, 2 * sizeof(int), h->stream);
+}
+
 // Newton statistics since they were last cleared: regions at the iteration cap, largest
 // iteration count, flags (1: zero pivot, 2: non-finite update).
 int read_newton_stats(ridg_t* h) {
-  int st[3] = {0, 0, 0};
-  RIDG_CUDA(h, cudaMemcpyAsync(st, h->nl_words + 1, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+  int w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  RIDG_CUDA(h, cudaMemcpyAsync(w, h->nl_words, sizeof(w), cudaMemcpyDeviceToHost, h->stream));
   RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
-  h->newton_unconverged = st[0];
-  h->newton_iters_max = st[1];
-  if (st[2] & 2) return set_err(h, RIDG_ENONFINITE, "Newton produced a non-finite update");
-  if (st[2] & 1) return set_err(h, RIDG_ENONFINITE, "zero pivot in a Newton block solve");
-  if (st[0] > 0)
-    return set_err(h, RIDG_ENOCONV, std::to_string(st[0]) + " regions hit the Newton iteration cap");
+  const int unconverged = w[1], iters_max = w[2], flags = w[3];
+  unsigned long long total = 0;
+  std::memcpy(&total, w + 6, sizeof(total));
+  h->newton_unconverged = unconverged;
+  h->newton_iters_max = iters_max;
+  h->newton_iters_total = (long long)total;
+  if (flags & 2) return set_err(h, RIDG_ENONFINITE, "Newton produced a non-finite update");
+  if (flags & 1) return set_err(h, RIDG_ENONFINITE, "zero pivot in a Newton block solve");
+  if (unconverged > 0)
+    return set_err(h, RIDG_ENOCONV, std::to_string(unconverged) + " regions hit the Newton iteration cap");
   return RIDG_OK;
 }
 
@@ -517,7 +528,7 @@ int ridg_predict(ridg_t* h, double* w_out, int on_device) {
   Grid g = grid_of(h);
   if (!is_linear(h)) {
     if (!(h->dt > 0)) return set_err(h, RIDG_ESTATE, "no dt yet: call ridg_set_state first");
-    RIDG_CUDA(h, cudaMemsetAsync(h->nl_words + 1, 0, 3 * sizeof(int), h->stream));
+    RIDG_CUDA(h, clear_newton_stats(h));
     int rc = enqueue_newton(h);
     if (rc) return rc;
     h->have_pred = true;
@@ -570,7 +581,7 @@ int ridg_step(ridg_t* h, int n) {
   int rc0 = ensure_digits(h);
   if (rc0) return rc0;
   if (!is_linear(h))  // Newton statistics of this call's steps (read by ridg_sync)
-    RIDG_CUDA(h, cudaMemsetAsync(h->nl_words + 1, 0, 3 * sizeof(int), h->stream));
+    RIDG_CUDA(h, clear_newton_stats(h));
   auto it = h->graphs.find(n);
   if (it == h->graphs.end()) {
     cudaGraph_t graph = nullptr;
@@ -622,7 +633,7 @@ int ridg_profile_step(ridg_t* h, int n, ridg_profile_t* out) {
   if (!(h->dt > 0)) return set_err(h, RIDG_ESTATE, "no dt yet: call ridg_set_state first");
   int rc0 = ensure_digits(h);
   if (rc0) return rc0;
-  if (!is_linear(h)) RIDG_CUDA(h, cudaMemsetAsync(h->nl_words + 1, 0, 3 * sizeof(int), h->stream));
+  if (!is_linear(h)) RIDG_CUDA(h, clear_newton_stats(h));
   cudaEvent_t ev[3];
   for (int i = 0; i < 3; ++i) RIDG_CUDA(h, cudaEventCreate(&ev[i]));
   double tp = 0, tc = 0;
@@ -672,6 +683,7 @@ int ridg_info(ridg_t* h, ridg_info_t* info) {
   info->steps = h->steps;
   info->newton_unconverged = h->newton_unconverged;
   info->newton_iters_max = h->newton_iters_max;
+  info->newton_iters_total = h->newton_iters_total;
   info->precision = h->opt.precision;
   info->slices = h->opt.slices;
   return RIDG_OK;

@@ -1,13 +1,17 @@
 // Newton prediction for a nonlinear flux in 2D (Sec. 3), one persistent CTA per region.
 //
 // For every cell the CTA solves the region system of eq. pred_full_system on the 3 x 3
-// region R_i by Newton's method: the residual by tensor Gauss quadrature (FP64), the Jacobian
-// quasi-quadrature-free (eqs. Jacproj, Jacobian2: F'(w) projected onto the degree-2M space-
-// time basis and contracted with sparse lists of triple-product integrals), and the linear
-// solve J dW = R by block elimination of the 3 x 3 block structure (corners, then edges,
-// then the centre), in T = double or, for the mixed form, T = float.  The blocks live in a
-// per-CTA slice of global memory (L2-resident while the CTA works on them); everything
-// else of the region stays in shared memory.  Iterates start from Q^n extended constant in
+// region R_i by Newton's method:
+//  * the residual by tensor Gauss quadrature, always in FP64 (it defines the fixed point);
+//  * the Jacobian quasi-quadrature-free (eqs. Jacproj, Jacobian2): F'(w) projected onto the
+//    degree-2M space-time basis by a tensor-product projection, then contracted with the
+//    triple-product lists merged per (k, l) pair; in T;
+//  * the linear solve J dW = R by block elimination of the 3 x 3 block structure (corners,
+//    edges, centre): every pivot block inverted by Gauss-Jordan with implicit row pivoting
+//    on a register-resident tile, the other blocks updated by register-tiled GEMMs; in T.
+// T = double (RIDG_PREC_FP64) or float (RIDG_PREC_MIXED_FP32: FP32 Jacobian and solves,
+// FP64 residual and iterate).  The blocks live in a per-CTA slice of global memory; the
+// rest of the region stays in shared memory.  Iterates start from Q^n extended constant in
 // time and stop when ||dW||_inf <= tol max(1, ||W||_inf) or after max_iters.
 #pragma once
 
@@ -29,15 +33,63 @@ struct Dims {
   static constexpr int NQ = (3 * (NB - 1) + 2) / 2, QV = NQ * NQ * NQ, QF = NQ * NQ;
   static constexpr int NP = 2 * NB - 1, QP = NP * NP * NP, QPF = NP * NP;
   static constexpr int MM = MV * MV;
+  static constexpr int CG = MV == 1 ? 9 : 1;              // cells assembled per list pass
+  static constexpr int FAS = (2 * QP + 8 * QPF) * MM;     // projected arrays of one cell
+  static constexpr int PB = 2 * MM * QP > 8 * MM * QPF ? 2 * MM * QP : 8 * MM * QPF;
 };
 
 constexpr size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 
+// packed assembly-list entries (see NlDev)
+template <typename T>
+struct Ent;
+template <>
+struct Ent<double> {
+  int off, pad;
+  double c;
+};
+template <>
+struct Ent<float> {
+  int off;
+  float c;
+};
+
+// per-precision table pointers
+template <typename T>
+struct Tab;
+template <>
+struct Tab<double> {
+  static __device__ __forceinline__ const double* Mt(const NlDev& t) { return t.Mt; }
+  static __device__ __forceinline__ const double* PsiAtP(const NlDev& t) { return t.PsiAtP; }
+  static __device__ __forceinline__ const double* PsiAtFP(const NlDev& t) { return t.PsiAtFP; }
+  static __device__ __forceinline__ const double* P1(const NlDev& t) { return t.P1; }
+  static __device__ __forceinline__ const Ent<double>* dent(const NlDev& t) {
+    return (const Ent<double>*)t.dent_d;
+  }
+  static __device__ __forceinline__ const Ent<double>* oent(const NlDev& t, int f) {
+    return (const Ent<double>*)t.oent_d[f];
+  }
+};
+template <>
+struct Tab<float> {
+  static __device__ __forceinline__ const float* Mt(const NlDev& t) { return t.Mt_f; }
+  static __device__ __forceinline__ const float* PsiAtP(const NlDev& t) { return t.PsiAtP_f; }
+  static __device__ __forceinline__ const float* PsiAtFP(const NlDev& t) { return t.PsiAtFP_f; }
+  static __device__ __forceinline__ const float* P1(const NlDev& t) { return t.P1_f; }
+  static __device__ __forceinline__ const Ent<float>* dent(const NlDev& t) {
+    return (const Ent<float>*)t.dent_f;
+  }
+  static __device__ __forceinline__ const Ent<float>* oent(const NlDev& t, int f) {
+    return (const Ent<float>*)t.oent_f[f];
+  }
+};
+
 // shared-memory layout (bytes) of one CTA
 template <typename T, int NB, int MV>
 struct Layout {
   using D = Dims<NB, MV>;
+  static constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;     // GEMM staging buffers
   static constexpr size_t oW = 0;
   static constexpr size_t oQ = up16(oW + sizeof(double) * 9 * D::BS);
   static constexpr size_t oR = up16(oQ + sizeof(double) * 9 * MV * D::THS);
@@ -45,17 +97,22 @@ struct Layout {
   static constexpr size_t oRed = up16(oAl + sizeof(double) * 16);
   static constexpr size_t oX = up16(oRed + sizeof(double) * 32);
   static constexpr size_t oCol = up16(oX + sizeof(T) * 9 * D::BP);
-  static constexpr size_t oPerm = up16(oCol + sizeof(T) * D::BP);
-  static constexpr size_t oMisc = up16(oPerm + sizeof(int) * D::BP);
+  static constexpr size_t oRow = up16(oCol + sizeof(T) * 2 * D::BP);
+  static constexpr size_t oUsed = up16(oRow + sizeof(T) * 2 * D::BP);
+  static constexpr size_t oProw = up16(oUsed + sizeof(int) * D::BP);
+  static constexpr size_t oRank = up16(oProw + sizeof(int) * D::BP);
+  static constexpr size_t oMisc = up16(oRank + sizeof(int) * D::BP);
   static constexpr size_t oArena = up16(oMisc + sizeof(int) * 16);
   // phase arenas
   static constexpr size_t aRes = sizeof(double) * (9 * 2 * MV * D::QV + 9 * 4 * MV * D::QF);
   static constexpr size_t aAlpha = sizeof(double) * 12 * D::QF;
-  static constexpr size_t aJac =
-      sizeof(double) * (MV * D::QP + 4 * D::MM * D::QP + 16 * D::MM * D::QPF);
+  static constexpr size_t oJW = up16(sizeof(T) * D::CG * D::FAS);     // after the FA arrays
+  static constexpr size_t oJB0 = up16(oJW + sizeof(T) * MV * D::QP);
+  static constexpr size_t oJB1 = up16(oJB0 + sizeof(T) * D::PB);
+  static constexpr size_t aJac = up16(oJB1 + sizeof(T) * D::PB);
   static constexpr size_t oSA = up16(sizeof(T) * D::BP * D::BP);
-  static constexpr size_t oSB = up16(oSA + sizeof(T) * D::BP * 17);
-  static constexpr size_t aLU = up16(oSB + sizeof(T) * 16 * D::BP);
+  static constexpr size_t oSB = up16(oSA + sizeof(T) * NBUF * D::BP * 17);
+  static constexpr size_t aLU = up16(oSB + sizeof(T) * NBUF * 16 * D::BP);
   static constexpr size_t bytes = oArena + cmax(cmax(aRes, aAlpha), cmax(aJac, aLU));
 };
 
@@ -73,11 +130,11 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 }
 
 // sum_k tab[k * stride + q] w[k]
-template <int N>
-__device__ __forceinline__ double dotcol(const double* tab, int stride, int q, const double* w) {
-  double acc = 0.0;
+template <int N, typename S, typename U>
+__device__ __forceinline__ S dotcol(const S* tab, int stride, int q, const U* w) {
+  S acc = S(0);
 #pragma unroll 4
-  for (int k = 0; k < N; ++k) acc = fma(tab[k * stride + q], w[k], acc);
+  for (int k = 0; k < N; ++k) acc = fma(tab[k * stride + q], (S)w[k], acc);
   return acc;
 }
 
@@ -94,20 +151,39 @@ __device__ __forceinline__ int region_nbr(int r, int dd, int side) {
   return (rx < 0 || rx > 2 || ry < 0 || ry > 2) ? -1 : ry * 3 + rx;
 }
 
-// one pass of the tensor-product projection along `axis` (stride NP^axis) of n components,
-// each a tensor of NP^ND values
-template <int NP, int ND>
-__device__ void proj_pass(const double* in, double* out, const double* P1, int ncomp, int axis) {
+// one pass of the tensor-product projection along `axis` (stride NP^axis) of ncomp
+// component tensors of NP^ND values: out[c][.] = sum_q P1[p][q] in[c][..q..]
+template <int NP, int ND, typename T>
+__device__ void proj_pass(const T* in, T* out, const T* P1, int ncomp, int axis) {
   constexpr int QN = ND == 3 ? NP * NP * NP : NP * NP;
   const int stride = axis == 0 ? 1 : (axis == 1 ? NP : NP * NP);
   for (int i = threadIdx.x; i < ncomp * QN; i += kThreads) {
     const int c = i / QN, pi = i % QN;
     const int pa = (pi / stride) % NP;
-    const double* src = in + c * QN + (pi - pa * stride);
-    double acc = 0.0;
+    const T* src = in + c * QN + (pi - pa * stride);
+    T acc = T(0);
 #pragma unroll
     for (int q = 0; q < NP; ++q) acc = fma(P1[pa * NP + q], src[q * stride], acc);
     out[i] = acc;
+  }
+}
+
+// the last pass, along the slowest axis, written point-major (m x m matrices contiguous)
+// with a per-component-group scale: out[(pbase(c) + p) * MM + ij] = scale(c) sum_q ...
+template <int NP, int ND, int MM, typename T>
+__device__ void proj_last(const T* in, T* out, const T* P1, int nsets, int set_base_stride,
+                          int set_base0, const T* scale) {
+  constexpr int QN = ND == 3 ? NP * NP * NP : NP * NP;
+  constexpr int stride = ND == 3 ? NP * NP : NP;
+  for (int i = threadIdx.x; i < nsets * MM * QN; i += kThreads) {
+    const int c = i / QN, pi = i % QN;
+    const int set = c / MM, ij = c % MM;
+    const int pa = pi / stride;
+    const T* src = in + c * QN + (pi - pa * stride);
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) acc = fma(P1[pa * NP + q], src[q * stride], acc);
+    out[(set_base0 + set * set_base_stride + pi) * MM + ij] = scale[set] * acc;
   }
 }
 
@@ -222,129 +298,152 @@ __device__ void residual(const NlDev& tb, const double* Ws, const double* Qs, do
 }
 
 // ---------------------------------------------------------------------------------------
-// quasi-quadrature-free Jacobian (eqs. Jacproj, Jacobian2) of region cell r: its diagonal
-// block and its blocks towards the region neighbours, written in T to the block slots
+// quasi-quadrature-free Jacobian (eqs. Jacproj, Jacobian2)
 // ---------------------------------------------------------------------------------------
+// Projected F' of region cell r into FA (point-major m x m matrices):
+//   [F'_x (QP) | F'_y (QP) | own face f (QPf) x 4 | neighbour face f (QPf) x 4]
+// scaled by -lam_d / 4 (volume) and +lam_d / 4 (faces), the factors of eq. Jacobian2.
 template <typename T, int NB, int MV, int FLUX>
-__device__ void jacobian_cell(const NlDev& tb, const NlPlan& plan, int r, const double* Ws,
-                              const double* alpha, double* arena, T* slots, const double* lam,
-                              double g) {
+__device__ void project_cell(const NlDev& tb, int r, const double* Ws, const double* alpha,
+                             T* FA, T* wp, T* b0, T* b1, const double* lam, double g) {
   using D = Dims<NB, MV>;
-  constexpr int MM = D::MM, QP = D::QP, QPF = D::QPF, NP = D::NP, THT = D::THT, BP = D::BP;
-  double* wp = arena;                    // [MV][QP]
-  double* bufA = wp + MV * QP;           // [2][MM][QP]
-  double* bufB = bufA + 2 * MM * QP;     // [2][MM][QP]
-  double* graw = bufB + 2 * MM * QP;     // [8][MM][QPF]: own (f) and neighbour (4 + f) sides
-  double* gtmp = graw + 8 * MM * QPF;    // [8][MM][QPF]
+  constexpr int MM = D::MM, QP = D::QP, QPF = D::QPF, NP = D::NP, THT = D::THT;
+  const T* PsiAtP = Tab<T>::PsiAtP(tb);
+  const T* PsiAtFP = Tab<T>::PsiAtFP(tb);
+  const T* P1 = Tab<T>::P1(tb);
+  const T gT = (T)g;
+  __shared__ T sclv[2], sclf[8];  // -lam_d / 4 per volume set, +lam_d / 4 per face set
+  if (threadIdx.x < 2) sclv[threadIdx.x] = (T)(-0.25 * lam[threadIdx.x]);
+  if (threadIdx.x < 8) sclf[threadIdx.x] = (T)(0.25 * lam[(threadIdx.x & 3) >> 1]);
+  // volume: values at the projection points, F'_d there, three passes
   for (int i = threadIdx.x; i < MV * QP; i += kThreads) {
     const int j = i / QP, q = i % QP;
-    wp[i] = dotcol<THT>(tb.PsiAtP, QP, q, Ws + (r * MV + j) * THT);
+    wp[i] = dotcol<THT>(PsiAtP, QP, q, Ws + (r * MV + j) * THT);
   }
+  __syncthreads();
+  for (int q = threadIdx.x; q < QP; q += kThreads) {
+    T w[MV], J[MM];
+    for (int j = 0; j < MV; ++j) w[j] = wp[j * QP + q];
+    for (int dd = 0; dd < 2; ++dd) {
+      nlflux::dF<FLUX>(w, dd, J, gT);
+      for (int ij = 0; ij < MM; ++ij) b0[(dd * MM + ij) * QP + q] = J[ij];
+    }
+  }
+  __syncthreads();
+  proj_pass<NP, 3>(b0, b1, P1, 2 * MM, 0);
+  __syncthreads();
+  proj_pass<NP, 3>(b1, b0, P1, 2 * MM, 1);
+  __syncthreads();
+  proj_last<NP, 3, MM>(b0, FA, P1, 2, QP, 0, sclv);
+  __syncthreads();
+  // faces: the Rusanov flux Jacobian on both sides, at the face projection points
   for (int i = threadIdx.x; i < 4 * QPF; i += kThreads) {
     const int f = i / QPF, q = i % QPF;
     const int dd = f >> 1, si = f & 1, side = si ? -1 : 1;
-    const double* to = tb.PsiAtFP + (size_t)(dd * 2 + si) * THT * QPF;
-    double wo[MV], Jo[MM];
+    const T* to = PsiAtFP + (size_t)(dd * 2 + si) * THT * QPF;
+    T wo[MV], Jo[MM];
     for (int j = 0; j < MV; ++j) wo[j] = dotcol<THT>(to, QPF, q, Ws + (r * MV + j) * THT);
-    nlflux::dF<FLUX>(wo, dd, Jo, g);
+    nlflux::dF<FLUX>(wo, dd, Jo, gT);
     const int r2 = region_nbr(r, dd, side);
     if (r2 < 0) {
-      for (int ij = 0; ij < MM; ++ij) graw[(f * MM + ij) * QPF + q] = side * Jo[ij];
+      for (int ij = 0; ij < MM; ++ij) {
+        b0[(f * MM + ij) * QPF + q] = side * Jo[ij];
+        b0[((4 + f) * MM + ij) * QPF + q] = T(0);
+      }
     } else {
-      const double* tn = tb.PsiAtFP + (size_t)(dd * 2 + (si ^ 1)) * THT * QPF;
-      double wn[MV], Jn[MM];
+      const T* tn = PsiAtFP + (size_t)(dd * 2 + (si ^ 1)) * THT * QPF;
+      T wn[MV], Jn[MM];
       for (int j = 0; j < MV; ++j) wn[j] = dotcol<THT>(tn, QPF, q, Ws + (r2 * MV + j) * THT);
-      nlflux::dF<FLUX>(wn, dd, Jn, g);
-      const double a = alpha[region_face(r % 3, r / 3, dd, side)];
+      nlflux::dF<FLUX>(wn, dd, Jn, gT);
+      const T a = (T)alpha[region_face(r % 3, r / 3, dd, side)];
       // d F-hat / d w_L = (F'(w_L) + alpha I) / 2, d F-hat / d w_R = (F'(w_R) - alpha I) / 2,
       // times the outward sign of the face
       for (int i2 = 0; i2 < MV; ++i2)
         for (int j2 = 0; j2 < MV; ++j2) {
           const int ij = i2 * MV + j2;
-          const double dg = i2 == j2 ? a : 0.0;
-          const double go = side > 0 ? 0.5 * (Jo[ij] + dg) : -0.5 * (Jo[ij] - dg);
-          const double gn = side > 0 ? 0.5 * (Jn[ij] - dg) : -0.5 * (Jn[ij] + dg);
-          graw[(f * MM + ij) * QPF + q] = go;
-          graw[((4 + f) * MM + ij) * QPF + q] = gn;
+          const T dg = i2 == j2 ? a : T(0);
+          b0[(f * MM + ij) * QPF + q] = side > 0 ? T(0.5) * (Jo[ij] + dg) : T(-0.5) * (Jo[ij] - dg);
+          b0[((4 + f) * MM + ij) * QPF + q] = side > 0 ? T(0.5) * (Jn[ij] - dg) : T(-0.5) * (Jn[ij] + dg);
         }
     }
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < QP; q += kThreads) {
-    double w[MV], J[MM];
-    for (int j = 0; j < MV; ++j) w[j] = wp[j * QP + q];
-    for (int dd = 0; dd < 2; ++dd) {
-      nlflux::dF<FLUX>(w, dd, J, g);
-      for (int ij = 0; ij < MM; ++ij) bufA[(dd * MM + ij) * QP + q] = J[ij];
+  proj_pass<NP, 2>(b0, b1, P1, 8 * MM, 0);
+  __syncthreads();
+  proj_last<NP, 2, MM>(b1, FA, P1, 8, QPF, 2 * QP, sclf);
+  __syncthreads();
+}
+
+// Assemble the diagonal blocks of cells r0 .. r0 + CG - 1 and their blocks towards the
+// region neighbours from the merged lists (one pass over the lists for all CG cells).
+template <typename T, int NB, int MV>
+__device__ void assemble_cells(const NlDev& tb, const NlPlan& plan, int r0, const T* FA,
+                               T* slots) {
+  using D = Dims<NB, MV>;
+  constexpr int MM = D::MM, THT = D::THT, BP = D::BP, CG = D::CG, FAS = D::FAS;
+  const Ent<T>* dent = Tab<T>::dent(tb);
+  const T* Mt = Tab<T>::Mt(tb);
+  for (int i = threadIdx.x; i < THT * THT; i += kThreads) {
+    const int k = i / THT, l = i % THT;
+    T acc[CG][MM];
+#pragma unroll
+    for (int g = 0; g < CG; ++g)
+#pragma unroll
+      for (int ij = 0; ij < MM; ++ij) acc[g][ij] = T(0);
+    const int e1 = tb.dptr[i + 1];
+    for (int e = tb.dptr[i]; e < e1; ++e) {
+      const Ent<T> en = dent[e];
+      const T* v = FA + en.off * MM;
+#pragma unroll
+      for (int g = 0; g < CG; ++g)
+#pragma unroll
+        for (int ij = 0; ij < MM; ++ij) acc[g][ij] = fma(en.c, v[g * FAS + ij], acc[g][ij]);
+    }
+    if (k % D::THS == l % D::THS) {
+      const T mt = Mt[(k / D::THS) * NB + l / D::THS];
+#pragma unroll
+      for (int g = 0; g < CG; ++g)
+#pragma unroll
+        for (int j = 0; j < MV; ++j) acc[g][j * MV + j] += mt;
+    }
+#pragma unroll
+    for (int g = 0; g < CG; ++g) {
+      T* blk = slots + (size_t)plan.slot[(r0 + g) * 10] * BP * BP;
+#pragma unroll
+      for (int i2 = 0; i2 < MV; ++i2)
+#pragma unroll
+        for (int j2 = 0; j2 < MV; ++j2) blk[(size_t)(i2 * THT + k) * BP + j2 * THT + l] = acc[g][i2 * MV + j2];
     }
   }
-  __syncthreads();
-  proj_pass<NP, 3>(bufA, bufB, tb.P1, 2 * MM, 0);
-  proj_pass<NP, 2>(graw, gtmp, tb.P1, 8 * MM, 0);
-  __syncthreads();
-  proj_pass<NP, 3>(bufB, bufA, tb.P1, 2 * MM, 1);
-  proj_pass<NP, 2>(gtmp, graw, tb.P1, 8 * MM, 1);
-  __syncthreads();
-  proj_pass<NP, 3>(bufA, bufB, tb.P1, 2 * MM, 2);
-  __syncthreads();
-  const double* Fp = bufB;   // [2][MM][QP]
-  const double* Gp = graw;   // [8][MM][QPF]
-  // diagonal block: time term - volume term + own-side face terms
-  {
-    T* blk = slots + (size_t)plan.slot[r * 9 + r] * BP * BP;
-    int nbrs[4];
-    for (int f = 0; f < 4; ++f) nbrs[f] = region_nbr(r, f >> 1, (f & 1) ? -1 : 1);
+  for (int f = 0; f < 4; ++f) {
+    const int dd = f >> 1, side = (f & 1) ? -1 : 1;
+    const Ent<T>* oent = Tab<T>::oent(tb, f);
+    const int* optr = tb.optr[f];
     for (int i = threadIdx.x; i < THT * THT; i += kThreads) {
       const int k = i / THT, l = i % THT;
-      double acc[MM];
-      for (int ij = 0; ij < MM; ++ij) acc[ij] = 0.0;
-      for (int dd = 0; dd < 2; ++dd) {
-        const double s = -0.25 * lam[dd];
-        const int e1 = tb.bptr[dd][i + 1];
-        for (int e = tb.bptr[dd][i]; e < e1; ++e) {
-          const double v = s * tb.bval[dd][e];
-          const double* fp = Fp + dd * MM * QP + tb.bp[dd][e];
-          for (int ij = 0; ij < MM; ++ij) acc[ij] = fma(v, fp[ij * QP], acc[ij]);
-        }
+      T acc[CG][MM];
+#pragma unroll
+      for (int g = 0; g < CG; ++g)
+#pragma unroll
+        for (int ij = 0; ij < MM; ++ij) acc[g][ij] = T(0);
+      const int e1 = optr[i + 1];
+      for (int e = optr[i]; e < e1; ++e) {
+        const Ent<T> en = oent[e];
+        const T* v = FA + en.off * MM;
+#pragma unroll
+        for (int g = 0; g < CG; ++g)
+#pragma unroll
+          for (int ij = 0; ij < MM; ++ij) acc[g][ij] = fma(en.c, v[g * FAS + ij], acc[g][ij]);
       }
-      for (int f = 0; f < 4; ++f) {
-        const int dd = f >> 1, si = f & 1, gi = dd * 4 + si * 2 + si;
-        const double s = 0.25 * lam[dd];
-        const int e1 = tb.gptr[gi][i + 1];
-        for (int e = tb.gptr[gi][i]; e < e1; ++e) {
-          const double v = s * tb.gval[gi][e];
-          const double* gp = Gp + f * MM * QPF + tb.gp[gi][e];
-          for (int ij = 0; ij < MM; ++ij) acc[ij] = fma(v, gp[ij * QPF], acc[ij]);
-        }
-      }
-      if (k % D::THS == l % D::THS) {
-        const double mt = tb.Mt[(k / D::THS) * NB + l / D::THS];
-        for (int j = 0; j < MV; ++j) acc[j * MV + j] += mt;
-      }
-      for (int i2 = 0; i2 < MV; ++i2)
-        for (int j2 = 0; j2 < MV; ++j2)
-          blk[(size_t)(i2 * THT + k) * BP + j2 * THT + l] = (T)acc[i2 * MV + j2];
-    }
-    // blocks towards the region neighbours: neighbour-side face terms
-    for (int f = 0; f < 4; ++f) {
-      const int r2 = nbrs[f];
-      if (r2 < 0) continue;
-      const int dd = f >> 1, si = f & 1, gi = dd * 4 + si * 2 + (si ^ 1);
-      const double s = 0.25 * lam[dd];
-      T* ob = slots + (size_t)plan.slot[r * 9 + r2] * BP * BP;
-      for (int i = threadIdx.x; i < THT * THT; i += kThreads) {
-        const int k = i / THT, l = i % THT;
-        double acc[MM];
-        for (int ij = 0; ij < MM; ++ij) acc[ij] = 0.0;
-        const int e1 = tb.gptr[gi][i + 1];
-        for (int e = tb.gptr[gi][i]; e < e1; ++e) {
-          const double v = s * tb.gval[gi][e];
-          const double* gp = Gp + (4 + f) * MM * QPF + tb.gp[gi][e];
-          for (int ij = 0; ij < MM; ++ij) acc[ij] = fma(v, gp[ij * QPF], acc[ij]);
-        }
+#pragma unroll
+      for (int g = 0; g < CG; ++g) {
+        const int r = r0 + g, r2 = region_nbr(r, dd, side);
+        if (r2 < 0) continue;
+        T* blk = slots + (size_t)plan.slot[r * 9 + r2] * BP * BP;
+#pragma unroll
         for (int i2 = 0; i2 < MV; ++i2)
-          for (int j2 = 0; j2 < MV; ++j2)
-            ob[(size_t)(i2 * THT + k) * BP + j2 * THT + l] = (T)acc[i2 * MV + j2];
+#pragma unroll
+          for (int j2 = 0; j2 < MV; ++j2) blk[(size_t)(i2 * THT + k) * BP + j2 * THT + l] = acc[g][i2 * MV + j2];
       }
     }
   }
@@ -352,103 +451,183 @@ __device__ void jacobian_cell(const NlDev& tb, const NlPlan& plan, int r, const 
 }
 
 // ---------------------------------------------------------------------------------------
-// dense block kernels of the elimination (T), all BP x BP row-major with zero padding
+// dense block kernels of the elimination (T), all BP x BP row-major with zero padding.
+// The 256 threads form a 16 x 16 grid; thread (ty, tx) owns rows ty + 16 a and columns
+// tx + 16 b (a, b < RR) of a tile.
 // ---------------------------------------------------------------------------------------
-// In-place Gauss-Jordan inverse of the leading BS x BS part of S (row stride BP), partial
-// pivoting by rows; the row interchanges are undone on the columns at the end.
-template <typename T, int BS, int BP>
-__device__ void gauss_jordan(T* S, T* colf, int* perm, int* misc, int* flags) {
-  const int tid = threadIdx.x, lane = tid & 31;
+// Inverse of the leading BS x BS part of A (global) into S (shared, BP x BP, zero padding):
+// Gauss-Jordan on a register-resident copy with implicit row pivoting (the pivot of column
+// c is the largest remaining entry among the rows not yet used; no rows move), then the
+// order is restored while writing S: with prow[c] the row that pivoted column c and rank its
+// inverse permutation, inv[rank[i]][prow[j]] = R[i][j].
+template <typename T, int BS, int BP, int RR>
+__device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* used, int* prow, int* rank,
+                           int* flags) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
+  T a[RR][RR];
+#pragma unroll
+  for (int i = 0; i < RR; ++i)
+#pragma unroll
+    for (int j = 0; j < RR; ++j) a[i][j] = A[(size_t)(ty + 16 * i) * BP + tx + 16 * j];
+  for (int r = tid; r < BP; r += kThreads) used[r] = r < BS ? 0 : 1;
+  __syncthreads();
   for (int c = 0; c < BS; ++c) {
-    if (tid < 32) {
-      T best = T(-1);
-      int bi = c;
-      for (int i = c + lane; i < BS; i += 32) {
-        const T v = fabs(S[i * BP + c]);
-        if (v > best) {
-          best = v;
-          bi = i;
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) {
-          best = ov;
-          bi = oi;
-        }
-      }
-      if (lane == 0) {
-        misc[1] = bi;
-        perm[c] = bi;
-        if (!(best > T(0))) atomicOr(flags, kFlagSingular);
+    T* cv = colv + (c & 1) * BP;
+    T* rp = rowp + (c & 1) * BP;
+    const int cb = c >> 4;
+    if (tx == (c & 15)) {
+#pragma unroll
+      for (int i = 0; i < RR; ++i) {
+        T v = T(0);
+#pragma unroll
+        for (int j = 0; j < RR; ++j)
+          if (j == cb) v = a[i][j];
+        cv[ty + 16 * i] = v;
       }
     }
     __syncthreads();
-    const int p = misc[1];
-    if (p != c)
-      for (int j = tid; j < BS; j += kThreads) {
-        const T t = S[c * BP + j];
-        S[c * BP + j] = S[p * BP + j];
-        S[p * BP + j] = t;
-      }
-    __syncthreads();
-    for (int i = tid; i < BS; i += kThreads) colf[i] = S[i * BP + c];
-    __syncthreads();
-    const T ipiv = T(1) / colf[c];
-    for (int j = tid; j < BS; j += kThreads) S[c * BP + j] = j == c ? ipiv : S[c * BP + j] * ipiv;
-    __syncthreads();
-    for (int idx = tid; idx < BS * BS; idx += kThreads) {
-      const int i = idx / BS, j = idx % BS;
-      if (i != c) {
-        const T v = j == c ? T(0) : S[i * BP + j];
-        S[i * BP + j] = v - colf[i] * S[c * BP + j];
+    // pivot: largest |entry| of column c among unused rows, ties to the lower row (all
+    // warps find the same row); a NaN column still yields an unused row
+    T best = T(-1);
+    int bi = BS;
+    for (int r = lane; r < BS; r += 32) {
+      if (used[r]) continue;
+      const T v = fabs(cv[r]);
+      if (bi == BS || v > best) {
+        best = v;
+        bi = r;
       }
     }
-    __syncthreads();
-  }
-  for (int c = BS - 1; c >= 0; --c) {
-    const int p = perm[c];
-    if (p != c)
-      for (int i = tid; i < BS; i += kThreads) {
-        const T t = S[i * BP + c];
-        S[i * BP + c] = S[i * BP + p];
-        S[i * BP + p] = t;
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const bool take = oi < BS && (bi == BS || ov > best || (ov == best && oi < bi));
+      if (take) {
+        best = ov;
+        bi = oi;
       }
+    }
+    bi = __shfl_sync(0xffffffffu, bi, 0);
+    best = __shfl_sync(0xffffffffu, best, 0);
+    const int p = bi < BS ? bi : 0;
+    if (ty == (p & 15)) {
+      const int pa = p >> 4;
+#pragma unroll
+      for (int j = 0; j < RR; ++j) {
+        T v = T(0);
+#pragma unroll
+        for (int i = 0; i < RR; ++i)
+          if (i == pa) v = a[i][j];
+        rp[tx + 16 * j] = v;
+      }
+    }
+    if (tid == 0) {
+      prow[c] = p;
+      if (!(best > T(0))) atomicOr(flags, kFlagSingular);
+    }
     __syncthreads();
+    if (tid == 0) used[p] = 1;
+    const T ipiv = T(1) / cv[p];
+    T prs[RR];
+#pragma unroll
+    for (int j = 0; j < RR; ++j) {
+      const int cj = tx + 16 * j;
+      prs[j] = cj == c ? ipiv : rp[cj] * ipiv;
+    }
+#pragma unroll
+    for (int i = 0; i < RR; ++i) {
+      const int ri = ty + 16 * i;
+      const T f = cv[ri];
+      if (ri == p) {
+#pragma unroll
+        for (int j = 0; j < RR; ++j) a[i][j] = prs[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < RR; ++j) a[i][j] = ((tx + 16 * j) == c ? T(0) : a[i][j]) - f * prs[j];
+      }
+    }
   }
+  __syncthreads();
+  for (int c = tid; c < BS; c += kThreads) rank[prow[c]] = c;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < RR; ++i) {
+    const int ri = ty + 16 * i;
+    if (ri >= BS) continue;
+    const int rr = rank[ri];
+#pragma unroll
+    for (int j = 0; j < RR; ++j) {
+      const int cj = tx + 16 * j;
+      if (cj < BS) S[rr * BP + prow[cj]] = a[i][j];
+    }
+  }
+  if constexpr (BP > BS) {
+    for (int idx = tid; idx < (BP - BS) * BP; idx += kThreads) {
+      S[BS * BP + idx] = T(0);                                 // padding rows
+      S[(idx / (BP - BS)) * BP + BS + idx % (BP - BS)] = T(0);  // padding columns
+    }
+  }
+  __syncthreads();
 }
 
-// C = (overwrite ? 0 : C) - A B  (A, B, C in global memory)
-template <typename T, int BP, int RR>
+// C = (overwrite ? 0 : C) - A B  (all global); staging double-buffered when NBUF == 2
+template <typename T, int BP, int RR, int NBUF>
 __device__ void gemm_sub(T* C, const T* A, const T* B, bool overwrite, T* sA, T* sB) {
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  constexpr int NCH = BP / 16;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   T acc[RR][RR];
 #pragma unroll
   for (int a = 0; a < RR; ++a)
 #pragma unroll
     for (int b = 0; b < RR; ++b) acc[a][b] = T(0);
-  for (int k0 = 0; k0 < BP; k0 += 16) {
-    for (int i = threadIdx.x; i < BP * 16; i += kThreads) {
-      const int row = i >> 4, kk = i & 15;
-      sA[row * 17 + kk] = A[(size_t)row * BP + k0 + kk];
-      const int kr = i / BP, col = i % BP;
-      sB[kr * BP + col] = B[(size_t)(k0 + kr) * BP + col];
+  T pa[RR], pb[RR];
+  auto gload = [&](int ch) {
+#pragma unroll
+    for (int u = 0; u < RR; ++u) {
+      const int idx = tid + kThreads * u;
+      pa[u] = A[(size_t)(idx >> 4) * BP + ch * 16 + (idx & 15)];
+      pb[u] = B[(size_t)(ch * 16 + idx / BP) * BP + idx % BP];
     }
-    __syncthreads();
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < RR; ++u) {
+      const int idx = tid + kThreads * u;
+      sA[buf * BP * 17 + (idx >> 4) * 17 + (idx & 15)] = pa[u];
+      sB[buf * 16 * BP + idx] = pb[u];
+    }
+  };
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  for (int ch = 0; ch < NCH; ++ch) {
+    const int buf = NBUF == 2 ? (ch & 1) : 0;
+    if (NBUF == 2 && ch + 1 < NCH) gload(ch + 1);
+    const T* a0 = sA + buf * BP * 17;
+    const T* b0 = sB + buf * 16 * BP;
 #pragma unroll 4
     for (int kk = 0; kk < 16; ++kk) {
       T av[RR], bv[RR];
 #pragma unroll
-      for (int a = 0; a < RR; ++a) av[a] = sA[(ty + 16 * a) * 17 + kk];
+      for (int a = 0; a < RR; ++a) av[a] = a0[(ty + 16 * a) * 17 + kk];
 #pragma unroll
-      for (int b = 0; b < RR; ++b) bv[b] = sB[kk * BP + tx + 16 * b];
+      for (int b = 0; b < RR; ++b) bv[b] = b0[kk * BP + tx + 16 * b];
 #pragma unroll
       for (int a = 0; a < RR; ++a)
 #pragma unroll
         for (int b = 0; b < RR; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
     }
-    __syncthreads();
+    if (NBUF == 2) {
+      if (ch + 1 < NCH) sstore(buf ^ 1);
+      __syncthreads();
+    } else {
+      __syncthreads();
+      if (ch + 1 < NCH) {
+        gload(ch + 1);
+        sstore(0);
+        __syncthreads();
+      }
+    }
   }
 #pragma unroll
   for (int a = 0; a < RR; ++a)
@@ -457,94 +636,129 @@ __device__ void gemm_sub(T* C, const T* A, const T* B, bool overwrite, T* sA, T*
       T* c = C + (size_t)(ty + 16 * a) * BP + tx + 16 * b;
       *c = (overwrite ? T(0) : *c) - acc[a][b];
     }
-  __syncthreads();
 }
 
 // B = S B in place (S in shared memory, B in global memory)
-template <typename T, int BP, int RR>
+template <typename T, int BP, int RR, int NBUF>
 __device__ void gemm_left_inplace(const T* S, T* B, T* sB) {
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  constexpr int NCH = BP / 16;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   T acc[RR][RR];
 #pragma unroll
   for (int a = 0; a < RR; ++a)
 #pragma unroll
     for (int b = 0; b < RR; ++b) acc[a][b] = T(0);
-  for (int k0 = 0; k0 < BP; k0 += 16) {
-    for (int i = threadIdx.x; i < BP * 16; i += kThreads) {
-      const int kr = i / BP, col = i % BP;
-      sB[kr * BP + col] = B[(size_t)(k0 + kr) * BP + col];
+  T pb[RR];
+  auto gload = [&](int ch) {
+#pragma unroll
+    for (int u = 0; u < RR; ++u) {
+      const int idx = tid + kThreads * u;
+      pb[u] = B[(size_t)(ch * 16 + idx / BP) * BP + idx % BP];
     }
-    __syncthreads();
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < RR; ++u) sB[buf * 16 * BP + tid + kThreads * u] = pb[u];
+  };
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  for (int ch = 0; ch < NCH; ++ch) {
+    const int buf = NBUF == 2 ? (ch & 1) : 0;
+    if (NBUF == 2 && ch + 1 < NCH) gload(ch + 1);
+    const T* b0 = sB + buf * 16 * BP;
 #pragma unroll 4
     for (int kk = 0; kk < 16; ++kk) {
       T av[RR], bv[RR];
 #pragma unroll
-      for (int a = 0; a < RR; ++a) av[a] = S[(ty + 16 * a) * BP + k0 + kk];
+      for (int a = 0; a < RR; ++a) av[a] = S[(ty + 16 * a) * BP + ch * 16 + kk];
 #pragma unroll
-      for (int b = 0; b < RR; ++b) bv[b] = sB[kk * BP + tx + 16 * b];
+      for (int b = 0; b < RR; ++b) bv[b] = b0[kk * BP + tx + 16 * b];
 #pragma unroll
       for (int a = 0; a < RR; ++a)
 #pragma unroll
         for (int b = 0; b < RR; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
     }
-    __syncthreads();
+    if (NBUF == 2) {
+      if (ch + 1 < NCH) sstore(buf ^ 1);
+      __syncthreads();
+    } else {
+      __syncthreads();
+      if (ch + 1 < NCH) {
+        gload(ch + 1);
+        sstore(0);
+        __syncthreads();
+      }
+    }
   }
 #pragma unroll
   for (int a = 0; a < RR; ++a)
 #pragma unroll
     for (int b = 0; b < RR; ++b) B[(size_t)(ty + 16 * a) * BP + tx + 16 * b] = acc[a][b];
-  __syncthreads();
 }
 
-// y -= M x for the first BS rows (M global, x and y shared); one warp per row
+// y -= M x for the first BS rows (M global or shared, x and y shared): each warp takes 4
+// rows at a time, so that every lane has 4 independent loads per column stride in flight
 template <typename T, int BS, int BP>
 __device__ void matvec_sub(const T* M, const T* x, T* y) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = warp; r < BS; r += kThreads / 32) {
-    T s = T(0);
-    for (int c = lane; c < BS; c += 32) s = fma(M[(size_t)r * BP + c], x[c], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) y[r] -= s;
+  for (int r0 = warp * 4; r0 < BS; r0 += 4 * (kThreads / 32)) {
+    T s[4] = {T(0), T(0), T(0), T(0)};
+    for (int c = lane; c < BS; c += 32) {
+      const T xv = x[c];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (r0 + u < BS) s[u] = fma(M[(size_t)(r0 + u) * BP + c], xv, s[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      for (int o = 16; o > 0; o >>= 1) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
+    if (lane < 4 && r0 + lane < BS) {
+      T v = s[0];
+#pragma unroll
+      for (int u = 1; u < 4; ++u)
+        if (lane == u) v = s[u];
+      y[r0 + lane] -= v;
+    }
   }
   __syncthreads();
 }
 
 // Solve J x = b by block elimination in the plan's order; b in xs (9 x BP), x returned there.
-template <typename T, int BS, int BP, int RR>
-__device__ void block_solve(T* slots, const NlPlan& plan, T* xs, T* S, T* sA, T* sB, T* colf,
-                            int* perm, int* misc, int* flags) {
+template <typename T, int BS, int BP, int RR, int NBUF>
+__device__ void block_solve(T* slots, const NlPlan& plan, T* xs, T* S, T* sA, T* sB, T* colv,
+                            T* rowp, int* used, int* prow, int* rank, int* flags) {
   const int tid = threadIdx.x;
   for (int t = 0; t < 9; ++t) {
     const int k = plan.order[t];
-    const T* Akk = slots + (size_t)plan.slot[k * 9 + k] * BP * BP;
-    for (int i = tid; i < BP * BP; i += kThreads) S[i] = Akk[i];
-    __syncthreads();
-    gauss_jordan<T, BS, BP>(S, colf, perm, misc, flags);
+    gj_inverse<T, BS, BP, RR>(slots + (size_t)plan.slot[k * 10] * BP * BP, S, colv, rowp, used,
+                              prow, rank, flags);
+    // x_k <- S x_k (via a zeroed copy: y = x - S x computed as 0 - (-S) x is avoided by
+    // writing the product straight into colv)
     T* xk = xs + k * BP;
-    if (tid < BS) {
-      T acc = T(0);
-      for (int c = 0; c < BS; ++c) acc = fma(S[tid * BP + c], xk[c], acc);
-      colf[tid] = acc;
-    }
+    for (int i = tid; i < BP; i += kThreads) colv[i] = T(0);
     __syncthreads();
-    if (tid < BS) xk[tid] = colf[tid];
+    matvec_sub<T, BS, BP>(S, xk, colv);  // colv = -S x_k
+    for (int i = tid; i < BS; i += kThreads) xk[i] = -colv[i];
     __syncthreads();
     const int nn = plan.nn[t];
     for (int a = 0; a < nn; ++a) {
       const int j = plan.nbr[t][a];
-      gemm_left_inplace<T, BP, RR>(S, slots + (size_t)plan.slot[k * 9 + j] * BP * BP, sB);
+      gemm_left_inplace<T, BP, RR, NBUF>(S, slots + (size_t)plan.slot[k * 9 + j] * BP * BP, sB);
     }
+    __syncthreads();
     for (int a = 0; a < nn; ++a) {
       const int i = plan.nbr[t][a];
       const T* Aik = slots + (size_t)plan.slot[i * 9 + k] * BP * BP;
       matvec_sub<T, BS, BP>(Aik, xk, xs + i * BP);
       for (int b = 0; b < nn; ++b) {
         const int j = plan.nbr[t][b];
-        gemm_sub<T, BP, RR>(slots + (size_t)plan.slot[i * 9 + j] * BP * BP, Aik,
-                            slots + (size_t)plan.slot[k * 9 + j] * BP * BP, plan.first[t][a][b] != 0,
-                            sA, sB);
+        gemm_sub<T, BP, RR, NBUF>(slots + (size_t)plan.slot[i * 9 + j] * BP * BP, Aik,
+                                  slots + (size_t)plan.slot[k * 9 + j] * BP * BP,
+                                  plan.first[t][a][b] != 0, sA, sB);
       }
     }
+    __syncthreads();
   }
   for (int t = 8; t >= 0; --t) {
     const int k = plan.order[t];
@@ -569,10 +783,17 @@ __global__ void __launch_bounds__(kThreads, 1) newton_kernel(const NewtonArgs a)
   double* alpha = (double*)(smem + L::oAl);
   double* red = (double*)(smem + L::oRed);
   T* xs = (T*)(smem + L::oX);
-  T* colf = (T*)(smem + L::oCol);
-  int* perm = (int*)(smem + L::oPerm);
+  T* colv = (T*)(smem + L::oCol);
+  T* rowp = (T*)(smem + L::oRow);
+  int* used = (int*)(smem + L::oUsed);
+  int* prow = (int*)(smem + L::oProw);
+  int* rank = (int*)(smem + L::oRank);
   int* misc = (int*)(smem + L::oMisc);
   unsigned char* arena = smem + L::oArena;
+  T* FA = (T*)arena;
+  T* jw = (T*)(arena + L::oJW);
+  T* jb0 = (T*)(arena + L::oJB0);
+  T* jb1 = (T*)(arena + L::oJB1);
   T* S = (T*)arena;
   T* sA = (T*)(arena + L::oSA);
   T* sB = (T*)(arena + L::oSB);
@@ -604,15 +825,19 @@ __global__ void __launch_bounds__(kThreads, 1) newton_kernel(const NewtonArgs a)
     bool conv = false, bad = false;
     while (it < a.max_iters && !conv && !bad) {
       residual<NB, MV, FLUX>(a.tb, Ws, Qs, Rs, alpha, (double*)arena, a.lam, a.gamma);
-      for (int r = 0; r < 9; ++r)
-        jacobian_cell<T, NB, MV, FLUX>(a.tb, a.plan, r, Ws, alpha, (double*)arena, slots, a.lam,
-                                       a.gamma);
+      for (int r0 = 0; r0 < 9; r0 += D::CG) {
+        for (int g = 0; g < D::CG; ++g)
+          project_cell<T, NB, MV, FLUX>(a.tb, r0 + g, Ws, alpha, FA + g * D::FAS, jw, jb0, jb1,
+                                        a.lam, a.gamma);
+        assemble_cells<T, NB, MV>(a.tb, a.plan, r0, FA, slots);
+      }
       for (int i = tid; i < 9 * D::BP; i += kThreads) {
         const int r = i / D::BP, c = i % D::BP;
         xs[i] = c < D::BS ? (T)Rs[r * D::BS + c] : T(0);
       }
       __syncthreads();
-      block_solve<T, D::BS, D::BP, D::RR>(slots, a.plan, xs, S, sA, sB, colf, perm, misc, flags);
+      block_solve<T, D::BS, D::BP, D::RR, L::NBUF>(slots, a.plan, xs, S, sA, sB, colv, rowp,
+                                                   used, prow, rank, flags);
       double dn = 0.0, wn = 0.0;
       bool fin = true;
       for (int i = tid; i < 9 * D::BS; i += kThreads) {
@@ -634,6 +859,7 @@ __global__ void __launch_bounds__(kThreads, 1) newton_kernel(const NewtonArgs a)
     if (tid == 0) {
       if (!conv) atomicAdd(&a.stats[0], 1);
       atomicMax(&a.stats[1], it);
+      atomicAdd(a.iters_total, (unsigned long long)it);
       if (bad) atomicOr(flags, kFlagNonFinite);
     }
     __syncthreads();

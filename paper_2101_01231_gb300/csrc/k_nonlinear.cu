@@ -69,6 +69,40 @@ int nl_tables_upload(int nb, NlDevTables& out, void* mem, size_t* bytes, cudaStr
         ig[g][1] = addi(G.p);
         ig[g][2] = addd(G.val);
       }
+  // merged assembly lists, packed per precision
+  NlAsmLists L = build_asm_lists(t);
+  struct EntD { int off; int pad; double c; };
+  struct EntF { int off; float c; };
+  auto packd = [](const std::vector<int>& o, const std::vector<double>& v) {
+    std::vector<EntD> e(o.size());
+    for (size_t i = 0; i < o.size(); ++i) e[i] = {o[i], 0, v[i]};
+    return e;
+  };
+  auto packf = [](const std::vector<int>& o, const std::vector<double>& v) {
+    std::vector<EntF> e(o.size());
+    for (size_t i = 0; i < o.size(); ++i) e[i] = {o[i], (float)v[i]};
+    return e;
+  };
+  std::vector<EntD> dd_ = packd(L.doff, L.dval);
+  std::vector<EntF> df_ = packf(L.doff, L.dval);
+  std::vector<EntD> od_[4];
+  std::vector<EntF> of_[4];
+  for (int f = 0; f < 4; ++f) {
+    od_[f] = packd(L.ooff[f], L.oval[f]);
+    of_[f] = packf(L.ooff[f], L.oval[f]);
+  }
+  const size_t idptr = addi(L.dptr), identd = add(dd_.data(), dd_.size() * sizeof(EntD)),
+               identf = add(df_.data(), df_.size() * sizeof(EntF));
+  size_t ioptr[4], ioentd[4], ioentf[4];
+  for (int f = 0; f < 4; ++f) {
+    ioptr[f] = addi(L.optr[f]);
+    ioentd[f] = add(od_[f].data(), od_[f].size() * sizeof(EntD));
+    ioentf[f] = add(of_[f].data(), of_[f].size() * sizeof(EntF));
+  }
+  auto tof = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+  std::vector<float> Mtf = tof(t.Mt), PsiAtPf = tof(t.PsiAtP), PsiAtFPf = tof(t.PsiAtFP), P1f = tof(t.P1);
+  const size_t iMtf = add(Mtf.data(), Mtf.size() * 4), iPsiAtPf = add(PsiAtPf.data(), PsiAtPf.size() * 4),
+               iPsiAtFPf = add(PsiAtFPf.data(), PsiAtFPf.size() * 4), iP1f = add(P1f.data(), P1f.size() * 4);
   const size_t total = (off + 255) & ~(size_t)255;
   if (!mem) {
     *bytes = total;
@@ -107,6 +141,19 @@ int nl_tables_upload(int nb, NlDevTables& out, void* mem, size_t* bytes, cudaStr
     tb.gp[g] = I(ig[g][1]);
     tb.gval[g] = D(ig[g][2]);
   }
+  tb.dptr = I(idptr);
+  tb.dent_d = base + pieces[identd].off;
+  tb.dent_f = base + pieces[identf].off;
+  for (int f = 0; f < 4; ++f) {
+    tb.optr[f] = I(ioptr[f]);
+    tb.oent_d[f] = base + pieces[ioentd[f]].off;
+    tb.oent_f[f] = base + pieces[ioentf[f]].off;
+  }
+  auto F = [&](size_t i) { return (const float*)(base + pieces[i].off); };
+  tb.Mt_f = F(iMtf);
+  tb.PsiAtP_f = F(iPsiAtPf);
+  tb.PsiAtFP_f = F(iPsiAtFPf);
+  tb.P1_f = F(iP1f);
   out.mem = mem;
   out.bytes = total;
   return RIDG_OK;

@@ -235,6 +235,43 @@ NlHostTables build_nl_tables(int M) {
   return t;
 }
 
+NlAsmLists build_asm_lists(const NlHostTables& t) {
+  NlAsmLists L;
+  const int npair = t.thT * t.thT;
+  L.dptr.assign(1, 0);
+  for (int kl = 0; kl < npair; ++kl) {
+    for (int d = 0; d < 2; ++d) {
+      const SparseTriple& B = t.beta[d];
+      for (int e = B.ptr[kl]; e < B.ptr[kl + 1]; ++e) {
+        L.doff.push_back(d * t.QP + B.p[e]);
+        L.dval.push_back(B.val[e]);
+      }
+    }
+    for (int f = 0; f < 4; ++f) {
+      const int d = f >> 1, si = f & 1;
+      const SparseTriple& G = t.gamma[d][si][si];
+      for (int e = G.ptr[kl]; e < G.ptr[kl + 1]; ++e) {
+        L.doff.push_back(2 * t.QP + f * t.QPf + G.p[e]);
+        L.dval.push_back(G.val[e]);
+      }
+    }
+    L.dptr.push_back((int)L.doff.size());
+  }
+  for (int f = 0; f < 4; ++f) {
+    const int d = f >> 1, si = f & 1;
+    const SparseTriple& G = t.gamma[d][si][si ^ 1];
+    L.optr[f].assign(1, 0);
+    for (int kl = 0; kl < npair; ++kl) {
+      for (int e = G.ptr[kl]; e < G.ptr[kl + 1]; ++e) {
+        L.ooff[f].push_back(2 * t.QP + (4 + f) * t.QPf + G.p[e]);
+        L.oval[f].push_back(G.val[e]);
+      }
+      L.optr[f].push_back((int)L.ooff[f].size());
+    }
+  }
+  return L;
+}
+
 // ---------------------------------------------------------------------------------------
 // elimination plan
 // ---------------------------------------------------------------------------------------

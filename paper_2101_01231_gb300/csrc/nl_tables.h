@@ -37,4 +37,18 @@ struct NlHostTables {
 // Build the tables for degree M in 2D.
 NlHostTables build_nl_tables(int M);
 
+// The Jacobian's triple-product lists merged per (k, l) pair for assembly.  The diagonal
+// block of a region cell takes, for every pair, the volume lists of both directions and the
+// own-side face lists of its four faces; an entry is (offset, coefficient) with the offset
+// (in units of m x m matrices) into the cell's projected arrays laid out as
+//   [F'_x (QP) | F'_y (QP) | own face 0..3 (QPf each) | neighbour face 0..3 (QPf each)].
+// The block towards the neighbour across face f takes the neighbour-side list of face f.
+struct NlAsmLists {
+  std::vector<int> dptr, doff;
+  std::vector<double> dval;
+  std::vector<int> optr[4], ooff[4];
+  std::vector<double> oval[4];
+};
+NlAsmLists build_asm_lists(const NlHostTables& t);
+
 }  // namespace ridg

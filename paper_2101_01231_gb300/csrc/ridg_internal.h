@@ -84,6 +84,14 @@ struct NlDev {
   const double* bval[2];
   const int *gptr[8], *gp[8];           // face lists, index dd * 4 + side_k * 2 + side_l
   const double* gval[8];
+  // merged assembly lists (nl_tables.h) with packed entries: {int offset; int pad; double c}
+  // for FP64 assembly, {int offset; float c} for FP32 assembly
+  const int* dptr;
+  const void *dent_d, *dent_f;
+  const int* optr[4];
+  const void *oent_d[4], *oent_f[4];
+  // FP32 copies of the projection tables and the time term (FP32 assembly)
+  const float *Mt_f, *PsiAtP_f, *PsiAtFP_f, *P1_f;
 };
 // Block elimination plan for the 3 x 3 region: blocks are eliminated corners first, then the
 // edge cells, then the centre; each pivot's later neighbours and the fill they create.
@@ -123,6 +131,7 @@ struct NewtonArgs {
   size_t scratch_per_cta;
   int* counter;      // work counter (zeroed before the launch)
   int* stats;        // [0] unconverged regions, [1] largest iteration count, [2] flags
+  unsigned long long* iters_total;  // Newton iterations summed over regions
 };
 cudaError_t launch_newton(int nb, int m, int flux_kind, bool fp32, const NewtonArgs& a, int grid,
                           cudaStream_t s);
@@ -186,7 +195,9 @@ struct ridg_handle {
   void* nl_scratch = nullptr;
   size_t nl_scratch_cta = 0;
   int nl_grid = 0;
-  int* nl_words = nullptr;  // [0] work counter, [1..3] Newton statistics, [4..5] max speed bits
+  int* nl_words = nullptr;  // [0] work counter, [1..3] Newton statistics, [4..5] max speed
+                            // bits, [6..7] total Newton iterations
+  long long newton_iters_total = 0;
   // Newton statistics of the last prediction
   long long newton_unconverged = 0;
   int newton_iters_max = 0;

@@ -42,7 +42,8 @@ class ridg_info_t(C.Structure):
     _fields_ = [("dim", C.c_int), ("order", C.c_int), ("m", C.c_int), ("theta_s", C.c_int),
                 ("theta_t", C.c_int), ("cells", C.c_longlong), ("dt", C.c_double),
                 ("t", C.c_double), ("steps", C.c_longlong), ("newton_unconverged", C.c_longlong),
-                ("newton_iters_max", C.c_int), ("precision", C.c_int), ("slices", C.c_int)]
+                ("newton_iters_max", C.c_int), ("precision", C.c_int), ("slices", C.c_int),
+                ("newton_iters_total", C.c_longlong)]
 
 
 class ridg_profile_t(C.Structure):
