@@ -388,7 +388,7 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
     ridg::nl_tables_upload(h->nb, h->nl, nullptr, &tb_bytes, h->stream);
     void* tb_mem = dev_alloc(h, tb_bytes);
     h->plan = ridg::build_elim_plan();
-    h->nl_grid = ridg::newton_grid(h->nb, h->m, h->opt.precision == RIDG_PREC_MIXED_FP32);
+    h->nl_grid = ridg::newton_grid(h->nb, h->m, h->flux.kind, h->opt.precision == RIDG_PREC_MIXED_FP32);
     h->nl_scratch_cta = ridg::newton_scratch_per_cta(h->nb, h->m,
                                                      h->opt.precision == RIDG_PREC_MIXED_FP32, h->plan);
     const size_t scratch = h->nl_scratch_cta * (size_t)h->nl_grid;

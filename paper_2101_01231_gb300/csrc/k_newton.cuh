@@ -98,8 +98,7 @@ struct Layout {
   static constexpr size_t oX = up16(oRed + sizeof(double) * 32);
   static constexpr size_t oCol = up16(oX + sizeof(T) * 9 * D::BP);
   static constexpr size_t oRow = up16(oCol + sizeof(T) * 2 * D::BP);
-  static constexpr size_t oUsed = up16(oRow + sizeof(T) * 2 * D::BP);
-  static constexpr size_t oProw = up16(oUsed + sizeof(int) * D::BP);
+  static constexpr size_t oProw = up16(oRow + sizeof(T) * 2 * D::BP);
   static constexpr size_t oRank = up16(oProw + sizeof(int) * D::BP);
   static constexpr size_t oMisc = up16(oRank + sizeof(int) * D::BP);
   static constexpr size_t oArena = up16(oMisc + sizeof(int) * 16);
@@ -114,6 +113,8 @@ struct Layout {
   static constexpr size_t oSB = up16(oSA + sizeof(T) * NBUF * D::BP * 17);
   static constexpr size_t aLU = up16(oSB + sizeof(T) * NBUF * 16 * D::BP);
   static constexpr size_t bytes = oArena + cmax(cmax(aRes, aAlpha), cmax(aJac, aLU));
+  // CTAs per SM: two where their shared memory fits (FP32 solves), else one
+  static constexpr int MINB = (sizeof(T) == 4 && 2 * (bytes + 1024) <= 233472) ? 2 : 1;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -460,17 +461,53 @@ __device__ void assemble_cells(const NlDev& tb, const NlPlan& plan, int r0, cons
 // c is the largest remaining entry among the rows not yet used; no rows move), then the
 // order is restored while writing S: with prow[c] the row that pivoted column c and rank its
 // inverse permutation, inv[rank[i]][prow[j]] = R[i][j].
+template <typename T>
+__device__ __forceinline__ T recip(T x);
+template <>
+__device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
+template <>
+__device__ __forceinline__ double recip<double>(double x) { return __drcp_rn(x); }
+
+// Largest |v| over the lanes' candidates (valid != 0), ties to the lower row; the same result
+// in every lane.  The magnitude's bit pattern orders like its value (v >= 0).
+__device__ __forceinline__ int warp_argmax(float v, int row, bool valid, bool* zero) {
+  const unsigned key = valid ? (__float_as_uint(v) | 0x80000000u) : 0u;
+  const unsigned m = __reduce_max_sync(0xffffffffu, key);
+  const unsigned p = __reduce_min_sync(0xffffffffu, key == m && valid ? (unsigned)row : 0xffffffffu);
+  *zero = (m & 0x7fffffffu) == 0u;
+  return (int)p;
+}
+__device__ __forceinline__ int warp_argmax(double v, int row, bool valid, bool* zero) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = valid ? ((unsigned)(b >> 32) | 0x80000000u) : 0u, lo = (unsigned)b;
+  const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+  const bool h = valid && hi == mh;
+  const unsigned ml = __reduce_max_sync(0xffffffffu, h ? lo : 0u);
+  const unsigned p = __reduce_min_sync(0xffffffffu, h && lo == ml ? (unsigned)row : 0xffffffffu);
+  *zero = (mh & 0x7fffffffu) == 0u && ml == 0u;
+  return (int)p;
+}
+
+// Inverse of the leading BS x BS part of A (global) into S (shared, BP x BP, zero padding):
+// Gauss-Jordan on a register-resident copy with implicit row pivoting (the pivot of column
+// c is the largest remaining entry among the rows not yet used; no rows move), then the
+// order is restored while writing S: with prow[c] the row that pivoted column c and rank its
+// inverse permutation, inv[rank[i]][prow[j]] = R[i][j].  Every warp finds the pivot itself
+// (each lane keeps the used flags of its rows lane + 32 k in a bit mask), so a column costs
+// two barriers: after its entries are published and after the pivot row is.
 template <typename T, int BS, int BP, int RR>
-__device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* used, int* prow, int* rank,
-                           int* flags) {
+__device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* prow, int* rank, int* flags) {
+  constexpr int NK = (BS + 31) / 32;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
   T a[RR][RR];
 #pragma unroll
   for (int i = 0; i < RR; ++i)
 #pragma unroll
     for (int j = 0; j < RR; ++j) a[i][j] = A[(size_t)(ty + 16 * i) * BP + tx + 16 * j];
-  for (int r = tid; r < BP; r += kThreads) used[r] = r < BS ? 0 : 1;
-  __syncthreads();
+  unsigned umask = 0u;
+#pragma unroll
+  for (int k = 0; k < NK; ++k)
+    if (lane + 32 * k >= BS) umask |= 1u << k;
   for (int c = 0; c < BS; ++c) {
     T* cv = colv + (c & 1) * BP;
     T* rp = rowp + (c & 1) * BP;
@@ -486,30 +523,23 @@ __device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* used, int* p
       }
     }
     __syncthreads();
-    // pivot: largest |entry| of column c among unused rows, ties to the lower row (all
-    // warps find the same row); a NaN column still yields an unused row
-    T best = T(-1);
-    int bi = BS;
-    for (int r = lane; r < BS; r += 32) {
-      if (used[r]) continue;
-      const T v = fabs(cv[r]);
-      if (bi == BS || v > best) {
+    T best = T(0);
+    int bi = 0;
+    bool have = false;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      if ((umask >> k) & 1u) continue;
+      const T v = fabs(cv[lane + 32 * k]);
+      if (!have || v > best) {
         best = v;
-        bi = r;
+        bi = lane + 32 * k;
+        have = true;
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      const bool take = oi < BS && (bi == BS || ov > best || (ov == best && oi < bi));
-      if (take) {
-        best = ov;
-        bi = oi;
-      }
-    }
-    bi = __shfl_sync(0xffffffffu, bi, 0);
-    best = __shfl_sync(0xffffffffu, best, 0);
-    const int p = bi < BS ? bi : 0;
+    bool zero = false;
+    int p = warp_argmax(best, bi, have, &zero);
+    if (p >= BS) p = 0;  // unreachable: an unused row is always left
+    if ((p & 31) == lane) umask |= 1u << (p >> 5);
     if (ty == (p & 15)) {
       const int pa = p >> 4;
 #pragma unroll
@@ -523,11 +553,10 @@ __device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* used, int* p
     }
     if (tid == 0) {
       prow[c] = p;
-      if (!(best > T(0))) atomicOr(flags, kFlagSingular);
+      if (zero) atomicOr(flags, kFlagSingular);
     }
     __syncthreads();
-    if (tid == 0) used[p] = 1;
-    const T ipiv = T(1) / cv[p];
+    const T ipiv = recip(cv[p]);
     T prs[RR];
 #pragma unroll
     for (int j = 0; j < RR; ++j) {
@@ -727,12 +756,12 @@ __device__ void matvec_sub(const T* M, const T* x, T* y) {
 // Solve J x = b by block elimination in the plan's order; b in xs (9 x BP), x returned there.
 template <typename T, int BS, int BP, int RR, int NBUF>
 __device__ void block_solve(T* slots, const NlPlan& plan, T* xs, T* S, T* sA, T* sB, T* colv,
-                            T* rowp, int* used, int* prow, int* rank, int* flags) {
+                            T* rowp, int* prow, int* rank, int* flags) {
   const int tid = threadIdx.x;
   for (int t = 0; t < 9; ++t) {
     const int k = plan.order[t];
-    gj_inverse<T, BS, BP, RR>(slots + (size_t)plan.slot[k * 10] * BP * BP, S, colv, rowp, used,
-                              prow, rank, flags);
+    gj_inverse<T, BS, BP, RR>(slots + (size_t)plan.slot[k * 10] * BP * BP, S, colv, rowp, prow,
+                              rank, flags);
     // x_k <- S x_k (via a zeroed copy: y = x - S x computed as 0 - (-S) x is avoided by
     // writing the product straight into colv)
     T* xk = xs + k * BP;
@@ -773,7 +802,7 @@ __device__ void block_solve(T* slots, const NlPlan& plan, T* xs, T* S, T* sA, T*
 // the kernel
 // ---------------------------------------------------------------------------------------
 template <typename T, int NB, int MV, int FLUX>
-__global__ void __launch_bounds__(kThreads, 1) newton_kernel(const NewtonArgs a) {
+__global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV>::MINB)) newton_kernel(const NewtonArgs a) {
   using D = Dims<NB, MV>;
   using L = Layout<T, NB, MV>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -785,7 +814,6 @@ __global__ void __launch_bounds__(kThreads, 1) newton_kernel(const NewtonArgs a)
   T* xs = (T*)(smem + L::oX);
   T* colv = (T*)(smem + L::oCol);
   T* rowp = (T*)(smem + L::oRow);
-  int* used = (int*)(smem + L::oUsed);
   int* prow = (int*)(smem + L::oProw);
   int* rank = (int*)(smem + L::oRank);
   int* misc = (int*)(smem + L::oMisc);
@@ -837,7 +865,7 @@ __global__ void __launch_bounds__(kThreads, 1) newton_kernel(const NewtonArgs a)
       }
       __syncthreads();
       block_solve<T, D::BS, D::BP, D::RR, L::NBUF>(slots, a.plan, xs, S, sA, sB, colv, rowp,
-                                                   used, prow, rank, flags);
+                                                   prow, rank, flags);
       double dn = 0.0, wn = 0.0;
       bool fin = true;
       for (int i = tid; i < 9 * D::BS; i += kThreads) {
@@ -877,6 +905,40 @@ cudaError_t launch_one(const NewtonArgs& a, int grid, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   newton_kernel<T, NB, MV, FLUX><<<grid, kThreads, L::bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T, int NB, int MV, int FLUX>
+int ctas_one() {
+  using L = Layout<T, NB, MV>;
+  if (cudaFuncSetAttribute(newton_kernel<T, NB, MV, FLUX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)L::bytes) != cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, newton_kernel<T, NB, MV, FLUX>, kThreads,
+                                                    L::bytes) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+// resident CTAs per SM of the Newton kernel for (nb, m, flux), 0 if unsupported
+template <typename T>
+int ctas_per_sm(int nb, int m, int kind) {
+  if (kind == RIDG_FLUX_BURGERS && m == 1) {
+    switch (nb) {
+      case 2: return ctas_one<T, 2, 1, RIDG_FLUX_BURGERS>();
+      case 3: return ctas_one<T, 3, 1, RIDG_FLUX_BURGERS>();
+      case 4: return ctas_one<T, 4, 1, RIDG_FLUX_BURGERS>();
+      case 5: return ctas_one<T, 5, 1, RIDG_FLUX_BURGERS>();
+      default: break;
+    }
+  } else if (kind == RIDG_FLUX_EULER && m == 4) {
+    switch (nb) {
+      case 2: return ctas_one<T, 2, 4, RIDG_FLUX_EULER>();
+      case 3: return ctas_one<T, 3, 4, RIDG_FLUX_EULER>();
+      default: break;
+    }
+  }
+  return 0;
 }
 
 template <typename T>

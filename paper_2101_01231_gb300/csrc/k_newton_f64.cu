@@ -6,4 +6,5 @@ cudaError_t launch_newton_f64(int nb, int m, int kind, const NewtonArgs& a, int 
                               cudaStream_t s) {
   return newton::launch_typed<double>(nb, m, kind, a, grid, s);
 }
+int newton_ctas_per_sm_f64(int nb, int m, int kind) { return newton::ctas_per_sm<double>(nb, m, kind); }
 }  // namespace ridg

@@ -307,12 +307,16 @@ cudaError_t launch_newton_f32(int nb, int m, int kind, const NewtonArgs& a, int 
 
 bool newton_supported(int nb, int m) { return (m == 1 && nb >= 2 && nb <= 5) || (m == 4 && nb >= 2 && nb <= 3); }
 
-int newton_grid(int, int, bool) {
+int newton_ctas_per_sm_f64(int nb, int m, int kind);
+int newton_ctas_per_sm_f32(int nb, int m, int kind);
+
+int newton_grid(int nb, int m, int kind, bool fp32) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
     return 0;
-  return sms;  // one CTA per SM (the kernel's shared memory allows no more)
+  const int per = fp32 ? newton_ctas_per_sm_f32(nb, m, kind) : newton_ctas_per_sm_f64(nb, m, kind);
+  return per > 0 ? per * sms : 0;  // a persistent grid: every resident CTA slot filled once
 }
 
 size_t newton_scratch_per_cta(int nb, int m, bool fp32, const NlPlan& plan) {

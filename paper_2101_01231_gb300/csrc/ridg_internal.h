@@ -114,7 +114,7 @@ struct NlDevTables {
 int nl_tables_upload(int nb, NlDevTables& out, void* mem, size_t* bytes, cudaStream_t s);
 bool newton_supported(int nb, int m);
 // CTAs of the persistent Newton kernel and the scratch each needs (bytes)
-int newton_grid(int nb, int m, bool fp32);
+int newton_grid(int nb, int m, int flux_kind, bool fp32);
 size_t newton_scratch_per_cta(int nb, int m, bool fp32, const NlPlan& plan);
 struct NewtonArgs {
   NlDev tb;
