@@ -43,6 +43,8 @@ def _args():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--newton-steps", type=int, default=1,
+                   help="timed steps of the Newton path (0: skip it)")
     return p.parse_args()
 
 
@@ -118,6 +120,69 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------------
+# the Newton path (nonlinear flux)
+# ---------------------------------------------------------------------------------------
+NL_WORKLOAD = "euler2d_n512_q2"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA pipes x 2 flop x max SM clock
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # FP64 FMA: 2 per clock per SM
+
+
+def newton_section(R, I, steps, cpu_cells):
+    """The Newton prediction + correction of the 2D Euler vortex (512 x 512, Q2, m = 4): FP32
+    Jacobian / solves with the FP64 residual at full size, FP64 solves on a 128 x 128 mesh of
+    the same problem, and the oracle on a sample of cells (extrapolated per step)."""
+    from oracle import nonlinear as ONL
+    out = {"workload": NL_WORKLOAD}
+    for tag, mesh, prec, peak in (("mixed_fp32", None, R.RIDG_PREC_MIXED_FP32, FP32_PEAK_TFLOPS),
+                                  ("fp64_128x128", (128, 128), R.RIDG_PREC_FP64, FP64_PEAK_TFLOPS)):
+        w = I.workload(NL_WORKLOAD, **({"n": mesh} if mesh else {}))
+        s = R.Solver(2, w["n"], w["M"], flux="euler", cfl=w["cfl"], lo=w["lo"], hi=w["hi"],
+                     gamma=w["gamma"], precision=prec)
+        q = I.initial_state(w)
+        s.set_state(q)
+        s.profile_step(1)                        # warm-up
+        p = s.profile_step(steps)
+        info = s.info()
+        s.close()
+        cells = int(np.prod(w["n"]))
+        bs = 4 * (w["M"] + 1) ** 3               # unknowns of one region cell (m theta_T)
+        iters = info["newton_iters_total"] / steps
+        # algorithmic work of the block elimination (3 x 3 region, corners - edges - centre):
+        # 9 block LUs (2/3 b^3), 17 block solves and 39 block updates (2 b^3 each) = 118 b^3
+        flops = 118.0 * bs ** 3 * iters
+        ach = flops / (p["predict_ms"] * 1e-3) / 1e12
+        r = {"mesh": list(w["n"]), "ms_per_step": p["step_ms"], "predict_ms": p["predict_ms"],
+             "correct_ms": p["correct_ms"],
+             "value": cells * 4 * (w["M"] + 1) ** 2 / (p["step_ms"] * 1e-3),
+             "unit": "element-DOF updates/s", "newton_iters_per_cell": iters / cells,
+             "newton_iters_max": info["newton_iters_max"],
+             "roofline": {"bound": "alu", "kernel": "newton_kernel", "achieved": ach, "peak": peak,
+                          "unit": "TFLOP/s", "frac": ach / peak,
+                          "traffic": (_recorded_traffic("newton_fp32", info["newton_iters_total"] / steps)
+                                      if tag == "mixed_fp32" else None),
+                          "peak_source": "nominal: FMA pipes x 2 flop x 2.07 GHz"}}
+        out[tag] = r
+    # the oracle: Newton prediction of a sample of cells and the correction of the whole
+    # mesh is not needed for a per-cell rate; extrapolated to every cell of the step
+    w = I.workload(NL_WORKLOAD, n=(32, 32))
+    q = I.initial_state(w)
+    from oracle import linear as OL
+    dt, _ = OL.time_step(w, ONL.max_speed(q, w))
+    cells = np.arange(cpu_cells)
+    t0 = time.perf_counter()
+    ONL.newton_predict(q, w, dt, cells=cells)
+    per_cell = (time.perf_counter() - t0) / cpu_cells
+    full = 512 * 512
+    out["cpu_oracle"] = {"kind": "oracle", "cores": os.cpu_count(),
+                         "seconds_per_cell": per_cell,
+                         "value": full * 4 * 9 / (per_cell * full),
+                         "unit": "element-DOF updates/s",
+                         "sample": f"Newton predictions of {cpu_cells} cells of the vortex "
+                                   "(numpy, all host cores), extrapolated to 512 x 512"}
+    return out
+
+
+# ---------------------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------------------
 class Clocks:
@@ -171,23 +236,30 @@ class Clocks:
 # ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
-def _recorded_traffic(prec_name):
+def _recorded_traffic(prec_name, units=None):
     """DRAM bytes per launch of the dominant kernel, from the committed ncu summaries under
-    profiles/ (a line `roofline-traffic: <precision> <source> sha256_16=<h> dram_bytes=<n>`),
-    used only while that kernel source is unchanged since the capture (else None)."""
+    profiles/ (a line `roofline-traffic: <name> <source> sha256_16=<h> dram_bytes=<n>
+    [units=<u>]`), used only while that kernel source is unchanged since the capture (else
+    None).  A capture of a smaller case carries the units (e.g. region-iterations) it
+    processed; its bytes are scaled to `units` of this launch."""
     import glob
     import hashlib
     for p in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(p):
             f = line.split()
-            if len(f) != 5 or f[0] != "roofline-traffic:" or f[1] != prec_name:
+            if len(f) < 5 or f[0] != "roofline-traffic:" or f[1] != prec_name:
                 continue
             kv = dict(x.split("=", 1) for x in f[3:])
             src = os.path.join(ROOT, "paper_2101_01231_gb300", "csrc", f[2])
             if not os.path.exists(src):
                 return None
             h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-            return int(kv["dram_bytes"]) if h == kv.get("sha256_16") else None
+            if h != kv.get("sha256_16"):
+                return None
+            b = int(kv["dram_bytes"])
+            if "units" in kv:
+                return None if units is None else b / int(kv["units"]) * units
+            return b
     return None
 
 
@@ -360,6 +432,8 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_oracle(w, args.cpu_seconds)
+    if args.newton_steps > 0:
+        line["newton"] = newton_section(R, I, args.newton_steps, 8 if args.no_cpu_baseline else 16)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
