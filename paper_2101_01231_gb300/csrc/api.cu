@@ -273,6 +273,17 @@ int read_newton_stats(ridg_t* h) {
   return RIDG_OK;
 }
 
+int read_status(ridg_t* h) {
+  int st = 0;
+  RIDG_CUDA(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (st & 2) return set_err(h, RIDG_ETIMEOUT, "a bounded tensor-core wait gave up");
+  if (st & 4)
+    return set_err(h, RIDG_ENONFINITE, "state outgrew the mixed-precision digit range in a step");
+  if (!is_linear(h)) return read_newton_stats(h);
+  return RIDG_OK;
+}
+
 int check_handle(const ridg_t* h) { return h ? RIDG_OK : RIDG_EINVAL; }
 
 }  // namespace
@@ -452,7 +463,7 @@ void ridg_destroy(ridg_t* h) {
   dev_free(h, h->ms.exps);
   dev_free(h, h->ms.maxbits);
   dev_free(h, h->nl.mem);
-  dev_free(h, h->nl_scratch);
+  if (!h->nl_scratch_shared) dev_free(h, h->nl_scratch);
   dev_free(h, h->nl_words);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -611,16 +622,6 @@ int ridg_step(ridg_t* h, int n) {
   return RIDG_OK;
 }
 
-int read_status(ridg_t* h) {
-  int st = 0;
-  RIDG_CUDA(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
-  if (st & 2) return set_err(h, RIDG_ETIMEOUT, "a bounded tensor-core wait gave up");
-  if (st & 4)
-    return set_err(h, RIDG_ENONFINITE, "state outgrew the mixed-precision digit range in a step");
-  if (!is_linear(h)) return read_newton_stats(h);
-  return RIDG_OK;
-}
 
 int ridg_sync(ridg_t* h) {
   if (check_handle(h)) return RIDG_EINVAL;
@@ -749,6 +750,7 @@ int ridg_l2_error(ridg_t* h, const double* x, int on_device, double* err) {
 // ------------------------------------------------------------------------------------------
 struct ridg_batch {
   std::vector<ridg_t*> inst;
+  void* nl_scratch = nullptr;  // Newton block storage shared by the instances (run in turn)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::map<int, cudaGraphExec_t> graphs;
@@ -785,6 +787,22 @@ int ridg_batch_create(int count, const ridg_mesh* meshes, const int* orders, con
     h->batch_owned = true;
     b->inst.push_back(h);
   }
+  // the instances' Newton kernels run one after another on the batch stream: one block
+  // storage, as large as the largest instance needs, serves them all
+  if (flux->kind != RIDG_FLUX_ADVECTION) {
+    size_t need = 0;
+    for (ridg_t* h : b->inst) need = std::max(need, h->nl_scratch_cta * (size_t)h->nl_grid);
+    b->nl_scratch = dev_alloc(b->inst[0], need);
+    if (!b->nl_scratch) {
+      ridg_batch_destroy(b);
+      return RIDG_ENOMEM;
+    }
+    for (ridg_t* h : b->inst) {
+      dev_free(h, h->nl_scratch);
+      h->nl_scratch = b->nl_scratch;
+      h->nl_scratch_shared = true;
+    }
+  }
   *out = b;
   return RIDG_OK;
 }
@@ -794,6 +812,7 @@ void ridg_batch_destroy(ridg_batch_t* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : b->defs) cudaGraphDestroy(kv.second);
+  if (b->nl_scratch && !b->inst.empty()) dev_free(b->inst[0], b->nl_scratch);
   for (ridg_t* h : b->inst) ridg_destroy(h);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -806,6 +825,10 @@ ridg_t* ridg_batch_instance(ridg_batch_t* b, int i) {
 
 int ridg_batch_step(ridg_batch_t* b, int n) {
   if (!b || n < 1) return RIDG_EINVAL;
+  for (ridg_t* h : b->inst) {
+    if (!(h->dt > 0)) return set_err(h, RIDG_ESTATE, "no dt yet: call ridg_set_state first");
+    if (!is_linear(h) && clear_newton_stats(h) != cudaSuccess) return RIDG_ECUDA;
+  }
   // a rebuilt operator (changed dt) of any instance invalidates the batch graphs
   bool stale = b->gens.size() != b->inst.size();
   for (size_t i = 0; !stale && i < b->inst.size(); ++i) stale = b->gens[i] != b->inst[i]->gen;
@@ -852,7 +875,15 @@ int ridg_batch_step(ridg_batch_t* b, int n) {
 
 int ridg_batch_sync(ridg_batch_t* b) {
   if (!b) return RIDG_EINVAL;
-  return cudaStreamSynchronize(b->stream) == cudaSuccess ? RIDG_OK : RIDG_ECUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return RIDG_ECUDA;
+  // every instance's device status (and Newton statistics); the most severe one is returned
+  // (ENOCONV only when nothing worse happened), each instance keeps its own message / info
+  int worst = RIDG_OK;
+  for (ridg_t* h : b->inst) {
+    const int rc = read_status(h);
+    if (rc != RIDG_OK && (worst == RIDG_OK || worst == RIDG_ENOCONV)) worst = rc;
+  }
+  return worst;
 }
 
 }  // extern "C"

@@ -416,6 +416,27 @@ __device__ void assemble_cells(const NlDev& tb, const NlPlan& plan, int r0, cons
         for (int j2 = 0; j2 < MV; ++j2) blk[(size_t)(i2 * THT + k) * BP + j2 * THT + l] = acc[g][i2 * MV + j2];
     }
   }
+  // zero padding rows / columns of every block written here: the block GEMMs run over the
+  // padded size, so padding must hold zeros whatever the scratch held before
+  if constexpr (BP > D::BS) {
+    constexpr int BS = D::BS, NPAD = (BP - BS) * BP + BS * (BP - BS);
+    for (int g = 0; g < CG; ++g) {
+      const int r = r0 + g;
+      for (int f = -1; f < 4; ++f) {
+        const int r2 = f < 0 ? r : region_nbr(r, f >> 1, (f & 1) ? -1 : 1);
+        if (r2 < 0) continue;
+        T* blk = slots + (size_t)plan.slot[r * 9 + r2] * BP * BP;
+        for (int i = threadIdx.x; i < NPAD; i += kThreads) {
+          if (i < (BP - BS) * BP) {
+            blk[BS * BP + i] = T(0);
+          } else {
+            const int j = i - (BP - BS) * BP;
+            blk[(j / (BP - BS)) * BP + BS + j % (BP - BS)] = T(0);
+          }
+        }
+      }
+    }
+  }
   for (int f = 0; f < 4; ++f) {
     const int dd = f >> 1, side = (f & 1) ? -1 : 1;
     const Ent<T>* oent = Tab<T>::oent(tb, f);

@@ -195,6 +195,7 @@ struct ridg_handle {
   void* nl_scratch = nullptr;
   size_t nl_scratch_cta = 0;
   int nl_grid = 0;
+  bool nl_scratch_shared = false;  // block storage owned by the batch
   int* nl_words = nullptr;  // [0] work counter, [1..3] Newton statistics, [4..5] max speed
                             // bits, [6..7] total Newton iterations
   long long newton_iters_total = 0;

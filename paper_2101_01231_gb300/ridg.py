@@ -283,7 +283,9 @@ def ridg_batch_step(b, n=1):
 
 
 def ridg_batch_sync(b):
-    return _check(_lib.ridg_batch_sync(b))
+    """Wait for the batch; RIDG_ENOCONV (returned, not raised) when Newton hit its cap in
+    some instance (see each instance's ridg_info)."""
+    return _check(_lib.ridg_batch_sync(b), allow=(RIDG_ENOCONV,))
 
 
 # ----- convenience wrapper ---------------------------------------------------------------
