@@ -141,6 +141,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// bring a TMA box into L2 ahead of its load (no shared memory, no barrier)
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                   (uint64_t)map),
+               "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+
 // 8 consecutive TMEM columns of this thread's lane (no wait: see tmem_wait_ld)
 __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
   asm volatile(
@@ -333,6 +341,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
       bulk_load(smem_u32(smem + L.b_off + off), (const unsigned char*)Bg + off,
                 min(32768u, L.bbytes - off), opload);
     for (int i = 0; i < NSL && i < nitems; ++i) issue_item(i);
+    // the later items' boxes: into L2 now, so that the ring's refills hit L2, not HBM
+    for (int item = NSL; item < nitems; ++item) {
+      const int kk = item / L.groups, q = item % L.groups;
+      const int tile = blockIdx.x + kk * gridDim.x;
+      const int x0 = (tile % ntx) * kTX, y0 = (tile / ntx) * kTY;
+      for (int ox = 0; ox < 3; ++ox) tma_prefetch_3d(&dmap, (x0 + ox) * 8, y0, q * L.G * L.P);
+    }
     if (OUTF2 && blockIdx.x == 0) {
       // rotate the running maximum: the correction that follows accumulates a fresh one
       maxbits[0] = maxbits[1];
@@ -541,6 +556,36 @@ __device__ __forceinline__ bool write_cell_digits(const double* q, int ix, int i
   return fits;
 }
 
+// digit rows of mode group p (8 coefficients v) of cell (ix, iy) and its ghost copies
+template <int NB, int S>
+__device__ __forceinline__ bool write_group_digits(const double* v, int p, int ix, int iy, int nx,
+                                                   int ny, int s, uint4* __restrict__ planes) {
+  constexpr int THS = NB * NB;
+  constexpr int P = ((THS + 15) / 16) * 2;
+  const long long plane = (long long)(nx + 2) * (ny + 2);
+  int px[2] = {ix + 1, -1}, py[2] = {iy + 1, -1};
+  if (ix == 0) px[1] = nx + 1;
+  if (ix == nx - 1) px[1] = 0;
+  if (iy == 0) py[1] = ny + 1;
+  if (iy == ny - 1) py[1] = 0;
+  uint4 rows[S];
+  const bool fits = make_digit_rows<S>(v, s, rows);
+#pragma unroll
+  for (int a = 0; a < S; ++a) {
+    uint4* base = planes + (long long)(a * P + p) * plane;
+#pragma unroll
+    for (int yi = 0; yi < 2; ++yi) {
+      if (py[yi] < 0) continue;
+#pragma unroll
+      for (int xi = 0; xi < 2; ++xi) {
+        if (px[xi] < 0) continue;
+        base[(long long)py[yi] * (nx + 2) + px[xi]] = rows[a];
+      }
+    }
+  }
+  return fits;
+}
+
 __device__ __forceinline__ unsigned long long block_max_bits(unsigned long long v,
                                                              unsigned long long* sh) {
 #pragma unroll
@@ -639,28 +684,36 @@ __global__ void __launch_bounds__(128) mixed_correct_kernel(
     double* __restrict__ Q, const float2* __restrict__ Y, int nx, int ny, CorrParams cp, int gmax,
     int sgnx, int sgny, int* __restrict__ exps, unsigned long long* __restrict__ maxbits,
     uint4* __restrict__ planes, int* status) {
+  // one thread per (cell, 8-mode group): P threads per cell, 128 / P cells per block
   constexpr int THS = NB * NB;
+  constexpr int P = ((THS + 15) / 16) * 2;
+  constexpr int CPB = 128 / P;
   constexpr int PITCH = THS + 1;  // odd pitch: conflict-free row access
-  __shared__ double sq[128 * PITCH];
+  __shared__ double sq[CPB * PITCH];
   __shared__ unsigned long long shmax[4];
   const long long ncell = (long long)nx * ny;
-  const long long e0 = (long long)blockIdx.x * 128;
-  const int nblk = (int)min((long long)128, ncell - e0);
+  const long long e0 = (long long)blockIdx.x * CPB;
+  const int nblk = (int)min((long long)CPB, ncell - e0);
   const int ys = exps[1];                                  // exponent of Y
   const int snext = exponent_above(maxbits[0]) + 1;        // exponent for the new digits
   // coalesced load of the block's state rows
   for (int i = threadIdx.x; i < nblk * THS; i += 128) sq[(i / THS) * PITCH + i % THS] = Q[e0 * THS + i];
   __syncthreads();
-  const long long e = e0 + threadIdx.x;
+  const int lc = threadIdx.x / P, pg = threadIdx.x % P, m0 = 8 * pg;
+  const long long e = e0 + lc;
   unsigned long long mymax = 0;
   bool fits = true;
-  if (threadIdx.x < nblk) {
+  if (lc < nblk) {
     const int ix = (int)(e % nx), iy = (int)(e / nx);
-    DF dq[THS];
+    DF dq[8];
 #pragma unroll
-    for (int s = 0; s < THS; ++s) {
-      const float2 y = Y[s * ncell + e];  // volume term V
-      dq[s] = DF{y.x, y.y};
+    for (int j = 0; j < 8; ++j) {
+      if (m0 + j < THS) {
+        const float2 y = Y[(m0 + j) * ncell + e];  // volume term V
+        dq[j] = DF{y.x, y.y};
+      } else {
+        dq[j] = DF{0.f, 0.f};
+      }
     }
 #pragma unroll
     for (int dd = 0; dd < 2; ++dd) {
@@ -677,33 +730,45 @@ __global__ void __launch_bounds__(128) mixed_correct_kernel(
       const float2* u = Y + (long long)(THS + dd * NB) * ncell;
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
+        const int base = dd == 0 ? t * NB : t;
+        bool any = false;  // does face trace t touch this thread's modes?
+#pragma unroll
+        for (int a2 = 0; a2 < NB; ++a2) any |= (base + a2 * st) / 8 == pg;
+        if (!any) continue;
         const float2 a = u[t * ncell + jr], b = u[t * ncell + jl];
         const DF fr = DF{a.x, a.y}, fl = DF{b.x, b.y};
         const DF w_even = df_add(fl, df_neg(fr));  // -F(i+1/2) + F(i-1/2)
         const DF w_odd = df_neg(df_add(fl, fr));   // -F(i+1/2) - F(i-1/2)
-        const int base = dd == 0 ? t * NB : t;
 #pragma unroll
         for (int a2 = 0; a2 < NB; ++a2) {
+          const int sm = base + a2 * st;
+          if (sm / 8 != pg) continue;
           const DF w = (a2 & 1) ? w_odd : w_even;
           const DF c = (a2 == 0) ? w : df_mul_const(cp.eph[a2], cp.epl[a2], w);
-          dq[base + a2 * st] = df_add(dq[base + a2 * st], c);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (m0 + j == sm) dq[j] = df_add(dq[j], c);
         }
       }
     }
     const int kfin = ys + gmax - 16;
-    double qn[THS];
-    double* q = sq + threadIdx.x * PITCH;
+    double qn[8];
+    double* q = sq + lc * PITCH;
 #pragma unroll
-    for (int s = 0; s < THS; ++s) {
-      double v = q[s];
-      v = v + f2d_scaled(dq[s].h, kfin);
-      v = v + f2d_scaled(dq[s].l, kfin);
-      q[s] = v;
-      qn[s] = v;
-      const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
-      mymax = a > mymax ? a : mymax;
+    for (int j = 0; j < 8; ++j) {
+      if (m0 + j < THS) {
+        double v = q[m0 + j];
+        v = v + f2d_scaled(dq[j].h, kfin);
+        v = v + f2d_scaled(dq[j].l, kfin);
+        q[m0 + j] = v;
+        qn[j] = v;
+        const unsigned long long ab = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+        mymax = ab > mymax ? ab : mymax;
+      } else {
+        qn[j] = 0.0;
+      }
     }
-    fits = write_cell_digits<NB, S>(qn, ix, iy, nx, ny, snext, planes);
+    fits = write_group_digits<NB, S>(qn, pg, ix, iy, nx, ny, snext, planes);
   }
   if (!fits) atomicOr(status, kStatusRange);
   const unsigned long long bm = block_max_bits(mymax, shmax);
@@ -862,7 +927,8 @@ template <int NB, int S>
 static cudaError_t launch_correct_t(const Grid& g, double* Q, const void* Y, int gmax,
                                     const CorrParams& cp, int sgnx, int sgny, MixedState& ms,
                                     cudaStream_t s) {
-  const unsigned blocks = (unsigned)((g.ncell + 127) / 128);
+  constexpr int CPB = 128 / (((NB * NB + 15) / 16) * 2);  // cells per block
+  const unsigned blocks = (unsigned)((g.ncell + CPB - 1) / CPB);
   mixed_correct_kernel<NB, S><<<blocks, 128, 0, s>>>(Q, (const float2*)Y, g.n[0], g.n[1], cp, gmax,
                                                      sgnx, sgny, ms.exps, ms.maxbits,
                                                      (uint4*)ms.planes, ms.status);

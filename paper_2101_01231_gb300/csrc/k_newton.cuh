@@ -489,100 +489,143 @@ __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
 template <>
 __device__ __forceinline__ double recip<double>(double x) { return __drcp_rn(x); }
 
-// Largest |v| over the lanes' candidates (valid != 0), ties to the lower row; the same result
-// in every lane.  The magnitude's bit pattern orders like its value (v >= 0).
-__device__ __forceinline__ int warp_argmax(float v, int row, bool valid, bool* zero) {
+// Largest |v| over the candidates of the lanes in `mask` (valid != 0), ties to the lower
+// row; the same result in every lane of the mask.  The magnitude's bit pattern orders like
+// its value (v >= 0).
+__device__ __forceinline__ int group_argmax(unsigned mask, float v, int row, bool valid, bool* zero) {
   const unsigned key = valid ? (__float_as_uint(v) | 0x80000000u) : 0u;
-  const unsigned m = __reduce_max_sync(0xffffffffu, key);
-  const unsigned p = __reduce_min_sync(0xffffffffu, key == m && valid ? (unsigned)row : 0xffffffffu);
+  const unsigned m = __reduce_max_sync(mask, key);
+  const unsigned p = __reduce_min_sync(mask, key == m && valid ? (unsigned)row : 0xffffffffu);
   *zero = (m & 0x7fffffffu) == 0u;
   return (int)p;
 }
-__device__ __forceinline__ int warp_argmax(double v, int row, bool valid, bool* zero) {
+__device__ __forceinline__ int group_argmax(unsigned mask, double v, int row, bool valid, bool* zero) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const unsigned hi = valid ? ((unsigned)(b >> 32) | 0x80000000u) : 0u, lo = (unsigned)b;
-  const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mh = __reduce_max_sync(mask, hi);
   const bool h = valid && hi == mh;
-  const unsigned ml = __reduce_max_sync(0xffffffffu, h ? lo : 0u);
-  const unsigned p = __reduce_min_sync(0xffffffffu, h && lo == ml ? (unsigned)row : 0xffffffffu);
+  const unsigned ml = __reduce_max_sync(mask, h ? lo : 0u);
+  const unsigned p = __reduce_min_sync(mask, h && lo == ml ? (unsigned)row : 0xffffffffu);
   *zero = (mh & 0x7fffffffu) == 0u && ml == 0u;
   return (int)p;
+}
+
+// x = a[k][j] (or a[j][k]) for a block-uniform index k, without dynamic register indexing
+template <typename T, int RR>
+__device__ __forceinline__ void pick_row(const T (&a)[RR][RR], int k, T (&x)[RR]) {
+  switch (k) {
+    default:
+#pragma unroll
+      for (int j = 0; j < RR; ++j) x[j] = a[0][j];
+      break;
+#define RIDG_PICK_ROW(K) \
+    case K:              \
+      if constexpr (K < RR) { _Pragma("unroll") for (int j = 0; j < RR; ++j) x[j] = a[K][j]; } break;
+    RIDG_PICK_ROW(1) RIDG_PICK_ROW(2) RIDG_PICK_ROW(3) RIDG_PICK_ROW(4) RIDG_PICK_ROW(5)
+    RIDG_PICK_ROW(6) RIDG_PICK_ROW(7)
+#undef RIDG_PICK_ROW
+  }
+}
+template <typename T, int RR>
+__device__ __forceinline__ void pick_col(const T (&a)[RR][RR], int k, T (&x)[RR]) {
+  switch (k) {
+    default:
+#pragma unroll
+      for (int i = 0; i < RR; ++i) x[i] = a[i][0];
+      break;
+#define RIDG_PICK_COL(K) \
+    case K:              \
+      if constexpr (K < RR) { _Pragma("unroll") for (int i = 0; i < RR; ++i) x[i] = a[i][K]; } break;
+    RIDG_PICK_COL(1) RIDG_PICK_COL(2) RIDG_PICK_COL(3) RIDG_PICK_COL(4) RIDG_PICK_COL(5)
+    RIDG_PICK_COL(6) RIDG_PICK_COL(7)
+#undef RIDG_PICK_COL
+  }
+}
+template <typename T, int RR>
+__device__ __forceinline__ void put_col(T (&a)[RR][RR], int k, const T (&x)[RR]) {
+  switch (k) {
+    default:
+#pragma unroll
+      for (int i = 0; i < RR; ++i) a[i][0] = x[i];
+      break;
+#define RIDG_PUT_COL(K) \
+    case K:             \
+      if constexpr (K < RR) { _Pragma("unroll") for (int i = 0; i < RR; ++i) a[i][K] = x[i]; } break;
+    RIDG_PUT_COL(1) RIDG_PUT_COL(2) RIDG_PUT_COL(3) RIDG_PUT_COL(4) RIDG_PUT_COL(5)
+    RIDG_PUT_COL(6) RIDG_PUT_COL(7)
+#undef RIDG_PUT_COL
+  }
 }
 
 // Inverse of the leading BS x BS part of A (global) into S (shared, BP x BP, zero padding):
 // Gauss-Jordan on a register-resident copy with implicit row pivoting (the pivot of column
 // c is the largest remaining entry among the rows not yet used; no rows move), then the
 // order is restored while writing S: with prow[c] the row that pivoted column c and rank its
-// inverse permutation, inv[rank[i]][prow[j]] = R[i][j].  Every warp finds the pivot itself
-// (each lane keeps the used flags of its rows lane + 32 k in a bit mask), so a column costs
-// two barriers: after its entries are published and after the pivot row is.
+// inverse permutation, inv[rank[i]][prow[j]] = R[i][j].
+// Thread (tx, ty) = (tid / 16, tid % 16) owns rows ty + 16 i and columns tx + 16 j, so a
+// column lives in one half-warp: that half-warp finds the pivot of its column and publishes
+// the column, and each thread takes the pivot row from its own half-warp by shuffles -- one
+// barrier per column.
 template <typename T, int BS, int BP, int RR>
 __device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* prow, int* rank, int* flags) {
-  constexpr int NK = (BS + 31) / 32;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
+  static_assert(RR <= 8, "register tile up to 8 x 8");
+  const int tid = threadIdx.x, tx = tid >> 4, ty = tid & 15;
+  const int lane = tid & 31, half = lane & 16, warp = tid >> 5;
+  const unsigned hmask = 0xFFFFu << half;
   T a[RR][RR];
 #pragma unroll
   for (int i = 0; i < RR; ++i)
 #pragma unroll
     for (int j = 0; j < RR; ++j) a[i][j] = A[(size_t)(ty + 16 * i) * BP + tx + 16 * j];
-  unsigned umask = 0u;
+  unsigned used = 0u;  // bit i: row ty + 16 i has pivoted (or is padding)
 #pragma unroll
-  for (int k = 0; k < NK; ++k)
-    if (lane + 32 * k >= BS) umask |= 1u << k;
+  for (int i = 0; i < RR; ++i)
+    if (ty + 16 * i >= BS) used |= 1u << i;
+  int* pv = rank;      // pivot rows of the last two columns (rank is rebuilt at the end)
   for (int c = 0; c < BS; ++c) {
-    T* cv = colv + (c & 1) * BP;
-    T* rp = rowp + (c & 1) * BP;
-    const int cb = c >> 4;
-    if (tx == (c & 15)) {
+    const int buf = c & 1, cb = c >> 4, cx = c & 15;
+    T* cv = colv + buf * BP;
+    if (warp == (cx >> 1)) {
+      // this warp's half (cx & 1) holds column c: pivot search and publication
+      if ((lane >> 4) == (cx & 1)) {
+        T col[RR];
+        pick_col(a, cb, col);
+        T best = T(0);
+        int bi = 0;
+        bool have = false;
 #pragma unroll
-      for (int i = 0; i < RR; ++i) {
-        T v = T(0);
+        for (int i = 0; i < RR; ++i) {
+          if ((used >> i) & 1u) continue;
+          const T v = fabs(col[i]);
+          if (!have || v > best) {
+            best = v;
+            bi = ty + 16 * i;
+            have = true;
+          }
+        }
+        bool zero = false;
+        int p = group_argmax(hmask, best, bi, have, &zero);
+        if (p >= BS) p = 0;  // unreachable: an unused row is always left
 #pragma unroll
-        for (int j = 0; j < RR; ++j)
-          if (j == cb) v = a[i][j];
-        cv[ty + 16 * i] = v;
+        for (int i = 0; i < RR; ++i) cv[ty + 16 * i] = col[i];
+        if (ty == 0) {
+          pv[buf] = p;
+          prow[c] = p;
+          if (zero) atomicOr(flags, kFlagSingular);
+        }
       }
     }
     __syncthreads();
-    T best = T(0);
-    int bi = 0;
-    bool have = false;
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-      if ((umask >> k) & 1u) continue;
-      const T v = fabs(cv[lane + 32 * k]);
-      if (!have || v > best) {
-        best = v;
-        bi = lane + 32 * k;
-        have = true;
-      }
-    }
-    bool zero = false;
-    int p = warp_argmax(best, bi, have, &zero);
-    if (p >= BS) p = 0;  // unreachable: an unused row is always left
-    if ((p & 31) == lane) umask |= 1u << (p >> 5);
-    if (ty == (p & 15)) {
-      const int pa = p >> 4;
-#pragma unroll
-      for (int j = 0; j < RR; ++j) {
-        T v = T(0);
-#pragma unroll
-        for (int i = 0; i < RR; ++i)
-          if (i == pa) v = a[i][j];
-        rp[tx + 16 * j] = v;
-      }
-    }
-    if (tid == 0) {
-      prow[c] = p;
-      if (zero) atomicOr(flags, kFlagSingular);
-    }
-    __syncthreads();
+    const int p = pv[buf];
     const T ipiv = recip(cv[p]);
-    T prs[RR];
+    // the pivot row's entries in my columns, from the thread of my half-warp owning row p
+    T mine[RR], prs[RR];
+    pick_row(a, p >> 4, mine);
+    const int src = half + (p & 15);
 #pragma unroll
     for (int j = 0; j < RR; ++j) {
-      const int cj = tx + 16 * j;
-      prs[j] = cj == c ? ipiv : rp[cj] * ipiv;
+      const T v = __shfl_sync(0xffffffffu, mine[j], src);
+      prs[j] = (tx + 16 * j) == c ? ipiv : v * ipiv;
     }
 #pragma unroll
     for (int i = 0; i < RR; ++i) {
@@ -593,9 +636,20 @@ __device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* prow, int* r
         for (int j = 0; j < RR; ++j) a[i][j] = prs[j];
       } else {
 #pragma unroll
-        for (int j = 0; j < RR; ++j) a[i][j] = ((tx + 16 * j) == c ? T(0) : a[i][j]) - f * prs[j];
+        for (int j = 0; j < RR; ++j) a[i][j] = fma(-f, prs[j], a[i][j]);
       }
     }
+    if (tx == cx) {
+      // column c: the elimination leaves -f_i / piv (1 / piv in the pivot row)
+      T col[RR];
+#pragma unroll
+      for (int i = 0; i < RR; ++i) {
+        const int ri = ty + 16 * i;
+        col[i] = ri == p ? ipiv : -cv[ri] * ipiv;
+      }
+      put_col(a, cb, col);
+    }
+    if ((p & 15) == ty) used |= 1u << (p >> 4);
   }
   __syncthreads();
   for (int c = tid; c < BS; c += kThreads) rank[prow[c]] = c;
