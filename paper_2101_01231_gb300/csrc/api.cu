@@ -94,7 +94,43 @@ int rebuild_linear(ridg_t* h) {
     return set_err(h, RIDG_EINVAL, "region system is singular for this dt");
   RIDG_CUDA(h, cudaMemcpyAsync(h->P, h->P_host.data(), sizeof(double) * h->P_host.size(),
                                cudaMemcpyHostToDevice, h->stream));
-  if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+  if (h->opt.precision == RIDG_PREC_MIXED_BF16 && h->dim == 3) {
+    // 3D: the time-mean rows P-bar (first theta_S rows of P) on the tensor cores; the
+    // correction stays the FP64 kernel
+    std::vector<double> Pbar(h->P_host.begin(), h->P_host.begin() + (size_t)h->thS * h->K);
+    std::vector<unsigned short> digits;
+    std::vector<double> rscale;
+    std::vector<float> rowmul;
+    int rc = ridg::mixed_build(3, h->nb, Pbar, h->thS, h->opt.slices, digits, rscale, rowmul,
+                               h->mixed);
+    if (rc != RIDG_OK) return set_err(h, rc, "3D mixed operator build failed");
+    if (!h->mixed.b_slices) {
+      h->mixed.b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
+      h->mixed.row_scale = (double*)dev_alloc(h, rscale.size() * sizeof(double));
+      if (!h->mixed.b_slices || !h->mixed.row_scale)
+        return set_err(h, RIDG_ENOMEM, "mixed operator allocation failed");
+    }
+    RIDG_CUDA(h, cudaMemcpyAsync(h->mixed.b_slices, digits.data(),
+                                 digits.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
+                                 h->stream));
+    RIDG_CUDA(h, cudaMemcpyAsync(h->mixed.row_scale, rscale.data(), rscale.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, h->stream));
+    RIDG_CUDA(h, cudaStreamSynchronize(h->stream));  // host vectors go out of scope
+    if (!h->ms.planes) {
+      Grid g = grid_of(h);
+      const size_t pb = ridg::mixed3_plane_bytes(g, h->nb, h->opt.slices);
+      h->ms.planes = dev_alloc(h, pb);
+      h->ms.exps = (int*)dev_alloc(h, 4 * sizeof(int));
+      h->ms.maxbits = (unsigned long long*)dev_alloc(h, 2 * sizeof(unsigned long long));
+      if (!h->ms.planes || !h->ms.exps || !h->ms.maxbits)
+        return set_err(h, RIDG_ENOMEM, "mixed-path allocation failed");
+      RIDG_CUDA(h, cudaMemsetAsync(h->ms.planes, 0, pb, h->stream));
+      if (ridg::mixed3_make_map(g, h->nb, h->opt.slices, h->ms.planes, h->ms.map) != RIDG_OK)
+        return set_err(h, RIDG_ECUDA, "tensor map creation failed");
+      h->ms.status = h->status;
+    }
+    h->ms.valid = false;
+  } else if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
     // fused step operator: rows [V; u_x; u_y] = C P-bar with C mapping the time mean W-bar to
     // the volume term sum_d nu_d (D along d) W-bar and the upwind face traces nu_d tr(W-bar)
     const int nb = h->nb, thS = h->thS, K = h->K, nout = thS + 2 * nb;
@@ -174,7 +210,10 @@ int sign_of(double v) { return v > 0 ? 1 : (v < 0 ? -1 : 0); }
 // Mixed path: make the digit planes describe the current state (outside graph capture).
 int ensure_digits(ridg_t* h) {
   if (h->opt.precision != RIDG_PREC_MIXED_BF16 || h->ms.valid) return RIDG_OK;
-  RIDG_CUDA(h, ridg::launch_mixed_refresh(grid_of(h), h->nb, h->opt.slices, h->Q, h->ms, h->stream));
+  if (h->dim == 3)
+    RIDG_CUDA(h, ridg::launch_mixed3_refresh(grid_of(h), h->nb, h->opt.slices, h->Q, h->ms, h->stream));
+  else
+    RIDG_CUDA(h, ridg::launch_mixed_refresh(grid_of(h), h->nb, h->opt.slices, h->Q, h->ms, h->stream));
   h->ms.valid = true;
   return RIDG_OK;
 }
@@ -218,7 +257,9 @@ int enqueue_nl_correct(ridg_t* h) {
 int enqueue_predict_mean(ridg_t* h) {
   if (!is_linear(h)) return enqueue_newton(h);
   Grid g = grid_of(h);
-  if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+  if (h->opt.precision == RIDG_PREC_MIXED_BF16 && h->dim == 3) {
+    RIDG_CUDA(h, ridg::launch_mixed3_gemm(g, h->nb, h->mixed, h->ms, h->Wbar, h->thS, h->stream));
+  } else if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
     RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed, h->ms, h->Y, 1, h->ncell, true,
                                          h->stream));
   } else {
@@ -231,7 +272,13 @@ int enqueue_predict_mean(ridg_t* h) {
 int enqueue_correct_after_mean(ridg_t* h) {
   if (!is_linear(h)) return enqueue_nl_correct(h);
   CorrParams cp = corr_params(h);
-  if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+  if (h->opt.precision == RIDG_PREC_MIXED_BF16 && h->dim == 3) {
+    // FP64 correction from the FP64 time means, then the new state's digit planes
+    RIDG_CUDA(h, ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->Wbar, h->thS, cp,
+                                             h->stream));
+    RIDG_CUDA(h, ridg::launch_mixed3_refresh(grid_of(h), h->nb, h->opt.slices, h->Q, h->ms,
+                                             h->stream));
+  } else if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
     RIDG_CUDA(h, ridg::launch_mixed_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
                                             h->mixed.gmax, cp, sign_of(h->flux.vel[0]),
                                             sign_of(h->flux.vel[1]), h->ms, h->stream));
@@ -355,7 +402,9 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
   h->flux = *flux;
   h->cfl = cfl;
   if (h->opt.precision == RIDG_PREC_MIXED_BF16 &&
-      (!ridg::mixed_supported(h->dim, h->nb, h->thT) || h->opt.slices < 2 || h->opt.slices > 7)) {
+      (h->dim == 3 ? !ridg::mixed3_supported(h->nb, h->opt.slices)
+                   : (!ridg::mixed_supported(h->dim, h->nb, h->thT) || h->opt.slices < 2 ||
+                      h->opt.slices > 7))) {
     delete h;
     return RIDG_EINVAL;
   }
@@ -550,7 +599,7 @@ int ridg_predict(ridg_t* h, double* w_out, int on_device) {
                                    h->stream));
     }
     return read_newton_stats(h);
-  } else if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+  } else if (h->opt.precision == RIDG_PREC_MIXED_BF16 && h->dim == 2) {
     int rc = ensure_digits(h);
     if (rc) return rc;
     RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed_pred, h->ms, h->W, h->thT, 1, false,

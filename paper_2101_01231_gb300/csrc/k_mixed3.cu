@@ -1,0 +1,419 @@
+// Mixed-precision linear prediction in 3D on the 5th-generation tensor cores (tcgen05 + TMA).
+//
+// What is computed: the time-mean prediction W-bar_e = P-bar X_e of every cell e (Sec. 2.2,
+// eq. pred_full_system for a linear flux; X_e = the theta_S coefficients of the 3 x 3 x 3
+// region, P-bar = the centre rows of the region operator that the correction of Sec. 2.3
+// needs), by the same split-operand refinement as the 2D path: the state as S balanced
+// base-256 digits (exact in BF16) times one exponent, the operator rows likewise, digit
+// products summed in FP32 per weight a + c' in TMEM and recombined with error-free sums.
+//
+// Tiles are 8 x 16 cells of one z-plane (M = 128).  The region offset (ox, oy, oz) is taken
+// as in 2D -- x by one of three x-shifted TMA copies, y by the descriptor start -- and z by
+// loading the plane z + oz.  In 3D the operator digits of all 27 offsets do not fit next to
+// the state digits in shared memory, so they stream too:
+//   A ring (4 slots): one digit of one input plane (3 x-copies x 8-mode groups x 8 x 18
+//     cells, 27.6 KB at Q2), loaded by 4D TMA boxes of the ghost-padded digit planes;
+//   B stages (3): the operator digits of the three x-offsets of one (oz, oy) row (36.9 KB),
+//     one bulk copy each; stage oy is refilled for the next oz once the last digit's MMAs
+//     on it are complete.
+// The MMA issuer runs oz -> digit a -> oy -> ox -> k-step; the epilogue writes FP64 W-bar,
+// which the FP64 correction uses.  Every wait is bounded (status bit on timeout).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "k_tc.cuh"
+#include "ridg_internal.h"
+
+namespace ridg {
+namespace {
+
+constexpr int kNA = 4;      // A slots
+constexpr int kNBst = 3;    // B stages (one per y-offset)
+constexpr int kNOUTP = 32;  // padded outputs (theta_S <= 27)
+
+struct Gemm3Layout {
+  int P, brows;
+  uint32_t copy_bytes, a_bytes, b_bytes, b_off, bar_off, bytes;
+};
+
+__host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS) {
+  Gemm3Layout l;
+  l.P = ((thS + 15) / 16) * 2;
+  l.brows = S * kNOUTP;
+  l.copy_bytes = (uint32_t)l.P * kCopy * 16;
+  l.a_bytes = (3u * l.copy_bytes + 1023u) & ~1023u;
+  l.b_bytes = 3u * l.P * l.brows * 16;
+  l.b_off = kNA * l.a_bytes;
+  l.bar_off = (l.b_off + kNBst * l.b_bytes + 63u) & ~63u;
+  l.bytes = l.bar_off + 256;
+  return l;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
+    const __grid_constant__ CUtensorMap dmap, const unsigned char* __restrict__ Bg,
+    const double* __restrict__ rscale, int S, int nout, double* __restrict__ Y, int ystride,
+    const int* __restrict__ exps, int nx, int ny, int nz, int* status) {
+  constexpr int THS = NB * NB * NB;
+  constexpr int P = ((THS + 15) / 16) * 2;
+  constexpr int KSTEPS = P / 2;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint32_t tmem_base_sh;
+  const Gemm3Layout L = gemm3_layout(S, THS);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
+  const int ntiles = ntx * nty * nz;
+  const int mytiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int tcols = S * kNOUTP;  // TMEM columns per stage (two stages)
+  const uint32_t bar = smem_u32(smem + L.bar_off);
+  const uint32_t afull0 = bar, afree0 = bar + 8u * kNA, bfull0 = bar + 16u * kNA,
+                 bfree0 = bfull0 + 8u * kNBst, tdone0 = bfree0 + 8u * kNBst, tempty0 = tdone0 + 16u;
+  const int sexp = exps[0];
+
+  auto tile_origin = [&](int k, int& x0, int& y0, int& z0) {
+    const int tile = blockIdx.x + k * gridDim.x;
+    x0 = (tile % ntx) * kTX;
+    y0 = ((tile / ntx) % nty) * kTY;
+    z0 = tile / (ntx * nty);
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < kNA; ++i) {
+      mbar_init(afull0 + 8u * i, 1);
+      mbar_init(afree0 + 8u * i, 1);
+    }
+    for (int i = 0; i < kNBst; ++i) {
+      mbar_init(bfull0 + 8u * i, 1);
+      mbar_init(bfree0 + 8u * i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tdone0 + 8u * i, 1);
+      mbar_init(tempty0 + 8u * i, 256);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer: B rows of offsets and A digit planes, in MMA order ----
+      bool ok = true;
+      int ia = 0;  // A items issued
+      for (int k = 0; k < mytiles && ok; ++k) {
+        int x0, y0, z0;
+        tile_origin(k, x0, y0, z0);
+        for (int oz = 0; oz < 3 && ok; ++oz) {
+          const int use = k * 3 + oz;  // use count of every B stage
+          for (int oy = 0; oy < 3; ++oy) {
+            if (use > 0 && !mbar_wait_sleep(bfree0 + 8u * oy, (use - 1) & 1)) { ok = false; break; }
+            const uint32_t fb = bfull0 + 8u * oy;
+            mbar_expect_tx(fb, L.b_bytes);
+            const unsigned char* src = Bg + (size_t)(oz * 3 + oy) * L.b_bytes;
+            const uint32_t dst = smem_u32(smem + L.b_off + oy * L.b_bytes);
+            for (uint32_t off = 0; off < L.b_bytes; off += 32768u)
+              bulk_load(dst + off, src + off, min(32768u, L.b_bytes - off), fb);
+          }
+          for (int a = 0; a < S && ok; ++a, ++ia) {
+            const int sl = ia % kNA;
+            if (ia >= kNA && !mbar_wait_sleep(afree0 + 8u * sl, ((ia / kNA) - 1) & 1)) { ok = false; break; }
+            const uint32_t fa = afull0 + 8u * sl;
+            mbar_expect_tx(fa, 3 * L.copy_bytes);  // out-of-range boxes are zero-filled and counted
+            const uint32_t dst = smem_u32(smem + sl * L.a_bytes);
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox)
+              tma_load_4d(dst + ox * L.copy_bytes, &dmap, (x0 + ox) * 8, y0, z0 + oz, a * P, fa);
+          }
+        }
+      }
+      if (!ok) atomicOr(status, kStatusTimeout);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t brows = (uint32_t)L.brows;
+      const uint32_t copy16 = L.copy_bytes / 16;
+      bool ok = true;
+      int ia = 0;
+      for (int k = 0; k < mytiles && ok; ++k) {
+        const int ts = k & 1;
+        if (k >= 2 && !mbar_wait(tempty0 + 8u * ts, ((k - 2) >> 1) & 1)) { ok = false; break; }
+        const uint32_t tst = tmem + (uint32_t)(ts * tcols);
+        for (int oz = 0; oz < 3 && ok; ++oz) {
+          const int use = k * 3 + oz;
+          for (int a = 0; a < S && ok; ++a, ++ia) {
+            const int sl = ia % kNA;
+            if (!mbar_wait(afull0 + 8u * sl, (ia / kNA) & 1)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // A: LBO = plane stride inside a copy, SBO = one halo row of 8 cells (128 B)
+            const uint64_t adesc0 = smem_desc(smem_u32(smem + sl * L.a_bytes), kCopy * 16, 128);
+            const uint32_t idesc = idesc_bf16(128, (S - a) * kNOUTP);
+            const uint32_t dcol = tst + (uint32_t)(a * kNOUTP);
+            for (int oy = 0; oy < 3; ++oy) {
+              if (a == 0) {
+                if (!mbar_wait(bfull0 + 8u * oy, use & 1)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              }
+              const uint64_t bdesc0 = smem_desc(smem_u32(smem + L.b_off + oy * L.b_bytes), brows * 16, 128);
+#pragma unroll
+              for (int ox = 0; ox < 3; ++ox) {
+#pragma unroll
+                for (int j = 0; j < KSTEPS; ++j) {
+                  const uint32_t aoff = (uint32_t)ox * copy16 + (uint32_t)(2 * j * kCopy) + (uint32_t)(oy * kTX);
+                  const uint32_t boff = (uint32_t)(ox * P + 2 * j) * brows;
+                  const uint32_t acc = (oz == 0 && a == 0 && oy == 0 && ox == 0 && j == 0) ? 0u : 1u;
+                  mma_bf16(dcol, adesc0 + aoff, bdesc0 + boff, idesc, acc);
+                }
+              }
+              if (a == S - 1)
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        bfree0 + 8u * oy)
+                    : "memory");
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    afree0 + 8u * sl)
+                : "memory");
+          }
+        }
+        if (ok)
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  tdone0 + 8u * ts)
+              : "memory");
+      }
+      if (!ok) atomicOr(status, kStatusTimeout);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: warps 2..9, two per TMEM lane quadrant ----------------
+    const int quad = warp & 3;
+    const int part = (warp - 2) >> 2;
+    const int cell = quad * 32 + lane;
+    const int ix = cell % kTX, iy = cell / kTX;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
+    const double tscale = __longlong_as_double((long long)(sexp + 1023) << 52);
+    for (int k = 0; k < mytiles; ++k) {
+      const int ts = k & 1;
+      if (!mbar_wait_sleep(tdone0 + 8u * ts, (k >> 1) & 1)) {
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int x0, y0, z0;
+      tile_origin(k, x0, y0, z0);
+      const int gx = x0 + ix, gy = y0 + iy;
+      const long long e = ((long long)z0 * ny + gy) * nx + gx;
+      const uint32_t tbase = lane_addr + (uint32_t)(ts * tcols);
+#pragma unroll 1
+      for (int cb = part * (kNOUTP / 2); cb < (part + 1) * (kNOUTP / 2); cb += 8) {
+        if (cb >= nout) break;
+        uint32_t raw[7][8];
+#pragma unroll
+        for (int t = 0; t < 7; ++t)
+          if (t < S) tmem_ld8_nowait(tbase + (uint32_t)(t * kNOUTP + cb), raw[t]);
+        tmem_wait_ld();
+        float hi[8], lo[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          hi[c] = __uint_as_float(raw[0][c]);
+          lo[c] = 0.f;
+        }
+        float w = 1.f;
+#pragma unroll
+        for (int t = 1; t < 7; ++t) {
+          if (t < S) {
+            w *= 1.f / 256.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              float s2, e2;
+              two_sum(hi[c], __uint_as_float(raw[t][c]) * w, s2, e2);
+              hi[c] = s2;
+              lo[c] += e2;
+            }
+          }
+        }
+        if (gx < nx && gy < ny) {
+          double* y = Y + e * ystride + cb;
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (cb + c < nout) y[c] = ((double)hi[c] + (double)lo[c]) * (tscale * rscale[cb + c]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(tempty0 + 8u * ts);
+    }
+  }
+  // drain: no MMA may still write TMEM when it is released (bounded)
+  if (tid == 0 && mytiles > 0) mbar_wait(tdone0 + 8u * ((mytiles - 1) & 1), ((mytiles - 1) >> 1) & 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ---------------------------------------------------------------------------------------
+// digit planes of the 3D state: plane (a * P + p), padded (z + 1, y + 1, x + 1), one thread
+// per (cell, 8-mode group); the cell's periodic ghost copies are written too
+// ---------------------------------------------------------------------------------------
+template <int NB, int S>
+__global__ void __launch_bounds__(128) state_digits3_kernel(const double* __restrict__ Q, int nx,
+                                                            int ny, int nz,
+                                                            const unsigned long long* maxbits,
+                                                            int* exps, uint4* __restrict__ planes,
+                                                            int* status) {
+  constexpr int THS = NB * NB * NB;
+  constexpr int P = ((THS + 15) / 16) * 2;
+  const long long ncell = (long long)nx * ny * nz;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = exponent_above(maxbits[1]) + 1;
+  if (i == 0) exps[0] = s;
+  if (i >= ncell * P) return;
+  const long long e = i / P;
+  const int p = (int)(i % P);
+  const int ix = (int)(e % nx), iy = (int)((e / nx) % ny), iz = (int)(e / ((long long)nx * ny));
+  double v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = (p * 8 + j < THS) ? Q[e * THS + p * 8 + j] : 0.0;
+  uint4 rows[S];
+  if (!make_digit_rows<S>(v, s, rows)) atomicOr(status, kStatusRange);
+  const long long pnx = nx + 2, pny = ny + 2;
+  const long long plane = pnx * pny * (nz + 2);
+  int px[2] = {ix + 1, -1}, py[2] = {iy + 1, -1}, pz[2] = {iz + 1, -1};
+  if (ix == 0) px[1] = nx + 1;
+  if (ix == nx - 1) px[1] = 0;
+  if (iy == 0) py[1] = ny + 1;
+  if (iy == ny - 1) py[1] = 0;
+  if (iz == 0) pz[1] = nz + 1;
+  if (iz == nz - 1) pz[1] = 0;
+#pragma unroll
+  for (int a = 0; a < S; ++a) {
+    uint4* base = planes + (long long)(a * P + p) * plane;
+#pragma unroll
+    for (int zi = 0; zi < 2; ++zi) {
+      if (pz[zi] < 0) continue;
+#pragma unroll
+      for (int yi = 0; yi < 2; ++yi) {
+        if (py[yi] < 0) continue;
+#pragma unroll
+        for (int xi = 0; xi < 2; ++xi) {
+          if (px[xi] < 0) continue;
+          base[((long long)pz[zi] * pny + py[yi]) * pnx + px[xi]] = rows[a];
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+bool mixed3_supported(int nb, int slices) {
+  if (nb < 2 || nb > 3 || slices < 2 || slices > 6) return false;
+  return gemm3_layout(slices, nb * nb * nb).bytes <= kSmemLimit;
+}
+
+size_t mixed3_plane_bytes(const Grid& g, int nb, int slices) {
+  const int thS = nb * nb * nb, P = ((thS + 15) / 16) * 2;
+  return (size_t)(g.n[0] + 2) * (g.n[1] + 2) * (g.n[2] + 2) * slices * P * 16;
+}
+
+int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_out) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return RIDG_ECUDA;
+  const int thS = nb * nb * nb, P = ((thS + 15) / 16) * 2;
+  const cuuint64_t px = g.n[0] + 2, py = g.n[1] + 2, pz = g.n[2] + 2;
+  // dims (fastest first): padded x times 8 modes (BF16), padded y, padded z, digit x group
+  cuuint64_t dims[4] = {px * 8, py, pz, (cuuint64_t)slices * P};
+  cuuint64_t strides[3] = {px * 16, px * py * 16, px * py * pz * 16};
+  cuuint32_t box[4] = {(cuuint32_t)kTX * 8, (cuuint32_t)kHY, 1u, (cuuint32_t)P};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = ((EncodeFn)fn)((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, planes,
+                              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RIDG_OK : RIDG_ECUDA;
+}
+
+template <int NB>
+static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& ms, double* Y,
+                                  int ystride, cudaStream_t s) {
+  const Gemm3Layout L = gemm3_layout(op.slices, NB * NB * NB);
+  // one CTA per SM: each allocates all 512 TMEM columns, so a second CTA on the SM would
+  // only wait for them -- ask for more than half the shared memory
+  const uint32_t smem = std::max<uint32_t>(L.bytes, 117u * 1024u);
+  auto kern = mixed3_gemm_kernel<NB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ntiles = ((g.n[0] + kTX - 1) / kTX) * ((g.n[1] + kTY - 1) / kTY) * g.n[2];
+  const int grid = std::min(ntiles, sms);
+  kern<<<grid, kGemmThreads, smem, s>>>(*(const CUtensorMap*)ms.map,
+                                           (const unsigned char*)op.b_slices, op.row_scale,
+                                           op.slices, op.nout, Y, ystride, ms.exps, g.n[0], g.n[1],
+                                           g.n[2], ms.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, double* Y,
+                               int ystride, cudaStream_t s) {
+  if (g.dim != 3) return cudaErrorInvalidValue;
+  switch (nb) {
+    case 2: return launch_gemm3_t<2>(g, op, ms, Y, ystride, s);
+    case 3: return launch_gemm3_t<3>(g, op, ms, Y, ystride, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int NB, int S>
+static cudaError_t launch_refresh3_t(const Grid& g, const double* Q, MixedState& ms, cudaStream_t s) {
+  constexpr int P = ((NB * NB * NB + 15) / 16) * 2;
+  cudaError_t e = cudaMemsetAsync(ms.maxbits, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  state_max_kernel<<<256, 256, 0, s>>>(Q, g.ncell * NB * NB * NB, ms.maxbits);
+  const unsigned blocks = (unsigned)((g.ncell * P + 127) / 128);
+  state_digits3_kernel<NB, S><<<blocks, 128, 0, s>>>(Q, g.n[0], g.n[1], g.n[2], ms.maxbits, ms.exps,
+                                                     (uint4*)ms.planes, ms.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed3_refresh(const Grid& g, int nb, int slices, const double* Q,
+                                  MixedState& ms, cudaStream_t s) {
+  if (g.dim != 3) return cudaErrorInvalidValue;
+  switch (nb * 16 + slices) {
+#define RIDG_R3(NBV, SV) \
+  case NBV * 16 + SV: return launch_refresh3_t<NBV, SV>(g, Q, ms, s);
+    RIDG_R3(2, 2) RIDG_R3(2, 3) RIDG_R3(2, 4) RIDG_R3(2, 5) RIDG_R3(2, 6)
+    RIDG_R3(3, 2) RIDG_R3(3, 3) RIDG_R3(3, 4) RIDG_R3(3, 5) RIDG_R3(3, 6)
+#undef RIDG_R3
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ridg

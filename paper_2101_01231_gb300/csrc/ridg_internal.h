@@ -71,6 +71,17 @@ cudaError_t launch_mixed_correct(const Grid& g, int nb, int slices, double* Q, c
                                  int gmax, const CorrParams& cp, int sgnx, int sgny,
                                  MixedState& ms, cudaStream_t s);
 
+// ---- mixed BF16 tensor-core prediction in 3D (k_mixed3.cu): the time mean only ----
+bool mixed3_supported(int nb, int slices);
+size_t mixed3_plane_bytes(const Grid& g, int nb, int slices);
+int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_out);
+// Y[e * ystride + c] = (P-bar X_e)[c] in FP64 from the digit planes in ms
+cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, double* Y,
+                               int ystride, cudaStream_t s);
+// max |Q| and the 3D digit planes of Q
+cudaError_t launch_mixed3_refresh(const Grid& g, int nb, int slices, const double* Q,
+                                  MixedState& ms, cudaStream_t s);
+
 // ---- nonlinear flux, 2D: Newton prediction (k_newton*.cu) and correction (k_nonlinear.cu) ----
 // Device copies of the host-built tables (nl_tables.h), all inside one allocation.
 struct NlDev {

@@ -1,0 +1,120 @@
+"""The 3D mixed-precision (BF16 tensor-core, split-operand) time-mean prediction with the FP64
+correction, against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import linear as OL
+from paper_2101_01231_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+# tiles are 8 x 16 cells of one z-plane: partial tiles in x and y, meshes smaller than a
+# tile, every velocity sign, degrees 1 and 2
+CASES = [
+    ((10, 17, 3), 2, (1.0, 0.7, 0.3)),
+    ((6, 5, 4), 2, (-0.5, 0.9, -0.3)),
+    ((9, 20, 3), 1, (0.3, -1.0, 0.6)),
+    ((16, 16, 5), 2, (-1.0, -1.0, 1.0)),
+    ((3, 3, 3), 1, (0.2, 0.0, -0.7)),
+]
+TOL_STEP = 1e-12
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2101_01231_gb300 import ridg
+    return ridg
+
+
+def _w(n, M, vel, cfl=0.30):
+    return dict(flux="advection", dim=3, n=tuple(n), M=M, vel=tuple(vel), lo=(0.0,) * 3,
+                hi=(1.0,) * 3, cfl=cfl, ic="sin")
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _mixed(R, w, slices=6):
+    return R.Solver(3, w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"], hi=w["hi"],
+                    precision=R.RIDG_PREC_MIXED_BF16, slices=slices)
+
+
+@pytest.mark.parametrize("n,M,vel", CASES)
+def test_mixed3_step_matches_oracle(R, n, M, vel):
+    w = _w(n, M, vel)
+    s = _mixed(R, w)
+    rng = np.random.default_rng(31)
+    q = rng.standard_normal((s.cells, s.theta_s))
+    s.set_state(q)
+    dt = s.info()["dt"]
+    s.step(1)
+    s.sync()
+    assert _rel(s.get_state(), OL.step(q, w, dt)) < TOL_STEP
+    # two more steps (the digit planes are rebuilt from the corrected state every step)
+    s.step(2)
+    s.sync()
+    assert _rel(s.get_state(), OL.run(q, w, dt, 3)) < 3 * TOL_STEP
+    s.close()
+
+
+def test_mixed3_profile_step_and_predict(R):
+    w = _w((12, 10, 4), 2, (1.0, 0.5, -0.25))
+    s = _mixed(R, w)
+    rng = np.random.default_rng(32)
+    q = rng.standard_normal((s.cells, s.theta_s))
+    s.set_state(q)
+    dt = s.info()["dt"]
+    W = s.predict()                         # the full prediction (all theta_T rows)
+    assert _rel(W, OL.predict(q, w, dt)) < TOL_STEP
+    s.set_state(q)
+    p = s.profile_step(2)
+    assert p["predict_ms"] > 0 and p["correct_ms"] > 0
+    assert _rel(s.get_state(), OL.run(q, w, dt, 2)) < 2 * TOL_STEP
+    s.close()
+
+
+def test_mixed3_mass_conserved_and_slices(R):
+    w = _w((8, 16, 4), 2, (0.6, -0.8, 0.4))
+    rng = np.random.default_rng(33)
+    q = rng.standard_normal((8 * 16 * 4, 27))
+    errs = []
+    for S in (2, 4, 6):
+        s = _mixed(R, w, slices=S)
+        s.set_state(q)
+        dt = s.info()["dt"]
+        m0 = s.mass()
+        s.step(5)
+        s.sync()
+        assert abs(s.mass()[0] - m0[0]) <= 1e-13 * max(1.0, abs(m0[0]))
+        errs.append(_rel(s.get_state(), OL.run(q, w, dt, 5)))
+        s.close()
+    # each pair of digits buys ~2^-16 relative accuracy
+    assert errs[0] > 1e-6 and errs[-1] < 1e-11 and errs[0] > errs[1] > errs[2]
+
+
+def test_mixed3_rejects_unsupported(R):
+    with pytest.raises(R.RidgError):
+        _mixed(R, _w((8, 8, 8), 3, (1.0, 1.0, 1.0)))       # Q3: theta_S = 64 > 32
+    with pytest.raises(R.RidgError):
+        _mixed(R, _w((8, 8, 8), 2, (1.0, 1.0, 1.0)), slices=7)   # does not fit shared memory
+
+
+def test_config3_mixed_full_size_sampled(R):
+    # 96^3, Q2, a = (1, 0.7, 0.3), product of sines plus seeded 1e-3 coefficient noise
+    w = I.workload("adv3d_n96_q2")
+    s = _mixed(R, w)
+    q0 = I.initial_state(w)
+    s.set_state(q0)
+    dt = s.info()["dt"]
+    s.step(1)
+    q1 = s.get_state()
+    rng = np.random.default_rng(36)
+    N = 96 ** 3
+    cells = np.unique(np.concatenate([[0, 95, 96 * 95, N - 1, 96 * 96 * 50 + 96 * 17 + 9],
+                                      rng.integers(0, N, 27)]))
+    assert _rel(q1[cells], OL.step_cells(q0, w, dt, cells)) < TOL_STEP
+    s.close()
