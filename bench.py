@@ -45,6 +45,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--newton-steps", type=int, default=1,
                    help="timed steps of the Newton path (0: skip it)")
+    p.add_argument("--mixed3d-steps", type=int, default=20,
+                   help="timed steps of the 3D tensor-core path (0: skip it)")
     return p.parse_args()
 
 
@@ -117,6 +119,45 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------------------
+# 3D: the tensor-core time-mean prediction at 96^3, Q2
+# ---------------------------------------------------------------------------------------
+def mixed3d_section(R, I, steps, warmup):
+    """2D's split-operand tensor-core prediction in 3D (96^3, Q2, product of sines + seeded
+    noise; the 191 MB state is larger than L2, so no flush is needed), with the FP64
+    correction, and the FP64 path beside it."""
+    w = I.workload("adv3d_n96_q2")
+    q = I.initial_state(w)
+    cells = int(np.prod(w["n"]))
+    thS = (w["M"] + 1) ** 3
+    K = 27 * thS
+    out = {"workload": w["name"], "cells": cells, "order": w["M"], "theta_s": thS,
+           "l2_flush": "none: the state (191 MB) is larger than L2"}
+    hbm, bf16, src = _peaks()
+    for tag, prec in (("mixed", R.RIDG_PREC_MIXED_BF16), ("fp64", R.RIDG_PREC_FP64)):
+        s = R.Solver(3, w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"], hi=w["hi"],
+                     precision=prec)
+        s.set_state(q)
+        s.profile_step(warmup)
+        p = s.profile_step(steps if tag == "mixed" else max(3, steps // 10))
+        S_ = s.info()["slices"]
+        s.close()
+        r = {"ms_per_step": p["step_ms"], "predict_ms": p["predict_ms"], "correct_ms": p["correct_ms"],
+             "value": cells * thS / (p["step_ms"] * 1e-3), "unit": "element-DOF updates/s"}
+        if tag == "mixed":
+            bytes_pred = 2.0 * 8 * thS * cells          # Q in, W-bar out (FP64)
+            executed = 2.0 * (S_ * (S_ + 1) // 2) * 32 * 27 * 32 * cells
+            ach = bytes_pred / (p["predict_ms"] * 1e-3) / 1e9
+            r["roofline"] = {"bound": "hbm", "kernel": "mixed3_gemm (time-mean prediction)",
+                             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                             "traffic": None, "peak_source": f"HBM copy, {src}",
+                             "tensor_executed_tflops": executed / (p["predict_ms"] * 1e-3) / 1e12,
+                             "tensor_peak_tflops": bf16,
+                             "algorithmic_tflops": 2.0 * thS * K * cells / (p["predict_ms"] * 1e-3) / 1e12}
+        out[tag] = r
+    return out
 
 
 # ---------------------------------------------------------------------------------------
@@ -432,6 +473,8 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_oracle(w, args.cpu_seconds)
+    if args.mixed3d_steps > 0:
+        line["mixed3d"] = mixed3d_section(R, I, args.mixed3d_steps, args.warmup)
     if args.newton_steps > 0:
         line["newton"] = newton_section(R, I, args.newton_steps, 8 if args.no_cpu_baseline else 16)
     if rank == 0:

@@ -83,6 +83,16 @@ CorrParams corr_params(const ridg_t* h) {
     cp.nup[d] = nu > 0 ? nu : 0.0;
     cp.num[d] = nu < 0 ? nu : 0.0;
   }
+  auto split = [](double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  };
+  for (int i = 0; i < ridg::kMaxNB * ridg::kMaxNB; ++i) split(cp.D[i], cp.Dh[i], cp.Dl[i]);
+  for (int d = 0; d < 3; ++d) {
+    split(cp.nu[d], cp.nuh[d], cp.nul[d]);
+    split(cp.nup[d], cp.nph[d], cp.npl[d]);
+    split(cp.num[d], cp.nmh[d], cp.nml[d]);
+  }
   return cp;
 }
 
@@ -107,9 +117,12 @@ int rebuild_linear(ridg_t* h) {
     if (!h->mixed.b_slices) {
       h->mixed.b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
       h->mixed.row_scale = (double*)dev_alloc(h, rscale.size() * sizeof(double));
-      if (!h->mixed.b_slices || !h->mixed.row_scale)
+      h->mixed.row_mul = (float*)dev_alloc(h, rowmul.size() * sizeof(float));
+      if (!h->mixed.b_slices || !h->mixed.row_scale || !h->mixed.row_mul)
         return set_err(h, RIDG_ENOMEM, "mixed operator allocation failed");
     }
+    RIDG_CUDA(h, cudaMemcpyAsync(h->mixed.row_mul, rowmul.data(), rowmul.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, h->stream));
     RIDG_CUDA(h, cudaMemcpyAsync(h->mixed.b_slices, digits.data(),
                                  digits.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
                                  h->stream));
@@ -118,6 +131,8 @@ int rebuild_linear(ridg_t* h) {
     RIDG_CUDA(h, cudaStreamSynchronize(h->stream));  // host vectors go out of scope
     if (!h->ms.planes) {
       Grid g = grid_of(h);
+      h->Y = (double*)dev_alloc(h, (size_t)h->ncell * h->thS * sizeof(double));  // float2 pairs
+      if (!h->Y) return set_err(h, RIDG_ENOMEM, "mixed-path allocation failed");
       const size_t pb = ridg::mixed3_plane_bytes(g, h->nb, h->opt.slices);
       h->ms.planes = dev_alloc(h, pb);
       h->ms.exps = (int*)dev_alloc(h, 4 * sizeof(int));
@@ -258,7 +273,7 @@ int enqueue_predict_mean(ridg_t* h) {
   if (!is_linear(h)) return enqueue_newton(h);
   Grid g = grid_of(h);
   if (h->opt.precision == RIDG_PREC_MIXED_BF16 && h->dim == 3) {
-    RIDG_CUDA(h, ridg::launch_mixed3_gemm(g, h->nb, h->mixed, h->ms, h->Wbar, h->thS, h->stream));
+    RIDG_CUDA(h, ridg::launch_mixed3_gemm(g, h->nb, h->mixed, h->ms, h->Y, h->stream));
   } else if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
     RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed, h->ms, h->Y, 1, h->ncell, true,
                                          h->stream));
@@ -273,11 +288,9 @@ int enqueue_correct_after_mean(ridg_t* h) {
   if (!is_linear(h)) return enqueue_nl_correct(h);
   CorrParams cp = corr_params(h);
   if (h->opt.precision == RIDG_PREC_MIXED_BF16 && h->dim == 3) {
-    // FP64 correction from the FP64 time means, then the new state's digit planes
-    RIDG_CUDA(h, ridg::launch_correct_linear(grid_of(h), h->nb, h->Q, h->Wbar, h->thS, cp,
-                                             h->stream));
-    RIDG_CUDA(h, ridg::launch_mixed3_refresh(grid_of(h), h->nb, h->opt.slices, h->Q, h->ms,
-                                             h->stream));
+    // double-float correction from the time means, with the new state's digit planes
+    RIDG_CUDA(h, ridg::launch_mixed3_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
+                                             h->Wbar, h->mixed.gmax, cp, h->ms, h->stream));
   } else if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
     RIDG_CUDA(h, ridg::launch_mixed_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
                                             h->mixed.gmax, cp, sign_of(h->flux.vel[0]),
@@ -390,6 +403,10 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
     h->h[d] = (h->hi[d] - h->lo[d]) / h->n[d];
     h->ncell *= h->n[d];
   }
+  if (h->ncell >= (1LL << 31)) {  // the kernels index cells with 32-bit arithmetic
+    delete h;
+    return RIDG_EINVAL;
+  }
   h->M = order;
   h->nb = order + 1;
   h->thS = 1;
@@ -436,7 +453,9 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
   h->red = (double*)dev_alloc(h, (size_t)h->red_blocks * 4 * sizeof(double));
   h->status = (int*)dev_alloc(h, 16 * sizeof(int));
   if (is_linear(h)) {
-    h->Wbar = (double*)dev_alloc(h, nQ * sizeof(double));
+    // (3D mixed path: also the face values of the correction, 3 (M+1)^2 float2 per cell)
+    const size_t nWbar = std::max(nQ, (size_t)h->ncell * 3 * h->nb * h->nb);
+    h->Wbar = (double*)dev_alloc(h, nWbar * sizeof(double));
     h->P = (double*)dev_alloc(h, (size_t)h->thT * h->K * sizeof(double));
   }
   if (!h->Q || !h->W || !h->red || !h->status || (is_linear(h) && (!h->Wbar || !h->P))) {

@@ -26,12 +26,13 @@ struct Coords {
   int x, y, z;
 };
 
+// (cell counts stay below 2^31: 32-bit division, far cheaper than 64-bit)
 __device__ __forceinline__ Coords cell_coords(long long e, int nx, int ny) {
   Coords c;
-  c.x = (int)(e % nx);
-  long long r = e / nx;
-  c.y = (int)(r % ny);
-  c.z = (int)(r / ny);
+  const unsigned u = (unsigned)e, r = u / (unsigned)nx;
+  c.x = (int)(u - r * (unsigned)nx);
+  c.y = (int)(r % (unsigned)ny);
+  c.z = (int)(r / (unsigned)ny);
   return c;
 }
 

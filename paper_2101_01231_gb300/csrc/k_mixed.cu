@@ -408,7 +408,8 @@ __global__ void state_digits_kernel(const double* __restrict__ Q, int nx, int ny
   double q[THS];
 #pragma unroll
   for (int i = 0; i < THS; ++i) q[i] = Q[e * THS + i];
-  if (!write_cell_digits<NB, S>(q, (int)(e % nx), (int)(e / nx), nx, ny, s, planes))
+  const unsigned ue = (unsigned)e, uy = ue / (unsigned)nx;
+  if (!write_cell_digits<NB, S>(q, (int)(ue - uy * (unsigned)nx), (int)uy, nx, ny, s, planes))
     atomicOr(status, kStatusRange);
 }
 
@@ -485,7 +486,8 @@ __global__ void __launch_bounds__(128) mixed_correct_kernel(
   unsigned long long mymax = 0;
   bool fits = true;
   if (lc < nblk) {
-    const int ix = (int)(e % nx), iy = (int)(e / nx);
+    const unsigned ue = (unsigned)e, uy = ue / (unsigned)nx;
+    const int ix = (int)(ue - uy * (unsigned)nx), iy = (int)uy;
     DF dq[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {

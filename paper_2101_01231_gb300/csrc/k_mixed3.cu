@@ -16,8 +16,10 @@
 //   B stages (3): the operator digits of the three x-offsets of one (oz, oy) row (36.9 KB),
 //     one bulk copy each; stage oy is refilled for the next oz once the last digit's MMAs
 //     on it are complete.
-// The MMA issuer runs oz -> digit a -> oy -> ox -> k-step; the epilogue writes FP64 W-bar,
-// which the FP64 correction uses.  Every wait is bounded (status bit on timeout).
+// The MMA issuer runs oz -> digit a -> oy -> ox -> k-step; the epilogue writes W-bar as
+// double-float pairs with a common exponent, and mixed3_correct_kernel applies the correction
+// in double-float FP32 (state update FP64) and writes the next step's digit planes.  Every
+// wait is bounded (status bit on timeout).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -35,6 +37,10 @@ namespace {
 constexpr int kNA = 4;      // A slots
 constexpr int kNBst = 3;    // B stages (one per y-offset)
 constexpr int kNOUTP = 32;  // padded outputs (theta_S <= 27)
+
+struct DF3 {
+  float h, l;
+};
 
 struct Gemm3Layout {
   int P, brows;
@@ -57,8 +63,8 @@ __host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS) {
 template <int NB>
 __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
     const __grid_constant__ CUtensorMap dmap, const unsigned char* __restrict__ Bg,
-    const double* __restrict__ rscale, int S, int nout, double* __restrict__ Y, int ystride,
-    const int* __restrict__ exps, int nx, int ny, int nz, int* status) {
+    const float* __restrict__ rowmul, int S, int nout, float2* __restrict__ Y, int* __restrict__ exps,
+    unsigned long long* __restrict__ maxbits, int nx, int ny, int nz, int* status) {
   constexpr int THS = NB * NB * NB;
   constexpr int P = ((THS + 15) / 16) * 2;
   constexpr int KSTEPS = P / 2;
@@ -96,6 +102,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
       mbar_init(tempty0 + 8u * i, 256);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (blockIdx.x == 0) {
+      // rotate the running maximum: the correction that follows accumulates a fresh one
+      maxbits[0] = maxbits[1];
+      maxbits[1] = 0;
+      exps[1] = sexp;  // exponent of this step's outputs, read by the correction
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -207,7 +219,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
     const int cell = quad * 32 + lane;
     const int ix = cell % kTX, iy = cell / kTX;
     const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
-    const double tscale = __longlong_as_double((long long)(sexp + 1023) << 52);
+    const long long ncell = (long long)nx * ny * nz;
     for (int k = 0; k < mytiles; ++k) {
       const int ts = k & 1;
       if (!mbar_wait_sleep(tdone0 + 8u * ts, (k >> 1) & 1)) {
@@ -249,10 +261,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
           }
         }
         if (gx < nx && gy < ny) {
-          double* y = Y + e * ystride + cb;
+          // (hi, lo) scaled to the common row exponent; value = (hi + lo) 2^(s + gmax - 16)
 #pragma unroll
           for (int c = 0; c < 8; ++c)
-            if (cb + c < nout) y[c] = ((double)hi[c] + (double)lo[c]) * (tscale * rscale[cb + c]);
+            if (cb + c < nout) {
+              const float m = rowmul[cb + c];
+              Y[(long long)(cb + c) * ncell + e] = make_float2(hi[c] * m, lo[c] * m);
+            }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -265,6 +280,196 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
   __syncthreads();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ---------------------------------------------------------------------------------------
+// the correction of Sec. 2.3 from the double-float time means (value (hi + lo) 2^k, k = the
+// outputs' exponent + gmax - 16): volume term sum_d nu_d (D along d) W-bar and upwind face
+// values nu_d^+ tr_+(left) + nu_d^- tr_-(right), in double-float FP32; each face value is
+// computed by both of its cells from the same traces in the same order (the same bits), the
+// state update is FP64.  The kernel then writes the new state's digit planes (exponent from
+// the previous maximum plus one bit of headroom, checked) and accumulates the new maximum.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ DF3 df3_mul(float ch, float cl, DF3 a) {
+  const float p = __fmul_rn(ch, a.h);
+  float e = __fmaf_rn(ch, a.h, -p);
+  e = __fmaf_rn(ch, a.l, e);
+  e = __fmaf_rn(cl, a.h, e);
+  const float s = __fadd_rn(p, e);
+  return DF3{s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+
+__device__ __forceinline__ DF3 df3_add(DF3 a, DF3 b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  const float s2 = __fadd_rn(s, e);
+  return DF3{s2, __fsub_rn(e, __fsub_rn(s2, s))};
+}
+
+
+// float * 2^k as a double, by exponent arithmetic on the bits (exact; 0 stays 0)
+__device__ __forceinline__ double f2d_scale(float f, int k) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e8 = (b >> 23) & 0xFF;
+  if (e8 == 0) return 0.0;
+  const int e11 = (int)e8 - 127 + 1023 + k;
+  if (e11 <= 0) return 0.0;
+  const uint32_t hiw = (b & 0x80000000u) | ((uint32_t)e11 << 20) | ((b & 0x7FFFFFu) >> 3);
+  const uint32_t low = (b & 0x7u) << 29;
+  return __hiloint2double((int)hiw, (int)low);
+}
+
+// Face values of the +d face of every cell for the NB^2 lines t crossing it:
+// F[(d NT + t) cells + e] = nu_d^+ tr_+(W-bar_e)[t] + nu_d^- tr_-(W-bar_right)[t], one thread
+// per (cell, d).  Each face value is computed once; both its cells read it.
+template <int NB>
+__global__ void __launch_bounds__(128) mixed3_faces_kernel(const float2* __restrict__ Y, int nx,
+                                                           int ny, int nz, CorrParams cp,
+                                                           float2* __restrict__ F) {
+  constexpr int NT = NB * NB;
+  const long long ncell = (long long)nx * ny * nz;
+  const int dd = blockIdx.y;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ncell) return;
+  const unsigned ue = (unsigned)e, ur = ue / (unsigned)nx;
+  const int ix = (int)(ue - ur * (unsigned)nx), iy = (int)(ur % (unsigned)ny), iz = (int)(ur / (unsigned)ny);
+  int rxi = ix, ryi = iy, rzi = iz;
+  if (dd == 0) rxi = ix + 1 == nx ? 0 : ix + 1;
+  if (dd == 1) ryi = iy + 1 == ny ? 0 : iy + 1;
+  if (dd == 2) rzi = iz + 1 == nz ? 0 : iz + 1;
+  const long long jr = ((long long)rzi * ny + ryi) * nx + rxi;
+  const int st = dd == 0 ? 1 : (dd == 1 ? NB : NB * NB);
+  const float nph = cp.nph[dd], npl = cp.npl[dd], nmh = cp.nmh[dd], nml = cp.nml[dd];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int base = t % st + (t / st) * st * NB;
+    DF3 tp{0.f, 0.f}, tm{0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const float sg = (b & 1) ? -1.f : 1.f;  // phi_b(-1) = (-1)^b phi_b(+1)
+      const float2 yo = Y[(base + b * st) * ncell + e];
+      const float2 yr = Y[(base + b * st) * ncell + jr];
+      tp = df3_add(tp, df3_mul(cp.eph[b], cp.epl[b], DF3{yo.x, yo.y}));
+      tm = df3_add(tm, df3_mul(sg * cp.eph[b], sg * cp.epl[b], DF3{yr.x, yr.y}));
+    }
+    const DF3 f = df3_add(df3_mul(nph, npl, tp), df3_mul(nmh, nml, tm));
+    F[(long long)(dd * NT + t) * ncell + e] = make_float2(f.h, f.l);
+  }
+}
+
+// The update: one thread per (cell, 8-mode group).  dQ = sum_d [nu_d (D along d) W-bar
+// - phi_a(+1) F(i + 1/2) + phi_a(-1) F(i - 1/2)] in double-float, Q += dQ in FP64, then the
+// group's digit rows of the new state (and ghost copies) and the running maximum.
+template <int NB, int S>
+__global__ void __launch_bounds__(128) mixed3_correct_kernel(
+    double* __restrict__ Q, const float2* __restrict__ Y, const float2* __restrict__ F, int nx,
+    int ny, int nz, CorrParams cp, int gmax, int* __restrict__ exps,
+    unsigned long long* __restrict__ maxbits, uint4* __restrict__ planes, int* status) {
+  constexpr int THS = NB * NB * NB, NT = NB * NB;
+  constexpr int P = ((THS + 15) / 16) * 2;
+  __shared__ unsigned long long shmax[4];
+  const long long ncell = (long long)nx * ny * nz;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int ys = exps[1];
+  const int snext = exponent_above(maxbits[0]) + 1;
+  unsigned long long mymax = 0;
+  bool fits = true;
+  if (i < ncell * P) {
+    const long long e = i / P;
+    const int pg = (int)(i % P), m0 = 8 * pg;
+    const unsigned ue = (unsigned)e, ur = ue / (unsigned)nx;
+    const int ix = (int)(ue - ur * (unsigned)nx), iy = (int)(ur % (unsigned)ny), iz = (int)(ur / (unsigned)ny);
+    const int co[3] = {ix, iy, iz}, nn[3] = {nx, ny, nz};
+    DF3 dq[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) dq[j] = DF3{0.f, 0.f};
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      const int st = dd == 0 ? 1 : (dd == 1 ? NB : NB * NB);
+      const float nuh = cp.nuh[dd], nul = cp.nul[dd];
+      int l[3] = {ix, iy, iz};
+      l[dd] = co[dd] == 0 ? nn[dd] - 1 : co[dd] - 1;
+      const long long jl = ((long long)l[2] * ny + l[1]) * nx + l[0];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int sm = m0 + j;
+        if (sm >= THS) continue;
+        const int a = (sm / st) % NB;                  // index along d
+        const int base = sm - a * st;                  // the line's first mode
+        const int t = (base % st) + (base / (st * NB)) * st;  // line index
+        // volume term (D[a][b] != 0 only for a > b, a + b odd)
+        DF3 acc{0.f, 0.f};
+        bool any = false;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          if (a > b && ((a + b) & 1)) {
+            const float2 y = Y[(base + b * st) * ncell + e];
+            acc = df3_add(acc, df3_mul(cp.Dh[a * kMaxNB + b], cp.Dl[a * kMaxNB + b], DF3{y.x, y.y}));
+            any = true;
+          }
+        DF3 v = dq[j];
+        if (any) v = df3_add(v, df3_mul(nuh, nul, acc));
+        const float2 fp = F[(long long)(dd * NT + t) * ncell + e];
+        const float2 fm = F[(long long)(dd * NT + t) * ncell + jl];
+        const float sg = (a & 1) ? -1.f : 1.f;
+        v = df3_add(v, df3_mul(-cp.eph[a], -cp.epl[a], DF3{fp.x, fp.y}));
+        v = df3_add(v, df3_mul(sg * cp.eph[a], sg * cp.epl[a], DF3{fm.x, fm.y}));
+        dq[j] = v;
+      }
+    }
+    const int kfin = ys + gmax - 16;
+    double qn[8];
+    double* q = Q + e * THS;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (m0 + j < THS) {
+        double v = q[m0 + j];
+        v = v + f2d_scale(dq[j].h, kfin);
+        v = v + f2d_scale(dq[j].l, kfin);
+        q[m0 + j] = v;
+        qn[j] = v;
+        const unsigned long long ab = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+        mymax = ab > mymax ? ab : mymax;
+      } else {
+        qn[j] = 0.0;
+      }
+    }
+    uint4 rows[S];
+    fits = make_digit_rows<S>(qn, snext, rows);
+    const long long pnx = nx + 2, pny = ny + 2;
+    const long long plane = pnx * pny * (nz + 2);
+    int px[2] = {ix + 1, -1}, py[2] = {iy + 1, -1}, pz[2] = {iz + 1, -1};
+    if (ix == 0) px[1] = nx + 1;
+    if (ix == nx - 1) px[1] = 0;
+    if (iy == 0) py[1] = ny + 1;
+    if (iy == ny - 1) py[1] = 0;
+    if (iz == 0) pz[1] = nz + 1;
+    if (iz == nz - 1) pz[1] = 0;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+      uint4* base = planes + (long long)(a * P + pg) * plane;
+#pragma unroll
+      for (int zi = 0; zi < 2; ++zi) {
+        if (pz[zi] < 0) continue;
+#pragma unroll
+        for (int yi = 0; yi < 2; ++yi) {
+          if (py[yi] < 0) continue;
+#pragma unroll
+          for (int xi = 0; xi < 2; ++xi) {
+            if (px[xi] < 0) continue;
+            base[((long long)pz[zi] * pny + py[yi]) * pnx + px[xi]] = rows[a];
+          }
+        }
+      }
+    }
+  }
+  if (!fits) atomicOr(status, kStatusRange);
+  const unsigned long long bm = block_max_bits(mymax, shmax);
+  if (threadIdx.x == 0) {
+    atomicMax(maxbits + 1, bm);
+    if (blockIdx.x == 0) exps[0] = snext;
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -286,7 +491,8 @@ __global__ void __launch_bounds__(128) state_digits3_kernel(const double* __rest
   if (i >= ncell * P) return;
   const long long e = i / P;
   const int p = (int)(i % P);
-  const int ix = (int)(e % nx), iy = (int)((e / nx) % ny), iz = (int)(e / ((long long)nx * ny));
+  const unsigned ue = (unsigned)e, ur = ue / (unsigned)nx;
+  const int ix = (int)(ue - ur * (unsigned)nx), iy = (int)(ur % (unsigned)ny), iz = (int)(ur / (unsigned)ny);
   double v[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = (p * 8 + j < THS) ? Q[e * THS + p * 8 + j] : 0.0;
@@ -360,8 +566,8 @@ int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_o
 }
 
 template <int NB>
-static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& ms, double* Y,
-                                  int ystride, cudaStream_t s) {
+static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& ms, void* Y,
+                                  cudaStream_t s) {
   const Gemm3Layout L = gemm3_layout(op.slices, NB * NB * NB);
   // one CTA per SM: each allocates all 512 TMEM columns, so a second CTA on the SM would
   // only wait for them -- ask for more than half the shared memory
@@ -375,18 +581,46 @@ static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& 
   const int ntiles = ((g.n[0] + kTX - 1) / kTX) * ((g.n[1] + kTY - 1) / kTY) * g.n[2];
   const int grid = std::min(ntiles, sms);
   kern<<<grid, kGemmThreads, smem, s>>>(*(const CUtensorMap*)ms.map,
-                                           (const unsigned char*)op.b_slices, op.row_scale,
-                                           op.slices, op.nout, Y, ystride, ms.exps, g.n[0], g.n[1],
-                                           g.n[2], ms.status);
+                                        (const unsigned char*)op.b_slices, op.row_mul, op.slices,
+                                        op.nout, (float2*)Y, ms.exps, ms.maxbits, g.n[0], g.n[1],
+                                        g.n[2], ms.status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, double* Y,
-                               int ystride, cudaStream_t s) {
+cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
+                               cudaStream_t s) {
   if (g.dim != 3) return cudaErrorInvalidValue;
   switch (nb) {
-    case 2: return launch_gemm3_t<2>(g, op, ms, Y, ystride, s);
-    case 3: return launch_gemm3_t<3>(g, op, ms, Y, ystride, s);
+    case 2: return launch_gemm3_t<2>(g, op, ms, Y, s);
+    case 3: return launch_gemm3_t<3>(g, op, ms, Y, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int NB, int S>
+static cudaError_t launch_correct3_t(const Grid& g, double* Q, const void* Y, void* F, int gmax,
+                                     const CorrParams& cp, MixedState& ms, cudaStream_t s) {
+  constexpr int P = ((NB * NB * NB + 15) / 16) * 2;
+  const dim3 fblocks((unsigned)((g.ncell + 127) / 128), 3);
+  mixed3_faces_kernel<NB><<<fblocks, 128, 0, s>>>((const float2*)Y, g.n[0], g.n[1], g.n[2], cp,
+                                                  (float2*)F);
+  const unsigned blocks = (unsigned)((g.ncell * P + 127) / 128);
+  mixed3_correct_kernel<NB, S><<<blocks, 128, 0, s>>>(Q, (const float2*)Y, (const float2*)F,
+                                                      g.n[0], g.n[1], g.n[2], cp, gmax, ms.exps,
+                                                      ms.maxbits, (uint4*)ms.planes, ms.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed3_correct(const Grid& g, int nb, int slices, double* Q, const void* Y,
+                                  void* F, int gmax, const CorrParams& cp, MixedState& ms,
+                                  cudaStream_t s) {
+  if (g.dim != 3) return cudaErrorInvalidValue;
+  switch (nb * 16 + slices) {
+#define RIDG_C3(NBV, SV) \
+  case NBV * 16 + SV: return launch_correct3_t<NBV, SV>(g, Q, Y, F, gmax, cp, ms, s);
+    RIDG_C3(2, 2) RIDG_C3(2, 3) RIDG_C3(2, 4) RIDG_C3(2, 5) RIDG_C3(2, 6)
+    RIDG_C3(3, 2) RIDG_C3(3, 3) RIDG_C3(3, 4) RIDG_C3(3, 5) RIDG_C3(3, 6)
+#undef RIDG_C3
     default: return cudaErrorInvalidValue;
   }
 }

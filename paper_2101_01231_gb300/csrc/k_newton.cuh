@@ -911,7 +911,8 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV>::MINB)) newton_ke
     const long long e = misc[0];
     __syncthreads();
     if (e >= a.ncell) break;
-    const int ix = (int)(e % nx), iy = (int)(e / nx);
+    const unsigned ue = (unsigned)e, uy = ue / (unsigned)nx;
+    const int ix = (int)(ue - uy * (unsigned)nx), iy = (int)uy;
     for (int i = tid; i < 9 * MV * D::THS; i += kThreads) {
       const int r = i / (MV * D::THS), rem = i % (MV * D::THS);
       const long long c = (long long)((iy + r / 3 - 1 + ny) % ny) * nx + (ix + r % 3 - 1 + nx) % nx;

@@ -181,7 +181,8 @@ __global__ void __launch_bounds__(kCorrThreads) nl_correct_kernel(NlDev tb, doub
   __shared__ double spd[4][QF];
   const int tid = threadIdx.x;
   const long long e = blockIdx.x;
-  const int ix = (int)(e % nx), iy = (int)(e / nx);
+  const unsigned ue = (unsigned)e, uy = ue / (unsigned)nx;
+  const int ix = (int)(ue - uy * (unsigned)nx), iy = (int)uy;
   const long long nbr[5] = {e, (long long)iy * nx + (ix + 1) % nx, (long long)iy * nx + (ix + nx - 1) % nx,
                             (long long)((iy + 1) % ny) * nx + ix, (long long)((iy + ny - 1) % ny) * nx + ix};
   for (int i = tid; i < 5 * BS; i += kCorrThreads) Wc[i / BS][i % BS] = W[nbr[i / BS] * BS + i % BS];

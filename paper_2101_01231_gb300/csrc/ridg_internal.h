@@ -19,6 +19,9 @@ struct CorrParams {
   float eph[kMaxNB], epl[kMaxNB];      // phi_b(+1) as a double-float pair
   double D[kMaxNB * kMaxNB];           // int phi_a' phi_b
   double nu[3], nup[3], num[3];        // a_d dt / h_d and its positive / negative parts
+  // the same constants as double-float pairs (hi, lo), for the FP32 correction kernels
+  float Dh[kMaxNB * kMaxNB], Dl[kMaxNB * kMaxNB];
+  float nuh[3], nul[3], nph[3], npl[3], nmh[3], nml[3];
 };
 
 struct Grid {
@@ -75,9 +78,15 @@ cudaError_t launch_mixed_correct(const Grid& g, int nb, int slices, double* Q, c
 bool mixed3_supported(int nb, int slices);
 size_t mixed3_plane_bytes(const Grid& g, int nb, int slices);
 int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_out);
-// Y[e * ystride + c] = (P-bar X_e)[c] in FP64 from the digit planes in ms
-cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, double* Y,
-                               int ystride, cudaStream_t s);
+// Y[c * cells + e] = (P-bar X_e)[c] as double-float pairs from the digit planes in ms (value
+// (hi + lo) 2^(exps[1] + gmax - 16))
+cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
+                               cudaStream_t s);
+// the correction from those outputs, plus the new state's digit planes and maximum
+// (F: scratch for the face values, 3 NB^2 float2 per cell)
+cudaError_t launch_mixed3_correct(const Grid& g, int nb, int slices, double* Q, const void* Y,
+                                  void* F, int gmax, const CorrParams& cp, MixedState& ms,
+                                  cudaStream_t s);
 // max |Q| and the 3D digit planes of Q
 cudaError_t launch_mixed3_refresh(const Grid& g, int nb, int slices, const double* Q,
                                   MixedState& ms, cudaStream_t s);
