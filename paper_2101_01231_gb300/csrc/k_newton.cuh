@@ -829,14 +829,18 @@ __device__ void matvec_sub(const T* M, const T* x, T* y) {
 }
 
 // Solve J x = b by block elimination in the plan's order; b in xs (9 x BP), x returned there.
-template <typename T, int BS, int BP, int RR, int NBUF>
+template <typename T, int BS, int BP, int RR, int NBUF, bool KEEP>
 __device__ void block_solve(T* slots, const NlPlan& plan, T* xs, T* S, T* sA, T* sB, T* colv,
                             T* rowp, int* prow, int* rank, int* flags) {
   const int tid = threadIdx.x;
   for (int t = 0; t < 9; ++t) {
     const int k = plan.order[t];
-    gj_inverse<T, BS, BP, RR>(slots + (size_t)plan.slot[k * 10] * BP * BP, S, colv, rowp, prow,
-                              rank, flags);
+    T* Akk = slots + (size_t)plan.slot[k * 10] * BP * BP;
+    gj_inverse<T, BS, BP, RR>(Akk, S, colv, rowp, prow, rank, flags);
+    if (KEEP) {
+      // keep the inverse in the (no longer needed) diagonal slot for later solves
+      for (int i = tid; i < BP * BP; i += kThreads) Akk[i] = S[i];
+    }
     // x_k <- S x_k (via a zeroed copy: y = x - S x computed as 0 - (-S) x is avoided by
     // writing the product straight into colv)
     T* xk = xs + k * BP;
@@ -863,6 +867,33 @@ __device__ void block_solve(T* slots, const NlPlan& plan, T* xs, T* S, T* sA, T*
       }
     }
     __syncthreads();
+  }
+  for (int t = 8; t >= 0; --t) {
+    const int k = plan.order[t];
+    for (int a = 0; a < plan.nn[t]; ++a) {
+      const int j = plan.nbr[t][a];
+      matvec_sub<T, BS, BP>(slots + (size_t)plan.slot[k * 9 + j] * BP * BP, xs + j * BP, xs + k * BP);
+    }
+  }
+}
+
+// Solve J x = b again with the factors block_solve<KEEP = true> left in the slots (pivot
+// inverses in the diagonal slots, A_ik below, U_kj above): block matvecs only.
+template <typename T, int BS, int BP>
+__device__ void stored_solve(const T* slots, const NlPlan& plan, T* xs, T* tmp) {
+  const int tid = threadIdx.x;
+  for (int t = 0; t < 9; ++t) {
+    const int k = plan.order[t];
+    T* xk = xs + k * BP;
+    for (int i = tid; i < BP; i += kThreads) tmp[i] = T(0);
+    __syncthreads();
+    matvec_sub<T, BS, BP>(slots + (size_t)plan.slot[k * 10] * BP * BP, xk, tmp);  // -inv x_k
+    for (int i = tid; i < BS; i += kThreads) xk[i] = -tmp[i];
+    __syncthreads();
+    for (int a = 0; a < plan.nn[t]; ++a) {
+      const int i = plan.nbr[t][a];
+      matvec_sub<T, BS, BP>(slots + (size_t)plan.slot[i * 9 + k] * BP * BP, xk, xs + i * BP);
+    }
   }
   for (int t = 8; t >= 0; --t) {
     const int k = plan.order[t];
@@ -925,23 +956,35 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV>::MINB)) newton_ke
     }
     __syncthreads();
     frozen_alpha<NB, MV, FLUX>(a.tb, Ws, alpha, (double*)arena, a.gamma);
-    int it = 0;
-    bool conv = false, bad = false;
-    while (it < a.max_iters && !conv && !bad) {
+    // FP64 form: Newton (a new Jacobian every iteration).  FP32 form: after a factorisation,
+    // refinement sweeps reuse it with the FP64 residual while each contracts the update by
+    // at least 10x (at most kSweeps per factorisation); max_iters caps the factorisations.
+    constexpr bool CHORD = sizeof(T) == 4;
+    constexpr int kSweeps = 3;
+    int it = 0, sweeps = 0;
+    bool conv = false, bad = false, refactor = true;
+    double dprev = 0.0;
+    while (!conv && !bad) {
+      if (refactor && it >= a.max_iters) break;
       residual<NB, MV, FLUX>(a.tb, Ws, Qs, Rs, alpha, (double*)arena, a.lam, a.gamma);
-      for (int r0 = 0; r0 < 9; r0 += D::CG) {
-        for (int g = 0; g < D::CG; ++g)
-          project_cell<T, NB, MV, FLUX>(a.tb, r0 + g, Ws, alpha, FA + g * D::FAS, jw, jb0, jb1,
-                                        a.lam, a.gamma);
-        assemble_cells<T, NB, MV>(a.tb, a.plan, r0, FA, slots);
+      if (refactor) {
+        for (int r0 = 0; r0 < 9; r0 += D::CG) {
+          for (int g = 0; g < D::CG; ++g)
+            project_cell<T, NB, MV, FLUX>(a.tb, r0 + g, Ws, alpha, FA + g * D::FAS, jw, jb0, jb1,
+                                          a.lam, a.gamma);
+          assemble_cells<T, NB, MV>(a.tb, a.plan, r0, FA, slots);
+        }
       }
       for (int i = tid; i < 9 * D::BP; i += kThreads) {
         const int r = i / D::BP, c = i % D::BP;
         xs[i] = c < D::BS ? (T)Rs[r * D::BS + c] : T(0);
       }
       __syncthreads();
-      block_solve<T, D::BS, D::BP, D::RR, L::NBUF>(slots, a.plan, xs, S, sA, sB, colv, rowp,
-                                                   prow, rank, flags);
+      if (refactor)
+        block_solve<T, D::BS, D::BP, D::RR, L::NBUF, CHORD>(slots, a.plan, xs, S, sA, sB, colv,
+                                                            rowp, prow, rank, flags);
+      else
+        stored_solve<T, D::BS, D::BP>(slots, a.plan, xs, colv);
       double dn = 0.0, wn = 0.0;
       bool fin = true;
       for (int i = tid; i < 9 * D::BS; i += kThreads) {
@@ -955,9 +998,16 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV>::MINB)) newton_ke
       const double nf = block_max(fin ? 0.0 : 1.0, red);
       dn = block_max(dn, red);
       wn = block_max(wn, red);
-      ++it;
+      if (refactor) {
+        ++it;
+        sweeps = 0;
+      } else {
+        ++sweeps;
+      }
       bad = nf > 0.0;
       conv = !bad && dn <= a.tol * fmax(1.0, wn);
+      refactor = !CHORD || (sweeps > 0 && dn > 0.1 * dprev) || sweeps >= kSweeps;
+      dprev = dn;
     }
     for (int i = tid; i < D::BS; i += kThreads) a.W[e * D::BS + i] = Ws[4 * D::BS + i];
     if (tid == 0) {
