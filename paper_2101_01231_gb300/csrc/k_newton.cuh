@@ -17,6 +17,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "k_nlflux.cuh"
 #include "ridg_internal.h"
 
@@ -801,30 +803,38 @@ __device__ void gemm_left_inplace(const T* S, T* B, T* sB) {
     for (int b = 0; b < RR; ++b) B[(size_t)(ty + 16 * a) * BP + tx + 16 * b] = acc[a][b];
 }
 
-// y -= M x for the first BS rows (M global or shared, x and y shared): each warp takes 4
-// rows at a time, so that every lane has 4 independent loads per column stride in flight
+// y -= M x for the first BS rows (M global or shared, x and y shared).  Two threads per row,
+// each summing half of the row with all of its vector loads issued back to back, so one
+// memory round trip serves the whole block (BP <= 128, 256 threads).
 template <typename T, int BS, int BP>
 __device__ void matvec_sub(const T* M, const T* x, T* y) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r0 = warp * 4; r0 < BS; r0 += 4 * (kThreads / 32)) {
-    T s[4] = {T(0), T(0), T(0), T(0)};
-    for (int c = lane; c < BS; c += 32) {
-      const T xv = x[c];
+  constexpr int VW = sizeof(T) == 4 ? 4 : 2;  // elements per 16-byte vector
+  constexpr int HALF = BP / 2;                // BP is a multiple of 16: HALF of VW
+  constexpr int NV = HALF / VW;
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
+  T s = T(0);
+  if (r < BS) {
+    const V* row = reinterpret_cast<const V*>(M + (size_t)r * BP + h * HALF);
+    V v[NV];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (r0 + u < BS) s[u] = fma(M[(size_t)(r0 + u) * BP + c], xv, s[u]);
-    }
+    for (int u = 0; u < NV; ++u) v[u] = row[u];
+    const T* xh = x + h * HALF;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      for (int o = 16; o > 0; o >>= 1) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
-    if (lane < 4 && r0 + lane < BS) {
-      T v = s[0];
-#pragma unroll
-      for (int u = 1; u < 4; ++u)
-        if (lane == u) v = s[u];
-      y[r0 + lane] -= v;
+    for (int u = 0; u < NV; ++u) {
+      if constexpr (sizeof(T) == 4) {
+        s = fma(v[u].x, xh[4 * u], s);
+        s = fma(v[u].y, xh[4 * u + 1], s);
+        s = fma(v[u].z, xh[4 * u + 2], s);
+        s = fma(v[u].w, xh[4 * u + 3], s);
+      } else {
+        s = fma(v[u].x, xh[2 * u], s);
+        s = fma(v[u].y, xh[2 * u + 1], s);
+      }
     }
   }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  if (r < BS && h == 0) y[r] -= s;
   __syncthreads();
 }
 
