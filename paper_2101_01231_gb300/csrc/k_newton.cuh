@@ -40,6 +40,20 @@ struct Dims {
   static constexpr int PB = 2 * MM * QP > 8 * MM * QPF ? 2 * MM * QP : 8 * MM * QPF;
 };
 
+// scratch sizes (doubles) of the residual's buffers
+template <int NB, int MV>
+struct ResBufs {
+  using D = Dims<NB, MV>;
+  static constexpr int C = 9 * MV, NQ = D::NQ, QV = D::QV, QF = D::QF;
+  static constexpr int c2max(int a, int b) { return a > b ? a : b; }
+  static constexpr int R1 = c2max(C * QV, 4 * C * QF);  // G_d; the faces' traces and fluxes
+  static constexpr int R2 = c2max(c2max(C * NB * NB * NQ, C * QV), c2max(2 * C * NB * NB, 2 * C * NQ * NB));
+  static constexpr int R3 = c2max(c2max(C * NB * NQ * NQ, C * NQ * NQ * NB), 2 * C * NB * NQ);
+  static constexpr int R4 = C * D::THT;                 // volume term
+  static constexpr int R5 = 4 * C * NB * NB;            // face terms, per face
+  static constexpr int total = R1 + R2 + R3 + R4 + R5;
+};
+
 constexpr size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 
@@ -105,7 +119,7 @@ struct Layout {
   static constexpr size_t oMisc = up16(oRank + sizeof(int) * D::BP);
   static constexpr size_t oArena = up16(oMisc + sizeof(int) * 16);
   // phase arenas
-  static constexpr size_t aRes = sizeof(double) * (9 * 2 * MV * D::QV + 9 * 4 * MV * D::QF);
+  static constexpr size_t aRes = sizeof(double) * ResBufs<NB, MV>::total;
   static constexpr size_t aAlpha = sizeof(double) * 12 * D::QF;
   static constexpr size_t oJW = up16(sizeof(T) * D::CG * D::FAS);     // after the FA arrays
   static constexpr size_t oJB0 = up16(oJW + sizeof(T) * MV * D::QP);
@@ -230,71 +244,149 @@ __device__ void frozen_alpha(const NlDev& tb, const double* Ws, double* alpha, d
 
 // ---------------------------------------------------------------------------------------
 // residual of eq. pred_full_system for the 9 region cells (FP64), divided by |T|:
-//   R = time term - psi(-1) Q - volume flux + surface flux
+//   R = time term - psi(-1) Q - volume flux + surface flux,
+// with the tensor-product quadrature evaluated by sum factorisation: every pass contracts
+// one axis of a [component][t][y][x] tensor with a 1D table.
 // ---------------------------------------------------------------------------------------
+// out[c][o2][o1][o0] (+)= sum_i M[o_ax * ldm + i] in[c][..i..]: axis AX (0 = fastest) of the
+// input [A2][A1][A0] contracted into NO outputs; components c >= csplit use M2 instead of M1
+template <int A2, int A1, int A0, int AX, int NO, bool ACC = false>
+__device__ void apply1d(const double* in, double* out, const double* M1, const double* M2,
+                        int ldm, int ncomp, int csplit) {
+  constexpr int NI = AX == 0 ? A0 : (AX == 1 ? A1 : A2);
+  constexpr int O2 = AX == 2 ? NO : A2, O1 = AX == 1 ? NO : A1, O0 = AX == 0 ? NO : A0;
+  constexpr int OSZ = O2 * O1 * O0, ISZ = A2 * A1 * A0;
+  constexpr int IST = AX == 0 ? 1 : (AX == 1 ? A0 : A0 * A1);
+  for (int idx = threadIdx.x; idx < ncomp * OSZ; idx += kThreads) {
+    const int c = idx / OSZ, o = idx % OSZ;
+    const int i2 = o / (O1 * O0), i1 = (o / O0) % O1, i0 = o % O0;
+    const int oa = AX == 0 ? i0 : (AX == 1 ? i1 : i2);
+    const int base = c * ISZ + (AX == 2 ? 0 : i2 * A1 * A0) + (AX == 1 ? 0 : i1 * A0) + (AX == 0 ? 0 : i0);
+    const double* M = (c >= csplit ? M2 : M1) + oa * ldm;
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) acc = fma(M[i], in[base + i * IST], acc);
+    if (ACC)
+      out[idx] += acc;
+    else
+      out[idx] = acc;
+  }
+}
+
 template <int NB, int MV, int FLUX>
 __device__ void residual(const NlDev& tb, const double* Ws, const double* Qs, double* Rs,
                          const double* alpha, double* arena, const double* lam, double g) {
   using D = Dims<NB, MV>;
-  double* G = arena;                              // [9][2][MV][QV]
-  double* H = arena + 9 * 2 * MV * D::QV;         // [9][4][MV][QF]
-  for (int i = threadIdx.x; i < 9 * D::QV; i += kThreads) {
-    const int r = i / D::QV, q = i % D::QV;
-    double w[MV], f[MV];
-    for (int j = 0; j < MV; ++j) w[j] = dotcol<D::THT>(tb.PsiV, D::QV, q, Ws + (r * MV + j) * D::THT);
-    for (int dd = 0; dd < 2; ++dd) {
+  using B = ResBufs<NB, MV>;
+  constexpr int C = B::C, NQ = D::NQ, QV = D::QV, QF = D::QF, THT = D::THT, THS = D::THS;
+  double* r1 = arena;
+  double* r2 = r1 + B::R1;
+  double* r3 = r2 + B::R2;
+  double* rv = r3 + B::R3;
+  double* k2 = rv + B::R4;
+  // ---- values of W at the volume points: x, y, t passes ----
+  apply1d<NB, NB, NB, 0, NQ>(Ws, r2, tb.V1T, tb.V1T, NB, C, C);
+  __syncthreads();
+  apply1d<NB, NB, NQ, 1, NQ>(r2, r3, tb.V1T, tb.V1T, NB, C, C);
+  __syncthreads();
+  apply1d<NB, NQ, NQ, 2, NQ>(r3, r2, tb.V1T, tb.V1T, NB, C, C);  // w: [c][qt][qy][qx]
+  __syncthreads();
+  // ---- volume term: sum_q d_d Psi_k w_q F_d, per direction ----
+  for (int dd = 0; dd < 2; ++dd) {
+    for (int i = threadIdx.x; i < 9 * QV; i += kThreads) {
+      const int r = i / QV, q = i % QV;
+      double w[MV], f[MV];
+      for (int j = 0; j < MV; ++j) w[j] = r2[(r * MV + j) * QV + q];
       nlflux::F<FLUX>(w, dd, f, g);
       const double s = 0.25 * lam[dd] * tb.wV[q];
-      for (int j = 0; j < MV; ++j) G[((r * 2 + dd) * MV + j) * D::QV + q] = s * f[j];
+      for (int j = 0; j < MV; ++j) r1[(r * MV + j) * QV + q] = s * f[j];
     }
+    __syncthreads();
+    const double* Mx = dd == 0 ? tb.dV1 : tb.V1;
+    const double* My = dd == 0 ? tb.V1 : tb.dV1;
+    apply1d<NQ, NQ, NQ, 0, NB>(r1, r3, Mx, Mx, NQ, C, C);
+    __syncthreads();
+    apply1d<NQ, NQ, NB, 1, NB>(r3, r1, My, My, NQ, C, C);
+    __syncthreads();
+    if (dd == 0)
+      apply1d<NQ, NB, NB, 2, NB, false>(r1, rv, tb.V1, tb.V1, NQ, C, C);
+    else
+      apply1d<NQ, NB, NB, 2, NB, true>(r1, rv, tb.V1, tb.V1, NQ, C, C);
+    __syncthreads();
   }
-  for (int i = threadIdx.x; i < 9 * 4 * D::QF; i += kThreads) {
-    const int r = i / (4 * D::QF), f = (i / D::QF) % 4, q = i % D::QF;
-    const int dd = f >> 1, si = f & 1, side = si ? -1 : 1;
-    const double* to = tb.PsiF + (size_t)(dd * 2 + si) * D::THT * D::QF;
-    double wo[MV], fo[MV], out[MV];
-    for (int j = 0; j < MV; ++j) wo[j] = dotcol<D::THT>(to, D::QF, q, Ws + (r * MV + j) * D::THT);
-    nlflux::F<FLUX>(wo, dd, fo, g);
-    const int r2 = region_nbr(r, dd, side);
-    if (r2 < 0) {
-      for (int j = 0; j < MV; ++j) out[j] = side * fo[j];  // region boundary: interior trace
+  // ---- faces, per direction: traces of both sides, Rusanov / interior fluxes, then the
+  // face basis (psi_a(t) phi_bo(other) phi_bd(+-1)) ----
+  for (int dd = 0; dd < 2; ++dd) {
+    double* trF = r1;              // [side][c][qt][qo]
+    double* H = r1 + 2 * C * QF;   // [side][c][qt][qo]
+    double* Z = r2;                // [side][c][a][bo]
+    double* Zo = r3;               // [side][c][a][qo]
+    if (dd == 0) {
+      apply1d<NB, NB, NB, 0, 1>(Ws, Z, tb.ep1, tb.ep1, NB, C, C);
+      apply1d<NB, NB, NB, 0, 1>(Ws, Z + C * NB * NB, tb.em1, tb.em1, NB, C, C);
+      __syncthreads();
+      apply1d<NB, NB, 1, 1, NQ>(Z, Zo, tb.V1T, tb.V1T, NB, 2 * C, 2 * C);
+      __syncthreads();
+      apply1d<NB, NQ, 1, 2, NQ>(Zo, trF, tb.V1T, tb.V1T, NB, 2 * C, 2 * C);
     } else {
-      const double* tn = tb.PsiF + (size_t)(dd * 2 + (si ^ 1)) * D::THT * D::QF;
-      double wn[MV], fn[MV];
-      for (int j = 0; j < MV; ++j) wn[j] = dotcol<D::THT>(tn, D::QF, q, Ws + (r2 * MV + j) * D::THT);
-      nlflux::F<FLUX>(wn, dd, fn, g);
-      const double a = alpha[region_face(r % 3, r / 3, dd, side)];
-      for (int j = 0; j < MV; ++j) {
-        const double fh = side > 0 ? 0.5 * (fo[j] + fn[j]) - 0.5 * a * (wn[j] - wo[j])
-                                   : 0.5 * (fn[j] + fo[j]) - 0.5 * a * (wo[j] - wn[j]);
-        out[j] = side * fh;
+      apply1d<NB, NB, NB, 1, 1>(Ws, Z, tb.ep1, tb.ep1, NB, C, C);
+      apply1d<NB, NB, NB, 1, 1>(Ws, Z + C * NB * NB, tb.em1, tb.em1, NB, C, C);
+      __syncthreads();
+      apply1d<NB, 1, NB, 0, NQ>(Z, Zo, tb.V1T, tb.V1T, NB, 2 * C, 2 * C);
+      __syncthreads();
+      apply1d<NB, 1, NQ, 2, NQ>(Zo, trF, tb.V1T, tb.V1T, NB, 2 * C, 2 * C);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * 9 * QF; i += kThreads) {
+      const int si = i / (9 * QF), r = (i / QF) % 9, q = i % QF;
+      const int side = si ? -1 : 1;
+      double wo[MV], fo[MV], out[MV];
+      for (int j = 0; j < MV; ++j) wo[j] = trF[(si * C + r * MV + j) * QF + q];
+      nlflux::F<FLUX>(wo, dd, fo, g);
+      const int r2n = region_nbr(r, dd, side);
+      if (r2n < 0) {
+        for (int j = 0; j < MV; ++j) out[j] = side * fo[j];  // region boundary: interior trace
+      } else {
+        double wn[MV], fn[MV];
+        for (int j = 0; j < MV; ++j) wn[j] = trF[((si ^ 1) * C + r2n * MV + j) * QF + q];
+        nlflux::F<FLUX>(wn, dd, fn, g);
+        const double a = alpha[region_face(r % 3, r / 3, dd, side)];
+        for (int j = 0; j < MV; ++j) {
+          const double fh = side > 0 ? 0.5 * (fo[j] + fn[j]) - 0.5 * a * (wn[j] - wo[j])
+                                     : 0.5 * (fn[j] + fo[j]) - 0.5 * a * (wo[j] - wn[j]);
+          out[j] = side * fh;
+        }
       }
+      const double s = 0.25 * lam[dd] * tb.wF[dd * QF + q];
+      for (int j = 0; j < MV; ++j) H[(si * C + r * MV + j) * QF + q] = s * out[j];
     }
-    const double s = 0.25 * lam[dd] * tb.wF[dd * D::QF + q];
-    for (int j = 0; j < MV; ++j) H[((r * 4 + f) * MV + j) * D::QF + q] = s * out[j];
+    __syncthreads();
+    double* K2 = k2 + dd * 2 * C * NB * NB;  // [side][c][a][bo]
+    if (dd == 0) {
+      apply1d<NQ, NQ, 1, 1, NB>(H, Zo, tb.V1, tb.V1, NQ, 2 * C, 2 * C);   // [side][c][qt][by]
+      __syncthreads();
+      apply1d<NQ, NB, 1, 2, NB>(Zo, K2, tb.V1, tb.V1, NQ, 2 * C, 2 * C);  // [side][c][a][by]
+    } else {
+      apply1d<NQ, 1, NQ, 0, NB>(H, Zo, tb.V1, tb.V1, NQ, 2 * C, 2 * C);   // [side][c][qt][bx]
+      __syncthreads();
+      apply1d<NQ, 1, NB, 2, NB>(Zo, K2, tb.V1, tb.V1, NQ, 2 * C, 2 * C);  // [side][c][a][bx]
+    }
+    __syncthreads();
   }
-  __syncthreads();
+  // ---- R = time term - source - volume + faces ----
   for (int i = threadIdx.x; i < 9 * D::BS; i += kThreads) {
-    const int r = i / D::BS, j = (i / D::THT) % MV, k = i % D::THT;
-    const int a = k / D::THS, s2 = k % D::THS;
-    const double* w = Ws + (r * MV + j) * D::THT;
+    const int c = i / THT, k = i % THT;  // c = r MV + j
+    const int a = k / THS, s2 = k % THS, by = s2 / NB, bx = s2 % NB;
+    const double* w = Ws + c * THT;
     double acc = 0.0;
-    for (int c = 0; c < NB; ++c) acc = fma(tb.Mt[a * NB + c], w[c * D::THS + s2], acc);
-    acc = fma(-tb.em[a], Qs[(r * MV + j) * D::THS + s2], acc);
-    for (int dd = 0; dd < 2; ++dd) {
-      const double* dp = tb.dPsiV + (size_t)(dd * D::THT + k) * D::QV;
-      const double* gg = G + ((r * 2 + dd) * MV + j) * D::QV;
-      double v = 0.0;
-      for (int q = 0; q < D::QV; ++q) v = fma(dp[q], gg[q], v);
-      acc -= v;
-    }
-    for (int f = 0; f < 4; ++f) {
-      const double* pf = tb.PsiF + (size_t)(f * D::THT + k) * D::QF;
-      const double* hh = H + ((r * 4 + f) * MV + j) * D::QF;
-      double v = 0.0;
-      for (int q = 0; q < D::QF; ++q) v = fma(pf[q], hh[q], v);
-      acc += v;
-    }
+    for (int e = 0; e < NB; ++e) acc = fma(tb.Mt[a * NB + e], w[e * THS + s2], acc);
+    acc = fma(-tb.em[a], Qs[c * THS + s2], acc);
+    acc -= rv[i];
+    // x faces: phi_bx(+-1) times the face term of (a, by); y faces: phi_by(+-1) times (a, bx)
+    acc = fma(tb.ep1[bx], k2[((0 * C + c) * NB + a) * NB + by], acc);
+    acc = fma(tb.em1[bx], k2[((1 * C + c) * NB + a) * NB + by], acc);
+    acc = fma(tb.ep1[by], k2[((2 * C + c) * NB + a) * NB + bx], acc);
+    acc = fma(tb.em1[by], k2[((3 * C + c) * NB + a) * NB + bx], acc);
     Rs[i] = acc;
   }
   __syncthreads();

@@ -54,6 +54,8 @@ int nl_tables_upload(int nb, NlDevTables& out, void* mem, size_t* bytes, cudaStr
                iwV = addd(t.wV), iPsiF = addd(t.PsiF), iwF = addd(t.wF), iPhiV = addd(t.PhiV),
                idPhiV = addd(t.dPhiV), iPhiF = addd(t.PhiF), iPsiAtP = addd(t.PsiAtP),
                iPsiAtFP = addd(t.PsiAtFP), iP1 = addd(t.P1), iPhiEq = addd(phieq);
+  const size_t iV1 = addd(t.V1), iV1T = addd(t.V1T), idV1 = addd(t.dV1), iep1 = addd(t.ep1),
+               iem1 = addd(t.em1);
   size_t ib[2][3], ig[8][3];
   for (int d = 0; d < 2; ++d) {
     ib[d][0] = addi(t.beta[d].ptr);
@@ -131,6 +133,11 @@ int nl_tables_upload(int nb, NlDevTables& out, void* mem, size_t* bytes, cudaStr
   tb.PsiAtFP = D(iPsiAtFP);
   tb.P1 = D(iP1);
   tb.PhiEq = D(iPhiEq);
+  tb.V1 = D(iV1);
+  tb.V1T = D(iV1T);
+  tb.dV1 = D(idV1);
+  tb.ep1 = D(iep1);
+  tb.em1 = D(iem1);
   for (int d = 0; d < 2; ++d) {
     tb.bptr[d] = I(ib[d][0]);
     tb.bp[d] = I(ib[d][1]);

@@ -91,6 +91,13 @@ NlHostTables build_nl_tables(int M) {
   values(nb, rq, V, dV);
   auto v1 = [&](int b, int q) { return V[(size_t)b * nq + q]; };
   auto d1 = [&](int b, int q) { return dV[(size_t)b * nq + q]; };
+  t.V1 = V;
+  t.dV1 = dV;
+  t.V1T.assign((size_t)nq * nb, 0.0);
+  for (int b = 0; b < nb; ++b)
+    for (int q = 0; q < nq; ++q) t.V1T[(size_t)q * nb + b] = V[(size_t)b * nq + q];
+  t.ep1 = t1.ep;
+  t.em1 = t1.em;
   t.wV.assign(t.Qv, 0.0);
   t.PsiV.assign((size_t)thT * t.Qv, 0.0);
   t.dPsiV.assign((size_t)2 * thT * t.Qv, 0.0);

@@ -21,6 +21,9 @@ struct NlHostTables {
   std::vector<double> em;         // psi_a(-1)
   std::vector<double> PsiV, dPsiV;   // thT x Qv, 2 x thT x Qv (d/dxi_x, d/dxi_y)
   std::vector<double> wV;            // Qv (tau slowest, then y, x)
+  // the same rule in 1D (for sum-factorised evaluation): phi_b(x_q) as nb x nq and nq x nb,
+  // phi_b'(x_q) as nb x nq, and the traces phi_b(+1), phi_b(-1)
+  std::vector<double> V1, V1T, dV1, ep1, em1;
   std::vector<double> PsiF;          // [dim][side (+1, -1)][thT][Qf]
   std::vector<double> wF;            // [dim][Qf] (tau slowest, then the other dimension)
   std::vector<double> PhiV, dPhiV;   // thS x Qv, 2 x thS x Qv (spatial basis, for the correction)

@@ -95,6 +95,7 @@ cudaError_t launch_mixed3_refresh(const Grid& g, int nb, int slices, const doubl
 // Device copies of the host-built tables (nl_tables.h), all inside one allocation.
 struct NlDev {
   const double *Mt, *em;                // time term, psi_a(-1)
+  const double *V1, *V1T, *dV1, *ep1, *em1;  // 1D residual rule (nl_tables.h)
   const double *PsiV, *dPsiV, *wV;      // residual volume rule
   const double *PsiF, *wF;              // residual face rule
   const double *PhiV, *dPhiV, *PhiF;    // spatial basis at the same points (correction)
