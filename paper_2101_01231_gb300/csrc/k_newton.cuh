@@ -469,6 +469,29 @@ __device__ void project_cell(const NlDev& tb, int r, const double* Ws, const dou
   __syncthreads();
 }
 
+// acc[g][ij] += sum over the list entries [e0, e1) of c * FA[g][off][ij]; the entries are
+// fetched several at a time so that their memory latencies overlap
+template <typename T, int CG, int MM, int FAS>
+__device__ __forceinline__ void list_accumulate(const Ent<T>* __restrict__ ent, int e0, int e1,
+                                                const T* FA, T (&acc)[CG][MM]) {
+  constexpr int U = MM == 1 ? 8 : 1;  // wide (system) accumulators leave no registers for more
+  for (int e = e0; e < e1; e += U) {
+    Ent<T> en[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (e + u < e1) en[u] = ent[e + u];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (e + u >= e1) break;
+      const T* v = FA + en[u].off * MM;
+#pragma unroll
+      for (int g = 0; g < CG; ++g)
+#pragma unroll
+        for (int ij = 0; ij < MM; ++ij) acc[g][ij] = fma(en[u].c, v[g * FAS + ij], acc[g][ij]);
+    }
+  }
+}
+
 // Assemble the diagonal blocks of cells r0 .. r0 + CG - 1 and their blocks towards the
 // region neighbours from the merged lists (one pass over the lists for all CG cells).
 template <typename T, int NB, int MV>
@@ -485,15 +508,7 @@ __device__ void assemble_cells(const NlDev& tb, const NlPlan& plan, int r0, cons
     for (int g = 0; g < CG; ++g)
 #pragma unroll
       for (int ij = 0; ij < MM; ++ij) acc[g][ij] = T(0);
-    const int e1 = tb.dptr[i + 1];
-    for (int e = tb.dptr[i]; e < e1; ++e) {
-      const Ent<T> en = dent[e];
-      const T* v = FA + en.off * MM;
-#pragma unroll
-      for (int g = 0; g < CG; ++g)
-#pragma unroll
-        for (int ij = 0; ij < MM; ++ij) acc[g][ij] = fma(en.c, v[g * FAS + ij], acc[g][ij]);
-    }
+    list_accumulate<T, CG, MM, FAS>(dent, tb.dptr[i], tb.dptr[i + 1], FA, acc);
     if (k % D::THS == l % D::THS) {
       const T mt = Mt[(k / D::THS) * NB + l / D::THS];
 #pragma unroll
@@ -542,15 +557,7 @@ __device__ void assemble_cells(const NlDev& tb, const NlPlan& plan, int r0, cons
       for (int g = 0; g < CG; ++g)
 #pragma unroll
         for (int ij = 0; ij < MM; ++ij) acc[g][ij] = T(0);
-      const int e1 = optr[i + 1];
-      for (int e = optr[i]; e < e1; ++e) {
-        const Ent<T> en = oent[e];
-        const T* v = FA + en.off * MM;
-#pragma unroll
-        for (int g = 0; g < CG; ++g)
-#pragma unroll
-          for (int ij = 0; ij < MM; ++ij) acc[g][ij] = fma(en.c, v[g * FAS + ij], acc[g][ij]);
-      }
+      list_accumulate<T, CG, MM, FAS>(oent, optr[i], optr[i + 1], FA, acc);
 #pragma unroll
       for (int g = 0; g < CG; ++g) {
         const int r = r0 + g, r2 = region_nbr(r, dd, side);
