@@ -152,7 +152,7 @@ def mixed3d_section(R, I, steps, warmup):
             ach = bytes_pred / (p["predict_ms"] * 1e-3) / 1e9
             r["roofline"] = {"bound": "hbm", "kernel": "mixed3_gemm (time-mean prediction)",
                              "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                             "traffic": None, "peak_source": f"HBM copy, {src}",
+                             "traffic": _recorded_traffic("mixed3"), "peak_source": f"HBM copy, {src}",
                              "tensor_executed_tflops": executed / (p["predict_ms"] * 1e-3) / 1e12,
                              "tensor_peak_tflops": bf16,
                              "algorithmic_tflops": 2.0 * thS * K * cells / (p["predict_ms"] * 1e-3) / 1e12}
