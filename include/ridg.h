@@ -77,8 +77,12 @@ enum {
   RIDG_PREC_MIXED_BF16 = 1,  /* linear prediction as a sliced BF16 tensor-core contraction
                                 with FP32 accumulation recombined in FP64 (split-operand
                                 refinement); correction, face sums and time in FP64       */
-  RIDG_PREC_MIXED_FP32 = 2   /* Newton linear solves in FP32 with the residual in FP64
+  RIDG_PREC_MIXED_FP32 = 2,  /* Newton linear solves in FP32 with the residual in FP64
                                 (nonlinear flux)                                          */
+  RIDG_PREC_MIXED_TF32 = 3   /* Newton linear solves with the Schur-complement block
+                                updates on the TF32 tensor cores (FP32 accumulation), FP32
+                                pivot inverses, and refinement sweeps against the FP64
+                                residual (nonlinear flux)                                 */
 };
 
 typedef void* (*ridg_alloc_fn)(size_t bytes, void* user);

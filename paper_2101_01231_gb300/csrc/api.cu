@@ -59,6 +59,12 @@ Grid grid_of(const ridg_t* h) {
 
 bool is_linear(const ridg_t* h) { return h->flux.kind == RIDG_FLUX_ADVECTION; }
 
+int newton_prec(const ridg_t* h) {
+  return h->opt.precision == RIDG_PREC_MIXED_TF32   ? ridg::kNewtonTF32
+         : h->opt.precision == RIDG_PREC_MIXED_FP32 ? ridg::kNewtonF32
+                                                    : ridg::kNewtonF64;
+}
+
 void drop_graphs(ridg_t* h) {
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : h->graph_defs) cudaGraphDestroy(kv.second);
@@ -254,8 +260,7 @@ int enqueue_newton(ridg_t* h) {
   a.counter = h->nl_words;
   a.stats = h->nl_words + 1;
   a.iters_total = (unsigned long long*)(h->nl_words + 6);
-  RIDG_CUDA(h, ridg::launch_newton(h->nb, h->m, h->flux.kind,
-                                   h->opt.precision == RIDG_PREC_MIXED_FP32, a, h->nl_grid,
+  RIDG_CUDA(h, ridg::launch_newton(h->nb, h->m, h->flux.kind, newton_prec(h), a, h->nl_grid,
                                    h->stream));
   return RIDG_OK;
 }
@@ -315,7 +320,7 @@ cudaError_t clear_newton_stats(ridg_t* h) {
 }
 
 // Newton statistics since they were last cleared: regions at the iteration cap, largest
-// iteration count, flags (1: zero pivot, 2: non-finite update).
+// iteration count, flags (1: zero pivot, 2: non-finite update, 4: tensor-core wait timed out).
 int read_newton_stats(ridg_t* h) {
   int w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   RIDG_CUDA(h, cudaMemcpyAsync(w, h->nl_words, sizeof(w), cudaMemcpyDeviceToHost, h->stream));
@@ -326,6 +331,7 @@ int read_newton_stats(ridg_t* h) {
   h->newton_unconverged = unconverged;
   h->newton_iters_max = iters_max;
   h->newton_iters_total = (long long)total;
+  if (flags & 4) return set_err(h, RIDG_ETIMEOUT, "a bounded tensor-core wait in the Newton solve gave up");
   if (flags & 2) return set_err(h, RIDG_ENONFINITE, "Newton produced a non-finite update");
   if (flags & 1) return set_err(h, RIDG_ENONFINITE, "zero pivot in a Newton block solve");
   if (unconverged > 0)
@@ -380,7 +386,8 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
   } else if (flux->kind == RIDG_FLUX_BURGERS || flux->kind == RIDG_FLUX_EULER) {
     m = flux->kind == RIDG_FLUX_EULER ? 4 : 1;
     if (mesh->dim != 2 || !ridg::newton_supported(order + 1, m)) return RIDG_EINVAL;
-    if (prec != RIDG_PREC_FP64 && prec != RIDG_PREC_MIXED_FP32) return RIDG_EINVAL;
+    if (prec != RIDG_PREC_FP64 && prec != RIDG_PREC_MIXED_FP32 && prec != RIDG_PREC_MIXED_TF32)
+      return RIDG_EINVAL;
     if (flux->kind == RIDG_FLUX_EULER && !(flux->gamma > 1.0)) return RIDG_EINVAL;
   } else {
     return RIDG_EINVAL;
@@ -467,9 +474,8 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
     ridg::nl_tables_upload(h->nb, h->nl, nullptr, &tb_bytes, h->stream);
     void* tb_mem = dev_alloc(h, tb_bytes);
     h->plan = ridg::build_elim_plan();
-    h->nl_grid = ridg::newton_grid(h->nb, h->m, h->flux.kind, h->opt.precision == RIDG_PREC_MIXED_FP32);
-    h->nl_scratch_cta = ridg::newton_scratch_per_cta(h->nb, h->m,
-                                                     h->opt.precision == RIDG_PREC_MIXED_FP32, h->plan);
+    h->nl_grid = ridg::newton_grid(h->nb, h->m, h->flux.kind, newton_prec(h));
+    h->nl_scratch_cta = ridg::newton_scratch_per_cta(h->nb, h->m, newton_prec(h), h->plan);
     const size_t scratch = h->nl_scratch_cta * (size_t)h->nl_grid;
     h->nl_scratch = h->nl_grid > 0 ? dev_alloc(h, scratch) : nullptr;
     h->nl_words = (int*)dev_alloc(h, 8 * sizeof(int));

@@ -10,8 +10,13 @@
 //    edges, centre): every pivot block inverted by Gauss-Jordan with implicit row pivoting
 //    on a register-resident tile, the other blocks updated by register-tiled GEMMs; in T.
 // T = double (RIDG_PREC_FP64) or float (RIDG_PREC_MIXED_FP32: FP32 Jacobian and solves,
-// FP64 residual and iterate).  The blocks live in a per-CTA slice of global memory; the
-// rest of the region stays in shared memory.  Iterates start from Q^n extended constant in
+// FP64 residual and iterate).  With TC (RIDG_PREC_MIXED_TF32, T = float) the block updates
+// of the elimination -- U_kj = A_kk^-1 A_kj and the Schur complements A_ij -= A_ik U_kj --
+// run on the 5th-generation tensor cores (tcgen05.mma kind::tf32, FP32 accumulation in
+// TMEM): every block is kept in the MMA's canonical K-major layout, the blocks right of the
+// pivot transposed, so that each product reads its two operands with plain bulk copies and
+// writes its result in the layout the next product reads.  The blocks live in a per-CTA
+// slice of global memory; the rest of the region stays in shared memory.  Iterates start from Q^n extended constant in
 // time and stop when ||dW||_inf <= tol max(1, ||W||_inf) or after max_iters.
 #pragma once
 
@@ -20,13 +25,14 @@
 #include <type_traits>
 
 #include "k_nlflux.cuh"
+#include "k_tcgen05.cuh"
 #include "ridg_internal.h"
 
 namespace ridg {
 namespace newton {
 
 constexpr int kThreads = 256;
-constexpr int kFlagSingular = 1, kFlagNonFinite = 2;
+constexpr int kFlagSingular = 1, kFlagNonFinite = 2, kFlagTimeout = 4;
 
 template <int NB, int MV>
 struct Dims {
@@ -101,8 +107,20 @@ struct Tab<float> {
   }
 };
 
+// tensor-core block products: K-slices of 16 columns, a ring of kStages slices of both
+// operands (the A operand followed by (128 - BP) spare rows, read by the M = 128 MMA into
+// accumulator lanes that are never used)
+constexpr int kStages = 4, kKS = 16;
+template <int BP>
+struct TcDims {
+  static constexpr uint32_t SL = kKS * BP * 4;          // one operand's K-slice (bytes)
+  static constexpr uint32_t PAD = (128 - BP) * 16;      // rows BP .. 127 of the A operand
+  static constexpr uint32_t STAGE = (2 * SL + PAD + 127) & ~127u;
+  static constexpr int NS = BP / kKS;                   // K-slices per product
+};
+
 // shared-memory layout (bytes) of one CTA
-template <typename T, int NB, int MV>
+template <typename T, int NB, int MV, bool TC = false>
 struct Layout {
   using D = Dims<NB, MV>;
   static constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;     // GEMM staging buffers
@@ -117,7 +135,10 @@ struct Layout {
   static constexpr size_t oProw = up16(oRow + sizeof(T) * 2 * D::BP);
   static constexpr size_t oRank = up16(oProw + sizeof(int) * D::BP);
   static constexpr size_t oMisc = up16(oRank + sizeof(int) * D::BP);
-  static constexpr size_t oArena = up16(oMisc + sizeof(int) * 16);
+  // mbarriers of the tensor-core products: full[kStages], empty[kStages], acc; TMEM address
+  static constexpr size_t oBar = up16(oMisc + sizeof(int) * 16);
+  static constexpr size_t oTmem = oBar + 8 * (2 * kStages + 1);
+  static constexpr size_t oArena = TC ? ((oTmem + 4 + 127) & ~(size_t)127) : up16(oMisc + sizeof(int) * 16);
   // phase arenas
   static constexpr size_t aRes = sizeof(double) * ResBufs<NB, MV>::total;
   static constexpr size_t aAlpha = sizeof(double) * 12 * D::QF;
@@ -127,11 +148,26 @@ struct Layout {
   static constexpr size_t aJac = up16(oJB1 + sizeof(T) * D::PB);
   static constexpr size_t oSA = up16(sizeof(T) * D::BP * D::BP);
   static constexpr size_t oSB = up16(oSA + sizeof(T) * NBUF * D::BP * 17);
-  static constexpr size_t aLU = up16(oSB + sizeof(T) * NBUF * 16 * D::BP);
+  static constexpr size_t aLU = TC ? (size_t)kStages * TcDims<D::BP>::STAGE
+                                   : up16(oSB + sizeof(T) * NBUF * 16 * D::BP);
   static constexpr size_t bytes = oArena + cmax(cmax(aRes, aAlpha), cmax(aJac, aLU));
   // CTAs per SM: two where their shared memory fits (FP32 solves), else one
   static constexpr int MINB = (sizeof(T) == 4 && 2 * (bytes + 1024) <= 233472) ? 2 : 1;
 };
+
+// offset of element (r, c) of a BP x BP block in its storage.  Plain forms: row-major.
+// Tensor-core form: the canonical K-major core-matrix order of the MMA operands -- 16-byte
+// rows of 4 consecutive columns, the BP rows of one 4-column chunk contiguous, the chunks in
+// column order -- of the block, or of its transpose when tr is set.
+template <bool TC, int BP>
+__device__ __forceinline__ int bidx(int r, int c, bool tr = false) {
+  if constexpr (!TC) {
+    return r * BP + c;
+  } else {
+    const int R = tr ? c : r, C = tr ? r : c;
+    return ((C >> 2) * BP + R) * 4 + (C & 3);
+  }
+}
 
 // ---------------------------------------------------------------------------------------
 // small helpers
@@ -493,8 +529,9 @@ __device__ __forceinline__ void list_accumulate(const Ent<T>* __restrict__ ent, 
 }
 
 // Assemble the diagonal blocks of cells r0 .. r0 + CG - 1 and their blocks towards the
-// region neighbours from the merged lists (one pass over the lists for all CG cells).
-template <typename T, int NB, int MV>
+// region neighbours from the merged lists (one pass over the lists for all CG cells).  In
+// the tensor-core form a block (r, r2) with r2 eliminated after r is stored transposed.
+template <typename T, int NB, int MV, bool TC>
 __device__ void assemble_cells(const NlDev& tb, const NlPlan& plan, int r0, const T* FA,
                                T* slots) {
   using D = Dims<NB, MV>;
@@ -522,11 +559,12 @@ __device__ void assemble_cells(const NlDev& tb, const NlPlan& plan, int r0, cons
 #pragma unroll
       for (int i2 = 0; i2 < MV; ++i2)
 #pragma unroll
-        for (int j2 = 0; j2 < MV; ++j2) blk[(size_t)(i2 * THT + k) * BP + j2 * THT + l] = acc[g][i2 * MV + j2];
+        for (int j2 = 0; j2 < MV; ++j2) blk[bidx<TC, BP>(i2 * THT + k, j2 * THT + l)] = acc[g][i2 * MV + j2];
     }
   }
   // zero padding rows / columns of every block written here: the block GEMMs run over the
-  // padded size, so padding must hold zeros whatever the scratch held before
+  // padded size, so padding must hold zeros whatever the scratch held before (the set of
+  // padding positions is the same for a block and its transpose)
   if constexpr (BP > D::BS) {
     constexpr int BS = D::BS, NPAD = (BP - BS) * BP + BS * (BP - BS);
     for (int g = 0; g < CG; ++g) {
@@ -537,10 +575,10 @@ __device__ void assemble_cells(const NlDev& tb, const NlPlan& plan, int r0, cons
         T* blk = slots + (size_t)plan.slot[r * 9 + r2] * BP * BP;
         for (int i = threadIdx.x; i < NPAD; i += kThreads) {
           if (i < (BP - BS) * BP) {
-            blk[BS * BP + i] = T(0);
+            blk[bidx<TC, BP>(BS + i / BP, i % BP)] = T(0);
           } else {
             const int j = i - (BP - BS) * BP;
-            blk[(j / (BP - BS)) * BP + BS + j % (BP - BS)] = T(0);
+            blk[bidx<TC, BP>(j / (BP - BS), BS + j % (BP - BS))] = T(0);
           }
         }
       }
@@ -563,13 +601,16 @@ __device__ void assemble_cells(const NlDev& tb, const NlPlan& plan, int r0, cons
         const int r = r0 + g, r2 = region_nbr(r, dd, side);
         if (r2 < 0) continue;
         T* blk = slots + (size_t)plan.slot[r * 9 + r2] * BP * BP;
+        const bool tr = TC && plan.pos[r] < plan.pos[r2];
 #pragma unroll
         for (int i2 = 0; i2 < MV; ++i2)
 #pragma unroll
-          for (int j2 = 0; j2 < MV; ++j2) blk[(size_t)(i2 * THT + k) * BP + j2 * THT + l] = acc[g][i2 * MV + j2];
+          for (int j2 = 0; j2 < MV; ++j2)
+            blk[bidx<TC, BP>(i2 * THT + k, j2 * THT + l, tr)] = acc[g][i2 * MV + j2];
       }
     }
   }
+  if constexpr (TC) asm volatile("fence.proxy.async.global;" ::: "memory");  // read by bulk copies
   __syncthreads();
 }
 
@@ -658,16 +699,17 @@ __device__ __forceinline__ void put_col(T (&a)[RR][RR], int k, const T (&x)[RR])
   }
 }
 
-// Inverse of the leading BS x BS part of A (global) into S (shared, BP x BP, zero padding):
-// Gauss-Jordan on a register-resident copy with implicit row pivoting (the pivot of column
-// c is the largest remaining entry among the rows not yet used; no rows move), then the
-// order is restored while writing S: with prow[c] the row that pivoted column c and rank its
-// inverse permutation, inv[rank[i]][prow[j]] = R[i][j].
+// Inverse of the leading BS x BS part of A (global) into S (BP x BP, zero padding; shared
+// memory, or in the tensor-core form the block's own storage): Gauss-Jordan on a
+// register-resident copy with implicit row pivoting (the pivot of column c is the largest
+// remaining entry among the rows not yet used; no rows move), then the order is restored
+// while writing S: with prow[c] the row that pivoted column c and rank its inverse
+// permutation, inv[rank[i]][prow[j]] = R[i][j].
 // Thread (tx, ty) = (tid / 16, tid % 16) owns rows ty + 16 i and columns tx + 16 j, so a
 // column lives in one half-warp: that half-warp finds the pivot of its column and publishes
 // the column, and each thread takes the pivot row from its own half-warp by shuffles -- one
 // barrier per column.
-template <typename T, int BS, int BP, int RR>
+template <typename T, int BS, int BP, int RR, bool TC = false>
 __device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* prow, int* rank, int* flags) {
   static_assert(RR <= 8, "register tile up to 8 x 8");
   const int tid = threadIdx.x, tx = tid >> 4, ty = tid & 15;
@@ -677,7 +719,7 @@ __device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* prow, int* r
 #pragma unroll
   for (int i = 0; i < RR; ++i)
 #pragma unroll
-    for (int j = 0; j < RR; ++j) a[i][j] = A[(size_t)(ty + 16 * i) * BP + tx + 16 * j];
+    for (int j = 0; j < RR; ++j) a[i][j] = A[bidx<TC, BP>(ty + 16 * i, tx + 16 * j)];
   unsigned used = 0u;  // bit i: row ty + 16 i has pivoted (or is padding)
 #pragma unroll
   for (int i = 0; i < RR; ++i)
@@ -763,15 +805,16 @@ __device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* prow, int* r
 #pragma unroll
     for (int j = 0; j < RR; ++j) {
       const int cj = tx + 16 * j;
-      if (cj < BS) S[rr * BP + prow[cj]] = a[i][j];
+      if (cj < BS) S[bidx<TC, BP>(rr, prow[cj])] = a[i][j];
     }
   }
   if constexpr (BP > BS) {
     for (int idx = tid; idx < (BP - BS) * BP; idx += kThreads) {
-      S[BS * BP + idx] = T(0);                                 // padding rows
-      S[(idx / (BP - BS)) * BP + BS + idx % (BP - BS)] = T(0);  // padding columns
+      S[bidx<TC, BP>(BS + idx / BP, idx % BP)] = T(0);                    // padding rows
+      S[bidx<TC, BP>(idx / (BP - BS), BS + idx % (BP - BS))] = T(0);      // padding columns
     }
   }
+  if constexpr (TC) asm volatile("fence.proxy.async.global;" ::: "memory");  // read by bulk copies
   __syncthreads();
 }
 
@@ -937,6 +980,193 @@ __device__ void matvec_sub(const T* M, const T* x, T* y) {
   __syncthreads();
 }
 
+// y -= M x for a block in the tensor-core storage (float): matvec_sub_c with M stored as
+// itself (row r of M = storage row r: one 16-byte vector per 4-column chunk, two threads
+// per row each taking half of the chunks), matvec_sub_t with M stored transposed (storage
+// row j holds column j of M: TPC threads share one 4-row chunk of y, each summing every
+// TPC-th column, then reduce by shuffles).
+template <int BS, int BP>
+__device__ void matvec_sub_c(const float* M, const float* x, float* y) {
+  constexpr int NC = BP / 4, HC = NC / 2;  // BP is a multiple of 16: NC even
+  const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
+  float s = 0.f;
+  if (r < BS) {
+    const float4* col = reinterpret_cast<const float4*>(M) + r;
+    float4 v[HC];
+#pragma unroll
+    for (int u = 0; u < HC; ++u) v[u] = col[(h * HC + u) * BP];
+    const float* xh = x + 4 * h * HC;
+#pragma unroll
+    for (int u = 0; u < HC; ++u) {
+      s = fmaf(v[u].x, xh[4 * u], s);
+      s = fmaf(v[u].y, xh[4 * u + 1], s);
+      s = fmaf(v[u].z, xh[4 * u + 2], s);
+      s = fmaf(v[u].w, xh[4 * u + 3], s);
+    }
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  if (r < BS && h == 0) y[r] -= s;
+  __syncthreads();
+}
+
+template <int BS, int BP>
+__device__ void matvec_sub_t(const float* M, const float* x, float* y) {
+  constexpr int NC = BP / 4;
+  constexpr int TPC = NC <= 8 ? 32 : (NC <= 16 ? 16 : 8);  // threads per chunk, NC * TPC <= 256
+  const int q = threadIdx.x / TPC, sub = threadIdx.x % TPC;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (q < NC) {
+    const float4* ch = reinterpret_cast<const float4*>(M) + q * BP;
+#pragma unroll 4
+    for (int j = sub; j < BS; j += TPC) {
+      const float4 v = ch[j];
+      const float xj = x[j];
+      acc.x = fmaf(v.x, xj, acc.x);
+      acc.y = fmaf(v.y, xj, acc.y);
+      acc.z = fmaf(v.z, xj, acc.z);
+      acc.w = fmaf(v.w, xj, acc.w);
+    }
+  }
+#pragma unroll
+  for (int o = TPC / 2; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+  }
+  if (q < NC && sub == 0) {
+    const int r = 4 * q;
+    if (r < BS) y[r] -= acc.x;
+    if (r + 1 < BS) y[r + 1] -= acc.y;
+    if (r + 2 < BS) y[r + 2] -= acc.z;
+    if (r + 3 < BS) y[r + 3] -= acc.w;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------
+// tensor-core block products (TC form).  One thread issues the bulk copies of the K-slices
+// and the MMAs; all threads then read the accumulator out of TMEM (thread <-> lane <-> row,
+// the two warpgroups splitting the columns) and combine it with the destination block.
+// Every wait is bounded: on a timeout the product reports failure (the CTA then stops).
+// ---------------------------------------------------------------------------------------
+struct TcCtx {
+  uint32_t tmem;   // accumulator: 128 lanes x BP columns
+  uint32_t ring;   // shared address of the stage ring
+  uint32_t bar;    // full[kStages], empty[kStages], acc
+  uint32_t fills;  // K-slices loaded so far (issuing thread only)
+  uint32_t done;   // K-slices whose copies were waited for (issuing thread only)
+  uint32_t gemms;  // products completed (every thread)
+};
+
+enum TcMode { kTcStore = 0, kTcNeg = 1, kTcSub = 2 };
+
+__device__ __forceinline__ uint32_t tc_full(const TcCtx& tc, int st) { return tc.bar + 8u * st; }
+__device__ __forceinline__ uint32_t tc_empty(const TcCtx& tc, int st) {
+  return tc.bar + 8u * (kStages + st);
+}
+__device__ __forceinline__ uint32_t tc_acc(const TcCtx& tc) { return tc.bar + 8u * (2 * kStages); }
+
+// D = Aop Bop^T over K = BP: Aop and Bop are BP x BP blocks in canonical storage (rows: M for
+// Aop, N for Bop; columns: K).  Then C = D (kTcStore), C = -D (kTcNeg) or C -= D (kTcSub),
+// with C in canonical storage whose rows are M.  Returns false (in every thread) if a wait
+// timed out.
+template <int BP>
+__device__ bool tc_gemm(TcCtx& tc, const float* Aop, const float* Bop, float* C, int mode) {
+  using TD = TcDims<BP>;
+  constexpr int NS = TD::NS;
+  const int tid = threadIdx.x;
+  bool ok = true;
+  if (tid == 0) {
+    const uint32_t idesc = idesc_tf32(128, BP);
+    const uint32_t base = tc.fills;
+    auto issue = [&](int sl) {
+      const uint32_t g = tc.fills;
+      const int st = (int)(g % kStages);
+      if (g >= (uint32_t)kStages && !mbar_wait(tc_empty(tc, st), ((g / kStages) - 1u) & 1u)) return false;
+      const uint32_t dst = tc.ring + st * TD::STAGE;
+      mbar_expect_tx(tc_full(tc, st), 2u * TD::SL);
+      bulk_load(dst, Aop + (size_t)sl * kKS * BP, TD::SL, tc_full(tc, st));
+      bulk_load(dst + TD::SL + TD::PAD, Bop + (size_t)sl * kKS * BP, TD::SL, tc_full(tc, st));
+      ++tc.fills;
+      return true;
+    };
+    int next = 0;
+    while (ok && next < NS && next < kStages) ok = issue(next++);
+    for (int sl = 0; ok && sl < NS; ++sl) {
+      const uint32_t g = base + sl;
+      const int st = (int)(g % kStages);
+      ok = mbar_wait(tc_full(tc, st), (g / kStages) & 1u);
+      if (!ok) break;
+      ++tc.done;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = tc.ring + st * TD::STAGE, b0 = a0 + TD::SL + TD::PAD;
+#pragma unroll
+      for (int kk = 0; kk < kKS / 8; ++kk)
+        mma_tf32(tc.tmem, smem_desc(a0 + kk * 2u * BP * 16u, BP * 16u, 128u),
+                 smem_desc(b0 + kk * 2u * BP * 16u, BP * 16u, 128u), idesc, (sl | kk) != 0);
+      mma_commit(tc_empty(tc, st));
+      // refill the stage of the previous slice (its MMAs are the oldest in flight)
+      if (sl >= 1 && next < NS && next == sl - 1 + kStages) ok = issue(next++);
+    }
+    mma_commit(tc_acc(tc));  // arrives once every MMA issued so far is complete
+  }
+  const bool waited = mbar_wait_sleep(tc_acc(tc), tc.gemms & 1u);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int warp = tid >> 5, lane = tid & 31, q = warp & 3, h = warp >> 2;
+  const int row = 32 * q + lane;
+  constexpr int HC = BP / 2, NG = HC / 8, GB = 4;  // column groups of 8, read GB at a time
+#pragma unroll
+  for (int g0 = 0; g0 < NG; g0 += GB) {
+    uint32_t r[GB][8];
+#pragma unroll
+    for (int gi = 0; gi < GB; ++gi)
+      if (g0 + gi < NG)
+        tmem_ld8_nowait(tc.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * HC + 8 * (g0 + gi)), r[gi]);
+    tmem_wait_ld();
+    if (waited && row < BP) {
+#pragma unroll
+      for (int gi = 0; gi < GB; ++gi) {
+        if (g0 + gi >= NG) break;
+        const int c0 = h * HC + 8 * (g0 + gi);
+        float4* p0 = reinterpret_cast<float4*>(C) + (c0 >> 2) * BP + row;
+        float4* p1 = p0 + BP;
+        float4 d0 = make_float4(__uint_as_float(r[gi][0]), __uint_as_float(r[gi][1]),
+                                __uint_as_float(r[gi][2]), __uint_as_float(r[gi][3]));
+        float4 d1 = make_float4(__uint_as_float(r[gi][4]), __uint_as_float(r[gi][5]),
+                                __uint_as_float(r[gi][6]), __uint_as_float(r[gi][7]));
+        if (mode == kTcSub) {
+          const float4 o0 = *p0, o1 = *p1;
+          d0 = make_float4(o0.x - d0.x, o0.y - d0.y, o0.z - d0.z, o0.w - d0.w);
+          d1 = make_float4(o1.x - d1.x, o1.y - d1.y, o1.z - d1.z, o1.w - d1.w);
+        } else if (mode == kTcNeg) {
+          d0 = make_float4(-d0.x, -d0.y, -d0.z, -d0.w);
+          d1 = make_float4(-d1.x, -d1.y, -d1.z, -d1.w);
+        }
+        *p0 = d0;
+        *p1 = d1;
+      }
+    }
+  }
+  asm volatile("fence.proxy.async.global;" ::: "memory");  // C is read by later bulk copies
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  const bool all = __syncthreads_and((tid != 0 || ok) && waited) != 0;
+  ++tc.gemms;
+  return all;
+}
+
+// The issuing thread waits (bounded) for copies still in flight after a failed product, so
+// that none lands in shared memory after the CTA has moved on or exited.
+__device__ __forceinline__ void tc_drain(TcCtx& tc) {
+  if (threadIdx.x == 0) {
+    for (; tc.done < tc.fills; ++tc.done) {
+      const uint32_t g = tc.done;
+      (void)mbar_wait(tc_full(tc, (int)(g % kStages)), (g / kStages) & 1u);
+    }
+  }
+  __syncthreads();
+}
+
 // Solve J x = b by block elimination in the plan's order; b in xs (9 x BP), x returned there.
 template <typename T, int BS, int BP, int RR, int NBUF, bool KEEP>
 __device__ void block_solve(T* slots, const NlPlan& plan, T* xs, T* S, T* sA, T* sB, T* colv,
@@ -1013,13 +1243,97 @@ __device__ void stored_solve(const T* slots, const NlPlan& plan, T* xs, T* tmp) 
   }
 }
 
+// Tensor-core form of block_solve (T = float; the pivot inverses kept in the diagonal
+// slots).  Storage: block (i, j) as itself when i is eliminated after j (or i == j), as its
+// transpose when before -- so U_kj = A_kk^-1 A_kj is formed as U_kj^T = A_kj^T A_kk^-T and
+// each Schur update A_ij -= A_ik U_kj as (A_ik)(U_kj^T)^T or, for a transposed A_ij, as
+// (U_kj^T)(A_ik)^T: in every product both operands are read as stored.  Returns false if a
+// tensor-core wait timed out.
+template <int BS, int BP, int RR>
+__device__ bool block_solve_tc(float* slots, const NlPlan& plan, float* xs, TcCtx& tc,
+                               float* colv, float* rowp, int* prow, int* rank, int* flags) {
+  const int tid = threadIdx.x;
+  auto slot = [&](int i, int j) { return slots + (size_t)plan.slot[i * 9 + j] * BP * BP; };
+  // the ring reuses shared memory the other phases wrote with ordinary stores
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  bool ok = true;
+  for (int t = 0; t < 9 && ok; ++t) {
+    const int k = plan.order[t];
+    float* Akk = slot(k, k);
+    gj_inverse<float, BS, BP, RR, true>(Akk, Akk, colv, rowp, prow, rank, flags);
+    float* xk = xs + k * BP;
+    for (int i = tid; i < BP; i += kThreads) colv[i] = 0.f;
+    __syncthreads();
+    matvec_sub_c<BS, BP>(Akk, xk, colv);  // colv = -A_kk^-1 x_k
+    for (int i = tid; i < BS; i += kThreads) xk[i] = -colv[i];
+    __syncthreads();
+    const int nn = plan.nn[t];
+    for (int a = 0; a < nn && ok; ++a) {
+      float* Akj = slot(k, plan.nbr[t][a]);
+      ok = tc_gemm<BP>(tc, Akj, Akk, Akj, kTcStore);
+    }
+    for (int a = 0; a < nn && ok; ++a) {
+      const int i = plan.nbr[t][a];
+      const float* Aik = slot(i, k);
+      matvec_sub_c<BS, BP>(Aik, xk, xs + i * BP);
+      for (int b = 0; b < nn && ok; ++b) {
+        const int j = plan.nbr[t][b];
+        const float* Ukj = slot(k, j);
+        const int mode = plan.first[t][a][b] ? kTcNeg : kTcSub;
+        if (plan.pos[i] < plan.pos[j])
+          ok = tc_gemm<BP>(tc, Ukj, Aik, slot(i, j), mode);
+        else
+          ok = tc_gemm<BP>(tc, Aik, Ukj, slot(i, j), mode);
+      }
+    }
+  }
+  if (!ok) return false;
+  for (int t = 8; t >= 0; --t) {
+    const int k = plan.order[t];
+    for (int a = 0; a < plan.nn[t]; ++a) {
+      const int j = plan.nbr[t][a];
+      matvec_sub_t<BS, BP>(slot(k, j), xs + j * BP, xs + k * BP);
+    }
+  }
+  return true;
+}
+
+// Solve J x = b again with the factors block_solve_tc left in the slots.
+template <int BS, int BP>
+__device__ void stored_solve_tc(const float* slots, const NlPlan& plan, float* xs, float* tmp) {
+  const int tid = threadIdx.x;
+  auto slot = [&](int i, int j) { return slots + (size_t)plan.slot[i * 9 + j] * BP * BP; };
+  for (int t = 0; t < 9; ++t) {
+    const int k = plan.order[t];
+    float* xk = xs + k * BP;
+    for (int i = tid; i < BP; i += kThreads) tmp[i] = 0.f;
+    __syncthreads();
+    matvec_sub_c<BS, BP>(slot(k, k), xk, tmp);  // -A_kk^-1 x_k
+    for (int i = tid; i < BS; i += kThreads) xk[i] = -tmp[i];
+    __syncthreads();
+    for (int a = 0; a < plan.nn[t]; ++a) {
+      const int i = plan.nbr[t][a];
+      matvec_sub_c<BS, BP>(slot(i, k), xk, xs + i * BP);
+    }
+  }
+  for (int t = 8; t >= 0; --t) {
+    const int k = plan.order[t];
+    for (int a = 0; a < plan.nn[t]; ++a) {
+      const int j = plan.nbr[t][a];
+      matvec_sub_t<BS, BP>(slot(k, j), xs + j * BP, xs + k * BP);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------------------
-template <typename T, int NB, int MV, int FLUX>
-__global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV>::MINB)) newton_kernel(const NewtonArgs a) {
+template <typename T, int NB, int MV, int FLUX, bool TC>
+__global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newton_kernel(const NewtonArgs a) {
+  static_assert(!TC || sizeof(T) == 4, "tensor-core block products are TF32 (T = float)");
   using D = Dims<NB, MV>;
-  using L = Layout<T, NB, MV>;
+  using L = Layout<T, NB, MV, TC>;
   extern __shared__ __align__(16) unsigned char smem[];
   double* Ws = (double*)(smem + L::oW);
   double* Qs = (double*)(smem + L::oQ);
@@ -1044,13 +1358,36 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV>::MINB)) newton_ke
   const int nx = a.nx, ny = a.ny;
   T* slots = (T*)((char*)a.scratch + (size_t)blockIdx.x * a.scratch_per_cta);
   int* flags = a.stats + 2;
+  TcCtx tc{};
+  if constexpr (TC) {
+    // TMEM accumulator (128 columns >= BP) and the ring's mbarriers
+    uint32_t* tslot = (uint32_t*)(smem + L::oTmem);
+    tc.bar = smem_u32(smem + L::oBar);
+    tc.ring = smem_u32(arena);
+    if (tid == 0) {
+      misc[1] = 0;
+      for (int i = 0; i < 2 * kStages + 1; ++i) mbar_init(tc.bar + 8u * i, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tslot)),
+                   "r"(128));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc.tmem = *tslot;
+  }
 
   for (;;) {
     if (tid == 0) misc[0] = atomicAdd(a.counter, 1);
     __syncthreads();
     const long long e = misc[0];
+    const bool stop = TC && misc[1] != 0;  // a tensor-core wait timed out
     __syncthreads();
-    if (e >= a.ncell) break;
+    if (e >= a.ncell || stop) break;
     const unsigned ue = (unsigned)e, uy = ue / (unsigned)nx;
     const int ix = (int)(ue - uy * (unsigned)nx), iy = (int)uy;
     for (int i = tid; i < 9 * MV * D::THS; i += kThreads) {
@@ -1068,8 +1405,9 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV>::MINB)) newton_ke
     // FP64 form: Newton (a new Jacobian every iteration).  FP32 form: after a factorisation,
     // refinement sweeps reuse it with the FP64 residual while each contracts the update by
     // at least 10x (at most kSweeps per factorisation); max_iters caps the factorisations.
+    // (TF32 block updates leave a coarser factorisation: more sweeps before a refactorisation)
     constexpr bool CHORD = sizeof(T) == 4;
-    constexpr int kSweeps = 3;
+    constexpr int kSweeps = TC ? 8 : 3;
     int it = 0, sweeps = 0;
     bool conv = false, bad = false, refactor = true;
     double dprev = 0.0;
@@ -1081,7 +1419,7 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV>::MINB)) newton_ke
           for (int g = 0; g < D::CG; ++g)
             project_cell<T, NB, MV, FLUX>(a.tb, r0 + g, Ws, alpha, FA + g * D::FAS, jw, jb0, jb1,
                                           a.lam, a.gamma);
-          assemble_cells<T, NB, MV>(a.tb, a.plan, r0, FA, slots);
+          assemble_cells<T, NB, MV, TC>(a.tb, a.plan, r0, FA, slots);
         }
       }
       for (int i = tid; i < 9 * D::BP; i += kThreads) {
@@ -1089,11 +1427,24 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV>::MINB)) newton_ke
         xs[i] = c < D::BS ? (T)Rs[r * D::BS + c] : T(0);
       }
       __syncthreads();
-      if (refactor)
-        block_solve<T, D::BS, D::BP, D::RR, L::NBUF, CHORD>(slots, a.plan, xs, S, sA, sB, colv,
-                                                            rowp, prow, rank, flags);
-      else
-        stored_solve<T, D::BS, D::BP>(slots, a.plan, xs, colv);
+      if constexpr (TC) {
+        if (refactor) {
+          if (!block_solve_tc<D::BS, D::BP, D::RR>(slots, a.plan, xs, tc, colv, rowp, prow, rank,
+                                                    flags)) {
+            if (tid == 0) atomicOr(flags, kFlagTimeout);
+            misc[1] = 1;  // stop: the CTA's remaining regions are not solved
+            break;
+          }
+        } else {
+          stored_solve_tc<D::BS, D::BP>(slots, a.plan, xs, colv);
+        }
+      } else {
+        if (refactor)
+          block_solve<T, D::BS, D::BP, D::RR, L::NBUF, CHORD>(slots, a.plan, xs, S, sA, sB, colv,
+                                                              rowp, prow, rank, flags);
+        else
+          stored_solve<T, D::BS, D::BP>(slots, a.plan, xs, colv);
+      }
       double dn = 0.0, wn = 0.0;
       bool fin = true;
       for (int i = tid; i < 9 * D::BS; i += kThreads) {
@@ -1127,69 +1478,78 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV>::MINB)) newton_ke
     }
     __syncthreads();
   }
+  if constexpr (TC) {
+    tc_drain(tc);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid < 32)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(128));
+  }
 }
 
-template <typename T, int NB, int MV, int FLUX>
+template <typename T, int NB, int MV, int FLUX, bool TC>
 cudaError_t launch_one(const NewtonArgs& a, int grid, cudaStream_t s) {
-  using L = Layout<T, NB, MV>;
+  using L = Layout<T, NB, MV, TC>;
   static_assert(L::bytes <= 232448, "Newton kernel shared memory above the per-CTA limit");
-  cudaError_t e = cudaFuncSetAttribute(newton_kernel<T, NB, MV, FLUX>,
+  cudaError_t e = cudaFuncSetAttribute(newton_kernel<T, NB, MV, FLUX, TC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  newton_kernel<T, NB, MV, FLUX><<<grid, kThreads, L::bytes, s>>>(a);
+  newton_kernel<T, NB, MV, FLUX, TC><<<grid, kThreads, L::bytes, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int NB, int MV, int FLUX>
+template <typename T, int NB, int MV, int FLUX, bool TC>
 int ctas_one() {
-  using L = Layout<T, NB, MV>;
-  if (cudaFuncSetAttribute(newton_kernel<T, NB, MV, FLUX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  using L = Layout<T, NB, MV, TC>;
+  if (cudaFuncSetAttribute(newton_kernel<T, NB, MV, FLUX, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)L::bytes) != cudaSuccess)
     return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, newton_kernel<T, NB, MV, FLUX>, kThreads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, newton_kernel<T, NB, MV, FLUX, TC>, kThreads,
                                                     L::bytes) != cudaSuccess)
     return 0;
-  return n;
+  // The occupancy calculator counts one CTA per SM for any kernel that uses tcgen05; the
+  // tensor-core form still runs as many CTAs as its shared memory and registers allow
+  // (MINB, at most 2 here), each holding 128 of the SM's 512 TMEM columns.
+  return TC ? L::MINB : n;
 }
 
 // resident CTAs per SM of the Newton kernel for (nb, m, flux), 0 if unsupported
-template <typename T>
+template <typename T, bool TC>
 int ctas_per_sm(int nb, int m, int kind) {
   if (kind == RIDG_FLUX_BURGERS && m == 1) {
     switch (nb) {
-      case 2: return ctas_one<T, 2, 1, RIDG_FLUX_BURGERS>();
-      case 3: return ctas_one<T, 3, 1, RIDG_FLUX_BURGERS>();
-      case 4: return ctas_one<T, 4, 1, RIDG_FLUX_BURGERS>();
-      case 5: return ctas_one<T, 5, 1, RIDG_FLUX_BURGERS>();
+      case 2: return ctas_one<T, 2, 1, RIDG_FLUX_BURGERS, TC>();
+      case 3: return ctas_one<T, 3, 1, RIDG_FLUX_BURGERS, TC>();
+      case 4: return ctas_one<T, 4, 1, RIDG_FLUX_BURGERS, TC>();
+      case 5: return ctas_one<T, 5, 1, RIDG_FLUX_BURGERS, TC>();
       default: break;
     }
   } else if (kind == RIDG_FLUX_EULER && m == 4) {
     switch (nb) {
-      case 2: return ctas_one<T, 2, 4, RIDG_FLUX_EULER>();
-      case 3: return ctas_one<T, 3, 4, RIDG_FLUX_EULER>();
+      case 2: return ctas_one<T, 2, 4, RIDG_FLUX_EULER, TC>();
+      case 3: return ctas_one<T, 3, 4, RIDG_FLUX_EULER, TC>();
       default: break;
     }
   }
   return 0;
 }
 
-template <typename T>
+template <typename T, bool TC>
 cudaError_t launch_typed(int nb, int m, int kind, const NewtonArgs& a, int grid, cudaStream_t s) {
   if (kind == RIDG_FLUX_BURGERS && m == 1) {
     switch (nb) {
-      case 2: return launch_one<T, 2, 1, RIDG_FLUX_BURGERS>(a, grid, s);
-      case 3: return launch_one<T, 3, 1, RIDG_FLUX_BURGERS>(a, grid, s);
-      case 4: return launch_one<T, 4, 1, RIDG_FLUX_BURGERS>(a, grid, s);
-      case 5: return launch_one<T, 5, 1, RIDG_FLUX_BURGERS>(a, grid, s);
+      case 2: return launch_one<T, 2, 1, RIDG_FLUX_BURGERS, TC>(a, grid, s);
+      case 3: return launch_one<T, 3, 1, RIDG_FLUX_BURGERS, TC>(a, grid, s);
+      case 4: return launch_one<T, 4, 1, RIDG_FLUX_BURGERS, TC>(a, grid, s);
+      case 5: return launch_one<T, 5, 1, RIDG_FLUX_BURGERS, TC>(a, grid, s);
       default: break;
     }
   } else if (kind == RIDG_FLUX_EULER && m == 4) {
     switch (nb) {
-      case 2: return launch_one<T, 2, 4, RIDG_FLUX_EULER>(a, grid, s);
-      case 3: return launch_one<T, 3, 4, RIDG_FLUX_EULER>(a, grid, s);
+      case 2: return launch_one<T, 2, 4, RIDG_FLUX_EULER, TC>(a, grid, s);
+      case 3: return launch_one<T, 3, 4, RIDG_FLUX_EULER, TC>(a, grid, s);
       default: break;
     }
   }

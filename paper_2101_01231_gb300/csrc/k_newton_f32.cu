@@ -5,7 +5,7 @@
 namespace ridg {
 cudaError_t launch_newton_f32(int nb, int m, int kind, const NewtonArgs& a, int grid,
                               cudaStream_t s) {
-  return newton::launch_typed<float>(nb, m, kind, a, grid, s);
+  return newton::launch_typed<float, false>(nb, m, kind, a, grid, s);
 }
-int newton_ctas_per_sm_f32(int nb, int m, int kind) { return newton::ctas_per_sm<float>(nb, m, kind); }
+int newton_ctas_per_sm_f32(int nb, int m, int kind) { return newton::ctas_per_sm<float, false>(nb, m, kind); }
 }  // namespace ridg

@@ -4,7 +4,7 @@
 namespace ridg {
 cudaError_t launch_newton_f64(int nb, int m, int kind, const NewtonArgs& a, int grid,
                               cudaStream_t s) {
-  return newton::launch_typed<double>(nb, m, kind, a, grid, s);
+  return newton::launch_typed<double, false>(nb, m, kind, a, grid, s);
 }
-int newton_ctas_per_sm_f64(int nb, int m, int kind) { return newton::ctas_per_sm<double>(nb, m, kind); }
+int newton_ctas_per_sm_f64(int nb, int m, int kind) { return newton::ctas_per_sm<double, false>(nb, m, kind); }
 }  // namespace ridg

@@ -312,31 +312,41 @@ cudaError_t launch_newton_f64(int nb, int m, int kind, const NewtonArgs& a, int 
                               cudaStream_t s);
 cudaError_t launch_newton_f32(int nb, int m, int kind, const NewtonArgs& a, int grid,
                               cudaStream_t s);
+cudaError_t launch_newton_tf32(int nb, int m, int kind, const NewtonArgs& a, int grid,
+                               cudaStream_t s);
 
 bool newton_supported(int nb, int m) { return (m == 1 && nb >= 2 && nb <= 5) || (m == 4 && nb >= 2 && nb <= 3); }
 
 int newton_ctas_per_sm_f64(int nb, int m, int kind);
 int newton_ctas_per_sm_f32(int nb, int m, int kind);
+int newton_ctas_per_sm_tf32(int nb, int m, int kind);
 
-int newton_grid(int nb, int m, int kind, bool fp32) {
+int newton_grid(int nb, int m, int kind, int prec) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
     return 0;
-  const int per = fp32 ? newton_ctas_per_sm_f32(nb, m, kind) : newton_ctas_per_sm_f64(nb, m, kind);
+  const int per = prec == kNewtonTF32  ? newton_ctas_per_sm_tf32(nb, m, kind)
+                  : prec == kNewtonF32 ? newton_ctas_per_sm_f32(nb, m, kind)
+                                       : newton_ctas_per_sm_f64(nb, m, kind);
   return per > 0 ? per * sms : 0;  // a persistent grid: every resident CTA slot filled once
 }
 
-size_t newton_scratch_per_cta(int nb, int m, bool fp32, const NlPlan& plan) {
+size_t newton_scratch_per_cta(int nb, int m, int prec, const NlPlan& plan) {
   const int bs = m * nb * nb * nb, bp = (bs + 15) / 16 * 16;
-  const size_t bytes = (size_t)plan.nslots * bp * bp * (fp32 ? sizeof(float) : sizeof(double));
+  const size_t bytes =
+      (size_t)plan.nslots * bp * bp * (prec == kNewtonF64 ? sizeof(double) : sizeof(float));
   return (bytes + 255) & ~(size_t)255;
 }
 
-cudaError_t launch_newton(int nb, int m, int flux_kind, bool fp32, const NewtonArgs& a, int grid,
+cudaError_t launch_newton(int nb, int m, int flux_kind, int prec, const NewtonArgs& a, int grid,
                           cudaStream_t s) {
-  return fp32 ? launch_newton_f32(nb, m, flux_kind, a, grid, s)
-              : launch_newton_f64(nb, m, flux_kind, a, grid, s);
+  switch (prec) {
+    case kNewtonF64: return launch_newton_f64(nb, m, flux_kind, a, grid, s);
+    case kNewtonF32: return launch_newton_f32(nb, m, flux_kind, a, grid, s);
+    case kNewtonTF32: return launch_newton_tf32(nb, m, flux_kind, a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_nl_correct(int nb, int m, int flux_kind, const NlDev& tb, double* Q,

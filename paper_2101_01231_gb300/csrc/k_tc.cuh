@@ -1,7 +1,7 @@
 // Shared device helpers of the tensor-core (tcgen05 + TMA) kernels of the mixed linear path:
-// shared-memory matrix descriptors, the BF16 MMA, bounded mbarrier waits, TMA and bulk
-// copies, TMEM loads, error-free FP32 sums, and the split of FP64 coefficients into balanced
-// base-256 digits (exact in BF16).
+// tile constants, TMA tensor copies, error-free FP32 sums, and the split of FP64 coefficients
+// into balanced base-256 digits (exact in BF16).  The tcgen05 / mbarrier / bulk-copy wrappers
+// are in k_tcgen05.cuh.
 #pragma once
 
 #include <cuda.h>
@@ -10,6 +10,8 @@
 
 #include <cstdint>
 
+#include "k_tcgen05.cuh"
+
 namespace ridg {
 namespace {
 
@@ -17,7 +19,6 @@ constexpr int kTX = 8, kTY = 16;             // cells per tile in x, y (128 = MM
 constexpr int kHX = kTX + 2, kHY = kTY + 2;  // halo
 constexpr int kCopy = kTX * kHY;             // cells of one x-shifted halo copy (8 x 18)
 constexpr int kBits = 8;                     // digit width
-constexpr long kWaitLimit = 1L << 22;        // bounded mbarrier polls (well under a second)
 constexpr int kGemmThreads = 320;            // warp 0: TMA, warp 1: MMA, warps 2..9: epilogue
 constexpr int kMaxSlots = 8;                 // ring of per-digit operand slots
 constexpr uint32_t kSmemLimit = 232448;      // opt-in shared memory per block
@@ -25,75 +26,6 @@ constexpr uint32_t kSmemLimit = 232448;      // opt-in shared memory per block
 // status bits
 constexpr int kStatusTimeout = 2;
 constexpr int kStatusRange = 4;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  // SWIZZLE_NONE, K-major: LBO = byte stride between core matrices along K,
-  // SBO = byte stride between 8-row groups along M/N; bits 46-47 = descriptor version 1.
-  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-__device__ __forceinline__ uint32_t idesc_bf16(int m, int n) {
-  // kind::f16: D = F32 (bit 4), A = B = BF16 (bits 7, 10), both K-major, N >> 3 at bit 17,
-  // M >> 4 at bit 24
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  uint32_t done = 0;
-  for (long it = 0; it < kWaitLimit && !done; ++it) {
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(phase)
-        : "memory");
-  }
-  return done != 0;
-}
-
-// the same bounded wait with a short sleep between polls (for warps that only consume)
-__device__ __forceinline__ bool mbar_wait_sleep(uint32_t mbar, uint32_t phase) {
-  uint32_t done = 0;
-  for (long it = 0; it < kWaitLimit && !done; ++it) {
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(phase)
-        : "memory");
-    if (!done) __nanosleep(64);
-  }
-  return done != 0;
-}
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
                                             int c2, uint32_t mbar) {
@@ -110,28 +42,6 @@ __device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int c0, 
                    (uint64_t)map),
                "r"(c0), "r"(c1), "r"(c2)
                : "memory");
-}
-
-// 8 consecutive TMEM columns of this thread's lane (no wait: see tmem_wait_ld)
-__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
-                                          uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(mbar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // error-free sum of two floats (Knuth): a + b = s + e exactly

@@ -290,6 +290,7 @@ NlPlan build_elim_plan() {
   for (int t = 0; t < 9; ++t) {
     p.order[t] = order[t];
     pos[order[t]] = t;
+    p.pos[order[t]] = t;
   }
   std::set<std::pair<int, int>> nz;
   for (int r = 0; r < 9; ++r) {

@@ -122,6 +122,7 @@ struct NlPlan {
   int nbr[9][3];
   int slot[81];        // storage slot of block (i, j), -1 if it stays zero
   int first[9][3][3];  // 1: this update creates the block (write, do not accumulate)
+  int pos[9];          // elimination step of each region cell (order[pos[r]] == r)
   int nslots;
 };
 NlPlan build_elim_plan();
@@ -134,9 +135,12 @@ struct NlDevTables {
 // with mem == nullptr first to get the size).
 int nl_tables_upload(int nb, NlDevTables& out, void* mem, size_t* bytes, cudaStream_t s);
 bool newton_supported(int nb, int m);
+// arithmetic of the Newton linear solves: FP64; FP32 on the CUDA cores; TF32 tensor-core
+// block updates with FP32 pivot inverses (both mixed forms keep the residual in FP64)
+enum NewtonPrec { kNewtonF64 = 0, kNewtonF32 = 1, kNewtonTF32 = 2 };
 // CTAs of the persistent Newton kernel and the scratch each needs (bytes)
-int newton_grid(int nb, int m, int flux_kind, bool fp32);
-size_t newton_scratch_per_cta(int nb, int m, bool fp32, const NlPlan& plan);
+int newton_grid(int nb, int m, int flux_kind, int prec);
+size_t newton_scratch_per_cta(int nb, int m, int prec, const NlPlan& plan);
 struct NewtonArgs {
   NlDev tb;
   NlPlan plan;
@@ -154,7 +158,7 @@ struct NewtonArgs {
   int* stats;        // [0] unconverged regions, [1] largest iteration count, [2] flags
   unsigned long long* iters_total;  // Newton iterations summed over regions
 };
-cudaError_t launch_newton(int nb, int m, int flux_kind, bool fp32, const NewtonArgs& a, int grid,
+cudaError_t launch_newton(int nb, int m, int flux_kind, int prec, const NewtonArgs& a, int grid,
                           cudaStream_t s);
 cudaError_t launch_nl_correct(int nb, int m, int flux_kind, const NlDev& tb, double* Q,
                               const double* W, int nx, int ny, long long ncell, double lamx,

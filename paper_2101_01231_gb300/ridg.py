@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libridg.so")
 RIDG_OK, RIDG_EINVAL, RIDG_ENOMEM, RIDG_ECUDA, RIDG_ENONFINITE, RIDG_ENOCONV, RIDG_ETIMEOUT, \
     RIDG_ESTATE, RIDG_ETOOBIG = range(9)
 RIDG_FLUX_ADVECTION, RIDG_FLUX_BURGERS, RIDG_FLUX_EULER = range(3)
-RIDG_PREC_FP64, RIDG_PREC_MIXED_BF16, RIDG_PREC_MIXED_FP32 = range(3)
+RIDG_PREC_FP64, RIDG_PREC_MIXED_BF16, RIDG_PREC_MIXED_FP32, RIDG_PREC_MIXED_TF32 = range(4)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)

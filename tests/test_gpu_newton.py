@@ -61,12 +61,16 @@ def _case(flux, n, M):
     return _burgers(n, M) if flux == "burgers" else _euler(n, M)
 
 
+def _prec(R, prec):
+    return {"fp64": R.RIDG_PREC_FP64, "fp32": R.RIDG_PREC_MIXED_FP32,
+            "tf32": R.RIDG_PREC_MIXED_TF32}[prec]
+
+
 @pytest.mark.parametrize("flux,n,M,k", CASES)
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
 def test_newton_prediction_matches_oracle(R, flux, n, M, k, prec):
     w = _case(flux, n, M)
-    p = R.RIDG_PREC_FP64 if prec == "fp64" else R.RIDG_PREC_MIXED_FP32
-    s = _solver(R, w, precision=p)
+    s = _solver(R, w, precision=_prec(R, prec))
     q = I.initial_state(w)
     s.set_state(q)
     dt = s.info()["dt"]
@@ -78,8 +82,8 @@ def test_newton_prediction_matches_oracle(R, flux, n, M, k, prec):
     if prec == "fp64":
         assert _rel(W[cells], Wo) < TOL_STEP
     else:
-        # FP32 solves reach the same FP64 fixed point where Newton converged; where the cap
-        # stopped it the iterate depends on the solve precision (parity unpinned there)
+        # FP32 / TF32 solves reach the same FP64 fixed point where Newton converged; where
+        # the cap stopped it the iterate depends on the solve precision (parity unpinned there)
         assert conv.any()
         assert _rel(W[cells][conv], Wo[conv]) < 1e-11
     info = s.info()
@@ -108,11 +112,10 @@ def test_newton_step_matches_oracle(R, flux, n, M):
 
 
 @pytest.mark.parametrize("flux,n,M", [("burgers", (11, 9), 3), ("euler", (16, 13), 2)])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
 def test_newton_mass_conserved(R, flux, n, M, prec):
     w = _case(flux, n, M)
-    p = R.RIDG_PREC_FP64 if prec == "fp64" else R.RIDG_PREC_MIXED_FP32
-    s = _solver(R, w, precision=p)
+    s = _solver(R, w, precision=_prec(R, prec))
     s.set_state(I.initial_state(w))
     m0 = s.mass()
     s.step(3)
@@ -216,11 +219,30 @@ def test_burgers_ensemble_batch_matches_oracle(R):
     ridg_batch_destroy(b)
 
 
+def test_newton_tf32_step_and_factorisations(R):
+    """TF32 tensor-core block updates: a full step matches the oracle, and the refinement
+    sweeps against the FP64 residual keep the factorisations per region near one."""
+    w = _euler((16, 13), 2)
+    q = I.initial_state(w)
+    s = _solver(R, w, precision=R.RIDG_PREC_MIXED_TF32)
+    s.set_state(q)
+    dt = s.info()["dt"]
+    s.step(1)
+    s.sync()
+    assert _rel(s.get_state(), NL.step(q, w, dt)) < 1e-11
+    info = s.info()
+    assert info["newton_unconverged"] == 0
+    assert info["newton_iters_total"] <= 2 * s.cells
+    s.close()
+
+
 # ---- full-size workloads, sampled cells -------------------------------------------------
-def test_euler_512_prediction_sampled(R):
-    """The 2D Euler vortex at 512 x 512, Q2 (FP32 solves): sampled cells vs the oracle."""
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_euler_512_prediction_sampled(R, prec):
+    """The 2D Euler vortex at 512 x 512, Q2 (FP32 / TF32 solves): sampled cells vs the
+    oracle."""
     w = I.workload("euler2d_n512_q2")
-    s = _solver(R, w, precision=R.RIDG_PREC_MIXED_FP32)
+    s = _solver(R, w, precision=_prec(R, prec))
     q = I.initial_state(w)
     s.set_state(q)
     dt = s.info()["dt"]
