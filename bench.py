@@ -169,12 +169,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # FP64 FMA: 2 per clock per S
 
 
 def newton_section(R, I, steps, cpu_cells):
-    """The Newton prediction + correction of the 2D Euler vortex (512 x 512, Q2, m = 4): FP32
-    Jacobian / solves with the FP64 residual at full size, FP64 solves on a 128 x 128 mesh of
-    the same problem, and the oracle on a sample of cells (extrapolated per step)."""
+    """The Newton prediction + correction of the 2D Euler vortex (512 x 512, Q2, m = 4): at full
+    size the TF32 tensor-core block updates and the FP32 solves (both with the FP64 residual),
+    FP64 solves on a 128 x 128 mesh of the same problem, and the oracle on a sample of cells
+    (extrapolated per step)."""
     from oracle import nonlinear as ONL
     out = {"workload": NL_WORKLOAD}
-    for tag, mesh, prec, peak in (("mixed_fp32", None, R.RIDG_PREC_MIXED_FP32, FP32_PEAK_TFLOPS),
+    for tag, mesh, prec, peak in (("mixed_tf32", None, R.RIDG_PREC_MIXED_TF32, FP32_PEAK_TFLOPS),
+                                  ("mixed_fp32", None, R.RIDG_PREC_MIXED_FP32, FP32_PEAK_TFLOPS),
                                   ("fp64_128x128", (128, 128), R.RIDG_PREC_FP64, FP64_PEAK_TFLOPS)):
         w = I.workload(NL_WORKLOAD, **({"n": mesh} if mesh else {}))
         s = R.Solver(2, w["n"], w["M"], flux="euler", cfl=w["cfl"], lo=w["lo"], hi=w["hi"],
@@ -199,9 +201,17 @@ def newton_section(R, I, steps, cpu_cells):
              "newton_iters_max": info["newton_iters_max"],
              "roofline": {"bound": "alu", "kernel": "newton_kernel", "achieved": ach, "peak": peak,
                           "unit": "TFLOP/s", "frac": ach / peak,
-                          "traffic": (_recorded_traffic("newton_fp32", info["newton_iters_total"] / steps)
-                                      if tag == "mixed_fp32" else None),
+                          "traffic": (_recorded_traffic("newton_" + tag[6:], info["newton_iters_total"] / steps)
+                                      if tag.startswith("mixed") else None),
                           "peak_source": "nominal: FMA pipes x 2 flop x 2.07 GHz"}}
+        if tag == "mixed_tf32":
+            # the 56 block products alone (2 b^3 flop each: 112 of the 118 b^3) on the TF32
+            # tensor cores: TF32 peak = the measured BF16 peak x the nominal TF32 / BF16 ratio
+            tf32_peak = _peaks()[1] * 0.5
+            upd = 112.0 * bs ** 3 * iters / (p["predict_ms"] * 1e-3) / 1e12
+            r["tensor"] = {"kernel": "newton_kernel (block updates)", "achieved": upd,
+                           "peak": tf32_peak, "unit": "TFLOP/s", "frac": upd / tf32_peak,
+                           "peak_source": "measured BF16 x nominal TF32/BF16 (1/2)"}
         out[tag] = r
     # the oracle: Newton prediction of a sample of cells and the correction of the whole
     # mesh is not needed for a per-cell rate; extrapolated to every cell of the step
