@@ -98,6 +98,9 @@ CorrParams corr_params(const ridg_t* h) {
     split(cp.nu[d], cp.nuh[d], cp.nul[d]);
     split(cp.nup[d], cp.nph[d], cp.npl[d]);
     split(cp.num[d], cp.nmh[d], cp.nml[d]);
+    for (int a = 0; a < ridg::kMaxNB; ++a)
+      split(a >= 1 && a < h->nb ? cp.nu[d] * cp.D[a * ridg::kMaxNB + a - 1] : 0.0, cp.vdh[d][a],
+            cp.vdl[d][a]);
   }
   return cp;
 }

@@ -358,64 +358,60 @@ __global__ void __launch_bounds__(128) mixed3_faces_kernel(const float2* __restr
   }
 }
 
-// The update: one thread per (cell, 8-mode group).  dQ = sum_d [nu_d (D along d) W-bar
-// - phi_a(+1) F(i + 1/2) + phi_a(-1) F(i - 1/2)] in double-float, Q += dQ in FP64, then the
-// group's digit rows of the new state (and ghost copies) and the running maximum.
+// The update: one thread per (cell, 8-mode group), the group uniform over a block and the P
+// blocks of the same 128 cells adjacent in launch order (so that they share the cells' state
+// rows in L2).  dQ = sum_d [(nu_d D[a][a-1]) W-bar(mode a-1 along d) + phi_a(+1) (s_a
+// F(i - 1/2) - F(i + 1/2))], s_a = (-1)^a = phi_a(-1) / phi_a(+1), in double-float; Q += dQ
+// in FP64; then the group's digit rows of the new state (and ghost copies) and the running
+// maximum.  Degrees up to 2: a mode has at most one volume-term source per direction.
 template <int NB, int S>
 __global__ void __launch_bounds__(128) mixed3_correct_kernel(
     double* __restrict__ Q, const float2* __restrict__ Y, const float2* __restrict__ F, int nx,
     int ny, int nz, CorrParams cp, int gmax, int* __restrict__ exps,
     unsigned long long* __restrict__ maxbits, uint4* __restrict__ planes, int* status) {
+  static_assert(NB <= 3, "one volume-term source per mode and direction");
   constexpr int THS = NB * NB * NB, NT = NB * NB;
   constexpr int P = ((THS + 15) / 16) * 2;
   __shared__ unsigned long long shmax[4];
   const long long ncell = (long long)nx * ny * nz;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int pg = (int)(blockIdx.x % P), m0 = 8 * pg;
+  const long long e = (long long)(blockIdx.x / P) * blockDim.x + threadIdx.x;
   const int ys = exps[1];
   const int snext = exponent_above(maxbits[0]) + 1;
   unsigned long long mymax = 0;
   bool fits = true;
-  if (i < ncell * P) {
-    const long long e = i / P;
-    const int pg = (int)(i % P), m0 = 8 * pg;
+  if (e < ncell) {
     const unsigned ue = (unsigned)e, ur = ue / (unsigned)nx;
     const int ix = (int)(ue - ur * (unsigned)nx), iy = (int)(ur % (unsigned)ny), iz = (int)(ur / (unsigned)ny);
-    const int co[3] = {ix, iy, iz}, nn[3] = {nx, ny, nz};
+    // left neighbours along x, y, z (periodic)
+    long long jl[3];
+    jl[0] = ix == 0 ? e + (nx - 1) : e - 1;
+    jl[1] = iy == 0 ? e + (long long)(ny - 1) * nx : e - nx;
+    jl[2] = iz == 0 ? e + (long long)(nz - 1) * nx * ny : e - (long long)nx * ny;
     DF3 dq[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) dq[j] = DF3{0.f, 0.f};
 #pragma unroll
     for (int dd = 0; dd < 3; ++dd) {
       const int st = dd == 0 ? 1 : (dd == 1 ? NB : NB * NB);
-      const float nuh = cp.nuh[dd], nul = cp.nul[dd];
-      int l[3] = {ix, iy, iz};
-      l[dd] = co[dd] == 0 ? nn[dd] - 1 : co[dd] - 1;
-      const long long jl = ((long long)l[2] * ny + l[1]) * nx + l[0];
+      const float2* Fd = F + (long long)dd * NT * ncell;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int sm = m0 + j;
         if (sm >= THS) continue;
-        const int a = (sm / st) % NB;                  // index along d
-        const int base = sm - a * st;                  // the line's first mode
-        const int t = (base % st) + (base / (st * NB)) * st;  // line index
-        // volume term (D[a][b] != 0 only for a > b, a + b odd)
-        DF3 acc{0.f, 0.f};
-        bool any = false;
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-          if (a > b && ((a + b) & 1)) {
-            const float2 y = Y[(base + b * st) * ncell + e];
-            acc = df3_add(acc, df3_mul(cp.Dh[a * kMaxNB + b], cp.Dl[a * kMaxNB + b], DF3{y.x, y.y}));
-            any = true;
-          }
+        const int a = (sm / st) % NB;                          // index along d
+        const int base = sm - a * st;                          // the line's first mode
+        const int t = (base % st) + (base / (st * NB)) * st;   // line index
         DF3 v = dq[j];
-        if (any) v = df3_add(v, df3_mul(nuh, nul, acc));
-        const float2 fp = F[(long long)(dd * NT + t) * ncell + e];
-        const float2 fm = F[(long long)(dd * NT + t) * ncell + jl];
+        if (a >= 1) {
+          const float2 y = Y[(base + (a - 1) * st) * ncell + e];
+          v = df3_add(v, df3_mul(cp.vdh[dd][a], cp.vdl[dd][a], DF3{y.x, y.y}));
+        }
+        const float2 fp = Fd[t * ncell + e];
+        const float2 fm = Fd[t * ncell + jl[dd]];
         const float sg = (a & 1) ? -1.f : 1.f;
-        v = df3_add(v, df3_mul(-cp.eph[a], -cp.epl[a], DF3{fp.x, fp.y}));
-        v = df3_add(v, df3_mul(sg * cp.eph[a], sg * cp.epl[a], DF3{fm.x, fm.y}));
-        dq[j] = v;
+        const DF3 df = df3_add(DF3{sg * fm.x, sg * fm.y}, DF3{-fp.x, -fp.y});
+        dq[j] = df3_add(v, df3_mul(cp.eph[a], cp.epl[a], df));
       }
     }
     const int kfin = ys + gmax - 16;
@@ -604,7 +600,7 @@ static cudaError_t launch_correct3_t(const Grid& g, double* Q, const void* Y, vo
   const dim3 fblocks((unsigned)((g.ncell + 127) / 128), 3);
   mixed3_faces_kernel<NB><<<fblocks, 128, 0, s>>>((const float2*)Y, g.n[0], g.n[1], g.n[2], cp,
                                                   (float2*)F);
-  const unsigned blocks = (unsigned)((g.ncell * P + 127) / 128);
+  const unsigned blocks = (unsigned)((g.ncell + 127) / 128) * P;
   mixed3_correct_kernel<NB, S><<<blocks, 128, 0, s>>>(Q, (const float2*)Y, (const float2*)F,
                                                       g.n[0], g.n[1], g.n[2], cp, gmax, ms.exps,
                                                       ms.maxbits, (uint4*)ms.planes, ms.status);

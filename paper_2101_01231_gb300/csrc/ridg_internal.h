@@ -22,6 +22,9 @@ struct CorrParams {
   // the same constants as double-float pairs (hi, lo), for the FP32 correction kernels
   float Dh[kMaxNB * kMaxNB], Dl[kMaxNB * kMaxNB];
   float nuh[3], nul[3], nph[3], npl[3], nmh[3], nml[3];
+  // nu_d D[a][a-1] as double-float pairs: the one volume-term coefficient of mode a along d
+  // for degrees up to 2 (D[a][b] != 0 only for a > b, a + b odd)
+  float vdh[3][kMaxNB], vdl[3][kMaxNB];
 };
 
 struct Grid {
