@@ -69,41 +69,53 @@ __device__ __forceinline__ long long to_fixed(double x, int s, int L) {
   return (u >> 63) ? -F : F;
 }
 
+// The S balanced base-256 digits of one coefficient (fixed point with 8 S fraction bits
+// relative to 2^s), most significant first, as BF16 bit patterns (exact: |digit| <= 256).
+// Returns false if the value does not fit below 2^s.
+template <int S>
+__device__ __forceinline__ bool value_digit_bits(double x, int s, uint32_t (&bits)[S]) {
+  constexpr int L = kBits * S;
+  const long long F = to_fixed(x, s, L);
+  const bool fits = (F < (1LL << L)) && (F > -(1LL << L));
+  const uint32_t lo32 = (uint32_t)F, hi32 = (uint32_t)((unsigned long long)F >> 32);
+  const int neg = (int)(hi32 >> 31);
+  int carry = 0;
+  int d[S];
+#pragma unroll
+  for (int a = S - 1; a >= 0; --a) {
+    const int k = S - 1 - a;  // byte index of digit a
+    const uint32_t byte = (k < 4 ? (lo32 >> (8 * k)) : (hi32 >> (8 * (k - 4)))) & 0xFFu;
+    if (a > 0) {
+      const int t = (int)byte + carry;
+      carry = (t + 128) >> 8;
+      d[a] = t - (carry << 8);
+    } else {
+      d[0] = (int)byte - (neg << 8) + carry;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < S; ++a)
+    // |d| <= 256: exact in FP32 by the 1.5 * 2^23 trick, and its BF16 is the top half
+    bits[a] = __float_as_uint(__int_as_float(0x4B400000 + d[a]) - 12582912.0f) >> 16;
+  return fits;
+}
+
 // S balanced base-256 digits of 8 consecutive coefficients, packed as BF16 (one 16 B row
 // per digit).  Returns false if a value does not fit below 2^s.
 template <int S>
 __device__ __forceinline__ bool make_digit_rows(const double* v, int s, uint4* rows) {
-  constexpr int L = kBits * S;
   uint32_t packed[S][4];
   bool fits = true;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const long long F = to_fixed(v[j], s, L);
-    fits &= (F < (1LL << L)) && (F > -(1LL << L));
-    const uint32_t lo32 = (uint32_t)F, hi32 = (uint32_t)((unsigned long long)F >> 32);
-    const int neg = (int)(hi32 >> 31);
-    int carry = 0;
-    int d[S];
-#pragma unroll
-    for (int a = S - 1; a >= 0; --a) {
-      const int k = S - 1 - a;  // byte index of digit a
-      const uint32_t byte = (k < 4 ? (lo32 >> (8 * k)) : (hi32 >> (8 * (k - 4)))) & 0xFFu;
-      if (a > 0) {
-        const int t = (int)byte + carry;
-        carry = (t + 128) >> 8;
-        d[a] = t - (carry << 8);
-      } else {
-        d[0] = (int)byte - (neg << 8) + carry;
-      }
-    }
+    uint32_t b[S];
+    fits &= value_digit_bits<S>(v[j], s, b);
 #pragma unroll
     for (int a = 0; a < S; ++a) {
-      // |d| <= 256: exact in FP32 by the 1.5 * 2^23 trick, and its BF16 is the top half
-      const uint32_t b = __float_as_uint(__int_as_float(0x4B400000 + d[a]) - 12582912.0f) >> 16;
       if (j & 1)
-        packed[a][j / 2] |= b << 16;
+        packed[a][j / 2] |= b[a] << 16;
       else
-        packed[a][j / 2] = b;
+        packed[a][j / 2] = b[a];
     }
   }
 #pragma unroll
