@@ -45,6 +45,10 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--newton-steps", type=int, default=1,
                    help="timed steps of the Newton path (0: skip it)")
+    p.add_argument("--adv1d-reps", type=int, default=20,
+                   help="whole 1D runs to T = 1 timed (0: skip the 1D section)")
+    p.add_argument("--ensemble-steps", type=int, default=1,
+                   help="full-size Burgers-ensemble steps timed (0: skip; ~45 s per step)")
     p.add_argument("--mixed3d-steps", type=int, default=20,
                    help="timed steps of the 3D tensor-core path (0: skip it)")
     return p.parse_args()
@@ -157,6 +161,126 @@ def mixed3d_section(R, I, steps, warmup):
                              "tensor_peak_tflops": bf16,
                              "algorithmic_tflops": 2.0 * thS * K * cells / (p["predict_ms"] * 1e-3) / 1e12}
         out[tag] = r
+    return out
+
+
+def adv1d_section(R, I, reps):
+    """1D advection, 64 cells, Q3, FP64, to t = 1: the whole run (one captured graph of all
+    its steps) timed with CUDA events, per step in ns; its L2 error against the exact
+    solution and the oracle's, and the oracle's own run on the host."""
+    import torch
+    from oracle import error as OE
+    from oracle import linear as OL
+    w = I.workload("adv1d_n64_q3")
+    q0 = I.initial_state(w)
+    s = R.Solver(1, w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"], hi=w["hi"])
+    s.set_state(q0)
+    nt = s.set_final_time(T_FINAL)
+    s.step(nt)                                  # warm-up (captures the nt-step graph)
+    s.sync()
+    exact = I.exact_coefficients(w, T_FINAL)
+    err = s.l2_error(exact)
+    dt = s.info()["dt"]
+    times = []
+    for _ in range(reps):
+        s.set_state(q0)
+        s.set_final_time(T_FINAL)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s.stream)
+        s.step(nt)
+        b.record(s.stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    s.close()
+    ms = float(np.median(times))
+    t0 = time.perf_counter()
+    qo = OL.run(q0, w, dt, nt)
+    t_or = time.perf_counter() - t0
+    err_or = OE.l2_relative_error(qo, exact, w["M"], 1)
+    cells, thS = int(np.prod(w["n"])), w["M"] + 1
+    return {"workload": w["name"], "steps_to_T": nt, "run_ms": ms, "ns_per_step": ms / nt * 1e6,
+            "value": cells * thS * nt / (ms * 1e-3), "unit": "element-DOF updates/s",
+            "roofline": None, "bound": "launch / latency (2 KB of state)",
+            "l2_error": err, "l2_error_oracle": err_or,
+            "cpu_oracle": {"kind": "oracle", "cores": 1, "seconds_per_run": t_or,
+                           "value": cells * thS * nt / t_or, "unit": "element-DOF updates/s",
+                           "sample": f"the whole run ({nt} steps)"}}
+
+
+def ensemble_section(R, I, steps, cpu_cells):
+    """The batched Burgers ensemble (64 instances, N ~ U{64..512}, Q1-Q4, seeded Fourier data)
+    advanced by ridg_batch_step: one captured graph per step holding one persistent Newton
+    launch per degree over all the instances of that degree, then the corrections; TF32
+    block updates with the FP64 residual.  Warm-up on the same ensemble capped at 64 x 64
+    (the same kernels), then `steps` full-size steps timed with CUDA events on the batch's
+    stream; the oracle's Newton prediction on a sample of cells per degree, extrapolated."""
+    import torch
+    from oracle import linear as OL
+    from oracle import nonlinear as ONL
+    ens = I.burgers_ensemble()
+    stream = torch.cuda.Stream()
+    opt = R.make_options(precision=R.RIDG_PREC_MIXED_TF32, stream=stream.cuda_stream)
+
+    def batch(ws):
+        b = R.ridg_batch_create([R.make_mesh(2, w["n"]) for w in ws], [w["M"] for w in ws],
+                                R.make_flux("burgers"), ws[0]["cfl"], opt)
+        for i, w in enumerate(ws):
+            R.ridg_set_state(R.ridg_batch_instance(b, i), I.initial_state(w))
+        return b
+
+    small = [dict(w, n=(min(w["n"][0], 64), min(w["n"][1], 64))) for w in ens]
+    b = batch(small)
+    R.ridg_batch_step(b, 1)
+    R.ridg_batch_sync(b)
+    R.ridg_batch_destroy(b)
+    b = batch(ens)
+    times, status = [], []
+    for _ in range(steps):
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        R.ridg_batch_step(b, 1)
+        a1.record(stream)
+        status.append(R.ridg_batch_sync(b))
+        times.append(a0.elapsed_time(a1))
+    infos = [R.ridg_info(R.ridg_batch_instance(b, i)) for i in range(len(ens))]
+    R.ridg_batch_destroy(b)
+    ms = float(np.mean(times))
+    dof = sum(int(np.prod(w["n"])) * (w["M"] + 1) ** 2 for w in ens)
+    # algorithmic work of the block eliminations: 118 b^3 flop per factorisation, b = theta_T
+    flops = sum(118.0 * (w["M"] + 1) ** 9 * inf["newton_iters_total"] for w, inf in zip(ens, infos))
+    ach = flops / (ms * 1e-3) / 1e12
+    out = {"workload": "burgers_ensemble_64", "instances": len(ens),
+           "cells": sum(int(np.prod(w["n"])) for w in ens),
+           "cells_per_degree": {str(m): sum(int(np.prod(w["n"])) for w in ens if w["M"] == m)
+                                for m in (1, 2, 3, 4)},
+           "precision": "mixed_tf32", "steps": steps, "ms_per_step": ms,
+           "value": dof / (ms * 1e-3), "unit": "element-DOF updates/s",
+           "launches_per_step": "1 Newton launch per degree + 1 correction per instance",
+           "newton_unconverged": sum(inf["newton_unconverged"] for inf in infos),
+           "status": [int(x) for x in status],
+           "roofline": {"bound": "alu", "kernel": "newton_kernel (4 launches, one per degree)",
+                        "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                        "peak_source": "nominal: FMA pipes x 2 flop x 2.07 GHz"}}
+    # the oracle: per-cell Newton prediction time per degree (a 32 x 32 copy of the first
+    # instance of each degree), extrapolated to the ensemble's cells
+    per = {}
+    for m in (1, 2, 3, 4):
+        w = dict(next(x for x in ens if x["M"] == m), n=(32, 32))
+        q = I.initial_state(w)
+        dt, _ = OL.time_step(w, ONL.max_speed(q, w))
+        k = cpu_cells if m < 3 else 2
+        t0 = time.perf_counter()
+        ONL.newton_predict(q, w, dt, cells=np.arange(k))
+        per[m] = (time.perf_counter() - t0) / k
+    t_or = sum(int(np.prod(w["n"])) * per[w["M"]] for w in ens)
+    out["cpu_oracle"] = {"kind": "oracle", "cores": os.cpu_count(),
+                         "seconds_per_cell": {str(m): v for m, v in per.items()},
+                         "value": dof / t_or, "unit": "element-DOF updates/s",
+                         "sample": f"Newton predictions of {cpu_cells} cells (Q1, Q2) / 2 cells "
+                                   "(Q3, Q4) per degree, extrapolated to the ensemble (numpy)"}
     return out
 
 
@@ -369,9 +493,9 @@ def run_ours(args):
 
     def timed(pname, steps, warmup, clocks=None):
         """Whole steps through ridg_step (the captured graph: prediction and correction back to
-        back, the correction a programmatic dependent of the prediction), timed with CUDA
-        events on the handle's stream, L2 flushed before each; then the per-kernel split
-        (prediction / correction, events around each launch) under the same flush."""
+        back), timed with CUDA events on the handle's stream, L2 flushed before each; then
+        the per-kernel split (prediction / correction, events around each launch) under the
+        same flush."""
         s = make(pname)
         s.set_state(q0)
         s.set_final_time(T_FINAL)
@@ -503,6 +627,10 @@ def run_ours(args):
         line["mixed3d"] = mixed3d_section(R, I, args.mixed3d_steps, args.warmup)
     if args.newton_steps > 0:
         line["newton"] = newton_section(R, I, args.newton_steps, 8 if args.no_cpu_baseline else 16)
+    if args.adv1d_reps > 0:
+        line["adv1d"] = adv1d_section(R, I, args.adv1d_reps)
+    if args.ensemble_steps > 0:
+        line["ensemble"] = ensemble_section(R, I, args.ensemble_steps, 4)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:

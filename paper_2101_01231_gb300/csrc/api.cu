@@ -825,15 +825,86 @@ int ridg_l2_error(ridg_t* h, const double* x, int on_device, double* err) {
 // batched ensemble: independent instances sharing one stream; n steps of all of them are
 // captured into a single graph and replayed.
 // ------------------------------------------------------------------------------------------
+// Instances of a nonlinear batch with the same degree: one persistent Newton launch covers
+// all their regions (instance table on the device, one region counter).
+struct NlGroup {
+  std::vector<int> idx;                // instances of the group, in batch order
+  std::vector<ridg::NlInst> host;      // the table, refreshed before every batch launch
+  ridg::NlInst* table = nullptr;       // device copy
+  int* counter = nullptr;              // region counter of the group's launch
+  long long regions = 0;
+};
+
 struct ridg_batch {
   std::vector<ridg_t*> inst;
-  void* nl_scratch = nullptr;  // Newton block storage shared by the instances (run in turn)
+  std::vector<NlGroup> groups;
+  void* nl_scratch = nullptr;  // Newton block storage shared by the launches (run in turn)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::map<int, cudaGraphExec_t> graphs;
   std::map<int, cudaGraph_t> defs;
   std::vector<unsigned long long> gens;  // operator generation of each instance at capture
 };
+
+namespace {
+
+// Copy the groups' instance tables (state pointers, meshes, dt / h, statistics words) to the
+// device on the batch stream, ahead of the batch graph that reads them.
+int refresh_nl_tables(ridg_batch_t* b) {
+  for (NlGroup& g : b->groups) {
+    long long cell0 = 0;
+    for (size_t j = 0; j < g.idx.size(); ++j) {
+      ridg_t* h = b->inst[g.idx[j]];
+      ridg::NlInst& t = g.host[j];
+      t.Q = h->Q;
+      t.W = h->W;
+      t.cell0 = cell0;
+      t.nx = h->n[0];
+      t.ny = h->n[1];
+      t.lam[0] = h->dt / h->h[0];
+      t.lam[1] = h->dt / h->h[1];
+      t.stats = h->nl_words + 1;
+      t.iters_total = (unsigned long long*)(h->nl_words + 6);
+      cell0 += h->ncell;
+    }
+    g.regions = cell0;
+    if (cudaMemcpyAsync(g.table, g.host.data(), g.host.size() * sizeof(ridg::NlInst),
+                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+      return RIDG_ECUDA;
+  }
+  return RIDG_OK;
+}
+
+// One persistent Newton launch over every region of the group's instances.
+int enqueue_newton_group(ridg_batch_t* b, const NlGroup& g) {
+  ridg_t* h = b->inst[g.idx[0]];
+  ridg::NewtonArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.tb = h->nl.tb;
+  a.plan = h->plan;
+  a.Q = h->Q;
+  a.W = h->W;
+  a.nx = h->n[0];
+  a.ny = h->n[1];
+  a.ncell = g.regions;
+  a.lam[0] = h->dt / h->h[0];
+  a.lam[1] = h->dt / h->h[1];
+  a.gamma = h->flux.gamma;
+  a.max_iters = h->opt.newton_max_iters;
+  a.tol = h->opt.newton_tol;
+  a.scratch = b->nl_scratch;
+  a.scratch_per_cta = h->nl_scratch_cta;
+  a.counter = g.counter;
+  a.stats = h->nl_words + 1;
+  a.iters_total = (unsigned long long*)(h->nl_words + 6);
+  a.inst = g.table;
+  a.ninst = (int)g.idx.size();
+  RIDG_CUDA(h, ridg::launch_newton(h->nb, h->m, h->flux.kind, newton_prec(h), a, h->nl_grid,
+                                   b->stream));
+  return RIDG_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -879,6 +950,24 @@ int ridg_batch_create(int count, const ridg_mesh* meshes, const int* orders, con
       h->nl_scratch = b->nl_scratch;
       h->nl_scratch_shared = true;
     }
+    std::map<int, int> gi;  // degree -> group
+    for (int i = 0; i < count; ++i) {
+      const int nb = b->inst[i]->nb;
+      if (!gi.count(nb)) {
+        gi[nb] = (int)b->groups.size();
+        b->groups.emplace_back();
+      }
+      b->groups[gi[nb]].idx.push_back(i);
+    }
+    for (NlGroup& g : b->groups) {
+      g.host.resize(g.idx.size());
+      g.table = (ridg::NlInst*)dev_alloc(b->inst[0], g.idx.size() * sizeof(ridg::NlInst));
+      g.counter = (int*)dev_alloc(b->inst[0], 4 * sizeof(int));
+      if (!g.table || !g.counter) {
+        ridg_batch_destroy(b);
+        return RIDG_ENOMEM;
+      }
+    }
   }
   *out = b;
   return RIDG_OK;
@@ -890,6 +979,10 @@ void ridg_batch_destroy(ridg_batch_t* b) {
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : b->defs) cudaGraphDestroy(kv.second);
   if (b->nl_scratch && !b->inst.empty()) dev_free(b->inst[0], b->nl_scratch);
+  for (NlGroup& g : b->groups) {
+    if (g.table) dev_free(b->inst[0], g.table);
+    if (g.counter) dev_free(b->inst[0], g.counter);
+  }
   for (ridg_t* h : b->inst) ridg_destroy(h);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -917,17 +1010,37 @@ int ridg_batch_step(ridg_batch_t* b, int n) {
     b->gens.clear();
     for (ridg_t* h : b->inst) b->gens.push_back(h->gen);
   }
+  // the instance tables (and the groups' region counts the graphs are captured with)
+  if (!b->groups.empty()) {
+    const int rc = refresh_nl_tables(b);
+    if (rc) return rc;
+  }
   auto it = b->graphs.find(n);
   if (it == b->graphs.end()) {
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return RIDG_ECUDA;
     int rc = RIDG_OK;
-    for (int i = 0; i < n && rc == RIDG_OK; ++i)
-      for (ridg_t* h : b->inst) {
-        rc = enqueue_step(h);
-        if (rc) break;
+    for (int i = 0; i < n && rc == RIDG_OK; ++i) {
+      if (b->groups.empty()) {
+        for (ridg_t* h : b->inst) {
+          rc = enqueue_step(h);
+          if (rc) break;
+        }
+      } else {
+        // nonlinear flux: one Newton launch per degree over all its instances, then the
+        // instances' corrections
+        for (const NlGroup& g : b->groups) {
+          rc = enqueue_newton_group(b, g);
+          if (rc) break;
+          for (int j : g.idx) {
+            rc = enqueue_nl_correct(b->inst[j]);
+            if (rc) break;
+          }
+          if (rc) break;
+        }
       }
+    }
     cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
     if (rc != RIDG_OK || ce != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);

@@ -119,6 +119,17 @@ struct TcDims {
   static constexpr int NS = BP / kKS;                   // K-slices per product
 };
 
+// the instance of the region a CTA is solving, kept in shared memory (read where needed,
+// so that it holds no registers through the Newton iteration)
+struct RegionCtx {
+  double lam[2];
+  double* W;
+  int* stats;
+  unsigned long long* itot;
+  long long e;  // the region (cell) within its instance
+};
+static_assert(sizeof(RegionCtx) <= 64, "RegionCtx slot");
+
 // shared-memory layout (bytes) of one CTA
 template <typename T, int NB, int MV, bool TC = false>
 struct Layout {
@@ -135,10 +146,12 @@ struct Layout {
   static constexpr size_t oProw = up16(oRow + sizeof(T) * 2 * D::BP);
   static constexpr size_t oRank = up16(oProw + sizeof(int) * D::BP);
   static constexpr size_t oMisc = up16(oRank + sizeof(int) * D::BP);
+  // the current region's instance (RegionCtx)
+  static constexpr size_t oCtx = up16(oMisc + sizeof(int) * 16);
   // mbarriers of the tensor-core products: full[kStages], empty[kStages], acc; TMEM address
-  static constexpr size_t oBar = up16(oMisc + sizeof(int) * 16);
+  static constexpr size_t oBar = up16(oCtx + 64);
   static constexpr size_t oTmem = oBar + 8 * (2 * kStages + 1);
-  static constexpr size_t oArena = TC ? ((oTmem + 4 + 127) & ~(size_t)127) : up16(oMisc + sizeof(int) * 16);
+  static constexpr size_t oArena = TC ? ((oTmem + 4 + 127) & ~(size_t)127) : up16(oCtx + 64);
   // phase arenas
   static constexpr size_t aRes = sizeof(double) * ResBufs<NB, MV>::total;
   static constexpr size_t aAlpha = sizeof(double) * 12 * D::QF;
@@ -1329,7 +1342,7 @@ __device__ void stored_solve_tc(const float* slots, const NlPlan& plan, float* x
 // ---------------------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------------------
-template <typename T, int NB, int MV, int FLUX, bool TC>
+template <typename T, int NB, int MV, int FLUX, bool TC, bool BATCH>
 __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newton_kernel(const NewtonArgs a) {
   static_assert(!TC || sizeof(T) == 4, "tensor-core block products are TF32 (T = float)");
   using D = Dims<NB, MV>;
@@ -1355,9 +1368,7 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newto
   T* sA = (T*)(arena + L::oSA);
   T* sB = (T*)(arena + L::oSB);
   const int tid = threadIdx.x;
-  const int nx = a.nx, ny = a.ny;
   T* slots = (T*)((char*)a.scratch + (size_t)blockIdx.x * a.scratch_per_cta);
-  int* flags = a.stats + 2;
   TcCtx tc{};
   if constexpr (TC) {
     // TMEM accumulator (128 columns >= BP) and the ring's mbarriers
@@ -1384,18 +1395,47 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newto
   for (;;) {
     if (tid == 0) misc[0] = atomicAdd(a.counter, 1);
     __syncthreads();
-    const long long e = misc[0];
+    const long long eg = misc[0];
     const bool stop = TC && misc[1] != 0;  // a tensor-core wait timed out
     __syncthreads();
-    if (e >= a.ncell || stop) break;
+    if (eg >= a.ncell || stop) break;
+    // the region's instance: the handle's own mesh (its parameters read from the launch's
+    // constant bank), or (batched launch) the last instance of the table whose first region
+    // is <= eg, its parameters kept in shared memory
+    RegionCtx* ctx = (RegionCtx*)(smem + L::oCtx);
+    const double* Qg = a.Q;
+    int nx = a.nx, ny = a.ny;
+    long long e = eg;
+    if constexpr (BATCH) {
+      int lo = 0, hi = a.ninst - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.inst[mid].cell0 <= eg) lo = mid; else hi = mid - 1;
+      }
+      const NlInst& in = a.inst[lo];
+      Qg = in.Q;
+      nx = in.nx;
+      ny = in.ny;
+      e = eg - in.cell0;
+      if (tid == 0) {
+        ctx->e = e;
+        ctx->lam[0] = in.lam[0];
+        ctx->lam[1] = in.lam[1];
+        ctx->W = in.W;
+        ctx->stats = in.stats;
+        ctx->itot = in.iters_total;
+      }
+    }
+    const double* lam = BATCH ? ctx->lam : a.lam;
     const unsigned ue = (unsigned)e, uy = ue / (unsigned)nx;
     const int ix = (int)(ue - uy * (unsigned)nx), iy = (int)uy;
     for (int i = tid; i < 9 * MV * D::THS; i += kThreads) {
       const int r = i / (MV * D::THS), rem = i % (MV * D::THS);
       const long long c = (long long)((iy + r / 3 - 1 + ny) % ny) * nx + (ix + r % 3 - 1 + nx) % nx;
-      Qs[i] = a.Q[c * MV * D::THS + rem];
+      Qs[i] = Qg[c * MV * D::THS + rem];
     }
     __syncthreads();
+    int* const stats = BATCH ? ctx->stats : a.stats;  // after the barrier: ctx is written
     for (int i = tid; i < 9 * D::BS; i += kThreads) {
       const int r = i / D::BS, j = (i / D::THT) % MV, k = i % D::THT;
       Ws[i] = k < D::THS ? Qs[(r * MV + j) * D::THS + k] : 0.0;  // Q^n extended in time
@@ -1413,12 +1453,12 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newto
     double dprev = 0.0;
     while (!conv && !bad) {
       if (refactor && it >= a.max_iters) break;
-      residual<NB, MV, FLUX>(a.tb, Ws, Qs, Rs, alpha, (double*)arena, a.lam, a.gamma);
+      residual<NB, MV, FLUX>(a.tb, Ws, Qs, Rs, alpha, (double*)arena, lam, a.gamma);
       if (refactor) {
         for (int r0 = 0; r0 < 9; r0 += D::CG) {
           for (int g = 0; g < D::CG; ++g)
             project_cell<T, NB, MV, FLUX>(a.tb, r0 + g, Ws, alpha, FA + g * D::FAS, jw, jb0, jb1,
-                                          a.lam, a.gamma);
+                                          lam, a.gamma);
           assemble_cells<T, NB, MV, TC>(a.tb, a.plan, r0, FA, slots);
         }
       }
@@ -1430,8 +1470,8 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newto
       if constexpr (TC) {
         if (refactor) {
           if (!block_solve_tc<D::BS, D::BP, D::RR>(slots, a.plan, xs, tc, colv, rowp, prow, rank,
-                                                    flags)) {
-            if (tid == 0) atomicOr(flags, kFlagTimeout);
+                                                    stats + 2)) {
+            if (tid == 0) atomicOr(stats + 2, kFlagTimeout);
             misc[1] = 1;  // stop: the CTA's remaining regions are not solved
             break;
           }
@@ -1441,7 +1481,7 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newto
       } else {
         if (refactor)
           block_solve<T, D::BS, D::BP, D::RR, L::NBUF, CHORD>(slots, a.plan, xs, S, sA, sB, colv,
-                                                              rowp, prow, rank, flags);
+                                                              rowp, prow, rank, stats + 2);
         else
           stored_solve<T, D::BS, D::BP>(slots, a.plan, xs, colv);
       }
@@ -1469,12 +1509,16 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newto
       refactor = !CHORD || (sweeps > 0 && dn > 0.1 * dprev) || sweeps >= kSweeps;
       dprev = dn;
     }
-    for (int i = tid; i < D::BS; i += kThreads) a.W[e * D::BS + i] = Ws[4 * D::BS + i];
+    {
+      double* W = BATCH ? ctx->W : a.W;
+      const long long eo = BATCH ? ctx->e : e;
+      for (int i = tid; i < D::BS; i += kThreads) W[eo * D::BS + i] = Ws[4 * D::BS + i];
+    }
     if (tid == 0) {
-      if (!conv) atomicAdd(&a.stats[0], 1);
-      atomicMax(&a.stats[1], it);
-      atomicAdd(a.iters_total, (unsigned long long)it);
-      if (bad) atomicOr(flags, kFlagNonFinite);
+      if (!conv) atomicAdd(&stats[0], 1);
+      atomicMax(&stats[1], it);
+      atomicAdd(BATCH ? ctx->itot : a.iters_total, (unsigned long long)it);
+      if (bad) atomicOr(stats + 2, kFlagNonFinite);
     }
     __syncthreads();
   }
@@ -1490,24 +1534,25 @@ template <typename T, int NB, int MV, int FLUX, bool TC>
 cudaError_t launch_one(const NewtonArgs& a, int grid, cudaStream_t s) {
   using L = Layout<T, NB, MV, TC>;
   static_assert(L::bytes <= 232448, "Newton kernel shared memory above the per-CTA limit");
-  cudaError_t e = cudaFuncSetAttribute(newton_kernel<T, NB, MV, FLUX, TC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+  auto kern = a.ninst > 0 ? newton_kernel<T, NB, MV, FLUX, TC, true>
+                          : newton_kernel<T, NB, MV, FLUX, TC, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  newton_kernel<T, NB, MV, FLUX, TC><<<grid, kThreads, L::bytes, s>>>(a);
+  kern<<<grid, kThreads, L::bytes, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T, int NB, int MV, int FLUX, bool TC>
 int ctas_one() {
   using L = Layout<T, NB, MV, TC>;
-  if (cudaFuncSetAttribute(newton_kernel<T, NB, MV, FLUX, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)L::bytes) != cudaSuccess)
+  if (cudaFuncSetAttribute(newton_kernel<T, NB, MV, FLUX, TC, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes) != cudaSuccess)
     return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, newton_kernel<T, NB, MV, FLUX, TC>, kThreads,
-                                                    L::bytes) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, newton_kernel<T, NB, MV, FLUX, TC, false>,
+                                                    kThreads, L::bytes) != cudaSuccess)
     return 0;
   // The occupancy calculator counts one CTA per SM for any kernel that uses tcgen05; the
   // tensor-core form still runs as many CTAs as its shared memory and registers allow

@@ -144,6 +144,18 @@ enum NewtonPrec { kNewtonF64 = 0, kNewtonF32 = 1, kNewtonTF32 = 2 };
 // CTAs of the persistent Newton kernel and the scratch each needs (bytes)
 int newton_grid(int nb, int m, int flux_kind, int prec);
 size_t newton_scratch_per_cta(int nb, int m, int prec, const NlPlan& plan);
+// One instance of a batched Newton launch (a device-resident table, sorted by cell0): the
+// launch's regions run over all its instances, region eg belonging to the last instance
+// whose cell0 <= eg.
+struct NlInst {
+  const double* Q;
+  double* W;
+  long long cell0;                  // first global region of the instance
+  int nx, ny;
+  double lam[2];                    // dt / h_d
+  int* stats;                       // [0] unconverged, [1] largest iteration count, [2] flags
+  unsigned long long* iters_total;  // iterations summed over the instance's regions
+};
 struct NewtonArgs {
   NlDev tb;
   NlPlan plan;
@@ -160,6 +172,8 @@ struct NewtonArgs {
   int* counter;      // work counter (zeroed before the launch)
   int* stats;        // [0] unconverged regions, [1] largest iteration count, [2] flags
   unsigned long long* iters_total;  // Newton iterations summed over regions
+  const NlInst* inst;  // batched launch: instance table (ncell = total regions), else nullptr
+  int ninst;
 };
 cudaError_t launch_newton(int nb, int m, int flux_kind, int prec, const NewtonArgs& a, int grid,
                           cudaStream_t s);
