@@ -310,6 +310,17 @@ int enqueue_correct_after_mean(ridg_t* h) {
   return RIDG_OK;
 }
 
+// Small 1D FP64 meshes run a whole sequence of steps in one launch.
+bool use_run1d(const ridg_t* h) {
+  return is_linear(h) && h->opt.precision == RIDG_PREC_FP64 && ridg::run1d_fits(grid_of(h), h->nb);
+}
+
+int enqueue_run1d(ridg_t* h, int n) {
+  const CorrParams cp = corr_params(h);
+  RIDG_CUDA(h, ridg::launch_run1d_fp64(grid_of(h), h->nb, h->Q, h->P, n, cp, h->stream));
+  return RIDG_OK;
+}
+
 int enqueue_step(ridg_t* h) {
   int rc = enqueue_predict_mean(h);
   if (rc) return rc;
@@ -675,7 +686,10 @@ int ridg_step(ridg_t* h, int n) {
     cudaGraph_t graph = nullptr;
     RIDG_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     int rc = RIDG_OK;
-    for (int i = 0; i < n && rc == RIDG_OK; ++i) rc = enqueue_step(h);
+    if (use_run1d(h))
+      rc = enqueue_run1d(h, n);
+    else
+      for (int i = 0; i < n && rc == RIDG_OK; ++i) rc = enqueue_step(h);
     cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
     if (rc != RIDG_OK) {
       if (graph) cudaGraphDestroy(graph);

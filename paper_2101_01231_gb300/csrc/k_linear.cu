@@ -186,6 +186,80 @@ __global__ void __launch_bounds__(128) correct_linear_kernel(double* __restrict_
   for (int s = 0; s < THS; ++s) q[s] = q[s] + dq[s];
 }
 
+// A whole run of n steps of a small 1D mesh in one CTA: the state and the time means stay in
+// shared memory, each step is the prediction (the same sums as predict_fp64_kernel) and the
+// correction (the same sums as correct_linear_kernel<1, NB>) separated by barriers.  Removes
+// the two launches per step that bound tiny meshes.
+template <int NB>
+__global__ void __launch_bounds__(256) run1d_fp64_kernel(double* __restrict__ Q,
+                                                         const double* __restrict__ P, int n,
+                                                         int nsteps, CorrParams cp) {
+  constexpr int K = 3 * NB;
+  extern __shared__ double sm1[];
+  double* sP = sm1;          // NB x K (the time-mean rows)
+  double* sQ = sP + NB * K;  // n x NB
+  double* sW = sQ + n * NB;  // n x NB
+  for (int i = threadIdx.x; i < NB * K; i += blockDim.x) sP[i] = P[i];
+  for (int i = threadIdx.x; i < n * NB; i += blockDim.x) sQ[i] = Q[i];
+  __syncthreads();
+  for (int step = 0; step < nsteps; ++step) {
+    for (int i = threadIdx.x; i < n * NB; i += blockDim.x) {
+      const int c = i / NB, k = i % NB;
+      double acc = 0.0;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const double* q = sQ + wrap(c + r - 1, n) * NB;
+        const double* p = sP + k * K + r * NB;
+#pragma unroll
+        for (int s2 = 0; s2 < NB; ++s2) acc = fma(p[s2], q[s2], acc);
+      }
+      sW[i] = acc;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const double* w = sW + c * NB;
+      double dq[NB];
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          if (a > b && ((a + b) & 1)) acc = fma(cp.D[a * kMaxNB + b], w[b], acc);
+        dq[a] = fma(cp.nu[0], acc, 0.0);
+      }
+      double trp, trm, nbt;
+      face_trace<1, NB>(w, 0, cp.ep, &trp);
+      face_trace<1, NB>(w, 0, cp.em, &trm);
+      face_trace<1, NB>(sW + wrap(c + 1, n) * NB, 0, cp.em, &nbt);
+      const double fp = face_value(trp, nbt, cp.nup[0], cp.num[0]);
+      face_trace<1, NB>(sW + wrap(c - 1, n) * NB, 0, cp.ep, &nbt);
+      const double fm = face_value(nbt, trm, cp.nup[0], cp.num[0]);
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        double v = dq[a];
+        v = fma(-cp.ep[a], fp, v);
+        v = fma(cp.em[a], fm, v);
+        sQ[c * NB + a] = sQ[c * NB + a] + v;
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n * NB; i += blockDim.x) Q[i] = sQ[i];
+}
+
+template <int NB>
+cudaError_t run1d_dispatch(const Grid& g, double* Q, const double* P, int nsteps,
+                           const CorrParams& cp, cudaStream_t s) {
+  const size_t smem = (size_t)(NB * 3 * NB + 2 * g.ncell * NB) * sizeof(double);
+  auto kern = run1d_fp64_kernel<NB>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<1, 256, smem, s>>>(Q, P, (int)g.ncell, nsteps, cp);
+  return cudaGetLastError();
+}
+
 template <int DIM, int NB>
 cudaError_t predict_dispatch_ch(const Grid& g, const double* Q, const double* P, int nout,
                                 double* W, int wstride, cudaStream_t s) {
@@ -248,6 +322,27 @@ cudaError_t launch_predict_fp64(const Grid& g, int nb, const double* Q, const do
     RIDG_DISPATCH_NB(3, predict_dispatch_ch, g, Q, P, nout, W, wstride, s)
   }
   return cudaErrorInvalidValue;
+}
+
+bool run1d_fits(const Grid& g, int nb) {
+  return g.dim == 1 && nb >= 1 && nb <= 8 && g.ncell <= kRun1dMaxCells &&
+         (size_t)(3 * nb * nb + 2 * g.ncell * nb) * sizeof(double) <= 96 * 1024;
+}
+
+cudaError_t launch_run1d_fp64(const Grid& g, int nb, double* Q, const double* P, int nsteps,
+                              const CorrParams& cp, cudaStream_t s) {
+  if (!run1d_fits(g, nb)) return cudaErrorInvalidValue;
+  switch (nb) {
+    case 1: return run1d_dispatch<1>(g, Q, P, nsteps, cp, s);
+    case 2: return run1d_dispatch<2>(g, Q, P, nsteps, cp, s);
+    case 3: return run1d_dispatch<3>(g, Q, P, nsteps, cp, s);
+    case 4: return run1d_dispatch<4>(g, Q, P, nsteps, cp, s);
+    case 5: return run1d_dispatch<5>(g, Q, P, nsteps, cp, s);
+    case 6: return run1d_dispatch<6>(g, Q, P, nsteps, cp, s);
+    case 7: return run1d_dispatch<7>(g, Q, P, nsteps, cp, s);
+    case 8: return run1d_dispatch<8>(g, Q, P, nsteps, cp, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_correct_linear(const Grid& g, int nb, double* Q, const double* Wbar,

@@ -38,6 +38,12 @@ struct Grid {
 cudaError_t launch_predict_fp64(const Grid& g, int nb, const double* Q, const double* P, int nout,
                                 double* W, int wstride, cudaStream_t s);
 // Q[e] += correction from the time means Wbar (stride wstride) of e and its face neighbours
+// Small 1D meshes: a whole run of nsteps FP64 steps (prediction of the time means with the
+// operator's first theta_S rows, then the correction) in one single-CTA launch.
+constexpr long long kRun1dMaxCells = 4096;
+bool run1d_fits(const Grid& g, int nb);
+cudaError_t launch_run1d_fp64(const Grid& g, int nb, double* Q, const double* P, int nsteps,
+                              const CorrParams& cp, cudaStream_t s);
 cudaError_t launch_correct_linear(const Grid& g, int nb, double* Q, const double* Wbar,
                                   int wstride, const CorrParams& cp, cudaStream_t s);
 

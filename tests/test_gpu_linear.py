@@ -119,6 +119,28 @@ def test_config1_full_run(R):
     s.close()
 
 
+@pytest.mark.parametrize("n,M,vel", [((64,), 3, (1.0,)), ((5,), 1, (-0.7,)), ((300,), 7, (0.4,)),
+                                     ((2000,), 2, (1.0,))])
+def test_run1d_single_launch_matches_step_kernels(R, n, M, vel):
+    """Small 1D meshes run ridg_step(n) as one single-CTA launch; it performs the same sums
+    as the prediction and correction kernels (ridg_profile_step), so the states agree bit
+    for bit, and match the oracle."""
+    w = _w(1, n, M, vel, cfl=0.45)
+    rng = np.random.default_rng(41)
+    q0 = rng.standard_normal((int(np.prod(n)), M + 1))
+    a, b = _solver(R, w), _solver(R, w)
+    a.set_state(q0)
+    b.set_state(q0)
+    dt = a.info()["dt"]
+    a.step(9)
+    b.profile_step(9)
+    qa, qb = a.get_state(), b.get_state()
+    assert np.array_equal(qa, qb)
+    assert _rel(qa, OL.run(q0, w, dt, 9)) < 9 * TOL_STEP
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("dim,n,M,vel", [CASES[0], CASES[3], CASES[6]])
 def test_mass_conserved(R, dim, n, M, vel):
     w = _w(dim, n, M, vel)
