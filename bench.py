@@ -140,9 +140,36 @@ def mixed3d_section(R, I, steps, warmup):
     out = {"workload": w["name"], "cells": cells, "order": w["M"], "theta_s": thS,
            "l2_flush": "none: the state (191 MB) is larger than L2"}
     hbm, bf16, src = _peaks()
+    # digit slices: the fewest whose L2 error against the exact solution at t = 1 is within
+    # 1.05x of the FP64 path's, on the noise-free variant (same mesh, degree and velocity:
+    # the exact solution of the noisy data is not available in closed form)
+    w0 = I.workload("adv3d_n96_q2", ic="sin")
+    exact = I.exact_coefficients(w0, T_FINAL)
+
+    def err_run(prec, S=0):
+        s = R.Solver(3, w0["n"], w0["M"], vel=w0["vel"], cfl=w0["cfl"], lo=w0["lo"], hi=w0["hi"],
+                     precision=prec, slices=S)
+        s.set_state(I.initial_state(w0))
+        nt = s.set_final_time(T_FINAL)
+        s.step(nt)
+        s.sync()
+        e = s.l2_error(exact)
+        s.close()
+        return e
+
+    e64 = err_run(R.RIDG_PREC_FP64)
+    sweep, S_best = {}, 6
+    for S in range(3, 7):
+        sweep[str(S)] = err_run(R.RIDG_PREC_MIXED_BF16, S)
+        if sweep[str(S)] <= 1.05 * e64:
+            S_best = S
+            break
+    out["accuracy_gate"] = {"workload": "adv3d_n96_q2, noise-free (ic = sin)", "T": T_FINAL,
+                            "l2_error_fp64_gpu": e64, "l2_error_mixed_by_slices": sweep,
+                            "slices": S_best}
     for tag, prec in (("mixed", R.RIDG_PREC_MIXED_BF16), ("fp64", R.RIDG_PREC_FP64)):
         s = R.Solver(3, w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"], hi=w["hi"],
-                     precision=prec)
+                     precision=prec, slices=S_best if tag == "mixed" else 0)
         s.set_state(q)
         s.profile_step(warmup)
         p = s.profile_step(steps if tag == "mixed" else max(3, steps // 10))
@@ -469,9 +496,12 @@ def run_ours(args):
         except R.RidgError:
             prec_name = "fp64"
 
-    def make(pname):
+    chosen = [args.slices]  # digit slices of the mixed path (0: the library's default)
+
+    def make(pname, slices=None):
         return R.Solver(w["dim"], w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"],
-                        hi=w["hi"], precision=prec[pname], slices=args.slices)
+                        hi=w["hi"], precision=prec[pname],
+                        slices=chosen[0] if slices is None else slices)
 
     cells = int(np.prod(w["n"]))
     thS = (w["M"] + 1) ** w["dim"]
@@ -479,8 +509,8 @@ def run_ours(args):
     dof = cells * thS
     q0 = I.initial_state(w)
 
-    def accuracy(pname):
-        s = make(pname)
+    def accuracy(pname, slices=None):
+        s = make(pname, slices)
         s.set_state(q0)
         nt = s.set_final_time(T_FINAL)
         s.step(nt)
@@ -540,6 +570,17 @@ def run_ours(args):
     except Exception:
         gpu_id = str(torch.cuda.current_device())
     clocks = Clocks(gpu_id)
+    # the mixed form's digit count: the fewest slices whose L2 error against the exact
+    # solution at t = 1 is within 1.05x of the FP64 path's (which matches the oracle's)
+    sweep = None
+    if prec_name == "mixed" and args.slices == 0:
+        e64_ref = accuracy("fp64")[0]
+        sweep = {}
+        for S in range(3, 8):
+            sweep[S] = accuracy("mixed", S)[0]
+            if sweep[S] <= 1.05 * e64_ref:
+                chosen[0] = S
+                break
     s, ms_step, ms_pred, ms_corr, ck = timed(prec_name, args.steps, args.warmup, clocks)
     slices_used = s.info()["slices"]
     t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
@@ -612,7 +653,8 @@ def run_ours(args):
         "config": {"workload": w["name"], "cells": cells, "order": w["M"], "theta_s": thS,
                    "precision": prec_name, "steps_to_T": nt, "l2_flush": "256 MB rewrite before each timed step",
                    "l2_error": err, "l2_error_fp64_gpu": err64, "l2_error_oracle": err_oracle,
-                   "equal_accuracy": (err <= 1.05 * err_oracle) if err_oracle else None},
+                   "equal_accuracy": (err <= 1.05 * err_oracle) if err_oracle else None,
+                   "slices_sweep_l2_error": ({str(k): v for k, v in sweep.items()} if sweep else None)},
         "kernels_ms": {"predict": ms_pred, "correct": ms_corr},
         "fp64_path": fp64,
         "roofline": roof,
