@@ -640,7 +640,7 @@ __device__ void assemble_cells(const NlDev& tb, const NlPlan& plan, int r0, cons
 template <typename T>
 __device__ __forceinline__ T recip(T x);
 template <>
-__device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float recip<float>(float x) { return __fdividef(1.0f, x); }  // ~2 ulp
 template <>
 __device__ __forceinline__ double recip<double>(double x) { return __drcp_rn(x); }
 
@@ -665,7 +665,7 @@ __device__ __forceinline__ int group_argmax(unsigned mask, double v, int row, bo
   return (int)p;
 }
 
-// x = a[k][j] (or a[j][k]) for a block-uniform index k, without dynamic register indexing
+// x = a[k][j] for a block-uniform index k, without dynamic register indexing
 template <typename T, int RR>
 __device__ __forceinline__ void pick_row(const T (&a)[RR][RR], int k, T (&x)[RR]) {
   switch (k) {
@@ -681,34 +681,35 @@ __device__ __forceinline__ void pick_row(const T (&a)[RR][RR], int k, T (&x)[RR]
 #undef RIDG_PICK_ROW
   }
 }
-template <typename T, int RR>
-__device__ __forceinline__ void pick_col(const T (&a)[RR][RR], int k, T (&x)[RR]) {
-  switch (k) {
-    default:
+// Pivot of one column, found by the half-warp that owns it (col = its entries in this
+// thread's rows ty + 16 i, used = the rows that have pivoted): the column is published to
+// cv, the pivot row to pv[0] and prow[c].
+template <typename T, int BS, int RR>
+__device__ __forceinline__ void gj_pivot(const T (&col)[RR], unsigned used, int ty,
+                                         unsigned hmask, int c, T* cv, int* pv, int* prow,
+                                         int* flags) {
+  T best = T(0);
+  int bi = 0;
+  bool have = false;
 #pragma unroll
-      for (int i = 0; i < RR; ++i) x[i] = a[i][0];
-      break;
-#define RIDG_PICK_COL(K) \
-    case K:              \
-      if constexpr (K < RR) { _Pragma("unroll") for (int i = 0; i < RR; ++i) x[i] = a[i][K]; } break;
-    RIDG_PICK_COL(1) RIDG_PICK_COL(2) RIDG_PICK_COL(3) RIDG_PICK_COL(4) RIDG_PICK_COL(5)
-    RIDG_PICK_COL(6) RIDG_PICK_COL(7)
-#undef RIDG_PICK_COL
+  for (int i = 0; i < RR; ++i) {
+    if ((used >> i) & 1u) continue;
+    const T v = fabs(col[i]);
+    if (!have || v > best) {
+      best = v;
+      bi = ty + 16 * i;
+      have = true;
+    }
   }
-}
-template <typename T, int RR>
-__device__ __forceinline__ void put_col(T (&a)[RR][RR], int k, const T (&x)[RR]) {
-  switch (k) {
-    default:
+  bool zero = false;
+  int p = group_argmax(hmask, best, bi, have, &zero);
+  if (p >= BS) p = 0;  // unreachable: an unused row is always left
 #pragma unroll
-      for (int i = 0; i < RR; ++i) a[i][0] = x[i];
-      break;
-#define RIDG_PUT_COL(K) \
-    case K:             \
-      if constexpr (K < RR) { _Pragma("unroll") for (int i = 0; i < RR; ++i) a[i][K] = x[i]; } break;
-    RIDG_PUT_COL(1) RIDG_PUT_COL(2) RIDG_PUT_COL(3) RIDG_PUT_COL(4) RIDG_PUT_COL(5)
-    RIDG_PUT_COL(6) RIDG_PUT_COL(7)
-#undef RIDG_PUT_COL
+  for (int i = 0; i < RR; ++i) cv[ty + 16 * i] = col[i];
+  if (ty == 0) {
+    pv[0] = p;
+    prow[c] = p;
+    if (zero) atomicOr(flags, kFlagSingular);
   }
 }
 
@@ -721,12 +722,15 @@ __device__ __forceinline__ void put_col(T (&a)[RR][RR], int k, const T (&x)[RR])
 // Thread (tx, ty) = (tid / 16, tid % 16) owns rows ty + 16 i and columns tx + 16 j, so a
 // column lives in one half-warp: that half-warp finds the pivot of its column and publishes
 // the column, and each thread takes the pivot row from its own half-warp by shuffles -- one
-// barrier per column.
+// barrier per column.  Look-ahead: right after a step's barrier, the half-warp owning the
+// next column updates that column alone, finds and publishes its pivot, and only then
+// updates the rest of its tile, so the pivot search overlaps the elimination.  The columns
+// run in blocks of 16 whose index cb is a compile-time constant (static register indexing).
 template <typename T, int BS, int BP, int RR, bool TC = false>
 __device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* prow, int* rank, int* flags) {
   static_assert(RR <= 8, "register tile up to 8 x 8");
   const int tid = threadIdx.x, tx = tid >> 4, ty = tid & 15;
-  const int lane = tid & 31, half = lane & 16, warp = tid >> 5;
+  const int lane = tid & 31, half = lane & 16;
   const unsigned hmask = 0xFFFFu << half;
   T a[RR][RR];
 #pragma unroll
@@ -738,74 +742,68 @@ __device__ void gj_inverse(const T* A, T* S, T* colv, T* rowp, int* prow, int* r
   for (int i = 0; i < RR; ++i)
     if (ty + 16 * i >= BS) used |= 1u << i;
   int* pv = rank;      // pivot rows of the last two columns (rank is rebuilt at the end)
-  for (int c = 0; c < BS; ++c) {
-    const int buf = c & 1, cb = c >> 4, cx = c & 15;
-    T* cv = colv + buf * BP;
-    if (warp == (cx >> 1)) {
-      // this warp's half (cx & 1) holds column c: pivot search and publication
-      if ((lane >> 4) == (cx & 1)) {
-        T col[RR];
-        pick_col(a, cb, col);
-        T best = T(0);
-        int bi = 0;
-        bool have = false;
+  if (tx == 0) {
+    T col[RR];
 #pragma unroll
-        for (int i = 0; i < RR; ++i) {
-          if ((used >> i) & 1u) continue;
-          const T v = fabs(col[i]);
-          if (!have || v > best) {
-            best = v;
-            bi = ty + 16 * i;
-            have = true;
+    for (int i = 0; i < RR; ++i) col[i] = a[i][0];
+    gj_pivot<T, BS, RR>(col, used, ty, hmask, 0, colv, pv, prow, flags);
+  }
+#pragma unroll
+  for (int cb = 0; cb < RR; ++cb) {
+    for (int cx = 0; cx < 16; ++cx) {
+      const int c = cb * 16 + cx;
+      if (c >= BS) break;
+      const int buf = c & 1;
+      const T* cv = colv + buf * BP;
+      __syncthreads();  // column c and its pivot are published
+      const int p = pv[buf];
+      const T ipiv = recip(cv[p]);
+      // the pivot row's entries in my columns, from the thread of my half-warp owning row p
+      T mine[RR], prs[RR];
+      pick_row(a, p >> 4, mine);
+      const int src = half + (p & 15);
+#pragma unroll
+      for (int j = 0; j < RR; ++j) {
+        const T v = __shfl_sync(0xffffffffu, mine[j], src);
+        prs[j] = (j == cb && tx == cx) ? ipiv : v * ipiv;
+      }
+      if ((p & 15) == ty) used |= 1u << (p >> 4);
+      // look-ahead: the owner of column c + 1 eliminates it first and publishes its pivot
+      const int cn = c + 1;
+      if (cn < BS && tx == (cn & 15)) {
+        T col[RR];
+        if ((cn >> 4) == cb) {
+#pragma unroll
+          for (int i = 0; i < RR; ++i) {
+            const int ri = ty + 16 * i;
+            col[i] = ri == p ? prs[cb] : fma(-cv[ri], prs[cb], a[i][cb]);
+          }
+        } else {
+          const int jn = cb + 1 < RR ? cb + 1 : RR - 1;  // cb + 1 (a column of the next block)
+#pragma unroll
+          for (int i = 0; i < RR; ++i) {
+            const int ri = ty + 16 * i;
+            col[i] = ri == p ? prs[jn] : fma(-cv[ri], prs[jn], a[i][jn]);
           }
         }
-        bool zero = false;
-        int p = group_argmax(hmask, best, bi, have, &zero);
-        if (p >= BS) p = 0;  // unreachable: an unused row is always left
-#pragma unroll
-        for (int i = 0; i < RR; ++i) cv[ty + 16 * i] = col[i];
-        if (ty == 0) {
-          pv[buf] = p;
-          prow[c] = p;
-          if (zero) atomicOr(flags, kFlagSingular);
-        }
+        gj_pivot<T, BS, RR>(col, used, ty, hmask, cn, colv + (buf ^ 1) * BP, pv + (buf ^ 1), prow,
+                            flags);
       }
-    }
-    __syncthreads();
-    const int p = pv[buf];
-    const T ipiv = recip(cv[p]);
-    // the pivot row's entries in my columns, from the thread of my half-warp owning row p
-    T mine[RR], prs[RR];
-    pick_row(a, p >> 4, mine);
-    const int src = half + (p & 15);
-#pragma unroll
-    for (int j = 0; j < RR; ++j) {
-      const T v = __shfl_sync(0xffffffffu, mine[j], src);
-      prs[j] = (tx + 16 * j) == c ? ipiv : v * ipiv;
-    }
-#pragma unroll
-    for (int i = 0; i < RR; ++i) {
-      const int ri = ty + 16 * i;
-      const T f = cv[ri];
-      if (ri == p) {
-#pragma unroll
-        for (int j = 0; j < RR; ++j) a[i][j] = prs[j];
-      } else {
-#pragma unroll
-        for (int j = 0; j < RR; ++j) a[i][j] = fma(-f, prs[j], a[i][j]);
-      }
-    }
-    if (tx == cx) {
-      // column c: the elimination leaves -f_i / piv (1 / piv in the pivot row)
-      T col[RR];
 #pragma unroll
       for (int i = 0; i < RR; ++i) {
         const int ri = ty + 16 * i;
-        col[i] = ri == p ? ipiv : -cv[ri] * ipiv;
+        const T f = cv[ri];
+        if (ri == p) {
+#pragma unroll
+          for (int j = 0; j < RR; ++j) a[i][j] = prs[j];
+        } else {
+#pragma unroll
+          for (int j = 0; j < RR; ++j) a[i][j] = fma(-f, prs[j], a[i][j]);
+          // column c: the elimination leaves -f_i / piv (1 / piv in the pivot row)
+          if (tx == cx) a[i][cb] = -f * ipiv;
+        }
       }
-      put_col(a, cb, col);
     }
-    if ((p & 15) == ty) used |= 1u << (p >> 4);
   }
   __syncthreads();
   for (int c = tid; c < BS; c += kThreads) rank[prow[c]] = c;

@@ -27,6 +27,7 @@ def main(argv=None):
     p.add_argument("--mesh", type=int, nargs="+", help="cells per dimension (override)")
     p.add_argument("--order", type=int, help="polynomial degree M (override)")
     p.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
+    p.add_argument("--slices", type=int, default=0, help="digit slices of the mixed BF16 path")
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=0)
     a = p.parse_args(argv)
@@ -38,7 +39,7 @@ def main(argv=None):
     w = I.workload(a.workload, **over)
     s = R.Solver(w["dim"], w["n"], w["M"], flux=w["flux"], vel=w.get("vel", (0.0, 0.0, 0.0)),
                  cfl=w["cfl"], lo=w["lo"], hi=w["hi"], gamma=w.get("gamma", 1.4),
-                 precision=PRECISIONS[a.precision])
+                 precision=PRECISIONS[a.precision], slices=a.slices)
     s.set_state(I.initial_state(w))
     if a.warmup:
         s.profile_step(a.warmup)

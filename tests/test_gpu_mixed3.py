@@ -118,3 +118,24 @@ def test_config3_mixed_full_size_sampled(R):
                                       rng.integers(0, N, 27)]))
     assert _rel(q1[cells], OL.step_cells(q0, w, dt, cells)) < TOL_STEP
     s.close()
+
+
+def test_config3_bench_slices_full_size_sampled(R):
+    """96^3 at S = 4, the digit count the benchmark's accuracy gate selects for this workload:
+    sampled cells against the oracle.  Four balanced base-256 digits hold the state and the
+    operator to 2^-32 of their largest entries, so a step carries ~1e-10 of the state's scale
+    (bounded here by 1e-9)."""
+    w = I.workload("adv3d_n96_q2")
+    s = _mixed(R, w, slices=4)
+    q0 = I.initial_state(w)
+    s.set_state(q0)
+    dt = s.info()["dt"]
+    s.step(1)
+    q1 = s.get_state()
+    rng = np.random.default_rng(37)
+    N = 96 ** 3
+    cells = np.unique(np.concatenate([[0, N - 1], rng.integers(0, N, 30)]))
+    ref = OL.step_cells(q0, w, dt, cells)
+    assert float(np.abs(q1[cells] - ref).max() / np.abs(q0).max()) < 1e-9
+    s.close()
+
