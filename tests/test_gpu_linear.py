@@ -141,6 +141,41 @@ def test_run1d_single_launch_matches_step_kernels(R, n, M, vel):
     b.close()
 
 
+@pytest.mark.parametrize("dim,n,M,vel,prec", [
+    (2, (12, 10), 3, (1.0, 0.0), "fp64"), (2, (12, 10), 3, (0.0, -0.8), "mixed"),
+    (3, (6, 5, 4), 2, (0.5, 0.0, -0.3), "fp64"), (3, (8, 6, 4), 2, (0.0, 0.7, 0.0), "mixed")])
+def test_zero_velocity_component(R, dim, n, M, vel, prec):
+    """A direction without transport (nu_d = 0): no volume or face terms along it."""
+    w = _w(dim, n, M, vel)
+    kw = {"precision": R.RIDG_PREC_MIXED_BF16} if prec == "mixed" else {}
+    s = _solver(R, w, **kw)
+    rng = np.random.default_rng(43)
+    q = rng.standard_normal((int(np.prod(n)), (M + 1) ** dim))
+    s.set_state(q)
+    dt = s.info()["dt"]
+    s.step(2)
+    assert _rel(s.get_state(), OL.run(q, w, dt, 2)) < 2 * TOL_STEP
+    s.close()
+
+
+@pytest.mark.parametrize("dim,n,M,prec", [(1, (9,), 2, "fp64"), (2, (8, 8), 3, "fp64"),
+                                          (2, (8, 8), 3, "mixed"), (3, (4, 4, 4), 1, "fp64"),
+                                          (3, (8, 8, 4), 2, "mixed")])
+def test_zero_velocity_is_identity(R, dim, n, M, prec):
+    """a = 0: the prediction is Q^n extended in time and the correction vanishes, so steps
+    leave the state unchanged (dt falls back to cfl h)."""
+    w = _w(dim, n, M, (0.0,) * dim)
+    kw = {"precision": R.RIDG_PREC_MIXED_BF16} if prec == "mixed" else {}
+    s = _solver(R, w, **kw)
+    rng = np.random.default_rng(44)
+    q = rng.standard_normal((int(np.prod(n)), (M + 1) ** dim))
+    s.set_state(q)
+    assert s.info()["dt"] > 0
+    s.step(3)
+    assert np.abs(s.get_state() - q).max() <= 1e-15 * np.abs(q).max()
+    s.close()
+
+
 @pytest.mark.parametrize("dim,n,M,vel", [CASES[0], CASES[3], CASES[6]])
 def test_mass_conserved(R, dim, n, M, vel):
     w = _w(dim, n, M, vel)
