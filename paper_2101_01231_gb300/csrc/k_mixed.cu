@@ -73,11 +73,11 @@ __host__ __device__ inline GemmLayout gemm_layout(int S, int thS, int nout_pad) 
   l.nmma = 0;
   for (int a = 0; a < S; ++a) l.nmma += gemm_nmma_digit(S, l.P, nout_pad, a);
   l.bbytes = (uint32_t)9 * l.P * l.brows * 16;
-  const uint32_t digit_bytes = 3u * l.P * kCopy * 16;
+  const uint32_t digit_bytes = 3u * l.P * kCopy * 16;  // one digit: three x-shifted copies
   const uint32_t rest = l.bbytes + 256 + 1024;
   const uint32_t avail = rest < kSmemLimit ? kSmemLimit - rest : 0;
   int G = S;
-  while (G > 1 && 2 * ((3u * G * l.P * kCopy * 16 + 1023) & ~1023u) > avail) --G;
+  while (G > 1 && 2 * ((G * digit_bytes + 1023) & ~1023u) > avail) --G;
   l.G = G;
   l.groups = (S + G - 1) / G;
   l.copy_bytes = (uint32_t)G * l.P * kCopy * 16;      // G digits, one x-shifted copy
@@ -644,7 +644,8 @@ int mixed_make_map(const Grid& g, int nb, int slices, int nout, void* planes, vo
                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
-  if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
       q != cudaDriverEntryPointSuccess || !fn)
     return RIDG_ECUDA;
   const int thS = nb * nb, P = ((thS + 15) / 16) * 2;

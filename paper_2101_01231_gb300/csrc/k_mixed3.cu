@@ -544,7 +544,8 @@ int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_o
                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
-  if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
       q != cudaDriverEntryPointSuccess || !fn)
     return RIDG_ECUDA;
   const int thS = nb * nb * nb, P = ((thS + 15) / 16) * 2;
