@@ -195,6 +195,15 @@ int ridg_l2_error(ridg_t* h, const double* x, int on_device, double* err);
 int ridg_l2_error_noalloc(const double* q, const double* x, long long cells, int m, int dim,
                           int order, void* stream, double* err);
 
+/* Failure-detection check (no GPU fault involved): launches a one-thread kernel whose bounded
+ * mbarrier wait -- the helper every tensor-core kernel waits with -- waits on an arrival
+ * that never comes, so the wait runs out of polls and the kernel reports it and returns.
+ * Returns RIDG_ETIMEOUT when that happened (the expected outcome), RIDG_OK if the wait
+ * completed (it cannot), RIDG_ENOMEM / RIDG_ECUDA on allocation / launch errors.  The
+ * device context stays usable.  seconds (nullable) receives the wait's device time.  Work
+ * is issued on `stream` (NULL = legacy default stream) and the call waits for it.          */
+int ridg_check_bounded_wait(void* stream, double* seconds);
+
 /* ----- tracing ---------------------------------------------------------------------------- */
 
 typedef struct {

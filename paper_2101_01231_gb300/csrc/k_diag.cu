@@ -4,6 +4,7 @@
 // partials in block order, so results are run-to-run deterministic.
 #include <cuda_runtime.h>
 
+#include "k_tcgen05.cuh"
 #include "ridg_internal.h"
 
 namespace ridg {
@@ -81,7 +82,25 @@ __global__ void finite_kernel(const double* __restrict__ q, long long count, int
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+// A bounded mbarrier wait (the helper every tensor-core kernel uses) on an arrival that
+// never comes: the wait must give up by itself and report it (status 1), the way the
+// kernels stop on a timeout.  status 0 would mean the wait completed, which cannot happen.
+__global__ void bounded_wait_probe_kernel(int* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    status[0] = mbar_wait(b, 0) ? 0 : 1;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_bounded_wait_probe(int* status, cudaStream_t s) {
+  bounded_wait_probe_kernel<<<1, 32, 0, s>>>(status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mass_partials(const double* Q, long long ncell, int m, int thS, double* out,
                                  int nblocks, cudaStream_t s) {
@@ -101,3 +120,29 @@ cudaError_t launch_finite_check(const double* q, long long count, int* flag, cud
 }
 
 }  // namespace ridg
+
+extern "C" int ridg_check_bounded_wait(void* stream, double* seconds) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return RIDG_ENOMEM;
+  int status = -1;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int rc = RIDG_ECUDA;
+  if (cudaMemsetAsync(d, 0xFF, sizeof(int), s) == cudaSuccess &&
+      cudaEventCreate(&ev[0]) == cudaSuccess && cudaEventCreate(&ev[1]) == cudaSuccess &&
+      cudaEventRecord(ev[0], s) == cudaSuccess &&
+      ridg::launch_bounded_wait_probe(d, s) == cudaSuccess &&
+      cudaEventRecord(ev[1], s) == cudaSuccess &&
+      cudaMemcpyAsync(&status, d, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+      cudaStreamSynchronize(s) == cudaSuccess) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    if (seconds) *seconds = ms * 1e-3;
+    rc = status == 1 ? RIDG_ETIMEOUT : (status == 0 ? RIDG_OK : RIDG_ECUDA);
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(d);
+  return rc;
+}
+

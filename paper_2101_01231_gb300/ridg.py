@@ -67,6 +67,7 @@ EXPORTS = {
     "ridg_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ridg_profile_t)]),
     "ridg_mass": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "ridg_l2_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "ridg_check_bounded_wait": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "ridg_l2_error_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_int,
                                         C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
     "ridg_batch_create": (C.c_int, [C.c_int, C.POINTER(ridg_mesh), C.POINTER(C.c_int),
@@ -246,6 +247,14 @@ def ridg_l2_error(h, x):
     e = C.c_double()
     _check(_lib.ridg_l2_error(h, p, dev, C.byref(e)), h)
     return e.value
+
+
+def ridg_check_bounded_wait(stream=None):
+    """Run the bounded-wait check; returns (status, seconds): RIDG_ETIMEOUT is the expected
+    status (the wait gave up and reported it)."""
+    sec = C.c_double(0.0)
+    st = _lib.ridg_check_bounded_wait(stream, C.byref(sec))
+    return st, sec.value
 
 
 def ridg_l2_error_noalloc(q, x, cells, m, dim, order, stream=None):

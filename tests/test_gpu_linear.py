@@ -307,3 +307,22 @@ def test_batched_instances_match_separate_runs(R):
         dt = ridg_info(h)["dt"]
         assert _rel(out, OL.run(qs[i], w, dt, 3)) < TOL_STEP
     ridg_batch_destroy(b)
+
+
+def test_bounded_wait_times_out_and_context_survives(R):
+    """Failure detection without a GPU fault: a kernel's bounded mbarrier wait on an arrival
+    that never comes gives up by itself and reports RIDG_ETIMEOUT; the context stays usable
+    (a step afterwards matches the oracle)."""
+    st, sec = R.ridg_check_bounded_wait()
+    assert st == R.RIDG_ETIMEOUT
+    assert 0.0 < sec < 5.0   # ~1 s: 2^18 polls of a suspending try_wait
+    w = _w(2, (12, 10), 3, (1.0, 0.5))
+    s = _solver(R, w)
+    rng = np.random.default_rng(45)
+    q = rng.standard_normal((120, 16))
+    s.set_state(q)
+    dt = s.info()["dt"]
+    s.step(1)
+    assert _rel(s.get_state(), OL.step(q, w, dt)) < TOL_STEP
+    s.close()
+
