@@ -61,6 +61,22 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device="cpu"):
+    """The largest of every rank's x (ws > 1: an all-reduce MAX over the process group)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(items, rank, ws):
+    """One rank's round-robin share of independent units (the ensemble's instances)."""
+    return list(items)[rank::ws]
+
+
 def _golden():
     p = os.path.join(ROOT, "tests", "golden", "oracle_accuracy.json")
     return json.load(open(p)) if os.path.exists(p) else {}
@@ -235,7 +251,7 @@ def adv1d_section(R, I, reps):
                            "sample": f"the whole run ({nt} steps)"}}
 
 
-def ensemble_section(R, I, steps, cpu_cells):
+def ensemble_section(R, I, steps, cpu_cells, rank=0, ws=1):
     """The batched Burgers ensemble (64 instances, N ~ U{64..512}, Q1-Q4, seeded Fourier data)
     advanced by ridg_batch_step: one captured graph per step holding one persistent Newton
     launch per degree over all the instances of that degree, then the corrections; TF32
@@ -245,7 +261,8 @@ def ensemble_section(R, I, steps, cpu_cells):
     import torch
     from oracle import linear as OL
     from oracle import nonlinear as ONL
-    ens = I.burgers_ensemble()
+    ens_all = I.burgers_ensemble()
+    ens = shard(ens_all, rank, ws)  # N GPUs: the instances round-robin over the ranks
     stream = torch.cuda.Stream()
     opt = R.make_options(precision=R.RIDG_PREC_MIXED_TF32, stream=stream.cuda_stream)
 
@@ -273,14 +290,15 @@ def ensemble_section(R, I, steps, cpu_cells):
         times.append(a0.elapsed_time(a1))
     infos = [R.ridg_info(R.ridg_batch_instance(b, i)) for i in range(len(ens))]
     R.ridg_batch_destroy(b)
-    ms = float(np.mean(times))
-    dof = sum(int(np.prod(w["n"])) * (w["M"] + 1) ** 2 for w in ens)
+    ms = max_over_ranks(float(np.mean(times)), ws, "cuda")
+    dof = sum(int(np.prod(w["n"])) * (w["M"] + 1) ** 2 for w in ens_all)
     # algorithmic work of the block eliminations: 118 b^3 flop per factorisation, b = theta_T
     flops = sum(118.0 * (w["M"] + 1) ** 9 * inf["newton_iters_total"] for w, inf in zip(ens, infos))
-    ach = flops / (ms * 1e-3) / 1e12
-    out = {"workload": "burgers_ensemble_64", "instances": len(ens),
-           "cells": sum(int(np.prod(w["n"])) for w in ens),
-           "cells_per_degree": {str(m): sum(int(np.prod(w["n"])) for w in ens if w["M"] == m)
+    ach = flops / (ms * 1e-3) / 1e12  # per GPU: this rank's instances over the step time
+    out = {"workload": "burgers_ensemble_64", "instances": len(ens_all),
+           "scaling": "strong: the 64 instances round-robin over the ranks",
+           "cells": sum(int(np.prod(w["n"])) for w in ens_all),
+           "cells_per_degree": {str(m): sum(int(np.prod(w["n"])) for w in ens_all if w["M"] == m)
                                 for m in (1, 2, 3, 4)},
            "precision": "mixed_tf32", "steps": steps, "ms_per_step": ms,
            "value": dof / (ms * 1e-3), "unit": "element-DOF updates/s",
@@ -293,16 +311,18 @@ def ensemble_section(R, I, steps, cpu_cells):
                         "peak_source": "nominal: FMA pipes x 2 flop x 2.07 GHz"}}
     # the oracle: per-cell Newton prediction time per degree (a 32 x 32 copy of the first
     # instance of each degree), extrapolated to the ensemble's cells
+    if rank != 0:
+        return out
     per = {}
     for m in (1, 2, 3, 4):
-        w = dict(next(x for x in ens if x["M"] == m), n=(32, 32))
+        w = dict(next(x for x in ens_all if x["M"] == m), n=(32, 32))
         q = I.initial_state(w)
         dt, _ = OL.time_step(w, ONL.max_speed(q, w))
         k = cpu_cells if m < 3 else 2
         t0 = time.perf_counter()
         ONL.newton_predict(q, w, dt, cells=np.arange(k))
         per[m] = (time.perf_counter() - t0) / k
-    t_or = sum(int(np.prod(w["n"])) * per[w["M"]] for w in ens)
+    t_or = sum(int(np.prod(w["n"])) * per[w["M"]] for w in ens_all)
     out["cpu_oracle"] = {"kind": "oracle", "cores": os.cpu_count(),
                          "seconds_per_cell": {str(m): v for m, v in per.items()},
                          "value": dof / t_or, "unit": "element-DOF updates/s",
@@ -583,10 +603,7 @@ def run_ours(args):
                 break
     s, ms_step, ms_pred, ms_corr, ck = timed(prec_name, args.steps, args.warmup, clocks)
     slices_used = s.info()["slices"]
-    t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, ws, "cuda")
     value = ws * dof / (ms_step * 1e-3)
 
     # end to end through the C ABI with host buffers: H2D state, one step, D2H state
@@ -602,7 +619,7 @@ def run_ours(args):
         s.set_state(qh)
         s.step(1)
         s.get_state(qh)
-    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / n_e2e, ws, "cuda")
     s.close()
 
     # the FP64 form beside the headline precision (same timing rules, fewer steps)
@@ -671,8 +688,8 @@ def run_ours(args):
         line["newton"] = newton_section(R, I, args.newton_steps, 8 if args.no_cpu_baseline else 16)
     if args.adv1d_reps > 0:
         line["adv1d"] = adv1d_section(R, I, args.adv1d_reps)
-    if args.ensemble_steps > 0:
-        line["ensemble"] = ensemble_section(R, I, args.ensemble_steps, 4)
+    if args.ensemble_steps > 0 and ws <= 64:
+        line["ensemble"] = ensemble_section(R, I, args.ensemble_steps, 4, rank, ws)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
