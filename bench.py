@@ -45,6 +45,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--newton-steps", type=int, default=1,
                    help="timed steps of the Newton path (0: skip it)")
+    p.add_argument("--paper1d", type=int, default=1,
+                   help="the paper's 1D table (degrees 3-11) on the GPU (0: skip)")
     p.add_argument("--adv1d-reps", type=int, default=20,
                    help="whole 1D runs to T = 1 timed (0: skip the 1D section)")
     p.add_argument("--ensemble-steps", type=int, default=1,
@@ -329,6 +331,72 @@ def ensemble_section(R, I, steps, cpu_cells, rank=0, ws=1):
                          "sample": f"Newton predictions of {cpu_cells} cells (Q1, Q2) / 2 cells "
                                    "(Q3, Q4) per degree, extrapolated to the ensemble (numpy)"}
     return out
+
+
+def paper1d_section(R, I):
+    """The paper's own 1D study (table table:1D): RIDG at nu = 0.9 on the C-infinity bump of
+    eq. adv1d, degrees 3 to 11 on the table's meshes, run to t = 1 (the paper states no final
+    time) on the GPU -- each run one single-CTA launch -- with its L2 error, observed order
+    (eq. Mratio), run time and quality = -log10(error x runtime) (eq. Quality); beside it the
+    oracle's error and host run time, and the paper's printed CPU figures."""
+    import torch
+    from oracle import error as OE
+    from oracle import linear as OL
+    ref = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_1d_table.json")))
+
+    def bump(x):
+        r2 = (x - 0.5) ** 2
+        out = np.zeros_like(x)
+        m = r2 < 1.0 / 9.0
+        out[m] = np.exp(1.0 / (r2[m] - 1.0 / 9.0))
+        return out
+
+    rows = {}
+    for M in (3, 5, 7, 9, 11):
+        meshes = ref["rows"][str(M)]["mesh"]
+        r = {"mesh": meshes, "l2_error": [], "order": [None], "gpu_run_s": [], "quality": [],
+             "l2_error_oracle": [], "oracle_run_s": [],
+             "paper_l2_error": ref["rows"][str(M)]["error"],
+             "paper_runtime_s": ref["runtime_s"][str(M)], "paper_quality": ref["quality"][str(M)]}
+        for N in meshes:
+            w = dict(flux="advection", dim=1, n=(N,), M=M, vel=(1.0,), lo=(0.0,), hi=(1.0,),
+                     cfl=0.9)
+            q0 = I.project_1d(bump, N, 0.0, 1.0, M + 1, nq=40)
+            X = I.project_1d(bump, N, 0.0, 1.0, M + 2, nq=40)
+            s = R.Solver(1, (N,), M, vel=(1.0,), cfl=0.9)
+            s.set_state(q0)
+            nt = s.set_final_time(T_FINAL)
+            s.step(nt)                       # warm-up (captures the run's graph)
+            s.sync()
+            times = []
+            for _ in range(5):
+                s.set_state(q0)
+                s.set_final_time(T_FINAL)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(s.stream)
+                s.step(nt)
+                b.record(s.stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b) * 1e-3)
+            e = s.l2_error(X)
+            dt = s.info()["dt"]
+            s.close()
+            t_gpu = float(np.median(times))
+            t0 = time.perf_counter()
+            qo = OL.run(q0, w, dt, nt)
+            t_or = time.perf_counter() - t0
+            r["l2_error"].append(e)
+            r["gpu_run_s"].append(t_gpu)
+            r["quality"].append(-np.log10(e * t_gpu))
+            r["l2_error_oracle"].append(OE.l2_relative_error(qo, X, M, 1))
+            r["oracle_run_s"].append(t_or)
+        for k in range(1, len(meshes)):
+            r["order"].append(OE.observed_order(r["l2_error"][k - 1], r["l2_error"][k],
+                                                1 / meshes[k - 1], 1 / meshes[k]))
+        rows[str(M)] = r
+    return {"workload": "adv1d bump (eq. adv1d), nu = 0.9, t = 1", "precision": "fp64",
+            "rows": rows}
 
 
 # ---------------------------------------------------------------------------------------
@@ -688,6 +756,8 @@ def run_ours(args):
         line["newton"] = newton_section(R, I, args.newton_steps, 8 if args.no_cpu_baseline else 16)
     if args.adv1d_reps > 0:
         line["adv1d"] = adv1d_section(R, I, args.adv1d_reps)
+    if args.paper1d > 0:
+        line["paper1d"] = paper1d_section(R, I)
     if args.ensemble_steps > 0 and ws <= 64:
         line["ensemble"] = ensemble_section(R, I, args.ensemble_steps, 4, rank, ws)
     if rank == 0:

@@ -310,6 +310,10 @@ cudaError_t launch_predict_fp64(const Grid& g, int nb, const double* Q, const do
       case 6: return predict_dispatch_ch<1, 6>(g, Q, P, nout, W, wstride, s);
       case 7: return predict_dispatch_ch<1, 7>(g, Q, P, nout, W, wstride, s);
       case 8: return predict_dispatch_ch<1, 8>(g, Q, P, nout, W, wstride, s);
+      case 9: return predict_dispatch_ch<1, 9>(g, Q, P, nout, W, wstride, s);
+      case 10: return predict_dispatch_ch<1, 10>(g, Q, P, nout, W, wstride, s);
+      case 11: return predict_dispatch_ch<1, 11>(g, Q, P, nout, W, wstride, s);
+      case 12: return predict_dispatch_ch<1, 12>(g, Q, P, nout, W, wstride, s);
       default: break;
     }
   } else if (g.dim == 2) {
@@ -325,7 +329,7 @@ cudaError_t launch_predict_fp64(const Grid& g, int nb, const double* Q, const do
 }
 
 bool run1d_fits(const Grid& g, int nb) {
-  return g.dim == 1 && nb >= 1 && nb <= 8 && g.ncell <= kRun1dMaxCells &&
+  return g.dim == 1 && nb >= 1 && nb <= kMaxNB && g.ncell <= kRun1dMaxCells &&
          (size_t)(3 * nb * nb + 2 * g.ncell * nb) * sizeof(double) <= 96 * 1024;
 }
 
@@ -341,6 +345,10 @@ cudaError_t launch_run1d_fp64(const Grid& g, int nb, double* Q, const double* P,
     case 6: return run1d_dispatch<6>(g, Q, P, nsteps, cp, s);
     case 7: return run1d_dispatch<7>(g, Q, P, nsteps, cp, s);
     case 8: return run1d_dispatch<8>(g, Q, P, nsteps, cp, s);
+    case 9: return run1d_dispatch<9>(g, Q, P, nsteps, cp, s);
+    case 10: return run1d_dispatch<10>(g, Q, P, nsteps, cp, s);
+    case 11: return run1d_dispatch<11>(g, Q, P, nsteps, cp, s);
+    case 12: return run1d_dispatch<12>(g, Q, P, nsteps, cp, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -354,6 +362,10 @@ cudaError_t launch_correct_linear(const Grid& g, int nb, double* Q, const double
       case 6: return correct_dispatch<1, 6>(g, Q, Wbar, wstride, cp, s);
       case 7: return correct_dispatch<1, 7>(g, Q, Wbar, wstride, cp, s);
       case 8: return correct_dispatch<1, 8>(g, Q, Wbar, wstride, cp, s);
+      case 9: return correct_dispatch<1, 9>(g, Q, Wbar, wstride, cp, s);
+      case 10: return correct_dispatch<1, 10>(g, Q, Wbar, wstride, cp, s);
+      case 11: return correct_dispatch<1, 11>(g, Q, Wbar, wstride, cp, s);
+      case 12: return correct_dispatch<1, 12>(g, Q, Wbar, wstride, cp, s);
       default: break;
     }
   } else if (g.dim == 2) {

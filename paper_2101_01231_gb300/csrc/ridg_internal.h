@@ -11,7 +11,7 @@
 
 namespace ridg {
 
-constexpr int kMaxNB = 8;  // largest supported M + 1
+constexpr int kMaxNB = 12;  // largest supported M + 1 (1D; 2D up to 5, 3D up to 4)
 
 // Per-launch constants of the correction (1D tables and CFL numbers), passed by value.
 struct CorrParams {

@@ -326,3 +326,72 @@ def test_bounded_wait_times_out_and_context_survives(R):
     assert _rel(s.get_state(), OL.step(q, w, dt)) < TOL_STEP
     s.close()
 
+
+def _region_rounding(M, nu):
+    """Rounding bound of one FP64 step at degree M: eps times the condition number of the
+    region matrix A (eq. pred_full_system; 3.2e8 at M = 11, nu = 0.9), whose solution two
+    FP64 implementations (the oracle's LU, the library's operator) may round differently."""
+    A, _ = OL.region_system(1, M, np.array([nu]))
+    return max(TOL_STEP, np.linalg.cond(A) * np.finfo(float).eps)
+
+
+@pytest.mark.parametrize("n,M", [((10,), 8), ((7,), 9), ((5,), 11)])
+def test_high_degree_1d_matches_oracle(R, n, M):
+    """1D up to degree 11 (the paper's highest, table table:1D): steps against the oracle,
+    within the FP64 rounding bound of the region solve."""
+    w = _w(1, n, M, (1.0,), cfl=0.9)
+    s = _solver(R, w)
+    rng = np.random.default_rng(46)
+    q = rng.standard_normal((n[0], M + 1))
+    s.set_state(q)
+    dt = s.info()["dt"]
+    s.step(3)
+    assert _rel(s.get_state(), OL.run(q, w, dt, 3)) < 3 * _region_rounding(M, 0.9)
+    s.close()
+    with pytest.raises(R.RidgError):
+        R.ridg_create(R.make_mesh(1, (8,)), 12, R.make_flux("advection", (1.0,)), 0.9)
+
+
+def _bump(x):
+    r2 = (x - 0.5) ** 2
+    out = np.zeros_like(x)
+    m = r2 < 1.0 / 9.0
+    out[m] = np.exp(1.0 / (r2[m] - 1.0 / 9.0))
+    return out
+
+
+@pytest.mark.parametrize("M", [7, 9, 11])
+def test_paper_1d_table_high_degree(R, M):
+    """Table table:1D, RIDG at nu = 0.9 on the bump of eq. adv1d, run to t = 1 on the GPU:
+    the final states equal the oracle's within the FP64 rounding of the region solves, and
+    the observed orders (eq. Mratio) match the paper's."""
+    import json
+    import os
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_1d_table.json")))
+    row = ref["rows"][str(M)]
+    errs = []
+    for N in row["mesh"]:
+        w = _w(1, (N,), M, (1.0,), cfl=0.9)
+        q0 = I.project_1d(_bump, N, 0.0, 1.0, M + 1, nq=40)
+        X = I.project_1d(_bump, N, 0.0, 1.0, M + 2, nq=40)
+        s = _solver(R, w)
+        s.set_state(q0)
+        nt = s.set_final_time(1.0)
+        dt = s.info()["dt"]
+        s.step(nt)
+        e = s.l2_error(X)
+        qg = s.get_state()
+        s.close()
+        assert _rel(qg, OL.run(q0, w, dt, nt)) < nt * _region_rounding(M, 0.9)
+        errs.append(e)
+    # orders from the second refinement on (the coarsest pair is pre-asymptotic, and the
+    # paper's final time is not stated), where both errors are above rounding
+    checked = 0
+    for k in range(2, len(errs)):
+        if errs[k] < 1e-12:
+            continue
+        order = oerr.observed_order(errs[k - 1], errs[k], 1 / row["mesh"][k - 1], 1 / row["mesh"][k])
+        assert abs(order - row["order"][k]) < 1.0, (M, row["mesh"][k], order)
+        checked += 1
+    assert checked >= 1
+
