@@ -54,6 +54,7 @@ Grid grid_of(const ridg_t* h) {
   g.n[1] = h->n[1];
   g.n[2] = h->n[2];
   g.ncell = h->ncell;
+  g.box = h->box;
   return g;
 }
 
@@ -109,7 +110,7 @@ CorrParams corr_params(const ridg_t* h) {
 int rebuild_linear(ridg_t* h) {
   double nu[3] = {0, 0, 0};
   for (int d = 0; d < h->dim; ++d) nu[d] = h->flux.vel[d] * h->dt / h->h[d];
-  if (!ridg::linear_operator(h->dim, h->M, nu, h->P_host))
+  if (!ridg::linear_operator(h->dim, h->M, nu, h->box, h->P_host))
     return set_err(h, RIDG_EINVAL, "region system is singular for this dt");
   RIDG_CUDA(h, cudaMemcpyAsync(h->P, h->P_host.data(), sizeof(double) * h->P_host.size(),
                                cudaMemcpyHostToDevice, h->stream));
@@ -120,8 +121,8 @@ int rebuild_linear(ridg_t* h) {
     std::vector<unsigned short> digits;
     std::vector<double> rscale;
     std::vector<float> rowmul;
-    int rc = ridg::mixed_build(3, h->nb, Pbar, h->thS, h->opt.slices, digits, rscale, rowmul,
-                               h->mixed);
+    int rc = ridg::mixed_build(3, h->nb, Pbar, h->thS, h->opt.slices, h->box, digits, rscale,
+                               rowmul, h->mixed);
     if (rc != RIDG_OK) return set_err(h, rc, "3D mixed operator build failed");
     if (!h->mixed.b_slices) {
       h->mixed.b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
@@ -185,8 +186,8 @@ int rebuild_linear(ridg_t* h) {
       std::vector<unsigned short> digits;
       std::vector<double> rscale;
       std::vector<float> rowmul;
-      int rc = ridg::mixed_build(h->dim, h->nb, *p.g, p.nout, h->opt.slices, digits, rscale,
-                                 rowmul, *p.op);
+      int rc = ridg::mixed_build(h->dim, h->nb, *p.g, p.nout, h->opt.slices, h->box, digits,
+                                 rscale, rowmul, *p.op);
       if (rc != RIDG_OK) return set_err(h, rc, "mixed operator build failed");
       if (!p.op->b_slices) {
         p.op->b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
@@ -435,9 +436,10 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
   h->thT = h->thS * h->nb;
   h->nR = 1;
   for (int d = 0; d < h->dim; ++d) h->nR *= 3;
-  h->K = h->nR * h->thS;
   h->m = m;
   h->flux = *flux;
+  if (is_linear(h)) h->box = ridg::upwind_box(h->dim, h->flux.vel);
+  h->K = h->box.n * h->thS;
   h->cfl = cfl;
   if (h->opt.precision == RIDG_PREC_MIXED_BF16 &&
       (h->dim == 3 ? !ridg::mixed3_supported(h->nb, h->opt.slices)

@@ -2,8 +2,10 @@
 //
 // Prediction (Sec. 2.2): for a linear flux on a uniform periodic mesh the region system
 // of eq. pred_full_system is the same for every cell, so the kept centre coefficients
-// are W_i = P X_i with X_i the 3^d theta_S region coefficients of cell i (gathered with
-// periodic wrap) and P the centre rows of the region solution operator.
+// are W_i = P X_i with X_i the theta_S coefficients of the region cells upstream of cell i
+// (the upwind box, 2^d of the 3^d cells for a velocity with no zero component; the others
+// have zero columns) gathered with periodic wrap, and P the centre rows of the region
+// solution operator.
 //
 // Correction (Sec. 2.3): with W-bar the time mean of W (all a linear flux needs, since
 // int psi_g dtau = 2 delta_g0),
@@ -54,10 +56,10 @@ template <int DIM, int NB, int CH>
 __global__ void __launch_bounds__(128) predict_fp64_kernel(const double* __restrict__ Q,
                                                            const double* __restrict__ P, int nout,
                                                            double* __restrict__ W, int wstride,
-                                                           int nx, int ny, int nz, long long ncell) {
+                                                           int nx, int ny, int nz, long long ncell,
+                                                           RegionBox box) {
   constexpr int THS = ipow_c(NB, DIM);
-  constexpr int NR = ipow_c(3, DIM);
-  constexpr int K = NR * THS;
+  const int K = box.n * THS;
   extern __shared__ double sP[];  // CH x K
   const int c0 = blockIdx.y * CH;
   for (int i = threadIdx.x; i < CH * K; i += blockDim.x) {
@@ -72,8 +74,10 @@ __global__ void __launch_bounds__(128) predict_fp64_kernel(const double* __restr
 #pragma unroll
   for (int j = 0; j < CH; ++j) acc[j] = 0.0;
 #pragma unroll 1
-  for (int r = 0; r < NR; ++r) {
-    const int ox = r % 3 - 1, oy = (r / 3) % 3 - 1, oz = r / 9 - 1;
+  for (int r = 0; r < box.n; ++r) {
+    const int ox = box.lo[0] + r % box.cnt[0];
+    const int oy = box.lo[1] + (r / box.cnt[0]) % box.cnt[1];
+    const int oz = box.lo[2] + r / (box.cnt[0] * box.cnt[1]);
     const double* q = Q + neighbour<DIM>(c, ox, oy, oz, nx, ny, nz) * THS;
     const double* p = sP + r * THS;
 #pragma unroll
@@ -193,8 +197,8 @@ __global__ void __launch_bounds__(128) correct_linear_kernel(double* __restrict_
 template <int NB>
 __global__ void __launch_bounds__(256) run1d_fp64_kernel(double* __restrict__ Q,
                                                          const double* __restrict__ P, int n,
-                                                         int nsteps, CorrParams cp) {
-  constexpr int K = 3 * NB;
+                                                         int nsteps, CorrParams cp, int lo, int nr) {
+  const int K = nr * NB;     // the upwind cells lo .. lo + nr - 1 of the region
   extern __shared__ double sm1[];
   double* sP = sm1;          // NB x K (the time-mean rows)
   double* sQ = sP + NB * K;  // n x NB
@@ -206,9 +210,8 @@ __global__ void __launch_bounds__(256) run1d_fp64_kernel(double* __restrict__ Q,
     for (int i = threadIdx.x; i < n * NB; i += blockDim.x) {
       const int c = i / NB, k = i % NB;
       double acc = 0.0;
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const double* q = sQ + wrap(c + r - 1, n) * NB;
+      for (int r = 0; r < nr; ++r) {
+        const double* q = sQ + wrap(c + lo + r, n) * NB;
         const double* p = sP + k * K + r * NB;
 #pragma unroll
         for (int s2 = 0; s2 < NB; ++s2) acc = fma(p[s2], q[s2], acc);
@@ -250,13 +253,13 @@ __global__ void __launch_bounds__(256) run1d_fp64_kernel(double* __restrict__ Q,
 template <int NB>
 cudaError_t run1d_dispatch(const Grid& g, double* Q, const double* P, int nsteps,
                            const CorrParams& cp, cudaStream_t s) {
-  const size_t smem = (size_t)(NB * 3 * NB + 2 * g.ncell * NB) * sizeof(double);
+  const size_t smem = (size_t)(NB * g.box.n * NB + 2 * g.ncell * NB) * sizeof(double);
   auto kern = run1d_fp64_kernel<NB>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<1, 256, smem, s>>>(Q, P, (int)g.ncell, nsteps, cp);
+  kern<<<1, 256, smem, s>>>(Q, P, (int)g.ncell, nsteps, cp, g.box.lo[0], g.box.cnt[0]);
   return cudaGetLastError();
 }
 
@@ -264,10 +267,11 @@ template <int DIM, int NB>
 cudaError_t predict_dispatch_ch(const Grid& g, const double* Q, const double* P, int nout,
                                 double* W, int wstride, cudaStream_t s) {
   constexpr int THS = ipow_c(NB, DIM);
-  constexpr int K = ipow_c(3, DIM) * THS;
+  constexpr int KMAX = ipow_c(2, DIM) * THS;  // the largest upwind box: 2^d cells
   // rows per thread: as many as fit 48 KB of shared memory, at most 16
-  constexpr int CH = (16 * K * 8 <= 48 * 1024) ? 16 : ((8 * K * 8 <= 48 * 1024) ? 8 : 4);
-  static_assert(CH * K * 8 <= 48 * 1024 || CH == 4, "operator chunk too large");
+  constexpr int CH = (16 * KMAX * 8 <= 48 * 1024) ? 16 : ((8 * KMAX * 8 <= 48 * 1024) ? 8 : 4);
+  if (g.box.n < 1 || g.box.n > ipow_c(2, DIM)) return cudaErrorInvalidValue;
+  const int K = g.box.n * THS;
   const int threads = 128;
   dim3 grid((unsigned)((g.ncell + threads - 1) / threads), (unsigned)((nout + CH - 1) / CH));
   size_t smem = (size_t)CH * K * sizeof(double);
@@ -276,7 +280,7 @@ cudaError_t predict_dispatch_ch(const Grid& g, const double* Q, const double* P,
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid, threads, smem, s>>>(Q, P, nout, W, wstride, g.n[0], g.n[1], g.n[2], g.ncell);
+  kern<<<grid, threads, smem, s>>>(Q, P, nout, W, wstride, g.n[0], g.n[1], g.n[2], g.ncell, g.box);
   return cudaGetLastError();
 }
 
@@ -330,7 +334,8 @@ cudaError_t launch_predict_fp64(const Grid& g, int nb, const double* Q, const do
 
 bool run1d_fits(const Grid& g, int nb) {
   return g.dim == 1 && nb >= 1 && nb <= kMaxNB && g.ncell <= kRun1dMaxCells &&
-         (size_t)(3 * nb * nb + 2 * g.ncell * nb) * sizeof(double) <= 96 * 1024;
+         g.box.n >= 1 && g.box.n <= 2 &&
+         (size_t)(g.box.n * nb * nb + 2 * g.ncell * nb) * sizeof(double) <= 96 * 1024;
 }
 
 cudaError_t launch_run1d_fp64(const Grid& g, int nb, double* Q, const double* P, int nsteps,

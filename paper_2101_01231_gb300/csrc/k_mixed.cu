@@ -2,7 +2,9 @@
 // (tcgen05 + TMA, sm_103a).
 //
 // What is computed.  Y[e][c] = sum_k G[c][k] X_e[k] for every cell e, where X_e holds the
-// theta_S coefficients of the 3 x 3 vertex neighbours of e (Sec. 2.2, eq. region) and G is
+// theta_S coefficients of the region cells upstream of e (Sec. 2.2, eq. region: the upwind
+// box, 2 x 2 of the 3 x 3 vertex neighbours for a velocity with no zero component; the
+// other cells' operator columns are exactly zero) and G is
 // the centre-row region operator (the prediction of eq. pred_full_system for a linear
 // flux), optionally composed with the linear correction functionals of Sec. 2.3 (volume
 // term and upwind face traces) -- the "fused" step outputs [V | u_x | u_y].
@@ -18,16 +20,16 @@
 //
 // Data path (one step = two kernels):
 //   mixed_gemm_kernel      persistent, warp-specialised pipeline per CTA:
-//     warp 0 / lane 0: TMA.  For every digit of an 8 x 16 cell tile the operand is
-//       three 3D TMA boxes of the ghost-padded digit planes [digit, 8-mode group][y + 2]
-//       [(x + 2) x 8 modes], 8 x 18 cells each, at x offsets 0, 1, 2: they land in shared
+//     warp 0 / lane 0: TMA.  For every digit of an 8 x 16 cell tile the operand is one
+//       3D TMA box of the ghost-padded digit planes [digit, 8-mode group][y + 2]
+//       [(x + 2) x 8 modes], 8 x 18 cells, per x-offset of the box: they land in shared
 //       memory exactly in the K-major core-matrix layout, so the A operand of the MMA for
-//       region offset (ox, oy) is copy ox with its descriptor start moved by oy halo rows
-//       (128 B, keeping every core matrix 128-byte aligned) -- an implicit im2col without
-//       any copy by the SM.  Digits stream through a ring of slots, so the TMA runs a tile
+//       region offset (ox, oy) is copy ox with its descriptor start moved by oy + 1 halo
+//       rows (128 B, keeping every core matrix 128-byte aligned) -- an implicit im2col
+//       without any copy by the SM.  Digits stream through a ring of slots, so the TMA runs a tile
 //       ahead of the tensor core.
 //     warp 1 / lane 0: MMA.  Descriptors are formed in registers (constant offsets).
-//       S x 9 x (theta_pad / 16) tcgen05.mma (M = 128); B = operator digits stacked so the
+//       S x (box cells) x (theta_pad / 16) tcgen05.mma (M = 128); B = operator digits stacked so the
 //       pair (a, c') lands in TMEM block a + c'.  One commit per tile.
 //     warps 2..9: epilogue (thread <-> TMEM lane <-> cell, two warps per lane quadrant);
 //       TMEM is double-buffered.
@@ -57,23 +59,24 @@ struct GemmLayout {
   uint32_t copy_bytes, slot_bytes, b_off, bbytes, bar_off, bytes;
 };
 
-// MMAs of digit a: 9 region offsets x k-steps x operator-digit chunks (N <= 256)
-__host__ __device__ inline int gemm_nmma_digit(int S, int P, int nout_pad, int a) {
+// MMAs of digit a: nreg region offsets x k-steps x operator-digit chunks (N <= 256)
+__host__ __device__ inline int gemm_nmma_digit(int S, int P, int nout_pad, int a, int nreg) {
   const int cmax = 256 / nout_pad;
-  return 9 * (P / 2) * ((S - a + cmax - 1) / cmax);
+  return nreg * (P / 2) * ((S - a + cmax - 1) / cmax);
 }
 
-// Shared memory: a ring of slots, each holding G digits of one tile (three x-shifted copies
-// of the 8 x 18 halo box per digit), then the operator digits, then the barriers.  G is
-// the largest group of digits for which two slots fit.
-__host__ __device__ inline GemmLayout gemm_layout(int S, int thS, int nout_pad) {
+// Shared memory: a ring of slots, each holding G digits of one tile (ncx x-shifted copies
+// of the 8 x 18 halo box per digit, one per x-offset of the upwind box), then the operator
+// digits of the box's nreg cells, then the barriers.  G is the largest group of digits for
+// which two slots fit.
+__host__ __device__ inline GemmLayout gemm_layout(int S, int thS, int nout_pad, int ncx, int nreg) {
   GemmLayout l;
   l.P = ((thS + 15) / 16) * 2;  // 8-mode groups after padding theta_S to a multiple of 16
   l.brows = S * nout_pad;
   l.nmma = 0;
-  for (int a = 0; a < S; ++a) l.nmma += gemm_nmma_digit(S, l.P, nout_pad, a);
-  l.bbytes = (uint32_t)9 * l.P * l.brows * 16;
-  const uint32_t digit_bytes = 3u * l.P * kCopy * 16;  // one digit: three x-shifted copies
+  for (int a = 0; a < S; ++a) l.nmma += gemm_nmma_digit(S, l.P, nout_pad, a, nreg);
+  l.bbytes = (uint32_t)nreg * l.P * l.brows * 16;
+  const uint32_t digit_bytes = (uint32_t)ncx * l.P * kCopy * 16;  // one digit: ncx copies
   const uint32_t rest = l.bbytes + 256 + 1024;
   const uint32_t avail = rest < kSmemLimit ? kSmemLimit - rest : 0;
   int G = S;
@@ -81,7 +84,7 @@ __host__ __device__ inline GemmLayout gemm_layout(int S, int thS, int nout_pad) 
   l.G = G;
   l.groups = (S + G - 1) / G;
   l.copy_bytes = (uint32_t)G * l.P * kCopy * 16;      // G digits, one x-shifted copy
-  l.slot_bytes = ((3 * l.copy_bytes) + 1023) & ~1023u;
+  l.slot_bytes = ((ncx * l.copy_bytes) + 1023) & ~1023u;
   int slots = (int)(avail / l.slot_bytes);
   l.slots = slots > kMaxSlots ? kMaxSlots : slots;
   l.b_off = (uint32_t)l.slots * l.slot_bytes;
@@ -93,16 +96,21 @@ __host__ __device__ inline GemmLayout gemm_layout(int S, int thS, int nout_pad) 
 // ---------------------------------------------------------------------------------------
 // the tensor-core contraction
 // ---------------------------------------------------------------------------------------
-template <int NB, int NOUTP, bool OUTF2>
+// NREGC = 4: the 2 x 2 box of a velocity with no zero component, the offset loop unrolled
+// (the single MMA-issuing thread is instruction-bound on a runtime loop: 27 vs 19 us per
+// launch at 256^2, Q3); NREGC = 0: any box, runtime loop.
+template <int NB, int NOUTP, bool OUTF2, int NREGC>
 __global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
     const __grid_constant__ CUtensorMap dmap, const uint4* __restrict__ Bg,
     const double* __restrict__ rscale, const float* __restrict__ rowmul, int S, int nout,
     void* __restrict__ Yv, long long ystride_e, long long ystride_c, int* __restrict__ exps,
-    unsigned long long* __restrict__ maxbits, int nx, int ny, int* status) {
+    unsigned long long* __restrict__ maxbits, int nx, int ny, RegionBox box, int* status) {
   constexpr int THS = NB * NB;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t tmem_base_sh;
-  const GemmLayout L = gemm_layout(S, THS, NOUTP);
+  const int ox0 = box.lo[0], oy0 = box.lo[1];
+  const int ncx = NREGC ? 2 : box.cnt[0], nreg = NREGC ? NREGC : box.n;
+  const GemmLayout L = gemm_layout(S, THS, NOUTP, ncx, nreg);
   const int NSL = L.slots;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
@@ -126,11 +134,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
     const int tile = blockIdx.x + kk * gridDim.x;
     const uint32_t dst = smem_u32(smem + sl * L.slot_bytes);
     const uint32_t fb = full0 + 8u * sl;
-    mbar_expect_tx(fb, 3 * copy_bytes);  // out-of-range planes are zero-filled and counted
+    mbar_expect_tx(fb, ncx * copy_bytes);  // out-of-range planes are zero-filled and counted
     const int x0 = (tile % ntx) * kTX, y0 = (tile / ntx) * kTY;
-#pragma unroll
-    for (int ox = 0; ox < 3; ++ox)  // x and the 8 modes form one contiguous dimension
-      tma_load_3d(dst + ox * copy_bytes, &dmap, (x0 + ox) * 8, y0, q * L.G * L.P, fb);
+    // copy jx holds x-offset ox0 + jx: padded column x0 + 1 + ox0 + jx (x and the 8 modes
+    // form one contiguous dimension, so the coordinate is a multiple of 8 elements)
+    for (int jx = 0; jx < ncx; ++jx)
+      tma_load_3d(dst + jx * copy_bytes, &dmap, (x0 + 1 + ox0 + jx) * 8, y0, q * L.G * L.P, fb);
   };
 
   if (tid == 0) {
@@ -155,7 +164,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
       const int kk = item / L.groups, q = item % L.groups;
       const int tile = blockIdx.x + kk * gridDim.x;
       const int x0 = (tile % ntx) * kTX, y0 = (tile / ntx) * kTY;
-      for (int ox = 0; ox < 3; ++ox) tma_prefetch_3d(&dmap, (x0 + ox) * 8, y0, q * L.G * L.P);
+      for (int jx = 0; jx < ncx; ++jx)
+        tma_prefetch_3d(&dmap, (x0 + 1 + ox0 + jx) * 8, y0, q * L.G * L.P);
     }
     if (OUTF2 && blockIdx.x == 0) {
       // rotate the running maximum: the correction that follows accumulates a fresh one
@@ -219,11 +229,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
               const uint32_t idesc = idesc_bf16(128, nn);
               const uint32_t dcol = tst + (uint32_t)((a + c0) * NOUTP);
 #pragma unroll
-              for (int r = 0; r < 9; ++r) {
+              for (int r = 0; r < (NREGC ? NREGC : nreg); ++r) {
+                // box cell r: x-offset ox0 + r % ncx (copy r % ncx), y-offset oy0 + r / ncx
+                // (descriptor start moved by oy0 + r / ncx + 1 halo rows)
+                const int jx = r % ncx, ry = oy0 + r / ncx + 1;
 #pragma unroll
                 for (int j = 0; j < KSTEPS; ++j) {
-                  const uint32_t aoff = (uint32_t)(r % 3) * copy16 + dig +
-                                        (uint32_t)(2 * j * kCopy) + (uint32_t)((r / 3) * kTX);
+                  const uint32_t aoff = (uint32_t)jx * copy16 + dig + (uint32_t)(2 * j * kCopy) +
+                                        (uint32_t)(ry * kTX);
                   const uint32_t boff = (uint32_t)(r * P + 2 * j) * brows + (uint32_t)(c0 * NOUTP);
                   const uint32_t acc = (a == 0 && r == 0 && j == 0) ? 0u : 1u;
                   mma_bf16(dcol, adesc0 + aoff, bdesc0 + boff, idesc, acc);
@@ -576,16 +589,18 @@ bool mixed_supported(int dim, int nb, int nout) {
 static int nout_pad_of(int nout) { return nout <= 32 ? 32 : 64; }
 
 int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int slices,
-                std::vector<unsigned short>& digits, std::vector<double>& rscale,
-                std::vector<float>& rowmul, MixedOp& op) {
+                const RegionBox& box, std::vector<unsigned short>& digits,
+                std::vector<double>& rscale, std::vector<float>& rowmul, MixedOp& op) {
   if (!mixed_supported(dim, nb, nout) || slices < 2 || slices > 7) return RIDG_EINVAL;
   if (dim == 3 && !mixed3_supported(nb, slices)) return RIDG_EINVAL;
-  const int nreg = dim == 3 ? 27 : 9;  // region cells, x fastest
+  // region cells of G's columns: the upwind box, x fastest
+  const int nreg = box.n, ncx = box.cnt[0];
+  if (box.n < 1 || box.n > (dim == 3 ? 8 : 4) || (dim == 2 && box.cnt[2] != 1)) return RIDG_EINVAL;
   const int thS = dim == 3 ? nb * nb * nb : nb * nb, K = nreg * thS;
   if ((int)G.size() < nout * K) return RIDG_EINVAL;
   const int NOUTP = nout_pad_of(nout);
   if (slices * NOUTP > 512) return RIDG_EINVAL;
-  const GemmLayout L = gemm_layout(slices, thS, NOUTP);
+  const GemmLayout L = gemm_layout(slices, thS, NOUTP, ncx, nreg);
   const int tpad = L.P * 8;
   // digits in the shared-memory layout [region][k-chunk][row = c' * NOUTP + c][8]
   digits.assign((size_t)nreg * L.P * L.brows * 8, 0);
@@ -655,7 +670,7 @@ int mixed_make_map(const Grid& g, int nb, int slices, int nout, void* planes, vo
                         (cuuint64_t)slices * P};
   cuuint64_t strides[2] = {(cuuint64_t)(g.n[0] + 2) * 16,
                            (cuuint64_t)(g.n[0] + 2) * (g.n[1] + 2) * 16};
-  const GemmLayout L = gemm_layout(slices, thS, nout_pad_of(nout));
+  const GemmLayout L = gemm_layout(slices, thS, nout_pad_of(nout), g.box.cnt[0], g.box.n);
   cuuint32_t box[3] = {(cuuint32_t)kTX * 8, (cuuint32_t)kHY, (cuuint32_t)(L.G * P)};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = ((EncodeFn)fn)((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, planes,
@@ -668,8 +683,9 @@ int mixed_make_map(const Grid& g, int nb, int slices, int nout, void* planes, vo
 template <int NB, int NOUTP, bool OUTF2>
 static cudaError_t launch_gemm_t(const Grid& g, const void* map, const MixedOp& op, void* Y,
                                  long long ys_e, long long ys_c, MixedState& ms, cudaStream_t s) {
-  const GemmLayout L = gemm_layout(op.slices, NB * NB, NOUTP);
-  auto kern = mixed_gemm_kernel<NB, NOUTP, OUTF2>;
+  const GemmLayout L = gemm_layout(op.slices, NB * NB, NOUTP, g.box.cnt[0], g.box.n);
+  const bool box22 = g.box.cnt[0] == 2 && g.box.cnt[1] == 2;
+  auto kern = box22 ? mixed_gemm_kernel<NB, NOUTP, OUTF2, 4> : mixed_gemm_kernel<NB, NOUTP, OUTF2, 0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -679,13 +695,15 @@ static cudaError_t launch_gemm_t(const Grid& g, const void* map, const MixedOp& 
   const int grid = std::min(ntiles, sms);
   kern<<<grid, kGemmThreads, L.bytes, s>>>(*(const CUtensorMap*)map, (const uint4*)op.b_slices,
                                            op.row_scale, op.row_mul, op.slices, op.nout, Y, ys_e,
-                                           ys_c, ms.exps, ms.maxbits, g.n[0], g.n[1], ms.status);
+                                           ys_c, ms.exps, ms.maxbits, g.n[0], g.n[1], g.box,
+                                           ms.status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mixed_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
                               long long ys_e, long long ys_c, bool fused, cudaStream_t s) {
-  if (g.dim != 2) return cudaErrorInvalidValue;
+  if (g.dim != 2 || g.box.n < 1 || g.box.n > 4 || op.K != g.box.n * nb * nb)
+    return cudaErrorInvalidValue;
 #define RIDG_GEMM_CASE(NBV, NP)                                                              \
   case NBV:                                                                                   \
     return fused ? launch_gemm_t<NBV, NP, true>(g, ms.map, op, Y, ys_e, ys_c, ms, s)          \

@@ -1,21 +1,24 @@
 // Mixed-precision linear prediction in 3D on the 5th-generation tensor cores (tcgen05 + TMA).
 //
 // What is computed: the time-mean prediction W-bar_e = P-bar X_e of every cell e (Sec. 2.2,
-// eq. pred_full_system for a linear flux; X_e = the theta_S coefficients of the 3 x 3 x 3
-// region, P-bar = the centre rows of the region operator that the correction of Sec. 2.3
-// needs), by the same split-operand refinement as the 2D path: the state as S balanced
+// eq. pred_full_system for a linear flux; X_e = the theta_S coefficients of the region cells
+// upstream of e -- the upwind box, 2 x 2 x 2 of the 3 x 3 x 3 for a velocity with no zero
+// component, the other cells' operator columns being zero -- and P-bar = the centre rows of
+// the region operator that the correction of Sec. 2.3 needs), by the same split-operand
+// refinement as the 2D path: the state as S balanced
 // base-256 digits (exact in BF16) times one exponent, the operator rows likewise, digit
 // products summed in FP32 per weight a + c' in TMEM and recombined with error-free sums.
 //
 // Tiles are 8 x 16 cells of one z-plane (M = 128).  The region offset (ox, oy, oz) is taken
-// as in 2D -- x by one of three x-shifted TMA copies, y by the descriptor start -- and z by
-// loading the plane z + oz.  In 3D the operator digits of all 27 offsets do not fit next to
-// the state digits in shared memory, so they stream too:
-//   A ring (4 slots): one digit of one input plane (3 x-copies x 8-mode groups x 8 x 18
-//     cells, 27.6 KB at Q2), loaded by 4D TMA boxes of the ghost-padded digit planes;
-//   B stages (3): the operator digits of the three x-offsets of one (oz, oy) row (36.9 KB),
-//     one bulk copy each; stage oy is refilled for the next oz once the last digit's MMAs
-//     on it are complete.
+// as in 2D -- x by one of the box's x-shifted TMA copies, y by the descriptor start -- and z
+// by loading the plane z + oz.  The operator digits of all the box's offsets do not fit next
+// to the state digits in shared memory, so they stream too:
+//   A ring (4 slots): one digit of one input plane (one x-copy per x-offset of the box, each
+//     8-mode groups x 8 x 18 cells: 18.4 KB at Q2 with two x-offsets), loaded by 4D TMA
+//     boxes of the ghost-padded digit planes;
+//   B stages (one per y-offset of the box): the operator digits of the x-offsets of one
+//     (oz, oy) row (24.6 KB), one bulk copy each; stage oy is refilled for the next oz once
+//     the last digit's MMAs on it are complete.
 // The MMA issuer runs oz -> digit a -> oy -> ox -> k-step; the epilogue writes W-bar as
 // double-float pairs with a common exponent, and mixed3_correct_kernel applies the correction
 // in double-float FP32 (state update FP64) and writes the next step's digit planes.  Every
@@ -47,30 +50,36 @@ struct Gemm3Layout {
   uint32_t copy_bytes, a_bytes, b_bytes, b_off, bar_off, bytes;
 };
 
-__host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS) {
+// ncx = x-offsets of the upwind box (x-shifted copies per A slot, operator blocks per B row)
+__host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int ncx) {
   Gemm3Layout l;
   l.P = ((thS + 15) / 16) * 2;
   l.brows = S * kNOUTP;
   l.copy_bytes = (uint32_t)l.P * kCopy * 16;
-  l.a_bytes = (3u * l.copy_bytes + 1023u) & ~1023u;
-  l.b_bytes = 3u * l.P * l.brows * 16;
+  l.a_bytes = ((uint32_t)ncx * l.copy_bytes + 1023u) & ~1023u;
+  l.b_bytes = (uint32_t)ncx * l.P * l.brows * 16;
   l.b_off = kNA * l.a_bytes;
   l.bar_off = (l.b_off + kNBst * l.b_bytes + 63u) & ~63u;
   l.bytes = l.bar_off + 256;
   return l;
 }
 
-template <int NB>
+// NCXC = 2: two x-offsets, the x loop unrolled; NCXC = 0: runtime count.
+template <int NB, int NCXC>
 __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
     const __grid_constant__ CUtensorMap dmap, const unsigned char* __restrict__ Bg,
     const float* __restrict__ rowmul, int S, int nout, float2* __restrict__ Y, int* __restrict__ exps,
-    unsigned long long* __restrict__ maxbits, int nx, int ny, int nz, int* status) {
+    unsigned long long* __restrict__ maxbits, int nx, int ny, int nz, RegionBox box,
+    int* status) {
   constexpr int THS = NB * NB * NB;
   constexpr int P = ((THS + 15) / 16) * 2;
   constexpr int KSTEPS = P / 2;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t tmem_base_sh;
-  const Gemm3Layout L = gemm3_layout(S, THS);
+  // the upwind box: offsets lo + 0 .. cnt - 1 per dimension (cnt 1 or 2, at most 3 B stages)
+  const int ox0 = box.lo[0], oy0 = box.lo[1], oz0 = box.lo[2];
+  const int ncx = NCXC ? NCXC : box.cnt[0], ncy = box.cnt[1], ncz = box.cnt[2];
+  const Gemm3Layout L = gemm3_layout(S, THS, ncx);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
   const int ntiles = ntx * nty * nz;
@@ -128,14 +137,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
       for (int k = 0; k < mytiles && ok; ++k) {
         int x0, y0, z0;
         tile_origin(k, x0, y0, z0);
-        for (int oz = 0; oz < 3 && ok; ++oz) {
-          const int use = k * 3 + oz;  // use count of every B stage
-          for (int oy = 0; oy < 3; ++oy) {
-            if (use > 0 && !mbar_wait_sleep(bfree0 + 8u * oy, (use - 1) & 1)) { ok = false; break; }
-            const uint32_t fb = bfull0 + 8u * oy;
+        for (int jz = 0; jz < ncz && ok; ++jz) {
+          const int use = k * ncz + jz;  // use count of every B stage
+          for (int jy = 0; jy < ncy; ++jy) {
+            if (use > 0 && !mbar_wait_sleep(bfree0 + 8u * jy, (use - 1) & 1)) { ok = false; break; }
+            const uint32_t fb = bfull0 + 8u * jy;
             mbar_expect_tx(fb, L.b_bytes);
-            const unsigned char* src = Bg + (size_t)(oz * 3 + oy) * L.b_bytes;
-            const uint32_t dst = smem_u32(smem + L.b_off + oy * L.b_bytes);
+            const unsigned char* src = Bg + (size_t)(jz * ncy + jy) * L.b_bytes;
+            const uint32_t dst = smem_u32(smem + L.b_off + jy * L.b_bytes);
             for (uint32_t off = 0; off < L.b_bytes; off += 32768u)
               bulk_load(dst + off, src + off, min(32768u, L.b_bytes - off), fb);
           }
@@ -143,11 +152,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
             const int sl = ia % kNA;
             if (ia >= kNA && !mbar_wait_sleep(afree0 + 8u * sl, ((ia / kNA) - 1) & 1)) { ok = false; break; }
             const uint32_t fa = afull0 + 8u * sl;
-            mbar_expect_tx(fa, 3 * L.copy_bytes);  // out-of-range boxes are zero-filled and counted
+            mbar_expect_tx(fa, ncx * L.copy_bytes);  // out-of-range boxes are zero-filled and counted
             const uint32_t dst = smem_u32(smem + sl * L.a_bytes);
-#pragma unroll
-            for (int ox = 0; ox < 3; ++ox)
-              tma_load_4d(dst + ox * L.copy_bytes, &dmap, (x0 + ox) * 8, y0, z0 + oz, a * P, fa);
+            // copy jx: x-offset ox0 + jx (padded column x0 + 1 + ox0 + jx, a multiple of 8
+            // elements), plane z-offset oz0 + jz (padded plane z0 + 1 + oz0 + jz)
+            for (int jx = 0; jx < ncx; ++jx)
+              tma_load_4d(dst + jx * L.copy_bytes, &dmap, (x0 + 1 + ox0 + jx) * 8, y0,
+                          z0 + 1 + oz0 + jz, a * P, fa);
           }
         }
       }
@@ -165,8 +176,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
         const int ts = k & 1;
         if (k >= 2 && !mbar_wait(tempty0 + 8u * ts, ((k - 2) >> 1) & 1)) { ok = false; break; }
         const uint32_t tst = tmem + (uint32_t)(ts * tcols);
-        for (int oz = 0; oz < 3 && ok; ++oz) {
-          const int use = k * 3 + oz;
+        for (int jz = 0; jz < ncz && ok; ++jz) {
+          const int use = k * ncz + jz;
           for (int a = 0; a < S && ok; ++a, ++ia) {
             const int sl = ia % kNA;
             if (!mbar_wait(afull0 + 8u * sl, (ia / kNA) & 1)) { ok = false; break; }
@@ -175,26 +186,28 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
             const uint64_t adesc0 = smem_desc(smem_u32(smem + sl * L.a_bytes), kCopy * 16, 128);
             const uint32_t idesc = idesc_bf16(128, (S - a) * kNOUTP);
             const uint32_t dcol = tst + (uint32_t)(a * kNOUTP);
-            for (int oy = 0; oy < 3; ++oy) {
+            for (int jy = 0; jy < ncy; ++jy) {
               if (a == 0) {
-                if (!mbar_wait(bfull0 + 8u * oy, use & 1)) { ok = false; break; }
+                if (!mbar_wait(bfull0 + 8u * jy, use & 1)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
               }
-              const uint64_t bdesc0 = smem_desc(smem_u32(smem + L.b_off + oy * L.b_bytes), brows * 16, 128);
+              const uint64_t bdesc0 = smem_desc(smem_u32(smem + L.b_off + jy * L.b_bytes), brows * 16, 128);
+              // y-offset oy0 + jy: the descriptor start moved by oy0 + jy + 1 halo rows
+              const uint32_t yoff = (uint32_t)((oy0 + jy + 1) * kTX);
 #pragma unroll
-              for (int ox = 0; ox < 3; ++ox) {
+              for (int jx = 0; jx < (NCXC ? NCXC : ncx); ++jx) {
 #pragma unroll
                 for (int j = 0; j < KSTEPS; ++j) {
-                  const uint32_t aoff = (uint32_t)ox * copy16 + (uint32_t)(2 * j * kCopy) + (uint32_t)(oy * kTX);
-                  const uint32_t boff = (uint32_t)(ox * P + 2 * j) * brows;
-                  const uint32_t acc = (oz == 0 && a == 0 && oy == 0 && ox == 0 && j == 0) ? 0u : 1u;
+                  const uint32_t aoff = (uint32_t)jx * copy16 + (uint32_t)(2 * j * kCopy) + yoff;
+                  const uint32_t boff = (uint32_t)(jx * P + 2 * j) * brows;
+                  const uint32_t acc = (jz == 0 && a == 0 && jy == 0 && jx == 0 && j == 0) ? 0u : 1u;
                   mma_bf16(dcol, adesc0 + aoff, bdesc0 + boff, idesc, acc);
                 }
               }
               if (a == S - 1)
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        bfree0 + 8u * oy)
+                        bfree0 + 8u * jy)
                     : "memory");
             }
             asm volatile(
@@ -529,7 +542,7 @@ __global__ void __launch_bounds__(128) state_digits3_kernel(const double* __rest
 // ------------------------------------------------------------------------------------------
 bool mixed3_supported(int nb, int slices) {
   if (nb < 2 || nb > 3 || slices < 2 || slices > 6) return false;
-  return gemm3_layout(slices, nb * nb * nb).bytes <= kSmemLimit;
+  return gemm3_layout(slices, nb * nb * nb, 3).bytes <= kSmemLimit;  // widest box
 }
 
 size_t mixed3_plane_bytes(const Grid& g, int nb, int slices) {
@@ -565,11 +578,11 @@ int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_o
 template <int NB>
 static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& ms, void* Y,
                                   cudaStream_t s) {
-  const Gemm3Layout L = gemm3_layout(op.slices, NB * NB * NB);
+  const Gemm3Layout L = gemm3_layout(op.slices, NB * NB * NB, g.box.cnt[0]);
   // one CTA per SM: each allocates all 512 TMEM columns, so a second CTA on the SM would
   // only wait for them -- ask for more than half the shared memory
   const uint32_t smem = std::max<uint32_t>(L.bytes, 117u * 1024u);
-  auto kern = mixed3_gemm_kernel<NB>;
+  auto kern = g.box.cnt[0] == 2 ? mixed3_gemm_kernel<NB, 2> : mixed3_gemm_kernel<NB, 0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -580,13 +593,14 @@ static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& 
   kern<<<grid, kGemmThreads, smem, s>>>(*(const CUtensorMap*)ms.map,
                                         (const unsigned char*)op.b_slices, op.row_mul, op.slices,
                                         op.nout, (float2*)Y, ms.exps, ms.maxbits, g.n[0], g.n[1],
-                                        g.n[2], ms.status);
+                                        g.n[2], g.box, ms.status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
                                cudaStream_t s) {
-  if (g.dim != 3) return cudaErrorInvalidValue;
+  if (g.dim != 3 || g.box.n < 1 || g.box.n > 8 || op.K != g.box.n * nb * nb * nb)
+    return cudaErrorInvalidValue;
   switch (nb) {
     case 2: return launch_gemm3_t<2>(g, op, ms, Y, s);
     case 3: return launch_gemm3_t<3>(g, op, ms, Y, s);

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/ridg.h"
+#include "tables.h"
 
 namespace ridg {
 
@@ -31,10 +32,12 @@ struct Grid {
   int dim;
   int n[3];
   long long ncell;
+  RegionBox box;  // linear flux: the region cells the prediction reads (tables.h)
 };
 
 // ---- FP64 linear path (k_linear.cu) ----
-// W[e * wstride + c0 + c] = sum_k P[c][k] X_e[k] for c < nout (rows of P, K = 3^d theta_S)
+// W[e * wstride + c0 + c] = sum_k P[c][k] X_e[k] for c < nout (rows of P, K = g.box.n theta_S:
+// X_e stacks the Q of the box's cells around e, x fastest)
 cudaError_t launch_predict_fp64(const Grid& g, int nb, const double* Q, const double* P, int nout,
                                 double* W, int wstride, cudaStream_t s);
 // Q[e] += correction from the time means Wbar (stride wstride) of e and its face neighbours
@@ -66,9 +69,11 @@ struct MixedState {
   bool valid = false;                     // planes describe the current state
 };
 bool mixed_supported(int dim, int nb, int nout);
+// Digits of the operator rows P (nout x K): K = box.n theta_S columns, the upwind box's
+// cells x fastest.
 int mixed_build(int dim, int nb, const std::vector<double>& P, int nout, int slices,
-                std::vector<unsigned short>& digits, std::vector<double>& rscale,
-                std::vector<float>& rowmul, MixedOp& op);
+                const RegionBox& box, std::vector<unsigned short>& digits,
+                std::vector<double>& rscale, std::vector<float>& rowmul, MixedOp& op);
 size_t mixed_plane_bytes(const Grid& g, int nb, int slices);
 int mixed_make_map(const Grid& g, int nb, int slices, int nout, void* planes, void* map_out);
 // Y[e * ys_e + c * ys_c] = (G X_e)[c]: FP64 (fused == false) or, for the fused step
@@ -207,7 +212,8 @@ struct ridg_handle {
   // problem
   int dim = 0, n[3] = {1, 1, 1};
   double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, h[3] = {1, 1, 1};
-  int M = 0, nb = 1, thS = 1, thT = 1, m = 1, nR = 1, K = 1;
+  int M = 0, nb = 1, thS = 1, thT = 1, m = 1, nR = 1, K = 1;  // K = box.n theta_S
+  ridg::RegionBox box;  // linear flux: the upwind region cells the prediction reads
   long long ncell = 0;
   ridg_flux flux{};
   double cfl = 0;

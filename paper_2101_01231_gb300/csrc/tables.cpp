@@ -1,6 +1,7 @@
 // Host-side FP64 numerics (see tables.h).
 #include "tables.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -150,73 +151,115 @@ inline int ipow(int b, int e) {
 }
 }  // namespace
 
-bool linear_operator(int dim, int M, const double* nu, std::vector<double>& P) {
-  const int nb = M + 1, thS = ipow(nb, dim), thT = nb * thS, nR = ipow(3, dim);
-  const int n = nR * thT, K = nR * thS;
+RegionBox upwind_box(int dim, const double* vel) {
+  RegionBox b;
+  for (int d = 0; d < dim; ++d) {
+    if (vel[d] > 0) {
+      b.lo[d] = -1;
+      b.cnt[d] = 2;
+    } else if (vel[d] < 0) {
+      b.lo[d] = 0;
+      b.cnt[d] = 2;
+    }
+  }
+  b.n = b.cnt[0] * b.cnt[1] * b.cnt[2];
+  return b;
+}
+
+bool linear_operator(int dim, int M, const double* nu, const RegionBox& box,
+                     std::vector<double>& P) {
+  const int nb = M + 1, thS = ipow(nb, dim), thT = nb * thS, nc = box.n;
+  const int K = nc * thS;
   Tables1D t = tables1d(nb);
   auto D = [&](int a, int b) { return t.D[a * nb + b]; };
-  std::vector<double> A((size_t)n * n, 0.0);
-  // spatial digit b_dd of mode s
   auto digit = [&](int s, int dd) { return (s / ipow(nb, dd)) % nb; };
-  auto off = [&](int r, int dd) { return (r / ipow(3, dd)) % 3 - 1; };
-  auto region_index = [&](const int* o) {
-    int r = 0;
-    for (int dd = dim - 1; dd >= 0; --dd) r = r * 3 + (o[dd] + 1);
-    return r;
+  // box cell i <-> region offsets o[] (x fastest)
+  auto offsets = [&](int i, int* o) {
+    o[0] = box.lo[0] + i % box.cnt[0];
+    o[1] = box.lo[1] + (i / box.cnt[0]) % box.cnt[1];
+    o[2] = box.lo[2] + i / (box.cnt[0] * box.cnt[1]);
   };
-  for (int r = 0; r < nR; ++r) {
-    int o[3] = {0, 0, 0};
-    for (int dd = 0; dd < dim; ++dd) o[dd] = off(r, dd);
+  auto box_index = [&](const int* o) {
+    return (o[0] - box.lo[0]) + box.cnt[0] * ((o[1] - box.lo[1]) + box.cnt[1] * (o[2] - box.lo[2]));
+  };
+  // Diagonal block of region cell o, stored transposed (At[l][k] = A[k][l]): time term,
+  // internal flux, and the cell's own trace on each face -- the upwind trace on a face
+  // shared with a region neighbour, the cell's own (interior) trace on the region boundary.
+  std::vector<std::vector<double>> LU(nc);
+  std::vector<std::vector<int>> perm(nc);
+  for (int i = 0; i < nc; ++i) {
+    int o[3];
+    offsets(i, o);
+    std::vector<double>& At = LU[i];
+    At.assign((size_t)thT * thT, 0.0);
+    auto add = [&](int k, int l, double v) { At[(size_t)l * thT + k] += v; };
     for (int k = 0; k < thT; ++k) {
       const int al = k / thS, s = k % thS;
-      double* row = A.data() + (size_t)(r * thT + k) * n;
-      // time term: [psi_a(1) psi_g(1) - D_ag] delta_ss'
-      for (int g = 0; g < nb; ++g) row[r * thT + g * thS + s] += t.ep[al] * t.ep[g] - D(al, g);
+      for (int g = 0; g < nb; ++g) add(k, g * thS + s, t.ep[al] * t.ep[g] - D(al, g));
       for (int dd = 0; dd < dim; ++dd) {
         const int st = ipow(nb, dd), bd = digit(s, dd), base = s - bd * st;
         const double nud = nu[dd], nup = nud > 0 ? nud : 0.0, num = nud < 0 ? nud : 0.0;
+        const bool has_plus = o[dd] + 1 <= 1, has_minus = o[dd] - 1 >= -1;
         for (int b2 = 0; b2 < nb; ++b2) {
-          const int l = al * thS + base + b2 * st;  // same time index, same other digits
-          // internal flux: -nu_d D[bd][b2]
-          row[r * thT + l] -= nud * D(bd, b2);
-          // face at +1 (outward +e_dd)
-          int o2[3] = {o[0], o[1], o[2]};
-          o2[dd] += 1;
-          if (o2[dd] <= 1) {
-            const int r2 = region_index(o2);
-            row[r * thT + l] += nup * t.ep[bd] * t.ep[b2];
-            row[r2 * thT + l] += num * t.ep[bd] * t.em[b2];
-          } else {
-            row[r * thT + l] += nud * t.ep[bd] * t.ep[b2];
-          }
-          // face at -1 (outward -e_dd)
-          o2[dd] -= 2;
-          if (o2[dd] >= -1) {
-            const int r2 = region_index(o2);
-            row[r2 * thT + l] -= nup * t.em[bd] * t.ep[b2];
-            row[r * thT + l] -= num * t.em[bd] * t.em[b2];
-          } else {
-            row[r * thT + l] -= nud * t.em[bd] * t.em[b2];
-          }
+          const int l = al * thS + base + b2 * st;
+          add(k, l, -nud * D(bd, b2));
+          add(k, l, (has_plus ? nup : nud) * t.ep[bd] * t.ep[b2]);
+          add(k, l, -(has_minus ? num : nud) * t.em[bd] * t.em[b2]);
         }
       }
     }
+    if (!lu_factor(thT, At.data(), perm[i])) return false;
   }
-  std::vector<int> perm;
-  if (!lu_factor(n, A.data(), perm)) return false;
-  // P[c][(r, s)] = sum_a z_c[(r, a, s)] psi_a(-1),  A^T z_c = e_{centre, c}
-  const int rc = (nR - 1) / 2;
+  // Box cells in sweep order: the centre first, then by the number of nonzero offsets, so
+  // that a cell's downstream neighbours (offset moved to 0 in one dimension) come earlier.
+  std::vector<int> order(nc);
+  for (int i = 0; i < nc; ++i) order[i] = i;
+  auto nonzero = [&](int i) {
+    int o[3];
+    offsets(i, o);
+    return (o[0] != 0) + (o[1] != 0) + (o[2] != 0);
+  };
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return nonzero(a) < nonzero(b); });
+  // Coupling of cell r to its downstream neighbour r' along dd: row (r', k') of A holds
+  // C[bd][b2] at column (r, l) for k' = (al, base + bd st), l = (al, base + b2 st), with
+  // C = -nu em (x) ep for nu > 0 (face -1 of r') and nu ep (x) em for nu < 0 (face +1).
+  // P[c][(i, s)] = sum_a z_i[(a, s)] psi_a(-1), where A^T z = e_(centre, c).
   P.assign((size_t)thT * K, 0.0);
+  int o0[3] = {0, 0, 0};
+  const int centre = box_index(o0);
 #pragma omp parallel for schedule(dynamic)
   for (int c = 0; c < thT; ++c) {
-    std::vector<double> z(n, 0.0);
-    z[rc * thT + c] = 1.0;
-    lu_solve_transpose(n, A.data(), perm, z.data());
-    for (int r = 0; r < nR; ++r)
+    std::vector<double> z((size_t)nc * thT, 0.0);
+    for (int i : order) {
+      int o[3];
+      offsets(i, o);
+      double* zi = z.data() + (size_t)i * thT;
+      if (i == centre) zi[c] = 1.0;
+      for (int dd = 0; dd < dim; ++dd) {
+        if (o[dd] == 0) continue;
+        int od[3] = {o[0], o[1], o[2]};
+        od[dd] = 0;
+        const double* zd = z.data() + (size_t)box_index(od) * thT;
+        const int st = ipow(nb, dd);
+        const double nud = nu[dd];
+        for (int l = 0; l < thT; ++l) {
+          const int al = l / thS, s = l % thS, b2 = digit(s, dd), base = s - b2 * st;
+          double acc = 0.0;
+          for (int bd = 0; bd < nb; ++bd) {
+            const double C = nud > 0 ? -nud * t.em[bd] * t.ep[b2] : nud * t.ep[bd] * t.em[b2];
+            acc += C * zd[al * thS + base + bd * st];
+          }
+          zi[l] -= acc;
+        }
+      }
+      lu_solve(thT, LU[i].data(), perm[i], zi);
+    }
+    for (int i = 0; i < nc; ++i)
       for (int s = 0; s < thS; ++s) {
         double acc = 0.0;
-        for (int a = 0; a < nb; ++a) acc += z[r * thT + a * thS + s] * t.em[a];
-        P[(size_t)c * K + r * thS + s] = acc;
+        for (int a = 0; a < nb; ++a) acc += z[(size_t)i * thT + a * thS + s] * t.em[a];
+        P[(size_t)c * K + i * thS + s] = acc;
       }
   }
   return true;

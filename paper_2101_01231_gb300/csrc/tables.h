@@ -21,11 +21,28 @@ struct Tables1D {
 };
 Tables1D tables1d(int nb);
 
+// The region cells a linear flux's prediction depends on (Sec. 2.2).  With upwind face
+// values the region system of eq. pred_full_system is block triangular in the flow
+// direction: a cell's equations reference only itself and its upstream face neighbours, so
+// the centre's solution depends only on the cells upstream of it.  Per dimension d that is
+// offsets {-1, 0} for a_d > 0, {0, +1} for a_d < 0 and {0} for a_d = 0: a box of
+// cnt[0] x cnt[1] x cnt[2] cells starting at offset lo[], x fastest.
+struct RegionBox {
+  int lo[3] = {0, 0, 0};
+  int cnt[3] = {1, 1, 1};
+  int n = 1;
+};
+RegionBox upwind_box(int dim, const double* vel);
+
 // Centre-row solution operator of the linear region system (Sec. 2.2):
-//   W_centre = P X,  X = the region's Q stacked (3^d blocks of theta_S, x fastest),
-// P has theta_T rows and K = 3^d theta_S columns (row-major).  nu[d] = a_d dt / h_d.
-// Returns false if the region matrix is singular.
-bool linear_operator(int dim, int M, const double* nu, std::vector<double>& P);
+//   W_centre = P X,  X = the Q of the box's cells stacked (box.n blocks of theta_S, x fastest),
+// P has theta_T rows and K = box.n theta_S columns (row-major); the region cells outside
+// the box have exactly zero columns and are left out.  nu[d] = a_d dt / h_d must have the
+// sign of the velocity the box was made from (or be zero).  The system is solved by block
+// substitution over the box (one dense LU per box cell's diagonal block).  Returns false if
+// a diagonal block is singular.
+bool linear_operator(int dim, int M, const double* nu, const RegionBox& box,
+                     std::vector<double>& P);
 
 // Dense LU with partial pivoting, in place (row-major n x n); perm[i] = original row of
 // row i of the factors.  Returns false on a zero pivot.

@@ -21,6 +21,7 @@ CASES = [
     ((3, 3), 1, (-0.4, 1.0)),
     ((40, 33), 3, (-1.0, -0.25)),
     ((24, 20), 3, (0.8, 0.0)),
+    ((11, 18), 2, (0.0, -0.6)),
 ]
 TOL_STEP = 1e-12
 TOL_FINAL = 1e-10

@@ -16,6 +16,7 @@ CASES = [
     ((9, 20, 3), 1, (0.3, -1.0, 0.6)),
     ((16, 16, 5), 2, (-1.0, -1.0, 1.0)),
     ((3, 3, 3), 1, (0.2, 0.0, -0.7)),
+    ((9, 17, 3), 2, (0.0, 0.8, 0.0)),
 ]
 TOL_STEP = 1e-12
 
