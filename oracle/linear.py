@@ -30,6 +30,8 @@ import math
 
 import numpy as np
 import scipy.linalg as sla
+import scipy.sparse as sps
+import scipy.sparse.linalg as spla
 
 from . import basis
 
@@ -70,14 +72,11 @@ def advection_time_step(w, T=None):
 # ---------------------------------------------------------------------------
 # the region system of eq. pred_full_system
 # ---------------------------------------------------------------------------
-def region_system(d: int, M: int, nu) -> tuple[np.ndarray, np.ndarray]:
-    """Return (A, B) with A W_R = B Q_R for one region.
-
-    W_R stacks the 3^d space-time blocks (region element r, then alpha, then s);
-    Q_R stacks the 3^d spatial blocks.  Everything is divided by |T_j|."""
+def _region_terms(d: int, M: int, nu, kron):
+    """The terms of eq. pred_full_system on one region, in the order they are summed:
+    yields ("A" or "B", row element, column element, block), blocks built with kron."""
     nb = M + 1
     thS = nb ** d
-    thT = nb * thS
     D = basis.deriv_matrix(nb)
     ep, em = basis.trace_plus(nb), basis.trace_minus(nb)
     I1 = np.eye(nb)
@@ -86,40 +85,80 @@ def region_system(d: int, M: int, nu) -> tuple[np.ndarray, np.ndarray]:
     def along(dd, X):  # spatial operator acting along dimension dd only
         mats = [I1] * d
         mats[dd] = X
-        return basis.kron_x_fastest(mats)
+        out = mats[-1]
+        for Y in reversed(mats[:-1]):   # x index fastest
+            out = kron(out, Y)
+        return out
 
     offs = basis.region_offsets(d)
     index = {tuple(o): r for r, o in enumerate(offs)}
-    nR = len(offs)
-    A = np.zeros((nR * thT, nR * thT))
-    B = np.zeros((nR * thT, nR * thS))
     time_term = np.outer(ep, ep) - D          # psi(1) psi(1)^T - int psi' psi
     source = em.reshape(nb, 1)                # psi_alpha(-1)
     for r, o in enumerate(offs):
-        rr = slice(r * thT, (r + 1) * thT)
-        A[rr, rr] += np.kron(time_term, IS)
-        B[rr, r * thS:(r + 1) * thS] += np.kron(source, IS)
+        yield "A", r, r, kron(time_term, IS)
+        yield "B", r, r, kron(source, IS)
         for dd in range(d):
             nu_d = float(nu[dd])
             nup, num = max(nu_d, 0.0), min(nu_d, 0.0)
-            A[rr, rr] -= nu_d * np.kron(I1, along(dd, D))           # internal flux
+            yield "A", r, r, -nu_d * kron(I1, along(dd, D))           # internal flux
             # face at xi_d = +1, outward normal +e_d
             o2 = o.copy(); o2[dd] += 1
             if tuple(o2) in index:
-                r2 = index[tuple(o2)]
-                A[rr, rr] += nup * np.kron(I1, along(dd, np.outer(ep, ep)))
-                A[rr, r2 * thT:(r2 + 1) * thT] += num * np.kron(I1, along(dd, np.outer(ep, em)))
+                yield "A", r, r, nup * kron(I1, along(dd, np.outer(ep, ep)))
+                yield "A", r, index[tuple(o2)], num * kron(I1, along(dd, np.outer(ep, em)))
             else:   # region boundary: own (interior) trace only
-                A[rr, rr] += nu_d * np.kron(I1, along(dd, np.outer(ep, ep)))
+                yield "A", r, r, nu_d * kron(I1, along(dd, np.outer(ep, ep)))
             # face at xi_d = -1, outward normal -e_d
             o2 = o.copy(); o2[dd] -= 1
             if tuple(o2) in index:
-                r2 = index[tuple(o2)]
-                A[rr, r2 * thT:(r2 + 1) * thT] -= nup * np.kron(I1, along(dd, np.outer(em, ep)))
-                A[rr, rr] -= num * np.kron(I1, along(dd, np.outer(em, em)))
+                yield "A", r, index[tuple(o2)], -nup * kron(I1, along(dd, np.outer(em, ep)))
+                yield "A", r, r, -num * kron(I1, along(dd, np.outer(em, em)))
             else:
-                A[rr, rr] -= nu_d * np.kron(I1, along(dd, np.outer(em, em)))
+                yield "A", r, r, -nu_d * kron(I1, along(dd, np.outer(em, em)))
+
+
+def region_system(d: int, M: int, nu) -> tuple[np.ndarray, np.ndarray]:
+    """Return (A, B) with A W_R = B Q_R for one region.
+
+    W_R stacks the 3^d space-time blocks (region element r, then alpha, then s);
+    Q_R stacks the 3^d spatial blocks.  Everything is divided by |T_j|."""
+    nb = M + 1
+    thS = nb ** d
+    thT = nb * thS
+    nR = 3 ** d
+    A = np.zeros((nR * thT, nR * thT))
+    B = np.zeros((nR * thT, nR * thS))
+    for which, r, c, blk in _region_terms(d, M, nu, np.kron):
+        if which == "A":
+            A[r * thT:(r + 1) * thT, c * thT:(c + 1) * thT] += blk
+        else:
+            B[r * thT:(r + 1) * thT, c * thS:(c + 1) * thS] += blk
     return A, B
+
+
+def region_system_sparse(d: int, M: int, nu):
+    """The same (A, B) as region_system, the same terms summed in the same order, stored
+    as scipy sparse matrices (A in CSC for a sparse LU) -- for degrees whose dense region
+    matrix does not fit (3D: 3^3 (M + 1)^4 unknowns)."""
+    nb = M + 1
+    thS = nb ** d
+    thT = nb * thS
+    nR = 3 ** d
+    Ab = [[None] * nR for _ in range(nR)]
+    Bb = [[None] * nR for _ in range(nR)]
+
+    def skron(X, Y):
+        return sps.kron(sps.csr_matrix(X), sps.csr_matrix(Y), format="csr")
+
+    for which, r, c, blk in _region_terms(d, M, nu, skron):
+        blocks = Ab if which == "A" else Bb
+        blocks[r][c] = blk if blocks[r][c] is None else blocks[r][c] + blk
+    for r in range(nR):   # bmat needs each block row and column sized
+        if Bb[r][r] is None:
+            Bb[r][r] = sps.csr_matrix((thT, thS))
+    A = sps.bmat(Ab, format="csc")
+    A.eliminate_zeros()   # terms with a zero factor (the downstream nu+- part) hold no entries
+    return A, sps.bmat(Bb, format="csr")
 
 
 def nu_of(w, dt) -> np.ndarray:
@@ -144,14 +183,30 @@ def gather_region(Q: np.ndarray, w) -> np.ndarray:
     return np.stack(out, axis=1)
 
 
+# above this many region unknowns the dense region matrix (n^2 doubles, 2.3 GB at 3D Q4) is
+# replaced by the same matrix in sparse form and a sparse LU (a library primitive)
+DENSE_MAX_UNKNOWNS = 8000
+
+
+def region_solver(d: int, M: int, nu):
+    """(solve, B) for the region system A W_R = B Q_R: solve(rhs) returns A^-1 rhs."""
+    n = 3 ** d * (M + 1) ** (d + 1)
+    if n <= DENSE_MAX_UNKNOWNS:
+        A, B = region_system(d, M, nu)
+        lu = sla.lu_factor(A)
+        return (lambda rhs: sla.lu_solve(lu, rhs)), B
+    A, B = region_system_sparse(d, M, nu)
+    lu = spla.splu(A)
+    return (lambda rhs: lu.solve(np.asarray(rhs))), B
+
+
 def predict(Q: np.ndarray, w, dt: float, chunk: int = 8192) -> np.ndarray:
     """Centre-element space-time coefficients W_i for every cell, shape (cells, theta_T).
     Each region system is solved with the LU factors of A (computed once)."""
     d, M = w["dim"], w["M"]
     nb = M + 1
     thS, thT = nb ** d, nb ** (d + 1)
-    A, B = region_system(d, M, nu_of(w, dt))
-    lu = sla.lu_factor(A)
+    solve, B = region_solver(d, M, nu_of(w, dt))
     rc = (3 ** d - 1) // 2
     ncell = Q.shape[0]
     W = np.empty((ncell, thT))
@@ -159,7 +214,7 @@ def predict(Q: np.ndarray, w, dt: float, chunk: int = 8192) -> np.ndarray:
         e1 = min(ncell, e0 + chunk)
         X = gather_region(Q, w)[e0:e1] if ncell <= chunk else _gather_rows(Q, w, e0, e1)
         rhs = B @ X.reshape(e1 - e0, -1).T                     # (n, cells)
-        sol = sla.lu_solve(lu, rhs)
+        sol = solve(rhs)
         W[e0:e1] = sol[rc * thT:(rc + 1) * thT].T
     return W
 
@@ -253,12 +308,11 @@ def predict_cells(Q: np.ndarray, w, dt: float, cells) -> np.ndarray:
     d, M = w["dim"], w["M"]
     nb = M + 1
     thT = nb ** (d + 1)
-    A, B = region_system(d, M, nu_of(w, dt))
-    lu = sla.lu_factor(A)
+    solve, B = region_solver(d, M, nu_of(w, dt))
     rc = (3 ** d - 1) // 2
     cells = np.asarray(cells)
     X = gather_cells(Q, w, cells)
-    sol = sla.lu_solve(lu, B @ X.reshape(len(cells), -1).T)
+    sol = solve(B @ X.reshape(len(cells), -1).T)
     return sol[rc * thT:(rc + 1) * thT].T
 
 

@@ -190,6 +190,52 @@ __global__ void __launch_bounds__(128) correct_linear_kernel(double* __restrict_
   for (int s = 0; s < THS; ++s) q[s] = q[s] + dq[s];
 }
 
+// The same correction with one thread per (cell, mode) output, for large theta_S (3D,
+// degree >= 4) where a thread holding a whole cell's time mean would spill.  Mode s has the
+// digit a = s_d along dimension d and lies on the fibre base + b st of that dimension; every
+// sum runs in the order of correct_linear_kernel (volume term, then the two face values,
+// each face value from the same traces by face_value), so both neighbours of a face apply
+// bitwise the same flux and the result equals correct_linear_kernel's bit for bit.
+template <int DIM, int NB>
+__global__ void __launch_bounds__(128) correct_modes_kernel(double* __restrict__ Q,
+                                                            const double* __restrict__ Wb,
+                                                            int wstride, int nx, int ny, int nz,
+                                                            long long ncell, CorrParams cp) {
+  constexpr int THS = ipow_c(NB, DIM);
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncell * THS) return;
+  const long long e = i / THS;
+  const int s = (int)(i - e * THS);
+  const Coords c = cell_coords(e, nx, ny);
+  const double* w = Wb + e * wstride;
+  double dq = 0.0;
+#pragma unroll
+  for (int dd = 0; dd < DIM; ++dd) {
+    const int st = dd == 0 ? 1 : (dd == 1 ? NB : NB * NB);
+    const int a = (s / st) % NB, base = s - a * st;
+    double acc = 0.0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (b < a && ((a + b) & 1)) acc = fma(cp.D[a * kMaxNB + b], w[base + b * st], acc);
+    dq = fma(cp.nu[dd], acc, dq);
+    double trp = 0.0, trm = 0.0, nbp = 0.0, nbm = 0.0;
+    const double* wr = Wb + neighbour<DIM>(c, dd == 0, dd == 1, dd == 2, nx, ny, nz) * wstride;
+    const double* wl = Wb + neighbour<DIM>(c, -(dd == 0), -(dd == 1), -(dd == 2), nx, ny, nz) * wstride;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      trp = fma(cp.ep[b], w[base + b * st], trp);
+      trm = fma(cp.em[b], w[base + b * st], trm);
+      nbm = fma(cp.em[b], wr[base + b * st], nbm);
+      nbp = fma(cp.ep[b], wl[base + b * st], nbp);
+    }
+    const double fp = face_value(trp, nbm, cp.nup[dd], cp.num[dd]);
+    const double fm = face_value(nbp, trm, cp.nup[dd], cp.num[dd]);
+    dq = fma(-cp.ep[a], fp, dq);
+    dq = fma(cp.em[a], fm, dq);
+  }
+  Q[e * THS + s] = Q[e * THS + s] + dq;
+}
+
 // A whole run of n steps of a small 1D mesh in one CTA: the state and the time means stay in
 // shared memory, each step is the prediction (the same sums as predict_fp64_kernel) and the
 // correction (the same sums as correct_linear_kernel<1, NB>) separated by barriers.  Removes
@@ -288,9 +334,15 @@ template <int DIM, int NB>
 cudaError_t correct_dispatch(const Grid& g, double* Q, const double* Wb, int wstride,
                              const CorrParams& cp, cudaStream_t s) {
   const int threads = 128;
-  const unsigned blocks = (unsigned)((g.ncell + threads - 1) / threads);
-  correct_linear_kernel<DIM, NB><<<blocks, threads, 0, s>>>(Q, Wb, wstride, g.n[0], g.n[1], g.n[2],
-                                                             g.ncell, cp);
+  if constexpr (DIM == 3 && NB >= 5) {
+    const unsigned blocks = (unsigned)((g.ncell * ipow_c(NB, DIM) + threads - 1) / threads);
+    correct_modes_kernel<DIM, NB><<<blocks, threads, 0, s>>>(Q, Wb, wstride, g.n[0], g.n[1],
+                                                             g.n[2], g.ncell, cp);
+  } else {
+    const unsigned blocks = (unsigned)((g.ncell + threads - 1) / threads);
+    correct_linear_kernel<DIM, NB><<<blocks, threads, 0, s>>>(Q, Wb, wstride, g.n[0], g.n[1],
+                                                              g.n[2], g.ncell, cp);
+  }
   return cudaGetLastError();
 }
 
@@ -328,6 +380,11 @@ cudaError_t launch_predict_fp64(const Grid& g, int nb, const double* Q, const do
     }
   } else if (g.dim == 3) {
     RIDG_DISPATCH_NB(3, predict_dispatch_ch, g, Q, P, nout, W, wstride, s)
+    switch (nb) {
+      case 5: return predict_dispatch_ch<3, 5>(g, Q, P, nout, W, wstride, s);
+      case 6: return predict_dispatch_ch<3, 6>(g, Q, P, nout, W, wstride, s);
+      default: break;
+    }
   }
   return cudaErrorInvalidValue;
 }
@@ -381,6 +438,11 @@ cudaError_t launch_correct_linear(const Grid& g, int nb, double* Q, const double
     }
   } else if (g.dim == 3) {
     RIDG_DISPATCH_NB(3, correct_dispatch, g, Q, Wbar, wstride, cp, s)
+    switch (nb) {
+      case 5: return correct_dispatch<3, 5>(g, Q, Wbar, wstride, cp, s);
+      case 6: return correct_dispatch<3, 6>(g, Q, Wbar, wstride, cp, s);
+      default: break;
+    }
   }
   return cudaErrorInvalidValue;
 }

@@ -142,6 +142,68 @@ def project_tensor(f, w: dict, nb: int, nq: int | None = None, m: int = 1,
     return out
 
 
+def paper_bump(*xs, c: float = 0.5, omega: float = 1.0 / 3.0):
+    """The C-infinity bump of the paper's advection studies (eqs. adv1d, adv2d, adv3d):
+    exp(1 / (|x - c|^2 - omega^2)) inside the ball |x - c| < omega, 0 outside."""
+    r2 = sum((np.asarray(x) - c) ** 2 for x in xs)
+    out = np.zeros(np.broadcast(*xs).shape)
+    m = r2 < omega * omega
+    out[m] = np.exp(1.0 / (r2[m] - omega * omega))
+    return out
+
+
+def project_bump(w: dict, nb: int, nq: int = 20, c: float = 0.5,
+                 omega: float = 1.0 / 3.0) -> np.ndarray:
+    """L2 projection of paper_bump onto the orthonormal tensor basis of w's mesh (dim 1-3),
+    shape (cells, nb^d), by tensor Gauss quadrature with nq points per dimension summed one
+    dimension at a time; cells that do not meet the bump's ball stay zero."""
+    d = w["dim"]
+    n = list(w["n"])
+    xi, wq = npleg.leggauss(nq)
+    Vw = _legendre_orthonormal(nb, xi) * wq[None, :]      # (nb, nq)
+    h = [(w["hi"][k] - w["lo"][k]) / n[k] for k in range(d)]
+    lo = [w["lo"][k] for k in range(d)]
+    pts = [lo[k] + (np.arange(n[k]) + 0.5)[:, None] * h[k] + 0.5 * h[k] * xi[None, :]
+           for k in range(d)]                             # pts[k][i, q]
+    # squared distance from c to the nearest point of each cell, per axis
+    near = [np.maximum(0.0, np.abs(lo[k] + (np.arange(n[k]) + 0.5) * h[k] - c) - 0.5 * h[k]) ** 2
+            for k in range(d)]
+    out = np.zeros((int(np.prod(n)), nb ** d))
+    if d == 1:
+        vals = paper_bump(pts[0], c=c, omega=omega)      # (i, q)
+        out[:] = 0.5 * vals @ Vw.T
+        return out
+    if d == 2:
+        for j in range(n[1]):
+            if near[1][j] >= omega * omega:
+                continue
+            X = pts[0][:, None, :]                        # (i, 1, qx)
+            Y = pts[1][j][None, :, None]                  # (1, qy, 1)
+            vals = paper_bump(X, Y, c=c, omega=omega)     # (i, p, q)
+            t = np.tensordot(vals, Vw, axes=([2], [1]))   # (i, p, bx)
+            t = np.tensordot(t, Vw, axes=([1], [1]))      # (i, bx, by)
+            out[j * n[0]:(j + 1) * n[0]] = 0.25 * t.transpose(0, 2, 1).reshape(n[0], nb * nb)
+        return out
+    for k in range(n[2]):
+        if near[2][k] >= omega * omega:
+            continue
+        js = [j for j in range(n[1]) if near[2][k] + near[1][j] < omega * omega]
+        if not js:
+            continue
+        X = pts[0][None, :, None, None, :]                # (1, i, 1, 1, qx)
+        Y = pts[1][js][:, None, None, :, None]            # (j, 1, 1, qy, 1)
+        Z = pts[2][k][None, None, :, None, None]          # (1, 1, qz, 1, 1)
+        vals = paper_bump(X, Y, Z, c=c, omega=omega)      # (j, i, o, p, q)
+        t = np.tensordot(vals, Vw, axes=([4], [1]))       # (j, i, o, p, bx)
+        t = np.tensordot(t, Vw, axes=([3], [1]))          # (j, i, o, bx, by)
+        t = np.tensordot(t, Vw, axes=([2], [1]))          # (j, i, bx, by, bz)
+        t = 0.125 * t.transpose(0, 1, 4, 3, 2).reshape(len(js), n[0], nb ** 3)
+        for jj, j in enumerate(js):
+            e0 = (k * n[1] + j) * n[0]
+            out[e0:e0 + n[0]] = t[jj]
+    return out
+
+
 # ---------------------------------------------------------------------------
 # initial data and exact solutions
 # ---------------------------------------------------------------------------

@@ -395,3 +395,43 @@ def test_paper_1d_table_high_degree(R, M):
         checked += 1
     assert checked >= 1
 
+
+
+def test_3d_degree4_matches_oracle(R):
+    """3D Q4 (theta_T = 625, a region system of 16,875 unknowns: the oracle's sparse LU) on a
+    3^3 mesh, every velocity sign: the full prediction and one step against the oracle."""
+    w = _w(3, (3, 3, 3), 4, (1.0, 0.7, -0.3), cfl=0.3)
+    s = _solver(R, w)
+    rng = np.random.default_rng(17)
+    q = rng.standard_normal((s.cells, s.theta_s))
+    s.set_state(q)
+    dt = s.info()["dt"]
+    W = s.predict()
+    Wo = OL.predict(q, w, dt)
+    assert _rel(W, Wo) < TOL_STEP
+    s.set_state(q)
+    s.step(1)
+    assert _rel(s.get_state(), OL.correct(q, Wo[:, :s.theta_s], w, dt)) < TOL_STEP
+    s.close()
+
+
+@pytest.mark.parametrize("M", [4, 5])
+def test_3d_high_degree_invariants(R, M):
+    """3D Q4-Q5 (the thread-per-mode correction): a constant state stays constant, and the
+    mass of random data is conserved to round-off over several steps."""
+    w = _w(3, (4, 5, 3), M, (-0.6, 1.0, 0.4), cfl=0.3)
+    s = _solver(R, w)
+    thS = s.theta_s
+    q = np.zeros((s.cells, thS))
+    q[:, 0] = 1.3
+    s.set_state(q)
+    s.step(3)
+    out = s.get_state()
+    assert np.abs(out[:, 0] - 1.3).max() < 1e-12 and np.abs(out[:, 1:]).max() < 1e-12
+    rng = np.random.default_rng(23)
+    q = rng.standard_normal((s.cells, thS))
+    s.set_state(q)
+    s.step(4)
+    out = s.get_state()
+    assert abs(out[:, 0].sum() - q[:, 0].sum()) < 1e-12 * np.abs(q[:, 0]).sum()
+    s.close()

@@ -83,3 +83,76 @@ def test_upwind_operator_matches_oracle_region_solve(exe, d, M, nu, tmp_path):
     for r in range(len(offs)):
         if r not in seen:
             assert np.abs(G[:, r * thS:(r + 1) * thS]).max() <= 1e-13 * scale
+
+
+def _step_symbol(d, M, nu, P, lo, cnt, theta):
+    """Amplification matrix of one linear RIDG step (prediction with the host operator P over
+    the upwind box, then the correction of Sec. 2.3) for the Fourier mode e^{i theta . j}."""
+    nb = M + 1
+    thS = nb ** d
+    D = basis.deriv_matrix(nb)
+    ep, em = basis.trace_plus(nb), basis.trace_minus(nb)
+
+    def along(dd, X):
+        mats = [np.eye(nb)] * d
+        mats[dd] = X
+        return basis.kron_x_fastest(mats)
+
+    n = cnt[0] * cnt[1] * cnt[2]
+    Wb = np.zeros((thS, thS), dtype=complex)
+    for i in range(n):
+        o = (lo[0] + i % cnt[0], lo[1] + (i // cnt[0]) % cnt[1], lo[2] + i // (cnt[0] * cnt[1]))
+        Wb += P[:thS, i * thS:(i + 1) * thS] * np.exp(1j * sum(theta[k] * o[k] for k in range(d)))
+    G = np.eye(thS, dtype=complex)
+    for dd in range(d):
+        ph = np.exp(1j * theta[dd])
+        nup, num = max(nu[dd], 0.0), min(nu[dd], 0.0)
+        # face value at +1/2: nu+ tr+(W_i) + nu- tr-(W_{i+e}), distributed with phi(+1); at
+        # -1/2 the same value shifted by -e, distributed with phi(-1)
+        Fp = along(dd, np.outer(ep, ep) * nup + np.outer(ep, em) * num * ph)
+        Fm = along(dd, (np.outer(em, ep) * nup + np.outer(em, em) * num * ph) / ph)
+        G = G + (nu[dd] * along(dd, D) - Fp + Fm) @ Wb
+    return G
+
+
+def test_step_symbol_matches_oracle_step(exe, tmp_path):
+    # the symbol built from the host operator equals the oracle's own step on a Fourier mode
+    d, M, N = 3, 1, 4
+    vel = (1.0, -0.7, 0.4)
+    w = dict(flux="advection", dim=d, n=(N,) * d, M=M, vel=vel, lo=(0.0,) * d, hi=(1.0,) * d)
+    dt = 0.6 / N
+    nu = np.asarray(vel) * dt * N
+    lo, cnt, n, P = _operator(exe, d, M, nu, tmp_path)
+    nb = M + 1
+    thS, thT = nb ** d, nb ** (d + 1)
+    P = P.reshape(thT, n * thS)
+    j = np.stack(np.meshgrid(*[np.arange(N)] * d, indexing="ij"), -1).reshape(-1, d)[:, ::-1]
+    for k in ((1, 2, 3), (0, 1, 0), (3, 3, 1)):
+        theta = 2 * np.pi * np.asarray(k) / N
+        phase = np.exp(1j * (j @ theta))
+        Go = np.zeros((thS, thS), dtype=complex)
+        for s in range(thS):
+            e = np.zeros(thS)
+            e[s] = 1.0
+            out = OL.step(np.real(phase)[:, None] * e, w, dt) + \
+                1j * OL.step(np.imag(phase)[:, None] * e, w, dt)
+            Go[:, s] = out[0]                # cell 0 carries the mode's amplitude
+        np.testing.assert_allclose(_step_symbol(d, M, nu, P, lo, cnt, theta), Go, atol=1e-13)
+
+
+def test_3d_cfl_readings(exe, tmp_path):
+    # The paper's 3D runs use nu = 0.6 with a = (1, 1, 1).  Per direction (dt = nu h / max
+    # |a_d|) the step grows at degree 3 (spectral radius 1.04 on this 8^3 wavenumber grid,
+    # 1.048 on a 12^3 one: a few percent per step); as dt = nu h / sum_d |a_d| (0.2 per
+    # direction) it is stable.
+    d, M = 3, 3
+    grid = 2 * np.pi * np.arange(8) / 8
+    rho = {}
+    for nud in (0.6, 0.2):
+        nu = np.full(3, nud)
+        lo, cnt, n, P = _operator(exe, d, M, nu, tmp_path)
+        P = P.reshape((M + 1) ** 4, n * (M + 1) ** 3)
+        rho[nud] = max(np.abs(np.linalg.eigvals(_step_symbol(d, M, nu, P, lo, cnt, th))).max()
+                       for th in itertools.product(grid, repeat=3))
+    assert rho[0.6] > 1.03, rho
+    assert rho[0.2] <= 1.0 + 1e-10, rho

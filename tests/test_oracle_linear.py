@@ -208,3 +208,23 @@ def test_error_metric_definition():
     ref = np.sqrt((X[:, ~inside] ** 2).sum() / (X ** 2).sum())
     assert abs(e - ref) < 1e-15
     assert oerr.l2_relative_error(Q + 1.0, X, 2, 2) > e
+
+
+@pytest.mark.parametrize("d,M,nu", [(1, 4, (0.9,)), (2, 2, (0.35, -0.2)), (3, 1, (0.3, 0.0, -0.6))])
+def test_sparse_region_system_equals_dense(d, M, nu):
+    # the sparse form (used when the dense region matrix does not fit) holds the same
+    # matrices as the dense assembly of eq. pred_full_system
+    A, B = L.region_system(d, M, np.asarray(nu))
+    As, Bs = L.region_system_sparse(d, M, np.asarray(nu))
+    np.testing.assert_allclose(As.toarray(), A, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(Bs.toarray(), B, rtol=0, atol=1e-15)
+
+
+def test_sparse_region_solve_predicts_like_dense(monkeypatch):
+    w = _w(3, 3, 1, (1.0, -0.7, 0.3))
+    rng = np.random.default_rng(5)
+    Q = rng.standard_normal((27, 8))
+    W = L.predict(Q, w, 0.05)
+    monkeypatch.setattr(L, "DENSE_MAX_UNKNOWNS", 0)
+    Ws = L.predict(Q, w, 0.05)
+    np.testing.assert_allclose(Ws, W, rtol=0, atol=1e-12 * np.abs(W).max())
