@@ -133,7 +133,9 @@ void ridg_destroy(ridg_t* h);
 /* ----- state ------------------------------------------------------------------------ */
 
 /* Copy the state in (canonical layout, cells * m * theta_S doubles); `on_device` != 0
- * means q is a device pointer.  Resets t = 0 and the step count.  For a nonlinear flux
+ * means q is a device pointer.  A page-locked host buffer (16-byte aligned) is read by
+ * the GPU's SMs directly, copy and finite check in one pass; other host memory goes
+ * through a copy-engine copy.  Resets t = 0 and the step count.  For a nonlinear flux
  * dt = cfl h_min / (largest wave speed of q) is computed here unless ridg_set_dt fixed
  * it.  RIDG_ENONFINITE if q holds a NaN or Inf.  Synchronous.                          */
 int ridg_set_state(ridg_t* h, const double* q, int on_device);

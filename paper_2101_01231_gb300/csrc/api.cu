@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -559,15 +560,32 @@ void ridg_destroy(ridg_t* h) {
   delete h;
 }
 
+// A host pointer the device can dereference as it stands: page-locked memory under unified
+// addressing (cudaHostAlloc, cudaHostRegister, torch's pin_memory).
+static bool pinned_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // not a CUDA pointer: clear the sticky-free error state
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
 int ridg_set_state(ridg_t* h, const double* q, int on_device) {
   if (check_handle(h) || !q) return RIDG_EINVAL;
   const size_t bytes = (size_t)h->ncell * h->m * h->thS * sizeof(double);
-  RIDG_CUDA(h, cudaMemcpyAsync(h->Q, q, bytes,
-                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                               h->stream));
+  const long long count = (long long)(bytes / sizeof(double));
   RIDG_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
-  RIDG_CUDA(h, ridg::launch_finite_check(h->Q, (long long)(bytes / sizeof(double)), h->status,
-                                         h->stream));
+  if (!on_device && pinned_host(q) && aligned16(q) && aligned16(h->Q)) {
+    // pinned host memory: the SMs read it over C2C, copy and finite check in one pass
+    RIDG_CUDA(h, ridg::launch_ingest(q, h->Q, count, h->status, h->stream));
+  } else {
+    RIDG_CUDA(h, cudaMemcpyAsync(h->Q, q, bytes,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 h->stream));
+    RIDG_CUDA(h, ridg::launch_finite_check(h->Q, count, h->status, h->stream));
+  }
   int flag = 0;
   RIDG_CUDA(h, cudaMemcpyAsync(&flag, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   RIDG_CUDA(h, cudaStreamSynchronize(h->stream));

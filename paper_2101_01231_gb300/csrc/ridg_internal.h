@@ -205,6 +205,10 @@ cudaError_t launch_l2_partials(const double* Q, const double* X, long long ncell
                                int nb, double* out, int nblocks, cudaStream_t s);
 // flag[0] |= 1 if any entry of q is not finite
 cudaError_t launch_finite_check(const double* q, long long count, int* flag, cudaStream_t s);
+// dev[0..count) = host[0..count) read by the SMs from a pinned (device-accessible) host buffer,
+// *flag |= 1 if any value is not finite; both pointers 16-byte aligned
+cudaError_t launch_ingest(const double* host, double* dev, long long count, int* flag,
+                          cudaStream_t s);
 
 }  // namespace ridg
 

@@ -435,3 +435,35 @@ def test_3d_high_degree_invariants(R, M):
     out = s.get_state()
     assert abs(out[:, 0].sum() - q[:, 0].sum()) < 1e-12 * np.abs(q[:, 0]).sum()
     s.close()
+
+
+def test_set_state_from_pinned_host_memory(R):
+    """A page-locked host buffer is read by the SMs (copy and finite check fused): the same
+    state and the same steps as from pageable memory, and a NaN is still refused."""
+    import torch
+    w = _w(2, (33, 17), 3, (1.0, -0.5))
+    s = _solver(R, w)
+    rng = np.random.default_rng(29)
+    q = rng.standard_normal((s.cells, s.theta_s))
+    s.set_state(q)                                   # pageable: copy engine
+    s.step(3)
+    ref = s.get_state()
+    qp = torch.from_numpy(q.copy()).pin_memory()     # page-locked: read by the SMs
+    s.set_state(qp.numpy())
+    assert np.array_equal(s.get_state(), q)
+    s.step(3)
+    assert np.array_equal(s.get_state(), ref)
+    qp[5, 3] = float("nan")
+    with pytest.raises(R.RidgError):
+        s.set_state(qp.numpy())
+    s.close()
+    # an odd number of values (the kernel's scalar tail) and a buffer off the 16-byte grid
+    # (the copy-engine path)
+    w1 = _w(1, (7,), 0, (0.8,))
+    s1 = _solver(R, w1)
+    big = torch.from_numpy(rng.standard_normal(8)).pin_memory()
+    s1.set_state(big.numpy()[:7].reshape(7, 1))
+    assert np.array_equal(s1.get_state(), big.numpy()[:7].reshape(7, 1))
+    s1.set_state(big.numpy()[1:8].reshape(7, 1))
+    assert np.array_equal(s1.get_state(), big.numpy()[1:8].reshape(7, 1))
+    s1.close()
