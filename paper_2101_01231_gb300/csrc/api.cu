@@ -46,7 +46,7 @@ void dev_free(ridg_t* h, void* p) {
     cudaFree(p);
 }
 
-int max_nb(int dim) { return dim == 1 ? 12 : (dim == 2 ? 5 : 6); }
+int max_nb(int dim) { return dim == 1 ? 12 : 6; }
 
 Grid grid_of(const ridg_t* h) {
   Grid g;

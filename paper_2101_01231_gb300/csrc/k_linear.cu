@@ -376,6 +376,7 @@ cudaError_t launch_predict_fp64(const Grid& g, int nb, const double* Q, const do
     RIDG_DISPATCH_NB(2, predict_dispatch_ch, g, Q, P, nout, W, wstride, s)
     switch (nb) {
       case 5: return predict_dispatch_ch<2, 5>(g, Q, P, nout, W, wstride, s);
+      case 6: return predict_dispatch_ch<2, 6>(g, Q, P, nout, W, wstride, s);
       default: break;
     }
   } else if (g.dim == 3) {
@@ -434,6 +435,7 @@ cudaError_t launch_correct_linear(const Grid& g, int nb, double* Q, const double
     RIDG_DISPATCH_NB(2, correct_dispatch, g, Q, Wbar, wstride, cp, s)
     switch (nb) {
       case 5: return correct_dispatch<2, 5>(g, Q, Wbar, wstride, cp, s);
+      case 6: return correct_dispatch<2, 6>(g, Q, Wbar, wstride, cp, s);
       default: break;
     }
   } else if (g.dim == 3) {

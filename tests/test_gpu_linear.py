@@ -17,6 +17,7 @@ CASES = [
     (2, (12, 10), 3, (1.0, 0.5)),
     (2, (3, 3), 2, (-0.4, 1.0)),
     (2, (17, 9), 4, (0.7, -0.9)),
+    (2, (9, 7), 5, (-0.6, 1.0)),
     (3, (6, 5, 4), 2, (1.0, 0.7, 0.3)),
     (3, (3, 3, 3), 3, (-1.0, 0.2, 0.5)),
     (3, (4, 4, 5), 1, (-0.3, -0.6, 0.9)),
