@@ -7,7 +7,9 @@
  *               system on its region R_i of 3^d vertex neighbours (eq. region) is solved
  *               and only the centre cell's space-time coefficients W_i are kept;
  *               for a linear flux this is a precomputed region-to-cell operator applied
- *               to every cell, for a nonlinear flux a Newton iteration (Sec. 3) with the
+ *               to every cell (over the region cells upstream of it, on which alone the
+ *               centre depends with upwind face values), for a nonlinear flux a Newton
+ *               iteration (Sec. 3) with the
  *               quasi-quadrature-free Jacobian (eqs. Jacproj, Jacobian2);
  *   correction  (Sec. 2.3): Q^{n+1}_i = Q^n_i + volume integral of grad Phi . F(w_i)
  *               - surface integral of the Rusanov flux, both from the predicted W.
@@ -117,12 +119,15 @@ typedef struct {
 /* ----- lifecycle -------------------------------------------------------------------- */
 
 /* Build the tables and operators for degree `order` (M >= 0) and allocate device state.
- * Linear flux: the region system of eq. pred_full_system (Sec. 2.2) is assembled and
- * LU-factored on the host in FP64 once, and the centre rows of its solution operator
+ * Linear flux: the region system of eq. pred_full_system (Sec. 2.2) is solved on the host
+ * in FP64 once -- by block substitution over the region cells upstream of the centre
+ * (offsets {-1, 0} along a_d > 0, {0, +1} along a_d < 0, {0} where a_d = 0; the others do
+ * not reach the centre) -- and the centre rows of its solution operator over those cells
  * (and their time mean) are copied to the device.  Nonlinear flux: the quadrature and
  * quasi-quadrature-free tables of Sec. 3 are built.  dt is set from `cfl` for advection
  * (dt = cfl h_min / max|a_d|); for nonlinear flux it is set by ridg_set_state.
- * Supported: ADVECTION d = 1..3; BURGERS d = 2; EULER d = 2.  `opt` may be NULL.
+ * Supported: ADVECTION d = 1 (M <= 11), d = 2, 3 (M <= 5; the mixed precisions M <= 3 in
+ * 2D, M <= 2 in 3D); BURGERS d = 2 (M <= 4); EULER d = 2 (M <= 2).  `opt` may be NULL.
  * On success *out owns the new handle.                                                 */
 int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double cfl,
                 const ridg_options* opt, ridg_t** out);
