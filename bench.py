@@ -119,6 +119,37 @@ def cpu_oracle(w, seconds, steps=None):
                        f"numpy/scipy on all host cores)")
 
 
+def cpu_oracle_sampled(w, q, nsample=4096, seed=0):
+    """One oracle step of w as it stands, estimated from timed parts: the region system's
+    factorisation (once per step), the region solves of a seeded sample of cells scaled to
+    all cells, and the correction of Sec. 2.3 timed on the whole mesh."""
+    from oracle import linear as OL
+    cells = int(np.prod(w["n"]))
+    thS = (w["M"] + 1) ** w["dim"]
+    dt, _ = OL.advection_time_step(w, T=T_FINAL)
+    sample = np.sort(np.random.default_rng(seed).choice(cells, size=min(nsample, cells),
+                                                        replace=False))
+    t0 = time.perf_counter()
+    OL.region_solver(w["dim"], w["M"], OL.nu_of(w, dt))
+    t_factor = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    W = OL.predict_cells(q, w, dt, sample)     # its own factorisation + the sample's solves
+    t_pred = time.perf_counter() - t0
+    Wbar = np.zeros((cells, thS))
+    Wbar[sample] = W[:, :thS]
+    t0 = time.perf_counter()
+    OL.correct(q, Wbar, w, dt)
+    t_corr = time.perf_counter() - t0
+    per_step = t_factor + max(t_pred - t_factor, 0.0) / len(sample) * cells + t_corr
+    dof = cells * thS
+    return dict(value=dof / per_step, unit="element-DOF updates/s", cores=os.cpu_count(),
+                kind="oracle", seconds=round(t_factor + t_pred + t_corr, 3),
+                extrapolated_step_s=per_step,
+                sample=f"one oracle step of {w['name']} ({cells} cells): the factorisation, "
+                       f"the region solves of {len(sample)} seeded cells scaled to all cells, "
+                       f"and the correction on the whole mesh (numpy/scipy, all host cores)")
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -156,7 +187,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 # 3D: the tensor-core time-mean prediction at 96^3, Q2
 # ---------------------------------------------------------------------------------------
-def mixed3d_section(R, I, steps, warmup):
+def mixed3d_section(R, I, steps, warmup, cpu=False):
     """2D's split-operand tensor-core prediction in 3D (96^3, Q2, product of sines + seeded
     noise; the 191 MB state is larger than L2, so no flush is needed), with the FP64
     correction, and the FP64 path beside it."""
@@ -216,6 +247,8 @@ def mixed3d_section(R, I, steps, warmup):
                              "tensor_peak_tflops": bf16,
                              "algorithmic_tflops": 2.0 * thS * K * cells / (p["predict_ms"] * 1e-3) / 1e12}
         out[tag] = r
+    if cpu:
+        out["cpu_oracle"] = cpu_oracle_sampled(w, q)
     return out
 
 
@@ -821,7 +854,8 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_oracle(w, args.cpu_seconds)
     if args.mixed3d_steps > 0:
-        line["mixed3d"] = mixed3d_section(R, I, args.mixed3d_steps, args.warmup)
+        line["mixed3d"] = mixed3d_section(R, I, args.mixed3d_steps, args.warmup,
+                                          cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline))
     if args.newton_steps > 0:
         line["newton"] = newton_section(R, I, args.newton_steps, 8 if args.no_cpu_baseline else 16)
     if args.adv1d_reps > 0:
