@@ -51,7 +51,8 @@ def _operator(exe, d, M, nu, tmp_path):
 CASES = [
     (1, 3, (0.9,)), (1, 6, (-0.45,)), (1, 2, (0.0,)),
     (2, 1, (0.35, 0.175)), (2, 3, (0.35, 0.175)), (2, 2, (-0.3, 0.2)), (2, 3, (0.3, -0.7)),
-    (2, 2, (0.0, -0.4)), (3, 1, (0.3, 0.21, 0.09)), (3, 2, (0.3, -0.21, 0.0)),
+    (2, 2, (0.0, -0.4)), (2, 4, (0.35, -0.35)), (2, 5, (-0.35, 0.2)),
+    (3, 1, (0.3, 0.21, 0.09)), (3, 2, (0.3, -0.21, 0.0)),
     (3, 1, (-0.6, -0.6, 0.6)),
 ]
 
