@@ -196,7 +196,10 @@ def region_solver(d: int, M: int, nu):
         lu = sla.lu_factor(A)
         return (lambda rhs: sla.lu_solve(lu, rhs)), B
     A, B = region_system_sparse(d, M, nu)
-    lu = spla.splu(A)
+    # unknowns in the order of the definition (region element, then time, then space): the
+    # matrix is block-structured by region element, and this order keeps the LU's fill
+    # inside its blocks (3D Q5: 2.2e8 entries, factored in ~1.5 minutes)
+    lu = spla.splu(A, permc_spec="NATURAL")
     return (lambda rhs: lu.solve(np.asarray(rhs))), B
 
 
