@@ -32,6 +32,14 @@ WORKLOADS = {
     "adv3d_n96_q2": dict(flux="advection", dim=3, n=(96, 96, 96), M=2,
                          vel=(1.0, 0.7, 0.3), lo=(0.0,) * 3, hi=(1.0,) * 3,
                          cfl=0.30, T=1.0, ic="sin+noise"),
+    # the paper's 2D and 3D advection studies (eqs. adv2d, adv3d): the C-infinity bump
+    # (paper_bump), a = (1, ..., 1), degree 5, its nu = 0.7 (2D) / 0.6 (3D) taken as
+    # dt = nu h / sum_d |a_d|
+    "adv2d_bump_n60_q5": dict(flux="advection", dim=2, n=(60, 60), M=5, vel=(1.0, 1.0),
+                              lo=(0.0, 0.0), hi=(1.0, 1.0), cfl=0.35, T=1.0, ic="bump"),
+    "adv3d_bump_n48_q5": dict(flux="advection", dim=3, n=(48, 48, 48), M=5,
+                              vel=(1.0, 1.0, 1.0), lo=(0.0,) * 3, hi=(1.0,) * 3, cfl=0.2,
+                              T=1.0, ic="bump"),
     # 2D compressible Euler, isentropic vortex on [0,10]^2, 512^2 cells, Q2
     "euler2d_n512_q2": dict(flux="euler", dim=2, n=(512, 512), M=2, gamma=1.4,
                             lo=(0.0, 0.0), hi=(10.0, 10.0), cfl=0.35, T=1.0,
@@ -222,6 +230,8 @@ def advection_noise(w: dict, seed: int = 0) -> np.ndarray:
 def initial_state(w: dict, seed: int = 0) -> np.ndarray:
     """Initial coefficients Q^0 in the canonical layout, shape (cells, m * theta_S)."""
     nb = w["M"] + 1
+    if w["flux"] == "advection" and w["ic"] == "bump":
+        return np.ascontiguousarray(project_bump(w, nb, nq=16))
     if w["flux"] == "advection":
         q = project_separable([_sin2pi(0.0)] * w["dim"], w, nb)
         if w["ic"] == "sin+noise":
@@ -240,6 +250,13 @@ def exact_coefficients(w: dict, t: float, nb: int | None = None) -> np.ndarray:
     """Projection of the exact solution at time t onto Q(nb-1) cell-wise (default
     nb = M + 2, the Q(M+1) space the L2 error definition of Sec. 4 needs)."""
     nb = nb or w["M"] + 2
+    if w["flux"] == "advection" and w["ic"] == "bump":
+        # the bump carried by a t around the periodic unit domain: offered where a t is a
+        # whole number of periods, i.e. the bump is back at its start
+        shift = np.asarray(w["vel"][: w["dim"]], dtype=float) * t
+        if np.abs(shift - np.round(shift)).max() > 1e-12:
+            raise ValueError("bump: exact coefficients only where a t is a whole period")
+        return np.ascontiguousarray(project_bump(w, nb, nq=16))
     if w["flux"] == "advection":
         if w["ic"] != "sin":
             raise ValueError("exact coefficients are available for the noise-free data only")

@@ -26,3 +26,15 @@ def test_project_bump_matches_tensor_projection(d, n, nb):
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
     # cells that do not meet the ball are exactly zero in both
     assert np.count_nonzero(np.abs(got).max(axis=1)) == np.count_nonzero(np.abs(ref).max(axis=1))
+
+
+def test_bump_workloads():
+    for name in ("adv2d_bump_n60_q5", "adv3d_bump_n48_q5"):
+        w = I.workload(name, n=(6,) * I.WORKLOADS[name]["dim"], M=1)
+        q0 = I.initial_state(w)
+        assert q0.shape == (6 ** w["dim"], 2 ** w["dim"])
+        np.testing.assert_array_equal(q0, I.project_bump(w, 2, nq=16))
+        # a = (1, ..., 1): at t = 1 the bump is back at its start
+        np.testing.assert_array_equal(I.exact_coefficients(w, 1.0), I.project_bump(w, 3, nq=16))
+        with pytest.raises(ValueError):
+            I.exact_coefficients(w, 0.5)
