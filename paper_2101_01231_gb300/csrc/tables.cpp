@@ -228,39 +228,78 @@ bool linear_operator(int dim, int M, const double* nu, const RegionBox& box,
   P.assign((size_t)thT * K, 0.0);
   int o0[3] = {0, 0, 0};
   const int centre = box_index(o0);
+  // The theta_T right-hand sides e_(centre, c) in blocks of CB columns: every row operation
+  // below runs over a block's columns at once, so each box cell's LU factors are read once
+  // per block rather than once per column (each column's arithmetic is unchanged).
+  constexpr int CB = 32;
+  const int nblk = (thT + CB - 1) / CB;
 #pragma omp parallel for schedule(dynamic)
-  for (int c = 0; c < thT; ++c) {
-    std::vector<double> z((size_t)nc * thT, 0.0);
+  for (int blk = 0; blk < nblk; ++blk) {
+    const int c0 = blk * CB, cw = std::min(CB, thT - c0);
+    std::vector<double> z((size_t)nc * thT * CB, 0.0);  // z[i][l][cc], cc < cw
+    std::vector<double> y((size_t)thT * CB);
     for (int i : order) {
       int o[3];
       offsets(i, o);
-      double* zi = z.data() + (size_t)i * thT;
-      if (i == centre) zi[c] = 1.0;
+      double* zi = z.data() + (size_t)i * thT * CB;
+      if (i == centre)
+        for (int cc = 0; cc < cw; ++cc) zi[(size_t)(c0 + cc) * CB + cc] = 1.0;
       for (int dd = 0; dd < dim; ++dd) {
         if (o[dd] == 0) continue;
         int od[3] = {o[0], o[1], o[2]};
         od[dd] = 0;
-        const double* zd = z.data() + (size_t)box_index(od) * thT;
+        const double* zd = z.data() + (size_t)box_index(od) * thT * CB;
         const int st = ipow(nb, dd);
         const double nud = nu[dd];
         for (int l = 0; l < thT; ++l) {
           const int al = l / thS, s = l % thS, b2 = digit(s, dd), base = s - b2 * st;
-          double acc = 0.0;
+          double acc[CB] = {};
           for (int bd = 0; bd < nb; ++bd) {
             const double C = nud > 0 ? -nud * t.em[bd] * t.ep[b2] : nud * t.ep[bd] * t.em[b2];
-            acc += C * zd[al * thS + base + bd * st];
+            const double* zr = zd + (size_t)(al * thS + base + bd * st) * CB;
+            for (int cc = 0; cc < CB; ++cc) acc[cc] += C * zr[cc];
           }
-          zi[l] -= acc;
+          double* zl = zi + (size_t)l * CB;
+          for (int cc = 0; cc < CB; ++cc) zl[cc] -= acc[cc];
         }
       }
-      lu_solve(thT, LU[i].data(), perm[i], zi);
-    }
-    for (int i = 0; i < nc; ++i)
-      for (int s = 0; s < thS; ++s) {
-        double acc = 0.0;
-        for (int a = 0; a < nb; ++a) acc += z[(size_t)i * thT + a * thS + s] * t.em[a];
-        P[(size_t)c * K + i * thS + s] = acc;
+      // zi = (A_ii^T)^-1 zi with the factors of A_ii^T (P A = L U, perm[r] = original row)
+      const double* A = LU[i].data();
+      const std::vector<int>& pr = perm[i];
+      for (int r = 0; r < thT; ++r)
+        std::memcpy(y.data() + (size_t)r * CB, zi + (size_t)pr[r] * CB, sizeof(double) * CB);
+      for (int r = 0; r < thT; ++r) {
+        double* yr = y.data() + (size_t)r * CB;
+        const double* Ar = A + (size_t)r * thT;
+        for (int jj = 0; jj < r; ++jj) {
+          const double a = Ar[jj];
+          if (a == 0.0) continue;
+          const double* yj = y.data() + (size_t)jj * CB;
+          for (int cc = 0; cc < CB; ++cc) yr[cc] -= a * yj[cc];
+        }
       }
+      for (int r = thT - 1; r >= 0; --r) {
+        double* yr = y.data() + (size_t)r * CB;
+        const double* Ar = A + (size_t)r * thT;
+        for (int jj = r + 1; jj < thT; ++jj) {
+          const double a = Ar[jj];
+          if (a == 0.0) continue;
+          const double* yj = y.data() + (size_t)jj * CB;
+          for (int cc = 0; cc < CB; ++cc) yr[cc] -= a * yj[cc];
+        }
+        const double d = Ar[r];
+        for (int cc = 0; cc < CB; ++cc) yr[cc] /= d;
+      }
+      std::memcpy(zi, y.data(), sizeof(double) * (size_t)thT * CB);
+    }
+    for (int cc = 0; cc < cw; ++cc)
+      for (int i = 0; i < nc; ++i)
+        for (int s = 0; s < thS; ++s) {
+          double acc = 0.0;
+          for (int a = 0; a < nb; ++a)
+            acc += z[((size_t)i * thT + a * thS + s) * CB + cc] * t.em[a];
+          P[(size_t)(c0 + cc) * K + i * thS + s] = acc;
+        }
   }
   return true;
 }
