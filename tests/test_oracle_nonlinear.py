@@ -40,7 +40,7 @@ def test_euler_flux_jacobian_matches_finite_differences():
             assert np.abs(A[:, j] - fd).max() < 1e-6
 
 
-@pytest.mark.parametrize("d,M", [(1, 2), (2, 1), (2, 2)])
+@pytest.mark.parametrize("d,M", [(1, 2), (2, 1), (2, 2), (3, 1)])
 def test_burgers_qqf_equals_quadrature_and_fd(d, M):
     # F'(w) = w has degree M <= 2M, so the projection of eq. Jacproj is exact and the
     # quasi-quadrature-free Jacobian equals the quadrature one (eq. Jacobian); both
@@ -56,7 +56,7 @@ def test_burgers_qqf_equals_quadrature_and_fd(d, M):
     Jd = NL.jacobian(W, Q, fl, tb, lam, al, "quad")
     scale = np.abs(Jd).max()
     assert np.abs(Jq - Jd).max() < 1e-13 * scale
-    if d * M <= 2:
+    if d * M <= 3:
         Jfd = _fd_jacobian(W, Q, fl, tb, lam, al)
         assert np.abs(Jd - Jfd).max() < 1e-7 * scale
 
@@ -150,3 +150,49 @@ def test_euler_uniform_flow_is_preserved():
     assert cv.all()
     Q1 = NL.correct(Q, W, w, dt)
     assert np.abs(Q1 - Q).max() < 1e-13
+
+
+def _burgers3d(n, M):
+    w = dict(flux="burgers", dim=3, n=(n,) * 3, M=M, lo=(0.0,) * 3, hi=(1.0,) * 3, cfl=0.3)
+    f = lambda x, y, z: (0.3 + 0.1 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+                         * np.sin(2 * np.pi * z) + 0.05 * np.cos(2 * np.pi * (x + z)))
+    Q = I.project_tensor(f, w, M + 1)[:, 0, :]
+    return w, np.ascontiguousarray(Q)
+
+
+def test_newton_converges_quadratically_for_burgers_3d():
+    # the 3 x 3 x 3 region of a 3D Burgers state: the QQF Newton iteration (exact Jacobian
+    # for Burgers) converges quadratically, as in 2D
+    w, Q = _burgers3d(4, 1)
+    dt, _ = L.time_step(w, NL.max_speed(Q, w))
+    tb = NL.Tables(3, 1)
+    fl = NL.Burgers()
+    lam = dt / L.cell_sizes(w)
+    QR = L.gather_cells(Q, w, [21]).reshape(1, 27, 1, tb.thS)
+    W = np.zeros((1, 27, 1, tb.thT))
+    W[..., : tb.thS] = QR
+    _, al0 = NL.residual(W, QR, fl, tb, lam)
+    norms = []
+    for _ in range(4):
+        R, _ = NL.residual(W, QR, fl, tb, lam, al0)
+        J = NL.jacobian(W, QR, fl, tb, lam, al0, "qqf")
+        dW = np.linalg.solve(J, R.reshape(1, -1, 1)).reshape(R.shape)
+        W -= dW
+        norms.append(np.abs(dW).max())
+    assert norms[2] < 10 * norms[1] ** 2 + 1e-15
+    assert norms[3] < 1e-12
+
+
+def test_burgers_3d_constant_state_and_mass():
+    w, Q = _burgers3d(4, 1)
+    dt, _ = L.time_step(w, NL.max_speed(Q, w))
+    # a constant state is a fixed point of the prediction and of the correction
+    Qc = np.zeros_like(Q)
+    Qc[:, 0] = 0.4
+    Wc = NL.newton_predict(Qc, w, dt)
+    assert np.abs(NL.correct(Qc, Wc, w, dt) - Qc).max() < 1e-14
+    # the correction conserves the mean
+    W, it, cv = NL.newton_predict(Q, w, dt, return_iters=True, max_iters=8)
+    assert cv.all()
+    Q1 = NL.correct(Q, W, w, dt)
+    assert abs(Q1[:, 0].sum() - Q[:, 0].sum()) < 1e-14 * np.abs(Q[:, 0]).sum()
