@@ -53,7 +53,7 @@ CASES = [
     (2, 1, (0.35, 0.175)), (2, 3, (0.35, 0.175)), (2, 2, (-0.3, 0.2)), (2, 3, (0.3, -0.7)),
     (2, 2, (0.0, -0.4)), (2, 4, (0.35, -0.35)), (2, 5, (-0.35, 0.2)),
     (3, 1, (0.3, 0.21, 0.09)), (3, 2, (0.3, -0.21, 0.0)),
-    (3, 1, (-0.6, -0.6, 0.6)),
+    (3, 1, (-0.6, -0.6, 0.6)), (3, 3, (0.3, -0.21, 0.09)),
 ]
 
 
