@@ -187,18 +187,21 @@ int ridg_mass(ridg_t* h, double* mass);
 int ridg_l2_error(ridg_t* h, const double* x, int on_device, double* err);
 
 /* The same relative L2 error as ridg_l2_error for a state q (cells * m * (order+1)^dim) and
- * exact coefficients x (cells * m * (order+2)^dim), both already in device memory, with no
- * handle and no allocation of any kind.  The paper has no counterpart: this entry point is
- * for callers that cannot call cudaMalloc where they need the diagnostic -- code running
- * while another component captures the stream into a CUDA graph, code whose device memory
- * is owned by a pool that must see every allocation, and time-critical loops that cannot
- * afford the device synchronisation of cudaMalloc / cudaFree.  Its scratch is a fixed
- * file-scope device array of 1 MiB (65536 pairs of partial sums, one pair per 256 cells),
- * held by every GPU that loads the library until the process exits; larger problems
- * (more than 16,777,216 cells) are rejected with RIDG_ETOOBIG before any work.  The first
- * call on a device looks up the array's device address (make that first call before any
- * stream capture).  Work is issued on `stream` (NULL = legacy default stream) and the call
- * waits for it.  Every call shares the array: calls that overlap on the GPU race.        */
+ * exact coefficients x (cells * m * (order+2)^dim), both already in device memory on the
+ * current device, with no handle and no allocation of any kind.  The paper has no
+ * counterpart: this entry point is for callers that cannot call cudaMalloc where they need
+ * the diagnostic -- code whose device memory is owned by a pool or arena that must see
+ * every allocation, and time-critical loops that cannot afford the device synchronisation
+ * of cudaMalloc / cudaFree.  Its scratch is a fixed file-scope device array of 1 MiB (65536
+ * pairs of partial sums, one pair per 256 cells), held by every GPU that loads the library
+ * until the process exits; larger problems (more than 16,777,216 cells) are rejected with
+ * RIDG_ETOOBIG before any work.  The first call on a device looks up the array's device
+ * address and keeps it; after a cudaDeviceReset of that device the kept address is stale
+ * and the entry point must not be called again in that process.  Work is issued on
+ * `stream` (NULL = legacy default stream) and the call copies the result back and waits
+ * for it, so `stream` must not be capturing a CUDA graph: a capturing stream (or the legacy
+ * stream while another stream captures in global mode) is refused with RIDG_ESTATE before
+ * any work.  Every call shares the array: calls that overlap on the GPU race.            */
 int ridg_l2_error_noalloc(const double* q, const double* x, long long cells, int m, int dim,
                           int order, void* stream, double* err);
 

@@ -1,12 +1,12 @@
 // ridg_l2_error_noalloc: the relative L2 error for callers that cannot allocate device
 // memory.  Some callers are not allowed to call cudaMalloc at the point where they need
-// this diagnostic: code that runs while another component is capturing the stream into a
-// CUDA graph (a device allocation there is an error or breaks the capture), code whose
-// device memory is owned entirely by a pool or arena that must see every allocation, and
-// time-critical loops that cannot afford the implicit device synchronisation of
-// cudaMalloc / cudaFree.  This entry point therefore allocates nothing: its scratch (one
-// pair of partial sums per 256 cells, plus the final pair) lives in a file-scope
-// __device__ array of fixed size that every GPU loading the library keeps until exit.
+// this diagnostic: code whose device memory is owned entirely by a pool or arena that must
+// see every allocation, and time-critical loops that cannot afford the implicit device
+// synchronisation of cudaMalloc / cudaFree.  This entry point therefore allocates nothing:
+// its scratch (one pair of partial sums per 256 cells, plus the final pair) lives in a
+// file-scope __device__ array of fixed size that every GPU loading the library keeps until
+// exit.  The call reads its result back and waits on the caller's stream, so that stream
+// must not be capturing a CUDA graph; a capturing stream is refused before any work.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -95,7 +95,9 @@ __global__ void l2_final_kernel(double* __restrict__ part, long long nparts) {
   }
 }
 
-// the device address of the scratch array on the current device (set up once per device)
+// the device address of the scratch array on the current device, looked up once per device
+// with that device current; a cudaDeviceReset (which tears the module down) makes the cached
+// address stale, so a process that resets a device must not call this entry point after it
 double* scratch_for_current_device(int* status) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -123,10 +125,18 @@ extern "C" int ridg_l2_error_noalloc(const double* q, const double* x, long long
     return RIDG_EINVAL;
   const long long nparts = (cells + kThreads - 1) / kThreads;
   if (nparts > kMaxPartials) return RIDG_ETOOBIG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the read-back and the wait below are illegal on a capturing stream (and on the legacy
+  // stream while another stream captures in global mode): refuse before touching anything
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+  if (ce != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    if (ce != cudaSuccess) cudaGetLastError();  // not sticky; keep it out of later calls
+    return RIDG_ESTATE;
+  }
   int st = RIDG_OK;
   double* part = scratch_for_current_device(&st);
   if (!part) return st;
-  cudaStream_t s = (cudaStream_t)stream;
   l2_partials_kernel<<<(unsigned)nparts, kThreads, 0, s>>>(q, x, cells, m, dim, order + 1, part);
   l2_final_kernel<<<1, kThreads, 0, s>>>(part, nparts);
   if (cudaGetLastError() != cudaSuccess) return RIDG_ECUDA;

@@ -258,14 +258,30 @@ def ridg_check_bounded_wait(stream=None):
 
 
 def ridg_l2_error_noalloc(q, x, cells, m, dim, order, stream=None):
-    """Relative L2 error of device arrays q and x with no device allocation (fixed scratch)."""
+    """Relative L2 error of device arrays q and x with no device allocation (fixed scratch).
+
+    q holds cells * m * (order+1)^dim and x cells * m * (order+2)^dim doubles, both on the
+    current CUDA device (the C side launches there and uses that device's scratch);
+    `stream` is a torch.cuda.Stream, a raw cudaStream_t as int, or None (legacy stream)."""
+    import torch
     pq, dq = _ptr(q)
     px, dx = _ptr(x)
     if not (dq and dx):
         raise ValueError("ridg_l2_error_noalloc takes device arrays")
+    cells, m, dim, order = int(cells), int(m), int(dim), int(order)
+    if dim < 1 or dim > 3 or m < 1 or order < 0 or cells < 1:
+        raise ValueError("bad sizes")
+    if q.numel() != cells * m * (order + 1) ** dim or x.numel() != cells * m * (order + 2) ** dim:
+        raise ValueError(f"sizes do not match: q {q.numel()}, x {x.numel()} for {cells} cells, "
+                         f"m={m}, dim={dim}, order={order}")
+    cur = torch.cuda.current_device()
+    if q.device.index != cur or x.device.index != cur:
+        raise ValueError("q and x must be on the current CUDA device")
+    if isinstance(stream, torch.cuda.Stream):
+        stream = stream.cuda_stream
     e = C.c_double()
-    _check(_lib.ridg_l2_error_noalloc(pq, px, int(cells), int(m), int(dim), int(order),
-                                      stream, C.byref(e)))
+    _check(_lib.ridg_l2_error_noalloc(pq, px, cells, m, dim, order,
+                                      C.c_void_p(stream) if stream else None, C.byref(e)))
     return e.value
 
 
