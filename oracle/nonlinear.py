@@ -13,8 +13,12 @@ Faces interior to the region use the Rusanov flux
 F-hat(w_L, w_R) = (F(w_L) + F(w_R)) / 2 - alpha (w_R - w_L) / 2 with alpha the largest
 wave speed |lambda(w_L)|, |lambda(w_R)| over the face's quadrature points; in the
 prediction alpha is evaluated once, from the initial iterate (Q^n extended in time), and
-held fixed during the Newton iteration.  Faces on the region boundary use the interior
-trace only, F(w_int) . n.
+held fixed during the Newton iteration (alpha="frozen", the reading the CUDA path
+implements).  Two other readings of Sec. 2.2 are available for comparison:
+alpha="live" re-evaluates the per-face alpha from every iterate in the residual (the
+Jacobian then holds that iterate's alpha fixed, so Newton converges linearly), and
+alpha="point" does the same with alpha taken pointwise at each face quadrature point.
+Faces on the region boundary use the interior trace only, F(w_int) . n.
 
 Jacobian (Sec. 3).  Newton W <- W - J^{-1} R (Sec. 3).  Two Jacobians are provided:
   * quadrature (eq. Jacobian): every integral int d Psi_k Psi_l F'(w) by quadrature;
@@ -228,13 +232,15 @@ class Tables:
 # ---------------------------------------------------------------------------
 # residual, Jacobians, Newton
 # ---------------------------------------------------------------------------
-def _rusanov(flux, wL, wR, dd, alpha=None):
-    """Rusanov flux with alpha the largest wave speed on the face (one value per face).
-    wL, wR: (m, E, q).  Returns (F-hat (m, E, q), alpha (E,)).  A given alpha is used
-    as is (frozen)."""
+def _rusanov(flux, wL, wR, dd, alpha=None, pointwise=False):
+    """Rusanov flux with alpha the largest wave speed on the face (one value per face, or
+    one per face point if pointwise).  wL, wR: (m, E, q).  Returns (F-hat (m, E, q),
+    alpha (E, 1) or (E, q)).  A given alpha is used as is (frozen)."""
     if alpha is None:
-        alpha = np.maximum(flux.speed(wL, dd), flux.speed(wR, dd)).max(axis=-1)
-    Fh = 0.5 * (flux.F(wL, dd) + flux.F(wR, dd)) - 0.5 * alpha[None, :, None] * (wR - wL)
+        alpha = np.maximum(flux.speed(wL, dd), flux.speed(wR, dd))
+        if not pointwise:
+            alpha = alpha.max(axis=-1, keepdims=True)
+    Fh = 0.5 * (flux.F(wL, dd) + flux.F(wR, dd)) - 0.5 * alpha[None] * (wR - wL)
     return Fh, alpha
 
 
@@ -253,10 +259,10 @@ def _region_neighbours(d):
     return offs, nbrs
 
 
-def residual(W, Q, flux, tb: Tables, lam, frozen=None):
+def residual(W, Q, flux, tb: Tables, lam, frozen=None, pointwise=False):
     """R for a batch of regions.  W: (E, nR, m, thT), Q: (E, nR, m, thS).
-    Returns (R, alpha) with alpha[(r, dd, side)] the face speeds (E,).  With `frozen`
-    (a previous alpha dict) the face speeds are not recomputed."""
+    Returns (R, alpha) with alpha[(r, dd, side)] the face speeds ((E, 1), or (E, q) if
+    pointwise).  With `frozen` (a previous alpha dict) the face speeds are not recomputed."""
     d = tb.d
     E, nR, m, _ = W.shape
     offs, nbrs = _region_neighbours(d)
@@ -278,9 +284,9 @@ def residual(W, Q, flux, tb: Tables, lam, frozen=None):
                     nb_ = np.einsum("ejk,kq->jeq", W[:, r2], tb.PsiF[dd][-side])
                     fz = None if frozen is None else frozen[(r, dd, side)]
                     if side == +1:
-                        Fh, al = _rusanov(flux, own, nb_, dd, fz)
+                        Fh, al = _rusanov(flux, own, nb_, dd, fz, pointwise)
                     else:
-                        Fh, al = _rusanov(flux, nb_, own, dd, fz)
+                        Fh, al = _rusanov(flux, nb_, own, dd, fz, pointwise)
                     alphas[(r, dd, side)] = al
                     Fn = side * Fh
                 R[:, r] += scale[dd] * np.einsum("kq,q,jeq->ejk", tb.PsiF[dd][side], tb.wF[dd], Fn)
@@ -325,11 +331,14 @@ def jacobian(W, Q, flux, tb: Tables, lam, alphas, kind: str = "qqf"):
                 if r2 is None:
                     blocks = [(r, side, flux.dF(own, dd) * side)]
                 else:
-                    al = alphas[(r, dd, side)][None, None, :, None]
+                    al = alphas[(r, dd, side)][None, None]
                     if kind == "qqf":
                         nbv = np.einsum("ejk,kq->jeq", W[:, r2], at_nb)
                     else:
                         nbv = np.einsum("ejk,kq->jeq", W[:, r2], tb.PsiF[dd][-side])
+                    if al.shape[-1] != 1:
+                        # pointwise speeds: this iterate's, at the points used here
+                        al = np.maximum(flux.speed(own, dd), flux.speed(nbv, dd))[None, None]
                     # d F-hat / d w_L = (F'(w_L) + alpha I)/2, d/d w_R = (F'(w_R) - alpha I)/2
                     if side == +1:   # own is L, neighbour is R
                         g_own = 0.5 * (flux.dF(own, dd) + al * eye)
@@ -351,8 +360,13 @@ def jacobian(W, Q, flux, tb: Tables, lam, alphas, kind: str = "qqf"):
 
 
 def newton_predict(Q, w, dt, kind="qqf", max_iters=4, tol=1e-10, chunk=16, cells=None,
-                   return_iters=False):
-    """Centre-element W (cells, m*thT) for every cell (or the listed `cells`)."""
+                   return_iters=False, alpha="frozen"):
+    """Centre-element W (cells, m*thT) for every cell (or the listed `cells`).
+    alpha: "frozen" (Rusanov speeds of the initial iterate held fixed), "live" (per-face
+    speeds of every iterate) or "point" (pointwise speeds of every iterate)."""
+    if alpha not in ("frozen", "live", "point"):
+        raise ValueError(alpha)
+    pointwise = alpha == "point"
     d, M = w["dim"], w["M"]
     tb = Tables(d, M)
     flux = flux_model(w)
@@ -374,13 +388,13 @@ def newton_predict(Q, w, dt, kind="qqf", max_iters=4, tol=1e-10, chunk=16, cells
         active = np.ones(len(sel), dtype=bool)
         it = np.zeros(len(sel), dtype=np.int64)
         # face speeds of the Rusanov flux, frozen at the initial iterate
-        _, alpha0 = residual(W, QR, flux, tb, lam)
+        _, alpha0 = residual(W, QR, flux, tb, lam, pointwise=pointwise)
         for _ in range(max_iters):
             idx = np.nonzero(active)[0]
             if idx.size == 0:
                 break
-            al_idx = {k: v[idx] for k, v in alpha0.items()}
-            R, al = residual(W[idx], QR[idx], flux, tb, lam, frozen=al_idx)
+            al_idx = {k: v[idx] for k, v in alpha0.items()} if alpha == "frozen" else None
+            R, al = residual(W[idx], QR[idx], flux, tb, lam, frozen=al_idx, pointwise=pointwise)
             J = jacobian(W[idx], QR[idx], flux, tb, lam, al, kind)
             delta = np.linalg.solve(J, R.reshape(idx.size, -1, 1)).reshape(R.shape)
             W[idx] -= delta
@@ -397,8 +411,9 @@ def newton_predict(Q, w, dt, kind="qqf", max_iters=4, tol=1e-10, chunk=16, cells
     return out
 
 
-def correct(Q, Wc, w, dt):
-    """Q^{n+1} from Q^n and every cell's predicted W (cells, m*thT)."""
+def correct(Q, Wc, w, dt, pointwise=False):
+    """Q^{n+1} from Q^n and every cell's predicted W (cells, m*thT); the Rusanov speed per
+    face (or per face point if pointwise) from the predicted traces."""
     d, M = w["dim"], w["M"]
     tb = Tables(d, M)
     flux = flux_model(w)
@@ -416,16 +431,16 @@ def correct(Q, Wc, w, dt):
         own_m = np.einsum("ejk,kq->jeq", Wr, tb.PsiF[dd][-1])     # at xi_d = -1
         ax = cell_axis(d, dd)
         right_m = np.roll(own_m.reshape((m,) + g + (-1,)), -1, axis=1 + ax).reshape(own_m.shape)
-        Fh, _ = _rusanov(flux, own_p, right_m, dd)                 # face i+1/2, once
+        Fh, _ = _rusanov(flux, own_p, right_m, dd, None, pointwise)  # face i+1/2, once
         dQ -= sc * np.einsum("sq,q,jeq->ejs", tb.PhiF[dd][+1], tb.wF[dd], Fh)
         Fl = np.roll(Fh.reshape((m,) + g + (-1,)), 1, axis=1 + ax).reshape(Fh.shape)
         dQ += sc * np.einsum("sq,q,jeq->ejs", tb.PhiF[dd][-1], tb.wF[dd], Fl)
     return Q + dQ.reshape(Q.shape)
 
 
-def step(Q, w, dt, kind="qqf", max_iters=4, tol=1e-10):
-    W = newton_predict(Q, w, dt, kind=kind, max_iters=max_iters, tol=tol)
-    return correct(Q, W, w, dt)
+def step(Q, w, dt, kind="qqf", max_iters=4, tol=1e-10, alpha="frozen"):
+    W = newton_predict(Q, w, dt, kind=kind, max_iters=max_iters, tol=tol, alpha=alpha)
+    return correct(Q, W, w, dt, pointwise=alpha == "point")
 
 
 def max_speed(Q, w, npts: int = 6):
