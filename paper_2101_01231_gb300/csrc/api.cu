@@ -103,6 +103,9 @@ CorrParams corr_params(const ridg_t* h) {
     for (int a = 0; a < ridg::kMaxNB; ++a)
       split(a >= 1 && a < h->nb ? cp.nu[d] * cp.D[a * ridg::kMaxNB + a - 1] : 0.0, cp.vdh[d][a],
             cp.vdl[d][a]);
+    for (int b = 0; b < ridg::kMaxNB; ++b)
+      split(b < h->nb ? cp.nu[d] * (cp.nu[d] > 0 ? cp.ep[b] : cp.em[b]) : 0.0, cp.tch[d][b],
+            cp.tcl[d][b]);
   }
   return cp;
 }
@@ -300,7 +303,7 @@ int enqueue_correct_after_mean(ridg_t* h) {
   if (h->opt.precision == RIDG_PREC_MIXED_BF16 && h->dim == 3) {
     // double-float correction from the time means, with the new state's digit planes
     RIDG_CUDA(h, ridg::launch_mixed3_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
-                                             h->Wbar, h->mixed.gmax, cp, h->ms, h->stream));
+                                             h->mixed.gmax, cp, h->ms, h->stream));
   } else if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
     RIDG_CUDA(h, ridg::launch_mixed_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
                                             h->mixed.gmax, cp, sign_of(h->flux.vel[0]),
@@ -477,9 +480,7 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
   h->red = (double*)dev_alloc(h, (size_t)h->red_blocks * 4 * sizeof(double));
   h->status = (int*)dev_alloc(h, 16 * sizeof(int));
   if (is_linear(h)) {
-    // (3D mixed path: also the face values of the correction, 3 (M+1)^2 float2 per cell)
-    const size_t nWbar = std::max(nQ, (size_t)h->ncell * 3 * h->nb * h->nb);
-    h->Wbar = (double*)dev_alloc(h, nWbar * sizeof(double));
+    h->Wbar = (double*)dev_alloc(h, nQ * sizeof(double));
     h->P = (double*)dev_alloc(h, (size_t)h->thT * h->K * sizeof(double));
   }
   if (!h->Q || !h->W || !h->red || !h->status || (is_linear(h) && (!h->Wbar || !h->P))) {

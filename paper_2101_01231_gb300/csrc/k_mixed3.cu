@@ -11,14 +11,13 @@
 //
 // Tiles are 8 x 16 cells of one z-plane (M = 128).  The region offset (ox, oy, oz) is taken
 // as in 2D -- x by one of the box's x-shifted TMA copies, y by the descriptor start -- and z
-// by loading the plane z + oz.  The operator digits of all the box's offsets do not fit next
-// to the state digits in shared memory, so they stream too:
-//   A ring (4 slots): one digit of one input plane (one x-copy per x-offset of the box, each
-//     8-mode groups x 8 x 18 cells: 18.4 KB at Q2 with two x-offsets), loaded by 4D TMA
-//     boxes of the ghost-padded digit planes;
-//   B stages (one per y-offset of the box): the operator digits of the x-offsets of one
-//     (oz, oy) row (24.6 KB), one bulk copy each; stage oy is refilled for the next oz once
-//     the last digit's MMAs on it are complete.
+// by loading the plane z + oz.  Shared memory holds
+//   the operator: the digits of every offset of the upwind box (at most 2 x 2 x 2 offsets,
+//     64 KB at Q2 with 4 slices, 98 KB with 6), one stage per (oz, oy) row, bulk-copied once
+//     per CTA and kept for all its tiles;
+//   an A ring (4 to 8 slots, as many as fit): one digit of one input plane (one x-copy per
+//     x-offset of the box, each 8-mode groups x 8 x 18 cells: 18.4 KB at Q2 with two
+//     x-offsets), loaded by 4D TMA boxes of the ghost-padded digit planes.
 // The MMA issuer runs oz -> digit a -> oy -> ox -> k-step; the epilogue writes W-bar as
 // double-float pairs with a common exponent, and mixed3_correct_kernel applies the correction
 // in double-float FP32 (state update FP64) and writes the next step's digit planes.  Every
@@ -37,29 +36,30 @@
 namespace ridg {
 namespace {
 
-constexpr int kNA = 4;      // A slots
-constexpr int kNBst = 3;    // B stages (one per y-offset)
+constexpr int kNAmax = 8;   // A slots (at most)
 constexpr int kNOUTP = 32;  // padded outputs (theta_S <= 27)
 
-struct DF3 {
-  float h, l;
-};
-
 struct Gemm3Layout {
-  int P, brows;
+  int P, brows, na, nst;
   uint32_t copy_bytes, a_bytes, b_bytes, b_off, bar_off, bytes;
 };
 
-// ncx = x-offsets of the upwind box (x-shifted copies per A slot, operator blocks per B row)
-__host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int ncx) {
+// ncx, ncy, ncz = offsets of the upwind box per dimension (x-shifted copies per A slot,
+// operator blocks per B stage, B stages = ncy ncz); the A ring takes the room that is left
+__host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int ncx, int ncy, int ncz) {
   Gemm3Layout l;
   l.P = ((thS + 15) / 16) * 2;
   l.brows = S * kNOUTP;
   l.copy_bytes = (uint32_t)l.P * kCopy * 16;
   l.a_bytes = ((uint32_t)ncx * l.copy_bytes + 1023u) & ~1023u;
   l.b_bytes = (uint32_t)ncx * l.P * l.brows * 16;
-  l.b_off = kNA * l.a_bytes;
-  l.bar_off = (l.b_off + kNBst * l.b_bytes + 63u) & ~63u;
+  l.nst = ncy * ncz;
+  const uint32_t btot = (uint32_t)l.nst * l.b_bytes;
+  const uint32_t room = kSmemLimit - 1024u - btot;  // barriers and alignment slack
+  int na = (int)(room / l.a_bytes);
+  l.na = na > kNAmax ? kNAmax : na;
+  l.b_off = (uint32_t)l.na * l.a_bytes;
+  l.bar_off = (l.b_off + btot + 63u) & ~63u;
   l.bytes = l.bar_off + 256;
   return l;
 }
@@ -79,15 +79,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
   // the upwind box: offsets lo + 0 .. cnt - 1 per dimension (cnt 1 or 2, at most 3 B stages)
   const int ox0 = box.lo[0], oy0 = box.lo[1], oz0 = box.lo[2];
   const int ncx = NCXC ? NCXC : box.cnt[0], ncy = box.cnt[1], ncz = box.cnt[2];
-  const Gemm3Layout L = gemm3_layout(S, THS, ncx);
+  const Gemm3Layout L = gemm3_layout(S, THS, ncx, ncy, ncz);
+  const int NA = L.na;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
   const int ntiles = ntx * nty * nz;
   const int mytiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int tcols = S * kNOUTP;  // TMEM columns per stage (two stages)
   const uint32_t bar = smem_u32(smem + L.bar_off);
-  const uint32_t afull0 = bar, afree0 = bar + 8u * kNA, bfull0 = bar + 16u * kNA,
-                 bfree0 = bfull0 + 8u * kNBst, tdone0 = bfree0 + 8u * kNBst, tempty0 = tdone0 + 16u;
+  const uint32_t afull0 = bar, afree0 = bar + 8u * kNAmax, bfull = bar + 16u * kNAmax,
+                 tdone0 = bfull + 8u, tempty0 = tdone0 + 16u;
   const int sexp = exps[0];
 
   auto tile_origin = [&](int k, int& x0, int& y0, int& z0) {
@@ -98,14 +99,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
   };
 
   if (tid == 0) {
-    for (int i = 0; i < kNA; ++i) {
+    for (int i = 0; i < NA; ++i) {
       mbar_init(afull0 + 8u * i, 1);
       mbar_init(afree0 + 8u * i, 1);
     }
-    for (int i = 0; i < kNBst; ++i) {
-      mbar_init(bfull0 + 8u * i, 1);
-      mbar_init(bfree0 + 8u * i, 1);
-    }
+    mbar_init(bfull, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(tdone0 + 8u * i, 1);
       mbar_init(tempty0 + 8u * i, 256);
@@ -131,26 +129,23 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- producer: B rows of offsets and A digit planes, in MMA order ----
+      // ---------------- producer: the operator once, then A digit planes in MMA order ----
       bool ok = true;
+      if (mytiles > 0) {
+        const uint32_t btot = (uint32_t)L.nst * L.b_bytes;
+        mbar_expect_tx(bfull, btot);
+        const uint32_t dst = smem_u32(smem + L.b_off);
+        for (uint32_t off = 0; off < btot; off += 32768u)
+          bulk_load(dst + off, Bg + off, min(32768u, btot - off), bfull);
+      }
       int ia = 0;  // A items issued
       for (int k = 0; k < mytiles && ok; ++k) {
         int x0, y0, z0;
         tile_origin(k, x0, y0, z0);
         for (int jz = 0; jz < ncz && ok; ++jz) {
-          const int use = k * ncz + jz;  // use count of every B stage
-          for (int jy = 0; jy < ncy; ++jy) {
-            if (use > 0 && !mbar_wait_sleep(bfree0 + 8u * jy, (use - 1) & 1)) { ok = false; break; }
-            const uint32_t fb = bfull0 + 8u * jy;
-            mbar_expect_tx(fb, L.b_bytes);
-            const unsigned char* src = Bg + (size_t)(jz * ncy + jy) * L.b_bytes;
-            const uint32_t dst = smem_u32(smem + L.b_off + jy * L.b_bytes);
-            for (uint32_t off = 0; off < L.b_bytes; off += 32768u)
-              bulk_load(dst + off, src + off, min(32768u, L.b_bytes - off), fb);
-          }
           for (int a = 0; a < S && ok; ++a, ++ia) {
-            const int sl = ia % kNA;
-            if (ia >= kNA && !mbar_wait_sleep(afree0 + 8u * sl, ((ia / kNA) - 1) & 1)) { ok = false; break; }
+            const int sl = ia % NA;
+            if (ia >= NA && !mbar_wait_sleep(afree0 + 8u * sl, ((ia / NA) - 1) & 1)) { ok = false; break; }
             const uint32_t fa = afull0 + 8u * sl;
             mbar_expect_tx(fa, ncx * L.copy_bytes);  // out-of-range boxes are zero-filled and counted
             const uint32_t dst = smem_u32(smem + sl * L.a_bytes);
@@ -171,27 +166,27 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
       const uint32_t brows = (uint32_t)L.brows;
       const uint32_t copy16 = L.copy_bytes / 16;
       bool ok = true;
+      if (mytiles > 0) {
+        ok = mbar_wait(bfull, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
       int ia = 0;
       for (int k = 0; k < mytiles && ok; ++k) {
         const int ts = k & 1;
         if (k >= 2 && !mbar_wait(tempty0 + 8u * ts, ((k - 2) >> 1) & 1)) { ok = false; break; }
         const uint32_t tst = tmem + (uint32_t)(ts * tcols);
         for (int jz = 0; jz < ncz && ok; ++jz) {
-          const int use = k * ncz + jz;
           for (int a = 0; a < S && ok; ++a, ++ia) {
-            const int sl = ia % kNA;
-            if (!mbar_wait(afull0 + 8u * sl, (ia / kNA) & 1)) { ok = false; break; }
+            const int sl = ia % NA;
+            if (!mbar_wait(afull0 + 8u * sl, (ia / NA) & 1)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // A: LBO = plane stride inside a copy, SBO = one halo row of 8 cells (128 B)
             const uint64_t adesc0 = smem_desc(smem_u32(smem + sl * L.a_bytes), kCopy * 16, 128);
             const uint32_t idesc = idesc_bf16(128, (S - a) * kNOUTP);
             const uint32_t dcol = tst + (uint32_t)(a * kNOUTP);
             for (int jy = 0; jy < ncy; ++jy) {
-              if (a == 0) {
-                if (!mbar_wait(bfull0 + 8u * jy, use & 1)) { ok = false; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              }
-              const uint64_t bdesc0 = smem_desc(smem_u32(smem + L.b_off + jy * L.b_bytes), brows * 16, 128);
+              const uint64_t bdesc0 =
+                  smem_desc(smem_u32(smem + L.b_off + (jz * ncy + jy) * L.b_bytes), brows * 16, 128);
               // y-offset oy0 + jy: the descriptor start moved by oy0 + jy + 1 halo rows
               const uint32_t yoff = (uint32_t)((oy0 + jy + 1) * kTX);
 #pragma unroll
@@ -204,11 +199,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
                   mma_bf16(dcol, adesc0 + aoff, bdesc0 + boff, idesc, acc);
                 }
               }
-              if (a == S - 1)
-                asm volatile(
-                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        bfree0 + 8u * jy)
-                    : "memory");
             }
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -303,24 +293,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
 // state update is FP64.  The kernel then writes the new state's digit planes (exponent from
 // the previous maximum plus one bit of headroom, checked) and accumulates the new maximum.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ DF3 df3_mul(float ch, float cl, DF3 a) {
-  const float p = __fmul_rn(ch, a.h);
-  float e = __fmaf_rn(ch, a.h, -p);
-  e = __fmaf_rn(ch, a.l, e);
-  e = __fmaf_rn(cl, a.h, e);
-  const float s = __fadd_rn(p, e);
-  return DF3{s, __fsub_rn(e, __fsub_rn(s, p))};
-}
-
-__device__ __forceinline__ DF3 df3_add(DF3 a, DF3 b) {
-  float s, e;
-  two_sum(a.h, b.h, s, e);
-  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
-  const float s2 = __fadd_rn(s, e);
-  return DF3{s2, __fsub_rn(e, __fsub_rn(s2, s))};
-}
-
-
 // float * 2^k as a double, by exponent arithmetic on the bits (exact; 0 stays 0)
 __device__ __forceinline__ double f2d_scale(float f, int k) {
   const uint32_t b = __float_as_uint(f);
@@ -333,62 +305,56 @@ __device__ __forceinline__ double f2d_scale(float f, int k) {
   return __hiloint2double((int)hiw, (int)low);
 }
 
-// Face values of the +d face of every cell for the NB^2 lines t crossing it:
-// F[(d NT + t) cells + e] = nu_d^+ tr_+(W-bar_e)[t] + nu_d^- tr_-(W-bar_right)[t], one thread
-// per (cell, d).  Each face value is computed once; both its cells read it.
-template <int NB>
-__global__ void __launch_bounds__(128) mixed3_faces_kernel(const float2* __restrict__ Y, int nx,
-                                                           int ny, int nz, CorrParams cp,
-                                                           float2* __restrict__ F) {
-  constexpr int NT = NB * NB;
-  const long long ncell = (long long)nx * ny * nz;
-  const int dd = blockIdx.y;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ncell) return;
-  const unsigned ue = (unsigned)e, ur = ue / (unsigned)nx;
-  const int ix = (int)(ue - ur * (unsigned)nx), iy = (int)(ur % (unsigned)ny), iz = (int)(ur / (unsigned)ny);
-  int rxi = ix, ryi = iy, rzi = iz;
-  if (dd == 0) rxi = ix + 1 == nx ? 0 : ix + 1;
-  if (dd == 1) ryi = iy + 1 == ny ? 0 : iy + 1;
-  if (dd == 2) rzi = iz + 1 == nz ? 0 : iz + 1;
-  const long long jr = ((long long)rzi * ny + ryi) * nx + rxi;
-  const int st = dd == 0 ? 1 : (dd == 1 ? NB : NB * NB);
-  const float nph = cp.nph[dd], npl = cp.npl[dd], nmh = cp.nmh[dd], nml = cp.nml[dd];
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    const int base = t % st + (t / st) * st * NB;
-    DF3 tp{0.f, 0.f}, tm{0.f, 0.f};
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const float sg = (b & 1) ? -1.f : 1.f;  // phi_b(-1) = (-1)^b phi_b(+1)
-      const float2 yo = Y[(base + b * st) * ncell + e];
-      const float2 yr = Y[(base + b * st) * ncell + jr];
-      tp = df3_add(tp, df3_mul(cp.eph[b], cp.epl[b], DF3{yo.x, yo.y}));
-      tm = df3_add(tm, df3_mul(sg * cp.eph[b], sg * cp.epl[b], DF3{yr.x, yr.y}));
-    }
-    const DF3 f = df3_add(df3_mul(nph, npl, tp), df3_mul(nmh, nml, tm));
-    F[(long long)(dd * NT + t) * ncell + e] = make_float2(f.h, f.l);
-  }
+// Unnormalised double-float values (s + e, |e| a few ulp of s at most) for the accumulations
+// of the correction: a product costs 4 instructions and an accumulation 8, where the
+// normalised pair arithmetic above costs 7 and 11; one normalisation at the end.
+struct DFU {
+  float s, e;
+};
+
+// c x, c = (ch, cl) and x = (xs, xe): ch xs exactly (product and FMA error), the cross terms
+// ch xe + cl xs into the error word (cl xe is below the precision carried)
+__device__ __forceinline__ DFU dfu_prod(float ch, float cl, float xs, float xe) {
+  const float p = __fmul_rn(ch, xs);
+  float e = __fmaf_rn(ch, xs, -p);
+  e = __fmaf_rn(ch, xe, e);
+  e = __fmaf_rn(cl, xs, e);
+  return DFU{p, e};
 }
 
-// The update: one thread per (cell, 8-mode group), the group uniform over a block and the P
-// blocks of the same 128 cells adjacent in launch order (so that they share the cells' state
-// rows in L2).  dQ = sum_d [(nu_d D[a][a-1]) W-bar(mode a-1 along d) + phi_a(+1) (s_a
-// F(i - 1/2) - F(i + 1/2))], s_a = (-1)^a = phi_a(-1) / phi_a(+1), in double-float; Q += dQ
-// in FP64; then the group's digit rows of the new state (and ghost copies) and the running
-// maximum.  Degrees up to 2: a mode has at most one volume-term source per direction.
+// a += x: the leading words by an error-free sum, the error words added plainly
+__device__ __forceinline__ void dfu_acc(DFU& a, DFU x) {
+  float s, err;
+  two_sum(a.s, x.s, s, err);
+  a.s = s;
+  a.e = __fadd_rn(a.e, __fadd_rn(x.e, err));
+}
+
+// The update, one thread per cell.  Per direction d with velocity sign sg_d (the upwind
+// side), per line t of the NB^2 lines of modes along d: the face values at the cell's two
+// d-faces are the upwind traces nu_d tr(W-bar) -- of this cell and of its upstream neighbour
+// (coalesced reads of the neighbour's time means; the neighbour's row was just read by the
+// threads of that cell, so it is served by L2) -- computed by the same code from the same
+// inputs in both cells of a face, so each face value has the same bits on both sides (exact
+// conservation).  dQ = sum_d [(nu_d D[a][a-1]) W-bar(mode a-1 along d) + phi_a(+1) (s_a
+// F(i - 1/2) - F(i + 1/2))], s_a = (-1)^a = phi_a(-1) / phi_a(+1), in double-float; then
+// Q += dQ in FP64, the new state's digit rows (and ghost copies) and the running maximum.
+// Degrees up to 2: a mode has at most one volume-term source per direction.
 template <int NB, int S>
 __global__ void __launch_bounds__(128) mixed3_correct_kernel(
-    double* __restrict__ Q, const float2* __restrict__ Y, const float2* __restrict__ F, int nx,
-    int ny, int nz, CorrParams cp, int gmax, int* __restrict__ exps,
-    unsigned long long* __restrict__ maxbits, uint4* __restrict__ planes, int* status) {
+    double* __restrict__ Q, const float2* __restrict__ Y, int nx, int ny, int nz, CorrParams cp,
+    int gmax, int* __restrict__ exps, unsigned long long* __restrict__ maxbits,
+    uint4* __restrict__ planes, int* status) {
   static_assert(NB <= 3, "one volume-term source per mode and direction");
   constexpr int THS = NB * NB * NB, NT = NB * NB;
   constexpr int P = ((THS + 15) / 16) * 2;
   __shared__ unsigned long long shmax[4];
+  // per-thread dQ accumulators (double-float), indexed by mode: in shared memory so that the
+  // loops over lines stay rolled (a fully unrolled body stalls on instruction fetch)
+  __shared__ float2 acc_sh[THS * 128];
+  float2* acc = acc_sh + threadIdx.x;  // mode s at acc[s * 128]
   const long long ncell = (long long)nx * ny * nz;
-  const int pg = (int)(blockIdx.x % P), m0 = 8 * pg;
-  const long long e = (long long)(blockIdx.x / P) * blockDim.x + threadIdx.x;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int ys = exps[1];
   const int snext = exponent_above(maxbits[0]) + 1;
   unsigned long long mymax = 0;
@@ -396,56 +362,92 @@ __global__ void __launch_bounds__(128) mixed3_correct_kernel(
   if (e < ncell) {
     const unsigned ue = (unsigned)e, ur = ue / (unsigned)nx;
     const int ix = (int)(ue - ur * (unsigned)nx), iy = (int)(ur % (unsigned)ny), iz = (int)(ur / (unsigned)ny);
-    // left neighbours along x, y, z (periodic)
-    long long jl[3];
-    jl[0] = ix == 0 ? e + (nx - 1) : e - 1;
-    jl[1] = iy == 0 ? e + (long long)(ny - 1) * nx : e - nx;
-    jl[2] = iz == 0 ? e + (long long)(nz - 1) * nx * ny : e - (long long)nx * ny;
-    DF3 dq[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) dq[j] = DF3{0.f, 0.f};
-#pragma unroll
+    for (int j = 0; j < THS; ++j) acc[j * 128] = make_float2(0.f, 0.f);
+#pragma unroll 1
     for (int dd = 0; dd < 3; ++dd) {
+      const double nu = cp.nu[dd];
+      if (nu == 0.0) continue;  // no flux along d: no volume or face term
+      const bool pos = nu > 0.0;
+      // the upstream neighbour along d (periodic): i - 1 for nu > 0, i + 1 for nu < 0
+      long long up;
+      if (dd == 0) up = pos ? (ix == 0 ? e + (nx - 1) : e - 1) : (ix == nx - 1 ? e - (nx - 1) : e + 1);
+      else if (dd == 1)
+        up = pos ? (iy == 0 ? e + (long long)(ny - 1) * nx : e - nx)
+                 : (iy == ny - 1 ? e - (long long)(ny - 1) * nx : e + nx);
+      else
+        up = pos ? (iz == 0 ? e + (long long)(nz - 1) * nx * ny : e - (long long)nx * ny)
+                 : (iz == nz - 1 ? e - (long long)(nz - 1) * nx * ny : e + (long long)nx * ny);
       const int st = dd == 0 ? 1 : (dd == 1 ? NB : NB * NB);
-      const float2* Fd = F + (long long)dd * NT * ncell;
+      // upwind trace coefficients nu phi_b(+1) of the left cell (nu > 0) or nu phi_b(-1) =
+      // nu (-1)^b phi_b(+1) of the right cell (nu < 0), as double-float pairs
+      float ch[NB], cl[NB];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int sm = m0 + j;
-        if (sm >= THS) continue;
-        const int a = (sm / st) % NB;                          // index along d
-        const int base = sm - a * st;                          // the line's first mode
-        const int t = (base % st) + (base / (st * NB)) * st;   // line index
-        DF3 v = dq[j];
-        if (a >= 1) {
-          const float2 y = Y[(base + (a - 1) * st) * ncell + e];
-          v = df3_add(v, df3_mul(cp.vdh[dd][a], cp.vdl[dd][a], DF3{y.x, y.y}));
+      for (int b = 0; b < NB; ++b) {
+        ch[b] = cp.tch[dd][b];
+        cl[b] = cp.tcl[dd][b];
+      }
+      // the NB values of line t (modes base + b st) of a cell's time means sit at
+      // Y[(base + b st) cells + e]; lines are walked as base = lo + hi, lo < st, hi in steps
+      // of st NB (no divisions)
+      const float2* Yo = Y + e;
+      const float2* Yu = Y + up;
+      const unsigned stn = (unsigned)st * (unsigned)ncell;
+      float2 co[NB], cu[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        co[b] = Yo[b * stn];
+        cu[b] = Yu[b * stn];
+      }
+      int lo = 0, hi = 0;
+#pragma unroll 1
+      for (int t = 0; t < NT; ++t) {
+        const int base = hi + lo;
+        // the next line, in flight while this one is computed
+        if (++lo == st) {
+          lo = 0;
+          hi += st * NB;
         }
-        const float2 fp = Fd[t * ncell + e];
-        const float2 fm = Fd[t * ncell + jl[dd]];
-        const float sg = (a & 1) ? -1.f : 1.f;
-        const DF3 df = df3_add(DF3{sg * fm.x, sg * fm.y}, DF3{-fp.x, -fp.y});
-        dq[j] = df3_add(v, df3_mul(cp.eph[a], cp.epl[a], df));
+        const unsigned noff = (unsigned)(t + 1 < NT ? hi + lo : base) * (unsigned)ncell;
+        float2 no[NB], nu2[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          no[b] = Yo[noff + b * stn];
+          nu2[b] = Yu[noff + b * stn];
+        }
+        // the face values nu tr(W-bar) of this cell and of the upstream neighbour (the same
+        // code from the same inputs in both cells of a face: the same bits)
+        DFU fo = dfu_prod(ch[0], cl[0], co[0].x, co[0].y);
+        DFU fu = dfu_prod(ch[0], cl[0], cu[0].x, cu[0].y);
+#pragma unroll
+        for (int b = 1; b < NB; ++b) {
+          dfu_acc(fo, dfu_prod(ch[b], cl[b], co[b].x, co[b].y));
+          dfu_acc(fu, dfu_prod(ch[b], cl[b], cu[b].x, cu[b].y));
+        }
+        // F(i - 1/2), F(i + 1/2); mode a gets phi_a(+1) (s_a F(i - 1/2) - F(i + 1/2)), s_a =
+        // (-1)^a: the even modes take dpos = F- - F+, the odd ones dneg = -(F- + F+)
+        const DFU fm = pos ? fu : fo, fp = pos ? fo : fu;
+        DFU dpos = fm, dneg = DFU{-fm.s, -fm.e};
+        dfu_acc(dpos, DFU{-fp.s, -fp.e});
+        dfu_acc(dneg, DFU{-fp.s, -fp.e});
+#pragma unroll
+        for (int a = 0; a < NB; ++a) {
+          const float2 c = acc[(base + a * st) * 128];
+          DFU v{c.x, c.y};
+          if (a >= 1) dfu_acc(v, dfu_prod(cp.vdh[dd][a], cp.vdl[dd][a], co[a - 1].x, co[a - 1].y));
+          const DFU df = (a & 1) ? dneg : dpos;
+          // phi_0(+1) = 1 exactly
+          dfu_acc(v, a == 0 ? df : dfu_prod(cp.eph[a], cp.epl[a], df.s, df.e));
+          acc[(base + a * st) * 128] = make_float2(v.s, v.e);
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          co[b] = no[b];
+          cu[b] = nu2[b];
+        }
       }
     }
     const int kfin = ys + gmax - 16;
-    double qn[8];
     double* q = Q + e * THS;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (m0 + j < THS) {
-        double v = q[m0 + j];
-        v = v + f2d_scale(dq[j].h, kfin);
-        v = v + f2d_scale(dq[j].l, kfin);
-        q[m0 + j] = v;
-        qn[j] = v;
-        const unsigned long long ab = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
-        mymax = ab > mymax ? ab : mymax;
-      } else {
-        qn[j] = 0.0;
-      }
-    }
-    uint4 rows[S];
-    fits = make_digit_rows<S>(qn, snext, rows);
     const long long pnx = nx + 2, pny = ny + 2;
     const long long plane = pnx * pny * (nz + 2);
     int px[2] = {ix + 1, -1}, py[2] = {iy + 1, -1}, pz[2] = {iz + 1, -1};
@@ -455,19 +457,41 @@ __global__ void __launch_bounds__(128) mixed3_correct_kernel(
     if (iy == ny - 1) py[1] = 0;
     if (iz == 0) pz[1] = nz + 1;
     if (iz == nz - 1) pz[1] = 0;
+#pragma unroll 1
+    for (int pg = 0; pg < P; ++pg) {
+      double qn[8];
 #pragma unroll
-    for (int a = 0; a < S; ++a) {
-      uint4* base = planes + (long long)(a * P + pg) * plane;
+      for (int j = 0; j < 8; ++j) {
+        const int sm = pg * 8 + j;
+        if (sm < THS) {
+          const float2 d = acc[sm * 128];
+          double v = q[sm];
+          v = v + f2d_scale(d.x, kfin);
+          v = v + f2d_scale(d.y, kfin);
+          q[sm] = v;
+          qn[j] = v;
+          const unsigned long long ab = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+          mymax = ab > mymax ? ab : mymax;
+        } else {
+          qn[j] = 0.0;
+        }
+      }
+      uint4 rows[S];
+      fits &= make_digit_rows<S>(qn, snext, rows);
 #pragma unroll
-      for (int zi = 0; zi < 2; ++zi) {
-        if (pz[zi] < 0) continue;
+      for (int a = 0; a < S; ++a) {
+        uint4* base = planes + (long long)(a * P + pg) * plane;
 #pragma unroll
-        for (int yi = 0; yi < 2; ++yi) {
-          if (py[yi] < 0) continue;
+        for (int zi = 0; zi < 2; ++zi) {
+          if (pz[zi] < 0) continue;
 #pragma unroll
-          for (int xi = 0; xi < 2; ++xi) {
-            if (px[xi] < 0) continue;
-            base[((long long)pz[zi] * pny + py[yi]) * pnx + px[xi]] = rows[a];
+          for (int yi = 0; yi < 2; ++yi) {
+            if (py[yi] < 0) continue;
+#pragma unroll
+            for (int xi = 0; xi < 2; ++xi) {
+              if (px[xi] < 0) continue;
+              base[((long long)pz[zi] * pny + py[yi]) * pnx + px[xi]] = rows[a];
+            }
           }
         }
       }
@@ -542,7 +566,8 @@ __global__ void __launch_bounds__(128) state_digits3_kernel(const double* __rest
 // ------------------------------------------------------------------------------------------
 bool mixed3_supported(int nb, int slices) {
   if (nb < 2 || nb > 3 || slices < 2 || slices > 6) return false;
-  return gemm3_layout(slices, nb * nb * nb, 3).bytes <= kSmemLimit;  // widest box
+  const Gemm3Layout l = gemm3_layout(slices, nb * nb * nb, 2, 2, 2);  // widest upwind box
+  return l.na >= 2 && l.bytes <= kSmemLimit;
 }
 
 size_t mixed3_plane_bytes(const Grid& g, int nb, int slices) {
@@ -578,7 +603,9 @@ int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_o
 template <int NB>
 static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& ms, void* Y,
                                   cudaStream_t s) {
-  const Gemm3Layout L = gemm3_layout(op.slices, NB * NB * NB, g.box.cnt[0]);
+  const Gemm3Layout L = gemm3_layout(op.slices, NB * NB * NB, g.box.cnt[0], g.box.cnt[1],
+                                     g.box.cnt[2]);
+  if (L.na < 2 || L.bytes > kSmemLimit) return cudaErrorInvalidValue;
   // one CTA per SM: each allocates all 512 TMEM columns, so a second CTA on the SM would
   // only wait for them -- ask for more than half the shared memory
   const uint32_t smem = std::max<uint32_t>(L.bytes, 117u * 1024u);
@@ -609,26 +636,24 @@ cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedSt
 }
 
 template <int NB, int S>
-static cudaError_t launch_correct3_t(const Grid& g, double* Q, const void* Y, void* F, int gmax,
+static cudaError_t launch_correct3_t(const Grid& g, double* Q, const void* Y, int gmax,
                                      const CorrParams& cp, MixedState& ms, cudaStream_t s) {
-  constexpr int P = ((NB * NB * NB + 15) / 16) * 2;
-  const dim3 fblocks((unsigned)((g.ncell + 127) / 128), 3);
-  mixed3_faces_kernel<NB><<<fblocks, 128, 0, s>>>((const float2*)Y, g.n[0], g.n[1], g.n[2], cp,
-                                                  (float2*)F);
-  const unsigned blocks = (unsigned)((g.ncell + 127) / 128) * P;
-  mixed3_correct_kernel<NB, S><<<blocks, 128, 0, s>>>(Q, (const float2*)Y, (const float2*)F,
-                                                      g.n[0], g.n[1], g.n[2], cp, gmax, ms.exps,
-                                                      ms.maxbits, (uint4*)ms.planes, ms.status);
+  // the kernel indexes the time means with 32-bit offsets (mode x cells)
+  if ((long long)g.ncell * NB * NB * NB >= (1LL << 32)) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)((g.ncell + 127) / 128);
+  mixed3_correct_kernel<NB, S><<<blocks, 128, 0, s>>>(Q, (const float2*)Y, g.n[0], g.n[1],
+                                                      g.n[2], cp, gmax, ms.exps, ms.maxbits,
+                                                      (uint4*)ms.planes, ms.status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mixed3_correct(const Grid& g, int nb, int slices, double* Q, const void* Y,
-                                  void* F, int gmax, const CorrParams& cp, MixedState& ms,
+                                  int gmax, const CorrParams& cp, MixedState& ms,
                                   cudaStream_t s) {
   if (g.dim != 3) return cudaErrorInvalidValue;
   switch (nb * 16 + slices) {
 #define RIDG_C3(NBV, SV) \
-  case NBV * 16 + SV: return launch_correct3_t<NBV, SV>(g, Q, Y, F, gmax, cp, ms, s);
+  case NBV * 16 + SV: return launch_correct3_t<NBV, SV>(g, Q, Y, gmax, cp, ms, s);
     RIDG_C3(2, 2) RIDG_C3(2, 3) RIDG_C3(2, 4) RIDG_C3(2, 5) RIDG_C3(2, 6)
     RIDG_C3(3, 2) RIDG_C3(3, 3) RIDG_C3(3, 4) RIDG_C3(3, 5) RIDG_C3(3, 6)
 #undef RIDG_C3

@@ -26,6 +26,9 @@ struct CorrParams {
   // nu_d D[a][a-1] as double-float pairs: the one volume-term coefficient of mode a along d
   // for degrees up to 2 (D[a][b] != 0 only for a > b, a + b odd)
   float vdh[3][kMaxNB], vdl[3][kMaxNB];
+  // the upwind trace coefficients along d as double-float pairs: nu_d phi_b(+1) for nu_d > 0
+  // (the left cell's trace), nu_d phi_b(-1) for nu_d < 0 (the right cell's), 0 for nu_d = 0
+  float tch[3][kMaxNB], tcl[3][kMaxNB];
 };
 
 struct Grid {
@@ -96,10 +99,10 @@ int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_o
 // (hi + lo) 2^(exps[1] + gmax - 16))
 cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
                                cudaStream_t s);
-// the correction from those outputs, plus the new state's digit planes and maximum
-// (F: scratch for the face values, 3 NB^2 float2 per cell)
+// the correction from those outputs (face values from each cell's own and upstream
+// neighbours' time means), plus the new state's digit planes and maximum
 cudaError_t launch_mixed3_correct(const Grid& g, int nb, int slices, double* Q, const void* Y,
-                                  void* F, int gmax, const CorrParams& cp, MixedState& ms,
+                                  int gmax, const CorrParams& cp, MixedState& ms,
                                   cudaStream_t s);
 // max |Q| and the 3D digit planes of Q
 cudaError_t launch_mixed3_refresh(const Grid& g, int nb, int slices, const double* Q,
