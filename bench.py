@@ -1,16 +1,18 @@
 #!/usr/bin/env python
 """RIDG step throughput on one GB300 (element-DOF updates/s).
 
-Workload: 2D linear advection u_t + u_x + 0.5 u_y = 0 on the periodic unit square,
-256 x 256 cells, tensor Q3 (16 spatial / 64 space-time coefficients), 3 x 3 regions,
-u0 = sin(2 pi x) sin(2 pi y), CFL 0.35, final time 1 (732 steps).  A step is one
-prediction + correction over the whole mesh.  Inputs are seeded synthetic data resident in
-HBM; before every timed step a 256 MB buffer (larger than the 129 MB L2) is rewritten so
-that each step starts with a cold L2.
+Headline workload: 3D linear advection with velocity (1, 0.7, 0.3) on the periodic unit
+cube, 96^3 cells, tensor Q2 (27 spatial / 81 space-time coefficients), 3 x 3 x 3 regions,
+u0 = product of sines plus seeded U(-1e-3, 1e-3) noise on every coefficient, CFL 0.30,
+final time 1 (320 steps).  A step is one prediction + correction over the whole mesh.
+Inputs are seeded synthetic data resident in HBM; the 191 MB state is larger than the
+129 MB L2, and a 256 MB buffer is rewritten before every timed step as well.
 
-The timed arm reports the precision chosen with --precision (default: the mixed BF16
-tensor-core prediction when the library supports it, else FP64) and, beside it, the FP64
-path and the oracle (on the host cores).  --impl reference times the oracle alone.
+The timed arm reports the mixed BF16 tensor-core path at the fewest digit slices whose L2
+error against the exact solution at t = 1 (the noisy piecewise polynomial carried by a t,
+integrated exactly on the sub-box overlaps) is within 1.05x of the FP64 path's, with the
+FP64 path beside it, the 2D 256^2 Q3 workload as an extra object, and the oracle on the
+host cores.  --impl reference times the oracle alone.
 """
 from __future__ import annotations
 
@@ -28,7 +30,8 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = "adv2d_n256_q3"
+WORKLOAD = "adv3d_n96_q2"
+WORKLOAD_2D = "adv2d_n256_q3"
 T_FINAL = 1.0
 
 
@@ -41,7 +44,7 @@ def upwind_cells(w):
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
@@ -61,8 +64,8 @@ def _args():
                    help="whole 1D runs to T = 1 timed (0: skip the 1D section)")
     p.add_argument("--ensemble-steps", type=int, default=1,
                    help="full-size Burgers-ensemble steps timed (0: skip; ~45 s per step)")
-    p.add_argument("--mixed3d-steps", type=int, default=20,
-                   help="timed steps of the 3D tensor-core path (0: skip it)")
+    p.add_argument("--adv2d-steps", type=int, default=200,
+                   help="timed steps of the 2D 256^2 Q3 workload beside the headline (0: skip)")
     return p.parse_args()
 
 
@@ -151,105 +154,53 @@ def cpu_oracle_sampled(w, q, nsample=4096, seed=0):
 
 
 def run_reference(args):
+    """The oracle on the host cores for the headline workload: each step a full oracle step
+    (2D) or, in 3D where a full oracle step takes minutes, one oracle step estimated from a
+    seeded sample of 1024 region solves scaled to the mesh plus the correction of the whole
+    mesh (cpu_oracle_sampled); at most about two minutes of host time in all."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     from paper_2101_01231_gb300 import inputs as I
     w = I.workload(args.workload)
-    for _ in range(max(1, min(args.warmup, 3))):
-        cpu_oracle(w, 0, steps=1)  # warm-up (tables, BLAS threads)
-    t_all = 0.0
-    n_all = 0
-    for _ in range(args.steps):
-        r = cpu_oracle(w, 0, steps=1)
-        t_all += r["seconds"]
-        n_all += 1
-        if t_all > 120:
-            break
     cells = int(np.prod(w["n"]))
     dof = cells * (w["M"] + 1) ** w["dim"]
-    value = dof * n_all / t_all
+    sampled = w["dim"] == 3
+    q = I.initial_state(w)
+
+    def one(seed):
+        if sampled:
+            r = cpu_oracle_sampled(w, q, nsample=1024, seed=seed)
+            return r["extrapolated_step_s"], r["seconds"]
+        r = cpu_oracle(w, 0, steps=1)
+        return r["seconds"], r["seconds"]
+
+    for i in range(max(1, min(args.warmup, 3))):
+        one(1000 + i)  # warm-up (tables, BLAS threads)
+    t_step, t_wall, n_all = 0.0, 0.0, 0
+    for i in range(args.steps):
+        ts, tw = one(i)
+        t_step += ts
+        t_wall += tw
+        n_all += 1
+        if t_wall > 120:
+            break
+    value = dof * n_all / t_step
+    sample = (f"{n_all} oracle steps, each estimated from 1024 seeded region solves scaled to "
+              f"{cells} cells plus the correction of the whole mesh" if sampled
+              else f"{n_all} full oracle steps")
     line = {
         "impl": "reference", "metric": "element-DOF updates/s per RIDG step",
         "value": value, "unit": "element-DOF updates/s", "n_gpus": ws, "steps": n_all,
-        "warmup": 1, "ms_per_step": 1e3 * t_all / n_all, "higher_is_better": True,
+        "warmup": 1, "ms_per_step": 1e3 * t_step / n_all, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["name"], "cells": cells, "order": w["M"], "steps_to_T": None},
         "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value,
-                         "unit": "element-DOF updates/s",
-                         "sample": f"{n_all} full oracle steps on the host cores"},
+                         "unit": "element-DOF updates/s", "sample": sample + " (host cores)"},
         "e2e": {"value": value, "unit": "element-DOF updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
-
-
-# ---------------------------------------------------------------------------------------
-# 3D: the tensor-core time-mean prediction at 96^3, Q2
-# ---------------------------------------------------------------------------------------
-def mixed3d_section(R, I, steps, warmup, cpu=False):
-    """2D's split-operand tensor-core prediction in 3D (96^3, Q2, product of sines + seeded
-    noise; the 191 MB state is larger than L2, so no flush is needed), with the FP64
-    correction, and the FP64 path beside it."""
-    w = I.workload("adv3d_n96_q2")
-    q = I.initial_state(w)
-    cells = int(np.prod(w["n"]))
-    thS = (w["M"] + 1) ** 3
-    K = upwind_cells(w) * thS      # the upwind box: 2 x 2 x 2 region cells
-    out = {"workload": w["name"], "cells": cells, "order": w["M"], "theta_s": thS,
-           "l2_flush": "none: the state (191 MB) is larger than L2"}
-    hbm, bf16, src = _peaks()
-    # digit slices: the fewest whose L2 error against the exact solution at t = 1 is within
-    # 1.05x of the FP64 path's, on the noise-free variant (same mesh, degree and velocity:
-    # the exact solution of the noisy data is not available in closed form)
-    w0 = I.workload("adv3d_n96_q2", ic="sin")
-    exact = I.exact_coefficients(w0, T_FINAL)
-
-    def err_run(prec, S=0):
-        s = R.Solver(3, w0["n"], w0["M"], vel=w0["vel"], cfl=w0["cfl"], lo=w0["lo"], hi=w0["hi"],
-                     precision=prec, slices=S)
-        s.set_state(I.initial_state(w0))
-        nt = s.set_final_time(T_FINAL)
-        s.step(nt)
-        s.sync()
-        e = s.l2_error(exact)
-        s.close()
-        return e
-
-    e64 = err_run(R.RIDG_PREC_FP64)
-    sweep, S_best = {}, 6
-    for S in range(3, 7):
-        sweep[str(S)] = err_run(R.RIDG_PREC_MIXED_BF16, S)
-        if sweep[str(S)] <= 1.05 * e64:
-            S_best = S
-            break
-    out["accuracy_gate"] = {"workload": "adv3d_n96_q2, noise-free (ic = sin)", "T": T_FINAL,
-                            "l2_error_fp64_gpu": e64, "l2_error_mixed_by_slices": sweep,
-                            "slices": S_best}
-    for tag, prec in (("mixed", R.RIDG_PREC_MIXED_BF16), ("fp64", R.RIDG_PREC_FP64)):
-        s = R.Solver(3, w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"], hi=w["hi"],
-                     precision=prec, slices=S_best if tag == "mixed" else 0)
-        s.set_state(q)
-        s.profile_step(warmup)
-        p = s.profile_step(steps if tag == "mixed" else max(3, steps // 10))
-        S_ = s.info()["slices"]
-        s.close()
-        r = {"ms_per_step": p["step_ms"], "predict_ms": p["predict_ms"], "correct_ms": p["correct_ms"],
-             "value": cells * thS / (p["step_ms"] * 1e-3), "unit": "element-DOF updates/s"}
-        if tag == "mixed":
-            bytes_pred = 2.0 * 8 * thS * cells          # Q in, W-bar out (FP64)
-            executed = 2.0 * (S_ * (S_ + 1) // 2) * 32 * upwind_cells(w) * 32 * cells
-            ach = bytes_pred / (p["predict_ms"] * 1e-3) / 1e9
-            r["roofline"] = {"bound": "hbm", "kernel": "mixed3_gemm (time-mean prediction)",
-                             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                             "traffic": _recorded_traffic("mixed3"), "peak_source": f"HBM copy, {src}",
-                             "tensor_executed_tflops": executed / (p["predict_ms"] * 1e-3) / 1e12,
-                             "tensor_peak_tflops": bf16,
-                             "algorithmic_tflops": 2.0 * thS * K * cells / (p["predict_ms"] * 1e-3) / 1e12}
-        out[tag] = r
-    if cpu:
-        out["cpu_oracle"] = cpu_oracle_sampled(w, q)
-    return out
 
 
 def adv1d_section(R, I, reps):
@@ -354,6 +305,7 @@ def ensemble_section(R, I, steps, cpu_cells, rank=0, ws=1):
                         "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
                         "peak_source": "nominal: FMA pipes x 2 flop x 2.07 GHz"}}
+    out["accuracy"] = ensemble_accuracy(R, I, R.RIDG_PREC_MIXED_TF32)
     # the oracle: per-cell Newton prediction time per degree (a 32 x 32 copy of the first
     # instance of each degree), extrapolated to the ensemble's cells
     if rank != 0:
@@ -548,6 +500,7 @@ def newton_section(R, I, steps, cpu_cells):
                            "peak": tf32_peak, "unit": "TFLOP/s", "frac": upd / tf32_peak,
                            "peak_source": "measured BF16 x nominal TF32/BF16 (1/2)"}
         out[tag] = r
+    out["accuracy"] = newton_accuracy(R, I)
     # the oracle: Newton prediction of a sample of cells and the correction of the whole
     # mesh is not needed for a per-cell rate; extrapolated to every cell of the step
     w = I.workload(NL_WORKLOAD, n=(32, 32))
@@ -566,6 +519,66 @@ def newton_section(R, I, steps, cpu_cells):
                          "sample": f"Newton predictions of {cpu_cells} cells of the vortex "
                                    "(numpy, all host cores), extrapolated to 512 x 512"}
     return out
+
+
+def newton_accuracy(R, I):
+    """The config's equal-accuracy check on a mesh the oracle can run to t = 1: the Euler
+    vortex at Q2 on 32^2 (27 steps) with each Newton precision, L2 error against the
+    translated vortex (eq. l2relerror) beside the oracle's (tests/golden)."""
+    from oracle import error as OE
+    g = _golden().get("euler2d_n32_q2")
+    if g is None:
+        return None
+    w = I.workload(NL_WORKLOAD, n=(32, 32))
+    X = I.exact_coefficients(w, 1.0)
+    out = {"workload": "euler2d Q2 on 32^2, t = 1", "steps": g["steps"],
+           "l2_error_oracle": g["l2_error"]}
+    for tag, prec in (("mixed_tf32", R.RIDG_PREC_MIXED_TF32), ("mixed_fp32", R.RIDG_PREC_MIXED_FP32),
+                      ("fp64", R.RIDG_PREC_FP64)):
+        s = R.Solver(2, w["n"], w["M"], flux="euler", cfl=w["cfl"], lo=w["lo"], hi=w["hi"],
+                     gamma=w["gamma"], precision=prec)
+        s.set_state(I.initial_state(w))
+        s.set_dt(g["dt"])
+        s.step(g["steps"])
+        s.sync()
+        e = OE.l2_relative_error(s.get_state(), X, w["M"], 2, m=4)
+        s.close()
+        out[tag] = {"l2_error": e, "equal_accuracy": bool(e <= 1.05 * g["l2_error"])}
+    return out
+
+
+def ensemble_accuracy(R, I, prec):
+    """The ensemble's equal-accuracy check on instances capped at 16^2 (the oracle's errors are
+    on record for them, tests/golden): one batched run, each instance to half its shock time
+    in a common step count; the worst ratio of an instance's L2 error against the exact
+    pre-shock solution to the oracle's."""
+    from oracle import error as OE
+    g = _golden().get("burgers_ens16")
+    if g is None:
+        return None
+    ens = [dict(w, n=(min(w["n"][0], 16), min(w["n"][1], 16))) for w in I.burgers_ensemble()]
+    b = R.ridg_batch_create([R.make_mesh(2, w["n"]) for w in ens], [w["M"] for w in ens],
+                            R.make_flux("burgers"), ens[0]["cfl"], R.make_options(precision=prec))
+    N = g["steps"]
+    for i, (w, T) in enumerate(zip(ens, g["T"])):
+        h = R.ridg_batch_instance(b, i)
+        R.ridg_set_state(h, I.initial_state(w))
+        R.ridg_set_dt(h, T / N)
+    R.ridg_batch_step(b, N)
+    R.ridg_batch_sync(b)
+    errs = []
+    for i in g["instances"]:            # the instances the oracle's errors are on record for
+        w, T = ens[i], g["T"][i]
+        q = np.empty((int(np.prod(w["n"])), (w["M"] + 1) ** 2))
+        R.ridg_get_state(R.ridg_batch_instance(b, i), q)
+        errs.append(OE.l2_relative_error(q, I.exact_coefficients(w, T), w["M"], 2))
+    R.ridg_batch_destroy(b)
+    ratios = [e / o for e, o in zip(errs, g["l2_error"])]
+    return {"workload": "burgers ensemble capped at 16^2, T_i = t_shock_i / 2 (all 64 "
+                        "instances in the batch; the first four of each degree checked "
+                        "against the oracle)", "steps": N,
+            "l2_error_max": max(errs), "l2_error_oracle_max": max(g["l2_error"]),
+            "worst_ratio_to_oracle": max(ratios), "equal_accuracy": bool(max(ratios) <= 1.05)}
 
 
 # ---------------------------------------------------------------------------------------
@@ -657,55 +670,51 @@ def _peaks():
     return 6800.0, 1900.0, "fallback"
 
 
-def run_ours(args):
+def linear_arm(R, I, w, args, ws, flush, clocks=None, steps=None):
+    """One linear-advection workload: the digit-count gate, the timed mixed path (whole steps
+    through ridg_step and the per-kernel split), the FP64 path beside it, the end-to-end
+    number through the C ABI with host buffers, the accuracy figures and the roofline of the
+    dominant kernel."""
     import torch
     import torch.distributed as dist
-
-    ws, rank, local = _dist()
-    if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    from paper_2101_01231_gb300 import inputs as I
-    from paper_2101_01231_gb300 import ridg as R
-
-    w = I.workload(args.workload)
-    prec_name = args.precision
+    steps = steps or args.steps
+    noisy = w.get("ic") == "sin+noise"
     prec = {"fp64": R.RIDG_PREC_FP64, "mixed": R.RIDG_PREC_MIXED_BF16}
-    if prec_name == "auto":
-        prec_name = "mixed"
-        try:
-            s_try = R.Solver(w["dim"], w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"],
-                             hi=w["hi"], precision=R.RIDG_PREC_MIXED_BF16, slices=args.slices)
-            s_try.close()
-        except R.RidgError:
-            prec_name = "fp64"
-
-    chosen = [args.slices]  # digit slices of the mixed path (0: the library's default)
+    prec_name = args.precision if args.precision != "auto" else "mixed"
+    chosen = [args.slices]
 
     def make(pname, slices=None):
         return R.Solver(w["dim"], w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"],
                         hi=w["hi"], precision=prec[pname],
                         slices=chosen[0] if slices is None else slices)
 
+    if prec_name == "mixed":
+        try:
+            make("mixed").close()
+        except R.RidgError:
+            prec_name = "fp64"
     cells = int(np.prod(w["n"]))
     thS = (w["M"] + 1) ** w["dim"]
     K = upwind_cells(w) * thS
     dof = cells * thS
     q0 = I.initial_state(w)
+    exact = None if noisy else I.exact_coefficients(w, T_FINAL)
 
     def accuracy(pname, slices=None):
+        """L2 error against the exact solution at t = 1: for the noisy data integrated exactly
+        on the sub-box overlaps of the carried piecewise polynomial, else eq. l2relerror
+        against the exact solution's Q(M+1) projection (ridg_l2_error)."""
         s = make(pname, slices)
         s.set_state(q0)
         nt = s.set_final_time(T_FINAL)
         s.step(nt)
         s.sync()
-        e = s.l2_error(I.exact_coefficients(w, T_FINAL))
+        e = (I.shifted_polynomial_error(w, q0, s.get_state(), T_FINAL) if noisy
+             else s.l2_error(exact))
         s.close()
         return e, nt
 
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB
-
-    def timed(pname, steps, warmup, clocks=None):
+    def timed(pname, nsteps, warmup, ck=None):
         """Whole steps through ridg_step (the captured graph: prediction and correction back to
         back), timed with CUDA events on the handle's stream, L2 flushed before each; then
         the per-kernel split (prediction / correction, events around each launch) under the
@@ -720,15 +729,15 @@ def run_ours(args):
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
-        if clocks:
-            clocks.start()
+        if ck:
+            ck.start()
         # a GPU-side wait (outside every timed interval) lets the host queue the flushes,
         # events and steps ahead of the GPU, so no host launch latency falls between an
         # event pair (on a slow host it otherwise does: +27 us per step seen once)
         with torch.cuda.stream(s.stream):
-            torch.cuda._sleep(int(2.0e9 * min(0.2, 1e-4 * steps + 0.02)))
+            torch.cuda._sleep(int(2.0e9 * min(0.2, 1e-4 * nsteps + 0.02)))
         evs = []
-        for i in range(steps):
+        for i in range(nsteps):
             with torch.cuda.stream(s.stream):
                 flush.fill_(float(i))
             a = torch.cuda.Event(enable_timing=True)
@@ -740,9 +749,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
-        ck = clocks.stop() if clocks else None
-        tt = sum(a.elapsed_time(b) for a, b in evs) / steps
-        nsplit = min(steps, 50)
+        ckr = ck.stop() if ck else None
+        tt = sum(a.elapsed_time(b) for a, b in evs) / nsteps
+        nsplit = min(nsteps, 50)
         tp = tc = 0.0
         for i in range(nsplit):
             with torch.cuda.stream(s.stream):
@@ -751,33 +760,29 @@ def run_ours(args):
             tp += p["predict_ms"]
             tc += p["correct_ms"]
         torch.cuda.synchronize()
-        return s, tt, tp / nsplit, tc / nsplit, ck
+        return s, tt, tp / nsplit, tc / nsplit, ckr
 
-    try:
-        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
-        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
-    except Exception:
-        gpu_id = str(torch.cuda.current_device())
-    clocks = Clocks(gpu_id)
     # the mixed form's digit count: the fewest slices whose L2 error against the exact
     # solution at t = 1 is within 1.05x of the FP64 path's (which matches the oracle's)
     sweep = None
+    e64, nt = accuracy("fp64")
     if prec_name == "mixed" and args.slices == 0:
-        e64_ref = accuracy("fp64")[0]
         sweep = {}
         for S in range(3, 8):
-            sweep[S] = accuracy("mixed", S)[0]
-            if sweep[S] <= 1.05 * e64_ref:
+            try:
+                sweep[S] = accuracy("mixed", S)[0]
+            except R.RidgError:
+                break
+            if sweep[S] <= 1.05 * e64:
                 chosen[0] = S
                 break
-    s, ms_step, ms_pred, ms_corr, ck = timed(prec_name, args.steps, args.warmup, clocks)
+    s, ms_step, ms_pred, ms_corr, ck = timed(prec_name, steps, args.warmup, clocks)
     slices_used = s.info()["slices"]
     ms_step = max_over_ranks(ms_step, ws, "cuda")
-    value = ws * dof / (ms_step * 1e-3)
 
     # end to end through the C ABI with host buffers: H2D state, one step, D2H state
     qh = torch.from_numpy(q0.copy()).pin_memory().numpy()
-    n_e2e = min(args.steps, 50)
+    n_e2e = min(steps, 20)
     for _ in range(3):
         s.set_state(qh)
         s.step(1)
@@ -791,71 +796,143 @@ def run_ours(args):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / n_e2e, ws, "cuda")
     s.close()
 
-    # the FP64 form beside the headline precision (same timing rules, fewer steps)
     fp64 = None
     if prec_name != "fp64":
-        s2, ms64, mp64, mc64, _ = timed("fp64", max(20, args.steps // 5), args.warmup)
+        s2, ms64, mp64, mc64, _ = timed("fp64", max(10, steps // 5), args.warmup)
         s2.close()
         fp64 = {"ms_per_step": ms64, "value": dof / (ms64 * 1e-3), "predict_ms": mp64,
                 "correct_ms": mc64}
-
-    err, nt = accuracy(prec_name)
-    err64 = accuracy("fp64")[0] if prec_name != "fp64" else err
-    gold = _golden().get(args.workload, {})
-    err_oracle = gold.get("l2_error")
+    err = accuracy(prec_name)[0] if prec_name != "fp64" else e64
 
     hbm, bf16, src = _peaks()
-    # Algorithmic work of the prediction launch (time mean): 2 theta_S K flop per cell with
-    # K = theta_S times the upwind region cells the centre depends on (the other region
-    # cells' operator columns are exactly zero), and the bytes it fundamentally moves: read
-    # Q and write W-bar, 2 x 8 theta_S B per cell.
+    # Algorithmic work per launch.  Prediction (time mean): 2 theta_S K flop per cell (K =
+    # theta_S x the upwind region cells; the other region cells' operator columns are exactly
+    # zero) and its bytes: read Q, write W-bar (2 x 8 theta_S B per cell).  Correction: read
+    # W-bar (8 theta_S; double-float pairs in the mixed path), read and write Q (16 theta_S);
+    # the 2D mixed correction reads the fused outputs instead of W-bar (theta_S + 2 (M + 1)
+    # pairs).
     flops_pred = 2.0 * thS * K * cells
     bytes_pred = 2.0 * 8 * thS * cells
-    traffic = _recorded_traffic(prec_name)
+    nfused = thS + 2 * (w["M"] + 1) if w["dim"] == 2 else thS
+    bytes_corr = (8.0 * nfused + 16.0 * thS) * cells
     if prec_name == "fp64":
         # FP64 FMA pipe: 152 SMs x 2 FP64 FMA / clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
         roof = {"bound": "alu", "kernel": "predict_fp64",
                 "achieved": flops_pred / (ms_pred * 1e-3) / 1e12, "peak": 1.25, "unit": "TFLOP/s",
-                "traffic": traffic,
+                "traffic": _recorded_traffic("fp64"),
                 "peak_source": "nominal FP64 rate (152 SMs x 4 flop/clk x 2.07 GHz)"}
     else:
-        # At 18 flop/B the contraction sits far below the ridge: it is bound by moving Q and
-        # W-bar through HBM.  The executed tensor work (S(S+1)/2 digit-pair products, padded
-        # to 32 outputs) is reported beside it.
         S_ = slices_used
         executed = 2.0 * (S_ * (S_ + 1) // 2) * 32 * K * cells
-        roof = {"bound": "hbm", "kernel": "mixed_gemm (fused prediction)",
+        tag = "mixed3" if w["dim"] == 3 else "mixed"
+        gemm = {"bound": "hbm", "kernel": f"{tag}_gemm (prediction)", "ms": ms_pred,
                 "achieved": bytes_pred / (ms_pred * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                "traffic": traffic, "peak_source": f"HBM copy, {src}",
+                "traffic": _recorded_traffic(tag + "gemm", cells),
+                "peak_source": f"HBM copy, {src}",
+                "algorithmic_bytes_per_cell": 16.0 * thS,
                 "tensor_executed_tflops": executed / (ms_pred * 1e-3) / 1e12,
-                "tensor_peak_tflops": bf16}
+                "tensor_peak_tflops": bf16,
+                "algorithmic_tflops": flops_pred / (ms_pred * 1e-3) / 1e12}
+        corr = {"bound": "hbm", "kernel": f"{tag}_correct (correction)", "ms": ms_corr,
+                "achieved": bytes_corr / (ms_corr * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "traffic": _recorded_traffic(tag + "corr", cells),
+                "peak_source": f"HBM copy, {src}",
+                "algorithmic_bytes_per_cell": bytes_corr / cells}
+        for r in (gemm, corr):
+            r["frac"] = r["achieved"] / r["peak"]
+        roof = dict(corr if ms_corr >= ms_pred else gemm)
+        roof["other_kernel"] = gemm if ms_corr >= ms_pred else corr
+        # the whole step against the bytes it fundamentally moves (Q in and out)
+        roof["step_bytes_per_cell"] = 16.0 * thS
+        roof["step_frac"] = 16.0 * thS * cells / (ms_step * 1e-3) / 1e9 / hbm
     roof["frac"] = roof["achieved"] / roof["peak"]
-
-    line = {
-        "metric": "element-DOF updates/s per RIDG step",
-        "value": value, "unit": "element-DOF updates/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec_name == "fp64" else "bf16x{}+f64".format(slices_used),
-        "data": "synthetic",
-        "config": {"workload": w["name"], "cells": cells, "order": w["M"], "theta_s": thS,
-                   "precision": prec_name, "steps_to_T": nt, "l2_flush": "256 MB rewrite before each timed step",
-                   "l2_error": err, "l2_error_fp64_gpu": err64, "l2_error_oracle": err_oracle,
-                   "equal_accuracy": (err <= 1.05 * err_oracle) if err_oracle else None,
-                   "slices_sweep_l2_error": ({str(k): v for k, v in sweep.items()} if sweep else None)},
+    gate_ref = e64
+    out = {
+        "workload": w["name"], "cells": cells, "order": w["M"], "theta_s": thS,
+        "precision": prec_name, "slices": slices_used if prec_name == "mixed" else None,
+        "steps": steps, "ms_per_step": ms_step, "value": ws * dof / (ms_step * 1e-3),
+        "unit": "element-DOF updates/s", "steps_to_T": nt,
         "kernels_ms": {"predict": ms_pred, "correct": ms_corr},
-        "fp64_path": fp64,
-        "roofline": roof,
+        "fp64_path": fp64, "roofline": roof,
         "e2e": {"value": ws * dof / e2e_s, "unit": "element-DOF updates/s",
                 "h2d_bytes_per_step": int(q0.nbytes), "d2h_bytes_per_step": int(q0.nbytes)},
-        "gpu_launches": 2 * args.steps,
+        "accuracy": {"T": T_FINAL,
+                     "measure": ("exact: the noisy piecewise polynomial carried by a t, "
+                                 "integrated on the sub-box overlaps") if noisy
+                                else "eq. l2relerror against the exact solution's Q(M+1) projection",
+                     "l2_error": err, "l2_error_fp64_gpu": e64,
+                     "equal_accuracy": bool(err <= 1.05 * gate_ref),
+                     "slices_sweep_l2_error": ({str(k): v for k, v in sweep.items()}
+                                               if sweep else None)},
         "clocks": ck,
     }
+    gold = _golden()
+    if w["name"] in gold and not noisy:
+        g = gold[w["name"]]
+        out["accuracy"]["l2_error_oracle"] = g["l2_error"]
+        out["accuracy"]["equal_accuracy_vs_oracle"] = bool(err <= 1.05 * g["l2_error"])
+    elif noisy and "adv3d_n24_q2_noise" in gold:
+        # the oracle at full size would take hours (~44 s per step on the host): its error is
+        # on record for the same data on a 24^3 mesh, where the GPU paths are checked against
+        # it by the GPU tests; at full size the FP64 GPU path (per-step parity 1e-12) stands in
+        out["accuracy"]["l2_error_oracle_24cubed"] = gold["adv3d_n24_q2_noise"]["l2_error"]
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2101_01231_gb300 import inputs as I
+    from paper_2101_01231_gb300 import ridg as R
+
+    w = I.workload(args.workload)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB
+    try:
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        gpu_id = str(torch.cuda.current_device())
+    head = linear_arm(R, I, w, args, ws, flush, Clocks(gpu_id))
+    acc = head["accuracy"]
+    line = {
+        "metric": "element-DOF updates/s per RIDG step",
+        "value": head["value"], "unit": "element-DOF updates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head["precision"] == "fp64" else "bf16x{}+f64".format(head["slices"]),
+        "data": "synthetic",
+        "config": {"workload": w["name"], "cells": head["cells"], "order": w["M"],
+                   "theta_s": head["theta_s"], "precision": head["precision"],
+                   "steps_to_T": head["steps_to_T"],
+                   "l2_flush": "state (191 MB) larger than L2, and a 256 MB rewrite before each "
+                               "timed step" if w["dim"] == 3 else
+                               "256 MB rewrite before each timed step",
+                   "l2_error": acc["l2_error"], "l2_error_fp64_gpu": acc["l2_error_fp64_gpu"],
+                   "l2_error_oracle": acc.get("l2_error_oracle",
+                                              acc.get("l2_error_oracle_24cubed")),
+                   "equal_accuracy": acc["equal_accuracy"],
+                   "slices_sweep_l2_error": acc["slices_sweep_l2_error"],
+                   "error_measure": acc["measure"]},
+        "kernels_ms": head["kernels_ms"],
+        "fp64_path": head["fp64_path"],
+        "roofline": head["roofline"],
+        "e2e": head["e2e"],
+        "gpu_launches": 2 * args.steps,
+        "clocks": head["clocks"],
+    }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_oracle(w, args.cpu_seconds)
-    if args.mixed3d_steps > 0:
-        line["mixed3d"] = mixed3d_section(R, I, args.mixed3d_steps, args.warmup,
-                                          cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline))
+        line["cpu_baseline"] = (cpu_oracle_sampled(w, I.initial_state(w)) if w["dim"] == 3
+                                else cpu_oracle(w, args.cpu_seconds))
+    if args.adv2d_steps > 0 and args.workload != WORKLOAD_2D:
+        w2 = I.workload(WORKLOAD_2D)
+        line["adv2d"] = linear_arm(R, I, w2, args, ws, flush, None, steps=args.adv2d_steps)
+        if rank == 0 and not args.no_cpu_baseline and ws == 1:
+            line["adv2d"]["cpu_oracle"] = cpu_oracle(w2, args.cpu_seconds)
     if args.newton_steps > 0:
         line["newton"] = newton_section(R, I, args.newton_steps, 8 if args.no_cpu_baseline else 16)
     if args.adv1d_reps > 0:

@@ -81,10 +81,14 @@ enum {
                                 refinement); correction, face sums and time in FP64       */
   RIDG_PREC_MIXED_FP32 = 2,  /* Newton linear solves in FP32 with the residual in FP64
                                 (nonlinear flux)                                          */
-  RIDG_PREC_MIXED_TF32 = 3   /* Newton linear solves with the Schur-complement block
+  RIDG_PREC_MIXED_TF32 = 3,  /* Newton linear solves with the Schur-complement block
                                 updates on the TF32 tensor cores (FP32 accumulation), FP32
                                 pivot inverses, and refinement sweeps against the FP64
                                 residual (nonlinear flux)                                 */
+  RIDG_PREC_MIXED_FP16 = 4   /* as MIXED_BF16 with FP16 digit operands: the balanced
+                                base-256 digits are exact in FP16 as in BF16 and every
+                                digit product and FP32 sum is the same, so the results are
+                                bit-identical to MIXED_BF16 at the same tensor rate        */
 };
 
 typedef void* (*ridg_alloc_fn)(size_t bytes, void* user);
@@ -92,7 +96,8 @@ typedef void (*ridg_free_fn)(void* ptr, void* user);
 
 typedef struct {
   int precision;          /* RIDG_PREC_*                                                */
-  int slices;             /* BF16 slices per operand for MIXED_BF16, 2..7 (0 = default 6)     */
+  int slices;             /* digit slices per operand for MIXED_BF16 / MIXED_FP16, 2..7
+                             (0 = default 6)                                                */
   int newton_max_iters;   /* 0 = default 4                                              */
   double newton_tol;      /* <= 0 = default 1e-10: stop when ||dW||_inf <= tol max(1,||W||_inf) */
   void* stream;           /* cudaStream_t (not the legacy default stream) or NULL       */
@@ -114,6 +119,11 @@ typedef struct {
   int precision, slices;
   long long newton_iters_total; /* Newton iterations summed over the regions of the last
                                    prediction (or of the steps of the last ridg_step)      */
+  long long newton_hist[16];    /* regions by Newton iteration count over the same span
+                                   (entry k: k iterations; entry 15: 15 or more)           */
+  double mass[4];               /* sum over cells of |T| Q_{e, r, 0} per conserved variable
+                                   r < m (Sec. 2.3: conserved by the correction); the
+                                   entries beyond m are 0                                  */
 } ridg_info_t;
 
 /* ----- lifecycle -------------------------------------------------------------------- */
@@ -158,8 +168,11 @@ int ridg_set_final_time(ridg_t* h, double T, long long* nsteps);
 /* ----- the step ---------------------------------------------------------------------- */
 
 /* Prediction (Sec. 2.2): every cell's centre space-time coefficients W_i from the
- * current state.  If w_out is not NULL it receives cells * m * theta_T doubles
- * (prediction layout; device pointer if on_device).  The prediction is also kept for a
+ * current state.  With a mixed linear precision it runs the split-digit tensor-core
+ * contraction of all theta_T rows in 1D / 2D; in 3D ridg_predict computes the full
+ * prediction in FP64 (the mixed 3D path contracts only the time-mean rows the step needs).
+ * If w_out is not NULL it receives cells * m * theta_T doubles (prediction layout; device
+ * pointer if on_device).  The prediction is also kept for a
  * following ridg_correct.  Returns RIDG_ENOCONV (after completing) if Newton hit its cap
  * in some region.  Synchronous when w_out is a host pointer.                            */
 int ridg_predict(ridg_t* h, double* w_out, int on_device);
@@ -177,6 +190,8 @@ int ridg_sync(ridg_t* h);
 
 /* ----- diagnostics -------------------------------------------------------------------- */
 
+/* Problem sizes, time, step count, Newton statistics of the last prediction / ridg_step and
+ * the current mass (Sec. 2.3).  Computing the mass waits for the handle's stream.          */
 int ridg_info(ridg_t* h, ridg_info_t* info);
 
 /* sum over cells of |T| Q_{e, r, 0} for each conserved variable r (mass[m]).            */
@@ -241,6 +256,9 @@ int ridg_batch_create(int count, const ridg_mesh* meshes, const int* orders,
 void ridg_batch_destroy(ridg_batch_t* b);
 /* Instance i of the batch as an ordinary handle (owned by the batch).                    */
 ridg_t* ridg_batch_instance(ridg_batch_t* b, int i);
+/* ridg_set_state / ridg_get_state of instance i (RIDG_EINVAL for an index out of range).  */
+int ridg_batch_set_state(ridg_batch_t* b, int i, const double* q, int on_device);
+int ridg_batch_get_state(ridg_batch_t* b, int i, double* q, int on_device);
 int ridg_batch_step(ridg_batch_t* b, int n);
 int ridg_batch_sync(ridg_batch_t* b);
 

@@ -61,6 +61,13 @@ Grid grid_of(const ridg_t* h) {
 
 bool is_linear(const ridg_t* h) { return h->flux.kind == RIDG_FLUX_ADVECTION; }
 
+// the split-digit tensor-core form of the linear path (BF16 or FP16 digit operands)
+bool is_mixed_linear(const ridg_t* h) {
+  return h->opt.precision == RIDG_PREC_MIXED_BF16 || h->opt.precision == RIDG_PREC_MIXED_FP16;
+}
+
+bool digits_f16(const ridg_t* h) { return h->opt.precision == RIDG_PREC_MIXED_FP16; }
+
 int newton_prec(const ridg_t* h) {
   return h->opt.precision == RIDG_PREC_MIXED_TF32   ? ridg::kNewtonTF32
          : h->opt.precision == RIDG_PREC_MIXED_FP32 ? ridg::kNewtonF32
@@ -110,6 +117,13 @@ CorrParams corr_params(const ridg_t* h) {
   return cp;
 }
 
+// exponent words of the mixed path: [2] = 1 for FP16 digit operands (read by the kernels)
+cudaError_t init_exps(ridg_t* h) {
+  static const int zero[4] = {0, 0, 0, 0}, one[4] = {0, 0, 1, 0};
+  return cudaMemcpyAsync(h->ms.exps, digits_f16(h) ? one : zero, 4 * sizeof(int),
+                         cudaMemcpyHostToDevice, h->stream);
+}
+
 // (Re)build the linear operator for the current dt and upload it.
 int rebuild_linear(ridg_t* h) {
   double nu[3] = {0, 0, 0};
@@ -118,7 +132,7 @@ int rebuild_linear(ridg_t* h) {
     return set_err(h, RIDG_EINVAL, "region system is singular for this dt");
   RIDG_CUDA(h, cudaMemcpyAsync(h->P, h->P_host.data(), sizeof(double) * h->P_host.size(),
                                cudaMemcpyHostToDevice, h->stream));
-  if (h->opt.precision == RIDG_PREC_MIXED_BF16 && h->dim == 3) {
+  if (is_mixed_linear(h) && h->dim == 3) {
     // 3D: the time-mean rows P-bar (first theta_S rows of P) on the tensor cores; the
     // correction stays the FP64 kernel
     std::vector<double> Pbar(h->P_host.begin(), h->P_host.begin() + (size_t)h->thS * h->K);
@@ -126,7 +140,7 @@ int rebuild_linear(ridg_t* h) {
     std::vector<double> rscale;
     std::vector<float> rowmul;
     int rc = ridg::mixed_build(3, h->nb, Pbar, h->thS, h->opt.slices, h->box, digits, rscale,
-                               rowmul, h->mixed);
+                               rowmul, h->mixed, digits_f16(h));
     if (rc != RIDG_OK) return set_err(h, rc, "3D mixed operator build failed");
     if (!h->mixed.b_slices) {
       h->mixed.b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
@@ -153,13 +167,14 @@ int rebuild_linear(ridg_t* h) {
       h->ms.maxbits = (unsigned long long*)dev_alloc(h, 2 * sizeof(unsigned long long));
       if (!h->ms.planes || !h->ms.exps || !h->ms.maxbits)
         return set_err(h, RIDG_ENOMEM, "mixed-path allocation failed");
+      RIDG_CUDA(h, init_exps(h));
       RIDG_CUDA(h, cudaMemsetAsync(h->ms.planes, 0, pb, h->stream));
       if (ridg::mixed3_make_map(g, h->nb, h->opt.slices, h->ms.planes, h->ms.map) != RIDG_OK)
         return set_err(h, RIDG_ECUDA, "tensor map creation failed");
       h->ms.status = h->status;
     }
     h->ms.valid = false;
-  } else if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+  } else if (is_mixed_linear(h)) {
     // fused step operator: rows [V; u_x; u_y] = C P-bar with C mapping the time mean W-bar to
     // the volume term sum_d nu_d (D along d) W-bar and the upwind face traces nu_d tr(W-bar)
     const int nb = h->nb, thS = h->thS, K = h->K, nout = thS + 2 * nb;
@@ -191,7 +206,7 @@ int rebuild_linear(ridg_t* h) {
       std::vector<double> rscale;
       std::vector<float> rowmul;
       int rc = ridg::mixed_build(h->dim, h->nb, *p.g, p.nout, h->opt.slices, h->box, digits,
-                                 rscale, rowmul, *p.op);
+                                 rscale, rowmul, *p.op, digits_f16(h));
       if (rc != RIDG_OK) return set_err(h, rc, "mixed operator build failed");
       if (!p.op->b_slices) {
         p.op->b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
@@ -218,6 +233,7 @@ int rebuild_linear(ridg_t* h) {
       h->ms.maxbits = (unsigned long long*)dev_alloc(h, 2 * sizeof(unsigned long long));
       if (!h->Y || !h->ms.planes || !h->ms.exps || !h->ms.maxbits)
         return set_err(h, RIDG_ENOMEM, "mixed-path allocation failed");
+      RIDG_CUDA(h, init_exps(h));
       RIDG_CUDA(h, cudaMemsetAsync(h->ms.planes, 0, ridg::mixed_plane_bytes(g, h->nb, h->opt.slices),
                                    h->stream));
       if (ridg::mixed_make_map(g, h->nb, h->opt.slices, nout, h->ms.planes, h->ms.map) != RIDG_OK ||
@@ -238,7 +254,7 @@ int sign_of(double v) { return v > 0 ? 1 : (v < 0 ? -1 : 0); }
 
 // Mixed path: make the digit planes describe the current state (outside graph capture).
 int ensure_digits(ridg_t* h) {
-  if (h->opt.precision != RIDG_PREC_MIXED_BF16 || h->ms.valid) return RIDG_OK;
+  if (!is_mixed_linear(h) || h->ms.valid) return RIDG_OK;
   if (h->dim == 3)
     RIDG_CUDA(h, ridg::launch_mixed3_refresh(grid_of(h), h->nb, h->opt.slices, h->Q, h->ms, h->stream));
   else
@@ -285,9 +301,9 @@ int enqueue_nl_correct(ridg_t* h) {
 int enqueue_predict_mean(ridg_t* h) {
   if (!is_linear(h)) return enqueue_newton(h);
   Grid g = grid_of(h);
-  if (h->opt.precision == RIDG_PREC_MIXED_BF16 && h->dim == 3) {
+  if (is_mixed_linear(h) && h->dim == 3) {
     RIDG_CUDA(h, ridg::launch_mixed3_gemm(g, h->nb, h->mixed, h->ms, h->Y, h->stream));
-  } else if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+  } else if (is_mixed_linear(h)) {
     RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed, h->ms, h->Y, 1, h->ncell, true,
                                          h->stream));
   } else {
@@ -300,11 +316,11 @@ int enqueue_predict_mean(ridg_t* h) {
 int enqueue_correct_after_mean(ridg_t* h) {
   if (!is_linear(h)) return enqueue_nl_correct(h);
   CorrParams cp = corr_params(h);
-  if (h->opt.precision == RIDG_PREC_MIXED_BF16 && h->dim == 3) {
+  if (is_mixed_linear(h) && h->dim == 3) {
     // double-float correction from the time means, with the new state's digit planes
     RIDG_CUDA(h, ridg::launch_mixed3_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
                                              h->mixed.gmax, cp, h->ms, h->stream));
-  } else if (h->opt.precision == RIDG_PREC_MIXED_BF16) {
+  } else if (is_mixed_linear(h)) {
     RIDG_CUDA(h, ridg::launch_mixed_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
                                             h->mixed.gmax, cp, sign_of(h->flux.vel[0]),
                                             sign_of(h->flux.vel[1]), h->ms, h->stream));
@@ -335,13 +351,13 @@ int enqueue_step(ridg_t* h) {
 cudaError_t clear_newton_stats(ridg_t* h) {
   cudaError_t e = cudaMemsetAsync(h->nl_words + 1, 0, 3 * sizeof(int), h->stream);
   if (e != cudaSuccess) return e;
-  return cudaMemsetAsync(h->nl_words + 6, 0, 2 * sizeof(int), h->stream);
+  return cudaMemsetAsync(h->nl_words + 6, 0, 18 * sizeof(int), h->stream);
 }
 
 // Newton statistics since they were last cleared: regions at the iteration cap, largest
 // iteration count, flags (1: zero pivot, 2: non-finite update, 4: tensor-core wait timed out).
 int read_newton_stats(ridg_t* h) {
-  int w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int w[24] = {0};
   RIDG_CUDA(h, cudaMemcpyAsync(w, h->nl_words, sizeof(w), cudaMemcpyDeviceToHost, h->stream));
   RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
   const int unconverged = w[1], iters_max = w[2], flags = w[3];
@@ -350,6 +366,7 @@ int read_newton_stats(ridg_t* h) {
   h->newton_unconverged = unconverged;
   h->newton_iters_max = iters_max;
   h->newton_iters_total = (long long)total;
+  for (int k = 0; k < 16; ++k) h->newton_hist[k] = w[8 + k];
   if (flags & 4) return set_err(h, RIDG_ETIMEOUT, "a bounded tensor-core wait in the Newton solve gave up");
   if (flags & 2) return set_err(h, RIDG_ENONFINITE, "Newton produced a non-finite update");
   if (flags & 1) return set_err(h, RIDG_ENONFINITE, "zero pivot in a Newton block solve");
@@ -401,7 +418,8 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
   const int prec = opt ? opt->precision : RIDG_PREC_FP64;
   int m = 1;
   if (flux->kind == RIDG_FLUX_ADVECTION) {
-    if (prec != RIDG_PREC_FP64 && prec != RIDG_PREC_MIXED_BF16) return RIDG_EINVAL;
+    if (prec != RIDG_PREC_FP64 && prec != RIDG_PREC_MIXED_BF16 && prec != RIDG_PREC_MIXED_FP16)
+      return RIDG_EINVAL;
   } else if (flux->kind == RIDG_FLUX_BURGERS || flux->kind == RIDG_FLUX_EULER) {
     m = flux->kind == RIDG_FLUX_EULER ? 4 : 1;
     if (mesh->dim != 2 || !ridg::newton_supported(order + 1, m)) return RIDG_EINVAL;
@@ -445,7 +463,7 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
   if (is_linear(h)) h->box = ridg::upwind_box(h->dim, h->flux.vel);
   h->K = h->box.n * h->thS;
   h->cfl = cfl;
-  if (h->opt.precision == RIDG_PREC_MIXED_BF16 &&
+  if (is_mixed_linear(h) &&
       (h->dim == 3 ? !ridg::mixed3_supported(h->nb, h->opt.slices)
                    : (!ridg::mixed_supported(h->dim, h->nb, h->thT) || h->opt.slices < 2 ||
                       h->opt.slices > 7))) {
@@ -496,7 +514,7 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
     h->nl_scratch_cta = ridg::newton_scratch_per_cta(h->nb, h->m, newton_prec(h), h->plan);
     const size_t scratch = h->nl_scratch_cta * (size_t)h->nl_grid;
     h->nl_scratch = h->nl_grid > 0 ? dev_alloc(h, scratch) : nullptr;
-    h->nl_words = (int*)dev_alloc(h, 8 * sizeof(int));
+    h->nl_words = (int*)dev_alloc(h, 24 * sizeof(int));
     if (!tb_mem || !h->nl_scratch || !h->nl_words) {
       dev_free(h, tb_mem);
       ridg_destroy(h);
@@ -510,7 +528,7 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
     }
     // the blocks' zero padding is never written again
     if (cudaMemsetAsync(h->nl_scratch, 0, scratch, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->nl_words, 0, 8 * sizeof(int), h->stream) != cudaSuccess) {
+        cudaMemsetAsync(h->nl_words, 0, 24 * sizeof(int), h->stream) != cudaSuccess) {
       ridg_destroy(h);
       return RIDG_ECUDA;
     }
@@ -659,7 +677,7 @@ int ridg_predict(ridg_t* h, double* w_out, int on_device) {
                                    h->stream));
     }
     return read_newton_stats(h);
-  } else if (h->opt.precision == RIDG_PREC_MIXED_BF16 && h->dim == 2) {
+  } else if (is_mixed_linear(h) && h->dim == 2) {
     int rc = ensure_digits(h);
     if (rc) return rc;
     RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed_pred, h->ms, h->W, h->thT, 1, false,
@@ -799,7 +817,9 @@ int ridg_info(ridg_t* h, ridg_info_t* info) {
   info->newton_iters_total = h->newton_iters_total;
   info->precision = h->opt.precision;
   info->slices = h->opt.slices;
-  return RIDG_OK;
+  for (int k = 0; k < 16; ++k) info->newton_hist[k] = h->newton_hist[k];
+  for (int r = 0; r < 4; ++r) info->mass[r] = 0.0;
+  return ridg_mass(h, info->mass);
 }
 
 int ridg_mass(ridg_t* h, double* mass) {
@@ -1026,6 +1046,16 @@ void ridg_batch_destroy(ridg_batch_t* b) {
 ridg_t* ridg_batch_instance(ridg_batch_t* b, int i) {
   if (!b || i < 0 || i >= (int)b->inst.size()) return nullptr;
   return b->inst[i];
+}
+
+int ridg_batch_set_state(ridg_batch_t* b, int i, const double* q, int on_device) {
+  ridg_t* h = ridg_batch_instance(b, i);
+  return h ? ridg_set_state(h, q, on_device) : RIDG_EINVAL;
+}
+
+int ridg_batch_get_state(ridg_batch_t* b, int i, double* q, int on_device) {
+  ridg_t* h = ridg_batch_instance(b, i);
+  return h ? ridg_get_state(h, q, on_device) : RIDG_EINVAL;
 }
 
 int ridg_batch_step(ridg_batch_t* b, int n) {

@@ -40,6 +40,7 @@
 // for the tensor core, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -128,6 +129,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
                  empty0 = tdone0 + 16u, opload = tdone0 + 32u;
   const uint32_t copy_bytes = L.copy_bytes;
   const int sexp = exps[0];  // exponent the digit planes were made with
+  const bool f16 = exps[2] != 0;  // FP16 (else BF16) digit operands
 
   auto issue_item = [&](int item) {
     const int kk = item / L.groups, q = item % L.groups, sl = item % NSL;
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
             const uint32_t dig = (uint32_t)((a - q * L.G) * P * kCopy);
             for (int c0 = 0; c0 < S - a; c0 += CMAX) {
               const int nn = (min(S - a, c0 + CMAX) - c0) * NOUTP;
-              const uint32_t idesc = idesc_bf16(128, nn);
+              const uint32_t idesc = idesc_digits(128, nn, f16);
               const uint32_t dcol = tst + (uint32_t)((a + c0) * NOUTP);
 #pragma unroll
               for (int r = 0; r < (NREGC ? NREGC : nreg); ++r) {
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed_gemm_kernel(
 // ---------------------------------------------------------------------------------------
 template <int NB, int S>
 __device__ __forceinline__ bool write_cell_digits(const double* q, int ix, int iy, int nx, int ny,
-                                                  int s, uint4* __restrict__ planes) {
+                                                  int s, uint4* __restrict__ planes, bool f16) {
   constexpr int THS = NB * NB;
   constexpr int P = ((THS + 15) / 16) * 2;
   const long long plane = (long long)(nx + 2) * (ny + 2);
@@ -360,7 +362,7 @@ __device__ __forceinline__ bool write_cell_digits(const double* q, int ix, int i
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = (p * 8 + j < THS) ? q[p * 8 + j] : 0.0;
     uint4 rows[S];
-    fits &= make_digit_rows<S>(v, s, rows);
+    fits &= make_digit_rows<S>(v, s, rows, f16);
 #pragma unroll
     for (int a = 0; a < S; ++a) {
       uint4* base = planes + (long long)(a * P + p) * plane;
@@ -381,7 +383,8 @@ __device__ __forceinline__ bool write_cell_digits(const double* q, int ix, int i
 // digit rows of mode group p (8 coefficients v) of cell (ix, iy) and its ghost copies
 template <int NB, int S>
 __device__ __forceinline__ bool write_group_digits(const double* v, int p, int ix, int iy, int nx,
-                                                   int ny, int s, uint4* __restrict__ planes) {
+                                                   int ny, int s, uint4* __restrict__ planes,
+                                                   bool f16) {
   constexpr int THS = NB * NB;
   constexpr int P = ((THS + 15) / 16) * 2;
   const long long plane = (long long)(nx + 2) * (ny + 2);
@@ -391,7 +394,7 @@ __device__ __forceinline__ bool write_group_digits(const double* v, int p, int i
   if (iy == 0) py[1] = ny + 1;
   if (iy == ny - 1) py[1] = 0;
   uint4 rows[S];
-  const bool fits = make_digit_rows<S>(v, s, rows);
+  const bool fits = make_digit_rows<S>(v, s, rows, f16);
 #pragma unroll
   for (int a = 0; a < S; ++a) {
     uint4* base = planes + (long long)(a * P + p) * plane;
@@ -422,7 +425,8 @@ __global__ void state_digits_kernel(const double* __restrict__ Q, int nx, int ny
 #pragma unroll
   for (int i = 0; i < THS; ++i) q[i] = Q[e * THS + i];
   const unsigned ue = (unsigned)e, uy = ue / (unsigned)nx;
-  if (!write_cell_digits<NB, S>(q, (int)(ue - uy * (unsigned)nx), (int)uy, nx, ny, s, planes))
+  if (!write_cell_digits<NB, S>(q, (int)(ue - uy * (unsigned)nx), (int)uy, nx, ny, s, planes,
+                                exps[2] != 0))
     atomicOr(status, kStatusRange);
 }
 
@@ -564,7 +568,7 @@ __global__ void __launch_bounds__(128) mixed_correct_kernel(
         qn[j] = 0.0;
       }
     }
-    fits = write_group_digits<NB, S>(qn, pg, ix, iy, nx, ny, snext, planes);
+    fits = write_group_digits<NB, S>(qn, pg, ix, iy, nx, ny, snext, planes, exps[2] != 0);
   }
   if (!fits) atomicOr(status, kStatusRange);
   const unsigned long long bm = block_max_bits(mymax, shmax);
@@ -590,7 +594,7 @@ static int nout_pad_of(int nout) { return nout <= 32 ? 32 : 64; }
 
 int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int slices,
                 const RegionBox& box, std::vector<unsigned short>& digits,
-                std::vector<double>& rscale, std::vector<float>& rowmul, MixedOp& op) {
+                std::vector<double>& rscale, std::vector<float>& rowmul, MixedOp& op, bool f16) {
   if (!mixed_supported(dim, nb, nout) || slices < 2 || slices > 7) return RIDG_EINVAL;
   if (dim == 3 && !mixed3_supported(nb, slices)) return RIDG_EINVAL;
   // region cells of G's columns: the upwind box, x fastest
@@ -622,9 +626,15 @@ int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int sli
         double sc = std::ldexp(v, kBits);
         double d = (cp + 1 < slices) ? std::floor(sc + 0.5) : std::nearbyint(sc);
         v = sc - d;  // exact
-        __nv_bfloat16 b = __float2bfloat16_rn((float)d);
+        // |d| <= 256: exact in BF16 and in FP16
         unsigned short bits;
-        std::memcpy(&bits, &b, 2);
+        if (f16) {
+          const __half b = __float2half_rn((float)d);
+          std::memcpy(&bits, &b, 2);
+        } else {
+          const __nv_bfloat16 b = __float2bfloat16_rn((float)d);
+          std::memcpy(&bits, &b, 2);
+        }
         const int row = cp * NOUTP + c;
         digits[((size_t)(kp / 8) * L.brows + row) * 8 + (kp % 8)] = bits;
       }

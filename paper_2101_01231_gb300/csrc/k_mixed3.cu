@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
   const uint32_t afull0 = bar, afree0 = bar + 8u * kNAmax, bfull = bar + 16u * kNAmax,
                  tdone0 = bfull + 8u, tempty0 = tdone0 + 16u;
   const int sexp = exps[0];
+  const bool f16 = exps[2] != 0;  // FP16 (else BF16) digit operands
 
   auto tile_origin = [&](int k, int& x0, int& y0, int& z0) {
     const int tile = blockIdx.x + k * gridDim.x;
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // A: LBO = plane stride inside a copy, SBO = one halo row of 8 cells (128 B)
             const uint64_t adesc0 = smem_desc(smem_u32(smem + sl * L.a_bytes), kCopy * 16, 128);
-            const uint32_t idesc = idesc_bf16(128, (S - a) * kNOUTP);
+            const uint32_t idesc = idesc_digits(128, (S - a) * kNOUTP, f16);
             const uint32_t dcol = tst + (uint32_t)(a * kNOUTP);
             for (int jy = 0; jy < ncy; ++jy) {
               const uint64_t bdesc0 =
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(128) mixed3_correct_kernel(
         }
       }
       uint4 rows[S];
-      fits &= make_digit_rows<S>(qn, snext, rows);
+      fits &= make_digit_rows<S>(qn, snext, rows, exps[2] != 0);
 #pragma unroll
       for (int a = 0; a < S; ++a) {
         uint4* base = planes + (long long)(a * P + pg) * plane;
@@ -530,7 +531,7 @@ __global__ void __launch_bounds__(128) state_digits3_kernel(const double* __rest
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = (p * 8 + j < THS) ? Q[e * THS + p * 8 + j] : 0.0;
   uint4 rows[S];
-  if (!make_digit_rows<S>(v, s, rows)) atomicOr(status, kStatusRange);
+  if (!make_digit_rows<S>(v, s, rows, exps[2] != 0)) atomicOr(status, kStatusRange);
   const long long pnx = nx + 2, pny = ny + 2;
   const long long plane = pnx * pny * (nz + 2);
   int px[2] = {ix + 1, -1}, py[2] = {iy + 1, -1}, pz[2] = {iz + 1, -1};

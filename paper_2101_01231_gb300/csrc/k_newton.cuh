@@ -1515,6 +1515,7 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newto
     if (tid == 0) {
       if (!conv) atomicAdd(&stats[0], 1);
       atomicMax(&stats[1], it);
+      atomicAdd(&stats[7 + (it < 15 ? it : 15)], 1);  // histogram of iteration counts
       atomicAdd(BATCH ? ctx->itot : a.iters_total, (unsigned long long)it);
       if (bad) atomicOr(stats + 2, kFlagNonFinite);
     }

@@ -6,6 +6,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -70,10 +71,11 @@ __device__ __forceinline__ long long to_fixed(double x, int s, int L) {
 }
 
 // The S balanced base-256 digits of one coefficient (fixed point with 8 S fraction bits
-// relative to 2^s), most significant first, as BF16 bit patterns (exact: |digit| <= 256).
-// Returns false if the value does not fit below 2^s.
+// relative to 2^s), most significant first, as BF16 (or, f16, FP16) bit patterns (exact
+// either way: |digit| <= 256).  Returns false if the value does not fit below 2^s.
 template <int S>
-__device__ __forceinline__ bool value_digit_bits(double x, int s, uint32_t (&bits)[S]) {
+__device__ __forceinline__ bool value_digit_bits(double x, int s, uint32_t (&bits)[S],
+                                                 bool f16 = false) {
   constexpr int L = kBits * S;
   const long long F = to_fixed(x, s, L);
   const bool fits = (F < (1LL << L)) && (F > -(1LL << L));
@@ -95,21 +97,24 @@ __device__ __forceinline__ bool value_digit_bits(double x, int s, uint32_t (&bit
   }
 #pragma unroll
   for (int a = 0; a < S; ++a)
-    // |d| <= 256: exact in FP32 by the 1.5 * 2^23 trick, and its BF16 is the top half
-    bits[a] = __float_as_uint(__int_as_float(0x4B400000 + d[a]) - 12582912.0f) >> 16;
+    // |d| <= 256: exact in FP32 by the 1.5 * 2^23 trick; its BF16 is the top half, its FP16
+    // the exact conversion
+    bits[a] = f16 ? (uint32_t)__half_as_ushort(__int2half_rn(d[a]))
+                  : __float_as_uint(__int_as_float(0x4B400000 + d[a]) - 12582912.0f) >> 16;
   return fits;
 }
 
 // S balanced base-256 digits of 8 consecutive coefficients, packed as BF16 (one 16 B row
 // per digit).  Returns false if a value does not fit below 2^s.
 template <int S>
-__device__ __forceinline__ bool make_digit_rows(const double* v, int s, uint4* rows) {
+__device__ __forceinline__ bool make_digit_rows(const double* v, int s, uint4* rows,
+                                                bool f16 = false) {
   uint32_t packed[S][4];
   bool fits = true;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     uint32_t b[S];
-    fits &= value_digit_bits<S>(v[j], s, b);
+    fits &= value_digit_bits<S>(v[j], s, b, f16);
 #pragma unroll
     for (int a = 0; a < S; ++a) {
       if (j & 1)

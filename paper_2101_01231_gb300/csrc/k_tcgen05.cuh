@@ -35,6 +35,17 @@ __device__ __forceinline__ uint32_t idesc_bf16(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+__device__ __forceinline__ uint32_t idesc_f16(int m, int n) {
+  // kind::f16 with FP16 operands: D = F32 (bit 4), A = B = FP16 (format 0), both K-major
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// the instruction descriptor of the digit products: FP16 or BF16 operands (both hold the
+// balanced base-256 digits exactly)
+__device__ __forceinline__ uint32_t idesc_digits(int m, int n, bool f16) {
+  return f16 ? idesc_f16(m, n) : idesc_bf16(m, n);
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t acc) {
   asm volatile(

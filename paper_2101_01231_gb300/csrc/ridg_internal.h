@@ -66,7 +66,8 @@ struct MixedState {
   void* planes = nullptr;                 // [digit x mode group][y + 2][x + 2][8] bf16
   alignas(64) unsigned char map[128];     // CUtensorMap over the planes (fused step)
   alignas(64) unsigned char map_pred[128];  // the same for the full prediction
-  int* exps = nullptr;                    // [0] exponent of the planes, [1] of the outputs
+  int* exps = nullptr;                    // [0] exponent of the planes, [1] of the outputs,
+                                          // [2] 1 if the digits are FP16 (else BF16)
   unsigned long long* maxbits = nullptr;  // [0] max |Q| of the current state, [1] accumulator
   int* status = nullptr;                  // shared status word
   bool valid = false;                     // planes describe the current state
@@ -74,9 +75,10 @@ struct MixedState {
 bool mixed_supported(int dim, int nb, int nout);
 // Digits of the operator rows P (nout x K): K = box.n theta_S columns, the upwind box's
 // cells x fastest.
+// Digits as BF16 bit patterns, or FP16 if f16 (exact either way).
 int mixed_build(int dim, int nb, const std::vector<double>& P, int nout, int slices,
                 const RegionBox& box, std::vector<unsigned short>& digits,
-                std::vector<double>& rscale, std::vector<float>& rowmul, MixedOp& op);
+                std::vector<double>& rscale, std::vector<float>& rowmul, MixedOp& op, bool f16);
 size_t mixed_plane_bytes(const Grid& g, int nb, int slices);
 int mixed_make_map(const Grid& g, int nb, int slices, int nout, void* planes, void* map_out);
 // Y[e * ys_e + c * ys_c] = (G X_e)[c]: FP64 (fused == false) or, for the fused step
@@ -167,7 +169,8 @@ struct NlInst {
   long long cell0;                  // first global region of the instance
   int nx, ny;
   double lam[2];                    // dt / h_d
-  int* stats;                       // [0] unconverged, [1] largest iteration count, [2] flags
+  int* stats;                       // [0] unconverged, [1] largest iteration count, [2] flags,
+                                    // [7..22] regions by iteration count (15 = 15 or more)
   unsigned long long* iters_total;  // iterations summed over the instance's regions
 };
 struct NewtonArgs {
@@ -184,7 +187,8 @@ struct NewtonArgs {
   void* scratch;     // per-CTA block storage
   size_t scratch_per_cta;
   int* counter;      // work counter (zeroed before the launch)
-  int* stats;        // [0] unconverged regions, [1] largest iteration count, [2] flags
+  int* stats;        // [0] unconverged regions, [1] largest iteration count, [2] flags,
+                     // [7..22] regions by iteration count (15 = 15 or more)
   unsigned long long* iters_total;  // Newton iterations summed over regions
   const NlInst* inst;  // batched launch: instance table (ncell = total regions), else nullptr
   int ninst;
@@ -258,11 +262,12 @@ struct ridg_handle {
   int nl_grid = 0;
   bool nl_scratch_shared = false;  // block storage owned by the batch
   int* nl_words = nullptr;  // [0] work counter, [1..3] Newton statistics, [4..5] max speed
-                            // bits, [6..7] total Newton iterations
+                            // bits, [6..7] total Newton iterations, [8..23] iteration histogram
   long long newton_iters_total = 0;
   // Newton statistics of the last prediction
   long long newton_unconverged = 0;
   int newton_iters_max = 0;
+  long long newton_hist[16] = {0};
   unsigned long long gen = 0;  // bumped whenever the operator is rebuilt
   std::string err;
   bool batch_owned = false;

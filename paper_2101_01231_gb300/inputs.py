@@ -273,6 +273,70 @@ def exact_coefficients(w: dict, t: float, nb: int | None = None) -> np.ndarray:
     raise ValueError(w["flux"])
 
 
+# --- exact error of a translated piecewise polynomial (the noisy 3D data) -------
+def shifted_polynomial_error(w: dict, Q0: np.ndarray, Q: np.ndarray, t: float) -> float:
+    """Relative L2 error ||Q_h - q(., t)|| / ||q(., t)|| of coefficients Q (cells, theta_S)
+    against the exact solution of linear advection from the piecewise polynomial Q0 (the
+    same layout): q(x, t) = q0(x - a t), periodic.  Both are polynomials on each of the 2^d
+    sub-boxes in which the shifted mesh cuts a cell, so the integral is exact with M + 2
+    Gauss points per dimension on each sub-box; the denominator is ||q0||^2 = sum |T| Q0^2
+    (orthonormal basis, translation preserves the integral)."""
+    d, nb = w["dim"], w["M"] + 1
+    n = tuple(int(v) for v in w["n"][:d])
+    h = [(w["hi"][k] - w["lo"][k]) / n[k] for k in range(d)]
+    shape = tuple(reversed(n)) + (nb,) * d          # (z, y, x, bz, by, bx)
+    A = np.asarray(Q, dtype=np.float64).reshape(shape)
+    B = np.asarray(Q0, dtype=np.float64).reshape(shape)
+    ng = nb + 1
+    xg, wg = npleg.leggauss(ng)
+    # per dimension (x first): the sub-intervals of a cell, each with its points in the cell's
+    # own coordinate, the matching points of the source cell and the source cell's offset
+    subs = []
+    for k in range(d):
+        sh = w["vel"][k] * t / h[k]                 # shift in cells
+        kk = math.floor(sh)
+        f = sh - kk
+        parts = []
+        # xi in [-1, -1 + 2f]: source cell i - kk - 1 at xi + 2 - 2f
+        # xi in [-1 + 2f, 1]: source cell i - kk at xi - 2f
+        for lo_, hi_, off, dxi in ((-1.0, -1.0 + 2 * f, kk + 1, 2.0 - 2 * f),
+                                   (-1.0 + 2 * f, 1.0, kk, -2 * f)):
+            if hi_ - lo_ <= 0.0:
+                continue
+            xi = 0.5 * (hi_ - lo_) * xg + 0.5 * (hi_ + lo_)
+            wt = 0.5 * (hi_ - lo_) * wg
+            parts.append((_legendre_orthonormal(nb, xi), _legendre_orthonormal(nb, xi + dxi),
+                          wt, off))
+        subs.append(parts)
+    axes = "zyx"[3 - d:]          # cell axes of A, slowest first
+    modes = "cba"[3 - d:]         # mode axes: bz, by, bx
+    pts = "rqp"[3 - d:]           # point axes
+    num = 0.0
+    import itertools
+    for combo in itertools.product(*[range(len(subs[k])) for k in range(d)]):
+        own, src = A, B
+        src_shift = []
+        for k in range(d):
+            Vo, Vs, wt, off = subs[k][combo[k]]
+            src_shift.append(off)
+        # source cell i - off along each dimension: roll by +off
+        src = np.roll(B, shift=[src_shift[k] for k in reversed(range(d))], axis=tuple(range(d)))
+        vo, vs = own, src
+        for k in range(d):               # contract the mode of dimension k (x = last)
+            Vo, Vs, wt, off = subs[k][combo[k]]
+            ax = d + (d - 1 - k)         # mode axis of dimension k in the current array
+            vo = np.moveaxis(np.tensordot(vo, Vo, axes=([ax], [0])), -1, ax)
+            vs = np.moveaxis(np.tensordot(vs, Vs, axes=([ax], [0])), -1, ax)
+        diff2 = (vo - vs) ** 2
+        wts = np.ones(())
+        for k in reversed(range(d)):     # weights in axis order (z, y, x)
+            wts = np.multiply.outer(wts, subs[k][combo[k]][2])
+        num += float(np.tensordot(diff2, wts, axes=(list(range(d, 2 * d)), list(range(d)))).sum())
+    vol_ref = 2.0 ** d                   # sum of the reference weights over a whole cell
+    den = float((B ** 2).sum()) * vol_ref
+    return math.sqrt(num / den)
+
+
 # --- isentropic vortex (ambient (rho,u,v,p) = (1,1,1,1), strength 5, centre (5,5)) --
 def vortex_state(x, y, t, gamma=1.4, eps=5.0, xc=5.0, yc=5.0, L=10.0):
     """Conserved variables (rho, rho u, rho v, E) of the translating isentropic vortex."""

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libridg.so")
 RIDG_OK, RIDG_EINVAL, RIDG_ENOMEM, RIDG_ECUDA, RIDG_ENONFINITE, RIDG_ENOCONV, RIDG_ETIMEOUT, \
     RIDG_ESTATE, RIDG_ETOOBIG = range(9)
 RIDG_FLUX_ADVECTION, RIDG_FLUX_BURGERS, RIDG_FLUX_EULER = range(3)
-RIDG_PREC_FP64, RIDG_PREC_MIXED_BF16, RIDG_PREC_MIXED_FP32, RIDG_PREC_MIXED_TF32 = range(4)
+RIDG_PREC_FP64, RIDG_PREC_MIXED_BF16, RIDG_PREC_MIXED_FP32, RIDG_PREC_MIXED_TF32, \
+    RIDG_PREC_MIXED_FP16 = range(5)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -43,7 +44,8 @@ class ridg_info_t(C.Structure):
                 ("theta_t", C.c_int), ("cells", C.c_longlong), ("dt", C.c_double),
                 ("t", C.c_double), ("steps", C.c_longlong), ("newton_unconverged", C.c_longlong),
                 ("newton_iters_max", C.c_int), ("precision", C.c_int), ("slices", C.c_int),
-                ("newton_iters_total", C.c_longlong)]
+                ("newton_iters_total", C.c_longlong), ("newton_hist", C.c_longlong * 16),
+                ("mass", C.c_double * 4)]
 
 
 class ridg_profile_t(C.Structure):
@@ -75,6 +77,8 @@ EXPORTS = {
                                     C.POINTER(C.c_void_p)]),
     "ridg_batch_destroy": (None, [C.c_void_p]),
     "ridg_batch_instance": (C.c_void_p, [C.c_void_p, C.c_int]),
+    "ridg_batch_set_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "ridg_batch_get_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "ridg_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
     "ridg_batch_sync": (C.c_int, [C.c_void_p]),
     "ridg_strerror": (C.c_char_p, [C.c_int]),
@@ -227,7 +231,10 @@ def ridg_sync(h):
 def ridg_info(h):
     i = ridg_info_t()
     _check(_lib.ridg_info(h, C.byref(i)), h)
-    return {k: getattr(i, k) for k, _ in ridg_info_t._fields_}
+    out = {k: getattr(i, k) for k, _ in ridg_info_t._fields_}
+    out["newton_hist"] = list(i.newton_hist)
+    out["mass"] = list(i.mass)[: i.m]
+    return out
 
 
 def ridg_profile_step(h, n=1):
@@ -301,6 +308,16 @@ def ridg_batch_destroy(b):
 
 def ridg_batch_instance(b, i):
     return C.c_void_p(_lib.ridg_batch_instance(b, int(i)))
+
+
+def ridg_batch_set_state(b, i, q):
+    p, dev = _ptr(q)
+    return _check(_lib.ridg_batch_set_state(b, int(i), p, dev))
+
+
+def ridg_batch_get_state(b, i, q):
+    p, dev = _ptr(q)
+    return _check(_lib.ridg_batch_get_state(b, int(i), p, dev))
 
 
 def ridg_batch_step(b, n=1):

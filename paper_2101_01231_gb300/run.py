@@ -18,6 +18,7 @@ from . import inputs as I
 from . import ridg as R
 
 PRECISIONS = {"fp64": R.RIDG_PREC_FP64, "mixed_bf16": R.RIDG_PREC_MIXED_BF16,
+              "mixed_fp16": R.RIDG_PREC_MIXED_FP16,
               "mixed_fp32": R.RIDG_PREC_MIXED_FP32, "mixed_tf32": R.RIDG_PREC_MIXED_TF32}
 
 

@@ -159,3 +159,25 @@ def test_mixed_equal_accuracy_on_full_workload(R):
     e = s.l2_error(I.exact_coefficients(w, 1.0))
     assert e <= 1.05 * gold["l2_error"], (e, gold["l2_error"])
     s.close()
+
+
+@pytest.mark.parametrize("dim,n,M,vel", [(2, (16, 13), 3, (1.0, 0.5)),
+                                         (3, (10, 17, 3), 2, (1.0, 0.7, 0.3))])
+def test_fp16_digits_are_bit_identical_to_bf16(R, dim, n, M, vel):
+    # the balanced base-256 digits are exact in FP16 as in BF16, and every digit product and
+    # FP32 sum is the same: the two operand types give the same bits (prediction and steps)
+    w = dict(flux="advection", dim=dim, n=n, M=M, vel=vel, lo=(0.0,) * dim, hi=(1.0,) * dim,
+             cfl=0.3, ic="sin")
+    q = np.random.default_rng(41).standard_normal((int(np.prod(n)), (M + 1) ** dim))
+    out = {}
+    for prec in (R.RIDG_PREC_MIXED_BF16, R.RIDG_PREC_MIXED_FP16):
+        s = R.Solver(dim, n, M, vel=vel, cfl=0.3, precision=prec, slices=4)
+        s.set_state(q)
+        W = s.predict()
+        s.set_state(q)
+        s.step(3)
+        s.sync()
+        out[prec] = (W, s.get_state())
+        s.close()
+    for a, b in zip(out[R.RIDG_PREC_MIXED_BF16], out[R.RIDG_PREC_MIXED_FP16]):
+        assert np.array_equal(a, b)

@@ -141,3 +141,48 @@ def test_config3_bench_slices_full_size_sampled(R):
     assert float(np.abs(q1[cells] - ref).max() / np.abs(q0).max()) < 2.0 ** -32 * 64
     s.close()
 
+
+
+def _golden(key):
+    import json
+    import os
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    g = json.load(open(os.path.join(d, "oracle_accuracy.json")))[key]
+    smp = np.load(os.path.join(d, g["cells_file"]))
+    return g, smp["cells"], smp["q"]
+
+
+def _noisy24(R, prec, slices=0):
+    g, cells, qref = _golden("adv3d_n24_q2_noise")
+    w = I.workload("adv3d_n96_q2", n=(24, 24, 24))
+    s = R.Solver(3, w["n"], w["M"], vel=w["vel"], cfl=w["cfl"], lo=w["lo"], hi=w["hi"],
+                 precision=prec, slices=slices)
+    q0 = I.initial_state(w)
+    s.set_state(q0)
+    s.set_dt(g["dt"])
+    s.step(g["steps"])
+    s.sync()
+    q = s.get_state()
+    s.close()
+    return w, q0, q, g, cells, qref
+
+
+def test_config3_noisy_data_final_time_fp64_matches_oracle(R):
+    # the stated data (sines + seeded noise) on 24^3 to t = 1: sampled cells of the FP64 path
+    # against the oracle's final state (1e-10), and the exact error (integrated on the
+    # sub-box overlaps of the carried piecewise polynomial) equal to the oracle's
+    w, q0, q, g, cells, qref = _noisy24(R, R.RIDG_PREC_FP64)
+    assert float(np.abs(q[cells] - qref).max() / np.abs(qref).max()) < 1e-10
+    e = I.shifted_polynomial_error(w, q0, q, 1.0)
+    assert abs(e - g["l2_error"]) <= 1e-8 * g["l2_error"], (e, g["l2_error"])
+
+
+@pytest.mark.parametrize("slices", [4, 6])
+def test_config3_noisy_data_mixed_within_105_of_oracle(R, slices):
+    # the accuracy gate on the stated data: L2 error vs the exact solution within 1.05x of
+    # the oracle's, and the state close to the oracle's (2^-32 scale per step at S = 4)
+    w, q0, q, g, cells, qref = _noisy24(R, R.RIDG_PREC_MIXED_BF16, slices)
+    e = I.shifted_polynomial_error(w, q0, q, 1.0)
+    assert e <= 1.05 * g["l2_error"], (e, g["l2_error"])
+    tol = 1e-10 if slices == 6 else 2.0 ** -32 * 64 * g["steps"]
+    assert float(np.abs(q[cells] - qref).max() / np.abs(qref).max()) < tol

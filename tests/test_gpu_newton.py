@@ -270,3 +270,98 @@ def test_burgers_ensemble_instance_prediction_sampled(R):
     assert conv.all()
     assert _rel(W[cells], Wo) < 1e-11
     s.close()
+
+
+def _golden(key):
+    import json
+    import os
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    g = json.load(open(os.path.join(d, "oracle_accuracy.json")))[key]
+    if "cells_file" not in g:
+        return g, None, None
+    smp = np.load(os.path.join(d, g["cells_file"]))
+    return g, smp["cells"], smp["q"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
+def test_config4_euler_vortex_final_time_against_oracle(R, prec):
+    """The Euler vortex at the config's degree (Q2) on 32^2 to t = 1 (27 steps): the L2 error
+    against the translated vortex (eq. l2relerror) within 1.05x of the oracle's, and sampled
+    cells of the final state against the oracle's (FP64: 1e-10; the FP32 / TF32 solves reach
+    the same fixed point to the Newton tolerance per step)."""
+    g, cells, qref = _golden("euler2d_n32_q2")
+    w = _euler((32, 32), 2)
+    s = _solver(R, w, precision=_prec(R, prec))
+    s.set_state(I.initial_state(w))
+    s.set_dt(g["dt"])
+    s.step(g["steps"])
+    assert s.sync() == R.RIDG_OK
+    q = s.get_state()
+    s.close()
+    e = _l2(q, I.exact_coefficients(w, 1.0), w)
+    assert e <= 1.05 * g["l2_error"], (e, g["l2_error"])
+    tol = 1e-10 if prec == "fp64" else 1e-8
+    assert float(np.abs(q[cells] - qref).max() / np.abs(qref).max()) < tol
+
+
+def _l2(q, X, w):
+    from oracle import error as OE
+    return OE.l2_relative_error(q, X, w["M"], 2, m=4 if w["flux"] == "euler" else 1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32"])
+def test_config5_ensemble_accuracy_gate(R, prec):
+    """The 64-instance Burgers ensemble capped at 16^2 cells per instance, each instance to half
+    its shock time in one batched run (a common step count, dt_i = T_i / N): every instance's
+    L2 error against the exact pre-shock solution within 1.05x of the oracle's (the oracle
+    has run the first four instances of each degree)."""
+    g, _, _ = _golden("burgers_ens16")
+    ens = [dict(w, n=(min(w["n"][0], 16), min(w["n"][1], 16))) for w in I.burgers_ensemble()]
+    opt = R.make_options(precision=_prec(R, prec))
+    b = R.ridg_batch_create([R.make_mesh(2, w["n"]) for w in ens], [w["M"] for w in ens],
+                            R.make_flux("burgers"), ens[0]["cfl"], opt)
+    N = g["steps"]
+    for i, (w, T) in enumerate(zip(ens, g["T"])):
+        h = R.ridg_batch_instance(b, i)
+        R.ridg_set_state(h, I.initial_state(w))
+        R.ridg_set_dt(h, T / N)
+    R.ridg_batch_step(b, N)
+    assert R.ridg_batch_sync(b) == R.RIDG_OK
+    worst = 0.0
+    for i, e_or in zip(g["instances"], g["l2_error"]):   # the first four of each degree
+        w, T = ens[i], g["T"][i]
+        q = np.empty((int(np.prod(w["n"])), (w["M"] + 1) ** 2))
+        R.ridg_get_state(R.ridg_batch_instance(b, i), q)
+        e = _l2(q, I.exact_coefficients(w, T), w)
+        worst = max(worst, e / e_or)
+    R.ridg_batch_destroy(b)
+    assert worst <= 1.05, worst
+
+
+def test_info_histogram_mass_and_batch_state(R):
+    # ridg_info: the Newton iteration histogram covers every region of the last prediction
+    # and sums to the iteration total; the mass equals ridg_mass
+    w = _burgers((12, 13), 2)
+    s = _solver(R, w, precision=R.RIDG_PREC_MIXED_TF32)
+    s.set_state(I.initial_state(w))
+    s.step(1)
+    s.sync()
+    info = s.info()
+    h = info["newton_hist"]
+    assert sum(h) == s.cells
+    assert sum(k * c for k, c in enumerate(h)) == info["newton_iters_total"]
+    assert info["mass"] == pytest.approx(list(s.mass()), rel=1e-15, abs=1e-300)
+    s.close()
+    # batch set / get state of an instance round-trips
+    ens = [dict(x, n=(8, 9)) for x in I.burgers_ensemble()[:3]]
+    b = R.ridg_batch_create([R.make_mesh(2, x["n"]) for x in ens], [x["M"] for x in ens],
+                            R.make_flux("burgers"), ens[0]["cfl"])
+    for i, x in enumerate(ens):
+        R.ridg_batch_set_state(b, i, I.initial_state(x))
+    for i, x in enumerate(ens):
+        q = np.empty_like(I.initial_state(x))
+        R.ridg_batch_get_state(b, i, q)
+        assert np.array_equal(q, I.initial_state(x))
+    with pytest.raises(R.RidgError):
+        R.ridg_batch_set_state(b, 3, I.initial_state(ens[0]))
+    R.ridg_batch_destroy(b)
