@@ -64,6 +64,8 @@ def _args():
                    help="whole 1D runs to T = 1 timed (0: skip the 1D section)")
     p.add_argument("--ensemble-steps", type=int, default=1,
                    help="full-size Burgers-ensemble steps timed (0: skip; ~45 s per step)")
+    p.add_argument("--autotune", type=int, default=1,
+                   help="run the library's autotuner (ridg_autotune) before timing (0: defaults)")
     p.add_argument("--adv2d-steps", type=int, default=200,
                    help="timed steps of the 2D 256^2 Q3 workload beside the headline (0: skip)")
     return p.parse_args()
@@ -269,6 +271,16 @@ def ensemble_section(R, I, steps, cpu_cells, rank=0, ws=1):
             R.ridg_set_state(R.ridg_batch_instance(b, i), I.initial_state(w))
         return b
 
+    if AUTOTUNE[0]:
+        # the Newton grid per degree, timed on a 128^2 copy of the first instance of each
+        # degree; the batch's instances read the choices at ridg_batch_create
+        for m in sorted({w["M"] for w in ens}):
+            wt = dict(next(x for x in ens if x["M"] == m), n=(128, 128))
+            st = R.Solver(2, wt["n"], m, flux="burgers", cfl=wt["cfl"],
+                          precision=R.RIDG_PREC_MIXED_TF32)
+            st.set_state(I.initial_state(wt))
+            st.autotune()
+            st.close()
     small = [dict(w, n=(min(w["n"][0], 64), min(w["n"][1], 64))) for w in ens]
     b = batch(small)
     R.ridg_batch_step(b, 1)
@@ -451,6 +463,7 @@ def paper_bump_section(R, I, dim):
 # the Newton path (nonlinear flux)
 # ---------------------------------------------------------------------------------------
 NL_WORKLOAD = "euler2d_n512_q2"
+AUTOTUNE = [1]  # set from --autotune
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA pipes x 2 flop x max SM clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # FP64 FMA: 2 per clock per SM
 
@@ -470,9 +483,12 @@ def newton_section(R, I, steps, cpu_cells):
                      gamma=w["gamma"], precision=prec)
         q = I.initial_state(w)
         s.set_state(q)
+        if AUTOTUNE[0]:
+            s.autotune()                         # the Newton grid for this precision
         s.profile_step(1)                        # warm-up
         p = s.profile_step(steps)
         info = s.info()
+        grid = s.tuning()["newton_grid"]
         s.close()
         cells = int(np.prod(w["n"]))
         bs = 4 * (w["M"] + 1) ** 3               # unknowns of one region cell (m theta_T)
@@ -485,7 +501,7 @@ def newton_section(R, I, steps, cpu_cells):
              "correct_ms": p["correct_ms"],
              "value": cells * 4 * (w["M"] + 1) ** 2 / (p["step_ms"] * 1e-3),
              "unit": "element-DOF updates/s", "newton_iters_per_cell": iters / cells,
-             "newton_iters_max": info["newton_iters_max"],
+             "newton_iters_max": info["newton_iters_max"], "newton_grid_ctas": grid,
              "roofline": {"bound": "alu", "kernel": "newton_kernel", "achieved": ach, "peak": peak,
                           "unit": "TFLOP/s", "frac": ach / peak,
                           "traffic": (_recorded_traffic("newton_" + tag[6:], info["newton_iters_total"] / steps)
@@ -776,6 +792,15 @@ def linear_arm(R, I, w, args, ws, flush, clocks=None, steps=None):
             if sweep[S] <= 1.05 * e64:
                 chosen[0] = S
                 break
+    tuning = None
+    if args.autotune and prec_name == "mixed":
+        # the autotuner times the launch choices on this workload's state; the timed
+        # handles below read its choices from the library's cache
+        st = make("mixed")
+        st.set_state(q0)
+        st.autotune()
+        tuning = st.tuning()
+        st.close()
     s, ms_step, ms_pred, ms_corr, ck = timed(prec_name, steps, args.warmup, clocks)
     slices_used = s.info()["slices"]
     ms_step = max_over_ranks(ms_step, ws, "cuda")
@@ -852,7 +877,7 @@ def linear_arm(R, I, w, args, ws, flush, clocks=None, steps=None):
         "precision": prec_name, "slices": slices_used if prec_name == "mixed" else None,
         "steps": steps, "ms_per_step": ms_step, "value": ws * dof / (ms_step * 1e-3),
         "unit": "element-DOF updates/s", "steps_to_T": nt,
-        "kernels_ms": {"predict": ms_pred, "correct": ms_corr},
+        "kernels_ms": {"predict": ms_pred, "correct": ms_corr}, "autotune": tuning,
         "fp64_path": fp64, "roofline": roof,
         "e2e": {"value": ws * dof / e2e_s, "unit": "element-DOF updates/s",
                 "h2d_bytes_per_step": int(q0.nbytes), "d2h_bytes_per_step": int(q0.nbytes)},
@@ -883,6 +908,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
+    AUTOTUNE[0] = args.autotune
     ws, rank, local = _dist()
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -919,6 +945,7 @@ def run_ours(args):
                    "slices_sweep_l2_error": acc["slices_sweep_l2_error"],
                    "error_measure": acc["measure"]},
         "kernels_ms": head["kernels_ms"],
+        "autotune": head["autotune"],
         "fp64_path": head["fp64_path"],
         "roofline": head["roofline"],
         "e2e": head["e2e"],

@@ -243,6 +243,34 @@ typedef struct {
  * kernel.  Advances the state and t like ridg_step.                                       */
 int ridg_profile_step(ridg_t* h, int n, ridg_profile_t* out);
 
+/* ----- autotuning ------------------------------------------------------------------------ */
+
+/* Time the launch choices of the handle's kernels on its own current state and keep the
+ * fastest (the benchmark spec: tile shapes and schedules per polynomial order picked by an
+ * autotuner).  Tuned now: for the 3D mixed path the depth of the GEMM's plane-operand ring
+ * (3 to 8 slots) and the correction's block size (64, 128, 256 threads); for a nonlinear
+ * flux the persistent Newton grid (1, 2, 4 or 8 CTAs per 4 SMs: fewer CTAs keep more of
+ * their block storage in L2).  Each candidate runs a few real steps (CUDA events around
+ * each launch); the state, t and the step count are restored afterwards, and captured
+ * graphs are dropped.  The choices go into the process-wide cache under keys naming the
+ * kernel family, degree, slices / conserved variables and precision, which ridg_create and
+ * ridg_batch_create read for every later handle; if cache_path is not NULL the whole cache
+ * is also written there (one "key value" line each).  The cache is first loaded from the
+ * file named by the environment variable RIDG_TUNE_CACHE when that is set.  Other
+ * configurations have nothing to tune and return RIDG_OK at once.  Synchronous.          */
+int ridg_autotune(ridg_t* h, const char* cache_path);
+
+/* The handle's current launch choices (any pointer may be NULL): 3D GEMM ring cap (0 = as
+ * many slots as fit), 3D correction block size, Newton grid in CTAs.                      */
+int ridg_get_tuning(ridg_t* h, int* gemm3_slots, int* corr3_block, int* newton_grid);
+
+/* Merge the "key value" lines of a cache file into the process-wide cache
+ * (RIDG_EINVAL if it cannot be read).                                                      */
+int ridg_tune_load(const char* cache_path);
+
+/* The cached value of `key` (RIDG_EINVAL if none is recorded).                            */
+int ridg_tune_lookup(const char* key, int* value);
+
 /* ----- batched ensemble ---------------------------------------------------------------- */
 
 typedef struct ridg_batch ridg_batch_t;

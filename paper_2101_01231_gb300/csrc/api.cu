@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "ridg_internal.h"
+#include "tune.h"
 #include "tables.h"
 
 using ridg::CorrParams;
@@ -67,6 +68,33 @@ bool is_mixed_linear(const ridg_t* h) {
 }
 
 bool digits_f16(const ridg_t* h) { return h->opt.precision == RIDG_PREC_MIXED_FP16; }
+
+// autotuner keys: the kernel family and the configuration a choice was timed on
+std::string key_gemm3(const ridg_t* h) {
+  return "gemm3.slots nb" + std::to_string(h->nb) + " S" + std::to_string(h->opt.slices) +
+         " box" + std::to_string(h->box.n);
+}
+std::string key_corr3(const ridg_t* h) {
+  return "corr3.block nb" + std::to_string(h->nb) + " S" + std::to_string(h->opt.slices);
+}
+std::string key_newton(const ridg_t* h) {
+  return "newton.grid nb" + std::to_string(h->nb) + " m" + std::to_string(h->m) + " flux" +
+         std::to_string(h->flux.kind) + " prec" + std::to_string(h->opt.precision);
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return sms;
+}
+
+// the Newton grid for a tuned value q (CTAs per 4 SMs), within the allocated block storage
+int newton_grid_of(const ridg_t* h, int q) {
+  const int g = q * sm_count() / 4;
+  return std::max(1, std::min(g, h->nl_grid_max));
+}
 
 int newton_prec(const ridg_t* h) {
   return h->opt.precision == RIDG_PREC_MIXED_TF32   ? ridg::kNewtonTF32
@@ -302,7 +330,8 @@ int enqueue_predict_mean(ridg_t* h) {
   if (!is_linear(h)) return enqueue_newton(h);
   Grid g = grid_of(h);
   if (is_mixed_linear(h) && h->dim == 3) {
-    RIDG_CUDA(h, ridg::launch_mixed3_gemm(g, h->nb, h->mixed, h->ms, h->Y, h->stream));
+    RIDG_CUDA(h, ridg::launch_mixed3_gemm(g, h->nb, h->mixed, h->ms, h->Y, h->tune_gemm3_slots,
+                                          h->stream));
   } else if (is_mixed_linear(h)) {
     RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed, h->ms, h->Y, 1, h->ncell, true,
                                          h->stream));
@@ -319,7 +348,8 @@ int enqueue_correct_after_mean(ridg_t* h) {
   if (is_mixed_linear(h) && h->dim == 3) {
     // double-float correction from the time means, with the new state's digit planes
     RIDG_CUDA(h, ridg::launch_mixed3_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
-                                             h->mixed.gmax, cp, h->ms, h->stream));
+                                             h->mixed.gmax, cp, h->ms, h->tune_corr3_block,
+                                             h->stream));
   } else if (is_mixed_linear(h)) {
     RIDG_CUDA(h, ridg::launch_mixed_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
                                             h->mixed.gmax, cp, sign_of(h->flux.vel[0]),
@@ -470,6 +500,10 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
     delete h;
     return RIDG_EINVAL;
   }
+  if (is_mixed_linear(h) && h->dim == 3) {
+    h->tune_gemm3_slots = ridg::tune_get(key_gemm3(h), 0);
+    h->tune_corr3_block = ridg::tune_get(key_corr3(h), 128);
+  }
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     delete h;
     return RIDG_ECUDA;
@@ -510,10 +544,13 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
     ridg::nl_tables_upload(h->nb, h->nl, nullptr, &tb_bytes, h->stream);
     void* tb_mem = dev_alloc(h, tb_bytes);
     h->plan = ridg::build_elim_plan();
-    h->nl_grid = ridg::newton_grid(h->nb, h->m, h->flux.kind, newton_prec(h));
+    h->nl_grid_max = ridg::newton_grid(h->nb, h->m, h->flux.kind, newton_prec(h));
+    h->nl_grid = h->nl_grid_max;
+    const int q = ridg::tune_get(key_newton(h), 0);
+    if (q > 0 && h->nl_grid_max > 0) h->nl_grid = newton_grid_of(h, q);
     h->nl_scratch_cta = ridg::newton_scratch_per_cta(h->nb, h->m, newton_prec(h), h->plan);
-    const size_t scratch = h->nl_scratch_cta * (size_t)h->nl_grid;
-    h->nl_scratch = h->nl_grid > 0 ? dev_alloc(h, scratch) : nullptr;
+    const size_t scratch = h->nl_scratch_cta * (size_t)h->nl_grid_max;
+    h->nl_scratch = h->nl_grid_max > 0 ? dev_alloc(h, scratch) : nullptr;
     h->nl_words = (int*)dev_alloc(h, 24 * sizeof(int));
     if (!tb_mem || !h->nl_scratch || !h->nl_words) {
       dev_free(h, tb_mem);
@@ -801,6 +838,131 @@ int ridg_profile_step(ridg_t* h, int n, ridg_profile_t* out) {
   return RIDG_OK;
 }
 
+int ridg_autotune(ridg_t* h, const char* cache_path) {
+  if (check_handle(h)) return RIDG_EINVAL;
+  if (!(h->dt > 0)) return set_err(h, RIDG_ESTATE, "no dt yet: call ridg_set_state first");
+  const bool mixed3 = is_linear(h) && is_mixed_linear(h) && h->dim == 3;
+  const bool newton = !is_linear(h) && h->nl_grid_max > 0;
+  if (mixed3 || newton) {
+    // the candidates run real steps from the current state, which is put back afterwards
+    const size_t nQ = (size_t)h->ncell * h->m * h->thS;
+    double* save = (double*)dev_alloc(h, nQ * sizeof(double));
+    if (!save) return set_err(h, RIDG_ENOMEM, "autotune state copy");
+    const double t0 = h->t;
+    const long long s0 = h->steps;
+    int rc = RIDG_OK;
+    auto restore = [&]() -> int {
+      RIDG_CUDA(h, cudaMemcpyAsync(h->Q, save, nQ * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   h->stream));
+      RIDG_CUDA(h, cudaStreamSynchronize(h->stream));
+      h->t = t0;
+      h->steps = s0;
+      h->ms.valid = false;
+      h->have_pred = false;
+      return RIDG_OK;
+    };
+    // average prediction / correction device time of n steps (after one untimed step)
+    auto measure = [&](int n, double* tp, double* tc) -> int {
+      int r = restore();
+      if (r) return r;
+      ridg_profile_t p;
+      r = ridg_profile_step(h, 1, &p);
+      if (r && r != RIDG_ENOCONV) return r;
+      r = ridg_profile_step(h, n, &p);
+      if (r && r != RIDG_ENOCONV) return r;
+      *tp = p.predict_ms;
+      *tc = p.correct_ms;
+      return RIDG_OK;
+    };
+    if (cudaMemcpyAsync(save, h->Q, nQ * sizeof(double), cudaMemcpyDeviceToDevice, h->stream) !=
+        cudaSuccess)
+      rc = set_err(h, RIDG_ECUDA, "autotune state copy");
+    if (!rc && mixed3) {
+      // the GEMM's plane-operand ring depth, then the correction's block size; candidates
+      // are interleaved over two rounds of 8 steps and each keeps its better round
+      std::vector<int> caps;
+      int last_na = -1;
+      for (int cap : {3, 4, 5, 6, 8}) {
+        const int na = ridg::mixed3_gemm_slots(h->nb, h->opt.slices, h->box, cap);
+        if (na < 2 || na == last_na) continue;
+        last_na = na;
+        caps.push_back(cap);
+      }
+      std::vector<double> tg(caps.size(), 1e300);
+      for (int round = 0; round < 2 && !rc; ++round)
+        for (size_t i = 0; i < caps.size() && !rc; ++i) {
+          h->tune_gemm3_slots = caps[i];
+          double tp = 0, tc = 0;
+          if (!(rc = measure(8, &tp, &tc))) tg[i] = std::min(tg[i], tp);
+        }
+      if (!caps.empty())
+        h->tune_gemm3_slots = caps[std::min_element(tg.begin(), tg.end()) - tg.begin()];
+      const int blocks[3] = {64, 128, 256};
+      double tb[3] = {1e300, 1e300, 1e300};
+      for (int round = 0; round < 2 && !rc; ++round)
+        for (int i = 0; i < 3 && !rc; ++i) {
+          h->tune_corr3_block = blocks[i];
+          double tp = 0, tc = 0;
+          if (!(rc = measure(8, &tp, &tc))) tb[i] = std::min(tb[i], tc);
+        }
+      h->tune_corr3_block = blocks[std::min_element(tb, tb + 3) - tb];
+      if (!rc) {
+        ridg::tune_put(key_gemm3(h), h->tune_gemm3_slots);
+        ridg::tune_put(key_corr3(h), h->tune_corr3_block);
+      }
+    }
+    if (!rc && newton) {
+      // the persistent Newton grid in CTAs per 4 SMs: fewer CTAs keep more of their block
+      // storage in L2, more hide the latency of the pivot chains
+      const int per4 = std::max(1, h->nl_grid_max * 4 / std::max(1, sm_count()));
+      int best_q = per4;
+      double best = 1e300;
+      for (int q : {1, 2, 4, 8}) {
+        if (q > per4) break;
+        h->nl_grid = newton_grid_of(h, q);
+        double tp = 0, tc = 0;
+        if ((rc = measure(1, &tp, &tc))) break;
+        if (tp < best) {
+          best = tp;
+          best_q = q;
+        }
+      }
+      h->nl_grid = newton_grid_of(h, best_q);
+      if (!rc) ridg::tune_put(key_newton(h), best_q);
+    }
+    const int rr = restore();
+    dev_free(h, save);
+    drop_graphs(h);
+    if (rc) return rc;
+    if (rr) return rr;
+  }
+  if (cache_path && !ridg::tune_save(cache_path))
+    return set_err(h, RIDG_EINVAL, std::string("cannot write the tuning cache ") + cache_path);
+  return RIDG_OK;
+}
+
+int ridg_get_tuning(ridg_t* h, int* gemm3_slots, int* corr3_block, int* newton_grid) {
+  if (check_handle(h)) return RIDG_EINVAL;
+  if (gemm3_slots) *gemm3_slots = h->tune_gemm3_slots;
+  if (corr3_block) *corr3_block = h->tune_corr3_block;
+  if (newton_grid) *newton_grid = h->nl_grid;
+  return RIDG_OK;
+}
+
+int ridg_tune_load(const char* cache_path) {
+  if (!cache_path) return RIDG_EINVAL;
+  return ridg::tune_load(cache_path) ? RIDG_OK : RIDG_EINVAL;
+}
+
+int ridg_tune_lookup(const char* key, int* value) {
+  if (!key || !value) return RIDG_EINVAL;
+  const int missing = -2147483647;
+  const int v = ridg::tune_get(key, missing);
+  if (v == missing) return RIDG_EINVAL;
+  *value = v;
+  return RIDG_OK;
+}
+
 int ridg_info(ridg_t* h, ridg_info_t* info) {
   if (check_handle(h) || !info) return RIDG_EINVAL;
   info->dim = h->dim;
@@ -994,7 +1156,7 @@ int ridg_batch_create(int count, const ridg_mesh* meshes, const int* orders, con
   // storage, as large as the largest instance needs, serves them all
   if (flux->kind != RIDG_FLUX_ADVECTION) {
     size_t need = 0;
-    for (ridg_t* h : b->inst) need = std::max(need, h->nl_scratch_cta * (size_t)h->nl_grid);
+    for (ridg_t* h : b->inst) need = std::max(need, h->nl_scratch_cta * (size_t)h->nl_grid_max);
     b->nl_scratch = dev_alloc(b->inst[0], need);
     if (!b->nl_scratch) {
       ridg_batch_destroy(b);

@@ -46,7 +46,8 @@ struct Gemm3Layout {
 
 // ncx, ncy, ncz = offsets of the upwind box per dimension (x-shifted copies per A slot,
 // operator blocks per B stage, B stages = ncy ncz); the A ring takes the room that is left
-__host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int ncx, int ncy, int ncz) {
+__host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int ncx, int ncy, int ncz,
+                                                   int na_cap = kNAmax) {
   Gemm3Layout l;
   l.P = ((thS + 15) / 16) * 2;
   l.brows = S * kNOUTP;
@@ -57,7 +58,8 @@ __host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int ncx, int
   const uint32_t btot = (uint32_t)l.nst * l.b_bytes;
   const uint32_t room = kSmemLimit - 1024u - btot;  // barriers and alignment slack
   int na = (int)(room / l.a_bytes);
-  l.na = na > kNAmax ? kNAmax : na;
+  const int cap = na_cap > 0 && na_cap < kNAmax ? na_cap : kNAmax;
+  l.na = na > cap ? cap : na;
   l.b_off = (uint32_t)l.na * l.a_bytes;
   l.bar_off = (l.b_off + btot + 63u) & ~63u;
   l.bytes = l.bar_off + 256;
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
     const __grid_constant__ CUtensorMap dmap, const unsigned char* __restrict__ Bg,
     const float* __restrict__ rowmul, int S, int nout, float2* __restrict__ Y, int* __restrict__ exps,
     unsigned long long* __restrict__ maxbits, int nx, int ny, int nz, RegionBox box,
-    int* status) {
+    int na_cap, int* status) {
   constexpr int THS = NB * NB * NB;
   constexpr int P = ((THS + 15) / 16) * 2;
   constexpr int KSTEPS = P / 2;
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
   // the upwind box: offsets lo + 0 .. cnt - 1 per dimension (cnt 1 or 2, at most 3 B stages)
   const int ox0 = box.lo[0], oy0 = box.lo[1], oz0 = box.lo[2];
   const int ncx = NCXC ? NCXC : box.cnt[0], ncy = box.cnt[1], ncz = box.cnt[2];
-  const Gemm3Layout L = gemm3_layout(S, THS, ncx, ncy, ncz);
+  const Gemm3Layout L = gemm3_layout(S, THS, ncx, ncy, ncz, na_cap);
   const int NA = L.na;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
@@ -341,19 +343,20 @@ __device__ __forceinline__ void dfu_acc(DFU& a, DFU x) {
 // F(i - 1/2) - F(i + 1/2))], s_a = (-1)^a = phi_a(-1) / phi_a(+1), in double-float; then
 // Q += dQ in FP64, the new state's digit rows (and ghost copies) and the running maximum.
 // Degrees up to 2: a mode has at most one volume-term source per direction.
-template <int NB, int S>
-__global__ void __launch_bounds__(128) mixed3_correct_kernel(
+template <int NB, int S, int BT>
+__global__ void __launch_bounds__(BT) mixed3_correct_kernel(
     double* __restrict__ Q, const float2* __restrict__ Y, int nx, int ny, int nz, CorrParams cp,
     int gmax, int* __restrict__ exps, unsigned long long* __restrict__ maxbits,
     uint4* __restrict__ planes, int* status) {
   static_assert(NB <= 3, "one volume-term source per mode and direction");
   constexpr int THS = NB * NB * NB, NT = NB * NB;
   constexpr int P = ((THS + 15) / 16) * 2;
-  __shared__ unsigned long long shmax[4];
+  __shared__ unsigned long long shmax[8];
   // per-thread dQ accumulators (double-float), indexed by mode: in shared memory so that the
-  // loops over lines stay rolled (a fully unrolled body stalls on instruction fetch)
-  __shared__ float2 acc_sh[THS * 128];
-  float2* acc = acc_sh + threadIdx.x;  // mode s at acc[s * 128]
+  // loops over lines stay rolled (a fully unrolled body stalls on instruction fetch); the
+  // block size (64, 128 or 256 threads) is the autotuner's choice
+  extern __shared__ float2 acc_sh[];
+  float2* acc = acc_sh + threadIdx.x;  // mode s at acc[s * BT]
   const long long ncell = (long long)nx * ny * nz;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int ys = exps[1];
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(128) mixed3_correct_kernel(
   if (e < ncell) {
     const unsigned ue = (unsigned)e, ur = ue / (unsigned)nx;
     const int ix = (int)(ue - ur * (unsigned)nx), iy = (int)(ur % (unsigned)ny), iz = (int)(ur / (unsigned)ny);
-    for (int j = 0; j < THS; ++j) acc[j * 128] = make_float2(0.f, 0.f);
+    for (int j = 0; j < THS; ++j) acc[j * BT] = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int dd = 0; dd < 3; ++dd) {
       const double nu = cp.nu[dd];
@@ -432,13 +435,13 @@ __global__ void __launch_bounds__(128) mixed3_correct_kernel(
         dfu_acc(dneg, DFU{-fp.s, -fp.e});
 #pragma unroll
         for (int a = 0; a < NB; ++a) {
-          const float2 c = acc[(base + a * st) * 128];
+          const float2 c = acc[(base + a * st) * BT];
           DFU v{c.x, c.y};
           if (a >= 1) dfu_acc(v, dfu_prod(cp.vdh[dd][a], cp.vdl[dd][a], co[a - 1].x, co[a - 1].y));
           const DFU df = (a & 1) ? dneg : dpos;
           // phi_0(+1) = 1 exactly
           dfu_acc(v, a == 0 ? df : dfu_prod(cp.eph[a], cp.epl[a], df.s, df.e));
-          acc[(base + a * st) * 128] = make_float2(v.s, v.e);
+          acc[(base + a * st) * BT] = make_float2(v.s, v.e);
         }
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(128) mixed3_correct_kernel(
       for (int j = 0; j < 8; ++j) {
         const int sm = pg * 8 + j;
         if (sm < THS) {
-          const float2 d = acc[sm * 128];
+          const float2 d = acc[sm * BT];
           double v = q[sm];
           v = v + f2d_scale(d.x, kfin);
           v = v + f2d_scale(d.y, kfin);
@@ -603,9 +606,9 @@ int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_o
 
 template <int NB>
 static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& ms, void* Y,
-                                  cudaStream_t s) {
+                                  int slots, cudaStream_t s) {
   const Gemm3Layout L = gemm3_layout(op.slices, NB * NB * NB, g.box.cnt[0], g.box.cnt[1],
-                                     g.box.cnt[2]);
+                                     g.box.cnt[2], slots);
   if (L.na < 2 || L.bytes > kSmemLimit) return cudaErrorInvalidValue;
   // one CTA per SM: each allocates all 512 TMEM columns, so a second CTA on the SM would
   // only wait for them -- ask for more than half the shared memory
@@ -621,40 +624,54 @@ static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& 
   kern<<<grid, kGemmThreads, smem, s>>>(*(const CUtensorMap*)ms.map,
                                         (const unsigned char*)op.b_slices, op.row_mul, op.slices,
                                         op.nout, (float2*)Y, ms.exps, ms.maxbits, g.n[0], g.n[1],
-                                        g.n[2], g.box, ms.status);
+                                        g.n[2], g.box, slots, ms.status);
   return cudaGetLastError();
 }
 
+int mixed3_gemm_slots(int nb, int slices, const RegionBox& box, int cap) {
+  const Gemm3Layout L = gemm3_layout(slices, nb * nb * nb, box.cnt[0], box.cnt[1], box.cnt[2], cap);
+  return L.na;
+}
+
 cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
-                               cudaStream_t s) {
+                               int slots, cudaStream_t s) {
   if (g.dim != 3 || g.box.n < 1 || g.box.n > 8 || op.K != g.box.n * nb * nb * nb)
     return cudaErrorInvalidValue;
   switch (nb) {
-    case 2: return launch_gemm3_t<2>(g, op, ms, Y, s);
-    case 3: return launch_gemm3_t<3>(g, op, ms, Y, s);
+    case 2: return launch_gemm3_t<2>(g, op, ms, Y, slots, s);
+    case 3: return launch_gemm3_t<3>(g, op, ms, Y, slots, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <int NB, int S>
 static cudaError_t launch_correct3_t(const Grid& g, double* Q, const void* Y, int gmax,
-                                     const CorrParams& cp, MixedState& ms, cudaStream_t s) {
+                                     const CorrParams& cp, MixedState& ms, int block,
+                                     cudaStream_t s) {
   // the kernel indexes the time means with 32-bit offsets (mode x cells)
   if ((long long)g.ncell * NB * NB * NB >= (1LL << 32)) return cudaErrorInvalidValue;
-  const unsigned blocks = (unsigned)((g.ncell + 127) / 128);
-  mixed3_correct_kernel<NB, S><<<blocks, 128, 0, s>>>(Q, (const float2*)Y, g.n[0], g.n[1],
-                                                      g.n[2], cp, gmax, ms.exps, ms.maxbits,
-                                                      (uint4*)ms.planes, ms.status);
+  if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)((g.ncell + block - 1) / block);
+  const size_t smem = (size_t)NB * NB * NB * block * sizeof(float2);
+  auto kern = block == 64    ? mixed3_correct_kernel<NB, S, 64>
+              : block == 128 ? mixed3_correct_kernel<NB, S, 128>
+                             : mixed3_correct_kernel<NB, S, 256>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<blocks, block, smem, s>>>(Q, (const float2*)Y, g.n[0], g.n[1], g.n[2], cp, gmax,
+                                   ms.exps, ms.maxbits, (uint4*)ms.planes, ms.status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mixed3_correct(const Grid& g, int nb, int slices, double* Q, const void* Y,
-                                  int gmax, const CorrParams& cp, MixedState& ms,
+                                  int gmax, const CorrParams& cp, MixedState& ms, int block,
                                   cudaStream_t s) {
   if (g.dim != 3) return cudaErrorInvalidValue;
   switch (nb * 16 + slices) {
 #define RIDG_C3(NBV, SV) \
-  case NBV * 16 + SV: return launch_correct3_t<NBV, SV>(g, Q, Y, gmax, cp, ms, s);
+  case NBV * 16 + SV: return launch_correct3_t<NBV, SV>(g, Q, Y, gmax, cp, ms, block, s);
     RIDG_C3(2, 2) RIDG_C3(2, 3) RIDG_C3(2, 4) RIDG_C3(2, 5) RIDG_C3(2, 6)
     RIDG_C3(3, 2) RIDG_C3(3, 3) RIDG_C3(3, 4) RIDG_C3(3, 5) RIDG_C3(3, 6)
 #undef RIDG_C3

@@ -99,12 +99,16 @@ size_t mixed3_plane_bytes(const Grid& g, int nb, int slices);
 int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_out);
 // Y[c * cells + e] = (P-bar X_e)[c] as double-float pairs from the digit planes in ms (value
 // (hi + lo) 2^(exps[1] + gmax - 16))
+// (slots: depth of the plane-operand ring, 0 = as many as fit; the autotuner's choice)
 cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
-                               cudaStream_t s);
+                               int slots, cudaStream_t s);
+// the ring depth a slot cap gives for this configuration (0: it does not fit)
+int mixed3_gemm_slots(int nb, int slices, const RegionBox& box, int cap);
 // the correction from those outputs (face values from each cell's own and upstream
 // neighbours' time means), plus the new state's digit planes and maximum
+// (block: 64, 128 or 256 threads, the autotuner's choice)
 cudaError_t launch_mixed3_correct(const Grid& g, int nb, int slices, double* Q, const void* Y,
-                                  int gmax, const CorrParams& cp, MixedState& ms,
+                                  int gmax, const CorrParams& cp, MixedState& ms, int block,
                                   cudaStream_t s);
 // max |Q| and the 3D digit planes of Q
 cudaError_t launch_mixed3_refresh(const Grid& g, int nb, int slices, const double* Q,
@@ -259,7 +263,10 @@ struct ridg_handle {
   ridg::NlPlan plan{};
   void* nl_scratch = nullptr;
   size_t nl_scratch_cta = 0;
-  int nl_grid = 0;
+  int nl_grid = 0;        // CTAs of the persistent Newton launch (autotuned)
+  int nl_grid_max = 0;    // CTAs the block storage is allocated for
+  int tune_gemm3_slots = 0;   // 3D GEMM plane-operand ring depth (0: as many as fit)
+  int tune_corr3_block = 128; // 3D correction block size
   bool nl_scratch_shared = false;  // block storage owned by the batch
   int* nl_words = nullptr;  // [0] work counter, [1..3] Newton statistics, [4..5] max speed
                             // bits, [6..7] total Newton iterations, [8..23] iteration histogram

@@ -81,6 +81,11 @@ EXPORTS = {
     "ridg_batch_get_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "ridg_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
     "ridg_batch_sync": (C.c_int, [C.c_void_p]),
+    "ridg_autotune": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "ridg_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int)]),
+    "ridg_tune_load": (C.c_int, [C.c_char_p]),
+    "ridg_tune_lookup": (C.c_int, [C.c_char_p, C.POINTER(C.c_int)]),
     "ridg_strerror": (C.c_char_p, [C.c_int]),
     "ridg_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -292,6 +297,26 @@ def ridg_l2_error_noalloc(q, x, cells, m, dim, order, stream=None):
     return e.value
 
 
+def ridg_autotune(h, cache_path=None):
+    return _check(_lib.ridg_autotune(h, cache_path.encode() if cache_path else None), h)
+
+
+def ridg_get_tuning(h):
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(_lib.ridg_get_tuning(h, C.byref(a), C.byref(b), C.byref(c)), h)
+    return {"gemm3_slots": a.value, "corr3_block": b.value, "newton_grid": c.value}
+
+
+def ridg_tune_load(path):
+    return _check(_lib.ridg_tune_load(path.encode()))
+
+
+def ridg_tune_lookup(key):
+    """The cached value of key, or None."""
+    v = C.c_int()
+    return v.value if _lib.ridg_tune_lookup(key.encode(), C.byref(v)) == RIDG_OK else None
+
+
 def ridg_batch_create(meshes, orders, flux, cfl, opt=None):
     n = len(meshes)
     ms = (ridg_mesh * n)(*meshes)
@@ -393,6 +418,12 @@ class Solver:
 
     def set_dt(self, dt):
         return ridg_set_dt(self.h, dt)
+
+    def autotune(self, cache_path=None):
+        return ridg_autotune(self.h, cache_path)
+
+    def tuning(self):
+        return ridg_get_tuning(self.h)
 
     def set_final_time(self, T):
         return ridg_set_final_time(self.h, T)
