@@ -290,6 +290,37 @@ int ridg_batch_get_state(ridg_batch_t* b, int i, double* q, int on_device);
 int ridg_batch_step(ridg_batch_t* b, int n);
 int ridg_batch_sync(ridg_batch_t* b);
 
+/* ----- a mesh sharded into slabs (domain decomposition, Sec. 5) ------------------------- */
+
+typedef struct ridg_shard ridg_shard_t;
+
+/* Partition a linear-advection mesh into `count` slabs along its slowest axis (x in 1D, y in
+ * 2D, z in 3D), slab i an ordinary handle on device devices[i] (NULL: every slab on the
+ * current device), with its own stream (opt->stream must be NULL).  Each slab's local mesh
+ * is its layers plus, when the velocity along the axis is nonzero, the two layers upstream
+ * of it (the halo: its first layer's correction reads the time mean of the layer below it,
+ * whose prediction reads one more layer), periodic locally; the local wrap only reaches
+ * halo cells, whose results are discarded, so every owned cell is computed exactly as in
+ * the unsharded step.  Every slab needs at least 2 layers.  The paper's decomposition uses
+ * two exchanges per step (the state, then the boundary predictions); with upwind face
+ * values one exchange of a two-layer state halo from the upstream slab suffices.          */
+int ridg_shard_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double cfl,
+                      const ridg_options* opt, int count, const int* devices,
+                      ridg_shard_t** out);
+void ridg_shard_destroy(ridg_shard_t* s);
+/* Slab i as an ordinary handle (owned by the shard): its info, mass, profile.             */
+ridg_t* ridg_shard_slab(ridg_shard_t* s, int i);
+/* The whole problem's state in the canonical layout (host memory, or device memory of the
+ * current device if on_device), scattered to / gathered from the slabs.  Synchronous.      */
+int ridg_shard_set_state(ridg_shard_t* s, const double* q, int on_device);
+int ridg_shard_get_state(ridg_shard_t* s, double* q, int on_device);
+/* n steps: per step every slab's halo is copied from its upstream neighbour (one contiguous
+ * copy, peer-to-peer between devices), ordered by events after that neighbour's previous
+ * step, then every slab runs its step graph once the copy that reads its own state is done.
+ * Returns after enqueueing; ridg_shard_sync waits (and reports a device-side status).     */
+int ridg_shard_step(ridg_shard_t* s, int n);
+int ridg_shard_sync(ridg_shard_t* s);
+
 /* ----- errors ------------------------------------------------------------------------- */
 const char* ridg_strerror(int status);
 const char* ridg_last_error(const ridg_t* h);

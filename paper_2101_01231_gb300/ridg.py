@@ -86,6 +86,15 @@ EXPORTS = {
                                   C.POINTER(C.c_int)]),
     "ridg_tune_load": (C.c_int, [C.c_char_p]),
     "ridg_tune_lookup": (C.c_int, [C.c_char_p, C.POINTER(C.c_int)]),
+    "ridg_shard_create": (C.c_int, [C.POINTER(ridg_mesh), C.c_int, C.POINTER(ridg_flux), C.c_double,
+                                    C.POINTER(ridg_options), C.c_int, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_void_p)]),
+    "ridg_shard_destroy": (None, [C.c_void_p]),
+    "ridg_shard_slab": (C.c_void_p, [C.c_void_p, C.c_int]),
+    "ridg_shard_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "ridg_shard_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "ridg_shard_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "ridg_shard_sync": (C.c_int, [C.c_void_p]),
     "ridg_strerror": (C.c_char_p, [C.c_int]),
     "ridg_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -315,6 +324,44 @@ def ridg_tune_lookup(key):
     """The cached value of key, or None."""
     v = C.c_int()
     return v.value if _lib.ridg_tune_lookup(key.encode(), C.byref(v)) == RIDG_OK else None
+
+
+class Shard:
+    """A linear-advection mesh sharded into slabs along its slowest axis (ridg_shard_*)."""
+
+    def __init__(self, dim, n, order, vel, cfl, count, lo=None, hi=None, precision=RIDG_PREC_FP64,
+                 slices=0, devices=None):
+        mesh = make_mesh(dim, n, lo, hi)
+        flux = make_flux("advection", vel)
+        opt = make_options(precision=precision, slices=slices)
+        devs = (C.c_int * count)(*devices) if devices else None
+        s = C.c_void_p()
+        _check(_lib.ridg_shard_create(C.byref(mesh), int(order), C.byref(flux), float(cfl),
+                                      C.byref(opt), int(count), devs, C.byref(s)))
+        self.s = s
+        self.count = count
+
+    def slab(self, i):
+        return C.c_void_p(_lib.ridg_shard_slab(self.s, int(i)))
+
+    def set_state(self, q):
+        p, dev = _ptr(q)
+        return _check(_lib.ridg_shard_set_state(self.s, p, dev))
+
+    def get_state(self, q):
+        p, dev = _ptr(q)
+        return _check(_lib.ridg_shard_get_state(self.s, p, dev))
+
+    def step(self, n=1):
+        return _check(_lib.ridg_shard_step(self.s, int(n)))
+
+    def sync(self):
+        return _check(_lib.ridg_shard_sync(self.s))
+
+    def close(self):
+        if self.s:
+            _lib.ridg_shard_destroy(self.s)
+            self.s = None
 
 
 def ridg_batch_create(meshes, orders, flux, cfl, opt=None):
