@@ -801,6 +801,7 @@ def linear_arm(R, I, w, args, ws, flush, clocks=None, steps=None):
         st.autotune()
         tuning = st.tuning()
         st.close()
+    hbm, bf16, src = _peaks()
     s, ms_step, ms_pred, ms_corr, ck = timed(prec_name, steps, args.warmup, clocks)
     slices_used = s.info()["slices"]
     ms_step = max_over_ranks(ms_step, ws, "cuda")
@@ -821,6 +822,9 @@ def linear_arm(R, I, w, args, ws, flush, clocks=None, steps=None):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / n_e2e, ws, "cuda")
     s.close()
 
+    predict_full = None
+    if prec_name == "mixed" and w["dim"] == 3:
+        predict_full = time_predict(R, I, w, make, q0, slices_used, hbm, bf16)
     fp64 = None
     if prec_name != "fp64":
         s2, ms64, mp64, mc64, _ = timed("fp64", max(10, steps // 5), args.warmup)
@@ -829,7 +833,6 @@ def linear_arm(R, I, w, args, ws, flush, clocks=None, steps=None):
                 "correct_ms": mc64}
     err = accuracy(prec_name)[0] if prec_name != "fp64" else e64
 
-    hbm, bf16, src = _peaks()
     # Algorithmic work per launch.  Prediction (time mean): 2 theta_S K flop per cell (K =
     # theta_S x the upwind region cells; the other region cells' operator columns are exactly
     # zero) and its bytes: read Q, write W-bar (2 x 8 theta_S B per cell).  Correction: read
@@ -878,7 +881,7 @@ def linear_arm(R, I, w, args, ws, flush, clocks=None, steps=None):
         "steps": steps, "ms_per_step": ms_step, "value": ws * dof / (ms_step * 1e-3),
         "unit": "element-DOF updates/s", "steps_to_T": nt,
         "kernels_ms": {"predict": ms_pred, "correct": ms_corr}, "autotune": tuning,
-        "fp64_path": fp64, "roofline": roof,
+        "fp64_path": fp64, "roofline": roof, "predict_full": predict_full,
         "e2e": {"value": ws * dof / e2e_s, "unit": "element-DOF updates/s",
                 "h2d_bytes_per_step": int(q0.nbytes), "d2h_bytes_per_step": int(q0.nbytes)},
         "accuracy": {"T": T_FINAL,
@@ -902,6 +905,41 @@ def linear_arm(R, I, w, args, ws, flush, clocks=None, steps=None):
         # it by the GPU tests; at full size the FP64 GPU path (per-step parity 1e-12) stands in
         out["accuracy"]["l2_error_oracle_24cubed"] = gold["adv3d_n24_q2_noise"]["l2_error"]
     return out
+
+
+def time_predict(R, I, w, make, q0, slices, hbm, bf16, reps=10):
+    """ridg_predict of every cell's full space-time prediction (all theta_T rows of the
+    operator, SURVEY's config-3 contraction) through the C ABI into a device buffer, timed
+    with CUDA events on the handle's stream: its executed tensor rate (digit-pair products,
+    outputs and K padded) against the BF16 peak, its algorithmic rate (2 theta_T K flop per
+    cell) and the bytes it must move (Q in, W out in FP64)."""
+    import torch
+    s = make("mixed", slices)
+    s.set_state(q0)
+    cells = int(np.prod(w["n"]))
+    thS = (w["M"] + 1) ** w["dim"]
+    thT = thS * (w["M"] + 1)
+    K = upwind_cells(w) * thS
+    Wd = torch.empty(cells, thT, dtype=torch.float64, device="cuda")
+    s.predict(Wd)                                 # warm-up (digit planes, attributes)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s.stream)
+    for _ in range(reps):
+        s.predict(Wd)
+    b.record(s.stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    s.close()
+    # executed: per time mode (M + 1 launches) S (S + 1) / 2 digit pairs x 32 padded outputs x
+    # the upwind cells' 32 padded modes each, per cell
+    executed = 2.0 * (w["M"] + 1) * (slices * (slices + 1) // 2) * 32 * upwind_cells(w) * 32 * cells
+    return {"kernel": "mixed3_gemm x (M + 1) + conversion to FP64 (ridg_predict)", "ms": ms,
+            "tensor_executed_tflops": executed / (ms * 1e-3) / 1e12, "tensor_peak_tflops": bf16,
+            "tensor_frac": executed / (ms * 1e-3) / 1e12 / bf16,
+            "algorithmic_tflops": 2.0 * thT * K * cells / (ms * 1e-3) / 1e12,
+            "hbm_gbs": 8.0 * (thS + thT) * cells / (ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm}
 
 
 def run_ours(args):
@@ -946,6 +984,7 @@ def run_ours(args):
                    "error_measure": acc["measure"]},
         "kernels_ms": head["kernels_ms"],
         "autotune": head["autotune"],
+        "predict_full": head["predict_full"],
         "fp64_path": head["fp64_path"],
         "roofline": head["roofline"],
         "e2e": head["e2e"],

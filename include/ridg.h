@@ -168,9 +168,9 @@ int ridg_set_final_time(ridg_t* h, double T, long long* nsteps);
 /* ----- the step ---------------------------------------------------------------------- */
 
 /* Prediction (Sec. 2.2): every cell's centre space-time coefficients W_i from the
- * current state.  With a mixed linear precision it runs the split-digit tensor-core
- * contraction of all theta_T rows in 1D / 2D; in 3D ridg_predict computes the full
- * prediction in FP64 (the mixed 3D path contracts only the time-mean rows the step needs).
+ * current state.  With a mixed linear precision (2D, 3D) it runs the split-digit
+ * tensor-core contraction of all theta_T rows (in 3D one launch per time mode's theta_S
+ * rows, each converted from double-float into its columns of W).
  * If w_out is not NULL it receives cells * m * theta_T doubles (prediction layout; device
  * pointer if on_device).  The prediction is also kept for a
  * following ridg_correct.  Returns RIDG_ENOCONV (after completing) if Newton hit its cap

@@ -161,30 +161,35 @@ int rebuild_linear(ridg_t* h) {
   RIDG_CUDA(h, cudaMemcpyAsync(h->P, h->P_host.data(), sizeof(double) * h->P_host.size(),
                                cudaMemcpyHostToDevice, h->stream));
   if (is_mixed_linear(h) && h->dim == 3) {
-    // 3D: the time-mean rows P-bar (first theta_S rows of P) on the tensor cores; the
-    // correction stays the FP64 kernel
-    std::vector<double> Pbar(h->P_host.begin(), h->P_host.begin() + (size_t)h->thS * h->K);
-    std::vector<unsigned short> digits;
-    std::vector<double> rscale;
-    std::vector<float> rowmul;
-    int rc = ridg::mixed_build(3, h->nb, Pbar, h->thS, h->opt.slices, h->box, digits, rscale,
-                               rowmul, h->mixed, digits_f16(h));
-    if (rc != RIDG_OK) return set_err(h, rc, "3D mixed operator build failed");
-    if (!h->mixed.b_slices) {
-      h->mixed.b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
-      h->mixed.row_scale = (double*)dev_alloc(h, rscale.size() * sizeof(double));
-      h->mixed.row_mul = (float*)dev_alloc(h, rowmul.size() * sizeof(float));
-      if (!h->mixed.b_slices || !h->mixed.row_scale || !h->mixed.row_mul)
-        return set_err(h, RIDG_ENOMEM, "mixed operator allocation failed");
+    // 3D: the time-mean rows P-bar (first theta_S rows of P) for the step, and for
+    // ridg_predict every block of theta_S rows (time mode a), each its own digit operator
+    for (int a = 0; a <= h->nb; ++a) {
+      ridg::MixedOp& op = a == 0 ? h->mixed : h->mixed3_pred[a - 1];
+      const int r0 = a == 0 ? 0 : (a - 1) * h->thS;
+      std::vector<double> rows(h->P_host.begin() + (size_t)r0 * h->K,
+                               h->P_host.begin() + (size_t)(r0 + h->thS) * h->K);
+      std::vector<unsigned short> digits;
+      std::vector<double> rscale;
+      std::vector<float> rowmul;
+      int rc = ridg::mixed_build(3, h->nb, rows, h->thS, h->opt.slices, h->box, digits, rscale,
+                                 rowmul, op, digits_f16(h));
+      if (rc != RIDG_OK) return set_err(h, rc, "3D mixed operator build failed");
+      if (!op.b_slices) {
+        op.b_slices = dev_alloc(h, digits.size() * sizeof(unsigned short));
+        op.row_scale = (double*)dev_alloc(h, rscale.size() * sizeof(double));
+        op.row_mul = (float*)dev_alloc(h, rowmul.size() * sizeof(float));
+        if (!op.b_slices || !op.row_scale || !op.row_mul)
+          return set_err(h, RIDG_ENOMEM, "mixed operator allocation failed");
+      }
+      RIDG_CUDA(h, cudaMemcpyAsync(op.row_mul, rowmul.data(), rowmul.size() * sizeof(float),
+                                   cudaMemcpyHostToDevice, h->stream));
+      RIDG_CUDA(h, cudaMemcpyAsync(op.b_slices, digits.data(),
+                                   digits.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
+                                   h->stream));
+      RIDG_CUDA(h, cudaMemcpyAsync(op.row_scale, rscale.data(), rscale.size() * sizeof(double),
+                                   cudaMemcpyHostToDevice, h->stream));
+      RIDG_CUDA(h, cudaStreamSynchronize(h->stream));  // host vectors go out of scope
     }
-    RIDG_CUDA(h, cudaMemcpyAsync(h->mixed.row_mul, rowmul.data(), rowmul.size() * sizeof(float),
-                                 cudaMemcpyHostToDevice, h->stream));
-    RIDG_CUDA(h, cudaMemcpyAsync(h->mixed.b_slices, digits.data(),
-                                 digits.size() * sizeof(unsigned short), cudaMemcpyHostToDevice,
-                                 h->stream));
-    RIDG_CUDA(h, cudaMemcpyAsync(h->mixed.row_scale, rscale.data(), rscale.size() * sizeof(double),
-                                 cudaMemcpyHostToDevice, h->stream));
-    RIDG_CUDA(h, cudaStreamSynchronize(h->stream));  // host vectors go out of scope
     if (!h->ms.planes) {
       Grid g = grid_of(h);
       h->Y = (double*)dev_alloc(h, (size_t)h->ncell * h->thS * sizeof(double));  // float2 pairs
@@ -331,7 +336,7 @@ int enqueue_predict_mean(ridg_t* h) {
   Grid g = grid_of(h);
   if (is_mixed_linear(h) && h->dim == 3) {
     RIDG_CUDA(h, ridg::launch_mixed3_gemm(g, h->nb, h->mixed, h->ms, h->Y, h->tune_gemm3_slots,
-                                          h->stream));
+                                          h->stream, true));
   } else if (is_mixed_linear(h)) {
     RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed, h->ms, h->Y, 1, h->ncell, true,
                                          h->stream));
@@ -605,6 +610,11 @@ void ridg_destroy(ridg_t* h) {
   dev_free(h, h->mixed_pred.b_slices);
   dev_free(h, h->mixed_pred.row_scale);
   dev_free(h, h->mixed_pred.row_mul);
+  for (auto& op : h->mixed3_pred) {
+    dev_free(h, op.b_slices);
+    dev_free(h, op.row_scale);
+    dev_free(h, op.row_mul);
+  }
   dev_free(h, h->Y);
   dev_free(h, h->ms.planes);
   dev_free(h, h->ms.exps);
@@ -719,6 +729,18 @@ int ridg_predict(ridg_t* h, double* w_out, int on_device) {
     if (rc) return rc;
     RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed_pred, h->ms, h->W, h->thT, 1, false,
                                          h->stream));
+  } else if (is_mixed_linear(h) && h->dim == 3) {
+    // every time mode's theta_S rows of P on the tensor cores (without the step's exponent
+    // bookkeeping), each block converted from double-float into its columns of W (FP64)
+    int rc = ensure_digits(h);
+    if (rc) return rc;
+    for (int a = 0; a < h->nb; ++a) {
+      const ridg::MixedOp& op = h->mixed3_pred[a];
+      RIDG_CUDA(h, ridg::launch_mixed3_gemm(g, h->nb, op, h->ms, h->Y, h->tune_gemm3_slots,
+                                            h->stream, false));
+      RIDG_CUDA(h, ridg::launch_mixed3_to_w(g, h->thS, a * h->thS, h->thT, h->Y, op.gmax, h->ms,
+                                            h->W, h->stream));
+    }
   } else {
     RIDG_CUDA(h, ridg::launch_predict_fp64(g, h->nb, h->Q, h->P, h->thT, h->W, h->thT, h->stream));
   }

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
     const __grid_constant__ CUtensorMap dmap, const unsigned char* __restrict__ Bg,
     const float* __restrict__ rowmul, int S, int nout, float2* __restrict__ Y, int* __restrict__ exps,
     unsigned long long* __restrict__ maxbits, int nx, int ny, int nz, RegionBox box,
-    int na_cap, int* status) {
+    int na_cap, int step, int* status) {
   constexpr int THS = NB * NB * NB;
   constexpr int P = ((THS + 15) / 16) * 2;
   constexpr int KSTEPS = P / 2;
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
       mbar_init(tempty0 + 8u * i, 256);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    if (blockIdx.x == 0) {
+    if (blockIdx.x == 0 && step) {
       // rotate the running maximum: the correction that follows accumulates a fresh one
       maxbits[0] = maxbits[1];
       maxbits[1] = 0;
@@ -563,11 +563,33 @@ __global__ void __launch_bounds__(128) state_digits3_kernel(const double* __rest
   }
 }
 
+// ridg_predict's outputs: W[e * wstride + c0 + c] = (hi + lo) 2^(s + gmax - 16) in FP64, s the
+// planes' exponent (the launch that produced Y left the step's bookkeeping alone)
+__global__ void mixed3_to_w_kernel(const float2* __restrict__ Y, long long ncell, int nout, int c0,
+                                   int wstride, const int* __restrict__ exps, int gmax,
+                                   double* __restrict__ W) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncell * nout) return;
+  const int c = (int)(i / ncell);
+  const long long e = i - (long long)c * ncell;
+  const int k = exps[0] + gmax - 16;
+  const float2 y = Y[i];
+  W[e * wstride + c0 + c] = f2d_scale(y.x, k) + f2d_scale(y.y, k);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
+cudaError_t launch_mixed3_to_w(const Grid& g, int nout, int c0, int wstride, const void* Y,
+                               int gmax, const MixedState& ms, double* W, cudaStream_t s) {
+  const long long n = g.ncell * nout;
+  mixed3_to_w_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float2*)Y, g.ncell, nout, c0,
+                                                                 wstride, ms.exps, gmax, W);
+  return cudaGetLastError();
+}
+
 bool mixed3_supported(int nb, int slices) {
   if (nb < 2 || nb > 3 || slices < 2 || slices > 6) return false;
   const Gemm3Layout l = gemm3_layout(slices, nb * nb * nb, 2, 2, 2);  // widest upwind box
@@ -606,7 +628,7 @@ int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_o
 
 template <int NB>
 static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& ms, void* Y,
-                                  int slots, cudaStream_t s) {
+                                  int slots, cudaStream_t s, bool step) {
   const Gemm3Layout L = gemm3_layout(op.slices, NB * NB * NB, g.box.cnt[0], g.box.cnt[1],
                                      g.box.cnt[2], slots);
   if (L.na < 2 || L.bytes > kSmemLimit) return cudaErrorInvalidValue;
@@ -624,7 +646,7 @@ static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& 
   kern<<<grid, kGemmThreads, smem, s>>>(*(const CUtensorMap*)ms.map,
                                         (const unsigned char*)op.b_slices, op.row_mul, op.slices,
                                         op.nout, (float2*)Y, ms.exps, ms.maxbits, g.n[0], g.n[1],
-                                        g.n[2], g.box, slots, ms.status);
+                                        g.n[2], g.box, slots, step ? 1 : 0, ms.status);
   return cudaGetLastError();
 }
 
@@ -634,12 +656,12 @@ int mixed3_gemm_slots(int nb, int slices, const RegionBox& box, int cap) {
 }
 
 cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
-                               int slots, cudaStream_t s) {
+                               int slots, cudaStream_t s, bool step) {
   if (g.dim != 3 || g.box.n < 1 || g.box.n > 8 || op.K != g.box.n * nb * nb * nb)
     return cudaErrorInvalidValue;
   switch (nb) {
-    case 2: return launch_gemm3_t<2>(g, op, ms, Y, slots, s);
-    case 3: return launch_gemm3_t<3>(g, op, ms, Y, slots, s);
+    case 2: return launch_gemm3_t<2>(g, op, ms, Y, slots, s, step);
+    case 3: return launch_gemm3_t<3>(g, op, ms, Y, slots, s, step);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -99,9 +99,16 @@ size_t mixed3_plane_bytes(const Grid& g, int nb, int slices);
 int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_out);
 // Y[c * cells + e] = (P-bar X_e)[c] as double-float pairs from the digit planes in ms (value
 // (hi + lo) 2^(exps[1] + gmax - 16))
-// (slots: depth of the plane-operand ring, 0 = as many as fit; the autotuner's choice)
+// (slots: depth of the plane-operand ring, 0 = as many as fit; the autotuner's choice.
+// step: the launch is the step's prediction -- it rotates the running maximum and records
+// the outputs' exponent in exps[1]; ridg_predict's launches leave both alone, their
+// outputs carry the planes' exponent exps[0])
 cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
-                               int slots, cudaStream_t s);
+                               int slots, cudaStream_t s, bool step);
+// W[e * wstride + c0 + c] = the double-float outputs Y[c * cells + e] of a prediction launch
+// (c < nout), as FP64 with the planes' exponent
+cudaError_t launch_mixed3_to_w(const Grid& g, int nout, int c0, int wstride, const void* Y,
+                               int gmax, const MixedState& ms, double* W, cudaStream_t s);
 // the ring depth a slot cap gives for this configuration (0: it does not fit)
 int mixed3_gemm_slots(int nb, int slices, const RegionBox& box, int cap);
 // the correction from those outputs (face values from each cell's own and upstream
@@ -250,6 +257,7 @@ struct ridg_handle {
   int red_blocks = 256;
   ridg::MixedOp mixed;       // fused step operator [V; u_x; u_y] P-bar (2D)
   ridg::MixedOp mixed_pred;  // full prediction operator P
+  ridg::MixedOp mixed3_pred[4];  // 3D: the theta_S rows of P of each time mode (nb <= 4)
   double* Y = nullptr;       // fused outputs of the mixed step (cells * nout pairs)
   ridg::MixedState ms;       // digit planes and exponent bookkeeping of the mixed path
   int ny_out = 0;

@@ -186,3 +186,21 @@ def test_config3_noisy_data_mixed_within_105_of_oracle(R, slices):
     assert e <= 1.05 * g["l2_error"], (e, g["l2_error"])
     tol = 1e-10 if slices == 6 else 2.0 ** -32 * 64 * g["steps"]
     assert float(np.abs(q[cells] - qref).max() / np.abs(qref).max()) < tol
+
+
+@pytest.mark.parametrize("M,vel", [(2, (1.0, 0.7, 0.3)), (1, (-0.6, 0.4, 0.0)), (2, (0.0, -1.0, 0.5))])
+def test_mixed3_full_prediction_matches_oracle(R, M, vel):
+    # ridg_predict on the tensor cores: every time mode's theta_S rows of the region operator
+    # (all theta_T outputs) at 6 slices, against the oracle's region solves
+    w = _w((10, 17, 3), M, vel)
+    s = _mixed(R, w)
+    q = np.random.default_rng(43).standard_normal((s.cells, s.theta_s))
+    s.set_state(q)
+    dt = s.info()["dt"]
+    W = s.predict()
+    assert _rel(W, OL.predict(q, w, dt)) < TOL_STEP
+    # the step that follows is unaffected (the prediction leaves its bookkeeping alone)
+    s.step(2)
+    s.sync()
+    assert _rel(s.get_state(), OL.run(q, w, dt, 2)) < 2 * TOL_STEP
+    s.close()
