@@ -31,6 +31,8 @@ def main(argv=None):
     p.add_argument("--slices", type=int, default=0, help="digit slices of the mixed BF16 path")
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=0)
+    p.add_argument("--autotune", action="store_true",
+                   help="run the library's autotuner on the state before the steps")
     a = p.parse_args(argv)
     over = {}
     if a.mesh:
@@ -42,10 +44,13 @@ def main(argv=None):
                  cfl=w["cfl"], lo=w["lo"], hi=w["hi"], gamma=w.get("gamma", 1.4),
                  precision=PRECISIONS[a.precision], slices=a.slices)
     s.set_state(I.initial_state(w))
+    if a.autotune:
+        s.autotune()
     if a.warmup:
         s.profile_step(a.warmup)
     prof = s.profile_step(a.steps)
     info = s.info()
+    tuning = s.tuning()
     s.close()
     cells = int(np.prod(w["n"]))
     print(json.dumps({"workload": a.workload, "mesh": list(w["n"]), "order": w["M"],
@@ -53,7 +58,7 @@ def main(argv=None):
                       "dof_per_s": cells * info["m"] * info["theta_s"] / (prof["step_ms"] * 1e-3),
                       "newton_iters_total": info["newton_iters_total"],
                       "newton_iters_max": info["newton_iters_max"],
-                      "newton_unconverged": info["newton_unconverged"]}))
+                      "newton_unconverged": info["newton_unconverged"], "tuning": tuning}))
 
 
 if __name__ == "__main__":
