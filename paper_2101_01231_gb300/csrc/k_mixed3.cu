@@ -396,22 +396,37 @@ __global__ void __launch_bounds__(BT) mixed3_correct_kernel(
       const float2* Yo = Y + e;
       const float2* Yu = Y + up;
       const unsigned stn = (unsigned)st * (unsigned)ncell;
-      float2 co[NB], cu[NB];
+      // lines are walked with two cursors: the line computed (a) and the line whose values
+      // are loaded, two ahead (b), so that two lines' loads are in flight
+      int alo = 0, ahi = 0, blo = 0, bhi = 0;
+      auto advance = [&](int& lo, int& hi) {
+        if (++lo == st) {
+          lo = 0;
+          hi += st * NB;
+        }
+      };
+      float2 co[NB], cu[NB], n1o[NB], n1u[NB];
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         co[b] = Yo[b * stn];
         cu[b] = Yu[b * stn];
       }
-      int lo = 0, hi = 0;
+      advance(blo, bhi);
+      {
+        const unsigned off = (unsigned)(NT > 1 ? bhi + blo : 0) * (unsigned)ncell;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          n1o[b] = Yo[off + b * stn];
+          n1u[b] = Yu[off + b * stn];
+        }
+      }
+      advance(blo, bhi);
 #pragma unroll 1
       for (int t = 0; t < NT; ++t) {
-        const int base = hi + lo;
-        // the next line, in flight while this one is computed
-        if (++lo == st) {
-          lo = 0;
-          hi += st * NB;
-        }
-        const unsigned noff = (unsigned)(t + 1 < NT ? hi + lo : base) * (unsigned)ncell;
+        const int base = ahi + alo;
+        advance(alo, ahi);
+        const unsigned noff = (unsigned)(t + 2 < NT ? bhi + blo : base) * (unsigned)ncell;
+        if (t + 2 < NT) advance(blo, bhi);
         float2 no[NB], nu2[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -445,8 +460,10 @@ __global__ void __launch_bounds__(BT) mixed3_correct_kernel(
         }
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          co[b] = no[b];
-          cu[b] = nu2[b];
+          co[b] = n1o[b];
+          cu[b] = n1u[b];
+          n1o[b] = no[b];
+          n1u[b] = nu2[b];
         }
       }
     }
