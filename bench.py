@@ -537,6 +537,56 @@ def newton_section(R, I, steps, cpu_cells):
     return out
 
 
+def newton3d_section(R, I, cpu=True):
+    """The 3D nonlinear prediction (3D Burgers, degree 1, smooth seeded data): one step at 32^3
+    with FP32 region solves (FP64 residual and update) and at 12^3 in FP64, each with the
+    rate of its dense per-region LU (2/3 n^3 flop per factorisation, n = 27 theta_T = 432)
+    against the FP32 / FP64 pipe, and the oracle's per-region time on the host."""
+    import torch
+    from oracle import linear as OL
+    from oracle import nonlinear as ONL
+
+    def data(n):
+        w = dict(flux="burgers", dim=3, n=(n,) * 3, M=1, lo=(0.0,) * 3, hi=(1.0,) * 3, cfl=0.3)
+        f = lambda x, y, z: (0.3 + 0.1 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+                             * np.sin(2 * np.pi * z) + 0.05 * np.cos(2 * np.pi * (x + z)))
+        return w, np.ascontiguousarray(I.project_tensor(f, w, 2)[:, 0, :])
+
+    out = {"workload": "burgers3d Q1, smooth data (sines)", "solver": "dense per-region LU"}
+    for tag, n, prec, peak in (("mixed_fp32", 32, R.RIDG_PREC_MIXED_FP32, FP32_PEAK_TFLOPS),
+                               ("fp64", 12, R.RIDG_PREC_FP64, FP64_PEAK_TFLOPS)):
+        w, q = data(n)
+        s = R.Solver(3, w["n"], 1, flux="burgers", cfl=w["cfl"], precision=prec,
+                     newton_max_iters=8)
+        s.set_state(q)
+        s.profile_step(1)                         # warm-up
+        s.set_state(q)
+        p = s.profile_step(1)
+        info = s.info()
+        s.close()
+        cells = n ** 3
+        flops = 2.0 / 3.0 * 432.0 ** 3 * info["newton_iters_total"]
+        ach = flops / (p["predict_ms"] * 1e-3) / 1e12
+        out[tag] = {"mesh": [n] * 3, "ms_per_step": p["step_ms"], "predict_ms": p["predict_ms"],
+                    "correct_ms": p["correct_ms"], "value": cells * 8 / (p["step_ms"] * 1e-3),
+                    "unit": "element-DOF updates/s",
+                    "newton_iters_per_cell": info["newton_iters_total"] / cells,
+                    "roofline": {"bound": "alu", "kernel": "newton3_kernel (LU flops)",
+                                 "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                 "frac": ach / peak, "traffic": None,
+                                 "peak_source": "nominal: FMA pipes x 2 flop x 2.07 GHz"}}
+    if cpu:
+        w, q = data(12)
+        dt, _ = OL.time_step(w, ONL.max_speed(q, w))
+        t0 = time.perf_counter()
+        ONL.newton_predict(q, w, dt, cells=np.arange(8), max_iters=8)
+        per = (time.perf_counter() - t0) / 8
+        out["cpu_oracle"] = {"kind": "oracle", "cores": os.cpu_count(), "seconds_per_cell": per,
+                             "value": 8 / per, "unit": "element-DOF updates/s",
+                             "sample": "Newton predictions of 8 cells (numpy, host cores)"}
+    return out
+
+
 def newton_accuracy(R, I):
     """The config's equal-accuracy check on a mesh the oracle can run to t = 1: the Euler
     vortex at Q2 on 32^2 (27 steps) with each Newton precision, L2 error against the
@@ -1001,6 +1051,7 @@ def run_ours(args):
             line["adv2d"]["cpu_oracle"] = cpu_oracle(w2, args.cpu_seconds)
     if args.newton_steps > 0:
         line["newton"] = newton_section(R, I, args.newton_steps, 8 if args.no_cpu_baseline else 16)
+        line["newton3d"] = newton3d_section(R, I, cpu=not args.no_cpu_baseline)
     if args.adv1d_reps > 0:
         line["adv1d"] = adv1d_section(R, I, args.adv1d_reps)
     if args.paper1d > 0:

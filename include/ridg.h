@@ -137,7 +137,9 @@ typedef struct {
  * quasi-quadrature-free tables of Sec. 3 are built.  dt is set from `cfl` for advection
  * (dt = cfl h_min / max|a_d|); for nonlinear flux it is set by ridg_set_state.
  * Supported: ADVECTION d = 1 (M <= 11), d = 2, 3 (M <= 5; the mixed precisions M <= 3 in
- * 2D, M <= 2 in 3D); BURGERS d = 2 (M <= 4); EULER d = 2 (M <= 2).  `opt` may be NULL.
+ * 2D, M <= 2 in 3D); BURGERS d = 2 (M <= 4) and d = 3 (M = 1: FP64 or MIXED_FP32 region
+ * solves, a dense LU of the 3 x 3 x 3 region's 432 unknowns per Newton iteration); EULER
+ * d = 2 (M <= 2).  `opt` may be NULL.
  * On success *out owns the new handle.                                                 */
 int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double cfl,
                 const ridg_options* opt, ridg_t** out);

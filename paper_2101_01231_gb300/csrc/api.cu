@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "nl3.h"
 #include "ridg_internal.h"
 #include "tune.h"
 #include "tables.h"
@@ -297,7 +298,31 @@ int ensure_digits(ridg_t* h) {
 }
 
 // Newton prediction of every cell's centre W (nonlinear flux).
+int enqueue_newton3(ridg_t* h) {
+  ridg::Newton3Args a;
+  std::memset(&a, 0, sizeof(a));
+  a.tb = h->nl3;
+  a.Q = h->Q;
+  a.W = h->W;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = h->n[d];
+    a.lam[d] = h->dt / h->h[d];
+  }
+  a.ncell = h->ncell;
+  a.max_iters = h->opt.newton_max_iters;
+  a.tol = h->opt.newton_tol;
+  a.scratch = h->nl_scratch;
+  a.scratch_per_cta = h->nl_scratch_cta;
+  a.counter = h->nl_words;
+  a.stats = h->nl_words + 1;
+  a.iters_total = (unsigned long long*)(h->nl_words + 6);
+  RIDG_CUDA(h, ridg::launch_newton3(h->nb, newton_prec(h) != ridg::kNewtonF64, a, h->nl_grid,
+                                    h->stream));
+  return RIDG_OK;
+}
+
 int enqueue_newton(ridg_t* h) {
+  if (h->dim == 3) return enqueue_newton3(h);
   ridg::NewtonArgs a;
   std::memset(&a, 0, sizeof(a));
   a.tb = h->nl.tb;
@@ -323,6 +348,13 @@ int enqueue_newton(ridg_t* h) {
 }
 
 int enqueue_nl_correct(ridg_t* h) {
+  if (h->dim == 3) {
+    double lam[3];
+    for (int d = 0; d < 3; ++d) lam[d] = h->dt / h->h[d];
+    RIDG_CUDA(h, ridg::launch_nl3_correct(h->nb, h->nl3, h->Q, h->W, h->n, h->ncell, lam,
+                                          h->stream));
+    return RIDG_OK;
+  }
   RIDG_CUDA(h, ridg::launch_nl_correct(h->nb, h->m, h->flux.kind, h->nl.tb, h->Q, h->W, h->n[0],
                                        h->n[1], h->ncell, h->dt / h->h[0], h->dt / h->h[1],
                                        h->flux.gamma, h->stream));
@@ -457,7 +489,14 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
       return RIDG_EINVAL;
   } else if (flux->kind == RIDG_FLUX_BURGERS || flux->kind == RIDG_FLUX_EULER) {
     m = flux->kind == RIDG_FLUX_EULER ? 4 : 1;
-    if (mesh->dim != 2 || !ridg::newton_supported(order + 1, m)) return RIDG_EINVAL;
+    if (mesh->dim == 3) {
+      // 3D: Burgers at degree 1, FP64 or FP32 region solves (dense per-region LU)
+      if (flux->kind != RIDG_FLUX_BURGERS || !ridg::newton3_supported(order + 1) ||
+          (prec != RIDG_PREC_FP64 && prec != RIDG_PREC_MIXED_FP32))
+        return RIDG_EINVAL;
+    } else if (mesh->dim != 2 || !ridg::newton_supported(order + 1, m)) {
+      return RIDG_EINVAL;
+    }
     if (prec != RIDG_PREC_FP64 && prec != RIDG_PREC_MIXED_FP32 && prec != RIDG_PREC_MIXED_TF32)
       return RIDG_EINVAL;
     if (flux->kind == RIDG_FLUX_EULER && !(flux->gamma > 1.0)) return RIDG_EINVAL;
@@ -544,7 +583,27 @@ int ridg_create(const ridg_mesh* mesh, int order, const ridg_flux* flux, double 
     ridg_destroy(h);
     return RIDG_ENOMEM;
   }
-  if (!is_linear(h)) {
+  if (!is_linear(h) && h->dim == 3) {
+    size_t tb_bytes = 0;
+    ridg::nl3_tables_upload(h->nb, h->nl3, nullptr, &tb_bytes, h->stream);
+    h->nl3_mem = dev_alloc(h, tb_bytes);
+    h->nl_grid = sm_count();  // one persistent CTA per SM (the region Jacobian lives in HBM)
+    h->nl_grid_max = 0;       // (nothing for the autotuner here)
+    h->nl_scratch_cta = ridg::newton3_scratch_per_cta(h->nb, newton_prec(h) != ridg::kNewtonF64);
+    h->nl_scratch = h->nl_grid > 0 ? dev_alloc(h, h->nl_scratch_cta * (size_t)h->nl_grid) : nullptr;
+    h->nl_words = (int*)dev_alloc(h, 24 * sizeof(int));
+    if (!h->nl3_mem || !h->nl_scratch || !h->nl_words) {
+      ridg_destroy(h);
+      return RIDG_ENOMEM;
+    }
+    int rc = ridg::nl3_tables_upload(h->nb, h->nl3, h->nl3_mem, &tb_bytes, h->stream);
+    if (rc == RIDG_OK && cudaMemsetAsync(h->nl_words, 0, 24 * sizeof(int), h->stream) != cudaSuccess)
+      rc = RIDG_ECUDA;
+    if (rc != RIDG_OK) {
+      ridg_destroy(h);
+      return rc;
+    }
+  } else if (!is_linear(h)) {
     size_t tb_bytes = 0;
     ridg::nl_tables_upload(h->nb, h->nl, nullptr, &tb_bytes, h->stream);
     void* tb_mem = dev_alloc(h, tb_bytes);
@@ -622,6 +681,7 @@ void ridg_destroy(ridg_t* h) {
   dev_free(h, h->nl.mem);
   if (!h->nl_scratch_shared) dev_free(h, h->nl_scratch);
   dev_free(h, h->nl_words);
+  dev_free(h, h->nl3_mem);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -663,6 +723,10 @@ int ridg_set_state(ridg_t* h, const double* q, int on_device) {
   if (!is_linear(h) && !h->dt_fixed) {
     // Sec. 5: dt = cfl h_min / (largest wave speed of the state)
     unsigned long long bits = 0;
+    if (h->dim == 3)
+      RIDG_CUDA(h, ridg::launch_max_speed3(h->nb, h->Q, h->ncell,
+                                           (unsigned long long*)(h->nl_words + 4), h->stream));
+    else
     RIDG_CUDA(h, ridg::launch_max_speed(h->nb, h->m, h->flux.kind, h->nl.tb, h->Q, h->ncell,
                                         h->flux.gamma, (unsigned long long*)(h->nl_words + 4),
                                         h->stream));
@@ -673,7 +737,9 @@ int ridg_set_state(ridg_t* h, const double* q, int on_device) {
     std::memcpy(&smax, &bits, sizeof(smax));
     if (!(smax > 0.0) || !std::isfinite(smax))
       return set_err(h, RIDG_EINVAL, "the state has no positive finite wave speed; set dt");
-    h->dt = h->cfl * std::min(h->h[0], h->h[1]) / smax;
+    double hmin = std::min(h->h[0], h->h[1]);
+    if (h->dim == 3) hmin = std::min(hmin, h->h[2]);
+    h->dt = h->cfl * hmin / smax;
     drop_graphs(h);
     h->gen += 1;
   }
@@ -1150,6 +1216,9 @@ extern "C" {
 int ridg_batch_create(int count, const ridg_mesh* meshes, const int* orders, const ridg_flux* flux,
                       double cfl, const ridg_options* opt, ridg_batch_t** out) {
   if (count < 1 || !meshes || !orders || !flux || !out) return RIDG_EINVAL;
+  if (flux->kind != RIDG_FLUX_ADVECTION)
+    for (int i = 0; i < count; ++i)
+      if (meshes[i].dim != 2) return RIDG_EINVAL;  // the batched Newton launch is 2D
   *out = nullptr;
   ridg_batch_t* b = new ridg_batch_t();
   ridg_options o{};

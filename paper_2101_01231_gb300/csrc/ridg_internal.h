@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/ridg.h"
+#include "nl3.h"
 #include "tables.h"
 
 namespace ridg {
@@ -269,6 +270,8 @@ struct ridg_handle {
   // nonlinear flux: tables, elimination plan, per-CTA block storage of the Newton kernel
   ridg::NlDevTables nl;
   ridg::NlPlan plan{};
+  ridg::Nl3Dev nl3{};          // 3D nonlinear flux: tables (in nl3_mem)
+  void* nl3_mem = nullptr;
   void* nl_scratch = nullptr;
   size_t nl_scratch_cta = 0;
   int nl_grid = 0;        // CTAs of the persistent Newton launch (autotuned)
