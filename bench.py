@@ -285,8 +285,13 @@ def ensemble_section(R, I, steps, cpu_cells, rank=0, ws=1):
     b = batch(small)
     R.ridg_batch_step(b, 1)
     R.ridg_batch_sync(b)
+    if AUTOTUNE[0]:
+        # the schedule (the whole ensemble in two launches, or a launch per degree and per
+        # instance), timed on the capped ensemble; the full batch reads the choice
+        R.ridg_batch_autotune(b)
     R.ridg_batch_destroy(b)
     b = batch(ens)
+    sched = R.ridg_batch_schedule(b)
     times, status = [], []
     for _ in range(steps):
         a0 = torch.cuda.Event(enable_timing=True)
@@ -310,10 +315,14 @@ def ensemble_section(R, I, steps, cpu_cells, rank=0, ws=1):
                                 for m in (1, 2, 3, 4)},
            "precision": "mixed_tf32", "steps": steps, "ms_per_step": ms,
            "value": dof / (ms * 1e-3), "unit": "element-DOF updates/s",
-           "launches_per_step": "1 Newton launch per degree + 1 correction per instance",
+           "schedule": ("the whole ensemble's Newton prediction in one launch (every degree's "
+                        "regions, highest degree first) + every instance's correction in one"
+                        if sched["schedule"] == 1 else
+                        "one Newton launch per degree + one correction per instance"),
+           "launches_per_step": sched["launches_per_step"],
            "newton_unconverged": sum(inf["newton_unconverged"] for inf in infos),
            "status": [int(x) for x in status],
-           "roofline": {"bound": "alu", "kernel": "newton_kernel (4 launches, one per degree)",
+           "roofline": {"bound": "alu", "kernel": "newton_kernel (all degrees)",
                         "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
                         "peak_source": "nominal: FMA pipes x 2 flop x 2.07 GHz"}}

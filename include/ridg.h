@@ -290,6 +290,16 @@ ridg_t* ridg_batch_instance(ridg_batch_t* b, int i);
 int ridg_batch_set_state(ridg_batch_t* b, int i, const double* q, int on_device);
 int ridg_batch_get_state(ridg_batch_t* b, int i, double* q, int on_device);
 int ridg_batch_step(ridg_batch_t* b, int n);
+/* The batch's schedule for a nonlinear flux (1: the whole ensemble's Newton prediction in one
+ * launch -- every degree's regions, highest degree first, each CTA moving to the next
+ * degree's queue as one runs out -- and every instance's correction in one more launch;
+ * 0: one Newton launch per degree and one correction per instance) and the kernel launches
+ * of one step.  Burgers batches default to 1 unless the autotuner recorded otherwise.     */
+int ridg_batch_schedule(ridg_batch_t* b, int* schedule, int* launches_per_step);
+/* Time one step in each schedule from the instances' current states (restored afterwards,
+ * graphs dropped) and keep the faster; the choice goes into the autotuner's cache (and to
+ * cache_path if not NULL) for later batches of the same flux and precision.               */
+int ridg_batch_autotune(ridg_batch_t* b, const char* cache_path);
 int ridg_batch_sync(ridg_batch_t* b);
 
 /* ----- a mesh sharded into slabs (domain decomposition, Sec. 5) ------------------------- */

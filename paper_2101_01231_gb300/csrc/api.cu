@@ -78,6 +78,10 @@ std::string key_gemm3(const ridg_t* h) {
 std::string key_corr3(const ridg_t* h) {
   return "corr3.block nb" + std::to_string(h->nb) + " S" + std::to_string(h->opt.slices);
 }
+std::string key_batch(const ridg_t* h) {
+  return "batch.schedule flux" + std::to_string(h->flux.kind) + " prec" +
+         std::to_string(h->opt.precision);
+}
 std::string key_newton(const ridg_t* h) {
   return "newton.grid nb" + std::to_string(h->nb) + " m" + std::to_string(h->m) + " flux" +
          std::to_string(h->flux.kind) + " prec" + std::to_string(h->opt.precision);
@@ -1149,6 +1153,13 @@ struct ridg_batch {
   std::map<int, cudaGraphExec_t> graphs;
   std::map<int, cudaGraph_t> defs;
   std::vector<unsigned long long> gens;  // operator generation of each instance at capture
+  // nonlinear flux: one Newton launch over every degree's regions and one correction launch
+  // over every instance's cells (schedule 1, the default) or one launch per degree and per
+  // instance (schedule 0); the autotuner may pick either
+  int schedule = 1;
+  std::vector<ridg::CorrInst> corr_host;  // all instances, cell0 increasing
+  ridg::CorrInst* corr_table = nullptr;
+  long long corr_cells = 0;
 };
 
 namespace {
@@ -1177,11 +1188,32 @@ int refresh_nl_tables(ridg_batch_t* b) {
                         cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
       return RIDG_ECUDA;
   }
+  if (b->corr_table) {
+    long long cell0 = 0;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+      ridg_t* h = b->inst[i];
+      ridg::CorrInst& c = b->corr_host[i];
+      c.Q = h->Q;
+      c.W = h->W;
+      c.cell0 = cell0;
+      c.nx = h->n[0];
+      c.ny = h->n[1];
+      c.nb = h->nb;
+      c.lamx = h->dt / h->h[0];
+      c.lamy = h->dt / h->h[1];
+      cell0 += h->ncell;
+    }
+    b->corr_cells = cell0;
+    if (cudaMemcpyAsync(b->corr_table, b->corr_host.data(),
+                        b->corr_host.size() * sizeof(ridg::CorrInst), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess)
+      return RIDG_ECUDA;
+  }
   return RIDG_OK;
 }
 
-// One persistent Newton launch over every region of the group's instances.
-int enqueue_newton_group(ridg_batch_t* b, const NlGroup& g) {
+// The arguments of a Newton launch over every region of the group's instances.
+ridg::NewtonArgs group_args(ridg_batch_t* b, const NlGroup& g) {
   ridg_t* h = b->inst[g.idx[0]];
   ridg::NewtonArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -1204,8 +1236,45 @@ int enqueue_newton_group(ridg_batch_t* b, const NlGroup& g) {
   a.iters_total = (unsigned long long*)(h->nl_words + 6);
   a.inst = g.table;
   a.ninst = (int)g.idx.size();
+  return a;
+}
+
+// One persistent Newton launch over every region of the group's instances.
+int enqueue_newton_group(ridg_batch_t* b, const NlGroup& g) {
+  ridg_t* h = b->inst[g.idx[0]];
+  const ridg::NewtonArgs a = group_args(b, g);
   RIDG_CUDA(h, ridg::launch_newton(h->nb, h->m, h->flux.kind, newton_prec(h), a, h->nl_grid,
                                    b->stream));
+  return RIDG_OK;
+}
+
+// The whole ensemble's Newton prediction in one launch (the degrees' queues, highest degree
+// first), then every instance's correction in one launch.
+int enqueue_batch_multi(ridg_batch_t* b) {
+  ridg_t* h0 = b->inst[0];
+  ridg::NewtonMulti m;
+  std::memset(&m, 0, sizeof(m));
+  std::vector<const NlGroup*> order;
+  for (const NlGroup& g : b->groups) order.push_back(&g);
+  std::sort(order.begin(), order.end(), [&](const NlGroup* x, const NlGroup* y) {
+    return b->inst[x->idx[0]]->nb > b->inst[y->idx[0]]->nb;
+  });
+  for (const NlGroup* g : order) {
+    m.a[m.count] = group_args(b, *g);
+    m.nb[m.count] = b->inst[g->idx[0]]->nb;
+    m.count += 1;
+  }
+  const int grid = ridg::newton_multi_ctas_per_sm(newton_prec(h0)) * sm_count();
+  RIDG_CUDA(h0, ridg::launch_newton_multi(newton_prec(h0), m, grid, b->stream));
+  ridg::CorrMulti c;
+  std::memset(&c, 0, sizeof(c));
+  for (const NlGroup& g : b->groups) {
+    ridg_t* h = b->inst[g.idx[0]];
+    c.tb[h->nb - 2] = h->nl.tb;
+  }
+  c.inst = b->corr_table;
+  c.ninst = (int)b->inst.size();
+  RIDG_CUDA(h0, ridg::launch_nl_correct_multi(c, b->corr_cells, b->stream));
   return RIDG_OK;
 }
 
@@ -1276,6 +1345,19 @@ int ridg_batch_create(int count, const ridg_mesh* meshes, const int* orders, con
         return RIDG_ENOMEM;
       }
     }
+    // the single-launch schedule (Burgers: the multi-degree kernels are built for one
+    // conserved variable); the autotuner's choice, if recorded, decides
+    if (flux->kind == RIDG_FLUX_BURGERS) {
+      b->corr_host.resize(count);
+      b->corr_table = (ridg::CorrInst*)dev_alloc(b->inst[0], count * sizeof(ridg::CorrInst));
+      if (!b->corr_table) {
+        ridg_batch_destroy(b);
+        return RIDG_ENOMEM;
+      }
+      b->schedule = ridg::tune_get(key_batch(b->inst[0]), 1);
+    } else {
+      b->schedule = 0;
+    }
   }
   *out = b;
   return RIDG_OK;
@@ -1291,6 +1373,7 @@ void ridg_batch_destroy(ridg_batch_t* b) {
     if (g.table) dev_free(b->inst[0], g.table);
     if (g.counter) dev_free(b->inst[0], g.counter);
   }
+  if (b->corr_table) dev_free(b->inst[0], b->corr_table);
   for (ridg_t* h : b->inst) ridg_destroy(h);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -1346,8 +1429,12 @@ int ridg_batch_step(ridg_batch_t* b, int n) {
           if (rc) break;
         }
       } else {
-        // nonlinear flux: one Newton launch per degree over all its instances, then the
-        // instances' corrections
+        // nonlinear flux: the whole ensemble in two launches, or one Newton launch per
+        // degree over all its instances, then the instances' corrections
+        if (b->schedule == 1 && b->corr_table) {
+          rc = enqueue_batch_multi(b);
+          continue;
+        }
         for (const NlGroup& g : b->groups) {
           rc = enqueue_newton_group(b, g);
           if (rc) break;
@@ -1378,6 +1465,88 @@ int ridg_batch_step(ridg_batch_t* b, int n) {
     h->t += n * h->dt;
     h->steps += n;
   }
+  return RIDG_OK;
+}
+
+int ridg_batch_schedule(ridg_batch_t* b, int* schedule, int* launches_per_step) {
+  if (!b) return RIDG_EINVAL;
+  const bool multi = b->schedule == 1 && b->corr_table;
+  if (schedule) *schedule = multi ? 1 : 0;
+  if (launches_per_step)
+    *launches_per_step = b->groups.empty() ? 2 * (int)b->inst.size()
+                         : multi          ? 2
+                                          : (int)(b->groups.size() + b->inst.size());
+  return RIDG_OK;
+}
+
+int ridg_batch_autotune(ridg_batch_t* b, const char* cache_path) {
+  if (!b || b->inst.empty()) return RIDG_EINVAL;
+  if (b->corr_table) {
+    // one step in each schedule from the instances' current states (put back afterwards)
+    std::vector<double*> save(b->inst.size(), nullptr);
+    std::vector<double> t0(b->inst.size());
+    std::vector<long long> s0(b->inst.size());
+    int rc = RIDG_OK;
+    for (size_t i = 0; i < b->inst.size() && !rc; ++i) {
+      ridg_t* h = b->inst[i];
+      const size_t bytes = (size_t)h->ncell * h->m * h->thS * sizeof(double);
+      save[i] = (double*)dev_alloc(h, bytes);
+      if (!save[i]) rc = RIDG_ENOMEM;
+      else if (cudaMemcpyAsync(save[i], h->Q, bytes, cudaMemcpyDeviceToDevice, b->stream) !=
+               cudaSuccess)
+        rc = RIDG_ECUDA;
+      t0[i] = h->t;
+      s0[i] = h->steps;
+    }
+    auto restore = [&]() {
+      for (size_t i = 0; i < b->inst.size(); ++i) {
+        ridg_t* h = b->inst[i];
+        if (save[i])
+          cudaMemcpyAsync(h->Q, save[i], (size_t)h->ncell * h->m * h->thS * sizeof(double),
+                          cudaMemcpyDeviceToDevice, b->stream);
+        h->t = t0[i];
+        h->steps = s0[i];
+      }
+    };
+    double best = 1e300;
+    int best_s = b->schedule;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+      rc = RIDG_ECUDA;
+    for (int sch = 1; sch >= 0 && !rc; --sch) {
+      b->schedule = sch;
+      for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+      for (auto& kv : b->defs) cudaGraphDestroy(kv.second);
+      b->graphs.clear();
+      b->defs.clear();
+      for (int rep = 0; rep < 2 && !rc; ++rep) {  // the first run captures the graph
+        restore();
+        cudaEventRecord(e0, b->stream);
+        rc = ridg_batch_step(b, 1);
+        cudaEventRecord(e1, b->stream);
+        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = RIDG_ECUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (!rc && rep == 1 && ms < best) {
+          best = ms;
+          best_s = sch;
+        }
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    restore();
+    cudaStreamSynchronize(b->stream);
+    for (size_t i = 0; i < b->inst.size(); ++i) dev_free(b->inst[i], save[i]);
+    b->schedule = best_s;
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : b->defs) cudaGraphDestroy(kv.second);
+    b->graphs.clear();
+    b->defs.clear();
+    if (rc && rc != RIDG_ENOCONV) return rc;
+    ridg::tune_put(key_batch(b->inst[0]), best_s);
+  }
+  if (cache_path && !ridg::tune_save(cache_path)) return RIDG_EINVAL;
   return RIDG_OK;
 }
 

@@ -1340,12 +1340,35 @@ __device__ void stored_solve_tc(const float* slots, const NlPlan& plan, float* x
 // ---------------------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------------------
+// TMEM for the block products: 128 columns (>= BP for every degree), allocated once per CTA
+__device__ __forceinline__ uint32_t tmem_alloc128(uint32_t* tslot) {
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return *tslot;
+}
+
+__device__ __forceinline__ void tmem_free128(uint32_t tmem) {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+}
+
+// Every region of one launch's degree, taken from its counter until it runs out.  The
+// shared memory is laid out for this degree; with TC the CTA's TMEM columns (tmem) are given
+// and the ring's barriers are initialised here (copies and products are all complete when
+// this returns, so the next degree may reuse the same shared memory and TMEM).
 template <typename T, int NB, int MV, int FLUX, bool TC, bool BATCH>
-__global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newton_kernel(const NewtonArgs a) {
+__device__ void newton_regions(const NewtonArgs& a, unsigned char* smem, uint32_t tmem) {
   static_assert(!TC || sizeof(T) == 4, "tensor-core block products are TF32 (T = float)");
   using D = Dims<NB, MV>;
   using L = Layout<T, NB, MV, TC>;
-  extern __shared__ __align__(16) unsigned char smem[];
   double* Ws = (double*)(smem + L::oW);
   double* Qs = (double*)(smem + L::oQ);
   double* Rs = (double*)(smem + L::oR);
@@ -1369,8 +1392,7 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newto
   T* slots = (T*)((char*)a.scratch + (size_t)blockIdx.x * a.scratch_per_cta);
   TcCtx tc{};
   if constexpr (TC) {
-    // TMEM accumulator (128 columns >= BP) and the ring's mbarriers
-    uint32_t* tslot = (uint32_t*)(smem + L::oTmem);
+    // the ring's mbarriers (the TMEM accumulator is the caller's)
     tc.bar = smem_u32(smem + L::oBar);
     tc.ring = smem_u32(arena);
     if (tid == 0) {
@@ -1378,16 +1400,8 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newto
       for (int i = 0; i < 2 * kStages + 1; ++i) mbar_init(tc.bar + 8u * i, 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < 32) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                       smem_u32(tslot)),
-                   "r"(128));
-      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    tc.tmem = *tslot;
+    tc.tmem = tmem;
   }
 
   for (;;) {
@@ -1521,12 +1535,73 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newto
     }
     __syncthreads();
   }
-  if constexpr (TC) {
-    tc_drain(tc);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid < 32)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(128));
+  if constexpr (TC) tc_drain(tc);
+  __syncthreads();
+}
+
+template <typename T, int NB, int MV, int FLUX, bool TC, bool BATCH>
+__global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newton_kernel(const NewtonArgs a) {
+  using L = Layout<T, NB, MV, TC>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t tmem = 0;
+  if constexpr (TC) tmem = tmem_alloc128((uint32_t*)(smem + L::oTmem));
+  newton_regions<T, NB, MV, FLUX, TC, BATCH>(a, smem, tmem);
+  if constexpr (TC) tmem_free128(tmem);
+}
+
+// The batched ensemble's Newton prediction in one launch: the degrees' region queues (each a
+// NewtonArgs with its instance table and counter) in the given order, highest degree first;
+// every CTA works through the first queue, then moves to the next as a queue runs out, so the
+// lower degrees fill the tail of the higher ones.  Burgers (one conserved variable), degrees
+// 1 to 4; shared memory and the launch bounds are those of the largest degree.
+template <typename T, bool TC>
+struct MultiLayout {
+  static constexpr size_t b2 = Layout<T, 2, 1, TC>::bytes, b3 = Layout<T, 3, 1, TC>::bytes,
+                          b4 = Layout<T, 4, 1, TC>::bytes, b5 = Layout<T, 5, 1, TC>::bytes;
+  static constexpr size_t bytes = cmax(cmax(b2, b3), cmax(b4, b5));
+  static constexpr int m2 = Layout<T, 2, 1, TC>::MINB, m3 = Layout<T, 3, 1, TC>::MINB,
+                       m4 = Layout<T, 4, 1, TC>::MINB, m5 = Layout<T, 5, 1, TC>::MINB;
+  static constexpr int MINB = (m2 < m3 ? m2 : m3) < (m4 < m5 ? m4 : m5) ? (m2 < m3 ? m2 : m3)
+                                                                         : (m4 < m5 ? m4 : m5);
+};
+
+template <typename T, bool TC>
+__global__ void __launch_bounds__(kThreads, (MultiLayout<T, TC>::MINB)) newton_multi_kernel(
+    const NewtonMulti m) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t tslot;
+  uint32_t tmem = 0;
+  if constexpr (TC) tmem = tmem_alloc128(&tslot);
+  for (int g = 0; g < m.count; ++g) {
+    switch (m.nb[g]) {
+      case 2: newton_regions<T, 2, 1, RIDG_FLUX_BURGERS, TC, true>(m.a[g], smem, tmem); break;
+      case 3: newton_regions<T, 3, 1, RIDG_FLUX_BURGERS, TC, true>(m.a[g], smem, tmem); break;
+      case 4: newton_regions<T, 4, 1, RIDG_FLUX_BURGERS, TC, true>(m.a[g], smem, tmem); break;
+      case 5: newton_regions<T, 5, 1, RIDG_FLUX_BURGERS, TC, true>(m.a[g], smem, tmem); break;
+      default: break;
+    }
   }
+  if constexpr (TC) tmem_free128(tmem);
+}
+
+template <typename T, bool TC>
+cudaError_t launch_multi_typed(const NewtonMulti& m, int grid, cudaStream_t s) {
+  using ML = MultiLayout<T, TC>;
+  static_assert(ML::bytes <= 232448, "Newton kernel shared memory above the per-CTA limit");
+  cudaError_t e = cudaFuncSetAttribute(newton_multi_kernel<T, TC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ML::bytes);
+  if (e != cudaSuccess) return e;
+  for (int g = 0; g < m.count; ++g) {
+    e = cudaMemsetAsync(m.a[g].counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
+  newton_multi_kernel<T, TC><<<grid, kThreads, ML::bytes, s>>>(m);
+  return cudaGetLastError();
+}
+
+template <typename T, bool TC>
+int multi_ctas_per_sm() {
+  return MultiLayout<T, TC>::MINB;
 }
 
 template <typename T, int NB, int MV, int FLUX, bool TC>

@@ -174,20 +174,28 @@ namespace {
 // ---------------------------------------------------------------------------------------
 constexpr int kCorrThreads = 128;
 
+// the correction of cell e of one mesh (a block of kCorrThreads threads); shared memory
+// carved from `sh` (nl_corr_smem<NB, MV>() bytes)
+template <int NB, int MV>
+constexpr size_t nl_corr_smem() {
+  constexpr int THT = NB * NB * NB, BS = MV * THT, NQ = (3 * (NB - 1) + 2) / 2;
+  constexpr int QV = NQ * NQ * NQ, QF = NQ * NQ;
+  return sizeof(double) * (5 * BS + 2 * MV * QV + 3 * 4 * MV * QF + 4 * QF);
+}
+
 template <int NB, int MV, int FLUX>
-__global__ void __launch_bounds__(kCorrThreads) nl_correct_kernel(NlDev tb, double* __restrict__ Q,
-                                                                  const double* __restrict__ W,
-                                                                  int nx, int ny, double lamx,
-                                                                  double lamy, double gamma) {
+__device__ void nl_correct_cell(const NlDev& tb, double* __restrict__ Q, const double* __restrict__ W,
+                                int nx, int ny, double lamx, double lamy, double gamma,
+                                long long e, double* sh) {
   constexpr int THS = NB * NB, THT = NB * THS, BS = MV * THT;
   constexpr int NQ = (3 * (NB - 1) + 2) / 2, QV = NQ * NQ * NQ, QF = NQ * NQ;
-  __shared__ double Wc[5][BS];          // own, +x, -x, +y, -y neighbours
-  __shared__ double G[2][MV][QV];       // sc_d w_q F_d(w) at the volume points
-  __shared__ double TL[4][MV][QF], TR[4][MV][QF];  // left / right traces per face
-  __shared__ double FH[4][MV][QF];      // sc w F-hat at the face points
-  __shared__ double spd[4][QF];
+  auto Wc = (double(*)[BS])sh;                               // own, +x, -x, +y, -y neighbours
+  auto G = (double(*)[MV][QV])(sh + 5 * BS);                 // sc_d w_q F_d(w), volume points
+  auto TL = (double(*)[MV][QF])(sh + 5 * BS + 2 * MV * QV);  // left / right traces per face
+  auto TR = (double(*)[MV][QF])(sh + 5 * BS + 2 * MV * QV + 4 * MV * QF);
+  auto FH = (double(*)[MV][QF])(sh + 5 * BS + 2 * MV * QV + 8 * MV * QF);  // sc w F-hat
+  auto spd = (double(*)[QF])(sh + 5 * BS + 2 * MV * QV + 12 * MV * QF);
   const int tid = threadIdx.x;
-  const long long e = blockIdx.x;
   const unsigned ue = (unsigned)e, uy = ue / (unsigned)nx;
   const int ix = (int)(ue - uy * (unsigned)nx), iy = (int)uy;
   const long long nbr[5] = {e, (long long)iy * nx + (ix + 1) % nx, (long long)iy * nx + (ix + nx - 1) % nx,
@@ -259,6 +267,38 @@ __global__ void __launch_bounds__(kCorrThreads) nl_correct_kernel(NlDev tb, doub
       acc = fma(sg, fs, acc);
     }
     Q[e * MV * THS + i] += acc;
+  }
+  __syncthreads();  // the shared arrays are reused by the block's next cell
+}
+
+template <int NB, int MV, int FLUX>
+__global__ void __launch_bounds__(kCorrThreads) nl_correct_kernel(NlDev tb, double* __restrict__ Q,
+                                                                  const double* __restrict__ W,
+                                                                  int nx, int ny, double lamx,
+                                                                  double lamy, double gamma) {
+  __shared__ double sh[nl_corr_smem<NB, MV>() / sizeof(double)];
+  nl_correct_cell<NB, MV, FLUX>(tb, Q, W, nx, ny, lamx, lamy, gamma, blockIdx.x, sh);
+}
+
+// Every instance's correction of a batched Burgers ensemble in one launch: block b takes the
+// cell b of the concatenated instances (the instance of the last table entry whose first
+// cell is <= b, found by bisection) and runs that instance's degree.
+__global__ void __launch_bounds__(kCorrThreads) nl_correct_multi_kernel(const CorrMulti m) {
+  __shared__ double sh[nl_corr_smem<5, 1>() / sizeof(double)];  // the largest degree
+  const long long b = blockIdx.x;
+  int lo = 0, hi = m.ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (m.inst[mid].cell0 <= b) lo = mid; else hi = mid - 1;
+  }
+  const CorrInst& in = m.inst[lo];
+  const long long e = b - in.cell0;
+  switch (in.nb) {
+    case 2: nl_correct_cell<2, 1, RIDG_FLUX_BURGERS>(m.tb[0], in.Q, in.W, in.nx, in.ny, in.lamx, in.lamy, 0.0, e, sh); break;
+    case 3: nl_correct_cell<3, 1, RIDG_FLUX_BURGERS>(m.tb[1], in.Q, in.W, in.nx, in.ny, in.lamx, in.lamy, 0.0, e, sh); break;
+    case 4: nl_correct_cell<4, 1, RIDG_FLUX_BURGERS>(m.tb[2], in.Q, in.W, in.nx, in.ny, in.lamx, in.lamy, 0.0, e, sh); break;
+    case 5: nl_correct_cell<5, 1, RIDG_FLUX_BURGERS>(m.tb[3], in.Q, in.W, in.nx, in.ny, in.lamx, in.lamy, 0.0, e, sh); break;
+    default: break;
   }
 }
 
@@ -349,12 +389,42 @@ cudaError_t launch_newton(int nb, int m, int flux_kind, int prec, const NewtonAr
   }
 }
 
+cudaError_t launch_newton_multi_f64(const NewtonMulti& m, int grid, cudaStream_t s);
+cudaError_t launch_newton_multi_f32(const NewtonMulti& m, int grid, cudaStream_t s);
+cudaError_t launch_newton_multi_tf32(const NewtonMulti& m, int grid, cudaStream_t s);
+int newton_multi_ctas_per_sm_f64();
+int newton_multi_ctas_per_sm_f32();
+int newton_multi_ctas_per_sm_tf32();
+
+cudaError_t launch_newton_multi(int prec, const NewtonMulti& m, int grid, cudaStream_t s) {
+  switch (prec) {
+    case kNewtonF64: return launch_newton_multi_f64(m, grid, s);
+    case kNewtonF32: return launch_newton_multi_f32(m, grid, s);
+    case kNewtonTF32: return launch_newton_multi_tf32(m, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int newton_multi_ctas_per_sm(int prec) {
+  switch (prec) {
+    case kNewtonF64: return newton_multi_ctas_per_sm_f64();
+    case kNewtonF32: return newton_multi_ctas_per_sm_f32();
+    case kNewtonTF32: return newton_multi_ctas_per_sm_tf32();
+    default: return 0;
+  }
+}
+
 cudaError_t launch_nl_correct(int nb, int m, int flux_kind, const NlDev& tb, double* Q,
                               const double* W, int nx, int ny, long long ncell, double lamx,
                               double lamy, double gamma, cudaStream_t s) {
   RIDG_NL_SWITCH(nb, m, flux_kind,
                  (nl_correct_kernel<NB, MV, FL><<<(unsigned)ncell, kCorrThreads, 0, s>>>(
                      tb, Q, W, nx, ny, lamx, lamy, gamma)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nl_correct_multi(const CorrMulti& m, long long cells, cudaStream_t s) {
+  nl_correct_multi_kernel<<<(unsigned)cells, kCorrThreads, 0, s>>>(m);
   return cudaGetLastError();
 }
 

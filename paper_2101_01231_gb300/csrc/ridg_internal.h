@@ -207,6 +207,31 @@ struct NewtonArgs {
 };
 cudaError_t launch_newton(int nb, int m, int flux_kind, int prec, const NewtonArgs& a, int grid,
                           cudaStream_t s);
+// The batched Burgers ensemble's Newton prediction in one launch: the degrees' region queues
+// a[0 .. count) (nb[g] = degree + 1, 2..5), highest degree first; every CTA works through
+// the queues in that order.  CTAs per SM of that launch for the precision.
+struct NewtonMulti {
+  NewtonArgs a[4];
+  int nb[4];
+  int count;
+};
+cudaError_t launch_newton_multi(int prec, const NewtonMulti& m, int grid, cudaStream_t s);
+int newton_multi_ctas_per_sm(int prec);
+// Every instance's correction of a batched Burgers ensemble in one launch (one block per
+// cell of the concatenated instances, sorted by cell0); tb[nb - 2]: the degree's tables.
+struct CorrInst {
+  double* Q;
+  const double* W;
+  long long cell0;
+  int nx, ny, nb;
+  double lamx, lamy;
+};
+struct CorrMulti {
+  NlDev tb[4];
+  const CorrInst* inst;
+  int ninst;
+};
+cudaError_t launch_nl_correct_multi(const CorrMulti& m, long long cells, cudaStream_t s);
 cudaError_t launch_nl_correct(int nb, int m, int flux_kind, const NlDev& tb, double* Q,
                               const double* W, int nx, int ny, long long ncell, double lamx,
                               double lamy, double gamma, cudaStream_t s);

@@ -80,6 +80,8 @@ EXPORTS = {
     "ridg_batch_set_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "ridg_batch_get_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "ridg_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "ridg_batch_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "ridg_batch_autotune": (C.c_int, [C.c_void_p, C.c_char_p]),
     "ridg_batch_sync": (C.c_int, [C.c_void_p]),
     "ridg_autotune": (C.c_int, [C.c_void_p, C.c_char_p]),
     "ridg_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -390,6 +392,17 @@ def ridg_batch_set_state(b, i, q):
 def ridg_batch_get_state(b, i, q):
     p, dev = _ptr(q)
     return _check(_lib.ridg_batch_get_state(b, int(i), p, dev))
+
+
+def ridg_batch_schedule(b):
+    sch, ln = C.c_int(), C.c_int()
+    _check(_lib.ridg_batch_schedule(b, C.byref(sch), C.byref(ln)))
+    return {"schedule": sch.value, "launches_per_step": ln.value}
+
+
+def ridg_batch_autotune(b, cache_path=None):
+    return _check(_lib.ridg_batch_autotune(b, cache_path.encode() if cache_path else None),
+                  allow=(RIDG_ENOCONV,))
 
 
 def ridg_batch_step(b, n=1):

@@ -365,3 +365,48 @@ def test_info_histogram_mass_and_batch_state(R):
     with pytest.raises(R.RidgError):
         R.ridg_batch_set_state(b, 3, I.initial_state(ens[0]))
     R.ridg_batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32"])
+def test_ensemble_single_launch_schedule_matches_per_degree(R, prec, tmp_path):
+    """The batch's two schedules -- the whole ensemble's Newton prediction in one launch over
+    every degree's region queue plus one correction launch, or one launch per degree and per
+    instance -- run the same per-region arithmetic: the same bits, instance by instance."""
+    ens = [dict(w, n=(min(w["n"][0], 12), min(w["n"][1], 11))) for w in I.burgers_ensemble()[:10]]
+    p = _prec(R, prec)
+    key = f"batch.schedule flux{R.RIDG_FLUX_BURGERS} prec{p}"
+    out = {}
+    for sch in (1, 0):
+        f = tmp_path / f"s{sch}.txt"
+        f.write_text(f"{key} {sch}\n")
+        R.ridg_tune_load(str(f))
+        b = R.ridg_batch_create([R.make_mesh(2, w["n"]) for w in ens], [w["M"] for w in ens],
+                                R.make_flux("burgers"), ens[0]["cfl"], R.make_options(precision=p))
+        info = R.ridg_batch_schedule(b)
+        assert info["schedule"] == sch
+        assert info["launches_per_step"] == (2 if sch == 1 else len({w["M"] for w in ens}) + len(ens))
+        for i, w in enumerate(ens):
+            R.ridg_batch_set_state(b, i, I.initial_state(w))
+        R.ridg_batch_step(b, 2)
+        assert R.ridg_batch_sync(b) == R.RIDG_OK
+        qs = []
+        for i, w in enumerate(ens):
+            q = np.empty_like(I.initial_state(w))
+            R.ridg_batch_get_state(b, i, q)
+            qs.append(q)
+        R.ridg_batch_destroy(b)
+        out[sch] = qs
+    for a, b2 in zip(out[1], out[0]):
+        assert np.array_equal(a, b2)
+    # the batch autotuner times both and records one of them
+    b = R.ridg_batch_create([R.make_mesh(2, w["n"]) for w in ens], [w["M"] for w in ens],
+                            R.make_flux("burgers"), ens[0]["cfl"], R.make_options(precision=p))
+    for i, w in enumerate(ens):
+        R.ridg_batch_set_state(b, i, I.initial_state(w))
+    R.ridg_batch_autotune(b)
+    assert R.ridg_batch_schedule(b)["schedule"] in (0, 1)
+    assert R.ridg_tune_lookup(key) in (0, 1)
+    q = np.empty_like(I.initial_state(ens[0]))
+    R.ridg_batch_get_state(b, 0, q)
+    assert np.array_equal(q, I.initial_state(ens[0]))     # the states were put back
+    R.ridg_batch_destroy(b)
