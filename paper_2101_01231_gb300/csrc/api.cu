@@ -1142,6 +1142,7 @@ struct NlGroup {
   ridg::NlInst* table = nullptr;       // device copy
   int* counter = nullptr;              // region counter of the group's launch
   long long regions = 0;
+  size_t scratch_off = 0;              // the degree's block storage in the batch's
 };
 
 struct ridg_batch {
@@ -1160,6 +1161,8 @@ struct ridg_batch {
   std::vector<ridg::CorrInst> corr_host;  // all instances, cell0 increasing
   ridg::CorrInst* corr_table = nullptr;
   long long corr_cells = 0;
+  ridg::NewtonMulti multi_host{};           // the single Newton launch's arguments
+  ridg::NewtonMulti* multi_dev = nullptr;   // and their device copy (read by the kernel)
 };
 
 namespace {
@@ -1229,7 +1232,7 @@ ridg::NewtonArgs group_args(ridg_batch_t* b, const NlGroup& g) {
   a.gamma = h->flux.gamma;
   a.max_iters = h->opt.newton_max_iters;
   a.tol = h->opt.newton_tol;
-  a.scratch = b->nl_scratch;
+  a.scratch = (char*)b->nl_scratch + g.scratch_off;
   a.scratch_per_cta = h->nl_scratch_cta;
   a.counter = g.counter;
   a.stats = h->nl_words + 1;
@@ -1250,9 +1253,8 @@ int enqueue_newton_group(ridg_batch_t* b, const NlGroup& g) {
 
 // The whole ensemble's Newton prediction in one launch (the degrees' queues, highest degree
 // first), then every instance's correction in one launch.
-int enqueue_batch_multi(ridg_batch_t* b) {
-  ridg_t* h0 = b->inst[0];
-  ridg::NewtonMulti m;
+int upload_batch_multi(ridg_batch_t* b) {
+  ridg::NewtonMulti& m = b->multi_host;
   std::memset(&m, 0, sizeof(m));
   std::vector<const NlGroup*> order;
   for (const NlGroup& g : b->groups) order.push_back(&g);
@@ -1264,8 +1266,17 @@ int enqueue_batch_multi(ridg_batch_t* b) {
     m.nb[m.count] = b->inst[g->idx[0]]->nb;
     m.count += 1;
   }
+  return cudaMemcpyAsync(b->multi_dev, &m, sizeof(m), cudaMemcpyHostToDevice, b->stream) ==
+                 cudaSuccess
+             ? RIDG_OK
+             : RIDG_ECUDA;
+}
+
+int enqueue_batch_multi(ridg_batch_t* b) {
+  ridg_t* h0 = b->inst[0];
   const int grid = ridg::newton_multi_ctas_per_sm(newton_prec(h0)) * sm_count();
-  RIDG_CUDA(h0, ridg::launch_newton_multi(newton_prec(h0), m, grid, b->stream));
+  RIDG_CUDA(h0, ridg::launch_newton_multi(newton_prec(h0), b->multi_host, b->multi_dev, grid,
+                                          b->stream));
   ridg::CorrMulti c;
   std::memset(&c, 0, sizeof(c));
   for (const NlGroup& g : b->groups) {
@@ -1312,21 +1323,7 @@ int ridg_batch_create(int count, const ridg_mesh* meshes, const int* orders, con
     h->batch_owned = true;
     b->inst.push_back(h);
   }
-  // the instances' Newton kernels run one after another on the batch stream: one block
-  // storage, as large as the largest instance needs, serves them all
   if (flux->kind != RIDG_FLUX_ADVECTION) {
-    size_t need = 0;
-    for (ridg_t* h : b->inst) need = std::max(need, h->nl_scratch_cta * (size_t)h->nl_grid_max);
-    b->nl_scratch = dev_alloc(b->inst[0], need);
-    if (!b->nl_scratch) {
-      ridg_batch_destroy(b);
-      return RIDG_ENOMEM;
-    }
-    for (ridg_t* h : b->inst) {
-      dev_free(h, h->nl_scratch);
-      h->nl_scratch = b->nl_scratch;
-      h->nl_scratch_shared = true;
-    }
     std::map<int, int> gi;  // degree -> group
     for (int i = 0; i < count; ++i) {
       const int nb = b->inst[i]->nb;
@@ -1336,6 +1333,35 @@ int ridg_batch_create(int count, const ridg_mesh* meshes, const int* orders, con
       }
       b->groups[gi[nb]].idx.push_back(i);
     }
+    // one block storage per degree, shared by the degree's instances (their Newton regions
+    // run from one queue): the degrees' block layouts differ, and in the single-launch
+    // schedule a CTA's slot of one degree is in use while another CTA works on the next
+    // degree, so the degrees never share bytes.  Zeroed once: the blocks' padding is never
+    // written again.
+    const int multi_grid = flux->kind == RIDG_FLUX_BURGERS
+                               ? ridg::newton_multi_ctas_per_sm(newton_prec(b->inst[0])) * sm_count()
+                               : 0;
+    size_t need = 0;
+    for (NlGroup& g : b->groups) {
+      ridg_t* h = b->inst[g.idx[0]];
+      g.scratch_off = need;
+      need += h->nl_scratch_cta * (size_t)std::max(h->nl_grid_max, multi_grid);
+    }
+    b->nl_scratch = dev_alloc(b->inst[0], need);
+    const int rc = !b->nl_scratch ? RIDG_ENOMEM
+                   : cudaMemsetAsync(b->nl_scratch, 0, need, b->stream) != cudaSuccess ? RIDG_ECUDA
+                                                                                       : RIDG_OK;
+    if (rc != RIDG_OK) {
+      ridg_batch_destroy(b);
+      return rc;
+    }
+    for (const NlGroup& g : b->groups)
+      for (int i : g.idx) {
+        ridg_t* h = b->inst[i];
+        dev_free(h, h->nl_scratch);
+        h->nl_scratch = (char*)b->nl_scratch + g.scratch_off;
+        h->nl_scratch_shared = true;
+      }
     for (NlGroup& g : b->groups) {
       g.host.resize(g.idx.size());
       g.table = (ridg::NlInst*)dev_alloc(b->inst[0], g.idx.size() * sizeof(ridg::NlInst));
@@ -1350,7 +1376,8 @@ int ridg_batch_create(int count, const ridg_mesh* meshes, const int* orders, con
     if (flux->kind == RIDG_FLUX_BURGERS) {
       b->corr_host.resize(count);
       b->corr_table = (ridg::CorrInst*)dev_alloc(b->inst[0], count * sizeof(ridg::CorrInst));
-      if (!b->corr_table) {
+      b->multi_dev = (ridg::NewtonMulti*)dev_alloc(b->inst[0], sizeof(ridg::NewtonMulti));
+      if (!b->corr_table || !b->multi_dev) {
         ridg_batch_destroy(b);
         return RIDG_ENOMEM;
       }
@@ -1374,6 +1401,7 @@ void ridg_batch_destroy(ridg_batch_t* b) {
     if (g.counter) dev_free(b->inst[0], g.counter);
   }
   if (b->corr_table) dev_free(b->inst[0], b->corr_table);
+  if (b->multi_dev) dev_free(b->inst[0], b->multi_dev);
   for (ridg_t* h : b->inst) ridg_destroy(h);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -1413,7 +1441,8 @@ int ridg_batch_step(ridg_batch_t* b, int n) {
   }
   // the instance tables (and the groups' region counts the graphs are captured with)
   if (!b->groups.empty()) {
-    const int rc = refresh_nl_tables(b);
+    int rc = refresh_nl_tables(b);
+    if (!rc && b->schedule == 1 && b->corr_table) rc = upload_batch_multi(b);
     if (rc) return rc;
   }
   auto it = b->graphs.find(n);

@@ -1565,37 +1565,43 @@ struct MultiLayout {
                                                                          : (m4 < m5 ? m4 : m5);
 };
 
+// (the degrees' arguments are read from device memory: four NewtonArgs are ~6 KB, more than
+// one kernel parameter block should carry)
 template <typename T, bool TC>
 __global__ void __launch_bounds__(kThreads, (MultiLayout<T, TC>::MINB)) newton_multi_kernel(
-    const NewtonMulti m) {
+    const NewtonMulti* __restrict__ m) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t tslot;
   uint32_t tmem = 0;
   if constexpr (TC) tmem = tmem_alloc128(&tslot);
-  for (int g = 0; g < m.count; ++g) {
-    switch (m.nb[g]) {
-      case 2: newton_regions<T, 2, 1, RIDG_FLUX_BURGERS, TC, true>(m.a[g], smem, tmem); break;
-      case 3: newton_regions<T, 3, 1, RIDG_FLUX_BURGERS, TC, true>(m.a[g], smem, tmem); break;
-      case 4: newton_regions<T, 4, 1, RIDG_FLUX_BURGERS, TC, true>(m.a[g], smem, tmem); break;
-      case 5: newton_regions<T, 5, 1, RIDG_FLUX_BURGERS, TC, true>(m.a[g], smem, tmem); break;
+  const int count = m->count;
+  for (int g = 0; g < count; ++g) {
+    const NewtonArgs& a = m->a[g];
+    switch (m->nb[g]) {
+      case 2: newton_regions<T, 2, 1, RIDG_FLUX_BURGERS, TC, true>(a, smem, tmem); break;
+      case 3: newton_regions<T, 3, 1, RIDG_FLUX_BURGERS, TC, true>(a, smem, tmem); break;
+      case 4: newton_regions<T, 4, 1, RIDG_FLUX_BURGERS, TC, true>(a, smem, tmem); break;
+      case 5: newton_regions<T, 5, 1, RIDG_FLUX_BURGERS, TC, true>(a, smem, tmem); break;
       default: break;
     }
   }
   if constexpr (TC) tmem_free128(tmem);
 }
 
+// host: the same arguments in host memory (the counters to zero); dev: their device copy
 template <typename T, bool TC>
-cudaError_t launch_multi_typed(const NewtonMulti& m, int grid, cudaStream_t s) {
+cudaError_t launch_multi_typed(const NewtonMulti& host, const NewtonMulti* dev, int grid,
+                               cudaStream_t s) {
   using ML = MultiLayout<T, TC>;
   static_assert(ML::bytes <= 232448, "Newton kernel shared memory above the per-CTA limit");
   cudaError_t e = cudaFuncSetAttribute(newton_multi_kernel<T, TC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ML::bytes);
   if (e != cudaSuccess) return e;
-  for (int g = 0; g < m.count; ++g) {
-    e = cudaMemsetAsync(m.a[g].counter, 0, sizeof(int), s);
+  for (int g = 0; g < host.count; ++g) {
+    e = cudaMemsetAsync(host.a[g].counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
   }
-  newton_multi_kernel<T, TC><<<grid, kThreads, ML::bytes, s>>>(m);
+  newton_multi_kernel<T, TC><<<grid, kThreads, ML::bytes, s>>>(dev);
   return cudaGetLastError();
 }
 

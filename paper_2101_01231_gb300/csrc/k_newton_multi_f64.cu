@@ -3,8 +3,9 @@
 #include "k_newton.cuh"
 
 namespace ridg {
-cudaError_t launch_newton_multi_f64(const NewtonMulti& m, int grid, cudaStream_t s) {
-  return newton::launch_multi_typed<double, false>(m, grid, s);
+cudaError_t launch_newton_multi_f64(const NewtonMulti& m, const NewtonMulti* dev, int grid,
+                                 cudaStream_t s) {
+  return newton::launch_multi_typed<double, false>(m, dev, grid, s);
 }
 int newton_multi_ctas_per_sm_f64() { return newton::multi_ctas_per_sm<double, false>(); }
 }  // namespace ridg

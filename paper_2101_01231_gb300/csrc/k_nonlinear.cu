@@ -389,18 +389,22 @@ cudaError_t launch_newton(int nb, int m, int flux_kind, int prec, const NewtonAr
   }
 }
 
-cudaError_t launch_newton_multi_f64(const NewtonMulti& m, int grid, cudaStream_t s);
-cudaError_t launch_newton_multi_f32(const NewtonMulti& m, int grid, cudaStream_t s);
-cudaError_t launch_newton_multi_tf32(const NewtonMulti& m, int grid, cudaStream_t s);
+cudaError_t launch_newton_multi_f64(const NewtonMulti& m, const NewtonMulti* dev, int grid,
+                                 cudaStream_t s);
+cudaError_t launch_newton_multi_f32(const NewtonMulti& m, const NewtonMulti* dev, int grid,
+                                 cudaStream_t s);
+cudaError_t launch_newton_multi_tf32(const NewtonMulti& m, const NewtonMulti* dev, int grid,
+                                 cudaStream_t s);
 int newton_multi_ctas_per_sm_f64();
 int newton_multi_ctas_per_sm_f32();
 int newton_multi_ctas_per_sm_tf32();
 
-cudaError_t launch_newton_multi(int prec, const NewtonMulti& m, int grid, cudaStream_t s) {
+cudaError_t launch_newton_multi(int prec, const NewtonMulti& m, const NewtonMulti* dev, int grid,
+                                cudaStream_t s) {
   switch (prec) {
-    case kNewtonF64: return launch_newton_multi_f64(m, grid, s);
-    case kNewtonF32: return launch_newton_multi_f32(m, grid, s);
-    case kNewtonTF32: return launch_newton_multi_tf32(m, grid, s);
+    case kNewtonF64: return launch_newton_multi_f64(m, dev, grid, s);
+    case kNewtonF32: return launch_newton_multi_f32(m, dev, grid, s);
+    case kNewtonTF32: return launch_newton_multi_tf32(m, dev, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

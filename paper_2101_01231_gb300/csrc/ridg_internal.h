@@ -215,7 +215,9 @@ struct NewtonMulti {
   int nb[4];
   int count;
 };
-cudaError_t launch_newton_multi(int prec, const NewtonMulti& m, int grid, cudaStream_t s);
+// (m: the arguments in host memory; dev: their device copy, which the kernel reads)
+cudaError_t launch_newton_multi(int prec, const NewtonMulti& m, const NewtonMulti* dev, int grid,
+                                cudaStream_t s);
 int newton_multi_ctas_per_sm(int prec);
 // Every instance's correction of a batched Burgers ensemble in one launch (one block per
 // cell of the concatenated instances, sorted by cell0); tb[nb - 2]: the degree's tables.
