@@ -166,17 +166,50 @@ int rebuild_linear(ridg_t* h) {
   RIDG_CUDA(h, cudaMemcpyAsync(h->P, h->P_host.data(), sizeof(double) * h->P_host.size(),
                                cudaMemcpyHostToDevice, h->stream));
   if (is_mixed_linear(h) && h->dim == 3) {
-    // 3D: the time-mean rows P-bar (first theta_S rows of P) for the step, and for
-    // ridg_predict every block of theta_S rows (time mode a), each its own digit operator
+    // 3D: the step's operator -- the fused step operator C P-bar where its digits fit (rows:
+    // the volume term sum_d nu_d (D along d) W-bar, then the upwind face trace nu_d tr(W-bar)
+    // of every line of modes along d), else the time-mean rows P-bar (first theta_S rows of
+    // P) --, and for ridg_predict every block of theta_S rows (time mode a), each its own
+    // digit operator
+    const int nb = h->nb, thS = h->thS, K = h->K, NT = nb * nb;
+    h->mixed3_fused = ridg::mixed3_fused_fits(nb, h->opt.slices);
     for (int a = 0; a <= h->nb; ++a) {
       ridg::MixedOp& op = a == 0 ? h->mixed : h->mixed3_pred[a - 1];
       const int r0 = a == 0 ? 0 : (a - 1) * h->thS;
       std::vector<double> rows(h->P_host.begin() + (size_t)r0 * h->K,
                                h->P_host.begin() + (size_t)(r0 + h->thS) * h->K);
+      int nout = thS;
+      if (a == 0 && h->mixed3_fused) {
+        nout = ridg::mixed3_fused_nout(nb);
+        ridg::Tables1D t1 = ridg::tables1d(nb);
+        std::vector<double> C((size_t)nout * thS, 0.0);
+        for (int d = 0; d < 3; ++d) {
+          const int st = d == 0 ? 1 : (d == 1 ? nb : nb * nb);
+          for (int s = 0; s < thS; ++s) {
+            const int ad = (s / st) % nb, base = s - ad * st;
+            for (int b = 0; b < nb; ++b) C[(size_t)s * thS + base + b * st] += nu[d] * t1.D[ad * nb + b];
+          }
+          const std::vector<double>& tr = nu[d] >= 0 ? t1.ep : t1.em;
+          for (int t = 0; t < NT; ++t) {
+            // line t: the modes with the other two indices fixed (the lower one fastest)
+            const int base = d == 0 ? t * nb : (d == 1 ? (t % nb) + (t / nb) * nb * nb : t);
+            for (int b = 0; b < nb; ++b)
+              C[(size_t)(thS + d * NT + t) * thS + base + b * st] = nu[d] * tr[b];
+          }
+        }
+        std::vector<double> G((size_t)nout * K, 0.0);
+        for (int r = 0; r < nout; ++r)
+          for (int s = 0; s < thS; ++s) {
+            const double c = C[(size_t)r * thS + s];
+            if (c == 0.0) continue;
+            for (int k = 0; k < K; ++k) G[(size_t)r * K + k] += c * rows[(size_t)s * K + k];
+          }
+        rows.swap(G);
+      }
       std::vector<unsigned short> digits;
       std::vector<double> rscale;
       std::vector<float> rowmul;
-      int rc = ridg::mixed_build(3, h->nb, rows, h->thS, h->opt.slices, h->box, digits, rscale,
+      int rc = ridg::mixed_build(3, h->nb, rows, nout, h->opt.slices, h->box, digits, rscale,
                                  rowmul, op, digits_f16(h));
       if (rc != RIDG_OK) return set_err(h, rc, "3D mixed operator build failed");
       if (!op.b_slices) {
@@ -197,7 +230,8 @@ int rebuild_linear(ridg_t* h) {
     }
     if (!h->ms.planes) {
       Grid g = grid_of(h);
-      h->Y = (double*)dev_alloc(h, (size_t)h->ncell * h->thS * sizeof(double));  // float2 pairs
+      // float2 pairs: the step's outputs, or a block of ridg_predict's
+      h->Y = (double*)dev_alloc(h, (size_t)h->ncell * std::max(h->thS, h->mixed.nout) * sizeof(double));
       if (!h->Y) return set_err(h, RIDG_ENOMEM, "mixed-path allocation failed");
       const size_t pb = ridg::mixed3_plane_bytes(g, h->nb, h->opt.slices);
       h->ms.planes = dev_alloc(h, pb);
@@ -390,6 +424,7 @@ int enqueue_correct_after_mean(ridg_t* h) {
     // double-float correction from the time means, with the new state's digit planes
     RIDG_CUDA(h, ridg::launch_mixed3_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
                                              h->mixed.gmax, cp, h->ms, h->tune_corr3_block,
+                                             h->mixed3_fused,
                                              h->stream));
   } else if (is_mixed_linear(h)) {
     RIDG_CUDA(h, ridg::launch_mixed_correct(grid_of(h), h->nb, h->opt.slices, h->Q, h->Y,
@@ -975,7 +1010,7 @@ int ridg_autotune(ridg_t* h, const char* cache_path) {
       std::vector<int> caps;
       int last_na = -1;
       for (int cap : {3, 4, 5, 6, 8}) {
-        const int na = ridg::mixed3_gemm_slots(h->nb, h->opt.slices, h->box, cap);
+        const int na = ridg::mixed3_gemm_slots(h->nb, h->opt.slices, h->mixed.npad, h->box, cap);
         if (na < 2 || na == last_na) continue;
         last_na = na;
         caps.push_back(cap);

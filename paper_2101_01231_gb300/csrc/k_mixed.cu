@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(128) mixed_correct_kernel(
 // host side
 // ------------------------------------------------------------------------------------------
 bool mixed_supported(int dim, int nb, int nout) {
-  if (dim == 3) return nb >= 2 && nb <= 3 && nout <= 32;
+  if (dim == 3) return nb >= 2 && nb <= 3 && nout <= 64;
   return dim == 2 && nb >= 2 && nb <= 4 && nout <= 64;
 }
 
@@ -603,7 +603,8 @@ int mixed_build(int dim, int nb, const std::vector<double>& G, int nout, int sli
   const int thS = dim == 3 ? nb * nb * nb : nb * nb, K = nreg * thS;
   if ((int)G.size() < nout * K) return RIDG_EINVAL;
   const int NOUTP = nout_pad_of(nout);
-  if (slices * NOUTP > 512) return RIDG_EINVAL;
+  // (3D: two TMEM stages of slices x NOUTP columns, and an MMA N of at most 256)
+  if (slices * NOUTP > (dim == 3 ? 256 : 512)) return RIDG_EINVAL;
   const GemmLayout L = gemm_layout(slices, thS, NOUTP, ncx, nreg);
   const int tpad = L.P * 8;
   // digits in the shared-memory layout [region][k-chunk][row = c' * NOUTP + c][8]

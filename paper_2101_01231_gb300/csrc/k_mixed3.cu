@@ -36,21 +36,21 @@
 namespace ridg {
 namespace {
 
-constexpr int kNAmax = 8;   // A slots (at most)
-constexpr int kNOUTP = 32;  // padded outputs (theta_S <= 27)
+constexpr int kNAmax = 8;  // A slots (at most)
 
 struct Gemm3Layout {
   int P, brows, na, nst;
   uint32_t copy_bytes, a_bytes, b_bytes, b_off, bar_off, bytes;
 };
 
-// ncx, ncy, ncz = offsets of the upwind box per dimension (x-shifted copies per A slot,
-// operator blocks per B stage, B stages = ncy ncz); the A ring takes the room that is left
-__host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int ncx, int ncy, int ncz,
-                                                   int na_cap = kNAmax) {
+// nop = padded output rows (32 or 64); ncx, ncy, ncz = offsets of the upwind box per
+// dimension (x-shifted copies per A slot, operator blocks per B stage, B stages = ncy ncz);
+// the A ring takes the room that is left
+__host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int nop, int ncx, int ncy,
+                                                   int ncz, int na_cap = kNAmax) {
   Gemm3Layout l;
   l.P = ((thS + 15) / 16) * 2;
-  l.brows = S * kNOUTP;
+  l.brows = S * nop;
   l.copy_bytes = (uint32_t)l.P * kCopy * 16;
   l.a_bytes = ((uint32_t)ncx * l.copy_bytes + 1023u) & ~1023u;
   l.b_bytes = (uint32_t)ncx * l.P * l.brows * 16;
@@ -70,7 +70,8 @@ __host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int ncx, int
 template <int NB, int NCXC>
 __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
     const __grid_constant__ CUtensorMap dmap, const unsigned char* __restrict__ Bg,
-    const float* __restrict__ rowmul, int S, int nout, float2* __restrict__ Y, int* __restrict__ exps,
+    const float* __restrict__ rowmul, int S, int nout, int nop, float2* __restrict__ Y,
+    int* __restrict__ exps,
     unsigned long long* __restrict__ maxbits, int nx, int ny, int nz, RegionBox box,
     int na_cap, int step, int* status) {
   constexpr int THS = NB * NB * NB;
@@ -81,13 +82,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
   // the upwind box: offsets lo + 0 .. cnt - 1 per dimension (cnt 1 or 2, at most 3 B stages)
   const int ox0 = box.lo[0], oy0 = box.lo[1], oz0 = box.lo[2];
   const int ncx = NCXC ? NCXC : box.cnt[0], ncy = box.cnt[1], ncz = box.cnt[2];
-  const Gemm3Layout L = gemm3_layout(S, THS, ncx, ncy, ncz, na_cap);
+  const Gemm3Layout L = gemm3_layout(S, THS, nop, ncx, ncy, ncz, na_cap);
   const int NA = L.na;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
   const int ntiles = ntx * nty * nz;
   const int mytiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int tcols = S * kNOUTP;  // TMEM columns per stage (two stages)
+  const int tcols = S * nop;  // TMEM columns per stage (two stages; S nop <= 256)
   const uint32_t bar = smem_u32(smem + L.bar_off);
   const uint32_t afull0 = bar, afree0 = bar + 8u * kNAmax, bfull = bar + 16u * kNAmax,
                  tdone0 = bfull + 8u, tempty0 = tdone0 + 16u;
@@ -185,8 +186,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // A: LBO = plane stride inside a copy, SBO = one halo row of 8 cells (128 B)
             const uint64_t adesc0 = smem_desc(smem_u32(smem + sl * L.a_bytes), kCopy * 16, 128);
-            const uint32_t idesc = idesc_digits(128, (S - a) * kNOUTP, f16);
-            const uint32_t dcol = tst + (uint32_t)(a * kNOUTP);
+            const uint32_t idesc = idesc_digits(128, (S - a) * nop, f16);
+            const uint32_t dcol = tst + (uint32_t)(a * nop);
             for (int jy = 0; jy < ncy; ++jy) {
               const uint64_t bdesc0 =
                   smem_desc(smem_u32(smem + L.b_off + (jz * ncy + jy) * L.b_bytes), brows * 16, 128);
@@ -239,12 +240,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
       const long long e = ((long long)z0 * ny + gy) * nx + gx;
       const uint32_t tbase = lane_addr + (uint32_t)(ts * tcols);
 #pragma unroll 1
-      for (int cb = part * (kNOUTP / 2); cb < (part + 1) * (kNOUTP / 2); cb += 8) {
+      for (int cb = part * (nop / 2); cb < (part + 1) * (nop / 2); cb += 8) {
         if (cb >= nout) break;
         uint32_t raw[7][8];
 #pragma unroll
         for (int t = 0; t < 7; ++t)
-          if (t < S) tmem_ld8_nowait(tbase + (uint32_t)(t * kNOUTP + cb), raw[t]);
+          if (t < S) tmem_ld8_nowait(tbase + (uint32_t)(t * nop + cb), raw[t]);
         tmem_wait_ld();
         float hi[8], lo[8];
 #pragma unroll
@@ -526,6 +527,156 @@ __global__ void __launch_bounds__(BT) mixed3_correct_kernel(
   }
 }
 
+// The update from the fused step operator's outputs, one thread per cell.  The prediction
+// launch wrote, per cell, the volume term V_s = sum_d nu_d (D along d) W-bar (rows 0 ..
+// theta_S - 1) and, per direction d and line t of the NB^2 lines of modes along d, the
+// cell's upwind trace nu_d tr(W-bar) on its downstream d-face (rows theta_S + d NB^2 + t) --
+// the face value of that face, read by both of its cells (the same bits on both sides:
+// exact conservation).  dQ_s = V_s + sum_d phi_a(+1) (s_a F(i - 1/2) - F(i + 1/2)), a the
+// mode's index along d, s_a = (-1)^a, F of a face = the trace of its upwind cell, in
+// double-float.  Then the block updates its cells' state rows together (Q += dQ in FP64,
+// read and written coalesced), and each thread writes its cell's digit rows (and ghost
+// copies) and the running maximum, as in the kernel above.
+template <int NB, int S, int BT>
+__global__ void __launch_bounds__(BT) mixed3_fcorrect_kernel(
+    double* __restrict__ Q, const float2* __restrict__ Y, int nx, int ny, int nz, CorrParams cp,
+    int gmax, int* __restrict__ exps, unsigned long long* __restrict__ maxbits,
+    uint4* __restrict__ planes, int* status) {
+  constexpr int THS = NB * NB * NB, NT = NB * NB;
+  constexpr int P = ((THS + 15) / 16) * 2;
+  constexpr int PITCH = THS | 1;  // odd row pitch (8-byte words): conflict-free rows
+  __shared__ unsigned long long shmax[8];
+  // row c of the block's cell c: its dQ (double-float pairs) while the face terms are
+  // summed, then its new state (FP64) in the same 8-byte words
+  extern __shared__ float2 acc_sh[];
+  float2* acc = acc_sh + threadIdx.x * PITCH;
+  const long long ncell = (long long)nx * ny * nz;
+  const long long e0 = (long long)blockIdx.x * BT;
+  const int nblk = (int)min((long long)BT, ncell - e0);
+  const long long e = e0 + threadIdx.x;
+  const int ys = exps[1];
+  const int snext = exponent_above(maxbits[0]) + 1;
+  unsigned long long mymax = 0;
+  bool fits = true;
+  const unsigned ue = (unsigned)e, ur = ue / (unsigned)nx;
+  const int ix = (int)(ue - ur * (unsigned)nx), iy = (int)(ur % (unsigned)ny), iz = (int)(ur / (unsigned)ny);
+  if (e < ncell) {
+    // the volume term (row 0, the cell mean's, is zero: the mean has no volume term)
+#pragma unroll
+    for (int j = 0; j < THS; ++j) acc[j] = Y[(unsigned)j * (unsigned)ncell + e];
+    const float2* U = Y + (long long)THS * ncell;
+#pragma unroll 1
+    for (int dd = 0; dd < 3; ++dd) {
+      const double nu = cp.nu[dd];
+      if (nu == 0.0) continue;  // no flux along d: no volume or face term
+      const bool pos = nu > 0.0;
+      // the upstream neighbour along d (periodic): i - 1 for nu > 0, i + 1 for nu < 0
+      long long up;
+      if (dd == 0) up = pos ? (ix == 0 ? e + (nx - 1) : e - 1) : (ix == nx - 1 ? e - (nx - 1) : e + 1);
+      else if (dd == 1)
+        up = pos ? (iy == 0 ? e + (long long)(ny - 1) * nx : e - nx)
+                 : (iy == ny - 1 ? e - (long long)(ny - 1) * nx : e + nx);
+      else
+        up = pos ? (iz == 0 ? e + (long long)(nz - 1) * nx * ny : e - (long long)nx * ny)
+                 : (iz == nz - 1 ? e - (long long)(nz - 1) * nx * ny : e + (long long)nx * ny);
+      const int st = dd == 0 ? 1 : (dd == 1 ? NB : NB * NB);
+      const float2* Uo = U + (long long)dd * NT * ncell + e;   // this cell's traces
+      const float2* Uu = U + (long long)dd * NT * ncell + up;  // the upstream neighbour's
+      // the direction's 2 NB^2 traces, all loads in flight at once
+      float2 to[NT], tu[NT];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        to[t] = Uo[(unsigned)t * (unsigned)ncell];
+        tu[t] = Uu[(unsigned)t * (unsigned)ncell];
+      }
+      // line t holds the modes base + a st; base walked as lo + hi (lo < st, hi in steps of
+      // st NB), no divisions
+      int lo = 0, hi = 0;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const int base = hi + lo;
+        if (++lo == st) {
+          lo = 0;
+          hi += st * NB;
+        }
+        // F(i - 1/2) (the upstream cell's trace for nu > 0, this cell's for nu < 0) and
+        // F(i + 1/2); even modes take dpos = F- - F+, odd ones dneg = -(F- + F+)
+        const DFU fo{to[t].x, to[t].y}, fu{tu[t].x, tu[t].y};
+        const DFU fm = pos ? fu : fo, fp = pos ? fo : fu;
+        DFU dpos = fm, dneg = DFU{-fm.s, -fm.e};
+        dfu_acc(dpos, DFU{-fp.s, -fp.e});
+        dfu_acc(dneg, DFU{-fp.s, -fp.e});
+#pragma unroll
+        for (int a = 0; a < NB; ++a) {
+          const float2 c = acc[base + a * st];
+          DFU v{c.x, c.y};
+          const DFU df = (a & 1) ? dneg : dpos;
+          // phi_0(+1) = 1 exactly
+          dfu_acc(v, a == 0 ? df : dfu_prod(cp.eph[a], cp.epl[a], df.s, df.e));
+          acc[base + a * st] = make_float2(v.s, v.e);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // Q += dQ over the block's rows, element i = (cell i / THS, mode i % THS): coalesced
+  const int kfin = ys + gmax - 16;
+  double* sq = (double*)acc_sh;
+  for (int i = threadIdx.x; i < nblk * THS; i += BT) {
+    const int c = i / THS, k = c * PITCH + (i - c * THS);
+    const float2 d = acc_sh[k];
+    double v = Q[e0 * THS + i];
+    v = v + f2d_scale(d.x, kfin);
+    v = v + f2d_scale(d.y, kfin);
+    Q[e0 * THS + i] = v;
+    sq[k] = v;
+    const unsigned long long ab = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+    mymax = ab > mymax ? ab : mymax;
+  }
+  __syncthreads();
+  if (e < ncell) {
+    const double* q = sq + threadIdx.x * PITCH;
+    const long long pnx = nx + 2, pny = ny + 2;
+    const long long plane = pnx * pny * (nz + 2);
+    const long long own = ((long long)(iz + 1) * pny + (iy + 1)) * pnx + (ix + 1);
+    // a boundary cell also writes its periodic ghost copies
+    const bool ghost = ix == 0 || ix == nx - 1 || iy == 0 || iy == ny - 1 || iz == 0 || iz == nz - 1;
+#pragma unroll 1
+    for (int pg = 0; pg < P; ++pg) {
+      double qn[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) qn[j] = pg * 8 + j < THS ? q[pg * 8 + j] : 0.0;
+      uint4 rows[S];
+      fits &= make_digit_rows<S>(qn, snext, rows, exps[2] != 0);
+#pragma unroll
+      for (int a = 0; a < S; ++a) planes[(long long)(a * P + pg) * plane + own] = rows[a];
+      if (ghost) {
+        int px[2] = {ix + 1, -1}, py[2] = {iy + 1, -1}, pz[2] = {iz + 1, -1};
+        if (ix == 0) px[1] = nx + 1;
+        if (ix == nx - 1) px[1] = 0;
+        if (iy == 0) py[1] = ny + 1;
+        if (iy == ny - 1) py[1] = 0;
+        if (iz == 0) pz[1] = nz + 1;
+        if (iz == nz - 1) pz[1] = 0;
+#pragma unroll 1
+        for (int g = 1; g < 8; ++g) {
+          const int zz = pz[g >> 2], yy = py[(g >> 1) & 1], xx = px[g & 1];
+          if (zz < 0 || yy < 0 || xx < 0) continue;
+          const long long o = ((long long)zz * pny + yy) * pnx + xx;
+#pragma unroll
+          for (int a = 0; a < S; ++a) planes[(long long)(a * P + pg) * plane + o] = rows[a];
+        }
+      }
+    }
+  }
+  if (!fits) atomicOr(status, kStatusRange);
+  const unsigned long long bm = block_max_bits(mymax, shmax);
+  if (threadIdx.x == 0) {
+    atomicMax(maxbits + 1, bm);
+    if (blockIdx.x == 0) exps[0] = snext;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // digit planes of the 3D state: plane (a * P + p), padded (z + 1, y + 1, x + 1), one thread
 // per (cell, 8-mode group); the cell's periodic ghost copies are written too
@@ -609,7 +760,17 @@ cudaError_t launch_mixed3_to_w(const Grid& g, int nout, int c0, int wstride, con
 
 bool mixed3_supported(int nb, int slices) {
   if (nb < 2 || nb > 3 || slices < 2 || slices > 6) return false;
-  const Gemm3Layout l = gemm3_layout(slices, nb * nb * nb, 2, 2, 2);  // widest upwind box
+  const Gemm3Layout l = gemm3_layout(slices, nb * nb * nb, 32, 2, 2, 2);  // widest upwind box
+  return l.na >= 2 && l.bytes <= kSmemLimit;
+}
+
+int mixed3_fused_nout(int nb) { return nb * nb * nb + 3 * nb * nb; }
+
+bool mixed3_fused_fits(int nb, int slices) {
+  if (!mixed3_supported(nb, slices)) return false;
+  const int nout = mixed3_fused_nout(nb), nop = nout <= 32 ? 32 : 64;
+  if (nout > 64 || slices * nop > 256) return false;  // two TMEM stages, MMA N <= 256
+  const Gemm3Layout l = gemm3_layout(slices, nb * nb * nb, nop, 2, 2, 2);
   return l.na >= 2 && l.bytes <= kSmemLimit;
 }
 
@@ -646,7 +807,9 @@ int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_o
 template <int NB>
 static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& ms, void* Y,
                                   int slots, cudaStream_t s, bool step) {
-  const Gemm3Layout L = gemm3_layout(op.slices, NB * NB * NB, g.box.cnt[0], g.box.cnt[1],
+  if (op.npad != 32 && op.npad != 64) return cudaErrorInvalidValue;
+  if (op.slices * op.npad > 256 || op.nout > op.npad) return cudaErrorInvalidValue;
+  const Gemm3Layout L = gemm3_layout(op.slices, NB * NB * NB, op.npad, g.box.cnt[0], g.box.cnt[1],
                                      g.box.cnt[2], slots);
   if (L.na < 2 || L.bytes > kSmemLimit) return cudaErrorInvalidValue;
   // one CTA per SM: each allocates all 512 TMEM columns, so a second CTA on the SM would
@@ -662,13 +825,14 @@ static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& 
   const int grid = std::min(ntiles, sms);
   kern<<<grid, kGemmThreads, smem, s>>>(*(const CUtensorMap*)ms.map,
                                         (const unsigned char*)op.b_slices, op.row_mul, op.slices,
-                                        op.nout, (float2*)Y, ms.exps, ms.maxbits, g.n[0], g.n[1],
+                                        op.nout, op.npad, (float2*)Y, ms.exps, ms.maxbits, g.n[0], g.n[1],
                                         g.n[2], g.box, slots, step ? 1 : 0, ms.status);
   return cudaGetLastError();
 }
 
-int mixed3_gemm_slots(int nb, int slices, const RegionBox& box, int cap) {
-  const Gemm3Layout L = gemm3_layout(slices, nb * nb * nb, box.cnt[0], box.cnt[1], box.cnt[2], cap);
+int mixed3_gemm_slots(int nb, int slices, int npad, const RegionBox& box, int cap) {
+  const Gemm3Layout L =
+      gemm3_layout(slices, nb * nb * nb, npad, box.cnt[0], box.cnt[1], box.cnt[2], cap);
   return L.na;
 }
 
@@ -685,16 +849,21 @@ cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedSt
 
 template <int NB, int S>
 static cudaError_t launch_correct3_t(const Grid& g, double* Q, const void* Y, int gmax,
-                                     const CorrParams& cp, MixedState& ms, int block,
+                                     const CorrParams& cp, MixedState& ms, int block, bool fused,
                                      cudaStream_t s) {
-  // the kernel indexes the time means with 32-bit offsets (mode x cells)
-  if ((long long)g.ncell * NB * NB * NB >= (1LL << 32)) return cudaErrorInvalidValue;
+  // the kernels index the outputs with 32-bit offsets (row x cells)
+  if ((long long)g.ncell * mixed3_fused_nout(NB) >= (1LL << 32)) return cudaErrorInvalidValue;
   if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
   const unsigned blocks = (unsigned)((g.ncell + block - 1) / block);
-  const size_t smem = (size_t)NB * NB * NB * block * sizeof(float2);
-  auto kern = block == 64    ? mixed3_correct_kernel<NB, S, 64>
-              : block == 128 ? mixed3_correct_kernel<NB, S, 128>
-                             : mixed3_correct_kernel<NB, S, 256>;
+  // (the fused form keeps its rows at an odd pitch)
+  constexpr int THS = NB * NB * NB;
+  const size_t smem = (size_t)block * (fused ? (THS | 1) : THS) * sizeof(float2);
+  auto kern = fused ? (block == 64    ? mixed3_fcorrect_kernel<NB, S, 64>
+                       : block == 128 ? mixed3_fcorrect_kernel<NB, S, 128>
+                                      : mixed3_fcorrect_kernel<NB, S, 256>)
+                    : (block == 64    ? mixed3_correct_kernel<NB, S, 64>
+                       : block == 128 ? mixed3_correct_kernel<NB, S, 128>
+                                      : mixed3_correct_kernel<NB, S, 256>);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -706,11 +875,11 @@ static cudaError_t launch_correct3_t(const Grid& g, double* Q, const void* Y, in
 
 cudaError_t launch_mixed3_correct(const Grid& g, int nb, int slices, double* Q, const void* Y,
                                   int gmax, const CorrParams& cp, MixedState& ms, int block,
-                                  cudaStream_t s) {
+                                  bool fused, cudaStream_t s) {
   if (g.dim != 3) return cudaErrorInvalidValue;
   switch (nb * 16 + slices) {
 #define RIDG_C3(NBV, SV) \
-  case NBV * 16 + SV: return launch_correct3_t<NBV, SV>(g, Q, Y, gmax, cp, ms, block, s);
+  case NBV * 16 + SV: return launch_correct3_t<NBV, SV>(g, Q, Y, gmax, cp, ms, block, fused, s);
     RIDG_C3(2, 2) RIDG_C3(2, 3) RIDG_C3(2, 4) RIDG_C3(2, 5) RIDG_C3(2, 6)
     RIDG_C3(3, 2) RIDG_C3(3, 3) RIDG_C3(3, 4) RIDG_C3(3, 5) RIDG_C3(3, 6)
 #undef RIDG_C3

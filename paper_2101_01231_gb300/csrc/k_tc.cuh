@@ -70,6 +70,28 @@ __device__ __forceinline__ long long to_fixed(double x, int s, int L) {
   return (u >> 63) ? -F : F;
 }
 
+// The same for L <= 24 fraction bits, in 32-bit arithmetic: F = round-half-up(|x| 2^(L - s))
+// with x's sign, |F| < 2^L (returns false, F = 0, where it is not).  With the 53-bit
+// significand m and sh = 1075 - e - L + s, F = (t + 1) >> 1 for t = floor(m / 2^(sh - 1)) --
+// the same value as (m + 2^(sh - 1)) >> sh; t is below 2^32 only for sh - 1 >= 21, and
+// F < 2^L needs more than that, so smaller shifts are out of range.
+template <int L>
+__device__ __forceinline__ bool to_fixed32(double x, int s, int& F) {
+  static_assert(L <= 24, "32-bit fixed point");
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const int ex = (int)((hi >> 20) & 0x7FFu);
+  F = 0;
+  if (ex == 0) return true;  // zero / subnormal: far below the state's scale
+  const int r = 1074 - ex - L + s;  // sh - 1
+  if (r < 21) return false;         // |x| 2^(L - s) >= 2^31 (or not finite)
+  const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;  // the significand's top 21 bits
+  const uint32_t t = r < 32 ? __funnelshift_r(lo, mh, r) : (r < 53 ? mh >> (r - 32) : 0u);
+  const uint32_t f = (t + 1u) >> 1;
+  if (f >= (1u << L)) return false;
+  F = (hi >> 31) ? -(int)f : (int)f;
+  return true;
+}
+
 // The S balanced base-256 digits of one coefficient (fixed point with 8 S fraction bits
 // relative to 2^s), most significant first, as BF16 (or, f16, FP16) bit patterns (exact
 // either way: |digit| <= 256).  Returns false if the value does not fit below 2^s.
@@ -77,9 +99,19 @@ template <int S>
 __device__ __forceinline__ bool value_digit_bits(double x, int s, uint32_t (&bits)[S],
                                                  bool f16 = false) {
   constexpr int L = kBits * S;
-  const long long F = to_fixed(x, s, L);
-  const bool fits = (F < (1LL << L)) && (F > -(1LL << L));
-  const uint32_t lo32 = (uint32_t)F, hi32 = (uint32_t)((unsigned long long)F >> 32);
+  uint32_t lo32, hi32;
+  bool fits;
+  if constexpr (L <= 24) {
+    int F;
+    fits = to_fixed32<L>(x, s, F);
+    lo32 = (uint32_t)F;
+    hi32 = F < 0 ? 0xFFFFFFFFu : 0u;
+  } else {
+    const long long F = to_fixed(x, s, L);
+    fits = (F < (1LL << L)) && (F > -(1LL << L));
+    lo32 = (uint32_t)F;
+    hi32 = (uint32_t)((unsigned long long)F >> 32);
+  }
   const int neg = (int)(hi32 >> 31);
   int carry = 0;
   int d[S];

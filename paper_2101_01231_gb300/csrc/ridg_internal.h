@@ -94,12 +94,18 @@ cudaError_t launch_mixed_correct(const Grid& g, int nb, int slices, double* Q, c
                                  int gmax, const CorrParams& cp, int sgnx, int sgny,
                                  MixedState& ms, cudaStream_t s);
 
-// ---- mixed BF16 tensor-core prediction in 3D (k_mixed3.cu): the time mean only ----
+// ---- mixed BF16 tensor-core prediction in 3D (k_mixed3.cu) ----
 bool mixed3_supported(int nb, int slices);
+// The fused step operator C P-bar of the 3D step (rows: the volume term, theta_S, then the
+// upwind face traces, NB^2 lines per direction): its row count, and whether its digits fit
+// the GEMM (two TMEM stages of slices x padded rows <= 256 columns)
+int mixed3_fused_nout(int nb);
+bool mixed3_fused_fits(int nb, int slices);
 size_t mixed3_plane_bytes(const Grid& g, int nb, int slices);
 int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_out);
-// Y[c * cells + e] = (P-bar X_e)[c] as double-float pairs from the digit planes in ms (value
-// (hi + lo) 2^(exps[1] + gmax - 16))
+// Y[c * cells + e] = (G X_e)[c] as double-float pairs from the digit planes in ms (value
+// (hi + lo) 2^(exps[1] + gmax - 16)); G = op's rows (P-bar, the fused step operator, or a
+// block of P's rows for ridg_predict), at most 64
 // (slots: depth of the plane-operand ring, 0 = as many as fit; the autotuner's choice.
 // step: the launch is the step's prediction -- it rotates the running maximum and records
 // the outputs' exponent in exps[1]; ridg_predict's launches leave both alone, their
@@ -111,13 +117,14 @@ cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedSt
 cudaError_t launch_mixed3_to_w(const Grid& g, int nout, int c0, int wstride, const void* Y,
                                int gmax, const MixedState& ms, double* W, cudaStream_t s);
 // the ring depth a slot cap gives for this configuration (0: it does not fit)
-int mixed3_gemm_slots(int nb, int slices, const RegionBox& box, int cap);
-// the correction from those outputs (face values from each cell's own and upstream
-// neighbours' time means), plus the new state's digit planes and maximum
+int mixed3_gemm_slots(int nb, int slices, int npad, const RegionBox& box, int cap);
+// the correction from those outputs, plus the new state's digit planes and maximum: fused =
+// the outputs of the fused step operator (volume term and face traces), else the time means
+// (face values from each cell's own and upstream neighbours' time means)
 // (block: 64, 128 or 256 threads, the autotuner's choice)
 cudaError_t launch_mixed3_correct(const Grid& g, int nb, int slices, double* Q, const void* Y,
                                   int gmax, const CorrParams& cp, MixedState& ms, int block,
-                                  cudaStream_t s);
+                                  bool fused, cudaStream_t s);
 // max |Q| and the 3D digit planes of Q
 cudaError_t launch_mixed3_refresh(const Grid& g, int nb, int slices, const double* Q,
                                   MixedState& ms, cudaStream_t s);
@@ -286,6 +293,7 @@ struct ridg_handle {
   ridg::MixedOp mixed;       // fused step operator [V; u_x; u_y] P-bar (2D)
   ridg::MixedOp mixed_pred;  // full prediction operator P
   ridg::MixedOp mixed3_pred[4];  // 3D: the theta_S rows of P of each time mode (nb <= 4)
+  bool mixed3_fused = false;     // 3D: mixed is the fused step operator (else P-bar)
   double* Y = nullptr;       // fused outputs of the mixed step (cells * nout pairs)
   ridg::MixedState ms;       // digit planes and exponent bookkeeping of the mixed path
   int ny_out = 0;
