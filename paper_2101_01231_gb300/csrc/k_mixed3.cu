@@ -37,6 +37,10 @@ namespace ridg {
 namespace {
 
 constexpr int kNAmax = 8;  // A slots (at most)
+// warp 0: TMA producer, warp 1: MMA issuer, warps 2..17: epilogue (four per TMEM lane
+// quadrant, each a quarter of the output columns)
+constexpr int kEpiWarps = 16;
+constexpr int kGemm3Threads = 32 * (2 + kEpiWarps);
 
 struct Gemm3Layout {
   int P, brows, na, nst;
@@ -68,7 +72,7 @@ __host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int nop, int
 
 // NCXC = 2: two x-offsets, the x loop unrolled; NCXC = 0: runtime count.
 template <int NB, int NCXC>
-__global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
+__global__ void __launch_bounds__(kGemm3Threads, 1) mixed3_gemm_kernel(
     const __grid_constant__ CUtensorMap dmap, const unsigned char* __restrict__ Bg,
     const float* __restrict__ rowmul, int S, int nout, int nop, float2* __restrict__ Y,
     int* __restrict__ exps,
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
     mbar_init(bfull, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(tdone0 + 8u * i, 1);
-      mbar_init(tempty0 + 8u * i, 256);
+      mbar_init(tempty0 + 8u * i, 32 * kEpiWarps);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (blockIdx.x == 0 && step) {
@@ -220,9 +224,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: warps 2..9, two per TMEM lane quadrant ----------------
-    const int quad = warp & 3;
+    // ---------------- epilogue: warps 2..17, four per TMEM lane quadrant ----------------
+    const int quad = warp & 3;  // (a warp reads the TMEM lanes of quadrant warp % 4)
     const int part = (warp - 2) >> 2;
+    const int ncols = nop / 4;
     const int cell = quad * 32 + lane;
     const int ix = cell % kTX, iy = cell / kTX;
     const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
@@ -240,11 +245,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
       const long long e = ((long long)z0 * ny + gy) * nx + gx;
       const uint32_t tbase = lane_addr + (uint32_t)(ts * tcols);
 #pragma unroll 1
-      for (int cb = part * (nop / 2); cb < (part + 1) * (nop / 2); cb += 8) {
+      for (int cb = part * ncols; cb < (part + 1) * ncols; cb += 8) {
         if (cb >= nout) break;
-        uint32_t raw[7][8];
+        uint32_t raw[6][8];
 #pragma unroll
-        for (int t = 0; t < 7; ++t)
+        for (int t = 0; t < 6; ++t)
           if (t < S) tmem_ld8_nowait(tbase + (uint32_t)(t * nop + cb), raw[t]);
         tmem_wait_ld();
         float hi[8], lo[8];
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mixed3_gemm_kernel(
         }
         float w = 1.f;
 #pragma unroll
-        for (int t = 1; t < 7; ++t) {
+        for (int t = 1; t < 6; ++t) {
           if (t < S) {
             w *= 1.f / 256.f;
 #pragma unroll
@@ -622,16 +627,32 @@ __global__ void __launch_bounds__(BT) mixed3_fcorrect_kernel(
   // Q += dQ over the block's rows, element i = (cell i / THS, mode i % THS): coalesced
   const int kfin = ys + gmax - 16;
   double* sq = (double*)acc_sh;
-  for (int i = threadIdx.x; i < nblk * THS; i += BT) {
-    const int c = i / THS, k = c * PITCH + (i - c * THS);
-    const float2 d = acc_sh[k];
-    double v = Q[e0 * THS + i];
-    v = v + f2d_scale(d.x, kfin);
-    v = v + f2d_scale(d.y, kfin);
-    Q[e0 * THS + i] = v;
-    sq[k] = v;
-    const unsigned long long ab = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
-    mymax = ab > mymax ? ab : mymax;
+  // (eight elements per thread at a time: their loads are in flight together)
+  const int nel = nblk * THS;
+  double* const Qb = Q + e0 * THS;
+#pragma unroll 1
+  for (int i0 = threadIdx.x; i0 < nel; i0 += 8 * BT) {
+    double qv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * BT;
+      qv[u] = i < nel ? Qb[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * BT;
+      if (i < nel) {
+        const int c = i / THS, k = c * PITCH + (i - c * THS);
+        const float2 d = acc_sh[k];
+        double v = qv[u];
+        v = v + f2d_scale(d.x, kfin);
+        v = v + f2d_scale(d.y, kfin);
+        Qb[i] = v;
+        sq[k] = v;
+        const unsigned long long ab = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+        mymax = ab > mymax ? ab : mymax;
+      }
+    }
   }
   __syncthreads();
   if (e < ncell) {
@@ -733,16 +754,28 @@ __global__ void __launch_bounds__(128) state_digits3_kernel(const double* __rest
 
 // ridg_predict's outputs: W[e * wstride + c0 + c] = (hi + lo) 2^(s + gmax - 16) in FP64, s the
 // planes' exponent (the launch that produced Y left the step's bookkeeping alone)
-__global__ void mixed3_to_w_kernel(const float2* __restrict__ Y, long long ncell, int nout, int c0,
-                                   int wstride, const int* __restrict__ exps, int gmax,
-                                   double* __restrict__ W) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ncell * nout) return;
-  const int c = (int)(i / ncell);
-  const long long e = i - (long long)c * ncell;
+// (a tile of 32 cells x nout outputs through shared memory: Y read along the cells, W
+// written along each cell's row)
+__global__ void __launch_bounds__(256) mixed3_to_w_kernel(const float2* __restrict__ Y,
+                                                          long long ncell, int nout, int c0,
+                                                          int wstride, const int* __restrict__ exps,
+                                                          int gmax, double* __restrict__ W) {
+  constexpr int TPITCH = 33;  // odd: conflict-free reads along a cell's row
+  __shared__ double tile[64 * TPITCH];
+  const long long e0 = (long long)blockIdx.x * 32;
+  const int nc = (int)min(32LL, ncell - e0);
+  const int j = threadIdx.x & 31, r = threadIdx.x >> 5;
   const int k = exps[0] + gmax - 16;
-  const float2 y = Y[i];
-  W[e * wstride + c0 + c] = f2d_scale(y.x, k) + f2d_scale(y.y, k);
+  if (j < nc)
+    for (int c = r; c < nout; c += 8) {
+      const float2 y = Y[(long long)c * ncell + e0 + j];
+      tile[c * TPITCH + j] = f2d_scale(y.x, k) + f2d_scale(y.y, k);
+    }
+  __syncthreads();
+  for (int f = threadIdx.x; f < nc * nout; f += 256) {
+    const int jj = f / nout, c = f - jj * nout;
+    W[(e0 + jj) * wstride + c0 + c] = tile[c * TPITCH + jj];
+  }
 }
 
 }  // namespace
@@ -752,9 +785,10 @@ __global__ void mixed3_to_w_kernel(const float2* __restrict__ Y, long long ncell
 // ------------------------------------------------------------------------------------------
 cudaError_t launch_mixed3_to_w(const Grid& g, int nout, int c0, int wstride, const void* Y,
                                int gmax, const MixedState& ms, double* W, cudaStream_t s) {
-  const long long n = g.ncell * nout;
-  mixed3_to_w_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float2*)Y, g.ncell, nout, c0,
-                                                                 wstride, ms.exps, gmax, W);
+  if (nout < 1 || nout > 64) return cudaErrorInvalidValue;
+  mixed3_to_w_kernel<<<(unsigned)((g.ncell + 31) / 32), 256, 0, s>>>((const float2*)Y, g.ncell,
+                                                                    nout, c0, wstride, ms.exps,
+                                                                    gmax, W);
   return cudaGetLastError();
 }
 
@@ -823,7 +857,7 @@ static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int ntiles = ((g.n[0] + kTX - 1) / kTX) * ((g.n[1] + kTY - 1) / kTY) * g.n[2];
   const int grid = std::min(ntiles, sms);
-  kern<<<grid, kGemmThreads, smem, s>>>(*(const CUtensorMap*)ms.map,
+  kern<<<grid, kGemm3Threads, smem, s>>>(*(const CUtensorMap*)ms.map,
                                         (const unsigned char*)op.b_slices, op.row_mul, op.slices,
                                         op.nout, op.npad, (float2*)Y, ms.exps, ms.maxbits, g.n[0], g.n[1],
                                         g.n[2], g.box, slots, step ? 1 : 0, ms.status);

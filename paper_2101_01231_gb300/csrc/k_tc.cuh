@@ -99,32 +99,36 @@ template <int S>
 __device__ __forceinline__ bool value_digit_bits(double x, int s, uint32_t (&bits)[S],
                                                  bool f16 = false) {
   constexpr int L = kBits * S;
-  uint32_t lo32, hi32;
   bool fits;
+  int d[S];
   if constexpr (L <= 24) {
+    // 32-bit: with 128 added at every lower digit position, the lower digits are the bytes
+    // minus 128 and the top digit is the arithmetic shift (the same balanced digits as the
+    // carry loop below)
     int F;
     fits = to_fixed32<L>(x, s, F);
-    lo32 = (uint32_t)F;
-    hi32 = F < 0 ? 0xFFFFFFFFu : 0u;
+    constexpr int kOff = S == 3 ? 0x8080 : (S == 2 ? 0x80 : 0);
+    const int G = F + kOff;
+#pragma unroll
+    for (int a = S - 1; a > 0; --a) d[a] = ((G >> (8 * (S - 1 - a))) & 0xFF) - 128;
+    d[0] = G >> (8 * (S - 1));
   } else {
     const long long F = to_fixed(x, s, L);
     fits = (F < (1LL << L)) && (F > -(1LL << L));
-    lo32 = (uint32_t)F;
-    hi32 = (uint32_t)((unsigned long long)F >> 32);
-  }
-  const int neg = (int)(hi32 >> 31);
-  int carry = 0;
-  int d[S];
+    const uint32_t lo32 = (uint32_t)F, hi32 = (uint32_t)((unsigned long long)F >> 32);
+    const int neg = (int)(hi32 >> 31);
+    int carry = 0;
 #pragma unroll
-  for (int a = S - 1; a >= 0; --a) {
-    const int k = S - 1 - a;  // byte index of digit a
-    const uint32_t byte = (k < 4 ? (lo32 >> (8 * k)) : (hi32 >> (8 * (k - 4)))) & 0xFFu;
-    if (a > 0) {
-      const int t = (int)byte + carry;
-      carry = (t + 128) >> 8;
-      d[a] = t - (carry << 8);
-    } else {
-      d[0] = (int)byte - (neg << 8) + carry;
+    for (int a = S - 1; a >= 0; --a) {
+      const int k = S - 1 - a;  // byte index of digit a
+      const uint32_t byte = (k < 4 ? (lo32 >> (8 * k)) : (hi32 >> (8 * (k - 4)))) & 0xFFu;
+      if (a > 0) {
+        const int t = (int)byte + carry;
+        carry = (t + 128) >> 8;
+        d[a] = t - (carry << 8);
+      } else {
+        d[0] = (int)byte - (neg << 8) + carry;
+      }
     }
   }
 #pragma unroll
