@@ -894,13 +894,22 @@ def linear_arm(R, I, w, args, ws, flush, clocks=None, steps=None):
 
     # Algorithmic work per launch.  Prediction (time mean): 2 theta_S K flop per cell (K =
     # theta_S x the upwind region cells; the other region cells' operator columns are exactly
-    # zero) and its bytes: read Q, write W-bar (2 x 8 theta_S B per cell).  Correction: read
-    # W-bar (8 theta_S; double-float pairs in the mixed path), read and write Q (16 theta_S);
-    # the 2D mixed correction reads the fused outputs instead of W-bar (theta_S + 2 (M + 1)
-    # pairs).
+    # zero) and its bytes: read Q (8 theta_S B per cell), write its outputs -- W-bar (8
+    # theta_S), or in the mixed path the fused step operator's outputs as double-float pairs:
+    # the volume term and the upwind face traces, theta_S + 2 (M + 1) in 2D and theta_S +
+    # 3 (M + 1)^2 in 3D where the digits fit the GEMM (3D: slices x padded rows <= 256), else
+    # W-bar.  Correction: read those outputs, read and write Q (16 theta_S).
     flops_pred = 2.0 * thS * K * cells
-    bytes_pred = 2.0 * 8 * thS * cells
-    nfused = thS + 2 * (w["M"] + 1) if w["dim"] == 2 else thS
+    nb_ = w["M"] + 1
+    if prec_name == "fp64":
+        nfused = thS
+    elif w["dim"] == 2:
+        nfused = thS + 2 * nb_
+    else:
+        nf3 = thS + 3 * nb_ * nb_
+        nfused = nf3 if slices_used * (32 if nf3 <= 32 else 64) <= 256 else thS
+    npad = 32 if nfused <= 32 else 64
+    bytes_pred = (8.0 * thS + 8.0 * nfused) * cells
     bytes_corr = (8.0 * nfused + 16.0 * thS) * cells
     if prec_name == "fp64":
         # FP64 FMA pipe: 152 SMs x 2 FP64 FMA / clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
@@ -910,19 +919,25 @@ def linear_arm(R, I, w, args, ws, flush, clocks=None, steps=None):
                 "peak_source": "nominal FP64 rate (152 SMs x 4 flop/clk x 2.07 GHz)"}
     else:
         S_ = slices_used
-        executed = 2.0 * (S_ * (S_ + 1) // 2) * 32 * K * cells
+        # executed on the tensor pipe: digit pairs x padded outputs x padded K (each region
+        # cell's modes padded to a multiple of 16)
+        kpad = upwind_cells(w) * ((thS + 15) // 16) * 16
+        executed = 2.0 * (S_ * (S_ + 1) // 2) * npad * kpad * cells
         tag = "mixed3" if w["dim"] == 3 else "mixed"
         gemm = {"bound": "hbm", "kernel": f"{tag}_gemm (prediction)", "ms": ms_pred,
                 "achieved": bytes_pred / (ms_pred * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "traffic": _recorded_traffic(tag + "gemm", cells),
                 "peak_source": f"HBM copy, {src}",
-                "algorithmic_bytes_per_cell": 16.0 * thS,
+                "algorithmic_bytes_per_cell": bytes_pred / cells, "outputs_per_cell": nfused,
                 "tensor_executed_tflops": executed / (ms_pred * 1e-3) / 1e12,
                 "tensor_peak_tflops": bf16,
                 "algorithmic_tflops": flops_pred / (ms_pred * 1e-3) / 1e12}
-        corr = {"bound": "hbm", "kernel": f"{tag}_correct (correction)", "ms": ms_corr,
+        # (3D: mixed3_fcorrect reads the fused step operator's outputs, mixed3_correct the
+        # time means where those digits do not fit the GEMM)
+        ctag = tag + ("_fcorrect" if w["dim"] == 3 and nfused > thS else "_correct")
+        corr = {"bound": "hbm", "kernel": f"{ctag} (correction)", "ms": ms_corr,
                 "achieved": bytes_corr / (ms_corr * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                "traffic": _recorded_traffic(tag + "corr", cells),
+                "traffic": _recorded_traffic(ctag.replace("_correct", "corr").replace("_", ""), cells),
                 "peak_source": f"HBM copy, {src}",
                 "algorithmic_bytes_per_cell": bytes_corr / cells}
         for r in (gemm, corr):
