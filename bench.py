@@ -1006,10 +1006,16 @@ def time_predict(R, I, w, make, q0, slices, hbm, bf16, reps=10):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
     s.close()
-    # executed: per time mode (M + 1 launches) S (S + 1) / 2 digit pairs x 32 padded outputs x
-    # the upwind cells' 32 padded modes each, per cell
-    executed = 2.0 * (w["M"] + 1) * (slices * (slices + 1) // 2) * 32 * upwind_cells(w) * 32 * cells
-    return {"kernel": "mixed3_gemm x (M + 1) + conversion to FP64 (ridg_predict)", "ms": ms,
+    # executed: P's theta_T rows in blocks of 64 (32 when slices x 64 > 256), one GEMM launch
+    # each: S (S + 1) / 2 digit pairs x the block's padded rows (32 or 64) x the upwind cells'
+    # padded modes, per cell
+    R = 64 if slices * 64 <= 256 else 32
+    blocks = [min(R, thT - r0) for r0 in range(0, thT, R)]
+    npads = sum(32 if b <= 32 else 64 for b in blocks)
+    kpad = upwind_cells(w) * ((thS + 15) // 16) * 16
+    executed = 2.0 * (slices * (slices + 1) // 2) * npads * kpad * cells
+    return {"kernel": f"mixed3_gemm x {len(blocks)} row blocks and their FP64 rows (ridg_predict)",
+            "ms": ms,
             "tensor_executed_tflops": executed / (ms * 1e-3) / 1e12, "tensor_peak_tflops": bf16,
             "tensor_frac": executed / (ms * 1e-3) / 1e12 / bf16,
             "algorithmic_tflops": 2.0 * thT * K * cells / (ms * 1e-3) / 1e12,

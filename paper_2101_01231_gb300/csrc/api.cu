@@ -169,16 +169,20 @@ int rebuild_linear(ridg_t* h) {
     // 3D: the step's operator -- the fused step operator C P-bar where its digits fit (rows:
     // the volume term sum_d nu_d (D along d) W-bar, then the upwind face trace nu_d tr(W-bar)
     // of every line of modes along d), else the time-mean rows P-bar (first theta_S rows of
-    // P) --, and for ridg_predict every block of theta_S rows (time mode a), each its own
-    // digit operator
+    // P) --, and for ridg_predict P's theta_T rows in blocks of 64 (32 where slices x 64
+    // columns exceed the GEMM's 256), each its own digit operator
     const int nb = h->nb, thS = h->thS, K = h->K, NT = nb * nb;
     h->mixed3_fused = ridg::mixed3_fused_fits(nb, h->opt.slices);
-    for (int a = 0; a <= h->nb; ++a) {
+    h->mixed3_pred_rows = h->opt.slices * 64 <= 256 ? 64 : 32;
+    const int nchunks = (h->thT + h->mixed3_pred_rows - 1) / h->mixed3_pred_rows;
+    if (nchunks > 4) return set_err(h, RIDG_EINVAL, "3D prediction blocks");
+    for (int a = 0; a <= nchunks; ++a) {
       ridg::MixedOp& op = a == 0 ? h->mixed : h->mixed3_pred[a - 1];
-      const int r0 = a == 0 ? 0 : (a - 1) * h->thS;
+      const int r0 = a == 0 ? 0 : (a - 1) * h->mixed3_pred_rows;
+      const int nr = a == 0 ? thS : std::min(h->mixed3_pred_rows, h->thT - r0);
       std::vector<double> rows(h->P_host.begin() + (size_t)r0 * h->K,
-                               h->P_host.begin() + (size_t)(r0 + h->thS) * h->K);
-      int nout = thS;
+                               h->P_host.begin() + (size_t)(r0 + nr) * h->K);
+      int nout = nr;
       if (a == 0 && h->mixed3_fused) {
         nout = ridg::mixed3_fused_nout(nb);
         ridg::Tables1D t1 = ridg::tables1d(nb);
@@ -231,7 +235,9 @@ int rebuild_linear(ridg_t* h) {
     if (!h->ms.planes) {
       Grid g = grid_of(h);
       // float2 pairs: the step's outputs, or a block of ridg_predict's
-      h->Y = (double*)dev_alloc(h, (size_t)h->ncell * std::max(h->thS, h->mixed.nout) * sizeof(double));
+      int ny = std::max(h->thS, h->mixed.nout);
+      for (int c = 0; c < nchunks; ++c) ny = std::max(ny, h->mixed3_pred[c].nout);
+      h->Y = (double*)dev_alloc(h, (size_t)h->ncell * ny * sizeof(double));
       if (!h->Y) return set_err(h, RIDG_ENOMEM, "mixed-path allocation failed");
       const size_t pb = ridg::mixed3_plane_bytes(g, h->nb, h->opt.slices);
       h->ms.planes = dev_alloc(h, pb);
@@ -835,16 +841,26 @@ int ridg_predict(ridg_t* h, double* w_out, int on_device) {
     RIDG_CUDA(h, ridg::launch_mixed_gemm(g, h->nb, h->mixed_pred, h->ms, h->W, h->thT, 1, false,
                                          h->stream));
   } else if (is_mixed_linear(h) && h->dim == 3) {
-    // every time mode's theta_S rows of P on the tensor cores (without the step's exponent
-    // bookkeeping), each block converted from double-float into its columns of W (FP64)
+    // P's theta_T rows on the tensor cores in blocks (without the step's exponent
+    // bookkeeping).  A block of up to 32 rows is written into its columns of W (FP64) by the
+    // GEMM's epilogue; a wider one leaves double-float pairs in Y (coalesced) for a tiled
+    // conversion: 64 doubles per cell written row-wise by each epilogue thread cost more in
+    // partial-sector stores than the round trip (measured at 96^3 Q2, 3 slices: 0.73 ms for
+    // the whole prediction this way, 0.97 ms with every block direct; at 6 slices the 32-row
+    // blocks direct: 1.19 ms against 1.50 ms with a conversion pass each)
     int rc = ensure_digits(h);
     if (rc) return rc;
-    for (int a = 0; a < h->nb; ++a) {
-      const ridg::MixedOp& op = h->mixed3_pred[a];
-      RIDG_CUDA(h, ridg::launch_mixed3_gemm(g, h->nb, op, h->ms, h->Y, h->tune_gemm3_slots,
-                                            h->stream, false));
-      RIDG_CUDA(h, ridg::launch_mixed3_to_w(g, h->thS, a * h->thS, h->thT, h->Y, op.gmax, h->ms,
-                                            h->W, h->stream));
+    for (int r0 = 0, c = 0; r0 < h->thT; r0 += h->mixed3_pred_rows, ++c) {
+      const ridg::MixedOp& op = h->mixed3_pred[c];
+      if (op.nout <= 32) {
+        RIDG_CUDA(h, ridg::launch_mixed3_predict(g, h->nb, op, h->ms, h->W, h->thT, r0,
+                                                 h->tune_gemm3_slots, h->stream));
+      } else {
+        RIDG_CUDA(h, ridg::launch_mixed3_gemm(g, h->nb, op, h->ms, h->Y, h->tune_gemm3_slots,
+                                              h->stream, false));
+        RIDG_CUDA(h, ridg::launch_mixed3_to_w(g, op.nout, r0, h->thT, h->Y, op.gmax, h->ms,
+                                              h->W, h->stream));
+      }
     }
   } else {
     RIDG_CUDA(h, ridg::launch_predict_fp64(g, h->nb, h->Q, h->P, h->thT, h->W, h->thT, h->stream));

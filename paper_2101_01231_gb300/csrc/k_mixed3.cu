@@ -70,14 +70,26 @@ __host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int nop, int
   return l;
 }
 
+// float * 2^k as a double, by exponent arithmetic on the bits (exact; 0 stays 0)
+__device__ __forceinline__ double f2d_scale(float f, int k) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e8 = (b >> 23) & 0xFF;
+  if (e8 == 0) return 0.0;
+  const int e11 = (int)e8 - 127 + 1023 + k;
+  if (e11 <= 0) return 0.0;
+  const uint32_t hiw = (b & 0x80000000u) | ((uint32_t)e11 << 20) | ((b & 0x7FFFFFu) >> 3);
+  const uint32_t low = (b & 0x7u) << 29;
+  return __hiloint2double((int)hiw, (int)low);
+}
+
 // NCXC = 2: two x-offsets, the x loop unrolled; NCXC = 0: runtime count.
 template <int NB, int NCXC>
 __global__ void __launch_bounds__(kGemm3Threads, 1) mixed3_gemm_kernel(
     const __grid_constant__ CUtensorMap dmap, const unsigned char* __restrict__ Bg,
     const float* __restrict__ rowmul, int S, int nout, int nop, float2* __restrict__ Y,
-    int* __restrict__ exps,
+    double* __restrict__ W, int wstride, int wc0, int* __restrict__ exps,
     unsigned long long* __restrict__ maxbits, int nx, int ny, int nz, RegionBox box,
-    int na_cap, int step, int* status) {
+    int na_cap, int step, int wgmax, int* status) {
   constexpr int THS = NB * NB * NB;
   constexpr int P = ((THS + 15) / 16) * 2;
   constexpr int KSTEPS = P / 2;
@@ -274,12 +286,24 @@ __global__ void __launch_bounds__(kGemm3Threads, 1) mixed3_gemm_kernel(
         }
         if (gx < nx && gy < ny) {
           // (hi, lo) scaled to the common row exponent; value = (hi + lo) 2^(s + gmax - 16)
+          if (W) {
+            // (ridg_predict: FP64 straight into the cell's row of W, s = the planes' exponent)
+            const int kw = sexp + wgmax - 16;
+            double* wrow = W + e * wstride + wc0 + cb;
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (cb + c < nout) {
-              const float m = rowmul[cb + c];
-              Y[(long long)(cb + c) * ncell + e] = make_float2(hi[c] * m, lo[c] * m);
-            }
+            for (int c = 0; c < 8; ++c)
+              if (cb + c < nout) {
+                const float m = rowmul[cb + c];
+                wrow[c] = f2d_scale(hi[c] * m, kw) + f2d_scale(lo[c] * m, kw);
+              }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              if (cb + c < nout) {
+                const float m = rowmul[cb + c];
+                Y[(long long)(cb + c) * ncell + e] = make_float2(hi[c] * m, lo[c] * m);
+              }
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -302,18 +326,6 @@ __global__ void __launch_bounds__(kGemm3Threads, 1) mixed3_gemm_kernel(
 // state update is FP64.  The kernel then writes the new state's digit planes (exponent from
 // the previous maximum plus one bit of headroom, checked) and accumulates the new maximum.
 // ---------------------------------------------------------------------------------------
-// float * 2^k as a double, by exponent arithmetic on the bits (exact; 0 stays 0)
-__device__ __forceinline__ double f2d_scale(float f, int k) {
-  const uint32_t b = __float_as_uint(f);
-  const uint32_t e8 = (b >> 23) & 0xFF;
-  if (e8 == 0) return 0.0;
-  const int e11 = (int)e8 - 127 + 1023 + k;
-  if (e11 <= 0) return 0.0;
-  const uint32_t hiw = (b & 0x80000000u) | ((uint32_t)e11 << 20) | ((b & 0x7FFFFFu) >> 3);
-  const uint32_t low = (b & 0x7u) << 29;
-  return __hiloint2double((int)hiw, (int)low);
-}
-
 // Unnormalised double-float values (s + e, |e| a few ulp of s at most) for the accumulations
 // of the correction: a product costs 4 instructions and an accumulation 8, where the
 // normalised pair arithmetic above costs 7 and 11; one normalisation at the end.
@@ -840,7 +852,8 @@ int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_o
 
 template <int NB>
 static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& ms, void* Y,
-                                  int slots, cudaStream_t s, bool step) {
+                                  double* W, int wstride, int wc0, int slots, cudaStream_t s,
+                                  bool step) {
   if (op.npad != 32 && op.npad != 64) return cudaErrorInvalidValue;
   if (op.slices * op.npad > 256 || op.nout > op.npad) return cudaErrorInvalidValue;
   const Gemm3Layout L = gemm3_layout(op.slices, NB * NB * NB, op.npad, g.box.cnt[0], g.box.cnt[1],
@@ -859,8 +872,9 @@ static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& 
   const int grid = std::min(ntiles, sms);
   kern<<<grid, kGemm3Threads, smem, s>>>(*(const CUtensorMap*)ms.map,
                                         (const unsigned char*)op.b_slices, op.row_mul, op.slices,
-                                        op.nout, op.npad, (float2*)Y, ms.exps, ms.maxbits, g.n[0], g.n[1],
-                                        g.n[2], g.box, slots, step ? 1 : 0, ms.status);
+                                        op.nout, op.npad, (float2*)Y, W, wstride, wc0, ms.exps,
+                                        ms.maxbits, g.n[0], g.n[1], g.n[2], g.box, slots,
+                                        step ? 1 : 0, op.gmax, ms.status);
   return cudaGetLastError();
 }
 
@@ -875,8 +889,20 @@ cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedSt
   if (g.dim != 3 || g.box.n < 1 || g.box.n > 8 || op.K != g.box.n * nb * nb * nb)
     return cudaErrorInvalidValue;
   switch (nb) {
-    case 2: return launch_gemm3_t<2>(g, op, ms, Y, slots, s, step);
-    case 3: return launch_gemm3_t<3>(g, op, ms, Y, slots, s, step);
+    case 2: return launch_gemm3_t<2>(g, op, ms, Y, nullptr, 0, 0, slots, s, step);
+    case 3: return launch_gemm3_t<3>(g, op, ms, Y, nullptr, 0, 0, slots, s, step);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_mixed3_predict(const Grid& g, int nb, const MixedOp& op, MixedState& ms,
+                                  double* W, int wstride, int c0, int slots, cudaStream_t s) {
+  if (g.dim != 3 || g.box.n < 1 || g.box.n > 8 || op.K != g.box.n * nb * nb * nb || !W ||
+      c0 < 0 || c0 + op.nout > wstride)
+    return cudaErrorInvalidValue;
+  switch (nb) {
+    case 2: return launch_gemm3_t<2>(g, op, ms, nullptr, W, wstride, c0, slots, s, false);
+    case 3: return launch_gemm3_t<3>(g, op, ms, nullptr, W, wstride, c0, slots, s, false);
     default: return cudaErrorInvalidValue;
   }
 }

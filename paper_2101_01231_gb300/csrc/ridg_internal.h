@@ -113,9 +113,13 @@ int mixed3_make_map(const Grid& g, int nb, int slices, void* planes, void* map_o
 cudaError_t launch_mixed3_gemm(const Grid& g, int nb, const MixedOp& op, MixedState& ms, void* Y,
                                int slots, cudaStream_t s, bool step);
 // W[e * wstride + c0 + c] = the double-float outputs Y[c * cells + e] of a prediction launch
-// (c < nout), as FP64 with the planes' exponent
+// (c < nout), as FP64 with the planes' exponent (through a shared-memory tile)
 cudaError_t launch_mixed3_to_w(const Grid& g, int nout, int c0, int wstride, const void* Y,
                                int gmax, const MixedState& ms, double* W, cudaStream_t s);
+// ridg_predict's block: W[e * wstride + c0 + c] = (G X_e)[c] in FP64 (c < op.nout), written by
+// the GEMM's epilogue (the planes' exponent; the step's bookkeeping left alone)
+cudaError_t launch_mixed3_predict(const Grid& g, int nb, const MixedOp& op, MixedState& ms,
+                                  double* W, int wstride, int c0, int slots, cudaStream_t s);
 // the ring depth a slot cap gives for this configuration (0: it does not fit)
 int mixed3_gemm_slots(int nb, int slices, int npad, const RegionBox& box, int cap);
 // the correction from those outputs, plus the new state's digit planes and maximum: fused =
@@ -292,7 +296,8 @@ struct ridg_handle {
   int red_blocks = 256;
   ridg::MixedOp mixed;       // fused step operator [V; u_x; u_y] P-bar (2D)
   ridg::MixedOp mixed_pred;  // full prediction operator P
-  ridg::MixedOp mixed3_pred[4];  // 3D: the theta_S rows of P of each time mode (nb <= 4)
+  ridg::MixedOp mixed3_pred[4];  // 3D: P's theta_T rows in blocks of mixed3_pred_rows
+  int mixed3_pred_rows = 0;
   bool mixed3_fused = false;     // 3D: mixed is the fused step operator (else P-bar)
   double* Y = nullptr;       // fused outputs of the mixed step (cells * nout pairs)
   ridg::MixedState ms;       // digit planes and exponent bookkeeping of the mixed path

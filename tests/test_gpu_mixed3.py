@@ -188,19 +188,24 @@ def test_config3_noisy_data_mixed_within_105_of_oracle(R, slices):
     assert float(np.abs(q[cells] - qref).max() / np.abs(qref).max()) < tol
 
 
-@pytest.mark.parametrize("M,vel", [(2, (1.0, 0.7, 0.3)), (1, (-0.6, 0.4, 0.0)), (2, (0.0, -1.0, 0.5))])
-def test_mixed3_full_prediction_matches_oracle(R, M, vel):
-    # ridg_predict on the tensor cores: every time mode's theta_S rows of the region operator
-    # (all theta_T outputs) at 6 slices, against the oracle's region solves
+@pytest.mark.parametrize("M,vel,slices", [(2, (1.0, 0.7, 0.3), 6), (1, (-0.6, 0.4, 0.0), 6),
+                                          (2, (0.0, -1.0, 0.5), 6), (2, (1.0, 0.7, 0.3), 4),
+                                          (2, (-0.5, 0.2, -0.9), 3), (1, (0.3, -0.8, 0.6), 3)])
+def test_mixed3_full_prediction_matches_oracle(R, M, vel, slices):
+    # ridg_predict on the tensor cores: P's theta_T rows in blocks (32 rows at 6 slices, 64 at
+    # 3-4: one GEMM launch each), against the oracle's region solves; at 3-4 slices the step
+    # runs the fused step operator.  Bound: the digit count's rounding (2^-8S relative) summed
+    # over K = 8 theta_S < 2^8 terms, else the FP64 parity bound
     w = _w((10, 17, 3), M, vel)
-    s = _mixed(R, w)
+    s = _mixed(R, w, slices=slices)
     q = np.random.default_rng(43).standard_normal((s.cells, s.theta_s))
     s.set_state(q)
     dt = s.info()["dt"]
+    tol = TOL_STEP if slices == 6 else 2.0 ** (-8 * slices) * 256
     W = s.predict()
-    assert _rel(W, OL.predict(q, w, dt)) < TOL_STEP
+    assert _rel(W, OL.predict(q, w, dt)) < tol
     # the step that follows is unaffected (the prediction leaves its bookkeeping alone)
     s.step(2)
     s.sync()
-    assert _rel(s.get_state(), OL.run(q, w, dt, 2)) < 2 * TOL_STEP
+    assert _rel(s.get_state(), OL.run(q, w, dt, 2)) < 2 * tol
     s.close()
