@@ -478,42 +478,39 @@ __device__ __forceinline__ double f2d_scaled(float f, int k) {
   return __hiloint2double((int)hiw, (int)low);
 }
 
+// One thread per cell: dQ = V + the upwind face terms of both directions, summed in
+// registers (every mode index a compile-time constant); the block's state rows are read and
+// written coalesced through shared memory; then the cell's digit rows, group by group.
 template <int NB, int S>
 __global__ void __launch_bounds__(128) mixed_correct_kernel(
     double* __restrict__ Q, const float2* __restrict__ Y, int nx, int ny, CorrParams cp, int gmax,
     int sgnx, int sgny, int* __restrict__ exps, unsigned long long* __restrict__ maxbits,
     uint4* __restrict__ planes, int* status) {
-  // one thread per (cell, 8-mode group): P threads per cell, 128 / P cells per block
   constexpr int THS = NB * NB;
   constexpr int P = ((THS + 15) / 16) * 2;
-  constexpr int CPB = 128 / P;
+  constexpr int BT = 128;
   constexpr int PITCH = THS + 1;  // odd pitch: conflict-free row access
-  __shared__ double sq[CPB * PITCH];
+  __shared__ double sq[BT * PITCH];
   __shared__ unsigned long long shmax[4];
   const long long ncell = (long long)nx * ny;
-  const long long e0 = (long long)blockIdx.x * CPB;
-  const int nblk = (int)min((long long)CPB, ncell - e0);
+  const long long e0 = (long long)blockIdx.x * BT;
+  const int nblk = (int)min((long long)BT, ncell - e0);
   const int ys = exps[1];                                  // exponent of Y
   const int snext = exponent_above(maxbits[0]) + 1;        // exponent for the new digits
   // coalesced load of the block's state rows
-  for (int i = threadIdx.x; i < nblk * THS; i += 128) sq[(i / THS) * PITCH + i % THS] = Q[e0 * THS + i];
+  for (int i = threadIdx.x; i < nblk * THS; i += BT) sq[(i / THS) * PITCH + i % THS] = Q[e0 * THS + i];
   __syncthreads();
-  const int lc = threadIdx.x / P, pg = threadIdx.x % P, m0 = 8 * pg;
-  const long long e = e0 + lc;
+  const long long e = e0 + threadIdx.x;
   unsigned long long mymax = 0;
   bool fits = true;
-  if (lc < nblk) {
+  if (threadIdx.x < nblk) {
     const unsigned ue = (unsigned)e, uy = ue / (unsigned)nx;
     const int ix = (int)(ue - uy * (unsigned)nx), iy = (int)uy;
-    DF dq[8];
+    DF dq[THS];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (m0 + j < THS) {
-        const float2 y = Y[(m0 + j) * ncell + e];  // volume term V
-        dq[j] = DF{y.x, y.y};
-      } else {
-        dq[j] = DF{0.f, 0.f};
-      }
+    for (int j = 0; j < THS; ++j) {
+      const float2 y = Y[(long long)j * ncell + e];  // volume term V
+      dq[j] = DF{y.x, y.y};
     }
 #pragma unroll
     for (int dd = 0; dd < 2; ++dd) {
@@ -528,47 +525,48 @@ __global__ void __launch_bounds__(128) mixed_correct_kernel(
       }
       const long long jr = (long long)ry * nx + rx, jl = (long long)ly * nx + lx;
       const float2* u = Y + (long long)(THS + dd * NB) * ncell;
+      float2 fa[NB], fb[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        fa[t] = u[t * ncell + jr];
+        fb[t] = u[t * ncell + jl];
+      }
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
         const int base = dd == 0 ? t * NB : t;
-        bool any = false;  // does face trace t touch this thread's modes?
-#pragma unroll
-        for (int a2 = 0; a2 < NB; ++a2) any |= (base + a2 * st) / 8 == pg;
-        if (!any) continue;
-        const float2 a = u[t * ncell + jr], b = u[t * ncell + jl];
-        const DF fr = DF{a.x, a.y}, fl = DF{b.x, b.y};
+        const DF fr = DF{fa[t].x, fa[t].y}, fl = DF{fb[t].x, fb[t].y};
         const DF w_even = df_add(fl, df_neg(fr));  // -F(i+1/2) + F(i-1/2)
         const DF w_odd = df_neg(df_add(fl, fr));   // -F(i+1/2) - F(i-1/2)
 #pragma unroll
         for (int a2 = 0; a2 < NB; ++a2) {
-          const int sm = base + a2 * st;
-          if (sm / 8 != pg) continue;
           const DF w = (a2 & 1) ? w_odd : w_even;
           const DF c = (a2 == 0) ? w : df_mul_const(cp.eph[a2], cp.epl[a2], w);
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (m0 + j == sm) dq[j] = df_add(dq[j], c);
+          dq[base + a2 * st] = df_add(dq[base + a2 * st], c);
         }
       }
     }
     const int kfin = ys + gmax - 16;
-    double qn[8];
-    double* q = sq + lc * PITCH;
+    double* q = sq + threadIdx.x * PITCH;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (m0 + j < THS) {
-        double v = q[m0 + j];
-        v = v + f2d_scaled(dq[j].h, kfin);
-        v = v + f2d_scaled(dq[j].l, kfin);
-        q[m0 + j] = v;
-        qn[j] = v;
-        const unsigned long long ab = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
-        mymax = ab > mymax ? ab : mymax;
-      } else {
-        qn[j] = 0.0;
+    for (int pg = 0; pg < P; ++pg) {
+      double qn[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int sm = pg * 8 + j;
+        if (sm < THS) {
+          double v = q[sm];
+          v = v + f2d_scaled(dq[sm].h, kfin);
+          v = v + f2d_scaled(dq[sm].l, kfin);
+          q[sm] = v;
+          qn[j] = v;
+          const unsigned long long ab = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+          mymax = ab > mymax ? ab : mymax;
+        } else {
+          qn[j] = 0.0;
+        }
       }
+      fits &= write_group_digits<NB, S>(qn, pg, ix, iy, nx, ny, snext, planes, exps[2] != 0);
     }
-    fits = write_group_digits<NB, S>(qn, pg, ix, iy, nx, ny, snext, planes, exps[2] != 0);
   }
   if (!fits) atomicOr(status, kStatusRange);
   const unsigned long long bm = block_max_bits(mymax, shmax);
@@ -577,7 +575,7 @@ __global__ void __launch_bounds__(128) mixed_correct_kernel(
     if (blockIdx.x == 0) exps[0] = snext;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < nblk * THS; i += 128) Q[e0 * THS + i] = sq[(i / THS) * PITCH + i % THS];
+  for (int i = threadIdx.x; i < nblk * THS; i += BT) Q[e0 * THS + i] = sq[(i / THS) * PITCH + i % THS];
 }
 
 }  // namespace
@@ -743,8 +741,7 @@ template <int NB, int S>
 static cudaError_t launch_correct_t(const Grid& g, double* Q, const void* Y, int gmax,
                                     const CorrParams& cp, int sgnx, int sgny, MixedState& ms,
                                     cudaStream_t s) {
-  constexpr int CPB = 128 / (((NB * NB + 15) / 16) * 2);  // cells per block
-  const unsigned blocks = (unsigned)((g.ncell + CPB - 1) / CPB);
+  const unsigned blocks = (unsigned)((g.ncell + 127) / 128);  // one thread per cell
   mixed_correct_kernel<NB, S><<<blocks, 128, 0, s>>>(Q, (const float2*)Y, g.n[0], g.n[1], cp, gmax,
                                                      sgnx, sgny, ms.exps, ms.maxbits,
                                                      (uint4*)ms.planes, ms.status);

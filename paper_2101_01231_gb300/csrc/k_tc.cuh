@@ -92,6 +92,34 @@ __device__ __forceinline__ bool to_fixed32(double x, int s, int& F) {
   return true;
 }
 
+// The same for 24 < L <= 52 fraction bits (|F| < 2^L in 64 bits): t = floor(m / 2^(sh - 1))
+// by funnel shifts of the significand's two words, F = (t + 1) >> 1.  Shifts below 0 are out
+// of range (|x| 2^(L - s) >= 2^52 >= 2^L).
+template <int L>
+__device__ __forceinline__ bool to_fixed64(double x, int s, long long& F) {
+  static_assert(L > 24 && L <= 52, "64-bit fixed point below the significand's width");
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const int ex = (int)((hi >> 20) & 0x7FFu);
+  F = 0;
+  if (ex == 0) return true;  // zero / subnormal: far below the state's scale
+  const int r = 1074 - ex - L + s;  // sh - 1
+  if (r < 0) return false;
+  const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+  uint32_t tl, th;
+  if (r < 32) {
+    tl = __funnelshift_r(lo, mh, r);
+    th = mh >> r;
+  } else {
+    tl = r < 53 ? mh >> (r - 32) : 0u;
+    th = 0u;
+  }
+  const unsigned long long t = ((unsigned long long)th << 32) | tl;
+  const unsigned long long f = (t + 1ull) >> 1;
+  if (f >= (1ull << L)) return false;
+  F = (hi >> 31) ? -(long long)f : (long long)f;
+  return true;
+}
+
 // The S balanced base-256 digits of one coefficient (fixed point with 8 S fraction bits
 // relative to 2^s), most significant first, as BF16 (or, f16, FP16) bit patterns (exact
 // either way: |digit| <= 256).  Returns false if the value does not fit below 2^s.
@@ -113,23 +141,25 @@ __device__ __forceinline__ bool value_digit_bits(double x, int s, uint32_t (&bit
     for (int a = S - 1; a > 0; --a) d[a] = ((G >> (8 * (S - 1 - a))) & 0xFF) - 128;
     d[0] = G >> (8 * (S - 1));
   } else {
-    const long long F = to_fixed(x, s, L);
-    fits = (F < (1LL << L)) && (F > -(1LL << L));
-    const uint32_t lo32 = (uint32_t)F, hi32 = (uint32_t)((unsigned long long)F >> 32);
-    const int neg = (int)(hi32 >> 31);
-    int carry = 0;
-#pragma unroll
-    for (int a = S - 1; a >= 0; --a) {
-      const int k = S - 1 - a;  // byte index of digit a
-      const uint32_t byte = (k < 4 ? (lo32 >> (8 * k)) : (hi32 >> (8 * (k - 4)))) & 0xFFu;
-      if (a > 0) {
-        const int t = (int)byte + carry;
-        carry = (t + 128) >> 8;
-        d[a] = t - (carry << 8);
-      } else {
-        d[0] = (int)byte - (neg << 8) + carry;
-      }
+    // 64-bit, the same offset (128 at each of the S - 1 lower digit positions)
+    long long F;
+    if constexpr (L <= 52) {
+      fits = to_fixed64<L>(x, s, F);
+    } else {
+      F = to_fixed(x, s, L);
+      fits = (F < (1LL << L)) && (F > -(1LL << L));
     }
+    unsigned long long off = 0;
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) off |= 0x80ull << (8 * k);
+    const long long G = F + (long long)off;
+    const uint32_t g0 = (uint32_t)G, g1 = (uint32_t)((unsigned long long)G >> 32);
+#pragma unroll
+    for (int a = S - 1; a > 0; --a) {
+      const int k = S - 1 - a;  // byte index of digit a
+      d[a] = (int)((k < 4 ? (g0 >> (8 * k)) : (g1 >> (8 * (k - 4)))) & 0xFFu) - 128;
+    }
+    d[0] = (int)(G >> (8 * (S - 1)));
   }
 #pragma unroll
   for (int a = 0; a < S; ++a)
