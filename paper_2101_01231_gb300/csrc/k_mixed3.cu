@@ -12,15 +12,17 @@
 // Tiles are 8 x 16 cells of one z-plane (M = 128).  The region offset (ox, oy, oz) is taken
 // as in 2D -- x by one of the box's x-shifted TMA copies, y by the descriptor start -- and z
 // by loading the plane z + oz.  Shared memory holds
-//   the operator: the digits of every offset of the upwind box (at most 2 x 2 x 2 offsets,
-//     64 KB at Q2 with 4 slices, 98 KB with 6), one stage per (oz, oy) row, bulk-copied once
-//     per CTA and kept for all its tiles;
-//   an A ring (4 to 8 slots, as many as fit): one digit of one input plane (one x-copy per
-//     x-offset of the box, each 8-mode groups x 8 x 18 cells: 18.4 KB at Q2 with two
-//     x-offsets), loaded by 4D TMA boxes of the ghost-padded digit planes.
-// The MMA issuer runs oz -> digit a -> oy -> ox -> k-step; the epilogue writes W-bar as
-// double-float pairs with a common exponent, and mixed3_correct_kernel applies the correction
-// in double-float FP32 (state update FP64) and writes the next step's digit planes.  Every
+//   the operator: the digits of every offset of the upwind box (at most 2 x 2 x 2 offsets;
+//     98 KB at Q2 for the fused step operator's 64 padded rows with 3 slices, or for the 32
+//     time-mean rows with 6), one stage per (oz, oy) row, bulk-copied once per CTA and kept
+//     for all its tiles;
+//   an A ring (2 to 8 slots, as many as fit): one digit of the box's input planes (per
+//     plane one x-copy per x-offset, each 8-mode groups x 8 x 18 cells: 36.9 KB at Q2 for
+//     two planes and two x-offsets), loaded by 4D TMA boxes of the ghost-padded digit planes.
+// The MMA issuer runs digit a -> oz -> oy -> ox -> k-step; the epilogue writes the outputs
+// as double-float pairs with a common exponent (or, for ridg_predict, FP64 rows), and the
+// correction kernels apply them in double-float FP32 (state update FP64) and write the next
+// step's digit planes.  Every
 // wait is bounded (status bit on timeout).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -44,19 +46,21 @@ constexpr int kGemm3Threads = 32 * (2 + kEpiWarps);
 
 struct Gemm3Layout {
   int P, brows, na, nst;
-  uint32_t copy_bytes, a_bytes, b_bytes, b_off, bar_off, bytes;
+  uint32_t copy_bytes, z_bytes, a_bytes, b_bytes, b_off, bar_off, bytes;
 };
 
 // nop = padded output rows (32 or 64); ncx, ncy, ncz = offsets of the upwind box per
-// dimension (x-shifted copies per A slot, operator blocks per B stage, B stages = ncy ncz);
-// the A ring takes the room that is left
+// dimension (an A slot holds one digit of the ncz input planes, each as ncx x-shifted
+// copies; operator blocks per B stage, B stages = ncy ncz); the A ring takes the room that
+// is left
 __host__ __device__ inline Gemm3Layout gemm3_layout(int S, int thS, int nop, int ncx, int ncy,
                                                    int ncz, int na_cap = kNAmax) {
   Gemm3Layout l;
   l.P = ((thS + 15) / 16) * 2;
   l.brows = S * nop;
   l.copy_bytes = (uint32_t)l.P * kCopy * 16;
-  l.a_bytes = ((uint32_t)ncx * l.copy_bytes + 1023u) & ~1023u;
+  l.z_bytes = ((uint32_t)ncx * l.copy_bytes + 1023u) & ~1023u;
+  l.a_bytes = (uint32_t)ncz * l.z_bytes;
   l.b_bytes = (uint32_t)ncx * l.P * l.brows * 16;
   l.nst = ncy * ncz;
   const uint32_t btot = (uint32_t)l.nst * l.b_bytes;
@@ -158,23 +162,23 @@ __global__ void __launch_bounds__(kGemm3Threads, 1) mixed3_gemm_kernel(
         for (uint32_t off = 0; off < btot; off += 32768u)
           bulk_load(dst + off, Bg + off, min(32768u, btot - off), bfull);
       }
-      int ia = 0;  // A items issued
+      int ia = 0;  // A items issued (one per tile and digit)
       for (int k = 0; k < mytiles && ok; ++k) {
         int x0, y0, z0;
         tile_origin(k, x0, y0, z0);
-        for (int jz = 0; jz < ncz && ok; ++jz) {
-          for (int a = 0; a < S && ok; ++a, ++ia) {
-            const int sl = ia % NA;
-            if (ia >= NA && !mbar_wait_sleep(afree0 + 8u * sl, ((ia / NA) - 1) & 1)) { ok = false; break; }
-            const uint32_t fa = afull0 + 8u * sl;
-            mbar_expect_tx(fa, ncx * L.copy_bytes);  // out-of-range boxes are zero-filled and counted
-            const uint32_t dst = smem_u32(smem + sl * L.a_bytes);
-            // copy jx: x-offset ox0 + jx (padded column x0 + 1 + ox0 + jx, a multiple of 8
-            // elements), plane z-offset oz0 + jz (padded plane z0 + 1 + oz0 + jz)
+        for (int a = 0; a < S && ok; ++a, ++ia) {
+          const int sl = ia % NA;
+          if (ia >= NA && !mbar_wait_sleep(afree0 + 8u * sl, ((ia / NA) - 1) & 1)) { ok = false; break; }
+          const uint32_t fa = afull0 + 8u * sl;
+          // out-of-range boxes are zero-filled and counted
+          mbar_expect_tx(fa, ncz * ncx * L.copy_bytes);
+          const uint32_t dst = smem_u32(smem + sl * L.a_bytes);
+          // plane jz, copy jx: x-offset ox0 + jx (padded column x0 + 1 + ox0 + jx, a multiple
+          // of 8 elements), z-offset oz0 + jz (padded plane z0 + 1 + oz0 + jz)
+          for (int jz = 0; jz < ncz; ++jz)
             for (int jx = 0; jx < ncx; ++jx)
-              tma_load_4d(dst + jx * L.copy_bytes, &dmap, (x0 + 1 + ox0 + jx) * 8, y0,
-                          z0 + 1 + oz0 + jz, a * P, fa);
-          }
+              tma_load_4d(dst + jz * L.z_bytes + jx * L.copy_bytes, &dmap,
+                          (x0 + 1 + ox0 + jx) * 8, y0, z0 + 1 + oz0 + jz, a * P, fa);
         }
       }
       if (!ok) atomicOr(status, kStatusTimeout);
@@ -195,15 +199,16 @@ __global__ void __launch_bounds__(kGemm3Threads, 1) mixed3_gemm_kernel(
         const int ts = k & 1;
         if (k >= 2 && !mbar_wait(tempty0 + 8u * ts, ((k - 2) >> 1) & 1)) { ok = false; break; }
         const uint32_t tst = tmem + (uint32_t)(ts * tcols);
-        for (int jz = 0; jz < ncz && ok; ++jz) {
-          for (int a = 0; a < S && ok; ++a, ++ia) {
-            const int sl = ia % NA;
-            if (!mbar_wait(afull0 + 8u * sl, (ia / NA) & 1)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int a = 0; a < S && ok; ++a, ++ia) {
+          const int sl = ia % NA;
+          if (!mbar_wait(afull0 + 8u * sl, (ia / NA) & 1)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t idesc = idesc_digits(128, (S - a) * nop, f16);
+          const uint32_t dcol = tst + (uint32_t)(a * nop);
+          for (int jz = 0; jz < ncz; ++jz) {
             // A: LBO = plane stride inside a copy, SBO = one halo row of 8 cells (128 B)
-            const uint64_t adesc0 = smem_desc(smem_u32(smem + sl * L.a_bytes), kCopy * 16, 128);
-            const uint32_t idesc = idesc_digits(128, (S - a) * nop, f16);
-            const uint32_t dcol = tst + (uint32_t)(a * nop);
+            const uint64_t adesc0 =
+                smem_desc(smem_u32(smem + sl * L.a_bytes + jz * L.z_bytes), kCopy * 16, 128);
             for (int jy = 0; jy < ncy; ++jy) {
               const uint64_t bdesc0 =
                   smem_desc(smem_u32(smem + L.b_off + (jz * ncy + jy) * L.b_bytes), brows * 16, 128);
@@ -220,11 +225,11 @@ __global__ void __launch_bounds__(kGemm3Threads, 1) mixed3_gemm_kernel(
                 }
               }
             }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    afree0 + 8u * sl)
-                : "memory");
           }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  afree0 + 8u * sl)
+              : "memory");
         }
         if (ok)
           asm volatile(
