@@ -86,7 +86,7 @@ __device__ __forceinline__ double f2d_scale(float f, int k) {
   return __hiloint2double((int)hiw, (int)low);
 }
 
-// NCXC = 2: two x-offsets, the x loop unrolled; NCXC = 0: runtime count.
+// NCXC = 2: the 2 x 2 x 2 upwind box, every offset loop unrolled; NCXC = 0: runtime counts.
 template <int NB, int NCXC>
 __global__ void __launch_bounds__(kGemm3Threads, 1) mixed3_gemm_kernel(
     const __grid_constant__ CUtensorMap dmap, const unsigned char* __restrict__ Bg,
@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(kGemm3Threads, 1) mixed3_gemm_kernel(
   __shared__ uint32_t tmem_base_sh;
   // the upwind box: offsets lo + 0 .. cnt - 1 per dimension (cnt 1 or 2, at most 3 B stages)
   const int ox0 = box.lo[0], oy0 = box.lo[1], oz0 = box.lo[2];
-  const int ncx = NCXC ? NCXC : box.cnt[0], ncy = box.cnt[1], ncz = box.cnt[2];
+  const int ncx = NCXC ? NCXC : box.cnt[0], ncy = NCXC ? NCXC : box.cnt[1],
+            ncz = NCXC ? NCXC : box.cnt[2];
   const Gemm3Layout L = gemm3_layout(S, THS, nop, ncx, ncy, ncz, na_cap);
   const int NA = L.na;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -205,10 +206,12 @@ __global__ void __launch_bounds__(kGemm3Threads, 1) mixed3_gemm_kernel(
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t idesc = idesc_digits(128, (S - a) * nop, f16);
           const uint32_t dcol = tst + (uint32_t)(a * nop);
+#pragma unroll
           for (int jz = 0; jz < ncz; ++jz) {
             // A: LBO = plane stride inside a copy, SBO = one halo row of 8 cells (128 B)
             const uint64_t adesc0 =
                 smem_desc(smem_u32(smem + sl * L.a_bytes + jz * L.z_bytes), kCopy * 16, 128);
+#pragma unroll
             for (int jy = 0; jy < ncy; ++jy) {
               const uint64_t bdesc0 =
                   smem_desc(smem_u32(smem + L.b_off + (jz * ncy + jy) * L.b_bytes), brows * 16, 128);
@@ -867,7 +870,8 @@ static cudaError_t launch_gemm3_t(const Grid& g, const MixedOp& op, MixedState& 
   // one CTA per SM: each allocates all 512 TMEM columns, so a second CTA on the SM would
   // only wait for them -- ask for more than half the shared memory
   const uint32_t smem = std::max<uint32_t>(L.bytes, 117u * 1024u);
-  auto kern = g.box.cnt[0] == 2 ? mixed3_gemm_kernel<NB, 2> : mixed3_gemm_kernel<NB, 0>;
+  const bool box222 = g.box.cnt[0] == 2 && g.box.cnt[1] == 2 && g.box.cnt[2] == 2;
+  auto kern = box222 ? mixed3_gemm_kernel<NB, 2> : mixed3_gemm_kernel<NB, 0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
