@@ -62,6 +62,32 @@ def test_mixed3_step_matches_oracle(R, n, M, vel):
     s.close()
 
 
+@pytest.mark.parametrize("n,M,vel", CASES)
+@pytest.mark.parametrize("slices", [3, 4])
+def test_mixed3_fused_step_matches_oracle(R, n, M, vel, slices):
+    """The step through the fused step operator (the volume term and the upwind face traces
+    from the tensor cores; at Q2 for 3-4 slices, at Q1 always) on every box shape of CASES,
+    including zero velocity components (a smaller upwind box, the kernel's run-time offset
+    loops): against the oracle within the digits' rounding, 2^-8S relative per operand summed
+    over K < 2^8 terms, per step; the mass to round-off."""
+    w = _w(n, M, vel)
+    s = _mixed(R, w, slices=slices)
+    rng = np.random.default_rng(32)
+    q = rng.standard_normal((s.cells, s.theta_s))
+    s.set_state(q)
+    dt = s.info()["dt"]
+    m0 = s.mass()
+    tol = 2.0 ** (-8 * slices) * 256
+    s.step(1)
+    s.sync()
+    assert _rel(s.get_state(), OL.step(q, w, dt)) < tol
+    s.step(2)
+    s.sync()
+    assert _rel(s.get_state(), OL.run(q, w, dt, 3)) < 3 * tol
+    assert abs(s.mass()[0] - m0[0]) <= 1e-13 * max(1.0, abs(m0[0]))
+    s.close()
+
+
 def test_mixed3_profile_step_and_predict(R):
     w = _w((12, 10, 4), 2, (1.0, 0.5, -0.25))
     s = _mixed(R, w)
