@@ -983,10 +983,10 @@ def linear_arm(R, I, w, args, ws, flush, clocks=None, steps=None):
 
 def time_predict(R, I, w, make, q0, slices, hbm, bf16, reps=10):
     """ridg_predict of every cell's full space-time prediction (all theta_T rows of the
-    operator, SURVEY's config-3 contraction) through the C ABI into a device buffer, timed
-    with CUDA events on the handle's stream: its executed tensor rate (digit-pair products,
-    outputs and K padded) against the BF16 peak, its algorithmic rate (2 theta_T K flop per
-    cell) and the bytes it must move (Q in, W out in FP64)."""
+    operator: the full space-time contraction of 3D advection, Q2) through the C ABI into a
+    device buffer, timed with CUDA events on the handle's stream: its executed tensor rate
+    (digit-pair products, outputs and K padded) against the BF16 peak, its algorithmic rate
+    (2 theta_T K flop per cell) and the bytes it must move (Q in, W out in FP64)."""
     import torch
     s = make("mixed", slices)
     s.set_state(q0)

@@ -248,9 +248,9 @@ int ridg_profile_step(ridg_t* h, int n, ridg_profile_t* out);
 /* ----- autotuning ------------------------------------------------------------------------ */
 
 /* Time the launch choices of the handle's kernels on its own current state and keep the
- * fastest (the benchmark spec: tile shapes and schedules per polynomial order picked by an
- * autotuner).  Tuned now: for the 3D mixed path the depth of the GEMM's plane-operand ring
- * (3 to 8 slots) and the correction's block size (64, 128, 256 threads); for a nonlinear
+ * fastest (tile shapes and schedules per polynomial order).  Tuned now: for the 3D mixed
+ * path the depth of the GEMM's operand ring (the slots that fit, up to 8) and the
+ * correction's block size (64, 128, 256 threads); for a nonlinear
  * flux the persistent Newton grid (1, 2, 4 or 8 CTAs per 4 SMs: fewer CTAs keep more of
  * their block storage in L2).  Each candidate runs a few real steps (CUDA events around
  * each launch); the state, t and the step count are restored afterwards, and captured
