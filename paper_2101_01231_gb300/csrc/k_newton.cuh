@@ -155,15 +155,23 @@ struct Layout {
   // phase arenas
   static constexpr size_t aRes = sizeof(double) * ResBufs<NB, MV>::total;
   static constexpr size_t aAlpha = sizeof(double) * 12 * D::QF;
-  static constexpr size_t oJW = up16(sizeof(T) * D::CG * D::FAS);     // after the FA arrays
+  // FP32 assembly of one conserved variable: one cell at a time, its triple products
+  // contracted one dimension at a time (assemble_cell_sf); else CG cells per list pass
+  static constexpr bool SF = sizeof(T) == 4 && MV == 1;
+  static constexpr int CGL = SF ? 1 : D::CG;
+  static constexpr size_t oJW = up16(sizeof(T) * CGL * D::FAS);       // after the FA arrays
   static constexpr size_t oJB0 = up16(oJW + sizeof(T) * MV * D::QP);
   static constexpr size_t oJB1 = up16(oJB0 + sizeof(T) * D::PB);
   static constexpr size_t aJac = up16(oJB1 + sizeof(T) * D::PB);
+  // the sum-factorised assembly's buffers, where the projection's were (after FA)
+  static constexpr int NB2 = NB * NB, NP2 = D::NP * D::NP;
+  static constexpr int SFN = 2 * NP2 * NB2 + D::NP * NB2 * NB2 + 4 * D::NP * NB2 + NB2 * NB2;
+  static constexpr size_t aSF = SF ? up16(oJW + sizeof(T) * SFN) : 0;
   static constexpr size_t oSA = up16(sizeof(T) * D::BP * D::BP);
   static constexpr size_t oSB = up16(oSA + sizeof(T) * NBUF * D::BP * 17);
   static constexpr size_t aLU = TC ? (size_t)kStages * TcDims<D::BP>::STAGE
                                    : up16(oSB + sizeof(T) * NBUF * 16 * D::BP);
-  static constexpr size_t bytes = oArena + cmax(cmax(aRes, aAlpha), cmax(aJac, aLU));
+  static constexpr size_t bytes = oArena + cmax(cmax(aRes, aAlpha), cmax(cmax(aJac, aSF), aLU));
   // CTAs per SM: two where their shared memory fits (FP32 solves), else one
   static constexpr int MINB = (sizeof(T) == 4 && 2 * (bytes + 1024) <= 233472) ? 2 : 1;
 };
@@ -620,6 +628,162 @@ __device__ void assemble_cells(const NlDev& tb, const NlPlan& plan, int r0, cons
 #pragma unroll
           for (int j2 = 0; j2 < MV; ++j2)
             blk[bidx<TC, BP>(i2 * THT + k, j2 * THT + l, tr)] = acc[g][i2 * MV + j2];
+      }
+    }
+  }
+  if constexpr (TC) asm volatile("fence.proxy.async.global;" ::: "memory");  // read by bulk copies
+  __syncthreads();
+}
+
+// The blocks of region cell r (one conserved variable, FP32) from its projected arrays FA,
+// the same sums as assemble_cells but factorised: with k = (a_k, y_k, x_k) (time, y, x
+// indices) and the triple products of eqs. Jacproj / Jacobian2 products of 1D factors
+// (T0 = int phi phi phi, T1 = int phi' phi phi, traces phi(+-1)), each dimension's sum is
+// taken once for all the others instead of per (k, l) pair:
+//   Vx[pt,py,xk,xl] = sum_px T1[xk,xl,px] Fx[pt,py,px],  Wy likewise with T0 and Fy;
+//   Hf[pt,ok,ol]    = sum_po T0[ok,ol,po] Ff[pt,po] for the own side of face f;
+//   U[pt,yk,yl,xk,xl] = sum_py (T0[yk,yl,py] Vx + T1[yk,yl,py] Wy)[pt,py,xk,xl]
+//                     + the faces' Hf times their trace pairs;
+//   J[k,l] = sum_pt T0[ak,al,pt] U[pt,yk,yl,xk,xl] (+ the time term);
+// and each neighbour block N_f[k,l] = tr(x or y of k) tr'(... of l) sum_pt T0[ak,al,pt]
+// Hn_f[pt,ok,ol].  S: the buffers (Layout::SFN floats).  At Q4 this takes ~0.4 M FMAs per
+// cell where the merged lists take ~1.5 M and one table load per FMA.
+template <int NB, bool TC>
+__device__ void assemble_cell_sf(const NlDev& tb, const NlPlan& plan, int r, const float* FA,
+                                 float* S, float* slots) {
+  using D = Dims<NB, 1>;
+  constexpr int NP = D::NP, QP = D::QP, QPF = D::QPF, THS = D::THS, THT = D::THT;
+  constexpr int BP = D::BP, BS = D::BS, NB2 = NB * NB, NB4 = NB2 * NB2, NP2 = NP * NP;
+  const int tid = threadIdx.x;
+  const float* T0 = tb.T0_f;
+  const float* T1 = tb.T1_f;
+  const float* ep = tb.ep1_f;
+  const float* em = tb.em1_f;
+  const float* Mt = tb.Mt_f;
+  float* Vx = S;
+  float* Wy = Vx + NP2 * NB2;
+  float* U = Wy + NP2 * NB2;
+  float* H = U + NP * NB4;
+  float* K = H + 4 * NP * NB2;
+  const float* Fx = FA;
+  const float* Fy = FA + QP;
+  const float* Ff = FA + 2 * QP;  // own side of face f at f QPF, the neighbour's at (4 + f) QPF
+  for (int i = tid; i < NP2 * NB2; i += kThreads) {
+    const int ptpy = i / NB2, kl = i - ptpy * NB2;
+    const float* fx = Fx + ptpy * NP;
+    const float* fy = Fy + ptpy * NP;
+    const float* t1 = T1 + kl * NP;
+    const float* t0 = T0 + kl * NP;
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      sx = fmaf(t1[p], fx[p], sx);
+      sy = fmaf(t0[p], fy[p], sy);
+    }
+    Vx[i] = sx;
+    Wy[i] = sy;
+  }
+  for (int i = tid; i < 4 * NP * NB2; i += kThreads) {
+    const int fpt = i / NB2, kl = i - fpt * NB2;  // fpt = f NP + pt
+    const int f = fpt / NP, pt = fpt - f * NP;
+    const float* ff = Ff + f * QPF + pt * NP;
+    const float* t0 = T0 + kl * NP;
+    float h = 0.f;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) h = fmaf(t0[p], ff[p], h);
+    H[i] = h;
+  }
+  __syncthreads();
+  for (int i = tid; i < NP * NB4; i += kThreads) {
+    const int pt = i / NB4, rem = i - pt * NB4, ykl = rem / NB2, xkl = rem - ykl * NB2;
+    const int yk = ykl / NB, yl = ykl - yk * NB, xk = xkl / NB, xl = xkl - xk * NB;
+    const float* t0 = T0 + ykl * NP;
+    const float* t1 = T1 + ykl * NP;
+    const float* vx = Vx + pt * NP * NB2 + xkl;
+    const float* wy = Wy + pt * NP * NB2 + xkl;
+    float u = 0.f;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      u = fmaf(t0[p], vx[p * NB2], u);
+      u = fmaf(t1[p], wy[p * NB2], u);
+    }
+    // own sides of the faces x+ (f 0), x- (1), y+ (2), y- (3): trace pairs of the normal index
+    u = fmaf(ep[xk] * ep[xl], H[(0 * NP + pt) * NB2 + ykl], u);
+    u = fmaf(em[xk] * em[xl], H[(1 * NP + pt) * NB2 + ykl], u);
+    u = fmaf(ep[yk] * ep[yl], H[(2 * NP + pt) * NB2 + xkl], u);
+    u = fmaf(em[yk] * em[yl], H[(3 * NP + pt) * NB2 + xkl], u);
+    U[i] = u;
+  }
+  __syncthreads();
+  {
+    float* blk = slots + (size_t)plan.slot[r * 10] * BP * BP;
+    for (int i = tid; i < THT * THT; i += kThreads) {
+      const int k = i / THT, l = i - k * THT;
+      const int ak = k / THS, sk = k - ak * THS, al = l / THS, sl = l - al * THS;
+      const int yk = sk / NB, xk = sk - yk * NB, yl = sl / NB, xl = sl - yl * NB;
+      const float* t0 = T0 + (ak * NB + al) * NP;
+      const float* u = U + (yk * NB + yl) * NB2 + xk * NB + xl;
+      float j = 0.f;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) j = fmaf(t0[p], u[p * NB4], j);
+      if (sk == sl) j += Mt[ak * NB + al];
+      blk[bidx<TC, BP>(k, l)] = j;
+    }
+  }
+  // the neighbour blocks, one face at a time (H and K reused)
+  for (int f = 0; f < 4; ++f) {
+    const int dd = f >> 1, si = f & 1;
+    const int r2 = region_nbr(r, dd, si ? -1 : 1);
+    if (r2 < 0) continue;  // (uniform over the block)
+    __syncthreads();       // the previous face's K is consumed
+    for (int i = tid; i < NP * NB2; i += kThreads) {
+      const int pt = i / NB2, kl = i - pt * NB2;
+      const float* ff = Ff + (4 + f) * QPF + pt * NP;
+      const float* t0 = T0 + kl * NP;
+      float h = 0.f;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) h = fmaf(t0[p], ff[p], h);
+      H[i] = h;
+    }
+    __syncthreads();
+    for (int i = tid; i < NB4; i += kThreads) {
+      const int akl = i / NB2, okl = i - akl * NB2;
+      const float* t0 = T0 + akl * NP;
+      float kk = 0.f;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) kk = fmaf(t0[p], H[p * NB2 + okl], kk);
+      K[i] = kk;
+    }
+    __syncthreads();
+    // test function on this cell's side si of the face, trial function on the neighbour's
+    // (opposite) side
+    const float* trk = si ? em : ep;
+    const float* trl = si ? ep : em;
+    float* blk = slots + (size_t)plan.slot[r * 9 + r2] * BP * BP;
+    const bool tr = TC && plan.pos[r] < plan.pos[r2];
+    for (int i = tid; i < THT * THT; i += kThreads) {
+      const int k = i / THT, l = i - k * THT;
+      const int ak = k / THS, sk = k - ak * THS, al = l / THS, sl = l - al * THS;
+      const int yk = sk / NB, xk = sk - yk * NB, yl = sl / NB, xl = sl - yl * NB;
+      const int nk = dd == 0 ? xk : yk, nl = dd == 0 ? xl : yl;  // normal indices
+      const int ok = dd == 0 ? yk : xk, ol = dd == 0 ? yl : xl;  // tangential indices
+      blk[bidx<TC, BP>(k, l, tr)] = trk[nk] * trl[nl] * K[(ak * NB + al) * NB2 + ok * NB + ol];
+    }
+  }
+  // zero padding rows / columns of every block written here (as in assemble_cells)
+  if constexpr (BP > BS) {
+    constexpr int NPAD = (BP - BS) * BP + BS * (BP - BS);
+    for (int f = -1; f < 4; ++f) {
+      const int r2 = f < 0 ? r : region_nbr(r, f >> 1, (f & 1) ? -1 : 1);
+      if (r2 < 0) continue;
+      float* blk = slots + (size_t)plan.slot[r * 9 + r2] * BP * BP;
+      for (int i = tid; i < NPAD; i += kThreads) {
+        if (i < (BP - BS) * BP) {
+          blk[bidx<TC, BP>(BS + i / BP, i % BP)] = 0.f;
+        } else {
+          const int j = i - (BP - BS) * BP;
+          blk[bidx<TC, BP>(j / (BP - BS), BS + j % (BP - BS))] = 0.f;
+        }
       }
     }
   }
@@ -1467,11 +1631,18 @@ __device__ void newton_regions(const NewtonArgs& a, unsigned char* smem, uint32_
       if (refactor && it >= a.max_iters) break;
       residual<NB, MV, FLUX>(a.tb, Ws, Qs, Rs, alpha, (double*)arena, lam, a.gamma);
       if (refactor) {
-        for (int r0 = 0; r0 < 9; r0 += D::CG) {
-          for (int g = 0; g < D::CG; ++g)
-            project_cell<T, NB, MV, FLUX>(a.tb, r0 + g, Ws, alpha, FA + g * D::FAS, jw, jb0, jb1,
-                                          lam, a.gamma);
-          assemble_cells<T, NB, MV, TC>(a.tb, a.plan, r0, FA, slots);
+        if constexpr (L::SF) {
+          for (int r = 0; r < 9; ++r) {
+            project_cell<T, NB, MV, FLUX>(a.tb, r, Ws, alpha, FA, jw, jb0, jb1, lam, a.gamma);
+            assemble_cell_sf<NB, TC>(a.tb, a.plan, r, (const float*)FA, (float*)jw, (float*)slots);
+          }
+        } else {
+          for (int r0 = 0; r0 < 9; r0 += D::CG) {
+            for (int g = 0; g < D::CG; ++g)
+              project_cell<T, NB, MV, FLUX>(a.tb, r0 + g, Ws, alpha, FA + g * D::FAS, jw, jb0,
+                                            jb1, lam, a.gamma);
+            assemble_cells<T, NB, MV, TC>(a.tb, a.plan, r0, FA, slots);
+          }
         }
       }
       for (int i = tid; i < 9 * D::BP; i += kThreads) {
@@ -1553,16 +1724,15 @@ __global__ void __launch_bounds__(kThreads, (Layout<T, NB, MV, TC>::MINB)) newto
 // NewtonArgs with its instance table and counter) in the given order, highest degree first;
 // every CTA works through the first queue, then moves to the next as a queue runs out, so the
 // lower degrees fill the tail of the higher ones.  Burgers (one conserved variable), degrees
-// 1 to 4; shared memory and the launch bounds are those of the largest degree.
+// 1 to 4; shared memory is that of the largest degree.
 template <typename T, bool TC>
 struct MultiLayout {
   static constexpr size_t b2 = Layout<T, 2, 1, TC>::bytes, b3 = Layout<T, 3, 1, TC>::bytes,
                           b4 = Layout<T, 4, 1, TC>::bytes, b5 = Layout<T, 5, 1, TC>::bytes;
   static constexpr size_t bytes = cmax(cmax(b2, b3), cmax(b4, b5));
-  static constexpr int m2 = Layout<T, 2, 1, TC>::MINB, m3 = Layout<T, 3, 1, TC>::MINB,
-                       m4 = Layout<T, 4, 1, TC>::MINB, m5 = Layout<T, 5, 1, TC>::MINB;
-  static constexpr int MINB = (m2 < m3 ? m2 : m3) < (m4 < m5 ? m4 : m5) ? (m2 < m3 ? m2 : m3)
-                                                                         : (m4 < m5 ? m4 : m5);
+  // one CTA per SM: the four degrees' code in one kernel needs more than the 128 registers
+  // a thread may hold at two CTAs of 256 threads (it spills 1 KB there)
+  static constexpr int MINB = 1;
 };
 
 // (the degrees' arguments are read from device memory: four NewtonArgs are ~6 KB, more than

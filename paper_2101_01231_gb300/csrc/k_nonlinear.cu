@@ -103,8 +103,11 @@ int nl_tables_upload(int nb, NlDevTables& out, void* mem, size_t* bytes, cudaStr
   }
   auto tof = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
   std::vector<float> Mtf = tof(t.Mt), PsiAtPf = tof(t.PsiAtP), PsiAtFPf = tof(t.PsiAtFP), P1f = tof(t.P1);
+  std::vector<float> T0f = tof(t.T0), T1f = tof(t.T1), ep1f = tof(t.ep1), em1f = tof(t.em1);
   const size_t iMtf = add(Mtf.data(), Mtf.size() * 4), iPsiAtPf = add(PsiAtPf.data(), PsiAtPf.size() * 4),
                iPsiAtFPf = add(PsiAtFPf.data(), PsiAtFPf.size() * 4), iP1f = add(P1f.data(), P1f.size() * 4);
+  const size_t iT0f = add(T0f.data(), T0f.size() * 4), iT1f = add(T1f.data(), T1f.size() * 4),
+               iep1f = add(ep1f.data(), ep1f.size() * 4), iem1f = add(em1f.data(), em1f.size() * 4);
   const size_t total = (off + 255) & ~(size_t)255;
   if (!mem) {
     *bytes = total;
@@ -161,6 +164,10 @@ int nl_tables_upload(int nb, NlDevTables& out, void* mem, size_t* bytes, cudaStr
   tb.PsiAtP_f = F(iPsiAtPf);
   tb.PsiAtFP_f = F(iPsiAtFPf);
   tb.P1_f = F(iP1f);
+  tb.T0_f = F(iT0f);
+  tb.T1_f = F(iT1f);
+  tb.ep1_f = F(iep1f);
+  tb.em1_f = F(iem1f);
   out.mem = mem;
   out.bytes = total;
   return RIDG_OK;

@@ -186,6 +186,8 @@ NlHostTables build_nl_tables(int M) {
   // --- sparse triple-product lists ---
   const std::vector<double> T0 = triple1d(nb, nb, np, false);  // int phi_a phi_b phi_c
   const std::vector<double> T1 = triple1d(nb, nb, np, true);   // int phi_a' phi_b phi_c
+  t.T0 = T0;
+  t.T1 = T1;
   auto t0 = [&](int a, int b, int c) { return T0[((size_t)a * nb + b) * np + c]; };
   auto t1d = [&](int a, int b, int c) { return T1[((size_t)a * nb + b) * np + c]; };
   const double tol = 1e-13;

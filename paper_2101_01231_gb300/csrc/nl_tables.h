@@ -34,6 +34,9 @@ struct NlHostTables {
   // eq. Jacproj onto Psi_p (volume) and onto the face basis are its tensor products
   std::vector<double> P1;
   SparseTriple beta[2];              // [dim]: int d_dim Psi_k Psi_l Psi_p (volume)
+  // the 1D factors of those triple products, [a][b][p] (a, b < nb, p < np): int phi_a phi_b
+  // phi_p, and the same with phi_a' (for the sum-factorised assembly)
+  std::vector<double> T0, T1;
   SparseTriple gamma[2][2][2];       // [dim][side_k][side_l]: face integrals
 };
 

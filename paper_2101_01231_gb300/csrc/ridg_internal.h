@@ -155,6 +155,9 @@ struct NlDev {
   const void *oent_d[4], *oent_f[4];
   // FP32 copies of the projection tables and the time term (FP32 assembly)
   const float *Mt_f, *PsiAtP_f, *PsiAtFP_f, *P1_f;
+  // FP32 1D triple products [a][b][p] (int phi_a phi_b phi_p; with phi_a') and the traces
+  // phi_b(+1), phi_b(-1): the factors of the sum-factorised FP32 assembly
+  const float *T0_f, *T1_f, *ep1_f, *em1_f;
 };
 // Block elimination plan for the 3 x 3 region: blocks are eliminated corners first, then the
 // edge cells, then the centre; each pivot's later neighbours and the fill they create.
