@@ -46,6 +46,10 @@ static int dump_tables(int M, const char* path) {
   put(f, "P1", t.P1);
   put(f, "V1", t.V1);
   put(f, "dV1", t.dV1);
+  put(f, "ep1", t.ep1);
+  put(f, "em1", t.em1);
+  put(f, "T0", t.T0);
+  put(f, "T1", t.T1);
   puti(f, "dptr", L.dptr);
   puti(f, "doff", L.doff);
   put(f, "dval", L.dval);

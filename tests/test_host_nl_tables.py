@@ -128,6 +128,66 @@ def test_nl_tables_match_oracle(exe, M, tmp_path):
         np.testing.assert_allclose(Do, ref, **lists)
 
 
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_factorised_assembly_matches_oracle_tensors(exe, M, tmp_path):
+    """The FP32 Newton kernels assemble a region cell's blocks (one conserved variable) by
+    sum factorisation: the projected arrays are contracted with the 1D triple products one
+    dimension at a time (x, then y, then time), the face terms folded in with their trace
+    pairs.  The same contractions written out here with the host's 1D factors, in the
+    kernel's index conventions, give the blocks the oracle's dense triple-product tensors
+    give (eqs. Jacproj, Jacobian2): the diagonal block (volume of both directions, own sides
+    of the four faces) and the block towards the neighbour across each face."""
+    c = _tables(exe, M, tmp_path)
+    tb = NL.Tables(2, M)
+    nb, npj = M + 1, 2 * M + 1
+    thT, QP, QPf = nb ** 3, npj ** 3, npj ** 2
+    T0 = c["T0"].reshape(nb, nb, npj)
+    T1 = c["T1"].reshape(nb, nb, npj)
+    ep, em = c["ep1"], c["em1"]
+    np.testing.assert_allclose(ep, basis.phi(nb, np.array([1.0]))[:, 0], rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(em, basis.phi(nb, np.array([-1.0]))[:, 0], rtol=1e-14, atol=1e-14)
+    rng = np.random.default_rng(7)
+    FA = rng.standard_normal(2 * QP + 8 * QPf)
+    Fx = FA[:QP].reshape(npj, npj, npj)              # [pt, py, px]
+    Fy = FA[QP:2 * QP].reshape(npj, npj, npj)
+    own = [FA[2 * QP + f * QPf:2 * QP + (f + 1) * QPf].reshape(npj, npj) for f in range(4)]
+    nbr = [FA[2 * QP + (4 + f) * QPf:2 * QP + (5 + f) * QPf].reshape(npj, npj) for f in range(4)]
+    # the kernel's passes: Vx, Wy (x sums), H (face tangential sums), U (y sums and faces),
+    # J (time sums); k = (a_k, y_k, x_k) with x fastest
+    Vx = np.einsum("klp,typ->tykl", T1, Fx)
+    Wy = np.einsum("klp,typ->tykl", T0, Fy)
+    H = [np.einsum("klp,tp->tkl", T0, own[f]) for f in range(4)]
+    U = (np.einsum("abp,tpkl->tabkl", T0, Vx) + np.einsum("abp,tpkl->tabkl", T1, Wy)
+         + np.einsum("k,l,tab->tabkl", ep, ep, H[0]) + np.einsum("k,l,tab->tabkl", em, em, H[1])
+         + np.einsum("a,b,tkl->tabkl", ep, ep, H[2]) + np.einsum("a,b,tkl->tabkl", em, em, H[3]))
+    J = np.einsum("cdt,tabkl->cakdbl", T0, U).reshape(thT, thT)
+    npair = thT * thT
+    ref = np.zeros((npair, 2 * QP + 8 * QPf))
+    for dd in range(2):
+        ref[:, dd * QP:(dd + 1) * QP] = tb.beta[dd].reshape(npair, QP)
+    for f in range(4):
+        dd, side = f >> 1, (+1, -1)[f & 1]
+        o = 2 * QP + f * QPf
+        ref[:, o:o + QPf] = tb.gamma[dd][(side, side)].reshape(npair, QPf)
+    scale = np.abs(ref).max() * np.abs(FA).max()
+    np.testing.assert_allclose(J, (ref @ FA).reshape(thT, thT), rtol=0, atol=1e-12 * scale)
+    # neighbour blocks: this cell's trace on its side of face f, the neighbour's on the other
+    for f in range(4):
+        dd, si = f >> 1, f & 1
+        side = (+1, -1)[si]
+        trk, trl = (em, ep) if si else (ep, em)
+        K = np.einsum("cdt,tab->cdab", T0, np.einsum("abp,tp->tab", T0, nbr[f]))
+        if dd == 0:   # normal x, tangential y
+            N = np.einsum("k,l,cdab->cakdbl", trk, trl, K)
+        else:         # normal y, tangential x
+            N = np.einsum("a,b,cdkl->cakdbl", trk, trl, K)
+        N = N.reshape(thT, thT)
+        o = 2 * QP + (4 + f) * QPf
+        G = tb.gamma[dd][(side, -side)].reshape(npair, QPf)
+        np.testing.assert_allclose(N, (G @ FA[o:o + QPf]).reshape(thT, thT), rtol=0,
+                                   atol=1e-12 * scale)
+
+
 def test_elimination_plan_solves_region_system(exe):
     r = subprocess.run([exe, "plan"], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
