@@ -77,8 +77,11 @@ typedef struct {
 enum {
   RIDG_PREC_FP64 = 0,        /* every step of the path in FP64                           */
   RIDG_PREC_MIXED_BF16 = 1,  /* linear prediction as a sliced BF16 tensor-core contraction
-                                with FP32 accumulation recombined in FP64 (split-operand
-                                refinement); correction, face sums and time in FP64       */
+                                with FP32 accumulation recombined into double-float pairs
+                                (split-operand refinement); in the step the contraction
+                                also yields the correction's volume term and face traces
+                                (one composed operator), the face terms are summed in
+                                double-float and the state update is FP64                 */
   RIDG_PREC_MIXED_FP32 = 2,  /* Newton linear solves in FP32 with the residual in FP64
                                 (nonlinear flux)                                          */
   RIDG_PREC_MIXED_TF32 = 3,  /* Newton linear solves with the Schur-complement block
@@ -171,8 +174,9 @@ int ridg_set_final_time(ridg_t* h, double T, long long* nsteps);
 
 /* Prediction (Sec. 2.2): every cell's centre space-time coefficients W_i from the
  * current state.  With a mixed linear precision (2D, 3D) it runs the split-digit
- * tensor-core contraction of all theta_T rows (in 3D one launch per time mode's theta_S
- * rows, each converted from double-float into its columns of W).
+ * tensor-core contraction of all theta_T rows (in 3D one launch per block of up to 64 rows,
+ * 32 at 5-6 slices: a block of up to 32 rows written in FP64 by its own launch, a wider one
+ * through a double-float buffer and a conversion pass).
  * If w_out is not NULL it receives cells * m * theta_T doubles (prediction layout; device
  * pointer if on_device).  The prediction is also kept for a
  * following ridg_correct.  Returns RIDG_ENOCONV (after completing) if Newton hit its cap
