@@ -80,8 +80,9 @@ enum {
                                 with FP32 accumulation recombined into double-float pairs
                                 (split-operand refinement); in the step the contraction
                                 also yields the correction's volume term and face traces
-                                (one composed operator), the face terms are summed in
-                                double-float and the state update is FP64                 */
+                                (one composed operator; in 3D at Q2 up to 4 slices, else
+                                the time means), the face terms are summed in double-float
+                                and the state update is FP64                              */
   RIDG_PREC_MIXED_FP32 = 2,  /* Newton linear solves in FP32 with the residual in FP64
                                 (nonlinear flux)                                          */
   RIDG_PREC_MIXED_TF32 = 3,  /* Newton linear solves with the Schur-complement block
