@@ -171,7 +171,7 @@ int rebuild_linear(ridg_t* h) {
     // of every line of modes along d), else the time-mean rows P-bar (first theta_S rows of
     // P) --, and for ridg_predict P's theta_T rows in blocks of 64 (32 where slices x 64
     // columns exceed the GEMM's 256), each its own digit operator
-    const int nb = h->nb, thS = h->thS, K = h->K, NT = nb * nb;
+    const int nb = h->nb, K = h->K;
     h->mixed3_fused = ridg::mixed3_fused_fits(nb, h->opt.slices);
     h->mixed3_pred_rows = h->opt.slices * 64 <= 256 ? 64 : 32;
     const int nchunks = (h->thT + h->mixed3_pred_rows - 1) / h->mixed3_pred_rows;
@@ -179,35 +179,14 @@ int rebuild_linear(ridg_t* h) {
     for (int a = 0; a <= nchunks; ++a) {
       ridg::MixedOp& op = a == 0 ? h->mixed : h->mixed3_pred[a - 1];
       const int r0 = a == 0 ? 0 : (a - 1) * h->mixed3_pred_rows;
-      const int nr = a == 0 ? thS : std::min(h->mixed3_pred_rows, h->thT - r0);
+      const int nr = a == 0 ? h->thS : std::min(h->mixed3_pred_rows, h->thT - r0);
       std::vector<double> rows(h->P_host.begin() + (size_t)r0 * h->K,
                                h->P_host.begin() + (size_t)(r0 + nr) * h->K);
       int nout = nr;
       if (a == 0 && h->mixed3_fused) {
         nout = ridg::mixed3_fused_nout(nb);
-        ridg::Tables1D t1 = ridg::tables1d(nb);
-        std::vector<double> C((size_t)nout * thS, 0.0);
-        for (int d = 0; d < 3; ++d) {
-          const int st = d == 0 ? 1 : (d == 1 ? nb : nb * nb);
-          for (int s = 0; s < thS; ++s) {
-            const int ad = (s / st) % nb, base = s - ad * st;
-            for (int b = 0; b < nb; ++b) C[(size_t)s * thS + base + b * st] += nu[d] * t1.D[ad * nb + b];
-          }
-          const std::vector<double>& tr = nu[d] >= 0 ? t1.ep : t1.em;
-          for (int t = 0; t < NT; ++t) {
-            // line t: the modes with the other two indices fixed (the lower one fastest)
-            const int base = d == 0 ? t * nb : (d == 1 ? (t % nb) + (t / nb) * nb * nb : t);
-            for (int b = 0; b < nb; ++b)
-              C[(size_t)(thS + d * NT + t) * thS + base + b * st] = nu[d] * tr[b];
-          }
-        }
-        std::vector<double> G((size_t)nout * K, 0.0);
-        for (int r = 0; r < nout; ++r)
-          for (int s = 0; s < thS; ++s) {
-            const double c = C[(size_t)r * thS + s];
-            if (c == 0.0) continue;
-            for (int k = 0; k < K; ++k) G[(size_t)r * K + k] += c * rows[(size_t)s * K + k];
-          }
+        std::vector<double> G;
+        ridg::fused_step_operator(3, nb, nu, rows, K, G);
         rows.swap(G);
       }
       std::vector<unsigned short> digits;
@@ -255,28 +234,10 @@ int rebuild_linear(ridg_t* h) {
   } else if (is_mixed_linear(h)) {
     // fused step operator: rows [V; u_x; u_y] = C P-bar with C mapping the time mean W-bar to
     // the volume term sum_d nu_d (D along d) W-bar and the upwind face traces nu_d tr(W-bar)
-    const int nb = h->nb, thS = h->thS, K = h->K, nout = thS + 2 * nb;
-    ridg::Tables1D t1 = ridg::tables1d(nb);
-    std::vector<double> C((size_t)nout * thS, 0.0);
-    for (int d = 0; d < 2; ++d) {
-      const int st = d == 0 ? 1 : nb;
-      for (int s = 0; s < thS; ++s) {
-        const int bd = (s / st) % nb, base = s - bd * st;
-        for (int b = 0; b < nb; ++b) C[(size_t)s * thS + base + b * st] += nu[d] * t1.D[bd * nb + b];
-      }
-      const std::vector<double>& tr = nu[d] >= 0 ? t1.ep : t1.em;
-      for (int t = 0; t < nb; ++t) {
-        const int base = d == 0 ? t * nb : t;  // other-dimension digit t
-        for (int b = 0; b < nb; ++b) C[(size_t)(thS + d * nb + t) * thS + base + b * st] = nu[d] * tr[b];
-      }
-    }
-    std::vector<double> G((size_t)nout * K, 0.0);
-    for (int r = 0; r < nout; ++r)
-      for (int s = 0; s < thS; ++s) {
-        const double c = C[(size_t)r * thS + s];
-        if (c == 0.0) continue;
-        for (int k = 0; k < K; ++k) G[(size_t)r * K + k] += c * h->P_host[(size_t)s * K + k];
-      }
+    const int nout = h->thS + 2 * h->nb;
+    std::vector<double> Pbar(h->P_host.begin(), h->P_host.begin() + (size_t)h->thS * h->K);
+    std::vector<double> G;
+    ridg::fused_step_operator(2, h->nb, nu, Pbar, h->K, G);
     struct Pending { ridg::MixedOp* op; const std::vector<double>* g; int nout; };
     Pending todo[2] = {{&h->mixed, &G, nout}, {&h->mixed_pred, &h->P_host, h->thT}};
     for (auto& p : todo) {

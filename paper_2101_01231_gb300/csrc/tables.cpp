@@ -304,4 +304,35 @@ bool linear_operator(int dim, int M, const double* nu, const RegionBox& box,
   return true;
 }
 
+void fused_step_operator(int dim, int nb, const double* nu, const std::vector<double>& Pbar,
+                         int K, std::vector<double>& G) {
+  const Tables1D t1 = tables1d(nb);
+  int thS = 1, NT = 1;
+  for (int d = 0; d < dim; ++d) thS *= nb;
+  NT = thS / nb;  // lines of modes along a direction
+  const int nout = thS + dim * NT;
+  std::vector<double> C((size_t)nout * thS, 0.0);
+  for (int d = 0; d < dim; ++d) {
+    int st = 1;
+    for (int e = 0; e < d; ++e) st *= nb;
+    for (int s = 0; s < thS; ++s) {
+      const int ad = (s / st) % nb, base = s - ad * st;
+      for (int b = 0; b < nb; ++b) C[(size_t)s * thS + base + b * st] += nu[d] * t1.D[ad * nb + b];
+    }
+    const std::vector<double>& tr = nu[d] >= 0 ? t1.ep : t1.em;
+    for (int t = 0; t < NT; ++t) {
+      // line t: the modes with the other indices fixed; its first mode (index 0 along d)
+      const int base = (t % st) + (t / st) * st * nb;
+      for (int b = 0; b < nb; ++b) C[(size_t)(thS + d * NT + t) * thS + base + b * st] = nu[d] * tr[b];
+    }
+  }
+  G.assign((size_t)nout * K, 0.0);
+  for (int r = 0; r < nout; ++r)
+    for (int s = 0; s < thS; ++s) {
+      const double c = C[(size_t)r * thS + s];
+      if (c == 0.0) continue;
+      for (int k = 0; k < K; ++k) G[(size_t)r * K + k] += c * Pbar[(size_t)s * K + k];
+    }
+}
+
 }  // namespace ridg

@@ -44,6 +44,17 @@ RegionBox upwind_box(int dim, const double* vel);
 bool linear_operator(int dim, int M, const double* nu, const RegionBox& box,
                      std::vector<double>& P);
 
+// The fused step operator G = C P-bar of the mixed path (dim 2 or 3): C maps a cell's time
+// mean W-bar (theta_S modes, x fastest) to the correction's linear functionals of it --
+// rows 0 .. theta_S - 1 the volume term sum_d nu_d (D along d) W-bar (Sec. 2.3), then per
+// direction d and line t of the nb^(dim-1) lines of modes along d (the other indices, the
+// lower one fastest) the upwind trace nu_d tr(W-bar) on the cell's downstream d-face
+// (phi_b(+1) for nu_d >= 0, phi_b(-1) for nu_d < 0): row theta_S + d nb^(dim-1) + t.  Pbar
+// holds the theta_S time-mean rows of the prediction operator (theta_S x K); G gets
+// (theta_S + dim nb^(dim-1)) x K.
+void fused_step_operator(int dim, int nb, const double* nu, const std::vector<double>& Pbar,
+                         int K, std::vector<double>& G);
+
 // Dense LU with partial pivoting, in place (row-major n x n); perm[i] = original row of
 // row i of the factors.  Returns false on a zero pivot.
 bool lu_factor(int n, double* A, std::vector<int>& perm);

@@ -36,11 +36,11 @@ def exe(tmp_path_factory):
     return out
 
 
-def _operator(exe, d, M, nu, tmp_path):
+def _operator(exe, d, M, nu, tmp_path, fused=False):
     path = str(tmp_path / "P.txt")
     nu3 = list(nu) + [0.0] * (3 - len(nu))
-    subprocess.run([exe, str(d), str(M)] + [repr(float(v)) for v in nu3] + [path], check=True,
-                   capture_output=True)
+    subprocess.run([exe, str(d), str(M)] + [repr(float(v)) for v in nu3] + [path]
+                   + (["fused"] if fused else []), check=True, capture_output=True)
     lines = open(path).read().split()
     lo, cnt = [int(v) for v in lines[0:3]], [int(v) for v in lines[3:6]]
     n, size = int(lines[6]), int(lines[7])
@@ -157,3 +157,66 @@ def test_3d_cfl_readings(exe, tmp_path):
                        for th in itertools.product(grid, repeat=3))
     assert rho[0.6] > 1.03, rho
     assert rho[0.2] <= 1.0 + 1e-10, rho
+
+
+FUSED_CASES = [
+    (2, 3, (0.35, 0.175)), (2, 2, (-0.3, 0.2)), (2, 1, (0.0, -0.4)),
+    (3, 2, (0.3, -0.21, 0.09)), (3, 1, (-0.2, 0.0, 0.25)), (3, 2, (0.0, 0.3, -0.2)),
+]
+
+
+@pytest.mark.parametrize("d,M,nu", FUSED_CASES)
+def test_fused_step_operator_reproduces_oracle_step(exe, d, M, nu, tmp_path):
+    """The mixed path's fused step operator (host-built G = C P-bar: the volume term and,
+    per direction and line of modes, the cell's upwind trace on its downstream face), applied
+    to every cell's upwind box and assembled into the update the way the correction kernels
+    do it -- F(i - 1/2) the upstream cell's trace output, F(i + 1/2) this cell's (the other
+    way round for a negative velocity), mode a of a line getting phi_a(+1) ((-1)^a F(i - 1/2)
+    - F(i + 1/2)) -- gives the oracle's step (its region solves and correction)."""
+    lo, cnt, n, G = _operator(exe, d, M, nu, tmp_path, fused=True)
+    nb = M + 1
+    thS, NT = nb ** d, nb ** (d - 1)
+    G = G.reshape(thS + d * NT, n * thS)
+    mesh = (5, 4) if d == 2 else (4, 3, 3)
+    n3 = list(mesh) + [1] * (3 - d)
+    vel = [nu[k] / mesh[k] for k in range(d)] + [0.0] * (3 - d)   # nu = vel dt / h at dt = 1
+    w = dict(flux="advection", dim=d, n=mesh, M=M, vel=tuple(vel), lo=(0.0,) * 3,
+             hi=(1.0,) * 3)
+    cells = int(np.prod(mesh))
+    Q = np.random.default_rng(5).standard_normal((cells, thS))
+
+    def cell(x, y, z):
+        return (x % n3[0]) + n3[0] * ((y % n3[1]) + n3[1] * (z % n3[2]))
+
+    box = [(lo[0] + i % cnt[0], lo[1] + (i // cnt[0]) % cnt[1], lo[2] + i // (cnt[0] * cnt[1]))
+           for i in range(n)]
+    Y = np.zeros((cells, G.shape[0]))
+    for z in range(n3[2]):
+        for y in range(n3[1]):
+            for x in range(n3[0]):
+                X = np.concatenate([Q[cell(x + o[0], y + o[1], z + o[2])] for o in box])
+                Y[cell(x, y, z)] = G @ X
+    ep = basis.trace_plus(nb)
+    out = Q.copy()
+    for z in range(n3[2]):
+        for y in range(n3[1]):
+            for x in range(n3[0]):
+                e = cell(x, y, z)
+                dq = Y[e, :thS].copy()
+                for dd in range(d):
+                    if nu[dd] == 0.0:
+                        continue
+                    step = [0, 0, 0]
+                    step[dd] = -1 if nu[dd] > 0 else 1
+                    up = cell(x + step[0], y + step[1], z + step[2])
+                    st = nb ** dd
+                    for t in range(NT):
+                        base = (t % st) + (t // st) * st * nb
+                        fo = Y[e, thS + dd * NT + t]
+                        fu = Y[up, thS + dd * NT + t]
+                        fm, fp = (fu, fo) if nu[dd] > 0 else (fo, fu)
+                        for a in range(nb):
+                            dq[base + a * st] += ep[a] * ((-1) ** a * fm - fp)
+                out[e] += dq
+    ref = OL.step(Q, w, 1.0)
+    assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
